@@ -1,0 +1,304 @@
+"""FP64 CPU oracle of the NNP energy/force path (test infrastructure only).
+
+Only the test suite, ``__graft_entry__.smoke()`` and the benchmark's CPU
+baseline may import this package.  The product library never loads it and
+shares no code with it.
+
+The arithmetic lives in ``nnp_oracle.c`` (plain C, double precision,
+single-threaded); this module compiles it with gcc on first use and wraps it
+with ctypes.  Descriptor constants are this module's own copy of the readings
+of the ANI descriptor (radial: 16 shifts 0.9 + 0.26875 m, eta 16, cutoff
+5.2 A; angular: 4 shifts 0.9 + 0.65 a, eta 8, zeta 32, sectors
+(2z + 1) pi / 16, cutoff 3.5 A; CELU alpha 0.1).
+
+Parity status per function
+--------------------------
+pairs_brute / pairs_cells : pinned (lattice shell counts, brute force = cells)
+aev                        : pinned (closed forms of special geometries,
+                             invariances, block placement)
+mlp                        : pinned (torch.nn.functional library routines)
+energy_forces              : pinned (finite differences, sum F = 0,
+                             translation / rotation / permutation invariance)
+aev_jvp, force_match       : pinned (finite differences in positions and in
+                             weights)
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "nnp_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+MAX_SPECIES = 8
+MAX_SHF = 32
+MAX_LAYERS = 8
+
+
+def build(force: bool = False) -> str:
+    """Compile nnp_oracle.c into liboracle.so (no fast-math: FP64 as written)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-shared",
+                               "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Model(ctypes.Structure):
+    _fields_ = [
+        ("n_species", ctypes.c_int),
+        ("n_rad", ctypes.c_int),
+        ("n_ang_r", ctypes.c_int),
+        ("n_ang_z", ctypes.c_int),
+        ("rc_r", ctypes.c_double), ("eta_r", ctypes.c_double),
+        ("rc_a", ctypes.c_double), ("eta_a", ctypes.c_double),
+        ("zeta", ctypes.c_double),
+        ("shf_r", ctypes.c_double * MAX_SHF),
+        ("shf_a", ctypes.c_double * MAX_SHF),
+        ("shf_z", ctypes.c_double * MAX_SHF),
+        ("n_layers", ctypes.c_int),
+        ("width", ctypes.c_int * (MAX_LAYERS + 1)),
+        ("celu_alpha", ctypes.c_double),
+        ("W", ctypes.POINTER(ctypes.c_double) * (MAX_SPECIES * MAX_LAYERS)),
+        ("b", ctypes.POINTER(ctypes.c_double) * (MAX_SPECIES * MAX_LAYERS)),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        L.or_pairs_brute.restype = ctypes.c_long
+        L.or_pairs_brute.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_long, ip, ip, dp]
+        L.or_pairs_cells.restype = ctypes.c_long
+        L.or_pairs_cells.argtypes = L.or_pairs_brute.argtypes
+        L.or_aev_length.restype = ctypes.c_int
+        L.or_aev.argtypes = [ctypes.POINTER(_Model), ctypes.c_int, ip, ctypes.c_long, ip, ip, dp, dp]
+        L.or_mlp.restype = ctypes.c_double
+        L.or_mlp.argtypes = [ctypes.POINTER(_Model), ctypes.c_int, dp, dp]
+        L.or_energy_forces.argtypes = [ctypes.POINTER(_Model), ctypes.c_int, dp, ip, dp, dp, dp, dp, dp]
+        L.or_energy_forces_subset.argtypes = [ctypes.POINTER(_Model), ctypes.c_int, dp, ip, dp,
+                                              ctypes.c_int, ip, dp, ctypes.c_int, ip, dp]
+        L.or_aev_jvp.argtypes = [ctypes.POINTER(_Model), ctypes.c_int, dp, ip, dp, dp, dp]
+        L.or_force_match.argtypes = [ctypes.POINTER(_Model), ctypes.c_int, dp, ip, dp, dp, dp,
+                                     ctypes.POINTER(dp), ctypes.POINTER(dp), dp]
+        L.or_pair_index.restype = ctypes.c_int
+        L.or_pair_index.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+@dataclass
+class Params:
+    """Descriptor and network hyper-parameters (the oracle's own copy)."""
+    atomic_numbers: tuple = (1, 8)
+    rc_r: float = 5.2
+    eta_r: float = 16.0
+    shf_r: tuple = tuple(0.9 + 0.26875 * m for m in range(16))
+    rc_a: float = 3.5
+    eta_a: float = 8.0
+    zeta: float = 32.0
+    shf_a: tuple = tuple(0.9 + 0.65 * a for a in range(4))
+    shf_z: tuple = tuple((2 * z + 1) * math.pi / 16 for z in range(8))
+    hidden: tuple = (160, 128, 96)
+    celu_alpha: float = 0.1
+
+    @property
+    def n_species(self) -> int:
+        return len(self.atomic_numbers)
+
+    @property
+    def aev_length(self) -> int:
+        S = self.n_species
+        return len(self.shf_r) * S + len(self.shf_a) * len(self.shf_z) * S * (S + 1) // 2
+
+    def species_of(self, Z) -> np.ndarray:
+        """Z -> species index in ascending-Z order; unknown Z raises."""
+        order = sorted(self.atomic_numbers)
+        lut = {z: k for k, z in enumerate(order)}
+        try:
+            return np.array([lut[int(z)] for z in np.asarray(Z)], dtype=np.int32)
+        except KeyError as e:
+            raise ValueError(f"unknown atomic number {e}") from None
+
+
+class Model:
+    """Parameters plus per-species weights [(W1,b1),...,(W4,b4)] (W: in x out)."""
+
+    def __init__(self, params: Params, weights):
+        self.p = params
+        S = params.n_species
+        if len(weights) != S:
+            raise ValueError("need one weight set per species")
+        self._keep = []
+        m = _Model()
+        m.n_species = S
+        m.n_rad = len(params.shf_r)
+        m.n_ang_r = len(params.shf_a)
+        m.n_ang_z = len(params.shf_z)
+        m.rc_r, m.eta_r = params.rc_r, params.eta_r
+        m.rc_a, m.eta_a, m.zeta = params.rc_a, params.eta_a, params.zeta
+        for k, v in enumerate(params.shf_r):
+            m.shf_r[k] = v
+        for k, v in enumerate(params.shf_a):
+            m.shf_a[k] = v
+        for k, v in enumerate(params.shf_z):
+            m.shf_z[k] = v
+        widths = (params.aev_length,) + tuple(params.hidden) + (1,)
+        m.n_layers = len(widths) - 1
+        for k, w in enumerate(widths):
+            m.width[k] = w
+        m.celu_alpha = params.celu_alpha
+        for s in range(S):
+            if len(weights[s]) != m.n_layers:
+                raise ValueError("wrong number of layers")
+            for l, (W, b) in enumerate(weights[s]):
+                W = np.ascontiguousarray(W, dtype=np.float64)
+                b = np.ascontiguousarray(b, dtype=np.float64).reshape(-1)
+                if W.shape != (widths[l], widths[l + 1]) or b.shape != (widths[l + 1],):
+                    raise ValueError(f"layer {l} of species {s} has shape {W.shape}")
+                self._keep += [W, b]
+                m.W[s * MAX_LAYERS + l] = _dp(W)
+                m.b[s * MAX_LAYERS + l] = _dp(b)
+        self.widths = widths
+        self.weights = weights
+        self._m = m
+
+    @property
+    def ref(self):
+        return ctypes.byref(self._m)
+
+
+def _pairs(fn, pos, box, rc):
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    n = pos.shape[0]
+    bx = None if box is None else np.ascontiguousarray(box, dtype=np.float64)
+    cap = max(16, n * 128)
+    while True:
+        pi = np.empty(cap, np.int32)
+        pj = np.empty(cap, np.int32)
+        pd = np.empty((cap, 3), np.float64)
+        cnt = fn(n, _dp(pos), None if bx is None else _dp(bx), rc, cap, _ip(pi), _ip(pj), _dp(pd))
+        if cnt <= cap:
+            return pi[:cnt].copy(), pj[:cnt].copy(), pd[:cnt].copy()
+        cap = int(cnt)
+
+
+def pairs_brute(pos, box, rc):
+    """(i, j, d) of every pair/image within rc, brute force over images."""
+    return _pairs(lib().or_pairs_brute, pos, box, rc)
+
+
+def pairs_cells(pos, box, rc):
+    """Same set as pairs_brute, through a cell list."""
+    return _pairs(lib().or_pairs_cells, pos, box, rc)
+
+
+def pair_index(S, s1, s2) -> int:
+    return lib().or_pair_index(S, s1, s2)
+
+
+def aev(model: Model, species, pairs) -> np.ndarray:
+    pi, pj, pd = pairs
+    species = np.ascontiguousarray(species, dtype=np.int32)
+    n = species.shape[0]
+    G = np.zeros((n, model.p.aev_length))
+    lib().or_aev(model.ref, n, _ip(species), len(pi), _ip(np.ascontiguousarray(pi)),
+                 _ip(np.ascontiguousarray(pj)), _dp(np.ascontiguousarray(pd)), _dp(G))
+    return G
+
+
+def mlp(model: Model, s: int, x) -> tuple[float, np.ndarray]:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    dx = np.zeros_like(x)
+    e = lib().or_mlp(model.ref, int(s), _dp(x), _dp(dx))
+    return e, dx
+
+
+def energy_forces(model: Model, pos, species, box):
+    """E (float), Ei (n,), F (n,3), G (n,D)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    species = np.ascontiguousarray(species, dtype=np.int32)
+    n = pos.shape[0]
+    bx = None if box is None else np.ascontiguousarray(box, dtype=np.float64)
+    E = np.zeros(1)
+    Ei = np.zeros(n)
+    F = np.zeros((n, 3))
+    G = np.zeros((n, model.p.aev_length))
+    lib().or_energy_forces(model.ref, n, _dp(pos), _ip(species),
+                           None if bx is None else _dp(bx), _dp(E), _dp(Ei), _dp(F), _dp(G))
+    return float(E[0]), Ei, F, G
+
+
+def energy_forces_subset(model: Model, pos, species, box, sel_e, sel_f):
+    """E_i for atoms sel_e and F_j for atoms sel_f of a (large) system, each
+    by the same definition as energy_forces."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    species = np.ascontiguousarray(species, dtype=np.int32)
+    sel_e = np.ascontiguousarray(sel_e, dtype=np.int32)
+    sel_f = np.ascontiguousarray(sel_f, dtype=np.int32)
+    n = pos.shape[0]
+    bx = None if box is None else np.ascontiguousarray(box, dtype=np.float64)
+    Ei = np.zeros(len(sel_e))
+    F = np.zeros((len(sel_f), 3))
+    lib().or_energy_forces_subset(model.ref, n, _dp(pos), _ip(species),
+                                  None if bx is None else _dp(bx), len(sel_e), _ip(sel_e),
+                                  _dp(Ei), len(sel_f), _ip(sel_f), _dp(F))
+    return Ei, F
+
+
+def aev_jvp(model: Model, pos, species, box, v) -> np.ndarray:
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    species = np.ascontiguousarray(species, dtype=np.int32)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    n = pos.shape[0]
+    bx = None if box is None else np.ascontiguousarray(box, dtype=np.float64)
+    T = np.zeros((n, model.p.aev_length))
+    lib().or_aev_jvp(model.ref, n, _dp(pos), _ip(species),
+                     None if bx is None else _dp(bx), _dp(v), _dp(T))
+    return T
+
+
+def force_match(model: Model, pos, species, box, Fref):
+    """L, dW (list per species of per-layer arrays), db (same), F."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    species = np.ascontiguousarray(species, dtype=np.int32)
+    Fref = np.ascontiguousarray(Fref, dtype=np.float64)
+    n = pos.shape[0]
+    bx = None if box is None else np.ascontiguousarray(box, dtype=np.float64)
+    S = model.p.n_species
+    dW = [[np.zeros_like(np.asarray(W, dtype=np.float64)) for W, _ in model.weights[s]]
+          for s in range(S)]
+    db = [[np.zeros(np.asarray(b).reshape(-1).shape[0]) for _, b in model.weights[s]]
+          for s in range(S)]
+    PW = (ctypes.POINTER(ctypes.c_double) * (MAX_SPECIES * MAX_LAYERS))()
+    PB = (ctypes.POINTER(ctypes.c_double) * (MAX_SPECIES * MAX_LAYERS))()
+    for s in range(S):
+        for l in range(len(dW[s])):
+            PW[s * MAX_LAYERS + l] = _dp(dW[s][l])
+            PB[s * MAX_LAYERS + l] = _dp(db[s][l])
+    L = np.zeros(1)
+    F = np.zeros((n, 3))
+    lib().or_force_match(model.ref, n, _dp(pos), _ip(species), None if bx is None else _dp(bx),
+                         _dp(Fref), _dp(L), PW, PB, _dp(F))
+    return float(L[0]), dW, db, F
