@@ -1,0 +1,414 @@
+"""Benchmark: NNP energy+force atom-steps/s on one B300 (BF16 vs FP32 forms).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32|fp8]
+                    [--impl ours|reference] [--workload 1..5]
+
+One step = one full evaluation of the hot path (wrap + cell lists,
+neighbour lists, descriptors, per-element networks with energy sum, network
+backward, descriptor backward to forces) for the 98,304-atom water box
+(32,768 rigid waters at 1 g/cm^3, 99.4 A, seeded synthetic input) unless
+--workload says otherwise.  `value` times the device-resident path
+(graph replay through nnp_eval_async on device pointers) with CUDA events on
+the library's stream; L2 is flushed (a 256 MB write) between timed steps,
+outside the event pair.  `e2e` times nnp_eval with host NumPy buffers
+(H2D of positions and atomic numbers, D2H of energy and forces inside the
+timed region).  Multi-GPU: one independent replica per rank (the path
+needs no exchange), value = all ranks' atom-steps / max rank time.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+build) on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NNP energy+force atom-steps/s: BF16 vs FP32 form on one B300 at stated force error"
+UNIT = "atom-steps/s"
+FP32_LANES_PER_SM = 128
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
+                "sm_max_mhz": 2032.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per stage (FP32 operations, FMA = 2), see the design doc
+
+def algorithmic_flops(n_pairs_r, n_triplets, n_rows, D, S):
+    """FP32 work of the descriptor forward / backward and the network."""
+    rad_fwd = n_pairs_r * 16 * 6          # x, x^2*eta, exp, fma per term
+    ang_fwd = n_triplets * (32 * 2 + 8 * 9 + 4 * 6)
+    rad_bwd = n_pairs_r * 16 * 9
+    ang_bwd = n_triplets * (8 * 27 + 4 * 8 + 40)
+    mlp = n_rows * 2 * (2 * (D * 160 + 160 * 128 + 128 * 96) + 96)
+    return rad_fwd + ang_fwd, mlp, rad_bwd + ang_bwd
+
+
+# ---------------------------------------------------------------------------
+
+def build_workload(k):
+    import synth
+    wl = synth.workload(k)
+    S = len(wl["atomic_numbers"])
+    D = synth.aev_length(S)
+    w = synth.xavier_weights(S, D, wl["weight_seed"])
+    return wl, w, S, D
+
+
+def concat(systems):
+    off = np.cumsum([0] + [s.n for s in systems]).astype(np.int64)
+    pos = np.concatenate([s.pos for s in systems])
+    Z = np.concatenate([s.Z for s in systems]).astype(np.int32)
+    boxes = np.stack([np.diag(s.box) for s in systems])
+    return off, pos, Z, boxes
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2604_21441_b300 as P
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    wl, w, S, D = build_workload(args.workload)
+    off, pos_h, Z_h, boxes = concat(wl["systems"])
+    B = len(wl["systems"])
+    n = int(off[-1])
+    stream = torch.cuda.Stream(device=dev)
+    w32 = [[(W.astype(np.float32), b.astype(np.float32)) for W, b in sp] for sp in w]
+
+    def make(prec, flags=0):
+        pot = P.NNP(atomic_numbers=wl["atomic_numbers"], precision=prec, max_atoms=n,
+                    max_systems=B, stream=stream, flags=flags)
+        pot.set_all_weights(w32)
+        return pot
+
+    pos = torch.tensor(pos_h, device=dev)
+    Z = torch.tensor(Z_h, device=dev)
+    E = torch.zeros(B, dtype=torch.float64, device=dev)
+    F = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step_async(pot):
+        if B == 1:
+            pot.eval_into(pos, Z, boxes[0], E, F, sync=False)
+        else:
+            pot._check(pot._L.nnp_eval_batch(
+                pot._h, B, P.ctypes.c_void_p(off.ctypes.data), P.ctypes.c_void_p(pos.data_ptr()),
+                P.ctypes.c_void_p(Z.data_ptr()), P.ctypes.c_void_p(boxes.ctypes.data),
+                P.ctypes.c_void_p(E.data_ptr()), P.ctypes.c_void_p(F.data_ptr())))
+
+    def timed(pot, K, W, stage=False):
+        for _ in range(W):
+            step_async(pot)
+            pot.sync()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        stages = []
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            for k in range(K):
+                flush.zero_()
+                starts[k].record(stream)
+                step_async(pot)
+                ends[k].record(stream)
+                if stage:
+                    stages.append(pot.profile_stages())
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        pot.sync()
+        ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        return ms, stages
+
+    forms = {}
+    prec_list = [args.precision] + [p for p in ("fp32", "bf16", "fp8")
+                                    if p != args.precision and p in args.compare]
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    main = None
+    for prec in prec_list:
+        try:
+            pot = make(prec)
+        except P.NNPError as e:
+            forms[prec] = {"unavailable": str(e)}
+            if prec == args.precision:
+                raise
+            continue
+        ms, _ = timed(pot, args.steps, args.warmup)
+        t = float(np.sum(ms)) / 1e3
+        forms[prec] = {"value": n * args.steps / t, "ms_per_step": float(np.mean(ms)),
+                       "ms_p10": float(np.percentile(ms, 10)), "ms_p90": float(np.percentile(ms, 90))}
+        if prec == args.precision:
+            main = (pot, ms)
+        else:
+            pot.close()
+    clk = clocks.stop()
+    pot, ms = main
+    # per-stage durations (instrumented graph, same protocol)
+    spot = make(args.precision, flags=P.FLAG_STAGE_EVENTS)
+    _, stages = timed(spot, max(3, min(args.steps, 20)), 2, stage=True)
+    stage_ms = np.mean(np.array(stages), axis=0)
+    nbr_r = spot.query("max_nbr")
+    spot.close()
+    # e2e through host buffers
+    Eh = np.zeros(B)
+    Fh = np.zeros((n, 3))
+    for _ in range(2):
+        if B == 1:
+            pot.eval(pos_h, Z_h, boxes[0])
+        else:
+            pot.eval_batch(off, pos_h, Z_h, boxes)
+    t0 = time.perf_counter()
+    K_e2e = max(3, args.steps // 2)
+    for _ in range(K_e2e):
+        if B == 1:
+            e_, f_ = pot.eval(pos_h, Z_h, boxes[0])
+        else:
+            e_, f_ = pot.eval_batch(off, pos_h, Z_h, boxes)
+    t_e2e = time.perf_counter() - t0
+    launches = pot.query("launches_per_eval")
+    return dict(n=n, B=B, S=S, D=D, ms=ms, forms=forms, clocks=clk, stage_ms=stage_ms.tolist(),
+                e2e=n * K_e2e / t_e2e, e2e_ms=t_e2e / K_e2e * 1e3, launches=launches,
+                wl=wl, pot=pot, pos_h=pos_h, Z_h=Z_h, boxes=boxes, w=w)
+
+
+def oracle_sample(wl, w, seconds=20.0, seed=0):
+    """Time the FP64 oracle on bounded samples of the workload: sampled atoms
+    get E_i and F_i, which evaluates them and every atom within the radial
+    cutoff of them.  Returns (atoms evaluated per second, description)."""
+    import oracle
+    S = len(wl["atomic_numbers"])
+    p = oracle.Params(atomic_numbers=tuple(wl["atomic_numbers"]))
+    m = oracle.Model(p, w)
+    s = wl["systems"][0]
+    sp = p.species_of(s.Z)
+    rng = np.random.default_rng(seed)
+    evaluated, t_tot, calls = 0, 0.0, 0
+    from scipy.spatial import cKDTree
+    tree = cKDTree(np.mod(s.pos, s.box[0]), boxsize=s.box[0])
+    while t_tot < seconds:
+        sel = np.sort(rng.choice(s.n, 4, replace=False))
+        need = set(sel.tolist())
+        for i in sel:
+            need.update(tree.query_ball_point(np.mod(s.pos[i], s.box[0]), p.rc_r))
+        t0 = time.perf_counter()
+        oracle.energy_forces_subset(m, s.pos, sp, s.box, sel, sel)
+        t_tot += time.perf_counter() - t0
+        evaluated += len(need)
+        calls += 1
+    desc = (f"{calls} oracle calls on the {s.n}-atom box, each E_i and F_i of 4 random atoms "
+            f"(fully evaluates them and their radial neighbours: {evaluated} atom evaluations, "
+            f"plus the O(N) pair search per call), {t_tot:.1f} s single-threaded FP64")
+    return evaluated / t_tot, desc, calls, t_tot
+
+
+def run_reference(args):
+    wl, w, S, D = build_workload(args.workload)
+    n = sum(s.n for s in wl["systems"])
+    for k in range(args.warmup):
+        oracle_sample(wl, w, seconds=0.5, seed=1000 + k)
+    vals = []
+    t_all = 0.0
+    descs = []
+    for k in range(args.steps):
+        v, d, calls, t = oracle_sample(wl, w, seconds=args.ref_seconds, seed=k)
+        vals.append(v)
+        t_all += t
+        descs.append(d)
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": n / value * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "atoms": n, "note": "FP64 CPU oracle, 1 thread"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": descs[0]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"])
+    ap.add_argument("--compare", default="fp32,bf16,fp8")
+    ap.add_argument("--workload", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=8.0)
+    args = ap.parse_args()
+    args.compare = args.compare.split(",")
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    r = run_ours(args, rank, world, local_rank)
+    t_rank = float(np.sum(r["ms"])) / 1e3
+    total_atoms = r["n"] * args.steps
+    if world > 1:
+        tt = torch.tensor([t_rank, float(total_atoms)], dtype=torch.float64, device="cuda")
+        tmax = tt[:1].clone()
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        tsum = tt[1:].clone()
+        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
+        t_rank, total_atoms = float(tmax.item()), float(tsum.item())
+    value = total_atoms / t_rank
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    pk, pk_kind = peaks()
+    names = ["cells", "neighbours", "descriptor", "network", "descriptor_backward"]
+    st = dict(zip(names, r["stage_ms"]))
+    # algorithmic work (counted from the workload's neighbour statistics)
+    n_pairs, n_trip = neighbour_stats(r)
+    fl_desc, fl_mlp, fl_bwd = algorithmic_flops(n_pairs, n_trip, r["n"], r["D"], r["S"])
+    sm_mhz_max = pk.get("sm_max_mhz", 2032.0)
+    alu_peak = 148 * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12  # TFLOP/s FP32
+    work = {"descriptor": (fl_desc, "alu"), "descriptor_backward": (fl_bwd, "alu"),
+            "network": (fl_mlp, "tensor" if args.precision != "fp32" else "alu")}
+    dom = max(work, key=lambda k: st[k])
+    fl, bound = work[dom]
+    achieved = fl / (st[dom] * 1e-3) / 1e12
+    if bound == "tensor":
+        peak = pk["bf16_tflops"] * (2.0 if args.precision == "fp8" else 1.0)
+    else:
+        peak = alu_peak
+    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": (f"{pk_kind} bf16" if bound == "tensor" else
+                                "148 SMs x 128 FP32 lanes x 2 x max SM clock"),
+                "stage_ms": st}
+    cpu_v, cpu_desc, _, _ = oracle_sample(r["wl"], r["w"], seconds=args.cpu_seconds)
+    ms_mean = float(np.mean(r["ms"]))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_mean, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else
+        ("bf16" if args.precision == "bf16" else "fp8-e4m3"),
+        "data": "synthetic (seeded water boxes, random Xavier weights)",
+        "config": {"workload": r["wl"]["name"], "atoms": r["n"], "systems": r["B"],
+                   "species": r["S"], "aev_length": r["D"], "precision": args.precision,
+                   "l2": "flushed (256 MB write) between timed steps, outside the timed events",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "forms": r["forms"],
+        "e2e": {"value": r["e2e"], "unit": UNIT, "ms_per_step": r["e2e_ms"],
+                "h2d_bytes_per_step": r["n"] * (24 + 4), "d2h_bytes_per_step": r["n"] * 24 + 8 * r["B"]},
+        "gpu_launches": int(r["launches"]) * args.steps,
+        "clocks": r["clocks"],
+        "roofline": roofline,
+        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": cpu_desc},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def neighbour_stats(r):
+    """Radial pairs and angular triplets of the workload (from the inputs)."""
+    from scipy.spatial import cKDTree
+    pairs, trip = 0, 0
+    for s in r["wl"]["systems"]:
+        L = s.box[0]
+        tree = cKDTree(np.mod(s.pos, L), boxsize=L)
+        pairs += 2 * len(tree.query_pairs(5.2, output_type="ndarray"))
+        na = np.zeros(s.n, dtype=np.int64)
+        pa = tree.query_pairs(3.5, output_type="ndarray")
+        np.add.at(na, pa[:, 0], 1)
+        np.add.at(na, pa[:, 1], 1)
+        trip += int((na * (na - 1) // 2).sum())
+    return pairs, trip
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * nnp.h -- C ABI of libnnp: energy and forces of an ANI-style neural-network
+ * potential on one B300 GPU (sm_103a).
+ *
+ * What the library computes.  The machine-learning part of an ML/MM energy,
+ * E_ML({r_i}, {Z_i}) (paper, Theory, Eq. 1), for the atoms handed to it, and
+ * the forces F_i = -dE_ML/dr_i (Eq. 2).  Inputs are the ones the paper's
+ * interface gives a model (Methods, "The nnpot Interface in GROMACS"):
+ * atomic numbers, positions and the periodic box.  E_ML = sum_i E_i with
+ * E_i = MLP_{s_i}(G_i): G_i is the ANI atomic environment vector (radial and
+ * angular symmetry functions with cosine cutoffs) and MLP_s a per-element
+ * network D -> h1 -> h2 -> h3 -> 1 with CELU activations.
+ *
+ * Units: Angstrom, eV, eV/Angstrom.  Unit conversion (GROMACS uses nm and
+ * kJ/mol) is the caller's job.
+ *
+ * Threading and streams.  A context is not thread-safe; use one context per
+ * host thread / CUDA stream.  All work runs on the context's stream.
+ *
+ * Pointers.  Arrays of positions, atomic numbers, energies and forces may be
+ * host or device pointers (detected with cudaPointerGetAttributes).  Host
+ * pointers are staged through pinned buffers; device pointers are read and
+ * written in place.  Boxes are always host pointers.  The caller owns every
+ * pointer it passes; the library never keeps one after a call returns.
+ *
+ * Errors.  Every call returns an nnp_status; no exception crosses the ABI and
+ * no GPU trap is used.  nnp_last_error() gives a one-line message.  Device
+ * checks (unknown atomic number, non-finite position, neighbour-list
+ * overflow) raise flags that the synchronous calls read back; a
+ * neighbour-list overflow makes nnp_eval grow its lists and evaluate again.
+ */
+#ifndef NNP_H
+#define NNP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nnp_ctx nnp_ctx;
+
+typedef enum {
+    NNP_OK = 0,
+    NNP_ERR_INVALID_ARG = 1,     /* null pointer, n <= 0, non-finite position, bad box */
+    NNP_ERR_UNKNOWN_SPECIES = 2, /* an atomic number outside the configured species */
+    NNP_ERR_UNSUPPORTED = 3,     /* triclinic box, box edge < radial cutoff, layer sizes */
+    NNP_ERR_CAPACITY = 4,        /* neighbour lists overflowed (async path) or > max */
+    NNP_ERR_CUDA = 5,            /* a CUDA runtime call failed */
+    NNP_ERR_TIMEOUT = 6,         /* a bounded device wait expired */
+    NNP_ERR_NO_WEIGHTS = 7,      /* nnp_eval before every species had weights */
+    NNP_ERR_NO_STATE = 8         /* nnp_force_match_grad before any nnp_eval */
+} nnp_status;
+
+typedef enum {
+    NNP_FP32 = 0, /* FP32 descriptors and FP32 SIMT network (reference form) */
+    NNP_BF16 = 1, /* FP32 descriptors, network on tcgen05 tensor cores in BF16 */
+    NNP_FP8 = 2   /* as BF16, forward layers in FP8 E4M3 with per-layer scales */
+} nnp_precision;
+
+#define NNP_MAX_SPECIES 8
+#define NNP_MAX_SHIFTS 32
+
+/* Context flags */
+#define NNP_FLAG_NO_GRAPH 0x1u      /* launch kernels directly instead of a CUDA graph */
+#define NNP_FLAG_NONDETERMINISTIC_BINS 0x2u /* skip the per-cell ordering pass */
+#define NNP_FLAG_STAGE_EVENTS 0x4u  /* record CUDA events between pipeline stages */
+
+/*
+ * Model hyper-parameters and capacities.  Fill with nnp_config_init() and
+ * adjust.  The descriptor follows the ANI atomic environment vector:
+ *
+ *   radial, neighbour j of species s_j, shift m (n_rad shifts):
+ *     G_i[s_j*n_rad + m] += 1/4 exp(-eta_r (r_ij - shf_r[m])^2) fc(r_ij; rc_r)
+ *   angular, unordered neighbour pair {j,k} within rc_a, shift a, sector z:
+ *     G_i[n_rad*S + p(s_j,s_k)*n_ang_r*n_ang_z + a*n_ang_z + z] +=
+ *       2^(1-zeta) (1 + cos(arccos(0.95 cos theta_ijk) - shf_z[z]))^zeta
+ *       * exp(-eta_a ((r_ij + r_ik)/2 - shf_a[a])^2) fc(r_ij; rc_a) fc(r_ik; rc_a)
+ *   fc(r; rc) = (cos(pi r / rc) + 1) / 2 for r < rc, else 0;
+ *   p(s1, s2) = row-major index of the unordered species pair (s1 <= s2).
+ *
+ * The kernels are specialised for n_rad = 16, n_ang_r = 4, n_ang_z = 8,
+ * zeta a power of two (<= 64), hidden = {160, 128, 96}, 1 <= S <= 4;
+ * other values give NNP_ERR_UNSUPPORTED.
+ */
+typedef struct {
+    int32_t n_species;                        /* S */
+    int32_t atomic_numbers[NNP_MAX_SPECIES];  /* species s has Z = atomic_numbers[s];
+                                                 must be ascending */
+    double rc_r, eta_r;
+    int32_t n_rad;
+    double shf_r[NNP_MAX_SHIFTS];
+    double rc_a, eta_a, zeta;
+    int32_t n_ang_r, n_ang_z;
+    double shf_a[NNP_MAX_SHIFTS];
+    double shf_z[NNP_MAX_SHIFTS];
+    int32_t hidden[3];
+    double celu_alpha;
+    int32_t precision;        /* nnp_precision */
+    int64_t max_atoms;        /* capacity hint (atoms over all systems); grows on demand */
+    int32_t max_systems;      /* capacity hint for nnp_eval_batch */
+    int32_t nbr_capacity;     /* radial neighbours per atom; 0 = 96; grows on overflow */
+    int32_t ang_capacity;     /* angular neighbours per atom; 0 = 32; grows on overflow */
+    void *stream;             /* cudaStream_t to run on; NULL = the library makes one */
+    uint32_t flags;           /* NNP_FLAG_* */
+} nnp_config;
+
+/* ANI-style defaults for n_species species with the given atomic numbers
+ * (ascending): radial 16 shifts 0.9 + 0.26875 m, eta_r 16, rc_r 5.2;
+ * angular 4 shifts 0.9 + 0.65 a, 8 sectors (2z+1) pi/16, eta_a 8, zeta 32,
+ * rc_a 3.5; hidden 160/128/96; CELU alpha 0.1; FP32; capacities 4096 atoms.
+ * Returns NNP_ERR_INVALID_ARG for a null cfg, S outside 1..8 or Z not
+ * ascending. */
+int nnp_config_init(nnp_config *cfg, int32_t n_species, const int32_t *atomic_numbers);
+
+/* Create a context: validates cfg, allocates device workspaces for the
+ * capacity hints, creates (or adopts) the stream.  *out receives the context
+ * or NULL on error. */
+int nnp_create(const nnp_config *cfg, nnp_ctx **out);
+
+/* Release every device and host resource of ctx (NULL is ignored). */
+void nnp_destroy(nnp_ctx *ctx);
+
+/* Message of the last error on ctx (or of the last failed nnp_create when
+ * ctx is NULL).  The string lives until the next call on ctx. */
+const char *nnp_last_error(const nnp_ctx *ctx);
+
+/* Weights of species s (index into atomic_numbers).  W[l] is row-major
+ * (fan_in x fan_out) FP32: W[0] D x h1, W[1] h1 x h2, W[2] h2 x h3,
+ * W[3] h3 x 1; b[l] has fan_out entries.  Host or device pointers; the data
+ * are copied (and rounded to BF16/FP8 for those precisions), the caller keeps
+ * ownership.  Captured graphs stay valid (weights live in fixed buffers). */
+int nnp_set_weights(nnp_ctx *ctx, int32_t species, const float *const W[4],
+                    const float *const b[4]);
+
+/* Energy and forces of one system of n atoms.
+ *   pos    n x 3 positions (Angstrom), any values (wrapped into the box);
+ *   Z      n atomic numbers;
+ *   box    9 doubles (3 x 3 row-major cell vectors, host pointer); only
+ *          orthorhombic cells (off-diagonals zero) with every edge >= rc_r
+ *          are supported; NULL = isolated system (no periodic images);
+ *   energy 1 double (eV), forces n x 3 doubles (eV/Angstrom); either may be
+ *          NULL to skip it.
+ * Synchronous: returns after the results are written. */
+int nnp_eval(nnp_ctx *ctx, int64_t n, const double *pos, const int32_t *Z,
+             const double *box, double *energy, double *forces);
+
+/* As nnp_eval, but pos, Z, energy and forces must be device pointers and
+ * the call returns without synchronising; device-side flags (unknown species,
+ * non-finite position, list overflow) are reported by the next nnp_sync(). */
+int nnp_eval_async(nnp_ctx *ctx, int64_t n, const double *pos, const int32_t *Z,
+                   const double *box, double *energy, double *forces);
+
+/* Wait for the context's stream and report device-side flags raised since
+ * the last check. */
+int nnp_sync(nnp_ctx *ctx);
+
+/* B independent systems in one pass (one CUDA graph launch).
+ *   offsets  B+1 host int64, offsets[0] = 0, system b owns atoms
+ *            [offsets[b], offsets[b+1]) of pos/Z/forces;
+ *   boxes    B x 9 host doubles (each as in nnp_eval; NULL = all isolated);
+ *   energies B doubles. */
+int nnp_eval_batch(nnp_ctx *ctx, int32_t B, const int64_t *offsets, const double *pos,
+                   const int32_t *Z, const double *boxes, double *energies, double *forces);
+
+/* Number of network parameters: S * sum_l (fan_in*fan_out + fan_out), packed
+ * per species as W1 b1 W2 b2 W3 b3 W4 b4 (each W row-major fan_in x fan_out). */
+int64_t nnp_param_count(const nnp_ctx *ctx);
+
+/* Weight gradient of a force loss.  Given v = dL/dF (n x 3, host or device,
+ * for the system of the last nnp_eval on ctx), writes
+ *   grad = dL/dtheta = sum_i v_i . dF_i/dtheta
+ * (nnp_param_count doubles, host or device, layout as above) and, if loss
+ * is non-NULL and Fref is non-NULL, sets v internally to
+ * 2 (F - Fref) / (3n) and *loss = |F - Fref|^2 / (3n) (the force-matching
+ * loss); pass v = NULL in that case.  Computed in FP32 with FP64 sums. */
+int nnp_force_match_grad(nnp_ctx *ctx, const double *v, const double *Fref, double *loss,
+                         double *grad);
+
+/* Per-atom energies E_i (eV) of the last evaluation, in input order
+ * (n doubles for nnp_eval, offsets[B] for nnp_eval_batch), host pointer.
+ * Synchronises the context's stream. */
+int nnp_atom_energies(nnp_ctx *ctx, double *out);
+
+/* Queries for tests and benchmarks. */
+typedef enum {
+    NNP_Q_LAUNCHES_PER_EVAL = 0,  /* kernels launched by one nnp_eval */
+    NNP_Q_NBR_CAPACITY = 1,       /* current radial list capacity */
+    NNP_Q_ANG_CAPACITY = 2,       /* current angular list capacity */
+    NNP_Q_MAX_NBR = 3,            /* max radial neighbours seen in the last eval */
+    NNP_Q_MAX_ANG = 4,            /* max angular neighbours seen in the last eval */
+    NNP_Q_ROWS = 5,               /* padded rows of the last eval */
+    NNP_Q_GRAPH_CAPTURES = 6      /* CUDA graphs captured so far */
+} nnp_query_key;
+
+int nnp_query(nnp_ctx *ctx, int32_t key, int64_t *value);
+
+/* Device durations (milliseconds) of the pipeline stages of the most recent
+ * evaluation, for profiling: out[k] for stage k in the order cells (wrap,
+ * bin, sort), neighbours, descriptor, network (forward, energy, backward),
+ * descriptor backward (forces).  Needs a context created with
+ * NNP_FLAG_STAGE_EVENTS (else NNP_ERR_UNSUPPORTED); waits for the stream.
+ * Writes min(n_out, 5) entries. */
+int nnp_profile_stages(nnp_ctx *ctx, double *out, int32_t n_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NNP_H */

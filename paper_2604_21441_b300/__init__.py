@@ -1,0 +1,321 @@
+"""libnnp Python binding: ANI-style neural-network-potential energy and forces
+on one B300 GPU.
+
+Thin ctypes layer over the C ABI declared in include/nnp.h.  Every step of
+an evaluation runs in the library's CUDA kernels; this module only marshals
+arguments (NumPy arrays or torch tensors, host or device) and raises on
+error codes.  There is no CPU fallback: if libnnp.so is missing the import
+fails.
+
+    from paper_2604_21441_b300 import NNP
+    pot = NNP(atomic_numbers=(1, 8), precision="fp32")
+    for s, layers in enumerate(weights):          # [(W1,b1),...,(W4,b4)]
+        pot.set_weights(s, layers)
+    E, F = pot.eval(pos, Z, box)                  # eV, eV/A
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = ["NNP", "NNPError", "lib", "LIB_PATH", "PRECISIONS", "ABI_FUNCTIONS"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnnp.so")
+
+NNP_MAX_SPECIES = 8
+NNP_MAX_SHIFTS = 32
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2}
+FLAG_NO_GRAPH = 0x1
+FLAG_NONDETERMINISTIC_BINS = 0x2
+FLAG_STAGE_EVENTS = 0x4
+STAGES = ("cells", "neighbours", "descriptor", "network", "descriptor_backward")
+
+# Every entry point declared in include/nnp.h.
+ABI_FUNCTIONS = ("nnp_config_init", "nnp_create", "nnp_destroy", "nnp_last_error",
+                 "nnp_set_weights", "nnp_eval", "nnp_eval_async", "nnp_sync",
+                 "nnp_eval_batch", "nnp_param_count", "nnp_force_match_grad", "nnp_query",
+                 "nnp_profile_stages", "nnp_atom_energies")
+
+QUERY = {"launches_per_eval": 0, "nbr_capacity": 1, "ang_capacity": 2, "max_nbr": 3,
+         "max_ang": 4, "rows": 5, "graph_captures": 6}
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNKNOWN_SPECIES", 3: "UNSUPPORTED", 4: "CAPACITY",
+          5: "CUDA", 6: "TIMEOUT", 7: "NO_WEIGHTS", 8: "NO_STATE"}
+
+
+class NNPError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libnnp {STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("n_species", ctypes.c_int32),
+        ("atomic_numbers", ctypes.c_int32 * NNP_MAX_SPECIES),
+        ("rc_r", ctypes.c_double), ("eta_r", ctypes.c_double),
+        ("n_rad", ctypes.c_int32),
+        ("shf_r", ctypes.c_double * NNP_MAX_SHIFTS),
+        ("rc_a", ctypes.c_double), ("eta_a", ctypes.c_double), ("zeta", ctypes.c_double),
+        ("n_ang_r", ctypes.c_int32), ("n_ang_z", ctypes.c_int32),
+        ("shf_a", ctypes.c_double * NNP_MAX_SHIFTS),
+        ("shf_z", ctypes.c_double * NNP_MAX_SHIFTS),
+        ("hidden", ctypes.c_int32 * 3),
+        ("celu_alpha", ctypes.c_double),
+        ("precision", ctypes.c_int32),
+        ("max_atoms", ctypes.c_int64),
+        ("max_systems", ctypes.c_int32),
+        ("nbr_capacity", ctypes.c_int32),
+        ("ang_capacity", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+        ("flags", ctypes.c_uint32),
+    ]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libnnp.so (built in-tree by paper_2604_21441_b300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_2604_21441_b300.build` (no CPU fallback exists)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+    L.nnp_config_init.argtypes = [ctypes.POINTER(Config), i32, ctypes.POINTER(i32)]
+    L.nnp_config_init.restype = ctypes.c_int
+    L.nnp_create.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(vp)]
+    L.nnp_create.restype = ctypes.c_int
+    L.nnp_destroy.argtypes = [vp]
+    L.nnp_destroy.restype = None
+    L.nnp_last_error.argtypes = [vp]
+    L.nnp_last_error.restype = ctypes.c_char_p
+    L.nnp_set_weights.argtypes = [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    L.nnp_set_weights.restype = ctypes.c_int
+    L.nnp_eval.argtypes = [vp, i64, dp, dp, dp, dp, dp]
+    L.nnp_eval.restype = ctypes.c_int
+    L.nnp_eval_async.argtypes = [vp, i64, dp, dp, dp, dp, dp]
+    L.nnp_eval_async.restype = ctypes.c_int
+    L.nnp_sync.argtypes = [vp]
+    L.nnp_sync.restype = ctypes.c_int
+    L.nnp_eval_batch.argtypes = [vp, i32, dp, dp, dp, dp, dp, dp]
+    L.nnp_eval_batch.restype = ctypes.c_int
+    L.nnp_param_count.argtypes = [vp]
+    L.nnp_param_count.restype = i64
+    L.nnp_force_match_grad.argtypes = [vp, dp, dp, dp, dp]
+    L.nnp_force_match_grad.restype = ctypes.c_int
+    L.nnp_query.argtypes = [vp, i32, ctypes.POINTER(i64)]
+    L.nnp_query.restype = ctypes.c_int
+    L.nnp_profile_stages.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32]
+    L.nnp_profile_stages.restype = ctypes.c_int
+    L.nnp_atom_energies.argtypes = [vp, dp]
+    L.nnp_atom_energies.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype):
+    """(pointer, keepalive) of a contiguous array of the given numpy dtype."""
+    if x is None:
+        return None, None
+    if _is_torch(x):
+        import torch
+        tdt = {np.float64: torch.float64, np.int32: torch.int32, np.float32: torch.float32}[dtype]
+        if x.dtype != tdt or not x.is_contiguous():
+            x = x.to(tdt).contiguous()
+        return ctypes.c_void_p(x.data_ptr()), x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return ctypes.c_void_p(a.ctypes.data), a
+
+
+def _box9(box):
+    """None, 3 edge lengths or a 3x3 cell -> host float64[9] (or None)."""
+    if box is None:
+        return None
+    b = box.detach().cpu().numpy() if _is_torch(box) else np.asarray(box)
+    b = np.asarray(b, dtype=np.float64)
+    if b.shape == (3,):
+        b = np.diag(b)
+    return np.ascontiguousarray(b.reshape(-1), dtype=np.float64)
+
+
+class NNP:
+    """One libnnp context (one CUDA stream)."""
+
+    def __init__(self, atomic_numbers=(1, 8), precision: str = "fp32", max_atoms: int = 4096,
+                 max_systems: int = 1, stream=None, flags: int = 0, **overrides):
+        L = lib()
+        self._L = L
+        zs = (ctypes.c_int32 * NNP_MAX_SPECIES)(*atomic_numbers)
+        cfg = Config()
+        rc = L.nnp_config_init(ctypes.byref(cfg), len(atomic_numbers), zs)
+        if rc:
+            raise NNPError(rc, "nnp_config_init rejected the species list")
+        cfg.precision = PRECISIONS[precision]
+        cfg.max_atoms = int(max_atoms)
+        cfg.max_systems = int(max_systems)
+        cfg.flags = int(flags)
+        if stream is not None:
+            cfg.stream = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+        for k, v in overrides.items():
+            if k in ("shf_r", "shf_a", "shf_z"):
+                arr = getattr(cfg, k)
+                for i, x in enumerate(v):
+                    arr[i] = x
+            else:
+                setattr(cfg, k, v)
+        self.cfg = cfg
+        self.atomic_numbers = tuple(atomic_numbers)
+        self.n_species = len(atomic_numbers)
+        self.precision = precision
+        h = ctypes.c_void_p()
+        rc = L.nnp_create(ctypes.byref(cfg), ctypes.byref(h))
+        if rc:
+            raise NNPError(rc, L.nnp_last_error(None).decode())
+        self._h = h
+
+    # -- helpers
+    def _check(self, rc):
+        if rc:
+            raise NNPError(rc, self._L.nnp_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.nnp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def aev_length(self) -> int:
+        S = self.n_species
+        return 16 * S + 32 * S * (S + 1) // 2
+
+    def param_count(self) -> int:
+        return int(self._L.nnp_param_count(self._h))
+
+    def query(self, key: str) -> int:
+        v = ctypes.c_int64()
+        self._check(self._L.nnp_query(self._h, QUERY[key], ctypes.byref(v)))
+        return int(v.value)
+
+    # -- weights
+    def set_weights(self, species: int, layers):
+        """layers = [(W1, b1), ..., (W4, b4)], W_l (fan_in x fan_out)."""
+        keep, Wp, bp = [], (ctypes.c_void_p * 4)(), (ctypes.c_void_p * 4)()
+        for l, (W, b) in enumerate(layers):
+            pw, kw = _ptr(W, np.float32)
+            pb, kb = _ptr(b, np.float32)
+            keep += [kw, kb]
+            Wp[l], bp[l] = pw.value, pb.value
+        self._check(self._L.nnp_set_weights(self._h, int(species), Wp, bp))
+
+    def set_all_weights(self, weights):
+        for s, layers in enumerate(weights):
+            self.set_weights(s, layers)
+
+    # -- evaluation
+    def eval(self, pos, Z, box=None, forces=True):
+        """Energy (float) and forces (n x 3, same library/device as pos)."""
+        n = int(pos.shape[0])
+        pp, kp = _ptr(pos, np.float64)
+        pz, kz = _ptr(Z, np.int32)
+        b9 = _box9(box)
+        pbox = None if b9 is None else ctypes.c_void_p(b9.ctypes.data)
+        if _is_torch(pos):
+            import torch
+            E = torch.zeros(1, dtype=torch.float64, device=pos.device)
+            F = torch.empty((n, 3), dtype=torch.float64, device=pos.device) if forces else None
+            pE = ctypes.c_void_p(E.data_ptr())
+            pF = ctypes.c_void_p(F.data_ptr()) if forces else None
+        else:
+            E = np.zeros(1)
+            F = np.empty((n, 3)) if forces else None
+            pE = ctypes.c_void_p(E.ctypes.data)
+            pF = ctypes.c_void_p(F.ctypes.data) if forces else None
+        self._check(self._L.nnp_eval(self._h, n, pp, pz, pbox, pE, pF))
+        return (float(E[0]) if not _is_torch(pos) else E[0]), F
+
+    def eval_into(self, pos, Z, box, E_out, F_out, sync: bool = True):
+        """Device-pointer evaluation into caller buffers (torch CUDA tensors)."""
+        b9 = _box9(box)
+        fn = self._L.nnp_eval if sync else self._L.nnp_eval_async
+        self._check(fn(self._h, int(pos.shape[0]), ctypes.c_void_p(pos.data_ptr()),
+                       ctypes.c_void_p(Z.data_ptr()), ctypes.c_void_p(b9.ctypes.data),
+                       ctypes.c_void_p(E_out.data_ptr()), ctypes.c_void_p(F_out.data_ptr())))
+
+    def sync(self):
+        self._check(self._L.nnp_sync(self._h))
+
+    def eval_batch(self, offsets, pos, Z, boxes):
+        """B systems: offsets (B+1), boxes (B x 3 edges or B x 3 x 3, or None)."""
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        B = off.shape[0] - 1
+        n = int(off[-1])
+        pp, kp = _ptr(pos, np.float64)
+        pz, kz = _ptr(Z, np.int32)
+        if boxes is None:
+            pbx, bx = None, None
+        else:
+            bx = np.asarray(boxes, dtype=np.float64)
+            if bx.ndim == 2 and bx.shape[1] == 3:
+                bx = np.stack([np.diag(r) for r in bx])
+            bx = np.ascontiguousarray(bx.reshape(B, 9))
+            pbx = ctypes.c_void_p(bx.ctypes.data)
+        if _is_torch(pos):
+            import torch
+            E = torch.zeros(B, dtype=torch.float64, device=pos.device)
+            F = torch.empty((n, 3), dtype=torch.float64, device=pos.device)
+            pE, pF = ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(F.data_ptr())
+        else:
+            E = np.zeros(B)
+            F = np.empty((n, 3))
+            pE, pF = ctypes.c_void_p(E.ctypes.data), ctypes.c_void_p(F.ctypes.data)
+        self._check(self._L.nnp_eval_batch(self._h, B, ctypes.c_void_p(off.ctypes.data), pp, pz,
+                                           pbx, pE, pF))
+        return E, F
+
+    def force_match_grad(self, v=None, Fref=None, want_loss: bool = False):
+        """dL/dtheta (packed, nnp_param_count doubles) for the last eval."""
+        g = np.zeros(self.param_count())
+        pv, kv = _ptr(v, np.float64)
+        pr, kr = _ptr(Fref, np.float64)
+        loss = np.zeros(1)
+        self._check(self._L.nnp_force_match_grad(
+            self._h, pv, pr, ctypes.c_void_p(loss.ctypes.data) if want_loss else None,
+            ctypes.c_void_p(g.ctypes.data)))
+        return (float(loss[0]), g) if want_loss else g
+
+    def atom_energies(self, n: int) -> np.ndarray:
+        """Per-atom energies of the last evaluation (input order)."""
+        out = np.zeros(n)
+        self._check(self._L.nnp_atom_energies(self._h, ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def profile_stages(self):
+        out = (ctypes.c_double * 5)()
+        self._check(self._L.nnp_profile_stages(self._h, out, 5))
+        return list(out)
+
+
+def pack_weights(weights) -> np.ndarray:
+    """Per-species [(W,b)...] -> the packed parameter layout of nnp_param_count."""
+    parts = []
+    for layers in weights:
+        for W, b in layers:
+            parts += [np.asarray(W, np.float64).reshape(-1), np.asarray(b, np.float64).reshape(-1)]
+    return np.concatenate(parts)

@@ -1,0 +1,125 @@
+// nnp_host.h -- the context object behind the C ABI and the kernel launch
+// entry points shared between the host translation units.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "../../include/nnp.h"
+#include "nnp_internal.cuh"
+
+namespace nnp {
+
+// k_cells.cu
+__global__ void k_bin(const EvalIO* io, const SysDesc* sys, const signed char* zlut, Workspace ws);
+__global__ void k_scan(const EvalIO* io, int S, Workspace ws);
+__global__ void k_scatter(const EvalIO* io, Workspace ws);
+__global__ void k_binsort(const EvalIO* io, int S, int sort, Workspace ws);
+__global__ void k_neighbors(const EvalIO* io, const SysDesc* sys, DescParams P, Workspace ws);
+
+// k_aev.cu
+void launch_aev_fwd(int grid, cudaStream_t st, const SysDesc* sys, const DescParams& P,
+                    const Workspace& ws, int bf16);
+void launch_aev_bwd(int grid, cudaStream_t st, const EvalIO* io, const SysDesc* sys,
+                    const DescParams& P, const Workspace& ws);
+cudaError_t aev_set_smem_limits();
+
+// k_mlp_f32.cu
+void launch_mlp_f32(int grid, cudaStream_t st, const EvalIO* io, const DescParams& P,
+                    const Workspace& ws, const MlpF32Weights& W);
+cudaError_t mlp_f32_set_smem_limits();
+
+}  // namespace nnp
+
+struct nnp_ctx;
+namespace nnp {
+// k_mlp_tc.cu (tensor-core network); returns an nnp_status
+int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t st, long long rows);
+int mlp_tc_init(nnp_ctx* ctx);
+int mlp_tc_set_weights(nnp_ctx* ctx, int species, const float* host_blob);
+void mlp_tc_free(nnp_ctx* ctx);
+}  // namespace nnp
+
+struct nnp_ctx {
+  nnp_config cfg{};
+  nnp::DescParams P{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 148;
+  std::string err;
+
+  // capacities
+  int cap_r = 96, cap_a = 32;
+  int total_cells = 0;
+
+  // device buffers (capacity in elements)
+  int *b_bin_count = nullptr, *b_bin_start = nullptr, *b_bin_len = nullptr;
+  size_t c_bins = 0, c_bins1 = 0, c_bins2 = 0;
+  int *b_atom_bin = nullptr, *b_atom_slot = nullptr, *b_atom_cell = nullptr, *b_atom_sys = nullptr;
+  float4* b_atom_off = nullptr;
+  size_t c_atoms1 = 0, c_atoms2 = 0, c_atoms3 = 0, c_atoms4 = 0, c_atoms5 = 0;
+  int *b_row_atom = nullptr, *b_row_info = nullptr, *b_row_cell = nullptr;
+  float4* b_pos4 = nullptr;
+  size_t c_rows1 = 0, c_rows2 = 0, c_rows3 = 0, c_rows4 = 0, c_rows5 = 0, c_rows6 = 0;
+  int *b_cnt_r = nullptr, *b_cnt_a = nullptr, *b_nbr_r = nullptr, *b_nbr_a = nullptr;
+  size_t c_nbr_r = 0, c_nbr_a = 0;
+  float *b_G = nullptr, *b_dEdG = nullptr, *b_Ei = nullptr;
+  __nv_bfloat16* b_Gh = nullptr;
+  size_t c_G = 0, c_Gh = 0, c_dEdG = 0, c_Ei = 0;
+  nnp::SysDesc* b_sys = nullptr;
+  size_t c_sys = 0;
+  double* b_pos_stage = nullptr;
+  int* b_Z_stage = nullptr;
+  double *b_F_stage = nullptr, *b_E_stage = nullptr;
+  size_t c_pos_stage = 0, c_Z_stage = 0, c_F_stage = 0, c_E_stage = 0;
+  int* b_seg = nullptr;
+  int* b_flags = nullptr;
+  signed char* d_zlut = nullptr;
+  nnp::EvalIO* d_io = nullptr;
+  nnp::EvalIO* h_io = nullptr;  // pinned
+  int* h_flags = nullptr;       // pinned
+
+  // weights
+  float* b_wf32 = nullptr;      // FP32 blob, all species
+  size_t wf32_stride = 0;       // floats per species
+  nnp::MlpF32Weights wf32{};
+  bool has_weights[nnp::kMaxS] = {false, false, false, false};
+  std::vector<float> host_weights;  // FP32 copy (layout of nnp_param_count), for re-quantisation
+  void* tc = nullptr;           // tensor-core network state (k_mlp_tc.cu)
+
+  // stage events (NNP_FLAG_STAGE_EVENTS)
+  cudaEvent_t stage_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  void mark_stage(int k, bool capturing);
+
+  // graph
+  cudaGraphExec_t gexec = nullptr;
+  long long g_key_n = -1, g_key_bins = -1;
+  int g_key_B = -1;
+  long long graph_captures = 0;
+
+  // last evaluation
+  std::vector<nnp::SysDesc> sys_h;
+  long long last_n = 0, last_rows = 0;
+  int last_B = 0;
+  bool has_state = false;
+  long long launches_per_eval = 0;
+  int max_nbr_r = 0, max_nbr_a = 0;
+
+  ~nnp_ctx();
+  int init_device();
+  int fail(int code, const char* fmt, ...);
+  int cuda_fail(cudaError_t e, const char* what);
+  int ensure_capacity(long long n, int B, long long bins, long long rows);
+  nnp::Workspace workspace() const;
+  void invalidate_graph();
+  int launch_pipeline(long long n, int B, long long bins, long long rows);
+  int prepare(int B, const int64_t* offsets, const double* pos_host, const double* boxes,
+              long long& bins, long long& rows);
+  int read_flags(int& fl);
+  int evaluate(int B, const int64_t* offsets, const double* pos, const int32_t* Z,
+               const double* boxes, double* energies, double* forces, bool sync);
+  int check_flags();
+  bool weights_ready() const;
+  int set_weights(int species, const float* const W[4], const float* const b[4]);
+  int force_match_grad(const double* v, const double* Fref, double* loss, double* grad);
+  int profile_stages(double* out, int n_out);
+};

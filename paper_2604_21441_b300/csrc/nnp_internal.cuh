@@ -1,0 +1,185 @@
+// nnp_internal.cuh -- device-side layouts and helpers shared by the libnnp
+// kernels (private to the library).
+//
+// Data layout in HBM (one evaluation, B systems, N atoms):
+//   * rows: atoms sorted species-major, then by system, then by cell
+//     (ascending input index inside a cell).  Each species segment starts on
+//     a multiple of kTileRows so that every network tile holds one species.
+//     Padding rows have row_atom = -1 and an all-zero descriptor.
+//   * pos4[row] = (x, y, z offset of the atom from its cell's lower corner in
+//     FP32, bits(orig << 3 | species)): displacements are formed as
+//     (off_j - off_i) + m * ell with m in {-1, 0, 1}^3, so FP32 rounding does
+//     not grow with the box edge.
+//   * neighbour entries: row index j (27 bits) | image code (5 bits), code =
+//     (mx+1)*9 + (my+1)*3 + (mz+1).  Lists are grouped by neighbour species
+//     (counts per species in cnt_r / cnt_a).
+//   * G / dEdG: row-major [rows][D] FP32 (plus a BF16 copy for tensor cores).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+namespace nnp {
+
+constexpr int kNRad = 16;      // radial shifts
+constexpr int kNAngR = 4;      // angular radial shifts
+constexpr int kNAngZ = 8;      // angular sectors
+constexpr int kNAng = kNAngR * kNAngZ;  // 32 features per species pair
+constexpr int kH1 = 160, kH2 = 128, kH3 = 96;
+constexpr int kMaxS = 4;       // species supported by the kernels
+constexpr int kTileRows = 128; // species segments are padded to this
+constexpr int kMaxD = kNRad * kMaxS + kNAng * kMaxS * (kMaxS + 1) / 2;  // 384
+
+// Error flag words (device): set by kernels, read by the host after sync.
+enum FlagWord {
+  kFlagBadSpecies = 0,
+  kFlagNonFinite = 1,
+  kFlagOverflowR = 2,   // radial list overflow
+  kFlagOverflowA = 3,   // angular list overflow
+  kFlagMaxNbrR = 4,     // max radial count seen (atomicMax)
+  kFlagMaxNbrA = 5,
+  kFlagBinOverflow = 6, // a bin held more than the per-bin sort capacity
+  kFlagTimeout = 7,
+  kNumFlags = 8
+};
+
+// Descriptor and network constants, passed by value to kernels.
+struct DescParams {
+  int S;              // species
+  int D;              // descriptor length
+  int zeta_sq;        // zeta = 2^zeta_sq
+  float rc_r, eta_r, rc_a, eta_a;
+  float shf_r[kNRad];
+  float shf_a[kNAngR];
+  float hcos_z[kNAngZ], hsin_z[kNAngZ];  // cos(theta_z)/2, sin(theta_z)/2
+  float celu_alpha;
+};
+
+// One periodic system.  Filled on the host, copied to the device per eval.
+struct SysDesc {
+  double L[3];      // edges (isolated systems: padded bounding box)
+  double ell[3];    // cell edges L / nc
+  double origin[3]; // subtracted before wrapping (isolated systems)
+  float ellf[3];
+  int nc[3];
+  int cell_base;    // first global cell of this system
+  int periodic;
+  long long atom_begin, atom_end;
+};
+
+// Per-evaluation IO descriptor (device memory, refreshed before each launch
+// so that captured graphs do not depend on caller pointers).
+struct EvalIO {
+  const double* pos;   // n x 3
+  const int* Z;        // n
+  double* forces;      // n x 3 (zeroed by the bin kernel)
+  double* energies;    // B (zeroed by the bin kernel)
+  long long n_atoms;
+  int n_sys;
+  int total_cells;     // sum of cells over systems
+};
+
+// Device workspace (all capacity-sized).
+struct Workspace {
+  // binning
+  int* bin_count;   // [S * max_cells]
+  int* bin_start;   // [S * max_cells + 1]
+  int* bin_len;     // [S * max_cells]
+  int* atom_bin;    // [max_atoms]
+  int* atom_slot;   // [max_atoms]
+  float4* atom_off; // [max_atoms]  (offsets, bits(orig<<3|s))
+  int* atom_cell;   // [max_atoms]  packed local cell
+  int* atom_sys;    // [max_atoms]  system index
+  int* seg;         // [kMaxS + 2]: species segment starts (rows), seg[S] = rows
+  // rows
+  int* row_atom;    // [max_rows]
+  float4* pos4;     // [max_rows]
+  int* row_info;    // [max_rows]  system index (bits 0..19) ; unused upper
+  int* row_cell;    // [max_rows]  local cell (cx | cy << 10 | cz << 20)
+  int* cnt_r;       // [max_rows * kMaxS]
+  int* cnt_a;       // [max_rows * kMaxS]
+  int* nbr_r;       // [max_rows * cap_r]
+  int* nbr_a;       // [max_rows * cap_a]
+  float* G;         // [max_rows * D]
+  __nv_bfloat16* Gh;  // [max_rows * D]
+  float* dEdG;      // [max_rows * D]
+  float* Ei;        // [max_rows]
+  int* flags;       // [kNumFlags]
+  int cap_r, cap_a;
+  long long max_rows;
+};
+
+// FP32 network weights per species: W_l row-major (fan_in x fan_out) and the
+// transposed copies W_l^T used by the backward pass.
+struct MlpF32Weights {
+  const float* W[kMaxS][4];
+  const float* WT[kMaxS][3];  // W1^T, W2^T, W3^T
+  const float* b[kMaxS][4];
+};
+
+// --------------------------------------------------------------------------
+// small device helpers
+
+__device__ __forceinline__ int warp_id_global() {
+  return (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+}
+
+__device__ __forceinline__ float3 image_shift(int code, const float ell[3]) {
+  int mx = code / 9 - 1, my = (code / 3) % 3 - 1, mz = code % 3 - 1;
+  return make_float3(mx * ell[0], my * ell[1], mz * ell[2]);
+}
+
+__device__ __forceinline__ int nbr_row(int e) { return e & 0x07FFFFFF; }
+__device__ __forceinline__ int nbr_code(int e) { return (int)((unsigned)e >> 27); }
+__device__ __forceinline__ int pack_nbr(int row, int code) {
+  return (int)((unsigned)row | ((unsigned)code << 27));
+}
+
+__device__ __forceinline__ int pos4_species(float4 p) {
+  return __float_as_int(p.w) & 7;
+}
+__device__ __forceinline__ int pos4_orig(float4 p) {
+  return (int)((unsigned)__float_as_int(p.w) >> 3);
+}
+
+// cosine cutoff and its derivative (accurate cospi/sinpi)
+__device__ __forceinline__ float cutoff_fc(float r, float rc) {
+  return r < rc ? 0.5f * cospif(r / rc) + 0.5f : 0.0f;
+}
+__device__ __forceinline__ float cutoff_dfc(float r, float rc) {
+  return r < rc ? -0.5f * (3.14159265358979f / rc) * sinpif(r / rc) : 0.0f;
+}
+
+// Reduce-scatter of V register values over the warp: afterwards lane l
+// holds the warp sum of value (l * V / 32) for V = 32 (V = 16: lanes 2k and
+// 2k+1 both hold value k).
+template <int V>
+__device__ __forceinline__ float warp_reduce_scatter(float (&v)[V], int lane) {
+  static_assert(V == 32 || V == 16, "V must be 16 or 32");
+#pragma unroll
+  for (int w = V / 2, bit = 16; w >= 1; w >>= 1, bit >>= 1) {
+    const bool upper = (lane & bit) != 0;
+#pragma unroll
+    for (int k = 0; k < w; ++k) {
+      float keep = upper ? v[k + w] : v[k];
+      float send = upper ? v[k] : v[k + w];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+    }
+  }
+  float r = v[0];
+  if (V == 16) r += __shfl_xor_sync(0xffffffffu, r, 1);
+  return r;
+}
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+__device__ __forceinline__ int pair_block(int S, int s1, int s2) {
+  // row-major upper triangle index of (s1 <= s2)
+  return s1 * S - (s1 * (s1 - 1)) / 2 + (s2 - s1);
+}
+
+}  // namespace nnp
