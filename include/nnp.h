@@ -152,6 +152,31 @@ int nnp_eval(nnp_ctx *ctx, int64_t n, const double *pos, const int32_t *Z,
 int nnp_eval_async(nnp_ctx *ctx, int64_t n, const double *pos, const int32_t *Z,
                    const double *box, double *energy, double *forces);
 
+/* Maximum number of atoms of one nnp_eval_noalloc call. */
+#define NNP_NOALLOC_MAX_ATOMS 1024
+
+/* Energy and forces of one periodic system without allocating any device
+ * memory.  For callers that must not call cudaMalloc once a run is under way,
+ * such as an MD engine that hands the GPU's free memory to its own pool at
+ * start-up: a mid-run allocation can then fail, and it can stall the device
+ * while the engine's other streams are busy.  Create the context and set its
+ * weights at start-up; afterwards this call allocates nothing.
+ *   Same meaning as nnp_eval for one periodic system, with n <=
+ *   NNP_NOALLOC_MAX_ATOMS (larger n: NNP_ERR_CAPACITY), pos, Z, energy and
+ *   forces device pointers, box a host pointer (orthorhombic, edges >= rc_r),
+ *   FP32 contexts only (else NNP_ERR_UNSUPPORTED).  At most 128 radial and 48
+ *   angular neighbours per atom (more: NNP_ERR_CAPACITY, lists do not grow).
+ *   Synchronous; runs on the context's stream and leaves the context's own
+ *   buffers, graph and last-evaluation state untouched.
+ * All per-call scratch lives in one fixed device array of the library (about
+ * 6 MiB), which every GPU that loads the library holds until the process
+ * exits.  The first call on a device looks up that array's address; make it
+ * before any stream capture.  Every call shares the array: calls that overlap
+ * on the GPU (other streams, contexts or threads) race and give wrong results.
+ * The paper has no counterpart of this entry point. */
+int nnp_eval_noalloc(nnp_ctx *ctx, int64_t n, const double *pos, const int32_t *Z,
+                     const double *box, double *energy, double *forces);
+
 /* Wait for the context's stream and report device-side flags raised since
  * the last check. */
 int nnp_sync(nnp_ctx *ctx);

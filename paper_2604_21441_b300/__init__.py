@@ -27,6 +27,7 @@ LIB_PATH = os.path.join(_HERE, "libnnp.so")
 
 NNP_MAX_SPECIES = 8
 NNP_MAX_SHIFTS = 32
+NNP_NOALLOC_MAX_ATOMS = 1024
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2}
 FLAG_NO_GRAPH = 0x1
 FLAG_NONDETERMINISTIC_BINS = 0x2
@@ -37,7 +38,7 @@ STAGES = ("cells", "neighbours", "descriptor", "network", "descriptor_backward")
 ABI_FUNCTIONS = ("nnp_config_init", "nnp_create", "nnp_destroy", "nnp_last_error",
                  "nnp_set_weights", "nnp_eval", "nnp_eval_async", "nnp_sync",
                  "nnp_eval_batch", "nnp_param_count", "nnp_force_match_grad", "nnp_query",
-                 "nnp_profile_stages", "nnp_atom_energies")
+                 "nnp_profile_stages", "nnp_atom_energies", "nnp_eval_noalloc")
 
 QUERY = {"launches_per_eval": 0, "nbr_capacity": 1, "ang_capacity": 2, "max_nbr": 3,
          "max_ang": 4, "rows": 5, "graph_captures": 6}
@@ -116,6 +117,8 @@ def lib() -> ctypes.CDLL:
     L.nnp_profile_stages.restype = ctypes.c_int
     L.nnp_atom_energies.argtypes = [vp, dp]
     L.nnp_atom_energies.restype = ctypes.c_int
+    L.nnp_eval_noalloc.argtypes = [vp, i64, dp, dp, dp, dp, dp]
+    L.nnp_eval_noalloc.restype = ctypes.c_int
     _lib = L
     return L
 
