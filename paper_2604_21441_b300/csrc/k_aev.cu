@@ -7,182 +7,341 @@
 //              * exp(-eta_a ((r_ij + r_ik)/2 - R_a)^2) fc(r_ij; rc_a) fc(r_ik; rc_a)
 //            with cos(theta' - theta_z) = u cos(theta_z) + sqrt(1 - u^2) sin(theta_z),
 //            u = 0.95 cos(theta_ijk), so no arccos is evaluated.
+//   fc(r; rc) = (cos(pi r / rc) + 1)/2 = cos^2(y), y = pi r / (2 rc).
 //
-// Forces follow Eq. 2 of the paper: F = -dE/dr, by the chain rule from
-// dE/dG_i (the network backward) through these terms.
+// Forces follow Eq. 2 of the paper, F = -dE/dr, by the chain rule from dE/dG_i
+// (the network backward) through these terms.
 //
-// Mapping: one warp per row (atom).  Radial: lanes over the neighbours of one
-// species, 16 register accumulators, warp reduce-scatter.  Angular: the
-// angular neighbours' unit vectors, distances and cutoffs are staged in
-// shared memory; lanes run over the triplets of one species-pair block with
-// 32 register accumulators (4 shifts x 8 sectors), then reduce-scatter so
-// lane l owns feature l of the block.  All arithmetic FP32; per-atom forces
-// are accumulated in FP64 (atomics into the caller's force array).
+// Mapping: half a warp (16 lanes) per row, the two halves of a warp in lock
+// step so that shuffles stay convergent.  Radial: lanes over the neighbours of
+// one species, 16 accumulators per lane, half-warp reduce-scatter (lane l ends
+// with feature l).  Angular: the neighbours inside rc_a (the first entries of
+// each species segment of the row's list) are staged in shared memory as unit
+// vector, distance and cutoff; lanes run over the neighbour pairs of one
+// species-pair block (a flat index mapped to a pair without search) with 32
+// accumulators (4 shifts x 8 sectors), then reduce-scatter so that lane l owns
+// features 2l and 2l+1.  Species loops are not unrolled, which keeps the code
+// inside the instruction cache.  FP32 throughout; forces are summed per
+// neighbour slot in shared memory and added once per slot in FP64.
 #include "nnp_internal.cuh"
 
 namespace nnp {
 
-struct AngGeo {
-  float ex, ey, ez, r;
-};
+namespace {
 
-// Map a flat triplet index t of block (s1, s2) to neighbour positions
-// (u, v) inside the angular list: off-diagonal blocks enumerate n1 x n2,
-// diagonal blocks the n(n-1)/2 pairs u < v.
-__device__ __forceinline__ void triplet_uv(int t, bool diag, int n1, int n2, int o1, int o2,
-                                           int& u, int& v) {
-  if (!diag) {
-    const int q = t / n2;
-    u = o1 + q;
-    v = o2 + (t - q * n2);
-  } else {
-    const int n = n1;
-    // row q holds pairs (q, q+1..n-1); first index of row q: q(2n - q - 1)/2
-    float disc = (float)((2 * n - 1) * (2 * n - 1) - 8 * t);
-    int q = (int)floorf(0.5f * ((float)(2 * n - 1) - sqrtf(fmaxf(disc, 0.f))));
-    q = max(0, min(q, n - 2));
-    while (q > 0 && q * (2 * n - q - 1) / 2 > t) --q;
-    while (q + 1 <= n - 2 && (q + 1) * (2 * n - q - 2) / 2 <= t) ++q;
-    const int first = q * (2 * n - q - 1) / 2;
-    u = o1 + q;
-    v = o1 + q + 1 + (t - first);
-  }
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kPi = 3.14159265358979f;
+
+// fc = cos^2(y), dfc/dr = -2 k sin(y) cos(y), y = k r, k = pi / (2 rc), from
+// the Taylor series of cos and sin about 0 (truncation error < 1e-8 for
+// 0 <= y <= pi/2).
+__device__ __forceinline__ void cutoff(float r, float rc, float k, float& fc, float& dfc) {
+  const float y = r * k, y2 = y * y;
+  float c = fmaf(y2, 1.0f / 479001600.0f, -1.0f / 3628800.0f);
+  c = fmaf(y2, c, 1.0f / 40320.0f);
+  c = fmaf(y2, c, -1.0f / 720.0f);
+  c = fmaf(y2, c, 1.0f / 24.0f);
+  c = fmaf(y2, c, -0.5f);
+  c = fmaf(y2, c, 1.0f);
+  float s = fmaf(y2, 1.0f / 6227020800.0f, -1.0f / 39916800.0f);
+  s = fmaf(y2, s, 1.0f / 362880.0f);
+  s = fmaf(y2, s, -1.0f / 5040.0f);
+  s = fmaf(y2, s, 1.0f / 120.0f);
+  s = fmaf(y2, s, -1.0f / 6.0f);
+  s = fmaf(y2, s, 1.0f);
+  s *= y;
+  const bool in = r < rc;
+  fc = in ? c * c : 0.f;
+  dfc = in ? -2.f * k * s * c : 0.f;
 }
 
-__device__ __forceinline__ float pow2k(float b, int k) {
-  for (int i = 0; i < k; ++i) b *= b;
+// b^zeta (zeta = 2^q) by q squarings, and b^(zeta-1) as the product of the
+// intermediate powers.
+template <int ZSQ>
+__device__ __forceinline__ void pow_zeta(float b, int zsq, float& bz, float& bzm1) {
+  float p = b, prod = 1.f;
+  if (ZSQ >= 0) {
+#pragma unroll
+    for (int i = 0; i < (ZSQ >= 0 ? ZSQ : 0); ++i) { prod *= p; p *= p; }
+  } else {
+    for (int i = 0; i < zsq; ++i) { prod *= p; p *= p; }
+  }
+  bz = p;
+  bzm1 = prod;
+}
+
+template <int ZSQ>
+__device__ __forceinline__ float pow_zeta1(float b, int zsq) {
+  if (ZSQ >= 0) {
+#pragma unroll
+    for (int i = 0; i < (ZSQ >= 0 ? ZSQ : 0); ++i) b *= b;
+  } else {
+    for (int i = 0; i < zsq; ++i) b *= b;
+  }
   return b;
 }
 
-// Stage the angular neighbours of one row (geometry + cutoff) in shared memory.
-__device__ __forceinline__ int stage_angular(const Workspace& ws, const DescParams& P, int row,
-                                             float4 pi, const float ell[3], AngGeo* geo,
-                                             float* fcs, float* dfcs, int* origs, int lane,
-                                             int (&na_s)[kMaxS], int (&oa_s)[kMaxS]) {
-  int na = 0;
+// Reduce-scatter of V values over the 16 lanes of each half warp (both halves
+// at once): lane l of a half keeps the half's sums of values V/16*l + k in
+// v[k], k < V/16.
+template <int V>
+__device__ __forceinline__ void hw_reduce_scatter(float (&v)[V], int hl) {
 #pragma unroll
-  for (int s = 0; s < kMaxS; ++s) {
-    na_s[s] = s < P.S ? ws.cnt_a[(size_t)row * kMaxS + s] : 0;
-    oa_s[s] = na;
-    na += na_s[s];
+  for (int w = V / 2, bit = 8; bit >= 1; w >>= 1, bit >>= 1) {
+    const bool upper = (hl & bit) != 0;
+#pragma unroll
+    for (int k = 0; k < w; ++k) {
+      const float keep = upper ? v[k + w] : v[k];
+      const float send = upper ? v[k] : v[k + w];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+    }
   }
-  const int* la = ws.nbr_a + (size_t)row * ws.cap_a;
-  for (int k = lane; k < na; k += 32) {
-    const int e = la[k];
-    const float4 pj = ws.pos4[nbr_row(e)];
-    const float3 sh = image_shift(nbr_code(e), ell);
-    const float dx = (pj.x - pi.x) + sh.x, dy = (pj.y - pi.y) + sh.y, dz = (pj.z - pi.z) + sh.z;
-    const float r = sqrtf(dx * dx + dy * dy + dz * dz);
-    const float ir = 1.0f / r;
-    geo[k] = AngGeo{dx * ir, dy * ir, dz * ir, r};
-    fcs[k] = cutoff_fc(r, P.rc_a);
-    if (dfcs) dfcs[k] = cutoff_dfc(r, P.rc_a);
-    if (origs) origs[k] = pos4_orig(pj);
-  }
-  __syncwarp();
-  return na;
 }
+
+__device__ __forceinline__ float hw_sum(float x) {
+#pragma unroll
+  for (int o = 8; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Flat pair index t of block (s1, s2) -> positions (u, v) in the staged
+// angular neighbours.  Off-diagonal blocks: t = q n2 + r.  Diagonal blocks
+// (n atoms): each unordered pair once, as (q, q + k mod n) with k <= K for the
+// first n K indices (K = (n-1)/2, or n/2 - 1 for even n), then (q, q + n/2).
+struct PairMap {
+  int n1, n2, o1, o2, K, nK;
+  float inv;
+  bool diag;
+};
+
+__device__ __forceinline__ PairMap make_map(bool diag, int n1, int n2, int o1, int o2) {
+  PairMap m;
+  m.diag = diag;
+  m.n1 = n1;
+  m.n2 = n2;
+  m.o1 = o1;
+  m.o2 = o2;
+  if (diag) {
+    m.K = (n1 & 1) ? (n1 - 1) / 2 : n1 / 2 - 1;
+    if (m.K < 0) m.K = 0;
+    m.nK = n1 * m.K;
+    m.inv = m.K > 0 ? 1.0f / (float)m.K : 0.f;
+  } else {
+    m.K = n2;
+    m.nK = 0;
+    m.inv = n2 > 0 ? 1.0f / (float)n2 : 0.f;
+  }
+  return m;
+}
+
+__device__ __forceinline__ void map_pair(const PairMap& m, int t, int& u, int& v) {
+  if (!m.diag || t < m.nK) {
+    int q = (int)(((float)t + 0.5f) * m.inv);
+    if (q * m.K > t) --q;
+    else if ((q + 1) * m.K <= t) ++q;
+    const int r = t - q * m.K;
+    if (!m.diag) {
+      u = m.o1 + q;
+      v = m.o2 + r;
+    } else {
+      int vv = q + r + 1;
+      if (vv >= m.n1) vv -= m.n1;
+      u = m.o1 + q;
+      v = m.o1 + vv;
+    }
+  } else {
+    const int tt = t - m.nK;
+    u = m.o1 + tt;
+    v = m.o1 + tt + (m.n1 >> 1);
+  }
+}
+
+__device__ __forceinline__ float4 shift_vec(int code, const float* ell) {
+  const int mx = code / 9 - 1, my = (code / 3) % 3 - 1, mz = code % 3 - 1;
+  return make_float4(mx * ell[0], my * ell[1], mz * ell[2], 0.f);
+}
+
+// Per half-warp row bookkeeping in shared memory: counts and offsets per species.
+struct RowCounts {
+  int nr[kMaxS], orr[kMaxS];  // radial entries and list offset per species
+  int na[kMaxS], oa[kMaxS];   // staged angular entries and staging offset per species
+};
+
+__device__ __forceinline__ void load_counts(const Workspace& ws, int S, int row, bool live, int cap_a,
+                                            RowCounts* rc, int hl) {
+  if (hl == 0) {
+    int o = 0, oa = 0;
+    for (int s = 0; s < kMaxS; ++s) {
+      const int n = (live && s < S) ? ws.cnt_r[(size_t)row * kMaxS + s] : 0;
+      int a = (live && s < S) ? ws.cnt_a[(size_t)row * kMaxS + s] : 0;
+      a = min(a, max(0, cap_a - oa));  // never stage past the buffer
+      rc->nr[s] = n;
+      rc->orr[s] = o;
+      rc->na[s] = a;
+      rc->oa[s] = oa;
+      o += n;
+      oa += a;
+    }
+  }
+}
+
+}  // namespace
 
 // --------------------------------------------------------------------------
 // forward
 
-template <int S>
+template <int S, int ZSQ>
 __global__ void __launch_bounds__(256) k_aev_fwd(const SysDesc* __restrict__ sys, DescParams P,
                                                  Workspace ws, int write_bf16) {
   constexpr int D = kNRad * S + kNAng * S * (S + 1) / 2;
-  extern __shared__ unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  AngGeo* geo = reinterpret_cast<AngGeo*>(smem_raw) + (size_t)w * ws.cap_a;
-  float* fcs = reinterpret_cast<float*>(reinterpret_cast<AngGeo*>(smem_raw) + 8 * (size_t)ws.cap_a) +
-               (size_t)w * ws.cap_a;
+  extern __shared__ float4 sm4[];
+  const int lane = threadIdx.x & 31, hl = lane & 15, half = lane >> 4;
+  const int hwb = threadIdx.x >> 4;  // half warp in block, 0..15
+  const int ca = ws.cap_a;
+  float4* geo = sm4 + (size_t)hwb * (ca + 27);
+  float4* sh = geo + ca;
+  float* fcs = reinterpret_cast<float*>(sm4 + 16 * (size_t)(ca + 27)) + (size_t)hwb * ca;
+  RowCounts* rc = reinterpret_cast<RowCounts*>(reinterpret_cast<float*>(sm4 + 16 * (size_t)(ca + 27)) +
+                                               16 * (size_t)ca) + hwb;
+  const float kr = -P.eta_r * kLog2e, ka = -P.eta_a * kLog2e;
+  const float kfr = kPi / (2.f * P.rc_r), kfa = kPi / (2.f * P.rc_a);
   const int rows = ws.seg[S];
-  for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows;
-       row += (gridDim.x * blockDim.x) >> 5) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  int cached_sys = -1;
+  for (int pr = warp; 2 * pr < rows; pr += nwarps) {
+    const int row = 2 * pr + half;
+    const bool inrow = row < rows;
+    const bool live = inrow && ws.row_atom[row] >= 0;
     float* Grow = ws.G + (size_t)row * D;
     __nv_bfloat16* Ghrow = ws.Gh + (size_t)row * D;
-    if (ws.row_atom[row] < 0) {
-      for (int f = lane; f < D; f += 32) {
+    if (inrow && !live) {  // padding row: zero descriptor
+      for (int f = hl; f < D; f += 16) {
         Grow[f] = 0.f;
         if (write_bf16) Ghrow[f] = __float2bfloat16(0.f);
       }
-      continue;
     }
-    const float4 pi = ws.pos4[row];
-    const SysDesc& sd = sys[ws.row_info[row]];
-    const float ell[3] = {sd.ellf[0], sd.ellf[1], sd.ellf[2]};
+    float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (live) {
+      pi = ws.pos4[row];
+      const int sid = ws.row_info[row];
+      if (sid != cached_sys) {
+        const SysDesc& sd = sys[sid];
+        const float ell[3] = {sd.ellf[0], sd.ellf[1], sd.ellf[2]};
+        for (int c = hl; c < 27; c += 16) sh[c] = shift_vec(c, ell);
+        cached_sys = sid;
+      }
+    }
+    load_counts(ws, S, row, live, ca, rc, hl);
+    __syncwarp();
+    const int* lr = ws.nbr_r + (size_t)row * ws.cap_r;
 
     // ---------------- radial
-    const int* lr = ws.nbr_r + (size_t)row * ws.cap_r;
-    int o = 0;
-#pragma unroll
+#pragma unroll 1
     for (int s = 0; s < S; ++s) {
-      const int n_s = ws.cnt_r[(size_t)row * kMaxS + s];
+      const int n_s = rc->nr[s], o_s = rc->orr[s];
+      const int nmax = max(n_s, __shfl_xor_sync(0xffffffffu, n_s, 16));
       float acc[kNRad];
 #pragma unroll
       for (int m = 0; m < kNRad; ++m) acc[m] = 0.f;
-      for (int k = lane; k < n_s; k += 32) {
-        const int e = lr[o + k];
-        const float4 pj = ws.pos4[nbr_row(e)];
-        const float3 sh = image_shift(nbr_code(e), ell);
-        const float dx = (pj.x - pi.x) + sh.x, dy = (pj.y - pi.y) + sh.y, dz = (pj.z - pi.z) + sh.z;
-        const float r = sqrtf(dx * dx + dy * dy + dz * dz);
-        const float f = 0.25f * cutoff_fc(r, P.rc_r);
+      for (int k0 = 0; k0 < nmax; k0 += 16) {
+        const int k = k0 + hl;
+        if (k < n_s) {
+          const int e = lr[o_s + k];
+          const float4 pj = ws.pos4[nbr_row(e)];
+          const float4 sv = sh[nbr_code(e)];
+          const float dx = (pj.x - pi.x) + sv.x, dy = (pj.y - pi.y) + sv.y, dz = (pj.z - pi.z) + sv.z;
+          const float r = sqrtf(dx * dx + dy * dy + dz * dz);
+          float fc, dfc;
+          cutoff(r, P.rc_r, kfr, fc, dfc);
+          const float f = 0.25f * fc;
 #pragma unroll
-        for (int m = 0; m < kNRad; ++m) {
-          const float x = r - P.shf_r[m];
-          acc[m] = fmaf(f, expf(-P.eta_r * x * x), acc[m]);
+          for (int m = 0; m < kNRad; ++m) {
+            const float x = r - P.shf_r[m];
+            acc[m] = fmaf(f, exp2f(kr * x * x), acc[m]);
+          }
         }
       }
-      o += n_s;
-      const float val = warp_reduce_scatter<kNRad>(acc, lane);
-      if ((lane & 1) == 0) {
-        Grow[s * kNRad + (lane >> 1)] = val;
-        if (write_bf16) Ghrow[s * kNRad + (lane >> 1)] = __float2bfloat16(val);
+      hw_reduce_scatter<kNRad>(acc, hl);
+      if (live) {
+        Grow[s * kNRad + hl] = acc[0];
+        if (write_bf16) Ghrow[s * kNRad + hl] = __float2bfloat16(acc[0]);
       }
     }
 
-    // ---------------- angular
-    int na_s[kMaxS], oa_s[kMaxS];
-    stage_angular(ws, P, row, pi, ell, geo, fcs, nullptr, nullptr, lane, na_s, oa_s);
-#pragma unroll
+    // ---------------- angular: stage the neighbours inside rc_a
+#pragma unroll 1
+    for (int s = 0; s < S; ++s) {
+      const int n_a = rc->na[s], o_r = rc->orr[s], o_a = rc->oa[s];
+      for (int k = hl; k < n_a; k += 16) {
+        const int e = lr[o_r + k];
+        const float4 pj = ws.pos4[nbr_row(e)];
+        const float4 sv = sh[nbr_code(e)];
+        const float dx = (pj.x - pi.x) + sv.x, dy = (pj.y - pi.y) + sv.y, dz = (pj.z - pi.z) + sv.z;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float ir = rsqrtf(r2);
+        const float r = r2 * ir;
+        float fc, dfc;
+        cutoff(r, P.rc_a, kfa, fc, dfc);
+        geo[o_a + k] = make_float4(dx * ir, dy * ir, dz * ir, r);
+        fcs[o_a + k] = fc;
+      }
+    }
+    __syncwarp();
+#pragma unroll 1
     for (int s1 = 0; s1 < S; ++s1) {
-#pragma unroll
+#pragma unroll 1
       for (int s2 = s1; s2 < S; ++s2) {
-        const int pblk = pair_block(S, s1, s2);
         const bool diag = s1 == s2;
-        const int n1 = na_s[s1], n2 = na_s[s2];
+        const int n1 = rc->na[s1], n2 = rc->na[s2];
         const int T = diag ? n1 * (n1 - 1) / 2 : n1 * n2;
+        const int Tmax = max(T, __shfl_xor_sync(0xffffffffu, T, 16));
+        const int f0 = kNRad * S + pair_block(S, s1, s2) * kNAng + 2 * hl;
+        if (Tmax == 0) {
+          if (live) {
+            *reinterpret_cast<float2*>(Grow + f0) = make_float2(0.f, 0.f);
+            if (write_bf16)
+              *reinterpret_cast<__nv_bfloat162*>(Ghrow + f0) = __floats2bfloat162_rn(0.f, 0.f);
+          }
+          continue;
+        }
+        const PairMap pm = make_map(diag, n1, n2, rc->oa[s1], rc->oa[s2]);
         float acc[kNAng];
 #pragma unroll
         for (int q = 0; q < kNAng; ++q) acc[q] = 0.f;
-        for (int t = lane; t < T; t += 32) {
-          int u, v;
-          triplet_uv(t, diag, n1, n2, oa_s[s1], oa_s[s2], u, v);
-          const AngGeo gu = geo[u], gv = geo[v];
-          const float c = gu.ex * gv.ex + gu.ey * gv.ey + gu.ez * gv.ez;
-          const float uc = 0.95f * c;
-          const float sn = sqrtf(fmaxf(0.f, 1.f - uc * uc));
-          const float rbar = 0.5f * (gu.r + gv.r);
-          const float fp = fcs[u] * fcs[v];
-          float B[kNAngR];
+        for (int t0 = 0; t0 < Tmax; t0 += 16) {
+          const int t = t0 + hl;
+          if (t < T) {
+            int u, v;
+            map_pair(pm, t, u, v);
+            const float4 gu = geo[u], gv = geo[v];
+            const float c = gu.x * gv.x + gu.y * gv.y + gu.z * gv.z;
+            const float uc = 0.95f * c;
+            const float sn = sqrtf(fmaxf(1.f - uc * uc, 0.f));
+            const float fp = fcs[u] * fcs[v];
+            const float rbar = 0.5f * (gu.w + gv.w);
+            float B[kNAngR];
 #pragma unroll
-          for (int a = 0; a < kNAngR; ++a) {
-            const float x = rbar - P.shf_a[a];
-            B[a] = fp * expf(-P.eta_a * x * x);
-          }
+            for (int a = 0; a < kNAngR; ++a) {
+              const float x = rbar - P.shf_a[a];
+              B[a] = fp * exp2f(ka * x * x);
+            }
 #pragma unroll
-          for (int z = 0; z < kNAngZ; ++z) {
-            const float base = 0.5f + uc * P.hcos_z[z] + sn * P.hsin_z[z];
-            const float A = pow2k(base, P.zeta_sq);
+            for (int z = 0; z < kNAngZ; ++z) {
+              const float base = fmaf(sn, P.hsin_z[z], fmaf(uc, P.hcos_z[z], 0.5f));
+              const float A = pow_zeta1<ZSQ>(base, P.zeta_sq);
 #pragma unroll
-            for (int a = 0; a < kNAngR; ++a) acc[a * kNAngZ + z] = fmaf(A, B[a], acc[a * kNAngZ + z]);
+              for (int a = 0; a < kNAngR; ++a) acc[a * kNAngZ + z] = fmaf(A, B[a], acc[a * kNAngZ + z]);
+            }
           }
         }
-        float val = 0.f;
-        if (__any_sync(0xffffffffu, T > 0)) val = 2.0f * warp_reduce_scatter<kNAng>(acc, lane);
-        const int f = kNRad * S + pblk * kNAng + lane;
-        Grow[f] = val;
-        if (write_bf16) Ghrow[f] = __float2bfloat16(val);
+        hw_reduce_scatter<kNAng>(acc, hl);
+        if (live) {
+          *reinterpret_cast<float2*>(Grow + f0) = make_float2(2.f * acc[0], 2.f * acc[1]);
+          if (write_bf16)
+            *reinterpret_cast<__nv_bfloat162*>(Ghrow + f0) =
+                __floats2bfloat162_rn(2.f * acc[0], 2.f * acc[1]);
+        }
       }
     }
     __syncwarp();
@@ -190,149 +349,222 @@ __global__ void __launch_bounds__(256) k_aev_fwd(const SysDesc* __restrict__ sys
 }
 
 // --------------------------------------------------------------------------
-// backward: dE/dG -> forces (FP64 accumulation)
+// backward: dE/dG -> forces (FP64 accumulation in the caller's array)
 
-template <int S>
-__global__ void __launch_bounds__(256) k_aev_bwd(const EvalIO* __restrict__ io,
+template <int S, int ZSQ>
+__global__ void __launch_bounds__(128) k_aev_bwd(const EvalIO* __restrict__ io,
                                                  const SysDesc* __restrict__ sys, DescParams P,
                                                  Workspace ws) {
   constexpr int D = kNRad * S + kNAng * S * (S + 1) / 2;
-  extern __shared__ unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int ca = ws.cap_a;
-  // per warp: geo[ca], fc[ca], dfc[ca], orig[ca], force slots[3*ca], dEdG[D]
-  unsigned char* base = smem_raw + (size_t)w * (ca * (sizeof(AngGeo) + 6 * sizeof(float)) + D * sizeof(float));
-  AngGeo* geo = reinterpret_cast<AngGeo*>(base);
-  float* fcs = reinterpret_cast<float*>(geo + ca);
-  float* dfcs = fcs + ca;
-  int* origs = reinterpret_cast<int*>(dfcs + ca);
-  float* fsl = reinterpret_cast<float*>(origs + ca);
-  float* wsm = fsl + 3 * ca;
+  extern __shared__ float4 sm4[];
+  const int lane = threadIdx.x & 31, hl = lane & 15, half = lane >> 4;
+  const int hwb = threadIdx.x >> 4;  // 0..7
+  const int ca = ws.cap_a, cr = ws.cap_r;
+  // per half warp: geo[ca], aux[ca] (fc, dfc, 1/r, slot), sh[27] | fsl[3 cr] | origs[cr] | w[D] | counts
+  const size_t n4 = (size_t)2 * ca + 27;
+  float4* geo = sm4 + hwb * n4;
+  float4* aux = geo + ca;
+  float4* sh = aux + ca;
+  float* fbase = reinterpret_cast<float*>(sm4 + 8 * n4);
+  const size_t nf = (size_t)4 * cr + D;
+  float* fsl = fbase + hwb * nf;
+  int* origs = reinterpret_cast<int*>(fsl + 3 * cr);
+  float* wsm = fsl + 4 * cr;
+  RowCounts* rc = reinterpret_cast<RowCounts*>(fbase + 8 * nf) + hwb;
+  const float kr = -P.eta_r * kLog2e, ka = -P.eta_a * kLog2e;
+  const float kfr = kPi / (2.f * P.rc_r), kfa = kPi / (2.f * P.rc_a);
+  const float zeta = (float)(1 << P.zeta_sq);
   double* F = io->forces;
   const int rows = ws.seg[S];
-  for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows;
-       row += (gridDim.x * blockDim.x) >> 5) {
-    if (ws.row_atom[row] < 0) continue;
-    const float4 pi = ws.pos4[row];
-    const SysDesc& sd = sys[ws.row_info[row]];
-    const float ell[3] = {sd.ellf[0], sd.ellf[1], sd.ellf[2]};
-    const float* dg = ws.dEdG + (size_t)row * D;
-    for (int f = lane; f < D; f += 32) wsm[f] = dg[f];
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  int cached_sys = -1;
+  for (int pr = warp; 2 * pr < rows; pr += nwarps) {
+    const int row = 2 * pr + half;
+    const bool live = row < rows && ws.row_atom[row] >= 0;
+    float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (live) {
+      pi = ws.pos4[row];
+      const int sid = ws.row_info[row];
+      if (sid != cached_sys) {
+        const SysDesc& sd = sys[sid];
+        const float ell[3] = {sd.ellf[0], sd.ellf[1], sd.ellf[2]};
+        for (int c = hl; c < 27; c += 16) sh[c] = shift_vec(c, ell);
+        cached_sys = sid;
+      }
+      const float4* dg = reinterpret_cast<const float4*>(ws.dEdG + (size_t)row * D);
+      for (int f = hl; f < D / 4; f += 16) reinterpret_cast<float4*>(wsm)[f] = dg[f];
+    }
+    load_counts(ws, S, row, live, ca, rc, hl);
     __syncwarp();
+    const int* lr = ws.nbr_r + (size_t)row * cr;
     float fix = 0.f, fiy = 0.f, fiz = 0.f;  // force on the centre atom
 
-    // ---------------- radial
-    const int* lr = ws.nbr_r + (size_t)row * ws.cap_r;
-    int o = 0;
-#pragma unroll
+    // ---------------- radial: every slot written once (initialises fsl)
+#pragma unroll 1
     for (int s = 0; s < S; ++s) {
-      const int n_s = ws.cnt_r[(size_t)row * kMaxS + s];
-      for (int k = lane; k < n_s; k += 32) {
-        const int e = lr[o + k];
-        const float4 pj = ws.pos4[nbr_row(e)];
-        const float3 sh = image_shift(nbr_code(e), ell);
-        const float dx = (pj.x - pi.x) + sh.x, dy = (pj.y - pi.y) + sh.y, dz = (pj.z - pi.z) + sh.z;
-        const float r = sqrtf(dx * dx + dy * dy + dz * dz);
-        const float fc = cutoff_fc(r, P.rc_r), dfc = cutoff_dfc(r, P.rc_r);
-        float g = 0.f;  // dE_i / dr
+      const int n_s = rc->nr[s], o_s = rc->orr[s];
+      const int nmax = max(n_s, __shfl_xor_sync(0xffffffffu, n_s, 16));
+      float w16[kNRad];
 #pragma unroll
-        for (int m = 0; m < kNRad; ++m) {
-          const float x = r - P.shf_r[m];
-          const float em = expf(-P.eta_r * x * x);
-          g = fmaf(wsm[s * kNRad + m] * em, fmaf(-2.f * P.eta_r * x, fc, dfc), g);
-        }
-        g *= 0.25f / r;
-        // dE_i/dr_j = g d, dE_i/dr_i = -g d; F = -dE/dr
-        const int oj = pos4_orig(pj);
-        atomicAdd(&F[3 * oj], (double)(-g * dx));
-        atomicAdd(&F[3 * oj + 1], (double)(-g * dy));
-        atomicAdd(&F[3 * oj + 2], (double)(-g * dz));
-        fix += g * dx; fiy += g * dy; fiz += g * dz;
+      for (int m = 0; m < kNRad; m += 4) {
+        const float4 q = reinterpret_cast<const float4*>(wsm + s * kNRad)[m / 4];
+        w16[m] = q.x; w16[m + 1] = q.y; w16[m + 2] = q.z; w16[m + 3] = q.w;
       }
-      o += n_s;
+      for (int k0 = 0; k0 < nmax; k0 += 16) {
+        const int k = k0 + hl;
+        if (k < n_s) {
+          const int e = lr[o_s + k];
+          const float4 pj = ws.pos4[nbr_row(e)];
+          const float4 sv = sh[nbr_code(e)];
+          const float dx = (pj.x - pi.x) + sv.x, dy = (pj.y - pi.y) + sv.y, dz = (pj.z - pi.z) + sv.z;
+          const float r2 = dx * dx + dy * dy + dz * dz;
+          const float ir = rsqrtf(r2);
+          const float r = r2 * ir;
+          float fc, dfc;
+          cutoff(r, P.rc_r, kfr, fc, dfc);
+          float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+          for (int m = 0; m < kNRad; ++m) {
+            const float x = r - P.shf_r[m];
+            const float we = w16[m] * exp2f(kr * x * x);
+            s0 += we;
+            s1 = fmaf(we, x, s1);
+          }
+          // dE_i/dr_ij divided by r_ij; dE_i/dr_j = g d, dE_i/dr_i = -g d
+          const float g = 0.25f * fmaf(dfc, s0, -2.f * P.eta_r * fc * s1) * ir;
+          const int slot = o_s + k;
+          fsl[3 * slot] = -g * dx;
+          fsl[3 * slot + 1] = -g * dy;
+          fsl[3 * slot + 2] = -g * dz;
+          origs[slot] = pos4_orig(pj);
+          fix = fmaf(g, dx, fix);
+          fiy = fmaf(g, dy, fiy);
+          fiz = fmaf(g, dz, fiz);
+        }
+      }
     }
 
-    // ---------------- angular
-    int na_s[kMaxS], oa_s[kMaxS];
-    const int na = stage_angular(ws, P, row, pi, ell, geo, fcs, dfcs, origs, lane, na_s, oa_s);
-    for (int k = lane; k < 3 * na; k += 32) fsl[k] = 0.f;
+    // ---------------- angular: stage the neighbours inside rc_a
+#pragma unroll 1
+    for (int s = 0; s < S; ++s) {
+      const int n_a = rc->na[s], o_r = rc->orr[s], o_a = rc->oa[s];
+      for (int k = hl; k < n_a; k += 16) {
+        const int e = lr[o_r + k];
+        const float4 pj = ws.pos4[nbr_row(e)];
+        const float4 sv = sh[nbr_code(e)];
+        const float dx = (pj.x - pi.x) + sv.x, dy = (pj.y - pi.y) + sv.y, dz = (pj.z - pi.z) + sv.z;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float ir = rsqrtf(r2);
+        const float r = r2 * ir;
+        float fc, dfc;
+        cutoff(r, P.rc_a, kfa, fc, dfc);
+        geo[o_a + k] = make_float4(dx * ir, dy * ir, dz * ir, r);
+        aux[o_a + k] = make_float4(fc, dfc, ir, __int_as_float(o_r + k));
+      }
+    }
     __syncwarp();
-#pragma unroll
+#pragma unroll 1
     for (int s1 = 0; s1 < S; ++s1) {
-#pragma unroll
+#pragma unroll 1
       for (int s2 = s1; s2 < S; ++s2) {
-        const int pblk = pair_block(S, s1, s2);
         const bool diag = s1 == s2;
-        const int n1 = na_s[s1], n2 = na_s[s2];
+        const int n1 = rc->na[s1], n2 = rc->na[s2];
         const int T = diag ? n1 * (n1 - 1) / 2 : n1 * n2;
-        if (T == 0) continue;
-        const float* wb = wsm + kNRad * S + pblk * kNAng;
-        for (int t = lane; t < T; t += 32) {
-          int u, v;
-          triplet_uv(t, diag, n1, n2, oa_s[s1], oa_s[s2], u, v);
-          const AngGeo gu = geo[u], gv = geo[v];
-          const float c = gu.ex * gv.ex + gu.ey * gv.ey + gu.ez * gv.ez;
-          const float uc = 0.95f * c;
-          const float sn = sqrtf(fmaxf(0.f, 1.f - uc * uc));
-          const float isn = 1.0f / sn;
-          const float rbar = 0.5f * (gu.r + gv.r);
-          float Be[kNAngR], Bq[kNAngR];
+        const int Tmax = max(T, __shfl_xor_sync(0xffffffffu, T, 16));
+        if (Tmax == 0) continue;
+        const PairMap pm = make_map(diag, n1, n2, rc->oa[s1], rc->oa[s2]);
+        float wr[kNAng];
+        const float4* wb = reinterpret_cast<const float4*>(wsm + kNRad * S + pair_block(S, s1, s2) * kNAng);
 #pragma unroll
-          for (int a = 0; a < kNAngR; ++a) {
-            const float x = rbar - P.shf_a[a];
-            Be[a] = expf(-P.eta_a * x * x);
-            Bq[a] = -2.f * P.eta_a * x * Be[a];
-          }
-          float Pv = 0.f, Qv = 0.f, Rv = 0.f;
-          const float zeta = (float)(1 << P.zeta_sq);
-#pragma unroll
-          for (int z = 0; z < kNAngZ; ++z) {
-            const float bz = 0.5f + uc * P.hcos_z[z] + sn * P.hsin_z[z];
-            const float bzm = pow2k(bz, P.zeta_sq) / bz;  // bz^(zeta-1), bz >= 0.19 here
-            const float A = 2.f * bzm * bz;
-            const float dA = 2.f * zeta * bzm * 0.95f * (P.hcos_z[z] - uc * P.hsin_z[z] * isn);
-            float Wz = 0.f, Wq = 0.f;
+        for (int q = 0; q < kNAng / 4; ++q) {
+          const float4 x = wb[q];
+          wr[4 * q] = x.x; wr[4 * q + 1] = x.y; wr[4 * q + 2] = x.z; wr[4 * q + 3] = x.w;
+        }
+        for (int t0 = 0; t0 < Tmax; t0 += 16) {
+          const int t = t0 + hl;
+          if (t < T) {
+            int u, v;
+            map_pair(pm, t, u, v);
+            const float4 gu = geo[u], gv = geo[v], au = aux[u], av = aux[v];
+            const float c = gu.x * gv.x + gu.y * gv.y + gu.z * gv.z;
+            const float uc = 0.95f * c;
+            const float s2q = fmaxf(1.f - uc * uc, 1e-12f);
+            const float isn = rsqrtf(s2q);
+            const float sn = s2q * isn;
+            const float ucisn = uc * isn;
+            const float rbar = 0.5f * (gu.w + gv.w);
+            float Be[kNAngR], Bq[kNAngR], X[kNAngR], Y[kNAngR];
 #pragma unroll
             for (int a = 0; a < kNAngR; ++a) {
-              const float wt = wb[a * kNAngZ + z];
-              Wz = fmaf(wt, Be[a], Wz);
-              Wq = fmaf(wt, Bq[a], Wq);
+              const float x = rbar - P.shf_a[a];
+              Be[a] = exp2f(ka * x * x);
+              Bq[a] = -2.f * P.eta_a * x * Be[a];
+              X[a] = 0.f;
+              Y[a] = 0.f;
             }
-            Pv = fmaf(A, Wz, Pv);
-            Qv = fmaf(A, Wq, Qv);
-            Rv = fmaf(dA, Wz, Rv);
+#pragma unroll
+            for (int z = 0; z < kNAngZ; ++z) {
+              const float base = fmaf(sn, P.hsin_z[z], fmaf(uc, P.hcos_z[z], 0.5f));
+              float bz, bzm1;
+              pow_zeta<ZSQ>(base, P.zeta_sq, bz, bzm1);
+              // d base / d cos(theta) = 0.95 (cos(theta_z) - sin(theta_z) u / sqrt(1-u^2)) / 2
+              const float dbase = 0.95f * fmaf(-ucisn, P.hsin_z[z], P.hcos_z[z]);
+              const float dA = zeta * bzm1 * dbase;
+#pragma unroll
+              for (int a = 0; a < kNAngR; ++a) {
+                X[a] = fmaf(wr[a * kNAngZ + z], bz, X[a]);
+                Y[a] = fmaf(wr[a * kNAngZ + z], dA, Y[a]);
+              }
+            }
+            float Pv = 0.f, Qv = 0.f, Rv = 0.f;
+#pragma unroll
+            for (int a = 0; a < kNAngR; ++a) {
+              Pv = fmaf(Be[a], X[a], Pv);
+              Qv = fmaf(Bq[a], X[a], Qv);
+              Rv = fmaf(Be[a], Y[a], Rv);
+            }
+            // the angular term carries a factor 2 (2 ((1 + cos)/2)^zeta)
+            const float fu = au.x, fv = av.x;
+            const float fuv = fu * fv;
+            const float dEdru = 2.f * fmaf(au.y * fv, Pv, 0.5f * fuv * Qv);
+            const float dEdrv = 2.f * fmaf(fu * av.y, Pv, 0.5f * fuv * Qv);
+            const float dEdc = 2.f * fuv * Rv;
+            // d cos/d d_u = (e_v - c e_u)/r_u ; d cos/d d_v = (e_u - c e_v)/r_v
+            const float Au = fmaf(-dEdc * c, au.z, dEdru), Bu = dEdc * au.z;
+            const float Av = fmaf(-dEdc * c, av.z, dEdrv), Bv = dEdc * av.z;
+            const float gux = fmaf(Au, gu.x, Bu * gv.x), guy = fmaf(Au, gu.y, Bu * gv.y),
+                        guz = fmaf(Au, gu.z, Bu * gv.z);
+            const float gvx = fmaf(Av, gv.x, Bv * gu.x), gvy = fmaf(Av, gv.y, Bv * gu.y),
+                        gvz = fmaf(Av, gv.z, Bv * gu.z);
+            const int su = __float_as_int(au.w), svs = __float_as_int(av.w);
+            atomicAdd(&fsl[3 * su], -gux);
+            atomicAdd(&fsl[3 * su + 1], -guy);
+            atomicAdd(&fsl[3 * su + 2], -guz);
+            atomicAdd(&fsl[3 * svs], -gvx);
+            atomicAdd(&fsl[3 * svs + 1], -gvy);
+            atomicAdd(&fsl[3 * svs + 2], -gvz);
+            fix += gux + gvx;
+            fiy += guy + gvy;
+            fiz += guz + gvz;
           }
-          const float fu = fcs[u], fv = fcs[v];
-          const float dEdru = dfcs[u] * fv * Pv + 0.5f * fu * fv * Qv;
-          const float dEdrv = fu * dfcs[v] * Pv + 0.5f * fu * fv * Qv;
-          const float dEdc = fu * fv * Rv;
-          const float iru = 1.f / gu.r, irv = 1.f / gv.r;
-          // dc/dd_u = (e_v - c e_u)/r_u ; dc/dd_v = (e_u - c e_v)/r_v
-          const float gux = dEdru * gu.ex + dEdc * (gv.ex - c * gu.ex) * iru;
-          const float guy = dEdru * gu.ey + dEdc * (gv.ey - c * gu.ey) * iru;
-          const float guz = dEdru * gu.ez + dEdc * (gv.ez - c * gu.ez) * iru;
-          const float gvx = dEdrv * gv.ex + dEdc * (gu.ex - c * gv.ex) * irv;
-          const float gvy = dEdrv * gv.ey + dEdc * (gu.ey - c * gv.ey) * irv;
-          const float gvz = dEdrv * gv.ez + dEdc * (gu.ez - c * gv.ez) * irv;
-          atomicAdd(&fsl[3 * u], -gux);
-          atomicAdd(&fsl[3 * u + 1], -guy);
-          atomicAdd(&fsl[3 * u + 2], -guz);
-          atomicAdd(&fsl[3 * v], -gvx);
-          atomicAdd(&fsl[3 * v + 1], -gvy);
-          atomicAdd(&fsl[3 * v + 2], -gvz);
-          fix += gux + gvx; fiy += guy + gvy; fiz += guz + gvz;
         }
       }
     }
     __syncwarp();
-    for (int k = lane; k < na; k += 32) {
+    // one FP64 add per neighbour slot and component
+    int ntot = 0;
+    for (int s = 0; s < S; ++s) ntot += rc->nr[s];
+    for (int k = hl; k < ntot; k += 16) {
       const int oj = origs[k];
       atomicAdd(&F[3 * oj], (double)fsl[3 * k]);
       atomicAdd(&F[3 * oj + 1], (double)fsl[3 * k + 1]);
       atomicAdd(&F[3 * oj + 2], (double)fsl[3 * k + 2]);
     }
-    fix = warp_sum(fix); fiy = warp_sum(fiy); fiz = warp_sum(fiz);
-    if (lane == 0) {
+    fix = hw_sum(fix);
+    fiy = hw_sum(fiy);
+    fiz = hw_sum(fiz);
+    if (live && hl == 0) {
       const int oi = pos4_orig(pi);
       atomicAdd(&F[3 * oi], (double)fix);
       atomicAdd(&F[3 * oi + 1], (double)fiy);
@@ -342,53 +574,72 @@ __global__ void __launch_bounds__(256) k_aev_bwd(const EvalIO* __restrict__ io,
   }
 }
 
-size_t aev_fwd_smem(int cap_a) { return 8 * (size_t)cap_a * (sizeof(AngGeo) + sizeof(float)); }
-size_t aev_bwd_smem(int cap_a, int D) {
-  return 8 * ((size_t)cap_a * (sizeof(AngGeo) + 6 * sizeof(float)) + (size_t)D * sizeof(float));
+// --------------------------------------------------------------------------
+// launchers
+
+size_t aev_fwd_smem(int cap_a) {
+  return 16 * ((size_t)(cap_a + 27) * sizeof(float4) + (size_t)cap_a * sizeof(float) + sizeof(RowCounts));
+}
+size_t aev_bwd_smem(int cap_a, int cap_r, int D) {
+  return 8 * ((size_t)(2 * cap_a + 27) * sizeof(float4) + ((size_t)4 * cap_r + D) * sizeof(float) +
+              sizeof(RowCounts));
 }
 
-template <int S>
-void launch_aev_fwd_t(int grid, cudaStream_t st, const SysDesc* sys, const DescParams& P,
-                      const Workspace& ws, int bf16) {
-  k_aev_fwd<S><<<grid, 256, aev_fwd_smem(ws.cap_a), st>>>(sys, P, ws, bf16);
-}
-template <int S>
-void launch_aev_bwd_t(int grid, cudaStream_t st, const EvalIO* io, const SysDesc* sys,
-                      const DescParams& P, const Workspace& ws) {
-  k_aev_bwd<S><<<grid, 256, aev_bwd_smem(ws.cap_a, P.D), st>>>(io, sys, P, ws);
+static int warps_grid(long long rows, int warps_per_block, int nsm, int per_sm) {
+  const long long warps = (rows + 1) / 2;
+  long long g = (warps + warps_per_block - 1) / warps_per_block;
+  const long long cap = (long long)nsm * per_sm;
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
 }
 
-void launch_aev_fwd(int grid, cudaStream_t st, const SysDesc* sys, const DescParams& P,
+template <int S, int ZSQ>
+static void fwd_t(long long rows, int nsm, cudaStream_t st, const SysDesc* sys, const DescParams& P,
+                  const Workspace& ws, int bf16) {
+  k_aev_fwd<S, ZSQ><<<warps_grid(rows, 8, nsm, 8), 256, aev_fwd_smem(ws.cap_a), st>>>(sys, P, ws, bf16);
+}
+template <int S, int ZSQ>
+static void bwd_t(long long rows, int nsm, cudaStream_t st, const EvalIO* io, const SysDesc* sys,
+                  const DescParams& P, const Workspace& ws) {
+  k_aev_bwd<S, ZSQ><<<warps_grid(rows, 4, nsm, 16), 128, aev_bwd_smem(ws.cap_a, ws.cap_r, P.D), st>>>(
+      io, sys, P, ws);
+}
+
+void launch_aev_fwd(long long rows, int nsm, cudaStream_t st, const SysDesc* sys, const DescParams& P,
                     const Workspace& ws, int bf16) {
+  const bool z5 = P.zeta_sq == 5;
   switch (P.S) {
-    case 1: launch_aev_fwd_t<1>(grid, st, sys, P, ws, bf16); break;
-    case 2: launch_aev_fwd_t<2>(grid, st, sys, P, ws, bf16); break;
-    case 3: launch_aev_fwd_t<3>(grid, st, sys, P, ws, bf16); break;
-    default: launch_aev_fwd_t<4>(grid, st, sys, P, ws, bf16); break;
+    case 1: z5 ? fwd_t<1, 5>(rows, nsm, st, sys, P, ws, bf16) : fwd_t<1, -1>(rows, nsm, st, sys, P, ws, bf16); break;
+    case 2: z5 ? fwd_t<2, 5>(rows, nsm, st, sys, P, ws, bf16) : fwd_t<2, -1>(rows, nsm, st, sys, P, ws, bf16); break;
+    case 3: z5 ? fwd_t<3, 5>(rows, nsm, st, sys, P, ws, bf16) : fwd_t<3, -1>(rows, nsm, st, sys, P, ws, bf16); break;
+    default: z5 ? fwd_t<4, 5>(rows, nsm, st, sys, P, ws, bf16) : fwd_t<4, -1>(rows, nsm, st, sys, P, ws, bf16); break;
   }
 }
 
-void launch_aev_bwd(int grid, cudaStream_t st, const EvalIO* io, const SysDesc* sys,
+void launch_aev_bwd(long long rows, int nsm, cudaStream_t st, const EvalIO* io, const SysDesc* sys,
                     const DescParams& P, const Workspace& ws) {
+  const bool z5 = P.zeta_sq == 5;
   switch (P.S) {
-    case 1: launch_aev_bwd_t<1>(grid, st, io, sys, P, ws); break;
-    case 2: launch_aev_bwd_t<2>(grid, st, io, sys, P, ws); break;
-    case 3: launch_aev_bwd_t<3>(grid, st, io, sys, P, ws); break;
-    default: launch_aev_bwd_t<4>(grid, st, io, sys, P, ws); break;
+    case 1: z5 ? bwd_t<1, 5>(rows, nsm, st, io, sys, P, ws) : bwd_t<1, -1>(rows, nsm, st, io, sys, P, ws); break;
+    case 2: z5 ? bwd_t<2, 5>(rows, nsm, st, io, sys, P, ws) : bwd_t<2, -1>(rows, nsm, st, io, sys, P, ws); break;
+    case 3: z5 ? bwd_t<3, 5>(rows, nsm, st, io, sys, P, ws) : bwd_t<3, -1>(rows, nsm, st, io, sys, P, ws); break;
+    default: z5 ? bwd_t<4, 5>(rows, nsm, st, io, sys, P, ws) : bwd_t<4, -1>(rows, nsm, st, io, sys, P, ws); break;
   }
+}
+
+template <class K>
+static cudaError_t big_smem(K k) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
 }
 
 cudaError_t aev_set_smem_limits() {
   cudaError_t e = cudaSuccess;
-  const int big = 200 * 1024;
-  e = cudaFuncSetAttribute(k_aev_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big); if (e) return e;
-  e = cudaFuncSetAttribute(k_aev_fwd<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big); if (e) return e;
-  e = cudaFuncSetAttribute(k_aev_fwd<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big); if (e) return e;
-  e = cudaFuncSetAttribute(k_aev_fwd<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big); if (e) return e;
-  e = cudaFuncSetAttribute(k_aev_bwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big); if (e) return e;
-  e = cudaFuncSetAttribute(k_aev_bwd<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big); if (e) return e;
-  e = cudaFuncSetAttribute(k_aev_bwd<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, big); if (e) return e;
-  e = cudaFuncSetAttribute(k_aev_bwd<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+#define BS(k) if ((e = big_smem(k)) != cudaSuccess) return e
+  BS((k_aev_fwd<1, 5>)); BS((k_aev_fwd<2, 5>)); BS((k_aev_fwd<3, 5>)); BS((k_aev_fwd<4, 5>));
+  BS((k_aev_fwd<1, -1>)); BS((k_aev_fwd<2, -1>)); BS((k_aev_fwd<3, -1>)); BS((k_aev_fwd<4, -1>));
+  BS((k_aev_bwd<1, 5>)); BS((k_aev_bwd<2, 5>)); BS((k_aev_bwd<3, 5>)); BS((k_aev_bwd<4, 5>));
+  BS((k_aev_bwd<1, -1>)); BS((k_aev_bwd<2, -1>)); BS((k_aev_bwd<3, -1>)); BS((k_aev_bwd<4, -1>));
+#undef BS
   return e;
 }
 

@@ -195,13 +195,17 @@ __global__ void __launch_bounds__(256) k_binsort(const EvalIO* __restrict__ io, 
 // Warp per row.  Candidates: for each neighbour species s', the atoms of the
 // 27 virtual cells around the row's cell, flattened into one index space so
 // that all 32 lanes test candidates.  A candidate (j, image m) is kept if
-// |off_j - off_i + m*ell| < rc_r and it is not the atom itself.
+// |off_j - off_i + m*ell| < rc_r and it is not the atom itself.  Entries
+// within rc_a go straight to the row's list; radial-only entries wait in a
+// per-warp shared buffer and are appended after the species' angular ones.
 __global__ void __launch_bounds__(256) k_neighbors(const EvalIO* __restrict__ io,
                                                    const SysDesc* __restrict__ sys,
                                                    DescParams P, Workspace ws) {
   __shared__ int s_start[8][32];
   __shared__ int s_excl[8][33];
+  extern __shared__ int s_stage[];  // [8][cap_r]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int* stage = s_stage + (size_t)w * ws.cap_r;
   const int rows = ws.seg[P.S];
   const int TC = io->total_cells;
   const float rcr2 = P.rc_r * P.rc_r, rca2 = P.rc_a * P.rc_a;
@@ -219,8 +223,7 @@ __global__ void __launch_bounds__(256) k_neighbors(const EvalIO* __restrict__ io
     const int cx = pc & 1023, cy = (pc >> 10) & 1023, cz = (pc >> 20) & 1023;
     const float ell[3] = {sd.ellf[0], sd.ellf[1], sd.ellf[2]};
     int* lr = ws.nbr_r + (size_t)row * ws.cap_r;
-    int* la = ws.nbr_a + (size_t)row * ws.cap_a;
-    int nr = 0, na = 0;  // written so far (all species)
+    int nr = 0, na = 0;  // entries found so far (all species), may exceed capacity
     for (int sp = 0; sp < P.S; ++sp) {
       int len = 0, st = 0;
       if (lane < 27) {
@@ -250,10 +253,10 @@ __global__ void __launch_bounds__(256) k_neighbors(const EvalIO* __restrict__ io
       s_excl[w][lane] = incl - len;
       if (lane == 31) s_excl[w][32] = total;
       __syncwarp();
-      int cnt_r_sp = 0, cnt_a_sp = 0;
+      int n_ang = 0, n_ro = 0;  // this species: angular entries, radial-only entries
       for (int t0 = 0; t0 < total; t0 += 32) {
         const int t = t0 + lane;
-        bool is_r = false, is_a = false;
+        bool is_a = false, is_ro = false;
         int entry = 0;
         if (t < total) {
           int lo = 0, hi = 26;
@@ -267,31 +270,37 @@ __global__ void __launch_bounds__(256) k_neighbors(const EvalIO* __restrict__ io
           const float dy = (pj.y - pi.y) + (float)((lo / 3) % 3 - 1) * ell[1];
           const float dz = (pj.z - pi.z) + (float)(lo % 3 - 1) * ell[2];
           const float r2 = dx * dx + dy * dy + dz * dz;
-          is_r = r2 < rcr2 && !(j == row && lo == 13);
+          const bool is_r = r2 < rcr2 && !(j == row && lo == 13);
           is_a = is_r && r2 < rca2;
+          is_ro = is_r && !is_a;
           entry = pack_nbr(j, lo);
         }
-        const unsigned br = __ballot_sync(0xffffffffu, is_r);
         const unsigned ba = __ballot_sync(0xffffffffu, is_a);
+        const unsigned bro = __ballot_sync(0xffffffffu, is_ro);
         const unsigned below = (1u << lane) - 1u;
-        if (is_r) {
-          const int pos = nr + cnt_r_sp + __popc(br & below);
+        if (is_a) {
+          const int pos = nr + n_ang + __popc(ba & below);
           if (pos < ws.cap_r) lr[pos] = entry;
         }
-        if (is_a) {
-          const int pos = na + cnt_a_sp + __popc(ba & below);
-          if (pos < ws.cap_a) la[pos] = entry;
+        if (is_ro) {
+          const int pos = n_ro + __popc(bro & below);
+          if (pos < ws.cap_r) stage[pos] = entry;
         }
-        cnt_r_sp += __popc(br);
-        cnt_a_sp += __popc(ba);
+        n_ang += __popc(ba);
+        n_ro += __popc(bro);
       }
       __syncwarp();
-      // store counts clamped to capacity so readers never run past a list
-      const int keep_r = max(0, min(cnt_r_sp, ws.cap_r - nr));
-      const int keep_a = max(0, min(cnt_a_sp, ws.cap_a - na));
-      if (lane == 0) { cr[sp] = keep_r; ca[sp] = keep_a; }
-      nr += cnt_r_sp;
-      na += cnt_a_sp;
+      // append the radial-only entries after this species' angular ones
+      const int base = nr + n_ang;
+      for (int k = lane; k < n_ro; k += 32)
+        if (base + k < ws.cap_r && k < ws.cap_r) lr[base + k] = stage[k];
+      __syncwarp();
+      // counts clamped to what the list holds, so readers never run past it
+      const int keep = max(0, min(n_ang + n_ro, ws.cap_r - nr));
+      const int keep_a = min(n_ang, keep);
+      if (lane == 0) { cr[sp] = keep; ca[sp] = keep_a; }
+      nr += n_ang + n_ro;
+      na += n_ang;
     }
     if (lane == 0) {
       for (int sp = P.S; sp < kMaxS; ++sp) { cr[sp] = 0; ca[sp] = 0; }
@@ -301,6 +310,13 @@ __global__ void __launch_bounds__(256) k_neighbors(const EvalIO* __restrict__ io
       if (na > ws.cap_a) atomicOr(&ws.flags[kFlagOverflowA], 1);
     }
   }
+}
+
+size_t neighbors_smem(int cap_r) { return 8 * sizeof(int) * (size_t)cap_r; }
+
+cudaError_t neighbors_set_smem_limits() {
+  return cudaFuncSetAttribute(k_neighbors, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)neighbors_smem(4096));
 }
 
 }  // namespace nnp

@@ -103,7 +103,6 @@ int nnp_ctx::ensure_capacity(long long n, int B, long long bins, long long rows)
   GR(b_cnt_r, c_rows5, (size_t)rows * kMaxS);
   GR(b_cnt_a, c_rows6, (size_t)rows * kMaxS);
   GR(b_nbr_r, c_nbr_r, (size_t)rows * cap_r);
-  GR(b_nbr_a, c_nbr_a, (size_t)rows * cap_a);
   GR(b_G, c_G, (size_t)rows * P.D);
   GR(b_Gh, c_Gh, (size_t)rows * P.D);
   GR(b_dEdG, c_dEdG, (size_t)rows * P.D);
@@ -136,7 +135,6 @@ Workspace nnp_ctx::workspace() const {
   w.cnt_r = b_cnt_r;
   w.cnt_a = b_cnt_a;
   w.nbr_r = b_nbr_r;
-  w.nbr_a = b_nbr_a;
   w.G = b_G;
   w.Gh = b_Gh;
   w.dEdG = b_dEdG;
@@ -175,10 +173,10 @@ int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows)
   k_binsort<<<g_bins, 256, 0, stream>>>(io, P.S, (cfg.flags & NNP_FLAG_NONDETERMINISTIC_BINS) ? 0 : 1,
                                         w); ++launches;
   mark_stage(1, capturing);
-  k_neighbors<<<g_rows, 256, 0, stream>>>(io, sys, P, w); ++launches;
+  k_neighbors<<<g_rows, 256, neighbors_smem(cap_r), stream>>>(io, sys, P, w); ++launches;
   mark_stage(2, capturing);
   const int bf16 = cfg.precision != NNP_FP32;
-  launch_aev_fwd(g_rows, stream, sys, P, w, bf16); ++launches;
+  launch_aev_fwd(rows, nsm, stream, sys, P, w, bf16); ++launches;
   mark_stage(3, capturing);
   const int g_tiles = (int)std::min<long long>(rows / 64, (long long)nsm);
   if (cfg.precision == NNP_FP32) {
@@ -189,7 +187,7 @@ int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows)
     ++launches;
   }
   mark_stage(4, capturing);
-  launch_aev_bwd(g_rows, stream, io, sys, P, w); ++launches;
+  launch_aev_bwd(rows, nsm, stream, io, sys, P, w); ++launches;
   mark_stage(5, capturing);
   CK(cudaGetLastError());
   launches_per_eval = launches;

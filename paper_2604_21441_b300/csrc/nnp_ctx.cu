@@ -27,6 +27,7 @@ int nnp_ctx::init_device() {
   }
   if (cfg.flags & NNP_FLAG_STAGE_EVENTS)
     for (auto& ev : stage_ev) CK(cudaEventCreate(&ev));
+  CK(neighbors_set_smem_limits());
   CK(aev_set_smem_limits());
   CK(mlp_f32_set_smem_limits());
   CK(cudaMalloc(&b_seg, sizeof(int) * (kMaxS + 2)));
@@ -82,7 +83,7 @@ nnp_ctx::~nnp_ctx() {
   mlp_tc_free(this);
   void* bufs[] = {b_bin_count, b_bin_start, b_bin_len, b_atom_bin, b_atom_slot, b_atom_cell,
                   b_atom_sys, b_atom_off, b_row_atom, b_row_info, b_row_cell, b_pos4, b_cnt_r,
-                  b_cnt_a, b_nbr_r, b_nbr_a, b_G, b_dEdG, b_Ei, b_Gh, b_sys, b_pos_stage,
+                  b_cnt_a, b_nbr_r, b_G, b_dEdG, b_Ei, b_Gh, b_sys, b_pos_stage,
                   b_Z_stage, b_F_stage, b_E_stage, b_seg, b_flags, d_zlut, d_io, b_wf32};
   for (void* p : bufs)
     if (p) cudaFree(p);

@@ -15,11 +15,14 @@ __global__ void k_scan(const EvalIO* io, int S, Workspace ws);
 __global__ void k_scatter(const EvalIO* io, Workspace ws);
 __global__ void k_binsort(const EvalIO* io, int S, int sort, Workspace ws);
 __global__ void k_neighbors(const EvalIO* io, const SysDesc* sys, DescParams P, Workspace ws);
+size_t neighbors_smem(int cap_r);
+cudaError_t neighbors_set_smem_limits();
 
 // k_aev.cu
-void launch_aev_fwd(int grid, cudaStream_t st, const SysDesc* sys, const DescParams& P,
+// rows: upper bound of the rows of the evaluation (grid sizing only)
+void launch_aev_fwd(long long rows, int nsm, cudaStream_t st, const SysDesc* sys, const DescParams& P,
                     const Workspace& ws, int bf16);
-void launch_aev_bwd(int grid, cudaStream_t st, const EvalIO* io, const SysDesc* sys,
+void launch_aev_bwd(long long rows, int nsm, cudaStream_t st, const EvalIO* io, const SysDesc* sys,
                     const DescParams& P, const Workspace& ws);
 cudaError_t aev_set_smem_limits();
 
@@ -60,8 +63,8 @@ struct nnp_ctx {
   int *b_row_atom = nullptr, *b_row_info = nullptr, *b_row_cell = nullptr;
   float4* b_pos4 = nullptr;
   size_t c_rows1 = 0, c_rows2 = 0, c_rows3 = 0, c_rows4 = 0, c_rows5 = 0, c_rows6 = 0;
-  int *b_cnt_r = nullptr, *b_cnt_a = nullptr, *b_nbr_r = nullptr, *b_nbr_a = nullptr;
-  size_t c_nbr_r = 0, c_nbr_a = 0;
+  int *b_cnt_r = nullptr, *b_cnt_a = nullptr, *b_nbr_r = nullptr;
+  size_t c_nbr_r = 0;
   float *b_G = nullptr, *b_dEdG = nullptr, *b_Ei = nullptr;
   __nv_bfloat16* b_Gh = nullptr;
   size_t c_G = 0, c_Gh = 0, c_dEdG = 0, c_Ei = 0;

@@ -11,8 +11,10 @@
 //     (off_j - off_i) + m * ell with m in {-1, 0, 1}^3, so FP32 rounding does
 //     not grow with the box edge.
 //   * neighbour entries: row index j (27 bits) | image code (5 bits), code =
-//     (mx+1)*9 + (my+1)*3 + (mz+1).  Lists are grouped by neighbour species
-//     (counts per species in cnt_r / cnt_a).
+//     (mx+1)*9 + (my+1)*3 + (mz+1).  One list per row, grouped by neighbour
+//     species; inside a species segment the entries within the angular
+//     cutoff come first (cnt_a of them), then the radial-only ones (cnt_r
+//     counts the whole segment).
 //   * G / dEdG: row-major [rows][D] FP32 (plus a BF16 copy for tensor cores).
 #pragma once
 #include <cstdint>
@@ -98,14 +100,14 @@ struct Workspace {
   int* row_cell;    // [max_rows]  local cell (cx | cy << 10 | cz << 20)
   int* cnt_r;       // [max_rows * kMaxS]
   int* cnt_a;       // [max_rows * kMaxS]
-  int* nbr_r;       // [max_rows * cap_r]
-  int* nbr_a;       // [max_rows * cap_a]
+  int* nbr_r;       // [max_rows * cap_r]: per neighbour species, angular entries first
   float* G;         // [max_rows * D]
   __nv_bfloat16* Gh;  // [max_rows * D]
   float* dEdG;      // [max_rows * D]
   float* Ei;        // [max_rows]
   int* flags;       // [kNumFlags]
-  int cap_r, cap_a;
+  int cap_r;        // radial list capacity per row
+  int cap_a;        // angular neighbours per row that the descriptor kernels stage
   long long max_rows;
 };
 

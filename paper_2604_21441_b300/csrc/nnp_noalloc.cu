@@ -58,8 +58,7 @@ constexpr size_t o_row_cell = o_row_info + al256(sizeof(int) * kNAMaxRows);
 constexpr size_t o_cnt_r = o_row_cell + al256(sizeof(int) * kNAMaxRows);
 constexpr size_t o_cnt_a = o_cnt_r + al256(sizeof(int) * kNAMaxRows * kMaxS);
 constexpr size_t o_nbr_r = o_cnt_a + al256(sizeof(int) * kNAMaxRows * kMaxS);
-constexpr size_t o_nbr_a = o_nbr_r + al256(sizeof(int) * kNAMaxRows * kNACapR);
-constexpr size_t o_G = o_nbr_a + al256(sizeof(int) * kNAMaxRows * kNACapA);
+constexpr size_t o_G = o_nbr_r + al256(sizeof(int) * kNAMaxRows * kNACapR);
 constexpr size_t o_dEdG = o_G + al256(sizeof(float) * kNAMaxRows * kMaxD);
 constexpr size_t o_Ei = o_dEdG + al256(sizeof(float) * kNAMaxRows * kMaxD);
 constexpr size_t o_flags = o_Ei + al256(sizeof(float) * kNAMaxRows);
@@ -188,7 +187,6 @@ extern "C" int nnp_eval_noalloc(nnp_ctx* ctx, int64_t n, const double* pos, cons
   w.cnt_r = reinterpret_cast<int*>(base + o_cnt_r);
   w.cnt_a = reinterpret_cast<int*>(base + o_cnt_a);
   w.nbr_r = reinterpret_cast<int*>(base + o_nbr_r);
-  w.nbr_a = reinterpret_cast<int*>(base + o_nbr_a);
   w.G = reinterpret_cast<float*>(base + o_G);
   w.Gh = reinterpret_cast<__nv_bfloat16*>(base + o_G);  // unused: FP32 form writes no BF16 copy
   w.dEdG = reinterpret_cast<float*>(base + o_dEdG);
@@ -223,10 +221,10 @@ extern "C" int nnp_eval_noalloc(nnp_ctx* ctx, int64_t n, const double* pos, cons
   k_scan<<<1, 1024, 0, st>>>(d_io, P.S, w);
   k_scatter<<<g_atoms, 256, 0, st>>>(d_io, w);
   k_binsort<<<g_bins, 256, 0, st>>>(d_io, P.S, 1, w);
-  k_neighbors<<<g_rows, 256, 0, st>>>(d_io, d_sys, P, w);
-  launch_aev_fwd(g_rows, st, d_sys, P, w, 0);
+  k_neighbors<<<g_rows, 256, neighbors_smem(w.cap_r), st>>>(d_io, d_sys, P, w);
+  launch_aev_fwd(rows, nsm, st, d_sys, P, w, 0);
   launch_mlp_f32(g_tiles > 0 ? g_tiles : 1, st, d_io, P, w, ctx->wf32);
-  launch_aev_bwd(g_rows, st, d_io, d_sys, P, w);
+  launch_aev_bwd(rows, nsm, st, d_io, d_sys, P, w);
   NA_CK(cudaGetLastError());
   NA_CK(cudaMemcpyAsync(hflags, w.flags, sizeof hflags, cudaMemcpyDeviceToHost, st));
   NA_CK(cudaStreamSynchronize(st));
