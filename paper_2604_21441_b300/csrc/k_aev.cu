@@ -213,12 +213,13 @@ __global__ void __launch_bounds__(256) k_aev_fwd(const SysDesc* __restrict__ sys
     const int row = 2 * pr + half;
     const bool inrow = row < rows;
     const bool live = inrow && ws.row_atom[row] >= 0;
+    // FP32 form: row-major G; tensor-core forms: the swizzled BF16 tile copy only
     float* Grow = ws.G + (size_t)row * D;
-    __nv_bfloat16* Ghrow = ws.Gh + (size_t)row * D;
+    char* Gh = reinterpret_cast<char*>(ws.Gh);
     if (inrow && !live) {  // padding row: zero descriptor
       for (int f = hl; f < D; f += 16) {
-        Grow[f] = 0.f;
-        if (write_bf16) Ghrow[f] = __float2bfloat16(0.f);
+        if (write_bf16) *reinterpret_cast<__nv_bfloat16*>(Gh + gh_offset(row, f, D)) = __float2bfloat16(0.f);
+        else Grow[f] = 0.f;
       }
     }
     float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -264,8 +265,9 @@ __global__ void __launch_bounds__(256) k_aev_fwd(const SysDesc* __restrict__ sys
       }
       hw_reduce_scatter<kNRad>(acc, hl);
       if (live) {
-        Grow[s * kNRad + hl] = acc[0];
-        if (write_bf16) Ghrow[s * kNRad + hl] = __float2bfloat16(acc[0]);
+        if (write_bf16)
+          *reinterpret_cast<__nv_bfloat16*>(Gh + gh_offset(row, s * kNRad + hl, D)) = __float2bfloat16(acc[0]);
+        else Grow[s * kNRad + hl] = acc[0];
       }
     }
 
@@ -299,9 +301,9 @@ __global__ void __launch_bounds__(256) k_aev_fwd(const SysDesc* __restrict__ sys
         const int f0 = kNRad * S + pair_block(S, s1, s2) * kNAng + 2 * hl;
         if (Tmax == 0) {
           if (live) {
-            *reinterpret_cast<float2*>(Grow + f0) = make_float2(0.f, 0.f);
             if (write_bf16)
-              *reinterpret_cast<__nv_bfloat162*>(Ghrow + f0) = __floats2bfloat162_rn(0.f, 0.f);
+              *reinterpret_cast<__nv_bfloat162*>(Gh + gh_offset(row, f0, D)) = __floats2bfloat162_rn(0.f, 0.f);
+            else *reinterpret_cast<float2*>(Grow + f0) = make_float2(0.f, 0.f);
           }
           continue;
         }
@@ -337,10 +339,10 @@ __global__ void __launch_bounds__(256) k_aev_fwd(const SysDesc* __restrict__ sys
         }
         hw_reduce_scatter<kNAng>(acc, hl);
         if (live) {
-          *reinterpret_cast<float2*>(Grow + f0) = make_float2(2.f * acc[0], 2.f * acc[1]);
           if (write_bf16)
-            *reinterpret_cast<__nv_bfloat162*>(Ghrow + f0) =
+            *reinterpret_cast<__nv_bfloat162*>(Gh + gh_offset(row, f0, D)) =
                 __floats2bfloat162_rn(2.f * acc[0], 2.f * acc[1]);
+          else *reinterpret_cast<float2*>(Grow + f0) = make_float2(2.f * acc[0], 2.f * acc[1]);
         }
       }
     }

@@ -1,15 +1,551 @@
-// k_mlp_tc.cu -- per-element network on tcgen05 tensor cores (BF16 / FP8).
+// k_mlp_tc.cu -- per-element network on the 5th-generation tensor cores
+// (tcgen05.mma, BF16 operands, FP32 accumulators in tensor memory), fused:
+// forward D -> 160 -> 128 -> 96 -> 1 with CELU, atom energies and their FP64
+// sum per system, and the backward pass to dE_i/dG_i (chain rule of Eq. 2):
+//
+//   z_l = h_{l-1} W_l + b_l, h_l = CELU(z_l), E_i = h_3 w_4 + b_4
+//   g_3 = w_4 * CELU'(z_3), g_{l-1} = (g_l W_l^T) * CELU'(z_{l-1}), dE/dG = g_1 W_1^T
+//
+// One CTA (4 warps) per SM, persistent over 128-row tiles (one species per
+// tile).  Thread t owns row t of the tile, which is TMEM lane t.  Thread 0
+// issues the bulk (TMA) copies and the MMAs; all threads run the epilogues.
+// Shared memory holds three activation buffers and two weight buffers, every
+// operand in the K-major 128-byte-swizzled layout (slabs of 64 columns x 128
+// rows, 16-byte chunk j of row r stored at chunk j ^ (r & 7)).  The descriptor
+// tile arrives in that layout from the descriptor kernel; the six weight
+// matrices per species are pre-swizzled on the host.  The next weight matrix
+// streams in while the current layer runs.
+//
+// TMEM columns (512 allocated): z1 [0,160)  z2 [160,288)  z3 [288,384)
+// g2' [384,512)  g1' [160,320)  dE/dG [0, D).  CELU' comes from the FP32
+// pre-activations kept in TMEM, so the backward does not lose precision to
+// the BF16 activations.
+//
+// Every wait on an mbarrier is bounded; on timeout the kernel raises the
+// timeout flag, stops issuing work, waits (bounded) for its own copies and
+// MMAs, frees its tensor memory and returns.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
 #include "nnp_host.h"
 
 namespace nnp {
 
-int mlp_tc_init(nnp_ctx* ctx) {
-  return ctx->fail(NNP_ERR_UNSUPPORTED, "tensor-core network not built yet");
+namespace {
+
+constexpr int kTM = 128;                 // rows per tile (MMA M)
+constexpr int kSlab = kTM * 128;         // bytes of one 64-column slab
+constexpr uint32_t kTmemCols = 512;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any wait
+
+__host__ __device__ constexpr int slabs_of(int K) { return (K + 63) / 64; }
+__host__ __device__ constexpr int mat_bytes(int N, int K) { return slabs_of(K) * N * 128; }
+
+// ---- PTX wrappers ---------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
-int mlp_tc_set_weights(nnp_ctx*, int, const float*) { return NNP_OK; }
-void mlp_tc_free(nnp_ctx*) {}
-int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t, long long) {
-  return ctx->fail(NNP_ERR_UNSUPPORTED, "tensor-core network not built yet");
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the phase of the given parity; false after kWaitNs nanoseconds.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try(bar, parity))
+    if (global_ns() - t0 > kWaitNs) return false;
+  return true;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// K-major operand, 128-byte swizzle: start address, leading byte offset
+// (unused for this layout, 16 B), stride byte offset 1024 B between 8-row
+// groups, fixed version bits 0b001 at [46,49), swizzle mode 2 at [61,64).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// kind::f16 instruction descriptor: FP32 accumulate, BF16 A and B, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D[128 x N] (+)= A[128 x K] B[N x K]^T, K in steps of 16 (one MMA each).
+__device__ __forceinline__ void issue_gemm(uint32_t d_tmem, const uint8_t* A, const uint8_t* B, int N,
+                                           int K, bool accumulate_first) {
+  const uint32_t idesc = idesc_bf16(kTM, N);
+  const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+  for (int k = 0; k < K / 16; ++k) {
+    const uint32_t a = a0 + (uint32_t)(k >> 2) * kSlab + (uint32_t)(k & 3) * 32;
+    const uint32_t b = b0 + (uint32_t)(k >> 2) * (uint32_t)(N * 128) + (uint32_t)(k & 3) * 32;
+    mma_bf16(d_tmem, sw128_desc(a), sw128_desc(b), idesc, (k > 0 || accumulate_first) ? 1u : 0u);
+  }
+}
+
+__device__ __forceinline__ float celu_f(float z, float al) { return z > 0.f ? z : al * (__expf(z / al) - 1.f); }
+__device__ __forceinline__ float dcelu_f(float z, float inv_al) { return z > 0.f ? 1.f : __expf(z * inv_al); }
+
+// Store 16 values of row r, columns [c0, c0+16), as BF16 into a swizzled buffer.
+__device__ __forceinline__ void store_row16(uint8_t* buf, int r, int c0, const float (&v)[16]) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int ch = (c0 >> 3) + h;  // 16-byte chunk index along K
+    uint4 q;
+    __nv_bfloat162 p0 = __floats2bfloat162_rn(v[8 * h + 0], v[8 * h + 1]);
+    __nv_bfloat162 p1 = __floats2bfloat162_rn(v[8 * h + 2], v[8 * h + 3]);
+    __nv_bfloat162 p2 = __floats2bfloat162_rn(v[8 * h + 4], v[8 * h + 5]);
+    __nv_bfloat162 p3 = __floats2bfloat162_rn(v[8 * h + 6], v[8 * h + 7]);
+    q.x = *reinterpret_cast<uint32_t*>(&p0);
+    q.y = *reinterpret_cast<uint32_t*>(&p1);
+    q.z = *reinterpret_cast<uint32_t*>(&p2);
+    q.w = *reinterpret_cast<uint32_t*>(&p3);
+    uint8_t* dst = buf + (ch >> 3) * kSlab + r * 128 + (((ch & 7) ^ (r & 7)) << 4);
+    *reinterpret_cast<uint4*>(dst) = q;
+  }
+}
+
+}  // namespace
+
+// Pre-swizzled BF16 weights per species: forward W1^T (160 x D), W2^T
+// (128 x 160), W3^T (96 x 128); backward W3 (128 x 96), W2 (160 x 128),
+// W1 (D x 160); each [N rows x K cols], K-major.
+struct MlpTcWeights {
+  const uint8_t* m[kMaxS][6];
+};
+
+template <int D>
+__global__ void __launch_bounds__(128, 1) k_mlp_bf16(const EvalIO* __restrict__ io, DescParams P,
+                                                    Workspace ws, MlpTcWeights Wt, MlpF32Weights Wf) {
+  constexpr int kBufA = slabs_of(D > kH2 ? D : kH2) * kSlab;  // G, later g2
+  constexpr int kBufB = slabs_of(kH1) * kSlab;                // h1, later g1
+  constexpr int kBufC = slabs_of(kH2) * kSlab;                // h2, later g3
+  constexpr int kWBuf = 48 * 1024;
+  static_assert(mat_bytes(kH1, D) <= kWBuf && mat_bytes(D, kH1) <= kWBuf, "weight buffer");
+  constexpr int NW[6] = {kH1, kH2, kH3, kH2, kH1, D};  // N of the six GEMMs
+  constexpr int KW[6] = {D, kH1, kH2, kH3, kH2, kH1};  // K of the six GEMMs
+
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  uint8_t* bufA = sm;
+  uint8_t* bufB = bufA + kBufA;
+  uint8_t* bufC = bufB + kBufB;
+  uint8_t* wbuf[2] = {bufC + kBufC, bufC + kBufC + kWBuf};
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wbuf[1] + kWBuf);  // [0,1] weights, [2] tile, [3] mma
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  float* sE = reinterpret_cast<float*>(abort_flag + 1);
+  int* sSys = reinterpret_cast<int*>(sE + kTM);
+  int* sValid = sSys + kTM;
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const float al = P.celu_alpha, inv_al = 1.f / P.celu_alpha;
+  const int rows = ws.seg[P.S];
+  const int ntiles = rows / kTM;
+
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    mbar_init(&bars[2], 1);
+    mbar_init(&bars[3], 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t tz1 = tmem + 0, tz2 = tmem + 160, tz3 = tmem + 288, tg2 = tmem + 384, tg1 = tmem + 160,
+                 tdg = tmem + 0;
+
+  // barrier parities and outstanding work (thread 0): bars 0,1 weights, 2 tile, 3 MMA
+  uint32_t ph[4] = {0, 0, 0, 0};
+  bool pend[4] = {false, false, false, false};
+
+  // thread 0: issue the load of weight matrix `which` of species sp into buffer b
+  auto load_w = [&](int sp, int which, int b) {
+    const int bytes = mat_bytes(NW[which], KW[which]);
+    mbar_expect_tx(&bars[b], (uint32_t)bytes);
+    bulk_g2s(wbuf[b], Wt.m[sp][which], (uint32_t)bytes, &bars[b]);
+    pend[b] = true;
+  };
+  auto load_tile = [&](int tile) {
+    const uint32_t bytes = (uint32_t)gh_tile_bytes(D);
+    mbar_expect_tx(&bars[2], bytes);
+    bulk_g2s(bufA, reinterpret_cast<const uint8_t*>(ws.Gh) + (size_t)tile * bytes, bytes, &bars[2]);
+    pend[2] = true;
+  };
+  auto commit = [&]() {
+    mma_commit(&bars[3]);
+    pend[3] = true;
+  };
+  // every thread: thread 0 polls barrier i (bounded), then all check the abort flag
+  auto sync_wait = [&](int i) -> bool {
+    if (tid == 0) {
+      if (mbar_wait(&bars[i], ph[i])) {
+        ph[i] ^= 1u;
+        pend[i] = false;
+      } else {
+        *abort_flag = 1;
+        atomicOr(&ws.flags[kFlagTimeout], 1);
+      }
+    }
+    __syncthreads();
+    return *abort_flag == 0;
+  };
+
+  int tile = blockIdx.x;
+  if (tile < ntiles && tid == 0) {
+    const int sp0 = pos4_species(ws.pos4[tile * kTM]);
+    load_tile(tile);
+    load_w(sp0, 0, 0);
+  }
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int row0 = tile * kTM;
+    const int sp = pos4_species(ws.pos4[row0]);
+    const int r = tid;
+    const int row = row0 + r;
+    // ---------------- layer 1: z1 = G W1
+    if (!sync_wait(2)) break;          // G tile
+    if (!sync_wait(0)) break;       // W1^T in wbuf[0]
+    if (tid == 0) {
+      load_w(sp, 1, 1);                              // W2^T -> wbuf[1]
+      tc_fence_after();
+      issue_gemm(tz1, bufA, wbuf[0], kH1, D, false);
+      commit();
+    }
+    if (!sync_wait(3)) break;
+    tc_fence_after();
+    for (int c0 = 0; c0 < kH1; c0 += 16) {
+      float v[16];
+      tmem_ld16(tz1 + lane_base + c0, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = celu_f(v[j] + Wf.b[sp][0][c0 + j], al);
+      store_row16(bufB, r, c0, v);
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    // ---------------- layer 2: z2 = h1 W2
+    if (!sync_wait(1)) break;
+    if (tid == 0) {
+      load_w(sp, 2, 0);                              // W3^T -> wbuf[0] (layer-1 MMA done)
+      tc_fence_after();
+      issue_gemm(tz2, bufB, wbuf[1], kH2, kH1, false);
+      commit();
+    }
+    if (!sync_wait(3)) break;
+    tc_fence_after();
+    for (int c0 = 0; c0 < kH2; c0 += 16) {
+      float v[16];
+      tmem_ld16(tz2 + lane_base + c0, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = celu_f(v[j] + Wf.b[sp][1][c0 + j], al);
+      store_row16(bufC, r, c0, v);
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    // ---------------- layer 3: z3 = h2 W3; energy and g3 = w4 CELU'(z3)
+    if (!sync_wait(0)) break;
+    if (tid == 0) {
+      load_w(sp, 3, 1);                              // W3 (backward) -> wbuf[1]
+      tc_fence_after();
+      issue_gemm(tz3, bufC, wbuf[0], kH3, kH2, false);
+      commit();
+    }
+    if (!sync_wait(3)) break;
+    tc_fence_after();
+    {
+      float e = 0.f;
+      const float* w4 = Wf.W[sp][3];
+      for (int c0 = 0; c0 < kH3; c0 += 16) {
+        float v[16];
+        tmem_ld16(tz3 + lane_base + c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float z = v[j] + Wf.b[sp][2][c0 + j];
+          const float ww = w4[c0 + j];
+          e = fmaf(celu_f(z, al), ww, e);
+          v[j] = ww * dcelu_f(z, inv_al);
+        }
+        store_row16(bufC, r, c0, v);   // h2 no longer needed: layer-3 MMA is done
+      }
+      e += Wf.b[sp][3][0];
+      const bool valid = ws.row_atom[row] >= 0;
+      sE[r] = e;
+      sValid[r] = valid;
+      sSys[r] = ws.row_info[row];
+      ws.Ei[row] = valid ? e : 0.f;
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    if (tid < kTM) {  // per-system energy of this tile (valid rows form a prefix)
+      if (sValid[r] && (r == 0 || sSys[r - 1] != sSys[r])) {
+        double sum = 0.0;
+        int q = r;
+        while (q < kTM && sValid[q] && sSys[q] == sSys[r]) sum += (double)sE[q++];
+        atomicAdd(&io->energies[sSys[r]], sum);
+      }
+    }
+    // ---------------- backward 3: g2' = g3 W3^T
+    if (!sync_wait(1)) break;
+    if (tid == 0) {
+      load_w(sp, 4, 0);                              // W2 (backward) -> wbuf[0]
+      tc_fence_after();
+      issue_gemm(tg2, bufC, wbuf[1], kH2, kH3, false);
+      commit();
+    }
+    if (!sync_wait(3)) break;
+    tc_fence_after();
+    for (int c0 = 0; c0 < kH2; c0 += 16) {
+      float g[16], z[16];
+      tmem_ld16(tg2 + lane_base + c0, g);
+      tmem_ld16(tz2 + lane_base + c0, z);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) g[j] *= dcelu_f(z[j] + Wf.b[sp][1][c0 + j], inv_al);
+      store_row16(bufA, r, c0, g);     // G tile no longer needed
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    // ---------------- backward 2: g1' = g2 W2^T
+    if (!sync_wait(0)) break;
+    if (tid == 0) {
+      load_w(sp, 5, 1);                              // W1 (backward) -> wbuf[1]
+      tc_fence_after();
+      issue_gemm(tg1, bufA, wbuf[0], kH1, kH2, false);
+      commit();
+    }
+    if (!sync_wait(3)) break;
+    tc_fence_after();
+    for (int c0 = 0; c0 < kH1; c0 += 16) {
+      float g[16], z[16];
+      tmem_ld16(tg1 + lane_base + c0, g);
+      tmem_ld16(tz1 + lane_base + c0, z);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) g[j] *= dcelu_f(z[j] + Wf.b[sp][0][c0 + j], inv_al);
+      store_row16(bufB, r, c0, g);
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    // ---------------- backward 1: dE/dG = g1 W1^T
+    if (!sync_wait(1)) break;
+    const int next = tile + gridDim.x;
+    if (tid == 0) {
+      tc_fence_after();
+      issue_gemm(tdg, bufB, wbuf[1], D, kH1, false);
+      commit();
+      if (next < ntiles) {  // bufA and wbuf[0] are free: prefetch the next tile
+        load_tile(next);
+        load_w(pos4_species(ws.pos4[next * kTM]), 0, 0);
+      }
+    }
+    if (!sync_wait(3)) break;
+    tc_fence_after();
+    {
+      float* out = ws.dEdG + (size_t)row * D;
+      for (int c0 = 0; c0 < D; c0 += 16) {
+        float v[16];
+        tmem_ld16(tdg + lane_base + c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; j += 4)
+          *reinterpret_cast<float4*>(out + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+  // on abort: give this CTA's outstanding copies and MMAs a bounded chance to land
+  if (tid == 0 && *abort_flag) {
+    for (int i = 0; i < 4; ++i)
+      if (pend[i]) mbar_wait(&bars[i], ph[i]);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+
+namespace {
+
+struct TcState {
+  uint8_t* blob = nullptr;   // pre-swizzled BF16 weights, all species
+  size_t per_species = 0;
+  size_t off[6] = {0, 0, 0, 0, 0, 0};
+  MlpTcWeights w{};
+};
+
+// Swizzled K-major image of a logical [N][K] matrix (value(n, k)).
+template <class F>
+void swizzle_into(uint8_t* dst, int N, int K, F value) {
+  memset(dst, 0, (size_t)mat_bytes(N, K));
+  for (int n = 0; n < N; ++n)
+    for (int k = 0; k < K; ++k) {
+      const int slab = k / 64, ch = (k % 64) / 8, e = k % 8;
+      const size_t off = (size_t)slab * N * 128 + (size_t)n * 128 + (size_t)((ch ^ (n & 7)) << 4) + e * 2;
+      __nv_bfloat16 h = __float2bfloat16(value(n, k));
+      memcpy(dst + off, &h, 2);
+    }
+}
+
+size_t smem_bytes(int D) {
+  const int a = slabs_of(D > kH2 ? D : kH2) * kSlab, b = slabs_of(kH1) * kSlab, c = slabs_of(kH2) * kSlab;
+  return 1024 + (size_t)a + b + c + 2 * 48 * 1024 + 4 * 8 + 8 + 3 * kTM * 4 + 64;
+}
+
+}  // namespace
+
+int mlp_tc_init(nnp_ctx* ctx) {
+  if (ctx->cfg.precision != NNP_BF16)
+    return ctx->fail(NNP_ERR_UNSUPPORTED, "only the BF16 tensor-core form is built so far");
+  const int D = ctx->P.D;
+  if (D != 128 && D != 48)
+    return ctx->fail(NNP_ERR_UNSUPPORTED, "the tensor-core network supports 1 or 2 species (D = 48, 128)");
+  TcState* st = new TcState();
+  const int NW[6] = {kH1, kH2, kH3, kH2, kH1, D};
+  const int KW[6] = {D, kH1, kH2, kH3, kH2, kH1};
+  size_t o = 0;
+  for (int i = 0; i < 6; ++i) {
+    st->off[i] = o;
+    o += (size_t)mat_bytes(NW[i], KW[i]);
+    o = (o + 1023) / 1024 * 1024;
+  }
+  st->per_species = o;
+  cudaError_t e = cudaMalloc(&st->blob, o * ctx->P.S);
+  if (e != cudaSuccess) {
+    delete st;
+    return ctx->cuda_fail(e, "cudaMalloc tensor-core weights");
+  }
+  cudaMemset(st->blob, 0, o * ctx->P.S);
+  for (int s = 0; s < ctx->P.S; ++s)
+    for (int i = 0; i < 6; ++i) st->w.m[s][i] = st->blob + o * s + st->off[i];
+  ctx->tc = st;
+  const size_t sm = smem_bytes(D);
+  e = (D == 128) ? cudaFuncSetAttribute(k_mlp_bf16<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+                 : cudaFuncSetAttribute(k_mlp_bf16<48>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaFuncSetAttribute(k_mlp_bf16)");
+  return NNP_OK;
+}
+
+int mlp_tc_set_weights(nnp_ctx* ctx, int s, const float* hb) {
+  TcState* st = static_cast<TcState*>(ctx->tc);
+  if (!st) return ctx->fail(NNP_ERR_UNSUPPORTED, "tensor-core state missing");
+  const int D = ctx->P.D;
+  // host blob layout: W1 (D x 160) b1 W2 (160 x 128) b2 W3 (128 x 96) b3 W4 b4
+  const float* W1 = hb;
+  const float* W2 = W1 + (size_t)D * kH1 + kH1;
+  const float* W3 = W2 + (size_t)kH1 * kH2 + kH2;
+  std::vector<uint8_t> img(st->per_species, 0);
+  swizzle_into(img.data() + st->off[0], kH1, D, [&](int n, int k) { return W1[(size_t)k * kH1 + n]; });
+  swizzle_into(img.data() + st->off[1], kH2, kH1, [&](int n, int k) { return W2[(size_t)k * kH2 + n]; });
+  swizzle_into(img.data() + st->off[2], kH3, kH2, [&](int n, int k) { return W3[(size_t)k * kH3 + n]; });
+  swizzle_into(img.data() + st->off[3], kH2, kH3, [&](int n, int k) { return W3[(size_t)n * kH3 + k]; });
+  swizzle_into(img.data() + st->off[4], kH1, kH2, [&](int n, int k) { return W2[(size_t)n * kH2 + k]; });
+  swizzle_into(img.data() + st->off[5], D, kH1, [&](int n, int k) { return W1[(size_t)n * kH1 + k]; });
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(st->blob + st->per_species * s, img.data(), st->per_species, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "upload tensor-core weights");
+  return NNP_OK;
+}
+
+void mlp_tc_free(nnp_ctx* ctx) {
+  TcState* st = static_cast<TcState*>(ctx->tc);
+  if (!st) return;
+  if (st->blob) cudaFree(st->blob);
+  delete st;
+  ctx->tc = nullptr;
+}
+
+int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t stream, long long rows) {
+  TcState* st = static_cast<TcState*>(ctx->tc);
+  if (!st) return ctx->fail(NNP_ERR_UNSUPPORTED, "tensor-core state missing");
+  const int D = ctx->P.D;
+  const long long tiles = (rows + kTM - 1) / kTM;
+  const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, ctx->num_sms));
+  const Workspace w = ctx->workspace();
+  const size_t sm = smem_bytes(D);
+  if (D == 128)
+    k_mlp_bf16<128><<<grid, 128, sm, stream>>>(ctx->d_io, ctx->P, w, st->w, ctx->wf32);
+  else
+    k_mlp_bf16<48><<<grid, 128, sm, stream>>>(ctx->d_io, ctx->P, w, st->w, ctx->wf32);
+  return NNP_OK;
 }
 
 }  // namespace nnp

@@ -104,7 +104,7 @@ int nnp_ctx::ensure_capacity(long long n, int B, long long bins, long long rows)
   GR(b_cnt_a, c_rows6, (size_t)rows * kMaxS);
   GR(b_nbr_r, c_nbr_r, (size_t)rows * cap_r);
   GR(b_G, c_G, (size_t)rows * P.D);
-  GR(b_Gh, c_Gh, (size_t)rows * P.D);
+  GR(b_Gh, c_Gh, (size_t)rows * ((P.D + 63) / 64 * 64));  // swizzled BF16 tiles
   GR(b_dEdG, c_dEdG, (size_t)rows * P.D);
   GR(b_Ei, c_Ei, (size_t)rows);
   GR(b_sys, c_sys, (size_t)B);

@@ -179,6 +179,19 @@ __device__ __forceinline__ float warp_sum(float x) {
   return x;
 }
 
+// BF16 copy of G for the tensor-core network: each 128-row tile is stored as
+// K-major slabs of 64 features (128 bytes per row), 16-byte chunks swizzled
+// by (chunk ^ (row & 7)) -- the operand layout tcgen05.mma reads with
+// 128-byte swizzling.  Byte offset of feature f of a row:
+__host__ __device__ __forceinline__ size_t gh_tile_bytes(int D) {
+  return (size_t)((D + 63) / 64) * 128 * 128;
+}
+__device__ __forceinline__ size_t gh_offset(int row, int f, int D) {
+  const int r = row & 127;
+  return (size_t)(row >> 7) * gh_tile_bytes(D) + (size_t)(f >> 6) * (128 * 128) + (size_t)r * 128 +
+         (size_t)((((f >> 3) & 7) ^ (r & 7)) << 4) + (size_t)(f & 7) * 2;
+}
+
 __device__ __forceinline__ int pair_block(int S, int s1, int s2) {
   // row-major upper triangle index of (s1 <= s2)
   return s1 * S - (s1 * (s1 - 1)) / 2 + (s2 - s1);
