@@ -67,8 +67,8 @@ __device__ __forceinline__ void zero_acc(float (&acc)[8][(N + 31) / 32]) {
     for (int j = 0; j < (N + 31) / 32; ++j) acc[i][j] = 0.f;
 }
 
-__device__ __forceinline__ float celu_f(float z, float al) {
-  return z > 0.f ? z : al * (expf(z / al) - 1.f);
+__device__ __forceinline__ float celu_f(float z, float al, float inv_al) {
+  return z > 0.f ? z : al * (expf(z * inv_al) - 1.f);
 }
 // CELU'(z) from h = CELU(z): 1 for h > 0, h/alpha + 1 otherwise
 __device__ __forceinline__ float dcelu_from_h(float h, float inv_al) {
@@ -78,7 +78,7 @@ __device__ __forceinline__ float dcelu_from_h(float h, float inv_al) {
 // Forward layer epilogue: H^T[col][row] = CELU(acc + b)
 template <int N>
 __device__ __forceinline__ void store_celu(const float (&acc)[8][(N + 31) / 32], const float* bias,
-                                           float* HT, float al) {
+                                           float* HT, float al, float inv_al) {
   const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
 #pragma unroll
   for (int j = 0; j < (N + 31) / 32; ++j) {
@@ -87,7 +87,7 @@ __device__ __forceinline__ void store_celu(const float (&acc)[8][(N + 31) / 32],
     const float bb = bias[col];
     float h[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) h[i] = celu_f(acc[i][j] + bb, al);
+    for (int i = 0; i < 8; ++i) h[i] = celu_f(acc[i][j] + bb, al, inv_al);
     *reinterpret_cast<float4*>(HT + col * kLDX + ty * 8) = make_float4(h[0], h[1], h[2], h[3]);
     *reinterpret_cast<float4*>(HT + col * kLDX + ty * 8 + 4) = make_float4(h[4], h[5], h[6], h[7]);
   }
@@ -124,9 +124,6 @@ __global__ void __launch_bounds__(256, 1) k_mlp_f32(const EvalIO* __restrict__ i
   float* Bs = H3T + kH3 * kLDX;           // [kKC][max N = max(160, D)]
   constexpr int kBsN = (D > kH1 ? D : kH1);
   float* As = Bs + kKC * kBsN;            // [kKC][kLDX]
-  __shared__ float sE[kTM];
-  __shared__ int sSys[kTM];
-  __shared__ int sValid[kTM];
   const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
   const float al = P.celu_alpha, inv_al = 1.f / P.celu_alpha;
   const int rows = ws.seg[S];
@@ -138,11 +135,11 @@ __global__ void __launch_bounds__(256, 1) k_mlp_f32(const EvalIO* __restrict__ i
     float acc1[8][kH1 / 32];
     zero_acc<kH1>(acc1);
     gemm_tile<kH1>(acc1, nullptr, ws.G + (size_t)row0 * D, D, D, Wt.W[sp][0], Bs, As);
-    store_celu<kH1>(acc1, Wt.b[sp][0], H1T, al);
+    store_celu<kH1>(acc1, Wt.b[sp][0], H1T, al, inv_al);
     float acc2[8][kH2 / 32];
     zero_acc<kH2>(acc2);
     gemm_tile<kH2>(acc2, H1T, nullptr, 0, kH1, Wt.W[sp][1], Bs, As);
-    store_celu<kH2>(acc2, Wt.b[sp][1], H2T, al);
+    store_celu<kH2>(acc2, Wt.b[sp][1], H2T, al, inv_al);
     float acc3[8][kH3 / 32];
     zero_acc<kH3>(acc3);
     gemm_tile<kH3>(acc3, H2T, nullptr, 0, kH2, Wt.W[sp][2], Bs, As);
@@ -161,7 +158,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_f32(const EvalIO* __restrict__ i
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const float z = acc3[i][j] + bb;
-          const float h = celu_f(z, al);
+          const float h = celu_f(z, al, inv_al);
           e[i] = fmaf(h, ww, e[i]);
           g[i] = ww * (z > 0.f ? 1.f : expf(z * inv_al));
         }
@@ -170,29 +167,25 @@ __global__ void __launch_bounds__(256, 1) k_mlp_f32(const EvalIO* __restrict__ i
       }
 #pragma unroll
       for (int i = 0; i < 8; ++i) e[i] = warp_sum(e[i]);
-      if (tx < 8) {
-        const int r = ty * 8 + tx;
-        float ev = e[0];
+      // rows ty*8 .. ty*8+7 of this warp: lane i < 8 holds row ty*8 + i
+      float ev = e[0];
 #pragma unroll
-        for (int i = 1; i < 8; ++i) ev = (tx == i) ? e[i] : ev;
-        ev += Wt.b[sp][3][0];
-        const int row = row0 + r;
-        const bool valid = ws.row_atom[row] >= 0;
-        sE[r] = ev;
-        sValid[r] = valid;
-        sSys[r] = ws.row_info[row];
-        ws.Ei[row] = valid ? ev : 0.f;
-      }
-    }
-    __syncthreads();
-    // per-system energy sums of this tile (valid rows form a prefix)
-    if (threadIdx.x < kTM) {
-      const int r = threadIdx.x;
-      if (sValid[r] && (r == 0 || sSys[r - 1] != sSys[r])) {
-        double sum = 0.0;
-        int q = r;
-        while (q < kTM && sValid[q] && sSys[q] == sSys[r]) sum += (double)sE[q++];
-        atomicAdd(&io->energies[sSys[r]], sum);
+      for (int i = 1; i < 8; ++i) ev = (tx == i) ? e[i] : ev;
+      const int row = row0 + ty * 8 + (tx & 7);
+      const bool valid = tx < 8 && ws.row_atom[row] >= 0;
+      const int sys = ws.row_info[row];
+      ev += Wt.b[sp][3][0];
+      if (tx < 8) ws.Ei[row] = valid ? ev : 0.f;
+      unsigned todo = __ballot_sync(0xffffffffu, valid);
+      while (todo) {  // per-system runs: shuffle sum, one FP64 add each
+        const int leader = __ffs(todo) - 1;
+        const int ls = __shfl_sync(0xffffffffu, sys, leader);
+        const bool mine = valid && sys == ls;
+        float x = mine ? ev : 0.f;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (tx == leader) atomicAdd(&io->energies[ls], (double)x);
+        todo &= ~__ballot_sync(0xffffffffu, mine);
       }
     }
     // ---- backward

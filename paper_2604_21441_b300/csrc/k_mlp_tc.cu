@@ -6,9 +6,11 @@
 //   z_l = h_{l-1} W_l + b_l, h_l = CELU(z_l), E_i = h_3 w_4 + b_4
 //   g_3 = w_4 * CELU'(z_3), g_{l-1} = (g_l W_l^T) * CELU'(z_{l-1}), dE/dG = g_1 W_1^T
 //
-// One CTA (4 warps) per SM, persistent over 128-row tiles (one species per
-// tile).  Thread t owns row t of the tile, which is TMEM lane t.  Thread 0
-// issues the bulk (TMA) copies and the MMAs; all threads run the epilogues.
+// One CTA (8 warps) per SM, persistent over 128-row tiles (one species per
+// tile).  Row r of a tile is TMEM lane r; warps w and w+4 share the lanes of
+// quarter w and split each epilogue's 16-column chunks.  Thread 0 issues the
+// bulk (TMA) copies and the MMAs; all threads run the epilogues, reading
+// biases from shared memory and keeping two TMEM loads in flight.
 // Shared memory holds three activation buffers and two weight buffers, every
 // operand in the K-major 128-byte-swizzled layout (slabs of 64 columns x 128
 // rows, 16-byte chunk j of row r stored at chunk j ^ (r & 7)).  The descriptor
@@ -151,8 +153,11 @@ __device__ __forceinline__ void issue_gemm(uint32_t d_tmem, const uint8_t* A, co
   }
 }
 
-__device__ __forceinline__ float celu_f(float z, float al) { return z > 0.f ? z : al * (__expf(z / al) - 1.f); }
-__device__ __forceinline__ float dcelu_f(float z, float inv_al) { return z > 0.f ? 1.f : __expf(z * inv_al); }
+// CELU and its derivative; k = log2(e) / alpha, so exp(z / alpha) = exp2(k z).
+__device__ __forceinline__ float celu_f(float z, float al, float k) {
+  return z > 0.f ? z : al * (exp2f(z * k) - 1.f);
+}
+__device__ __forceinline__ float dcelu_f(float z, float k) { return z > 0.f ? 1.f : exp2f(z * k); }
 
 // Store 16 values of row r, columns [c0, c0+16), as BF16 into a swizzled buffer.
 __device__ __forceinline__ void store_row16(uint8_t* buf, int r, int c0, const float (&v)[16]) {
@@ -182,16 +187,88 @@ struct MlpTcWeights {
   const uint8_t* m[kMaxS][6];
 };
 
+// Per-system energy sums of one warp's 32 rows: rows of a system are
+// contiguous, so each run is summed by shuffles and added once in FP64.
+__device__ __forceinline__ void tile_energy_sums(float e, bool valid, int sys, int lane, double* energies) {
+  unsigned todo = __ballot_sync(0xffffffffu, valid);
+  while (todo) {
+    const int leader = __ffs(todo) - 1;
+    const int ls = __shfl_sync(0xffffffffu, sys, leader);
+    const bool mine = valid && sys == ls;
+    float x = mine ? e : 0.f;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == leader) atomicAdd(&energies[ls], (double)x);
+    todo &= ~__ballot_sync(0xffffffffu, mine);
+  }
+}
+
+// Issue the TMEM load of 16 columns (no wait).
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Epilogue skeleton: the warp's half h handles 16-column chunks h, h+2, ...;
+// two chunks are loaded from TMEM per wait.  f(chunk_col0, values[16]).
+template <int N, class F>
+__device__ __forceinline__ void for_chunks(uint32_t tcol, int h, F f) {
+  constexpr int NCH = N / 16;
+  for (int c = h; c < NCH; c += 4) {
+    uint32_t a[16], b[16];
+    const bool two = c + 2 < NCH;
+    tmem_ld16_nowait(tcol + c * 16, a);
+    if (two) tmem_ld16_nowait(tcol + (c + 2) * 16, b);
+    tmem_wait_ld();
+    float v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(a[j]);
+    f(c * 16, v);
+    if (two) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(b[j]);
+      f((c + 2) * 16, v);
+    }
+  }
+}
+
+// Same, with a second TMEM operand (the pre-activation) per chunk.
+template <int N, class F>
+__device__ __forceinline__ void for_chunks2(uint32_t tcol, uint32_t tcol2, int h, F f) {
+  constexpr int NCH = N / 16;
+  for (int c = h; c < NCH; c += 2) {
+    uint32_t a[16], b[16];
+    tmem_ld16_nowait(tcol + c * 16, a);
+    tmem_ld16_nowait(tcol2 + c * 16, b);
+    tmem_wait_ld();
+    float g[16], z[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      g[j] = __uint_as_float(a[j]);
+      z[j] = __uint_as_float(b[j]);
+    }
+    f(c * 16, g, z);
+  }
+}
+
 template <int D>
-__global__ void __launch_bounds__(128, 1) k_mlp_bf16(const EvalIO* __restrict__ io, DescParams P,
+__global__ void __launch_bounds__(256, 1) k_mlp_bf16(const EvalIO* __restrict__ io, DescParams P,
                                                     Workspace ws, MlpTcWeights Wt, MlpF32Weights Wf) {
   constexpr int kBufA = slabs_of(D > kH2 ? D : kH2) * kSlab;  // G, later g2
   constexpr int kBufB = slabs_of(kH1) * kSlab;                // h1, later g1
   constexpr int kBufC = slabs_of(kH2) * kSlab;                // h2, later g3
   constexpr int kWBuf = 48 * 1024;
   static_assert(mat_bytes(kH1, D) <= kWBuf && mat_bytes(D, kH1) <= kWBuf, "weight buffer");
+  static_assert(D % 16 == 0, "D must be a multiple of 16");
   constexpr int NW[6] = {kH1, kH2, kH3, kH2, kH1, D};  // N of the six GEMMs
   constexpr int KW[6] = {D, kH1, kH2, kH3, kH2, kH1};  // K of the six GEMMs
+  constexpr int kNB = kH1 + kH2 + kH3 + kH3 + 1;       // b1 b2 b3 w4 b4
 
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
@@ -202,12 +279,18 @@ __global__ void __launch_bounds__(128, 1) k_mlp_bf16(const EvalIO* __restrict__ 
   uint64_t* bars = reinterpret_cast<uint64_t*>(wbuf[1] + kWBuf);  // [0,1] weights, [2] tile, [3] mma
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
-  float* sE = reinterpret_cast<float*>(abort_flag + 1);
-  int* sSys = reinterpret_cast<int*>(sE + kTM);
-  int* sValid = sSys + kTM;
+  float* sE = reinterpret_cast<float*>(abort_flag + 1);  // [2][kTM] partial energies
+  float* sb = sE + 2 * kTM;  // [kNB] biases and w4 of the tile's species
+  float* sb1 = sb;
+  float* sb2 = sb1 + kH1;
+  float* sb3 = sb2 + kH2;
+  float* sw4 = sb3 + kH3;
+  float* sb4 = sw4 + kH3;
 
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const float al = P.celu_alpha, inv_al = 1.f / P.celu_alpha;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quarter = warp & 3, h = warp >> 2;  // TMEM lane quarter; column half
+  const int r = quarter * 32 + lane;            // row of the tile (TMEM lane)
+  const float al = P.celu_alpha, kexp = 1.4426950408889634f / P.celu_alpha;
   const int rows = ws.seg[P.S];
   const int ntiles = rows / kTM;
 
@@ -224,32 +307,32 @@ __global__ void __launch_bounds__(128, 1) k_mlp_bf16(const EvalIO* __restrict__ 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-  const uint32_t tz1 = tmem + 0, tz2 = tmem + 160, tz3 = tmem + 288, tg2 = tmem + 384, tg1 = tmem + 160,
-                 tdg = tmem + 0;
+  const uint32_t lb = (uint32_t)(quarter * 32) << 16;
+  const uint32_t tz1 = tmem + lb + 0, tz2 = tmem + lb + 160, tz3 = tmem + lb + 288,
+                 tg2 = tmem + lb + 384, tg1 = tmem + lb + 160, tdg = tmem + lb + 0;
+  const uint32_t mz1 = tmem + 0, mz2 = tmem + 160, mz3 = tmem + 288, mg2 = tmem + 384, mg1 = tmem + 160,
+                 mdg = tmem + 0;  // MMA destinations (lane 0)
 
   // barrier parities and outstanding work (thread 0): bars 0,1 weights, 2 tile, 3 MMA
   uint32_t ph[4] = {0, 0, 0, 0};
   bool pend[4] = {false, false, false, false};
 
-  // thread 0: issue the load of weight matrix `which` of species sp into buffer b
   auto load_w = [&](int sp, int which, int b) {
     const int bytes = mat_bytes(NW[which], KW[which]);
     mbar_expect_tx(&bars[b], (uint32_t)bytes);
     bulk_g2s(wbuf[b], Wt.m[sp][which], (uint32_t)bytes, &bars[b]);
     pend[b] = true;
   };
-  auto load_tile = [&](int tile) {
+  auto load_tile = [&](int t) {
     const uint32_t bytes = (uint32_t)gh_tile_bytes(D);
     mbar_expect_tx(&bars[2], bytes);
-    bulk_g2s(bufA, reinterpret_cast<const uint8_t*>(ws.Gh) + (size_t)tile * bytes, bytes, &bars[2]);
+    bulk_g2s(bufA, reinterpret_cast<const uint8_t*>(ws.Gh) + (size_t)t * bytes, bytes, &bars[2]);
     pend[2] = true;
   };
   auto commit = [&]() {
     mma_commit(&bars[3]);
     pend[3] = true;
   };
-  // every thread: thread 0 polls barrier i (bounded), then all check the abort flag
   auto sync_wait = [&](int i) -> bool {
     if (tid == 0) {
       if (mbar_wait(&bars[i], ph[i])) {
@@ -263,150 +346,135 @@ __global__ void __launch_bounds__(128, 1) k_mlp_bf16(const EvalIO* __restrict__ 
     __syncthreads();
     return *abort_flag == 0;
   };
+  // epilogue writes (generic proxy) -> next MMA (async proxy); TMEM reads -> next MMA
+  auto end_epilogue = [&]() {
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+  };
 
   int tile = blockIdx.x;
   if (tile < ntiles && tid == 0) {
-    const int sp0 = pos4_species(ws.pos4[tile * kTM]);
     load_tile(tile);
-    load_w(sp0, 0, 0);
+    load_w(pos4_species(ws.pos4[tile * kTM]), 0, 0);
   }
   for (; tile < ntiles; tile += gridDim.x) {
     const int row0 = tile * kTM;
     const int sp = pos4_species(ws.pos4[row0]);
-    const int r = tid;
     const int row = row0 + r;
+    const int my_atom = ws.row_atom[row];  // consumed by the energy epilogue
+    const int my_sys = ws.row_info[row];
+    for (int i = tid; i < kNB; i += blockDim.x) {
+      float v;
+      if (i < kH1) v = Wf.b[sp][0][i];
+      else if (i < kH1 + kH2) v = Wf.b[sp][1][i - kH1];
+      else if (i < kH1 + kH2 + kH3) v = Wf.b[sp][2][i - kH1 - kH2];
+      else if (i < kH1 + kH2 + 2 * kH3) v = Wf.W[sp][3][i - kH1 - kH2 - kH3];
+      else v = Wf.b[sp][3][0];
+      sb[i] = v;
+    }
     // ---------------- layer 1: z1 = G W1
-    if (!sync_wait(2)) break;          // G tile
-    if (!sync_wait(0)) break;       // W1^T in wbuf[0]
+    if (!sync_wait(2)) break;                        // G tile (also publishes sb)
+    if (!sync_wait(0)) break;                        // W1^T in wbuf[0]
     if (tid == 0) {
       load_w(sp, 1, 1);                              // W2^T -> wbuf[1]
       tc_fence_after();
-      issue_gemm(tz1, bufA, wbuf[0], kH1, D, false);
+      issue_gemm(mz1, bufA, wbuf[0], kH1, D, false);
       commit();
     }
     if (!sync_wait(3)) break;
     tc_fence_after();
-    for (int c0 = 0; c0 < kH1; c0 += 16) {
-      float v[16];
-      tmem_ld16(tz1 + lane_base + c0, v);
+    for_chunks<kH1>(tz1, h, [&](int c0, float (&v)[16]) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = celu_f(v[j] + Wf.b[sp][0][c0 + j], al);
+      for (int j = 0; j < 16; ++j) v[j] = celu_f(v[j] + sb1[c0 + j], al, kexp);
       store_row16(bufB, r, c0, v);
-    }
-    fence_proxy_async();
-    tc_fence_before();
-    __syncthreads();
+    });
+    end_epilogue();
     // ---------------- layer 2: z2 = h1 W2
     if (!sync_wait(1)) break;
     if (tid == 0) {
-      load_w(sp, 2, 0);                              // W3^T -> wbuf[0] (layer-1 MMA done)
+      load_w(sp, 2, 0);                              // W3^T -> wbuf[0]
       tc_fence_after();
-      issue_gemm(tz2, bufB, wbuf[1], kH2, kH1, false);
+      issue_gemm(mz2, bufB, wbuf[1], kH2, kH1, false);
       commit();
     }
     if (!sync_wait(3)) break;
     tc_fence_after();
-    for (int c0 = 0; c0 < kH2; c0 += 16) {
-      float v[16];
-      tmem_ld16(tz2 + lane_base + c0, v);
+    for_chunks<kH2>(tz2, h, [&](int c0, float (&v)[16]) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = celu_f(v[j] + Wf.b[sp][1][c0 + j], al);
+      for (int j = 0; j < 16; ++j) v[j] = celu_f(v[j] + sb2[c0 + j], al, kexp);
       store_row16(bufC, r, c0, v);
-    }
-    fence_proxy_async();
-    tc_fence_before();
-    __syncthreads();
+    });
+    end_epilogue();
     // ---------------- layer 3: z3 = h2 W3; energy and g3 = w4 CELU'(z3)
     if (!sync_wait(0)) break;
     if (tid == 0) {
       load_w(sp, 3, 1);                              // W3 (backward) -> wbuf[1]
       tc_fence_after();
-      issue_gemm(tz3, bufC, wbuf[0], kH3, kH2, false);
+      issue_gemm(mz3, bufC, wbuf[0], kH3, kH2, false);
       commit();
     }
     if (!sync_wait(3)) break;
     tc_fence_after();
     {
       float e = 0.f;
-      const float* w4 = Wf.W[sp][3];
-      for (int c0 = 0; c0 < kH3; c0 += 16) {
-        float v[16];
-        tmem_ld16(tz3 + lane_base + c0, v);
+      for_chunks<kH3>(tz3, h, [&](int c0, float (&v)[16]) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const float z = v[j] + Wf.b[sp][2][c0 + j];
-          const float ww = w4[c0 + j];
-          e = fmaf(celu_f(z, al), ww, e);
-          v[j] = ww * dcelu_f(z, inv_al);
+          const float z = v[j] + sb3[c0 + j];
+          const float ww = sw4[c0 + j];
+          e = fmaf(celu_f(z, al, kexp), ww, e);
+          v[j] = ww * dcelu_f(z, kexp);
         }
-        store_row16(bufC, r, c0, v);   // h2 no longer needed: layer-3 MMA is done
-      }
-      e += Wf.b[sp][3][0];
-      const bool valid = ws.row_atom[row] >= 0;
-      sE[r] = e;
-      sValid[r] = valid;
-      sSys[r] = ws.row_info[row];
-      ws.Ei[row] = valid ? e : 0.f;
+        store_row16(bufC, r, c0, v);  // h2 no longer needed: the layer-3 MMA is done
+      });
+      sE[h * kTM + r] = e;
     }
-    fence_proxy_async();
-    tc_fence_before();
-    __syncthreads();
-    if (tid < kTM) {  // per-system energy of this tile (valid rows form a prefix)
-      if (sValid[r] && (r == 0 || sSys[r - 1] != sSys[r])) {
-        double sum = 0.0;
-        int q = r;
-        while (q < kTM && sValid[q] && sSys[q] == sSys[r]) sum += (double)sE[q++];
-        atomicAdd(&io->energies[sSys[r]], sum);
-      }
+    end_epilogue();
+    if (h == 0) {  // warps 0-3: one row per thread
+      const float e = sE[r] + sE[kTM + r] + *sb4;
+      const bool valid = my_atom >= 0;
+      ws.Ei[row] = valid ? e : 0.f;
+      tile_energy_sums(valid ? e : 0.f, valid, my_sys, lane, io->energies);
     }
     // ---------------- backward 3: g2' = g3 W3^T
     if (!sync_wait(1)) break;
     if (tid == 0) {
       load_w(sp, 4, 0);                              // W2 (backward) -> wbuf[0]
       tc_fence_after();
-      issue_gemm(tg2, bufC, wbuf[1], kH2, kH3, false);
+      issue_gemm(mg2, bufC, wbuf[1], kH2, kH3, false);
       commit();
     }
     if (!sync_wait(3)) break;
     tc_fence_after();
-    for (int c0 = 0; c0 < kH2; c0 += 16) {
-      float g[16], z[16];
-      tmem_ld16(tg2 + lane_base + c0, g);
-      tmem_ld16(tz2 + lane_base + c0, z);
+    for_chunks2<kH2>(tg2, tz2, h, [&](int c0, float (&g)[16], float (&z)[16]) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) g[j] *= dcelu_f(z[j] + Wf.b[sp][1][c0 + j], inv_al);
-      store_row16(bufA, r, c0, g);     // G tile no longer needed
-    }
-    fence_proxy_async();
-    tc_fence_before();
-    __syncthreads();
+      for (int j = 0; j < 16; ++j) g[j] *= dcelu_f(z[j] + sb2[c0 + j], kexp);
+      store_row16(bufA, r, c0, g);  // the G tile is no longer needed
+    });
+    end_epilogue();
     // ---------------- backward 2: g1' = g2 W2^T
     if (!sync_wait(0)) break;
     if (tid == 0) {
       load_w(sp, 5, 1);                              // W1 (backward) -> wbuf[1]
       tc_fence_after();
-      issue_gemm(tg1, bufA, wbuf[0], kH1, kH2, false);
+      issue_gemm(mg1, bufA, wbuf[0], kH1, kH2, false);
       commit();
     }
     if (!sync_wait(3)) break;
     tc_fence_after();
-    for (int c0 = 0; c0 < kH1; c0 += 16) {
-      float g[16], z[16];
-      tmem_ld16(tg1 + lane_base + c0, g);
-      tmem_ld16(tz1 + lane_base + c0, z);
+    for_chunks2<kH1>(tg1, tz1, h, [&](int c0, float (&g)[16], float (&z)[16]) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) g[j] *= dcelu_f(z[j] + Wf.b[sp][0][c0 + j], inv_al);
+      for (int j = 0; j < 16; ++j) g[j] *= dcelu_f(z[j] + sb1[c0 + j], kexp);
       store_row16(bufB, r, c0, g);
-    }
-    fence_proxy_async();
-    tc_fence_before();
-    __syncthreads();
+    });
+    end_epilogue();
     // ---------------- backward 1: dE/dG = g1 W1^T
     if (!sync_wait(1)) break;
     const int next = tile + gridDim.x;
     if (tid == 0) {
       tc_fence_after();
-      issue_gemm(tdg, bufB, wbuf[1], D, kH1, false);
+      issue_gemm(mdg, bufB, wbuf[1], D, kH1, false);
       commit();
       if (next < ntiles) {  // bufA and wbuf[0] are free: prefetch the next tile
         load_tile(next);
@@ -417,13 +485,11 @@ __global__ void __launch_bounds__(128, 1) k_mlp_bf16(const EvalIO* __restrict__ 
     tc_fence_after();
     {
       float* out = ws.dEdG + (size_t)row * D;
-      for (int c0 = 0; c0 < D; c0 += 16) {
-        float v[16];
-        tmem_ld16(tdg + lane_base + c0, v);
+      for_chunks<D>(tdg, h, [&](int c0, float (&v)[16]) {
 #pragma unroll
         for (int j = 0; j < 16; j += 4)
           *reinterpret_cast<float4*>(out + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-      }
+      });
     }
     tc_fence_before();
     __syncthreads();
@@ -466,7 +532,8 @@ void swizzle_into(uint8_t* dst, int N, int K, F value) {
 
 size_t smem_bytes(int D) {
   const int a = slabs_of(D > kH2 ? D : kH2) * kSlab, b = slabs_of(kH1) * kSlab, c = slabs_of(kH2) * kSlab;
-  return 1024 + (size_t)a + b + c + 2 * 48 * 1024 + 4 * 8 + 8 + 3 * kTM * 4 + 64;
+  return 1024 + (size_t)a + b + c + 2 * 48 * 1024 + 4 * 8 + 8 + 4 * kTM * 4 +
+         (kH1 + kH2 + 2 * kH3 + 1) * 4 + 64;
 }
 
 }  // namespace
@@ -542,9 +609,9 @@ int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t stream, long long rows) {
   const Workspace w = ctx->workspace();
   const size_t sm = smem_bytes(D);
   if (D == 128)
-    k_mlp_bf16<128><<<grid, 128, sm, stream>>>(ctx->d_io, ctx->P, w, st->w, ctx->wf32);
+    k_mlp_bf16<128><<<grid, 256, sm, stream>>>(ctx->d_io, ctx->P, w, st->w, ctx->wf32);
   else
-    k_mlp_bf16<48><<<grid, 128, sm, stream>>>(ctx->d_io, ctx->P, w, st->w, ctx->wf32);
+    k_mlp_bf16<48><<<grid, 256, sm, stream>>>(ctx->d_io, ctx->P, w, st->w, ctx->wf32);
   return NNP_OK;
 }
 
