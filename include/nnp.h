@@ -193,13 +193,17 @@ int nnp_eval_batch(nnp_ctx *ctx, int32_t B, const int64_t *offsets, const double
  * per species as W1 b1 W2 b2 W3 b3 W4 b4 (each W row-major fan_in x fan_out). */
 int64_t nnp_param_count(const nnp_ctx *ctx);
 
-/* Weight gradient of a force loss.  Given v = dL/dF (n x 3, host or device,
- * for the system of the last nnp_eval on ctx), writes
- *   grad = dL/dtheta = sum_i v_i . dF_i/dtheta
- * (nnp_param_count doubles, host or device, layout as above) and, if loss
- * is non-NULL and Fref is non-NULL, sets v internally to
- * 2 (F - Fref) / (3n) and *loss = |F - Fref|^2 / (3n) (the force-matching
- * loss); pass v = NULL in that case.  Computed in FP32 with FP64 sums. */
+/* Weight gradient of a force loss L(F) (force matching, the training signal
+ * of Eq. 2's forces): writes grad = dL/dtheta = sum_i v_i . dF_i/dtheta
+ * (nnp_param_count doubles, host or device, layout as above) for the system(s)
+ * of the last nnp_eval / nnp_eval_batch on ctx, whose configuration the
+ * context keeps.  Pass either
+ *   v    = dL/dF (n x 3, host or device) for any loss, Fref = NULL; or
+ *   Fref = reference forces (n x 3): then L = |F - Fref|^2 / (3n), v =
+ *          2 (F - Fref) / (3n), and *loss (if non-NULL) receives L.
+ * F and the gradient are computed in the FP32 form (whatever the context's
+ * precision) with FP64 sums: directional derivative of the descriptors along
+ * v, then forward-over-reverse through the per-element networks. */
 int nnp_force_match_grad(nnp_ctx *ctx, const double *v, const double *Fref, double *loss,
                          double *grad);
 

@@ -577,6 +577,206 @@ __global__ void __launch_bounds__(128) k_aev_bwd(const EvalIO* __restrict__ io,
 }
 
 // --------------------------------------------------------------------------
+// directional derivative: dG_i = sum_j (dG_i / dr_j) . v_j (force-matching
+// gradients).  Same mapping as the forward; v is per atom in input order.
+//   radial:  d term_m = 1/4 exp(-eta_r x_m^2) (-2 eta_r x_m fc + fc') dr,
+//            dr = e_ij . (v_j - v_i)
+//   angular: d T_az = Be_a (C_z + D_z X) + Bq_a D_z Y with
+//            C_z = 2 zeta b_z^(zeta-1) dbase_z dc fc_u fc_v,  D_z = 2 b_z^zeta,
+//            X = fc'_u fc_v dr_u + fc_u fc'_v dr_v,  Y = fc_u fc_v (dr_u + dr_v) / 2,
+//            Bq_a = dBe_a / drbar,  dc = ((e_v - c e_u).dv_u)/r_u + ((e_u - c e_v).dv_v)/r_v.
+
+static int warps_grid_jvp(long long rows, int nsm) {
+  long long g = ((rows + 1) / 2 + 7) / 8;
+  if (g > (long long)nsm * 8) g = (long long)nsm * 8;
+  return (int)(g < 1 ? 1 : g);
+}
+
+template <int S, int ZSQ>
+__global__ void __launch_bounds__(256) k_aev_jvp(const SysDesc* __restrict__ sys, DescParams P,
+                                                 Workspace ws, const double* __restrict__ vel,
+                                                 float* __restrict__ dG) {
+  constexpr int D = kNRad * S + kNAng * S * (S + 1) / 2;
+  extern __shared__ float4 sm4[];
+  const int lane = threadIdx.x & 31, hl = lane & 15, half = lane >> 4;
+  const int hwb = threadIdx.x >> 4;
+  const int ca = ws.cap_a;
+  // per half warp: geo[ca] (unit vector, r), aux[ca] (fc, dfc, 1/r, -), dv[ca], sh[27]
+  const size_t n4 = (size_t)3 * ca + 27;
+  float4* geo = sm4 + hwb * n4;
+  float4* aux = geo + ca;
+  float4* dvs = aux + ca;
+  float4* sh = dvs + ca;
+  RowCounts* rc = reinterpret_cast<RowCounts*>(sm4 + 16 * n4) + hwb;
+  const float kr = -P.eta_r * kLog2e, ka = -P.eta_a * kLog2e;
+  const float kfr = kPi / (2.f * P.rc_r), kfa = kPi / (2.f * P.rc_a);
+  const float zeta = (float)(1 << P.zeta_sq);
+  const int rows = ws.seg[S];
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  int cached_sys = -1;
+  for (int pr = warp; 2 * pr < rows; pr += nwarps) {
+    const int row = 2 * pr + half;
+    const bool inrow = row < rows;
+    const bool live = inrow && ws.row_atom[row] >= 0;
+    float* out = dG + (size_t)row * D;
+    if (inrow && !live)
+      for (int f = hl; f < D; f += 16) out[f] = 0.f;
+    float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
+    float vix = 0.f, viy = 0.f, viz = 0.f;
+    if (live) {
+      pi = ws.pos4[row];
+      const int oi = pos4_orig(pi);
+      vix = (float)vel[3 * oi];
+      viy = (float)vel[3 * oi + 1];
+      viz = (float)vel[3 * oi + 2];
+      const int sid = ws.row_info[row];
+      if (sid != cached_sys) {
+        const SysDesc& sd = sys[sid];
+        const float ell[3] = {sd.ellf[0], sd.ellf[1], sd.ellf[2]};
+        for (int c = hl; c < 27; c += 16) sh[c] = shift_vec(c, ell);
+        cached_sys = sid;
+      }
+    }
+    load_counts(ws, S, row, live, ca, rc, hl);
+    __syncwarp();
+    const int* lr = ws.nbr_r + (size_t)row * ws.cap_r;
+
+    // ---------------- radial
+#pragma unroll 1
+    for (int s = 0; s < S; ++s) {
+      const int n_s = rc->nr[s], o_s = rc->orr[s];
+      const int nmax = max(n_s, __shfl_xor_sync(0xffffffffu, n_s, 16));
+      float acc[kNRad];
+#pragma unroll
+      for (int m = 0; m < kNRad; ++m) acc[m] = 0.f;
+      for (int k0 = 0; k0 < nmax; k0 += 16) {
+        const int k = k0 + hl;
+        if (k < n_s) {
+          const int e = lr[o_s + k];
+          const float4 pj = ws.pos4[nbr_row(e)];
+          const float4 sv = sh[nbr_code(e)];
+          const float dx = (pj.x - pi.x) + sv.x, dy = (pj.y - pi.y) + sv.y, dz = (pj.z - pi.z) + sv.z;
+          const float r2 = dx * dx + dy * dy + dz * dz;
+          const float ir = rsqrtf(r2);
+          const float r = r2 * ir;
+          const int oj = pos4_orig(pj);
+          const float dr = ((float)vel[3 * oj] - vix) * dx * ir + ((float)vel[3 * oj + 1] - viy) * dy * ir +
+                           ((float)vel[3 * oj + 2] - viz) * dz * ir;
+          float fc, dfc;
+          cutoff(r, P.rc_r, kfr, fc, dfc);
+#pragma unroll
+          for (int m = 0; m < kNRad; ++m) {
+            const float x = r - P.shf_r[m];
+            const float em = exp2f(kr * x * x);
+            acc[m] = fmaf(0.25f * em * fmaf(-2.f * P.eta_r * x, fc, dfc), dr, acc[m]);
+          }
+        }
+      }
+      hw_reduce_scatter<kNRad>(acc, hl);
+      if (live) out[s * kNRad + hl] = acc[0];
+    }
+
+    // ---------------- angular: stage geometry and relative displacements
+#pragma unroll 1
+    for (int s = 0; s < S; ++s) {
+      const int n_a = rc->na[s], o_r = rc->orr[s], o_a = rc->oa[s];
+      for (int k = hl; k < n_a; k += 16) {
+        const int e = lr[o_r + k];
+        const float4 pj = ws.pos4[nbr_row(e)];
+        const float4 sv = sh[nbr_code(e)];
+        const float dx = (pj.x - pi.x) + sv.x, dy = (pj.y - pi.y) + sv.y, dz = (pj.z - pi.z) + sv.z;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float ir = rsqrtf(r2);
+        const float r = r2 * ir;
+        float fc, dfc;
+        cutoff(r, P.rc_a, kfa, fc, dfc);
+        const int oj = pos4_orig(pj);
+        geo[o_a + k] = make_float4(dx * ir, dy * ir, dz * ir, r);
+        aux[o_a + k] = make_float4(fc, dfc, ir, 0.f);
+        dvs[o_a + k] = make_float4((float)vel[3 * oj] - vix, (float)vel[3 * oj + 1] - viy,
+                                   (float)vel[3 * oj + 2] - viz, 0.f);
+      }
+    }
+    __syncwarp();
+#pragma unroll 1
+    for (int s1 = 0; s1 < S; ++s1) {
+#pragma unroll 1
+      for (int s2 = s1; s2 < S; ++s2) {
+        const bool diag = s1 == s2;
+        const int n1 = rc->na[s1], n2 = rc->na[s2];
+        const int T = diag ? n1 * (n1 - 1) / 2 : n1 * n2;
+        const int Tmax = max(T, __shfl_xor_sync(0xffffffffu, T, 16));
+        const int f0 = kNRad * S + pair_block(S, s1, s2) * kNAng + 2 * hl;
+        if (Tmax == 0) {
+          if (live) *reinterpret_cast<float2*>(out + f0) = make_float2(0.f, 0.f);
+          continue;
+        }
+        const PairMap pm = make_map(diag, n1, n2, rc->oa[s1], rc->oa[s2]);
+        float acc[kNAng];
+#pragma unroll
+        for (int q = 0; q < kNAng; ++q) acc[q] = 0.f;
+        for (int t0 = 0; t0 < Tmax; t0 += 16) {
+          const int t = t0 + hl;
+          if (t < T) {
+            int u, v;
+            map_pair(pm, t, u, v);
+            const float4 gu = geo[u], gv = geo[v], au = aux[u], av = aux[v], du = dvs[u], dv = dvs[v];
+            const float c = gu.x * gv.x + gu.y * gv.y + gu.z * gv.z;
+            const float uc = 0.95f * c;
+            const float s2q = fmaxf(1.f - uc * uc, 1e-12f);
+            const float isn = rsqrtf(s2q);
+            const float sn = s2q * isn;
+            const float ucisn = uc * isn;
+            const float rbar = 0.5f * (gu.w + gv.w);
+            const float dru = gu.x * du.x + gu.y * du.y + gu.z * du.z;
+            const float drv = gv.x * dv.x + gv.y * dv.y + gv.z * dv.z;
+            const float dcv = ((gv.x - c * gu.x) * du.x + (gv.y - c * gu.y) * du.y + (gv.z - c * gu.z) * du.z) * au.z +
+                              ((gu.x - c * gv.x) * dv.x + (gu.y - c * gv.y) * dv.y + (gu.z - c * gv.z) * dv.z) * av.z;
+            const float fuv = au.x * av.x;
+            const float X = au.y * av.x * dru + au.x * av.y * drv;
+            const float Y = 0.5f * fuv * (dru + drv);
+            float Be[kNAngR], Bq[kNAngR];
+#pragma unroll
+            for (int a = 0; a < kNAngR; ++a) {
+              const float x = rbar - P.shf_a[a];
+              Be[a] = exp2f(ka * x * x);
+              Bq[a] = -2.f * P.eta_a * x * Be[a];
+            }
+#pragma unroll
+            for (int z = 0; z < kNAngZ; ++z) {
+              const float base = fmaf(sn, P.hsin_z[z], fmaf(uc, P.hcos_z[z], 0.5f));
+              float bz, bzm1;
+              pow_zeta<ZSQ>(base, P.zeta_sq, bz, bzm1);
+              const float dbase = 0.95f * fmaf(-ucisn, P.hsin_z[z], P.hcos_z[z]);
+              const float Cz = 2.f * zeta * bzm1 * dbase * dcv * fuv;
+              const float Dz = 2.f * bz;
+              const float CDX = fmaf(Dz, X, Cz), DY = Dz * Y;
+#pragma unroll
+              for (int a = 0; a < kNAngR; ++a)
+                acc[a * kNAngZ + z] = fmaf(Be[a], CDX, fmaf(Bq[a], DY, acc[a * kNAngZ + z]));
+            }
+          }
+        }
+        hw_reduce_scatter<kNAng>(acc, hl);
+        if (live) *reinterpret_cast<float2*>(out + f0) = make_float2(acc[0], acc[1]);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+size_t aev_jvp_smem(int cap_a) {
+  return 16 * ((size_t)(3 * cap_a + 27) * sizeof(float4) + sizeof(RowCounts));
+}
+
+template <int S, int ZSQ>
+static void jvp_t(long long rows, int nsm, cudaStream_t st, const SysDesc* sys, const DescParams& P,
+                  const Workspace& ws, const double* v, float* dG) {
+  k_aev_jvp<S, ZSQ><<<warps_grid_jvp(rows, nsm), 256, aev_jvp_smem(ws.cap_a), st>>>(sys, P, ws, v, dG);
+}
+
+// --------------------------------------------------------------------------
 // launchers
 
 size_t aev_fwd_smem(int cap_a) {
@@ -634,6 +834,17 @@ static cudaError_t big_smem(K k) {
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
 }
 
+void launch_aev_jvp(long long rows, int nsm, cudaStream_t st, const SysDesc* sys, const DescParams& P,
+                    const Workspace& ws, const double* v, float* dG) {
+  const bool z5 = P.zeta_sq == 5;
+  switch (P.S) {
+    case 1: z5 ? jvp_t<1, 5>(rows, nsm, st, sys, P, ws, v, dG) : jvp_t<1, -1>(rows, nsm, st, sys, P, ws, v, dG); break;
+    case 2: z5 ? jvp_t<2, 5>(rows, nsm, st, sys, P, ws, v, dG) : jvp_t<2, -1>(rows, nsm, st, sys, P, ws, v, dG); break;
+    case 3: z5 ? jvp_t<3, 5>(rows, nsm, st, sys, P, ws, v, dG) : jvp_t<3, -1>(rows, nsm, st, sys, P, ws, v, dG); break;
+    default: z5 ? jvp_t<4, 5>(rows, nsm, st, sys, P, ws, v, dG) : jvp_t<4, -1>(rows, nsm, st, sys, P, ws, v, dG); break;
+  }
+}
+
 cudaError_t aev_set_smem_limits() {
   cudaError_t e = cudaSuccess;
 #define BS(k) if ((e = big_smem(k)) != cudaSuccess) return e
@@ -641,6 +852,8 @@ cudaError_t aev_set_smem_limits() {
   BS((k_aev_fwd<1, -1>)); BS((k_aev_fwd<2, -1>)); BS((k_aev_fwd<3, -1>)); BS((k_aev_fwd<4, -1>));
   BS((k_aev_bwd<1, 5>)); BS((k_aev_bwd<2, 5>)); BS((k_aev_bwd<3, 5>)); BS((k_aev_bwd<4, 5>));
   BS((k_aev_bwd<1, -1>)); BS((k_aev_bwd<2, -1>)); BS((k_aev_bwd<3, -1>)); BS((k_aev_bwd<4, -1>));
+  BS((k_aev_jvp<1, 5>)); BS((k_aev_jvp<2, 5>)); BS((k_aev_jvp<3, 5>)); BS((k_aev_jvp<4, 5>));
+  BS((k_aev_jvp<1, -1>)); BS((k_aev_jvp<2, -1>)); BS((k_aev_jvp<3, -1>)); BS((k_aev_jvp<4, -1>));
 #undef BS
   return e;
 }

@@ -211,6 +211,289 @@ __global__ void __launch_bounds__(256, 1) k_mlp_f32(const EvalIO* __restrict__ i
   }
 }
 
+// --------------------------------------------------------------------------
+// Force-matching weight gradients (FP32, second order).
+// With v = dL/dF, dL/dtheta = -d/dtheta sum_i <dE_i/dG_i, dG_i> where dG_i is
+// the directional derivative of atom i's descriptor along v (computed by the
+// descriptor kernels).  Per atom, forward-over-reverse through the network:
+//   tangent forward:  dz_l = dh_{l-1} W_l,  dh_l = CELU'(z_l) dz_l  (dh_0 = dG)
+//   reverse of phi = dh_3 . w_4:
+//     t_3 = w_4 CELU'(z_3),                 p_3 = w_4 CELU''(z_3) dz_3
+//     t_l = CELU'(z_l) (t_{l+1} W_{l+1}^T),  p_l = CELU'(z_l) (p_{l+1} W_{l+1}^T) + CELU''(z_l) dz_l (t_{l+1} W_{l+1}^T)
+//   dL/dW_l = -sum_i (dh_{l-1}^T t_l + h_{l-1}^T p_l),  dL/db_l = -sum_i p_l,
+//   dL/dw_4 = -sum_i dh_3,  dL/db_4 = 0.
+// Per-row buffers [rows][384]: z1 | z2 | z3 (160 | 128 | 96) and the same for dz, t, p.
+
+constexpr int kFmW = kH1 + kH2 + kH3;  // 384
+__host__ __device__ constexpr int fm_off(int layer0) {  // z1 | z2 | z3 column offsets
+  return layer0 == 0 ? 0 : (layer0 == 1 ? kH1 : kH1 + kH2);
+}
+
+__device__ __forceinline__ float d2celu(float z, float inv_al) {
+  return z > 0.f ? 0.f : expf(z * inv_al) * inv_al;
+}
+
+// Forward epilogue of the tangent pass: z = acc + b, dz = accd; store both rows-major
+// in global buffers and h, dh transposed in shared memory.
+template <int N>
+__device__ __forceinline__ void fm_store_fwd(const float (&acc)[8][N / 32], const float (&accd)[8][N / 32],
+                                             const float* bias, float* HT, float* DHT, float* z, float* dz,
+                                             int row0, int off, float al, float inv_al) {
+  const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < N / 32; ++j) {
+    const int col = tx + 32 * j;
+    const float bb = bias[col];
+    float h[8], dh[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float zz = acc[i][j] + bb;
+      const size_t g = (size_t)(row0 + ty * 8 + i) * kFmW + off + col;
+      z[g] = zz;
+      dz[g] = accd[i][j];
+      h[i] = celu_f(zz, al, inv_al);
+      dh[i] = dcelu_from_h(h[i], inv_al) * accd[i][j];
+    }
+    if (HT) {
+      *reinterpret_cast<float4*>(HT + col * kLDX + ty * 8) = make_float4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<float4*>(HT + col * kLDX + ty * 8 + 4) = make_float4(h[4], h[5], h[6], h[7]);
+      *reinterpret_cast<float4*>(DHT + col * kLDX + ty * 8) = make_float4(dh[0], dh[1], dh[2], dh[3]);
+      *reinterpret_cast<float4*>(DHT + col * kLDX + ty * 8 + 4) = make_float4(dh[4], dh[5], dh[6], dh[7]);
+    }
+  }
+}
+
+template <int S>
+__global__ void __launch_bounds__(256, 1) k_fm_fwd(DescParams P, Workspace ws, MlpF32Weights Wt,
+                                                   const float* __restrict__ dG, float* z, float* dz) {
+  constexpr int D = kNRad * S + kNAng * S * (S + 1) / 2;
+  extern __shared__ float smf[];
+  float* H1T = smf;
+  float* DH1T = H1T + kH1 * kLDX;
+  float* H2T = DH1T + kH1 * kLDX;
+  float* DH2T = H2T + kH2 * kLDX;
+  float* Bs = DH2T + kH2 * kLDX;
+  constexpr int kBsN = (D > kH1 ? D : kH1);
+  float* As = Bs + kKC * kBsN;
+  const float al = P.celu_alpha, inv_al = 1.f / P.celu_alpha;
+  const int ntiles = ws.seg[S] / kTM;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int row0 = tile * kTM;
+    const int sp = pos4_species(ws.pos4[row0]);
+    {
+      float acc[8][kH1 / 32], accd[8][kH1 / 32];
+      zero_acc<kH1>(acc);
+      zero_acc<kH1>(accd);
+      gemm_tile<kH1>(acc, nullptr, ws.G + (size_t)row0 * D, D, D, Wt.W[sp][0], Bs, As);
+      gemm_tile<kH1>(accd, nullptr, dG + (size_t)row0 * D, D, D, Wt.W[sp][0], Bs, As);
+      fm_store_fwd<kH1>(acc, accd, Wt.b[sp][0], H1T, DH1T, z, dz, row0, fm_off(0), al, inv_al);
+    }
+    {
+      float acc[8][kH2 / 32], accd[8][kH2 / 32];
+      zero_acc<kH2>(acc);
+      zero_acc<kH2>(accd);
+      gemm_tile<kH2>(acc, H1T, nullptr, 0, kH1, Wt.W[sp][1], Bs, As);
+      gemm_tile<kH2>(accd, DH1T, nullptr, 0, kH1, Wt.W[sp][1], Bs, As);
+      fm_store_fwd<kH2>(acc, accd, Wt.b[sp][1], H2T, DH2T, z, dz, row0, fm_off(1), al, inv_al);
+    }
+    {
+      float acc[8][kH3 / 32], accd[8][kH3 / 32];
+      zero_acc<kH3>(acc);
+      zero_acc<kH3>(accd);
+      gemm_tile<kH3>(acc, H2T, nullptr, 0, kH2, Wt.W[sp][2], Bs, As);
+      gemm_tile<kH3>(accd, DH2T, nullptr, 0, kH2, Wt.W[sp][2], Bs, As);
+      fm_store_fwd<kH3>(acc, accd, Wt.b[sp][2], nullptr, nullptr, z, dz, row0, fm_off(2), al, inv_al);
+    }
+    __syncthreads();
+  }
+}
+
+// Reverse epilogue: t = s' th, p = s' ph + s'' dz th (zero on padding rows);
+// store rows-major in global buffers and transposed in shared memory.
+template <int N>
+__device__ __forceinline__ void fm_store_rev(const float (&th)[8][N / 32], const float (&ph)[8][N / 32],
+                                             const float* z, const float* dz, float* t, float* p,
+                                             float* TT, float* PT, int row0, int off,
+                                             const int (&valid)[8], float inv_al) {
+  const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < N / 32; ++j) {
+    const int col = tx + 32 * j;
+    float tv[8], pv[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const size_t g = (size_t)(row0 + ty * 8 + i) * kFmW + off + col;
+      const float zz = z[g], dd = dz[g];
+      const float s1 = zz > 0.f ? 1.f : expf(zz * inv_al);
+      tv[i] = valid[i] ? s1 * th[i][j] : 0.f;
+      pv[i] = valid[i] ? fmaf(s1, ph[i][j], d2celu(zz, inv_al) * dd * th[i][j]) : 0.f;
+      t[g] = tv[i];
+      p[g] = pv[i];
+    }
+    if (TT) {
+      *reinterpret_cast<float4*>(TT + col * kLDX + ty * 8) = make_float4(tv[0], tv[1], tv[2], tv[3]);
+      *reinterpret_cast<float4*>(TT + col * kLDX + ty * 8 + 4) = make_float4(tv[4], tv[5], tv[6], tv[7]);
+      *reinterpret_cast<float4*>(PT + col * kLDX + ty * 8) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+      *reinterpret_cast<float4*>(PT + col * kLDX + ty * 8 + 4) = make_float4(pv[4], pv[5], pv[6], pv[7]);
+    }
+  }
+}
+
+template <int S>
+__global__ void __launch_bounds__(256, 1) k_fm_rev(DescParams P, Workspace ws, MlpF32Weights Wt,
+                                                   const float* z, const float* dz, float* t, float* p) {
+  extern __shared__ float smf[];
+  float* T3 = smf;
+  float* P3 = T3 + kH3 * kLDX;
+  float* T2 = P3 + kH3 * kLDX;
+  float* P2 = T2 + kH2 * kLDX;
+  float* Bs = P2 + kH2 * kLDX;
+  float* As = Bs + kKC * kH1;
+  const float inv_al = 1.f / P.celu_alpha;
+  const int ty = threadIdx.x >> 5;
+  const int ntiles = ws.seg[S] / kTM;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int row0 = tile * kTM;
+    const int sp = pos4_species(ws.pos4[row0]);
+    int valid[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) valid[i] = ws.row_atom[row0 + ty * 8 + i] >= 0;
+    {  // layer 3: th3 = w4, ph3 = 0
+      float th[8][kH3 / 32], ph[8][kH3 / 32];
+      const int tx = threadIdx.x & 31;
+#pragma unroll
+      for (int j = 0; j < kH3 / 32; ++j)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          th[i][j] = Wt.W[sp][3][tx + 32 * j];
+          ph[i][j] = 0.f;
+        }
+      fm_store_rev<kH3>(th, ph, z, dz, t, p, T3, P3, row0, fm_off(2), valid, inv_al);
+    }
+    {  // layer 2: th2 = t3 W3^T, ph2 = p3 W3^T
+      float th[8][kH2 / 32], ph[8][kH2 / 32];
+      zero_acc<kH2>(th);
+      zero_acc<kH2>(ph);
+      gemm_tile<kH2>(th, T3, nullptr, 0, kH3, Wt.WT[sp][2], Bs, As);
+      gemm_tile<kH2>(ph, P3, nullptr, 0, kH3, Wt.WT[sp][2], Bs, As);
+      fm_store_rev<kH2>(th, ph, z, dz, t, p, T2, P2, row0, fm_off(1), valid, inv_al);
+    }
+    {  // layer 1: th1 = t2 W2^T, ph1 = p2 W2^T
+      float th[8][kH1 / 32], ph[8][kH1 / 32];
+      zero_acc<kH1>(th);
+      zero_acc<kH1>(ph);
+      gemm_tile<kH1>(th, T2, nullptr, 0, kH2, Wt.WT[sp][1], Bs, As);
+      gemm_tile<kH1>(ph, P2, nullptr, 0, kH2, Wt.WT[sp][1], Bs, As);
+      fm_store_rev<kH1>(th, ph, z, dz, t, p, nullptr, nullptr, row0, fm_off(0), valid, inv_al);
+    }
+    __syncthreads();
+  }
+}
+
+// Weight-gradient reduction over the rows of one species.  Job = a 32 x 32
+// tile (i0, o0) of layer l's (fan_in x fan_out) gradient, for rows [r0, r1);
+// l = 4 means w4 (tile of 32 x 1).  FP32 partials per 64-row chunk, FP64 sums,
+// FP64 atomic add into the packed gradient (zeroed before).
+__global__ void __launch_bounds__(256) k_fm_wgrad(DescParams P, const FmJob* __restrict__ jobs, int njobs,
+                                                  const float* __restrict__ G, const float* __restrict__ dG,
+                                                  const float* __restrict__ z, const float* __restrict__ dz,
+                                                  const float* __restrict__ t, const float* __restrict__ p,
+                                                  double* grad) {
+  __shared__ float Hc[64][33], DHc[64][33], Tc[64][33], Pc[64][33];
+  const int D = P.D;
+  const float al = P.celu_alpha, inv_al = 1.f / P.celu_alpha;
+  const int tid = threadIdx.x;
+  const int il = tid >> 3;          // 0..31 : input index in the tile
+  const int ol = (tid & 7) * 4;     // 0..28 : first of four output indices
+  for (int jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
+    const FmJob jbv = jobs[jb];
+    const int l = jbv.l;
+    const int fin = l == 1 ? D : (l == 2 ? kH1 : (l == 3 ? kH2 : kH3));
+    const int fout = l == 1 ? kH1 : (l == 2 ? kH2 : (l == 3 ? kH3 : 1));
+    double accd[4] = {0.0, 0.0, 0.0, 0.0};
+    double bacc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int c0 = jbv.r0; c0 < jbv.r1; c0 += 64) {
+      const int nr = min(64, jbv.r1 - c0);
+      __syncthreads();
+      for (int e = tid; e < 64 * 32; e += 256) {
+        const int rr = e >> 5, cc = e & 31;
+        const int r = c0 + rr, i = jbv.i0 + cc, o = jbv.o0 + cc;
+        float hv = 0.f, dhv = 0.f, tv = 0.f, pv = 0.f;
+        if (rr < nr) {
+          if (i < fin) {
+            if (l == 1) {
+              hv = G[(size_t)r * D + i];
+              dhv = dG[(size_t)r * D + i];
+            } else {
+              const int off = fm_off(l - 2);
+              const float zz = z[(size_t)r * kFmW + off + i];
+              hv = celu_f(zz, al, inv_al);
+              dhv = dcelu_from_h(hv, inv_al) * dz[(size_t)r * kFmW + off + i];
+            }
+          }
+          if (l < 4 && o < fout) {
+            tv = t[(size_t)r * kFmW + fm_off(l - 1) + o];
+            pv = p[(size_t)r * kFmW + fm_off(l - 1) + o];
+          } else if (l == 4 && cc == 0) {
+            tv = 1.f;  // phi = dh_3 . w4: adjoint of w4 is dh_3
+          }
+        }
+        Hc[rr][cc] = hv;
+        DHc[rr][cc] = dhv;
+        Tc[rr][cc] = tv;
+        Pc[rr][cc] = pv;
+      }
+      __syncthreads();
+      float a[4] = {0.f, 0.f, 0.f, 0.f}, b[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int rr = 0; rr < nr; ++rr) {
+        const float hv = Hc[rr][il], dhv = DHc[rr][il];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          a[k] = fmaf(dhv, Tc[rr][ol + k], fmaf(hv, Pc[rr][ol + k], a[k]));
+          b[k] += Pc[rr][ol + k];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        accd[k] += (double)a[k];
+        bacc[k] += (double)b[k];
+      }
+    }
+    const int i = jbv.i0 + il;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int o = jbv.o0 + ol + k;
+      if (i < fin && o < fout) atomicAdd(&grad[jbv.w_off + (size_t)i * fout + o], -accd[k]);
+      if (jbv.i0 == 0 && il == 0 && o < fout && l < 4) atomicAdd(&grad[jbv.b_off + o], -bacc[k]);
+    }
+  }
+}
+
+size_t fm_fwd_smem(int D) {
+  const int bsn = D > kH1 ? D : kH1;
+  return sizeof(float) * ((size_t)(2 * kH1 + 2 * kH2) * kLDX + (size_t)kKC * bsn + (size_t)kKC * kLDX);
+}
+size_t fm_rev_smem() {
+  return sizeof(float) * ((size_t)(2 * kH3 + 2 * kH2) * kLDX + (size_t)kKC * kH1 + (size_t)kKC * kLDX);
+}
+
+void launch_fm(int grid, cudaStream_t st, const DescParams& P, const Workspace& ws, const MlpF32Weights& W,
+               const float* dG, float* z, float* dz, float* t, float* p) {
+  const size_t sf = fm_fwd_smem(P.D), sr = fm_rev_smem();
+  switch (P.S) {
+    case 1: k_fm_fwd<1><<<grid, 256, sf, st>>>(P, ws, W, dG, z, dz); k_fm_rev<1><<<grid, 256, sr, st>>>(P, ws, W, z, dz, t, p); break;
+    case 2: k_fm_fwd<2><<<grid, 256, sf, st>>>(P, ws, W, dG, z, dz); k_fm_rev<2><<<grid, 256, sr, st>>>(P, ws, W, z, dz, t, p); break;
+    case 3: k_fm_fwd<3><<<grid, 256, sf, st>>>(P, ws, W, dG, z, dz); k_fm_rev<3><<<grid, 256, sr, st>>>(P, ws, W, z, dz, t, p); break;
+    default: k_fm_fwd<4><<<grid, 256, sf, st>>>(P, ws, W, dG, z, dz); k_fm_rev<4><<<grid, 256, sr, st>>>(P, ws, W, z, dz, t, p); break;
+  }
+}
+
+void launch_fm_wgrad(int grid, cudaStream_t st, const DescParams& P, const FmJob* jobs, int njobs,
+                     const float* G, const float* dG, const float* z, const float* dz, const float* t,
+                     const float* p, double* grad) {
+  k_fm_wgrad<<<grid, 256, 0, st>>>(P, jobs, njobs, G, dG, z, dz, t, p, grad);
+}
+
 size_t mlp_f32_smem(int D) {
   const int bsn = D > kH1 ? D : kH1;
   return sizeof(float) * ((size_t)(kH1 + kH2 + kH3) * kLDX + (size_t)kKC * bsn + (size_t)kKC * kLDX);
@@ -232,7 +515,14 @@ cudaError_t mlp_f32_set_smem_limits() {
   e = cudaFuncSetAttribute(k_mlp_f32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_f32_smem(48)); if (e) return e;
   e = cudaFuncSetAttribute(k_mlp_f32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_f32_smem(128)); if (e) return e;
   e = cudaFuncSetAttribute(k_mlp_f32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_f32_smem(240)); if (e) return e;
-  e = cudaFuncSetAttribute(k_mlp_f32<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_f32_smem(384));
+  e = cudaFuncSetAttribute(k_mlp_f32<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_f32_smem(384)); if (e) return e;
+  const int Ds[4] = {48, 128, 240, 384};
+  const void* fwd[4] = {(const void*)k_fm_fwd<1>, (const void*)k_fm_fwd<2>, (const void*)k_fm_fwd<3>, (const void*)k_fm_fwd<4>};
+  const void* rev[4] = {(const void*)k_fm_rev<1>, (const void*)k_fm_rev<2>, (const void*)k_fm_rev<3>, (const void*)k_fm_rev<4>};
+  for (int q = 0; q < 4; ++q) {
+    e = cudaFuncSetAttribute(fwd[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fm_fwd_smem(Ds[q])); if (e) return e;
+    e = cudaFuncSetAttribute(rev[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fm_rev_smem()); if (e) return e;
+  }
   return e;
 }
 

@@ -84,7 +84,8 @@ nnp_ctx::~nnp_ctx() {
   void* bufs[] = {b_bin_count, b_bin_start, b_bin_len, b_atom_bin, b_atom_slot, b_atom_cell,
                   b_atom_sys, b_atom_off, b_row_atom, b_row_info, b_row_cell, b_pos4, b_cnt_r,
                   b_cnt_a, b_nbr_r, b_G, b_dEdG, b_Ei, b_Gh, b_sys, b_pos_stage,
-                  b_Z_stage, b_F_stage, b_E_stage, b_seg, b_flags, d_zlut, d_io, b_wf32};
+                  b_Z_stage, b_F_stage, b_E_stage, b_seg, b_flags, d_zlut, d_io, b_wf32,
+                  fm_z, fm_dz, fm_t, fm_p, fm_v, fm_ref, fm_grad, fm_jobs};
   for (void* p : bufs)
     if (p) cudaFree(p);
   for (auto& ev : stage_ev)
@@ -94,7 +95,7 @@ nnp_ctx::~nnp_ctx() {
   if (own_stream && stream) cudaStreamDestroy(stream);
 }
 
-static bool dev_ptr(const void* p) {
+bool nnp_ctx::is_device(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
@@ -111,9 +112,9 @@ int nnp_ctx::set_weights(int s, const float* const W[4], const float* const b[4]
     w[l].resize((size_t)fin[l] * fout[l]);
     bb[l].resize(fout[l]);
     const size_t wb = sizeof(float) * w[l].size(), bbytes = sizeof(float) * bb[l].size();
-    if (dev_ptr(W[l])) CK(cudaMemcpy(w[l].data(), W[l], wb, cudaMemcpyDeviceToHost));
+    if (is_device(W[l])) CK(cudaMemcpy(w[l].data(), W[l], wb, cudaMemcpyDeviceToHost));
     else memcpy(w[l].data(), W[l], wb);
-    if (dev_ptr(b[l])) CK(cudaMemcpy(bb[l].data(), b[l], bbytes, cudaMemcpyDeviceToHost));
+    if (is_device(b[l])) CK(cudaMemcpy(bb[l].data(), b[l], bbytes, cudaMemcpyDeviceToHost));
     else memcpy(bb[l].data(), b[l], bbytes);
     for (float x : w[l])
       if (!std::isfinite(x)) return fail(NNP_ERR_INVALID_ARG, "non-finite weight in layer %d", l);
@@ -149,8 +150,118 @@ int nnp_ctx::set_weights(int s, const float* const W[4], const float* const b[4]
   return NNP_OK;
 }
 
-int nnp_ctx::force_match_grad(const double*, const double*, double*, double*) {
-  return fail(NNP_ERR_UNSUPPORTED, "force-matching gradients are not built yet");
+// v = 2 (F - Fref) / (3n) and loss = |F - Fref|^2 / (3n) (FP64).
+__global__ void k_fm_v(const double* __restrict__ F, const double* __restrict__ Fref, long long n3,
+                       double scale, double* v, double* loss) {
+  double part = 0.0;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n3;
+       q += (long long)gridDim.x * blockDim.x) {
+    const double e = F[q] - Fref[q];
+    v[q] = 2.0 * e * scale;
+    part += e * e;
+  }
+  for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, part * scale);
+}
+
+template <class T>
+static cudaError_t grow_buf(T*& p, size_t& cap, size_t need) {
+  if (p && cap >= need) return cudaSuccess;
+  if (p) cudaFree(p);
+  p = nullptr;
+  cap = 0;
+  cudaError_t e = cudaMalloc(&p, need * sizeof(T));
+  if (e == cudaSuccess) cap = need;
+  return e;
+}
+
+int nnp_ctx::force_match_grad(const double* v, const double* Fref, double* loss, double* grad) {
+  if (!has_state) return fail(NNP_ERR_NO_STATE, "nnp_force_match_grad needs a previous nnp_eval");
+  if (!grad) return fail(NNP_ERR_INVALID_ARG, "null gradient output");
+  if (!v && !Fref) return fail(NNP_ERR_INVALID_ARG, "pass v = dL/dF or the reference forces");
+  const long long n = last_n, rows = last_rows;
+  const int D = P.D;
+  const size_t npar = (size_t)nnp_param_count(this);
+  CK(cudaStreamSynchronize(stream));
+  CK(grow_buf(fm_z, fm_cap, (size_t)rows * 384));
+  CK(grow_buf(fm_dz, fm_cap2, (size_t)rows * 384));
+  CK(grow_buf(fm_t, fm_cap3, (size_t)rows * 384));
+  CK(grow_buf(fm_p, fm_cap4, (size_t)rows * 384));
+  CK(grow_buf(fm_v, fm_vcap, (size_t)n * 3));
+  CK(grow_buf(fm_ref, fm_refcap, (size_t)n * 3));
+  CK(grow_buf(fm_grad, fm_gcap, npar + 1));  // last entry: loss
+  const Workspace w = workspace();
+  // 1. FP32 forces of the last evaluated configuration into internal buffers
+  EvalIO io = *h_io;
+  io.forces = b_F_stage;
+  io.energies = b_E_stage;
+  *h_io = io;
+  CK(cudaMemcpyAsync(d_io, h_io, sizeof(EvalIO), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemsetAsync(b_F_stage, 0, sizeof(double) * 3 * n, stream));
+  CK(cudaMemsetAsync(b_E_stage, 0, sizeof(double) * last_B, stream));
+  launch_aev_fwd(rows, num_sms, stream, b_sys, P, w, 0);
+  const int g_tiles = (int)std::max<long long>(1, std::min<long long>(rows / 64, (long long)num_sms));
+  launch_mlp_f32(g_tiles, stream, d_io, P, w, wf32);
+  launch_aev_bwd(rows, num_sms, stream, d_io, b_sys, P, w);
+  // 2. v = dL/dF (given, or from the reference forces)
+  double* lossd = fm_grad + npar;
+  CK(cudaMemsetAsync(fm_grad, 0, sizeof(double) * (npar + 1), stream));
+  if (Fref) {
+    const double* fr = Fref;
+    if (!is_device(Fref)) {
+      CK(cudaMemcpyAsync(fm_ref, Fref, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, stream));
+      fr = fm_ref;
+    }
+    k_fm_v<<<std::max(1, std::min(num_sms * 4, (int)((3 * n + 255) / 256))), 256, 0, stream>>>(
+        b_F_stage, fr, 3 * n, 1.0 / (3.0 * (double)n), fm_v, lossd);
+  } else {
+    CK(cudaMemcpyAsync(fm_v, v, sizeof(double) * 3 * n,
+                       is_device(v) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, stream));
+  }
+  // 3. tangent descriptors dG = J_G v (into the dE/dG buffer)
+  launch_aev_jvp(rows, num_sms, stream, b_sys, P, w, fm_v, b_dEdG);
+  // 4. network: primal + tangent forward, reverse adjoints
+  launch_fm(g_tiles, stream, P, w, wf32, b_dEdG, fm_z, fm_dz, fm_t, fm_p);
+  // 5. weight-gradient jobs per species, layer, 32 x 32 tile and row segment
+  int seg[kMaxS + 2];
+  CK(cudaMemcpyAsync(seg, b_seg, sizeof(seg), cudaMemcpyDeviceToHost, stream));
+  CK(cudaStreamSynchronize(stream));
+  std::vector<FmJob> jobs;
+  const int fin[4] = {D, kH1, kH2, kH3}, fout[4] = {kH1, kH2, kH3, 1};
+  const size_t per = npar / P.S;
+  for (int sp = 0; sp < P.S; ++sp) {
+    size_t off = per * sp;
+    size_t woff[4], boff[4];
+    for (int l = 0; l < 4; ++l) {
+      woff[l] = off;
+      off += (size_t)fin[l] * fout[l];
+      boff[l] = off;
+      off += fout[l];
+    }
+    for (int r0 = seg[sp]; r0 < seg[sp + 1]; r0 += 2048) {
+      const int r1 = std::min(seg[sp + 1], r0 + 2048);
+      for (int l = 0; l < 4; ++l)
+        for (int i0 = 0; i0 < fin[l]; i0 += 32)
+          for (int o0 = 0; o0 < fout[l]; o0 += 32)
+            jobs.push_back(FmJob{l + 1, i0, o0, r0, r1, (long long)woff[l], (long long)boff[l]});
+    }
+  }
+  CK(grow_buf(fm_jobs, fm_jcap, jobs.size() + 1));
+  CK(cudaMemcpyAsync(fm_jobs, jobs.data(), sizeof(FmJob) * jobs.size(), cudaMemcpyHostToDevice, stream));
+  launch_fm_wgrad(std::max(1, std::min((int)jobs.size(), num_sms * 8)), stream, P, fm_jobs, (int)jobs.size(),
+                  b_G, b_dEdG, fm_z, fm_dz, fm_t, fm_p, fm_grad);
+  CK(cudaGetLastError());
+  // 6. results
+  CK(cudaMemcpyAsync(grad, fm_grad, sizeof(double) * npar,
+                     is_device(grad) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream));
+  if (loss) {
+    double lh = 0.0;
+    CK(cudaMemcpyAsync(&lh, lossd, sizeof(double), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    *loss = Fref ? lh : 0.0;
+  }
+  CK(cudaStreamSynchronize(stream));
+  return NNP_OK;
 }
 
 int nnp_ctx::profile_stages(double* out, int n_out) {

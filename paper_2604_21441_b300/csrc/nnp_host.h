@@ -30,6 +30,13 @@ cudaError_t aev_set_smem_limits();
 void launch_mlp_f32(int grid, cudaStream_t st, const EvalIO* io, const DescParams& P,
                     const Workspace& ws, const MlpF32Weights& W);
 cudaError_t mlp_f32_set_smem_limits();
+void launch_fm(int grid, cudaStream_t st, const DescParams& P, const Workspace& ws, const MlpF32Weights& W,
+               const float* dG, float* z, float* dz, float* t, float* p);
+void launch_fm_wgrad(int grid, cudaStream_t st, const DescParams& P, const FmJob* jobs, int njobs,
+                     const float* G, const float* dG, const float* z, const float* dz, const float* t,
+                     const float* p, double* grad);
+void launch_aev_jvp(long long rows, int nsm, cudaStream_t st, const SysDesc* sys, const DescParams& P,
+                    const Workspace& ws, const double* v, float* dG);
 
 }  // namespace nnp
 
@@ -88,6 +95,13 @@ struct nnp_ctx {
   bool has_weights[nnp::kMaxS] = {false, false, false, false};
   std::vector<float> host_weights;  // FP32 copy (layout of nnp_param_count), for re-quantisation
   void* tc = nullptr;           // tensor-core network state (k_mlp_tc.cu)
+
+  // force-matching buffers (allocated on first use)
+  float *fm_z = nullptr, *fm_dz = nullptr, *fm_t = nullptr, *fm_p = nullptr;
+  double *fm_v = nullptr, *fm_ref = nullptr, *fm_grad = nullptr;
+  nnp::FmJob* fm_jobs = nullptr;
+  size_t fm_cap = 0, fm_cap2 = 0, fm_cap3 = 0, fm_cap4 = 0, fm_vcap = 0, fm_refcap = 0, fm_gcap = 0, fm_jcap = 0;
+  static bool is_device(const void* p);
 
   // stage events (NNP_FLAG_STAGE_EVENTS)
   cudaEvent_t stage_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};

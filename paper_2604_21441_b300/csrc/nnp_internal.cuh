@@ -119,6 +119,14 @@ struct MlpF32Weights {
   const float* b[kMaxS][4];
 };
 
+// One block of the force-matching weight-gradient reduction: a 32 x 32 tile
+// (i0, o0) of layer l's gradient (l = 4: the output weights), over rows
+// [r0, r1) of one species; w_off / b_off index the packed gradient.
+struct FmJob {
+  int l, i0, o0, r0, r1;
+  long long w_off, b_off;
+};
+
 // --------------------------------------------------------------------------
 // small device helpers
 
