@@ -177,8 +177,11 @@ int nnp_eval_async(nnp_ctx *ctx, int64_t n, const double *pos, const int32_t *Z,
 int nnp_eval_noalloc(nnp_ctx *ctx, int64_t n, const double *pos, const int32_t *Z,
                      const double *box, double *energy, double *forces);
 
-/* Wait for the context's stream and report device-side flags raised since
- * the last check. */
+/* Wait for the context's stream and report device-side flags raised by the
+ * asynchronous evaluations since the last check (they accumulate until this
+ * call reads and clears them).  A list overflow grows the capacity for the
+ * next evaluation and returns NNP_ERR_CAPACITY: results since the last check
+ * are not valid. */
 int nnp_sync(nnp_ctx *ctx);
 
 /* B independent systems in one pass (one CUDA graph launch).

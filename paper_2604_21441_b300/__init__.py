@@ -168,8 +168,15 @@ class NNP:
         cfg.max_atoms = int(max_atoms)
         cfg.max_systems = int(max_systems)
         cfg.flags = int(flags)
+        self.torch_stream = None
         if stream is not None:
-            cfg.stream = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+            handle = stream if isinstance(stream, int) else stream.cuda_stream
+            if not handle:
+                raise ValueError("pass a non-default CUDA stream (the legacy default stream "
+                                 "does not order against the library's own stream)")
+            cfg.stream = ctypes.c_void_p(handle)
+            if not isinstance(stream, int):
+                self.torch_stream = stream
         for k, v in overrides.items():
             if k in ("shf_r", "shf_a", "shf_z"):
                 arr = getattr(cfg, k)

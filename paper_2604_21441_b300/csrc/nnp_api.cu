@@ -165,7 +165,6 @@ int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows)
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   CK(cudaStreamIsCapturing(stream, &cs));
   const bool capturing = cs == cudaStreamCaptureStatusActive;
-  CK(cudaMemsetAsync(b_flags, 0, sizeof(int) * kNumFlags, stream));
   mark_stage(0, capturing);
   k_bin<<<g_atoms, 256, 0, stream>>>(io, sys, d_zlut, w); ++launches;
   k_scan<<<1, 1024, 0, stream>>>(io, P.S, w); ++launches;
@@ -323,6 +322,9 @@ int nnp_ctx::evaluate(int B, const int64_t* offsets, const double* pos, const in
     if (!Z_dev) CK(cudaMemcpyAsync(b_Z_stage, Z, sizeof(int) * n, cudaMemcpyHostToDevice, stream));
     CK(cudaMemcpyAsync(d_io, h_io, sizeof(EvalIO), cudaMemcpyHostToDevice, stream));
     CK(cudaMemcpyAsync(b_sys, sys_h.data(), sizeof(SysDesc) * B, cudaMemcpyHostToDevice, stream));
+    // device flags accumulate over asynchronous evaluations until nnp_sync reads them;
+    // a synchronous evaluation reports only its own
+    if (sync) CK(cudaMemsetAsync(b_flags, 0, sizeof(int) * kNumFlags, stream));
     const bool use_graph = !(cfg.flags & NNP_FLAG_NO_GRAPH);
     if (use_graph) {
       if (!gexec || g_key_n != n || g_key_B != B || g_key_bins != bins) {
@@ -515,8 +517,13 @@ int nnp_sync(nnp_ctx* ctx) {
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaStreamSynchronize");
   if (!ctx->has_state) return NNP_OK;
+  e = cudaMemcpy(ctx->h_flags, ctx->b_flags, sizeof(int) * kNumFlags, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(ctx->b_flags, 0, sizeof(int) * kNumFlags);
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "nnp_sync flags");
   int st = ctx->check_flags();
-  if (st == -1) return ctx->fail(NNP_ERR_CAPACITY, "neighbour lists overflowed; capacity grown, evaluate again");
+  if (st == -1)
+    return ctx->fail(NNP_ERR_CAPACITY,
+                     "neighbour lists overflowed since the last check; capacity grown, evaluate again");
   return st;
 }
 
