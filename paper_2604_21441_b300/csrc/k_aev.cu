@@ -483,9 +483,16 @@ __global__ void __launch_bounds__(128) k_aev_bwd(const EvalIO* __restrict__ io,
           const float4 x = wb[q];
           wr[4 * q] = x.x; wr[4 * q + 1] = x.y; wr[4 * q + 2] = x.z; wr[4 * q + 3] = x.w;
         }
-        for (int t0 = 0; t0 < Tmax; t0 += 16) {
-          const int t = t0 + hl;
-          if (t < T) {
+        // each lane walks a contiguous chunk of the pair index: the first
+        // neighbour u stays fixed over runs, so its force is summed in
+        // registers and flushed once per run; only v needs an atomic per pair
+        const int chunk = (T + 15) >> 4;
+        const int cmax = max(chunk, __shfl_xor_sync(0xffffffffu, chunk, 16));
+        int cur_u = -1;
+        float aux_ = 0.f, auy = 0.f, auz = 0.f;
+        for (int j = 0; j < cmax; ++j) {
+          const int t = hl * chunk + j;
+          if (j < chunk && t < T) {
             int u, v;
             map_pair(pm, t, u, v);
             const float4 gu = geo[u], gv = geo[v], au = aux[u], av = aux[v];
@@ -540,9 +547,18 @@ __global__ void __launch_bounds__(128) k_aev_bwd(const EvalIO* __restrict__ io,
             const float gvx = fmaf(Av, gv.x, Bv * gu.x), gvy = fmaf(Av, gv.y, Bv * gu.y),
                         gvz = fmaf(Av, gv.z, Bv * gu.z);
             const int su = __float_as_int(au.w), svs = __float_as_int(av.w);
-            atomicAdd(&fsl[3 * su], -gux);
-            atomicAdd(&fsl[3 * su + 1], -guy);
-            atomicAdd(&fsl[3 * su + 2], -guz);
+            if (su != cur_u) {
+              if (cur_u >= 0) {
+                atomicAdd(&fsl[3 * cur_u], aux_);
+                atomicAdd(&fsl[3 * cur_u + 1], auy);
+                atomicAdd(&fsl[3 * cur_u + 2], auz);
+              }
+              cur_u = su;
+              aux_ = auy = auz = 0.f;
+            }
+            aux_ -= gux;
+            auy -= guy;
+            auz -= guz;
             atomicAdd(&fsl[3 * svs], -gvx);
             atomicAdd(&fsl[3 * svs + 1], -gvy);
             atomicAdd(&fsl[3 * svs + 2], -gvz);
@@ -550,6 +566,11 @@ __global__ void __launch_bounds__(128) k_aev_bwd(const EvalIO* __restrict__ io,
             fiy += guy + gvy;
             fiz += guz + gvz;
           }
+        }
+        if (cur_u >= 0) {
+          atomicAdd(&fsl[3 * cur_u], aux_);
+          atomicAdd(&fsl[3 * cur_u + 1], auy);
+          atomicAdd(&fsl[3 * cur_u + 2], auz);
         }
       }
     }
