@@ -364,7 +364,8 @@ def main():
     else:
         peak = alu_peak
     roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": profiled_traffic(dom, args.precision),
                 "peak_source": (f"{pk_kind} bf16" if bound == "tensor" else
                                 "148 SMs x 128 FP32 lanes x 2 x max SM clock"),
                 "stage_ms": st}
@@ -392,6 +393,29 @@ def main():
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+STAGE_KERNEL = {"descriptor": "k_aev_fwd", "descriptor_backward": "k_aev_bwd",
+                "neighbours": "k_neighbors", "network": None}
+
+
+def profiled_traffic(stage, precision):
+    """DRAM bytes per launch of the stage's kernel from the committed ncu
+    record (profiles/ncu_traffic.json), or None if that kernel's source file
+    changed since the capture."""
+    import hashlib
+    kernel = STAGE_KERNEL.get(stage) or ("k_mlp_f32" if precision == "fp32" else "k_mlp_bf16")
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            rec = json.load(f).get(kernel)
+        if not rec or "source" not in rec:
+            return None
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != rec["source_sha256"]:
+                return None
+        return rec["bytes_per_launch"]
+    except (OSError, ValueError, KeyError):
+        return None
 
 
 def neighbour_stats(r):
