@@ -155,7 +155,7 @@ def run_ours(args, rank, world, local_rank):
 
     def make(prec, flags=0):
         pot = P.NNP(atomic_numbers=wl["atomic_numbers"], precision=prec, max_atoms=n,
-                    max_systems=B, stream=stream, flags=flags)
+                    max_systems=B, stream=stream, flags=flags | P.FLAG_AUTOTUNE)
         pot.set_all_weights(w32)
         return pot
 
@@ -169,12 +169,16 @@ def run_ours(args, rank, world, local_rank):
         if B == 1:
             pot.eval_into(pos, Z, boxes[0], E, F, sync=False)
         else:
-            pot._check(pot._L.nnp_eval_batch(
-                pot._h, B, P.ctypes.c_void_p(off.ctypes.data), P.ctypes.c_void_p(pos.data_ptr()),
-                P.ctypes.c_void_p(Z.data_ptr()), P.ctypes.c_void_p(boxes.ctypes.data),
-                P.ctypes.c_void_p(E.data_ptr()), P.ctypes.c_void_p(F.data_ptr())))
+            pot.eval_batch_into(off, pos, Z, boxes, E, F, sync=False)
+
+    def step_sync(pot):
+        if B == 1:
+            pot.eval_into(pos, Z, boxes[0], E, F, sync=True)
+        else:
+            pot.eval_batch_into(off, pos, Z, boxes, E, F, sync=True)
 
     def timed(pot, K, W, stage=False):
+        step_sync(pot)  # settles list capacities (synchronous calls regrow them)
         for _ in range(W):
             step_async(pot)
             pot.sync()
@@ -246,7 +250,40 @@ def run_ours(args, rank, world, local_rank):
             e_, f_ = pot.eval_batch(off, pos_h, Z_h, boxes)
     t_e2e = time.perf_counter() - t0
     launches = pot.query("launches_per_eval")
-    return dict(n=n, B=B, S=S, D=D, ms=ms, forms=forms, clocks=clk, stage_ms=stage_ms.tolist(),
+    tuned = {k: pot.query("tune_" + k) for k in ("neighbours", "descriptor", "backward")}
+    per_system = None
+    if B > 1:  # the same batch as one graph launch per system (one context each)
+        pots = [P.NNP(atomic_numbers=wl["atomic_numbers"], precision=args.precision,
+                      max_atoms=int(off[b + 1] - off[b]), stream=stream) for b in range(B)]
+        for q in pots:
+            q.set_all_weights(w32)
+
+        def per_sys_step():
+            for b, q in enumerate(pots):
+                q.eval_into(pos[off[b]:off[b + 1]], Z[off[b]:off[b + 1]], boxes[b],
+                            E[b:b + 1], F[off[b]:off[b + 1]], sync=False)
+        for b, q in enumerate(pots):
+            q.eval_into(pos[off[b]:off[b + 1]], Z[off[b]:off[b + 1]], boxes[b],
+                        E[b:b + 1], F[off[b]:off[b + 1]], sync=True)
+        for _ in range(2):
+            per_sys_step()
+            for q in pots:
+                q.sync()
+        ts = []
+        with torch.cuda.stream(stream):
+            for _ in range(max(3, args.steps // 3)):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                per_sys_step()
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+        for q in pots:
+            q.sync()
+            q.close()
+        per_system = float(np.mean(ts))
+    return dict(tuned=tuned, per_system_ms=per_system, n=n, B=B, S=S, D=D, ms=ms, forms=forms, clocks=clk, stage_ms=stage_ms.tolist(),
                 e2e=n * K_e2e / t_e2e, e2e_ms=t_e2e / K_e2e * 1e3, launches=launches,
                 wl=wl, pot=pot, pos_h=pos_h, Z_h=Z_h, boxes=boxes, w=w)
 
@@ -385,11 +422,16 @@ def main():
         "e2e": {"value": r["e2e"], "unit": UNIT, "ms_per_step": r["e2e_ms"],
                 "h2d_bytes_per_step": r["n"] * (24 + 4), "d2h_bytes_per_step": r["n"] * 24 + 8 * r["B"]},
         "gpu_launches": int(r["launches"]) * args.steps,
+        "autotuned_blocks_per_sm": r["tuned"],
         "clocks": r["clocks"],
         "roofline": roofline,
         "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": cpu_desc},
     }
+    if r["per_system_ms"] is not None:
+        line["batch"] = {"systems": r["B"], "one_graph_launch_ms": ms_mean,
+                         "one_launch_per_system_ms": r["per_system_ms"],
+                         "speedup": r["per_system_ms"] / ms_mean}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

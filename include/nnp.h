@@ -66,6 +66,8 @@ typedef enum {
 #define NNP_FLAG_NO_GRAPH 0x1u      /* launch kernels directly instead of a CUDA graph */
 #define NNP_FLAG_NONDETERMINISTIC_BINS 0x2u /* skip the per-cell ordering pass */
 #define NNP_FLAG_STAGE_EVENTS 0x4u  /* record CUDA events between pipeline stages */
+#define NNP_FLAG_AUTOTUNE 0x8u      /* pick launch shapes by timing them (cached per shape bucket;
+                                       file cache: environment NNP_AUTOTUNE_CACHE) */
 
 /*
  * Model hyper-parameters and capacities.  Fill with nnp_config_init() and
@@ -192,6 +194,12 @@ int nnp_sync(nnp_ctx *ctx);
 int nnp_eval_batch(nnp_ctx *ctx, int32_t B, const int64_t *offsets, const double *pos,
                    const int32_t *Z, const double *boxes, double *energies, double *forces);
 
+/* As nnp_eval_batch, but pos, Z, energies and forces must be device pointers
+ * and the call returns without synchronising (flags: see nnp_sync).  Boxes
+ * are host pointers and must be given (periodic systems). */
+int nnp_eval_batch_async(nnp_ctx *ctx, int32_t B, const int64_t *offsets, const double *pos,
+                         const int32_t *Z, const double *boxes, double *energies, double *forces);
+
 /* Number of network parameters: S * sum_l (fan_in*fan_out + fan_out), packed
  * per species as W1 b1 W2 b2 W3 b3 W4 b4 (each W row-major fan_in x fan_out). */
 int64_t nnp_param_count(const nnp_ctx *ctx);
@@ -223,7 +231,10 @@ typedef enum {
     NNP_Q_MAX_NBR = 3,            /* max radial neighbours seen in the last eval */
     NNP_Q_MAX_ANG = 4,            /* max angular neighbours seen in the last eval */
     NNP_Q_ROWS = 5,               /* padded rows of the last eval */
-    NNP_Q_GRAPH_CAPTURES = 6      /* CUDA graphs captured so far */
+    NNP_Q_GRAPH_CAPTURES = 6,     /* CUDA graphs captured so far */
+    NNP_Q_TUNE_NEIGHBOURS = 7,    /* blocks-per-SM cap of the neighbour kernel */
+    NNP_Q_TUNE_DESCRIPTOR = 8,    /* ... of the descriptor kernel */
+    NNP_Q_TUNE_BACKWARD = 9       /* ... of the descriptor-backward kernel */
 } nnp_query_key;
 
 int nnp_query(nnp_ctx *ctx, int32_t key, int64_t *value);

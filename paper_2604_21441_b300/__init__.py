@@ -32,16 +32,19 @@ PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2}
 FLAG_NO_GRAPH = 0x1
 FLAG_NONDETERMINISTIC_BINS = 0x2
 FLAG_STAGE_EVENTS = 0x4
+FLAG_AUTOTUNE = 0x8
 STAGES = ("cells", "neighbours", "descriptor", "network", "descriptor_backward")
 
 # Every entry point declared in include/nnp.h.
 ABI_FUNCTIONS = ("nnp_config_init", "nnp_create", "nnp_destroy", "nnp_last_error",
                  "nnp_set_weights", "nnp_eval", "nnp_eval_async", "nnp_sync",
                  "nnp_eval_batch", "nnp_param_count", "nnp_force_match_grad", "nnp_query",
-                 "nnp_profile_stages", "nnp_atom_energies", "nnp_eval_noalloc")
+                 "nnp_profile_stages", "nnp_atom_energies", "nnp_eval_noalloc",
+                 "nnp_eval_batch_async")
 
 QUERY = {"launches_per_eval": 0, "nbr_capacity": 1, "ang_capacity": 2, "max_nbr": 3,
-         "max_ang": 4, "rows": 5, "graph_captures": 6}
+         "max_ang": 4, "rows": 5, "graph_captures": 6,
+         "tune_neighbours": 7, "tune_descriptor": 8, "tune_backward": 9}
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNKNOWN_SPECIES", 3: "UNSUPPORTED", 4: "CAPACITY",
           5: "CUDA", 6: "TIMEOUT", 7: "NO_WEIGHTS", 8: "NO_STATE"}
@@ -107,6 +110,8 @@ def lib() -> ctypes.CDLL:
     L.nnp_sync.restype = ctypes.c_int
     L.nnp_eval_batch.argtypes = [vp, i32, dp, dp, dp, dp, dp, dp]
     L.nnp_eval_batch.restype = ctypes.c_int
+    L.nnp_eval_batch_async.argtypes = [vp, i32, dp, dp, dp, dp, dp, dp]
+    L.nnp_eval_batch_async.restype = ctypes.c_int
     L.nnp_param_count.argtypes = [vp]
     L.nnp_param_count.restype = i64
     L.nnp_force_match_grad.argtypes = [vp, dp, dp, dp, dp]
@@ -298,6 +303,19 @@ class NNP:
         self._check(self._L.nnp_eval_batch(self._h, B, ctypes.c_void_p(off.ctypes.data), pp, pz,
                                            pbx, pE, pF))
         return E, F
+
+    def eval_batch_into(self, offsets, pos, Z, boxes, E_out, F_out, sync: bool = True):
+        """Batch evaluation on device tensors into caller buffers."""
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        bx = np.asarray(boxes, dtype=np.float64)
+        if bx.ndim == 2 and bx.shape[1] == 3:
+            bx = np.stack([np.diag(r) for r in bx])
+        bx = np.ascontiguousarray(bx.reshape(-1, 9))
+        fn = self._L.nnp_eval_batch if sync else self._L.nnp_eval_batch_async
+        self._check(fn(self._h, int(off.shape[0] - 1), ctypes.c_void_p(off.ctypes.data),
+                       ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(Z.data_ptr()),
+                       ctypes.c_void_p(bx.ctypes.data), ctypes.c_void_p(E_out.data_ptr()),
+                       ctypes.c_void_p(F_out.data_ptr())))
 
     def force_match_grad(self, v=None, Fref=None, want_loss: bool = False):
         """dL/dtheta (packed, nnp_param_count doubles) for the last eval."""

@@ -816,20 +816,24 @@ static int warps_grid(long long rows, int warps_per_block, int nsm, int per_sm) 
   return (int)(g < 1 ? 1 : g);
 }
 
+static int g_fwd_per_sm = 8, g_bwd_per_sm = 16;  // set per launch by the callers
+
 template <int S, int ZSQ>
 static void fwd_t(long long rows, int nsm, cudaStream_t st, const SysDesc* sys, const DescParams& P,
                   const Workspace& ws, int bf16) {
-  k_aev_fwd<S, ZSQ><<<warps_grid(rows, 8, nsm, 8), 256, aev_fwd_smem(ws.cap_a), st>>>(sys, P, ws, bf16);
+  k_aev_fwd<S, ZSQ><<<warps_grid(rows, 8, nsm, g_fwd_per_sm), 256, aev_fwd_smem(ws.cap_a), st>>>(sys, P, ws,
+                                                                                                  bf16);
 }
 template <int S, int ZSQ>
 static void bwd_t(long long rows, int nsm, cudaStream_t st, const EvalIO* io, const SysDesc* sys,
                   const DescParams& P, const Workspace& ws) {
-  k_aev_bwd<S, ZSQ><<<warps_grid(rows, 4, nsm, 16), 128, aev_bwd_smem(ws.cap_a, ws.cap_r, P.D), st>>>(
-      io, sys, P, ws);
+  k_aev_bwd<S, ZSQ><<<warps_grid(rows, 4, nsm, g_bwd_per_sm), 128, aev_bwd_smem(ws.cap_a, ws.cap_r, P.D),
+                      st>>>(io, sys, P, ws);
 }
 
 void launch_aev_fwd(long long rows, int nsm, cudaStream_t st, const SysDesc* sys, const DescParams& P,
-                    const Workspace& ws, int bf16) {
+                    const Workspace& ws, int bf16, int per_sm) {
+  g_fwd_per_sm = per_sm > 0 ? per_sm : 8;
   const bool z5 = P.zeta_sq == 5;
   switch (P.S) {
     case 1: z5 ? fwd_t<1, 5>(rows, nsm, st, sys, P, ws, bf16) : fwd_t<1, -1>(rows, nsm, st, sys, P, ws, bf16); break;
@@ -840,7 +844,8 @@ void launch_aev_fwd(long long rows, int nsm, cudaStream_t st, const SysDesc* sys
 }
 
 void launch_aev_bwd(long long rows, int nsm, cudaStream_t st, const EvalIO* io, const SysDesc* sys,
-                    const DescParams& P, const Workspace& ws) {
+                    const DescParams& P, const Workspace& ws, int per_sm) {
+  g_bwd_per_sm = per_sm > 0 ? per_sm : 16;
   const bool z5 = P.zeta_sq == 5;
   switch (P.S) {
     case 1: z5 ? bwd_t<1, 5>(rows, nsm, st, io, sys, P, ws) : bwd_t<1, -1>(rows, nsm, st, io, sys, P, ws); break;

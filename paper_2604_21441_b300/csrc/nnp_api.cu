@@ -157,7 +157,7 @@ int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows)
   const Workspace w = workspace();
   const int nsm = num_sms;
   const int g_atoms = grid_for(n, 256, nsm * 8);
-  const int g_rows = grid_for(rows * 32, 256, nsm * 16);
+  const int g_rows = grid_for(rows * 32, 256, nsm * tune.nbr);
   const int g_bins = grid_for(bins * 32, 256, nsm * 16);
   const EvalIO* io = d_io;
   const SysDesc* sys = b_sys;
@@ -175,7 +175,7 @@ int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows)
   k_neighbors<<<g_rows, 256, neighbors_smem(cap_r), stream>>>(io, sys, P, w); ++launches;
   mark_stage(2, capturing);
   const int bf16 = cfg.precision != NNP_FP32;
-  launch_aev_fwd(rows, nsm, stream, sys, P, w, bf16); ++launches;
+  launch_aev_fwd(rows, nsm, stream, sys, P, w, bf16, tune.fwd); ++launches;
   mark_stage(3, capturing);
   const int g_tiles = (int)std::min<long long>(rows / 64, (long long)nsm);
   if (cfg.precision == NNP_FP32) {
@@ -186,7 +186,7 @@ int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows)
     ++launches;
   }
   mark_stage(4, capturing);
-  launch_aev_bwd(rows, nsm, stream, io, sys, P, w); ++launches;
+  launch_aev_bwd(rows, nsm, stream, io, sys, P, w, tune.bwd); ++launches;
   mark_stage(5, capturing);
   CK(cudaGetLastError());
   launches_per_eval = launches;
@@ -325,6 +325,10 @@ int nnp_ctx::evaluate(int B, const int64_t* offsets, const double* pos, const in
     // device flags accumulate over asynchronous evaluations until nnp_sync reads them;
     // a synchronous evaluation reports only its own
     if (sync) CK(cudaMemsetAsync(b_flags, 0, sizeof(int) * kNumFlags, stream));
+    if ((cfg.flags & NNP_FLAG_AUTOTUNE) && sync) {
+      rc = autotune(n, B, bins, rows);
+      if (rc) return rc;
+    }
     const bool use_graph = !(cfg.flags & NNP_FLAG_NO_GRAPH);
     if (use_graph) {
       if (!gexec || g_key_n != n || g_key_B != B || g_key_bins != bins) {
@@ -536,6 +540,16 @@ int nnp_eval_batch(nnp_ctx* ctx, int32_t B, const int64_t* offsets, const double
   return ctx->evaluate(B, offsets, pos, Z, boxes, energies, forces, true);
 }
 
+int nnp_eval_batch_async(nnp_ctx* ctx, int32_t B, const int64_t* offsets, const double* pos, const int32_t* Z,
+                         const double* boxes, double* energies, double* forces) {
+  if (!ctx) return NNP_ERR_INVALID_ARG;
+  if (B < 1 || !offsets) return ctx->fail(NNP_ERR_INVALID_ARG, "B < 1 or null offsets");
+  if (!boxes) return ctx->fail(NNP_ERR_INVALID_ARG, "nnp_eval_batch_async needs periodic boxes");
+  for (int b = 0; b < B; ++b)
+    if (offsets[b + 1] <= offsets[b]) return ctx->fail(NNP_ERR_INVALID_ARG, "offsets must increase");
+  return ctx->evaluate(B, offsets, pos, Z, boxes, energies, forces, false);
+}
+
 int64_t nnp_param_count(const nnp_ctx* ctx) {
   if (!ctx) return -1;
   const int64_t D = ctx->P.D;
@@ -557,6 +571,9 @@ int nnp_query(nnp_ctx* ctx, int32_t key, int64_t* value) {
     case NNP_Q_MAX_ANG: *value = ctx->max_nbr_a; break;
     case NNP_Q_ROWS: *value = ctx->last_rows; break;
     case NNP_Q_GRAPH_CAPTURES: *value = ctx->graph_captures; break;
+    case NNP_Q_TUNE_NEIGHBOURS: *value = ctx->tune.nbr; break;
+    case NNP_Q_TUNE_DESCRIPTOR: *value = ctx->tune.fwd; break;
+    case NNP_Q_TUNE_BACKWARD: *value = ctx->tune.bwd; break;
     default: return ctx->fail(NNP_ERR_INVALID_ARG, "unknown query key %d", key);
   }
   return NNP_OK;

@@ -20,10 +20,11 @@ cudaError_t neighbors_set_smem_limits();
 
 // k_aev.cu
 // rows: upper bound of the rows of the evaluation (grid sizing only)
+// per_sm: cap on resident blocks per SM of the grid (0 = built-in default)
 void launch_aev_fwd(long long rows, int nsm, cudaStream_t st, const SysDesc* sys, const DescParams& P,
-                    const Workspace& ws, int bf16);
+                    const Workspace& ws, int bf16, int per_sm = 0);
 void launch_aev_bwd(long long rows, int nsm, cudaStream_t st, const EvalIO* io, const SysDesc* sys,
-                    const DescParams& P, const Workspace& ws);
+                    const DescParams& P, const Workspace& ws, int per_sm = 0);
 cudaError_t aev_set_smem_limits();
 
 // k_mlp_f32.cu
@@ -102,6 +103,11 @@ struct nnp_ctx {
   nnp::FmJob* fm_jobs = nullptr;
   size_t fm_cap = 0, fm_cap2 = 0, fm_cap3 = 0, fm_cap4 = 0, fm_vcap = 0, fm_refcap = 0, fm_gcap = 0, fm_jcap = 0;
   static bool is_device(const void* p);
+
+  // launch shape (blocks per SM caps), chosen by the autotuner (NNP_FLAG_AUTOTUNE)
+  struct Tune { int nbr = 16, fwd = 8, bwd = 16; } tune;
+  long long tuned_key = -1;
+  int autotune(long long n, int B, long long bins, long long rows);
 
   // stage events (NNP_FLAG_STAGE_EVENTS)
   cudaEvent_t stage_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
