@@ -204,6 +204,7 @@ def run_ours(args, rank, world, local_rank):
         return ms, stages
 
     forms = {}
+    results = {}
     prec_list = [args.precision] + [p for p in ("fp32", "bf16", "fp8")
                                     if p != args.precision and p in args.compare]
     clocks = ClockSampler(local_rank)
@@ -221,11 +222,27 @@ def run_ours(args, rank, world, local_rank):
         t = float(np.sum(ms)) / 1e3
         forms[prec] = {"value": n * args.steps / t, "ms_per_step": float(np.mean(ms)),
                        "ms_p10": float(np.percentile(ms, 10)), "ms_p90": float(np.percentile(ms, 90))}
+        results[prec] = (E.cpu().numpy().copy(), F.cpu().numpy().copy())
+        if prec == "fp32":
+            ei_abs = float(np.abs(pot.atom_energies(n)).sum())
         if prec == args.precision:
             main = (pot, ms)
         else:
             pot.close()
     clk = clocks.stop()
+    # error of the reduced-precision forms against the FP32 form (which the
+    # parity tests hold to 1e-6 relative energy and 1e-4 eV/A of the FP64 oracle)
+    if "fp32" in results:
+        E32, F32 = results["fp32"]
+        for prec, (Eq, Fq) in results.items():
+            if prec != "fp32":
+                dF = Fq - F32
+                forms[prec]["vs_fp32"] = {
+                    "max_abs_dF_eV_per_A": float(np.abs(dF).max()),
+                    "rms_dF_eV_per_A": float(np.sqrt((dF ** 2).mean())),
+                    "rms_F_eV_per_A": float(np.sqrt((F32 ** 2).mean())),
+                    # |sum dE| / max(|E|, sum_i |E_i|), the normalisation of the FP32 parity bound
+                    "rel_dE": float(abs(Eq.sum() - E32.sum()) / max(abs(E32.sum()), ei_abs))}
     pot, ms = main
     # per-stage durations (instrumented graph, same protocol)
     spot = make(args.precision, flags=P.FLAG_STAGE_EVENTS)
@@ -446,7 +463,8 @@ def profiled_traffic(stage, precision):
     record (profiles/ncu_traffic.json), or None if that kernel's source file
     changed since the capture."""
     import hashlib
-    kernel = STAGE_KERNEL.get(stage) or ("k_mlp_f32" if precision == "fp32" else "k_mlp_bf16")
+    kernel = STAGE_KERNEL.get(stage) or ("k_mlp_f32" if precision == "fp32" else
+                                              "k_mlp_tc" if precision == "bf16" else "k_mlp_tc_fp8")
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             rec = json.load(f).get(kernel)

@@ -56,7 +56,14 @@ typedef enum {
 typedef enum {
     NNP_FP32 = 0, /* FP32 descriptors and FP32 SIMT network (reference form) */
     NNP_BF16 = 1, /* FP32 descriptors, network on tcgen05 tensor cores in BF16 */
-    NNP_FP8 = 2   /* as BF16, forward layers in FP8 E4M3 with per-layer scales */
+    NNP_FP8 = 2   /* as BF16, but the three forward GEMMs in FP8 E4M3 with one static
+                     scale per layer and species for activations and one per output
+                     column for weights: s_W[n] = max_k |W[k][n]| / 448 at
+                     nnp_set_weights; activations s_x = max|x| / 448 from an FP32
+                     calibration pass over the first evaluation's input (and again
+                     after new weights, or while a species has not been seen).  The
+                     calibration pass makes that evaluation synchronous.  The backward
+                     stays BF16.  Two species (D = 128) only. */
 } nnp_precision;
 
 #define NNP_MAX_SPECIES 8
@@ -132,7 +139,9 @@ const char *nnp_last_error(const nnp_ctx *ctx);
  * (fan_in x fan_out) FP32: W[0] D x h1, W[1] h1 x h2, W[2] h2 x h3,
  * W[3] h3 x 1; b[l] has fan_out entries.  Host or device pointers; the data
  * are copied (and rounded to BF16/FP8 for those precisions), the caller keeps
- * ownership.  Captured graphs stay valid (weights live in fixed buffers). */
+ * ownership.  Captured graphs stay valid (weights live in fixed buffers).
+ * FP8: also resets the activation scales of every species (recalibrated at the
+ * next evaluation). */
 int nnp_set_weights(nnp_ctx *ctx, int32_t species, const float *const W[4],
                     const float *const b[4]);
 
@@ -234,7 +243,8 @@ typedef enum {
     NNP_Q_GRAPH_CAPTURES = 6,     /* CUDA graphs captured so far */
     NNP_Q_TUNE_NEIGHBOURS = 7,    /* blocks-per-SM cap of the neighbour kernel */
     NNP_Q_TUNE_DESCRIPTOR = 8,    /* ... of the descriptor kernel */
-    NNP_Q_TUNE_BACKWARD = 9       /* ... of the descriptor-backward kernel */
+    NNP_Q_TUNE_BACKWARD = 9,      /* ... of the descriptor-backward kernel */
+    NNP_Q_FP8_CALIBRATED = 10     /* 1 once every species' FP8 activation scales are set */
 } nnp_query_key;
 
 int nnp_query(nnp_ctx *ctx, int32_t key, int64_t *value);

@@ -192,7 +192,7 @@ __device__ __forceinline__ void load_counts(const Workspace& ws, int S, int row,
 
 template <int S, int ZSQ>
 __global__ void __launch_bounds__(256) k_aev_fwd(const SysDesc* __restrict__ sys, DescParams P,
-                                                 Workspace ws, int write_bf16) {
+                                                 Workspace ws, int mode) {
   constexpr int D = kNRad * S + kNAng * S * (S + 1) / 2;
   extern __shared__ float4 sm4[];
   const int lane = threadIdx.x & 31, hl = lane & 15, half = lane >> 4;
@@ -213,18 +213,31 @@ __global__ void __launch_bounds__(256) k_aev_fwd(const SysDesc* __restrict__ sys
     const int row = 2 * pr + half;
     const bool inrow = row < rows;
     const bool live = inrow && ws.row_atom[row] >= 0;
-    // FP32 form: row-major G; tensor-core forms: the swizzled BF16 tile copy only
+    // FP32 form: row-major G; tensor-core forms: only the swizzled BF16 or
+    // FP8 tile copy (FP8: G / s_G with the species' calibrated step s_G)
     float* Grow = ws.G + (size_t)row * D;
     char* Gh = reinterpret_cast<char*>(ws.Gh);
+    float q = 1.f;
+    auto put1 = [&](int f, float v) {
+      if (mode == kGFp32) Grow[f] = v;
+      else if (mode == kGBf16) *reinterpret_cast<__nv_bfloat16*>(Gh + gh_offset(row, f, D)) = __float2bfloat16(v);
+      else Gh[gh8_offset(row, f, D)] = (char)__nv_cvt_float_to_fp8(v * q, __NV_SATFINITE, __NV_E4M3);
+    };
+    auto put2 = [&](int f, float v0, float v1) {  // f even
+      if (mode == kGFp32) *reinterpret_cast<float2*>(Grow + f) = make_float2(v0, v1);
+      else if (mode == kGBf16)
+        *reinterpret_cast<__nv_bfloat162*>(Gh + gh_offset(row, f, D)) = __floats2bfloat162_rn(v0, v1);
+      else
+        *reinterpret_cast<__nv_fp8x2_storage_t*>(Gh + gh8_offset(row, f, D)) =
+            __nv_cvt_float2_to_fp8x2(make_float2(v0 * q, v1 * q), __NV_SATFINITE, __NV_E4M3);
+    };
     if (inrow && !live) {  // padding row: zero descriptor
-      for (int f = hl; f < D; f += 16) {
-        if (write_bf16) *reinterpret_cast<__nv_bfloat16*>(Gh + gh_offset(row, f, D)) = __float2bfloat16(0.f);
-        else Grow[f] = 0.f;
-      }
+      for (int f = hl; f < D; f += 16) put1(f, 0.f);
     }
     float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
     if (live) {
       pi = ws.pos4[row];
+      if (mode == kGFp8) q = 1.f / fp8_step(ws.q8[8 * pos4_species(pi)]);
       const int sid = ws.row_info[row];
       if (sid != cached_sys) {
         const SysDesc& sd = sys[sid];
@@ -264,11 +277,7 @@ __global__ void __launch_bounds__(256) k_aev_fwd(const SysDesc* __restrict__ sys
         }
       }
       hw_reduce_scatter<kNRad>(acc, hl);
-      if (live) {
-        if (write_bf16)
-          *reinterpret_cast<__nv_bfloat16*>(Gh + gh_offset(row, s * kNRad + hl, D)) = __float2bfloat16(acc[0]);
-        else Grow[s * kNRad + hl] = acc[0];
-      }
+      if (live) put1(s * kNRad + hl, acc[0]);
     }
 
     // ---------------- angular: stage the neighbours inside rc_a
@@ -300,11 +309,7 @@ __global__ void __launch_bounds__(256) k_aev_fwd(const SysDesc* __restrict__ sys
         const int Tmax = max(T, __shfl_xor_sync(0xffffffffu, T, 16));
         const int f0 = kNRad * S + pair_block(S, s1, s2) * kNAng + 2 * hl;
         if (Tmax == 0) {
-          if (live) {
-            if (write_bf16)
-              *reinterpret_cast<__nv_bfloat162*>(Gh + gh_offset(row, f0, D)) = __floats2bfloat162_rn(0.f, 0.f);
-            else *reinterpret_cast<float2*>(Grow + f0) = make_float2(0.f, 0.f);
-          }
+          if (live) put2(f0, 0.f, 0.f);
           continue;
         }
         const PairMap pm = make_map(diag, n1, n2, rc->oa[s1], rc->oa[s2]);
@@ -338,12 +343,7 @@ __global__ void __launch_bounds__(256) k_aev_fwd(const SysDesc* __restrict__ sys
           }
         }
         hw_reduce_scatter<kNAng>(acc, hl);
-        if (live) {
-          if (write_bf16)
-            *reinterpret_cast<__nv_bfloat162*>(Gh + gh_offset(row, f0, D)) =
-                __floats2bfloat162_rn(2.f * acc[0], 2.f * acc[1]);
-          else *reinterpret_cast<float2*>(Grow + f0) = make_float2(2.f * acc[0], 2.f * acc[1]);
-        }
+        if (live) put2(f0, 2.f * acc[0], 2.f * acc[1]);
       }
     }
     __syncwarp();
@@ -820,9 +820,9 @@ static int g_fwd_per_sm = 8, g_bwd_per_sm = 16;  // set per launch by the caller
 
 template <int S, int ZSQ>
 static void fwd_t(long long rows, int nsm, cudaStream_t st, const SysDesc* sys, const DescParams& P,
-                  const Workspace& ws, int bf16) {
+                  const Workspace& ws, int mode) {
   k_aev_fwd<S, ZSQ><<<warps_grid(rows, 8, nsm, g_fwd_per_sm), 256, aev_fwd_smem(ws.cap_a), st>>>(sys, P, ws,
-                                                                                                  bf16);
+                                                                                                  mode);
 }
 template <int S, int ZSQ>
 static void bwd_t(long long rows, int nsm, cudaStream_t st, const EvalIO* io, const SysDesc* sys,
@@ -832,14 +832,14 @@ static void bwd_t(long long rows, int nsm, cudaStream_t st, const EvalIO* io, co
 }
 
 void launch_aev_fwd(long long rows, int nsm, cudaStream_t st, const SysDesc* sys, const DescParams& P,
-                    const Workspace& ws, int bf16, int per_sm) {
+                    const Workspace& ws, int mode, int per_sm) {
   g_fwd_per_sm = per_sm > 0 ? per_sm : 8;
   const bool z5 = P.zeta_sq == 5;
   switch (P.S) {
-    case 1: z5 ? fwd_t<1, 5>(rows, nsm, st, sys, P, ws, bf16) : fwd_t<1, -1>(rows, nsm, st, sys, P, ws, bf16); break;
-    case 2: z5 ? fwd_t<2, 5>(rows, nsm, st, sys, P, ws, bf16) : fwd_t<2, -1>(rows, nsm, st, sys, P, ws, bf16); break;
-    case 3: z5 ? fwd_t<3, 5>(rows, nsm, st, sys, P, ws, bf16) : fwd_t<3, -1>(rows, nsm, st, sys, P, ws, bf16); break;
-    default: z5 ? fwd_t<4, 5>(rows, nsm, st, sys, P, ws, bf16) : fwd_t<4, -1>(rows, nsm, st, sys, P, ws, bf16); break;
+    case 1: z5 ? fwd_t<1, 5>(rows, nsm, st, sys, P, ws, mode) : fwd_t<1, -1>(rows, nsm, st, sys, P, ws, mode); break;
+    case 2: z5 ? fwd_t<2, 5>(rows, nsm, st, sys, P, ws, mode) : fwd_t<2, -1>(rows, nsm, st, sys, P, ws, mode); break;
+    case 3: z5 ? fwd_t<3, 5>(rows, nsm, st, sys, P, ws, mode) : fwd_t<3, -1>(rows, nsm, st, sys, P, ws, mode); break;
+    default: z5 ? fwd_t<4, 5>(rows, nsm, st, sys, P, ws, mode) : fwd_t<4, -1>(rows, nsm, st, sys, P, ws, mode); break;
   }
 }
 

@@ -1,5 +1,5 @@
 // k_mlp_tc.cu -- per-element network on the 5th-generation tensor cores
-// (tcgen05.mma, BF16 operands, FP32 accumulators in tensor memory), fused:
+// (tcgen05.mma, BF16 or FP8 operands, FP32 accumulators in tensor memory), fused:
 // forward D -> 160 -> 128 -> 96 -> 1 with CELU, atom energies and their FP64
 // sum per system, and the backward pass to dE_i/dG_i (chain rule of Eq. 2):
 //
@@ -23,6 +23,14 @@
 // pre-activations kept in TMEM, so the backward does not lose precision to
 // the BF16 activations.
 //
+// FP8 form: the three forward GEMMs take E4M3 operands (kind::f8f6f4, twice
+// the BF16 rate) with static scales: activations x_q = x / s_x with one s_x
+// per layer and species from a calibration pass of the FP32 form over the
+// first input; weights W_q[., n] = W[., n] / s_W[n] with one scale per output
+// column, s_W[n] = max_k |W[k, n]| / 448.  The accumulator of column n is
+// rescaled by s_x s_W[n] in the epilogue, before the bias.  The backward
+// GEMMs stay BF16; CELU' comes from the FP8 forward's z.
+//
 // Every wait on an mbarrier is bounded; on timeout the kernel raises the
 // timeout flag, stops issuing work, waits (bounded) for its own copies and
 // MMAs, frees its tensor memory and returns.
@@ -43,6 +51,9 @@ constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any wait
 
 __host__ __device__ constexpr int slabs_of(int K) { return (K + 63) / 64; }
 __host__ __device__ constexpr int mat_bytes(int N, int K) { return slabs_of(K) * N * 128; }
+// FP8 operands: 128 one-byte K columns per slab
+__host__ __device__ constexpr int slabs8_of(int K) { return (K + 127) / 128; }
+__host__ __device__ constexpr int mat8_bytes(int N, int K) { return slabs8_of(K) * N * 128; }
 
 // ---- PTX wrappers ---------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -110,6 +121,14 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
       : "memory");
 }
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    smem_u32(bar))
@@ -141,15 +160,25 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// D[128 x N] (+)= A[128 x K] B[N x K]^T, K in steps of 16 (one MMA each).
-__device__ __forceinline__ void issue_gemm(uint32_t d_tmem, const uint8_t* A, const uint8_t* B, int N,
-                                           int K, bool accumulate_first) {
-  const uint32_t idesc = idesc_bf16(kTM, N);
+// kind::f8f6f4 instruction descriptor: FP32 accumulate, E4M3 A and B (format
+// code 0 in both fields), both K-major.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D[128 x N] = A[128 x K] B[N x K]^T.  One MMA covers 32 bytes of K (16 BF16
+// or 32 E4M3 values), so both types advance 32 bytes per MMA inside a
+// 128-byte swizzle row and one slab per four MMAs.
+template <bool F8>
+__device__ __forceinline__ void issue_gemm(uint32_t d_tmem, const uint8_t* A, const uint8_t* B, int N, int K) {
+  const uint32_t idesc = F8 ? idesc_e4m3(kTM, N) : idesc_bf16(kTM, N);
   const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
-  for (int k = 0; k < K / 16; ++k) {
+  const int nk = K / (F8 ? 32 : 16);
+  for (int k = 0; k < nk; ++k) {
     const uint32_t a = a0 + (uint32_t)(k >> 2) * kSlab + (uint32_t)(k & 3) * 32;
     const uint32_t b = b0 + (uint32_t)(k >> 2) * (uint32_t)(N * 128) + (uint32_t)(k & 3) * 32;
-    mma_bf16(d_tmem, sw128_desc(a), sw128_desc(b), idesc, (k > 0 || accumulate_first) ? 1u : 0u);
+    if (F8) mma_e4m3(d_tmem, sw128_desc(a), sw128_desc(b), idesc, k > 0 ? 1u : 0u);
+    else mma_bf16(d_tmem, sw128_desc(a), sw128_desc(b), idesc, k > 0 ? 1u : 0u);
   }
 }
 
@@ -178,13 +207,30 @@ __device__ __forceinline__ void store_row16(uint8_t* buf, int r, int c0, const f
   }
 }
 
+// Store 16 values of row r, columns [c0, c0+16), times q as E4M3 (one 16-byte chunk).
+__device__ __forceinline__ void store_row16_e4m3(uint8_t* buf, int r, int c0, const float (&v)[16], float q) {
+  uint32_t w[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v[4 * i] * q, v[4 * i + 1] * q), __NV_SATFINITE,
+                                                 __NV_E4M3);
+    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v[4 * i + 2] * q, v[4 * i + 3] * q),
+                                                 __NV_SATFINITE, __NV_E4M3);
+    w[i] = lo | (hi << 16);
+  }
+  const int ch = c0 >> 4;  // 16-byte chunk index along K
+  uint8_t* dst = buf + (ch >> 3) * kSlab + r * 128 + (((ch & 7) ^ (r & 7)) << 4);
+  *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
 }  // namespace
 
-// Pre-swizzled BF16 weights per species: forward W1^T (160 x D), W2^T
+// Pre-swizzled weights per species: forward W1^T (160 x D), W2^T
 // (128 x 160), W3^T (96 x 128); backward W3 (128 x 96), W2 (160 x 128),
 // W1 (D x 160); each [N rows x K cols], K-major.
 struct MlpTcWeights {
   const uint8_t* m[kMaxS][6];
+  const float* wsc[kMaxS];  // FP8: per-output-column scales s_W[n] of W1, W2, W3 (160 + 128 + 96)
 };
 
 // Per-system energy sums of one warp's 32 rows: rows of a system are
@@ -257,15 +303,15 @@ __device__ __forceinline__ void for_chunks2(uint32_t tcol, uint32_t tcol2, int h
   }
 }
 
-template <int D>
-__global__ void __launch_bounds__(256, 1) k_mlp_bf16(const EvalIO* __restrict__ io, DescParams P,
-                                                    Workspace ws, MlpTcWeights Wt, MlpF32Weights Wf) {
+template <int D, bool F8>
+__global__ void __launch_bounds__(256, 1) k_mlp_tc(const EvalIO* __restrict__ io, DescParams P,
+                                                  Workspace ws, MlpTcWeights Wt, MlpF32Weights Wf) {
   constexpr int kBufA = slabs_of(D > kH2 ? D : kH2) * kSlab;  // G, later g2
   constexpr int kBufB = slabs_of(kH1) * kSlab;                // h1, later g1
   constexpr int kBufC = slabs_of(kH2) * kSlab;                // h2, later g3
   constexpr int kWBuf = 48 * 1024;
   static_assert(mat_bytes(kH1, D) <= kWBuf && mat_bytes(D, kH1) <= kWBuf, "weight buffer");
-  static_assert(D % 16 == 0, "D must be a multiple of 16");
+  static_assert(D % (F8 ? 32 : 16) == 0, "D must be a multiple of one MMA's K");
   constexpr int NW[6] = {kH1, kH2, kH3, kH2, kH1, D};  // N of the six GEMMs
   constexpr int KW[6] = {D, kH1, kH2, kH3, kH2, kH1};  // K of the six GEMMs
   constexpr int kNB = kH1 + kH2 + kH3 + kH3 + 1;       // b1 b2 b3 w4 b4
@@ -286,6 +332,10 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bf16(const EvalIO* __restrict__ 
   float* sb3 = sb2 + kH2;
   float* sw4 = sb3 + kH3;
   float* sb4 = sw4 + kH3;
+  float* ssc = sb + kNB;     // FP8: [kH1 + kH2 + kH3] per-column dequantisation s_x s_W[n]
+  float* ssc1 = ssc;
+  float* ssc2 = ssc1 + kH1;
+  float* ssc3 = ssc2 + kH2;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int quarter = warp & 3, h = warp >> 2;  // TMEM lane quarter; column half
@@ -318,13 +368,13 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bf16(const EvalIO* __restrict__ 
   bool pend[4] = {false, false, false, false};
 
   auto load_w = [&](int sp, int which, int b) {
-    const int bytes = mat_bytes(NW[which], KW[which]);
+    const int bytes = (F8 && which < 3) ? mat8_bytes(NW[which], KW[which]) : mat_bytes(NW[which], KW[which]);
     mbar_expect_tx(&bars[b], (uint32_t)bytes);
     bulk_g2s(wbuf[b], Wt.m[sp][which], (uint32_t)bytes, &bars[b]);
     pend[b] = true;
   };
   auto load_tile = [&](int t) {
-    const uint32_t bytes = (uint32_t)gh_tile_bytes(D);
+    const uint32_t bytes = (uint32_t)(F8 ? gh8_tile_bytes(D) : gh_tile_bytes(D));
     mbar_expect_tx(&bars[2], bytes);
     bulk_g2s(bufA, reinterpret_cast<const uint8_t*>(ws.Gh) + (size_t)t * bytes, bytes, &bars[2]);
     pend[2] = true;
@@ -364,6 +414,16 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bf16(const EvalIO* __restrict__ 
     const int row = row0 + r;
     const int my_atom = ws.row_atom[row];  // consumed by the energy epilogue
     const int my_sys = ws.row_info[row];
+    // FP8: z_l[n] = acc_l[n] * s_x s_W[n] + b_l[n]; q_l = 1 / s_{h_l} quantises h_l
+    float q1 = 1.f, q2 = 1.f;
+    if (F8) {
+      const int* qs = ws.q8 + 8 * sp;
+      const float sx0 = fp8_step(qs[0]), sx1 = fp8_step(qs[1]), sx2 = fp8_step(qs[2]);
+      q1 = 1.f / sx1;
+      q2 = 1.f / sx2;
+      for (int i = tid; i < kH1 + kH2 + kH3; i += blockDim.x)
+        ssc[i] = Wt.wsc[sp][i] * (i < kH1 ? sx0 : (i < kH1 + kH2 ? sx1 : sx2));
+    }
     for (int i = tid; i < kNB; i += blockDim.x) {
       float v;
       if (i < kH1) v = Wf.b[sp][0][i];
@@ -379,15 +439,16 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bf16(const EvalIO* __restrict__ 
     if (tid == 0) {
       load_w(sp, 1, 1);                              // W2^T -> wbuf[1]
       tc_fence_after();
-      issue_gemm(mz1, bufA, wbuf[0], kH1, D, false);
+      issue_gemm<F8>(mz1, bufA, wbuf[0], kH1, D);
       commit();
     }
     if (!sync_wait(3)) break;
     tc_fence_after();
     for_chunks<kH1>(tz1, h, [&](int c0, float (&v)[16]) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = celu_f(v[j] + sb1[c0 + j], al, kexp);
-      store_row16(bufB, r, c0, v);
+      for (int j = 0; j < 16; ++j) v[j] = celu_f(fmaf(v[j], F8 ? ssc1[c0 + j] : 1.f, sb1[c0 + j]), al, kexp);
+      if (F8) store_row16_e4m3(bufB, r, c0, v, q1);
+      else store_row16(bufB, r, c0, v);
     });
     end_epilogue();
     // ---------------- layer 2: z2 = h1 W2
@@ -395,15 +456,16 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bf16(const EvalIO* __restrict__ 
     if (tid == 0) {
       load_w(sp, 2, 0);                              // W3^T -> wbuf[0]
       tc_fence_after();
-      issue_gemm(mz2, bufB, wbuf[1], kH2, kH1, false);
+      issue_gemm<F8>(mz2, bufB, wbuf[1], kH2, kH1);
       commit();
     }
     if (!sync_wait(3)) break;
     tc_fence_after();
     for_chunks<kH2>(tz2, h, [&](int c0, float (&v)[16]) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = celu_f(v[j] + sb2[c0 + j], al, kexp);
-      store_row16(bufC, r, c0, v);
+      for (int j = 0; j < 16; ++j) v[j] = celu_f(fmaf(v[j], F8 ? ssc2[c0 + j] : 1.f, sb2[c0 + j]), al, kexp);
+      if (F8) store_row16_e4m3(bufC, r, c0, v, q2);
+      else store_row16(bufC, r, c0, v);
     });
     end_epilogue();
     // ---------------- layer 3: z3 = h2 W3; energy and g3 = w4 CELU'(z3)
@@ -411,7 +473,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bf16(const EvalIO* __restrict__ 
     if (tid == 0) {
       load_w(sp, 3, 1);                              // W3 (backward) -> wbuf[1]
       tc_fence_after();
-      issue_gemm(mz3, bufC, wbuf[0], kH3, kH2, false);
+      issue_gemm<F8>(mz3, bufC, wbuf[0], kH3, kH2);
       commit();
     }
     if (!sync_wait(3)) break;
@@ -421,7 +483,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bf16(const EvalIO* __restrict__ 
       for_chunks<kH3>(tz3, h, [&](int c0, float (&v)[16]) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const float z = v[j] + sb3[c0 + j];
+          const float z = fmaf(v[j], F8 ? ssc3[c0 + j] : 1.f, sb3[c0 + j]);
           const float ww = sw4[c0 + j];
           e = fmaf(celu_f(z, al, kexp), ww, e);
           v[j] = ww * dcelu_f(z, kexp);
@@ -442,14 +504,14 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bf16(const EvalIO* __restrict__ 
     if (tid == 0) {
       load_w(sp, 4, 0);                              // W2 (backward) -> wbuf[0]
       tc_fence_after();
-      issue_gemm(mg2, bufC, wbuf[1], kH2, kH3, false);
+      issue_gemm<false>(mg2, bufC, wbuf[1], kH2, kH3);
       commit();
     }
     if (!sync_wait(3)) break;
     tc_fence_after();
     for_chunks2<kH2>(tg2, tz2, h, [&](int c0, float (&g)[16], float (&z)[16]) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) g[j] *= dcelu_f(z[j] + sb2[c0 + j], kexp);
+      for (int j = 0; j < 16; ++j) g[j] *= dcelu_f(fmaf(z[j], F8 ? ssc2[c0 + j] : 1.f, sb2[c0 + j]), kexp);
       store_row16(bufA, r, c0, g);  // the G tile is no longer needed
     });
     end_epilogue();
@@ -458,14 +520,14 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bf16(const EvalIO* __restrict__ 
     if (tid == 0) {
       load_w(sp, 5, 1);                              // W1 (backward) -> wbuf[1]
       tc_fence_after();
-      issue_gemm(mg1, bufA, wbuf[0], kH1, kH2, false);
+      issue_gemm<false>(mg1, bufA, wbuf[0], kH1, kH2);
       commit();
     }
     if (!sync_wait(3)) break;
     tc_fence_after();
     for_chunks2<kH1>(tg1, tz1, h, [&](int c0, float (&g)[16], float (&z)[16]) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) g[j] *= dcelu_f(z[j] + sb1[c0 + j], kexp);
+      for (int j = 0; j < 16; ++j) g[j] *= dcelu_f(fmaf(z[j], F8 ? ssc1[c0 + j] : 1.f, sb1[c0 + j]), kexp);
       store_row16(bufB, r, c0, g);
     });
     end_epilogue();
@@ -474,7 +536,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bf16(const EvalIO* __restrict__ 
     const int next = tile + gridDim.x;
     if (tid == 0) {
       tc_fence_after();
-      issue_gemm(mdg, bufB, wbuf[1], D, kH1, false);
+      issue_gemm<false>(mdg, bufB, wbuf[1], D, kH1);
       commit();
       if (next < ntiles) {  // bufA and wbuf[0] are free: prefetch the next tile
         load_tile(next);
@@ -506,67 +568,165 @@ __global__ void __launch_bounds__(256, 1) k_mlp_bf16(const EvalIO* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
+// FP8 calibration: one warp per row runs the FP32 forward of layers 1-2 from
+// the FP32 descriptor and raises the species' |max| of G, h1 and h2 (float
+// bits, non-negative, so integer atomicMax orders them).  Rows are species
+// sorted, so a warp flushes its running maxima only when the species changes.
+__global__ void __launch_bounds__(256) k_fp8_calib(DescParams P, Workspace ws, MlpF32Weights Wf) {
+  __shared__ float xs[8][kH1], ys[8][kH1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int D = P.D, rows = ws.seg[P.S];
+  const float al = P.celu_alpha, inv_al = 1.f / P.celu_alpha;
+  float* x = xs[warp];
+  float* y = ys[warp];
+  int cur = -1;
+  float m[3] = {0.f, 0.f, 0.f};
+  auto flush = [&]() {
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      float v = m[l];
+      for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if (lane == 0 && cur >= 0) atomicMax(&ws.q8[8 * cur + l], __float_as_int(v));
+      m[l] = 0.f;
+    }
+  };
+  for (int row = blockIdx.x * 8 + warp; row < rows; row += gridDim.x * 8) {
+    if (ws.row_atom[row] < 0) continue;  // padding (warp-uniform)
+    const int sp = pos4_species(ws.pos4[row]);
+    if (sp != cur) {
+      flush();
+      cur = sp;
+    }
+    const float* g = ws.G + (size_t)row * D;
+    __syncwarp();
+    for (int k = lane; k < D; k += 32) {
+      x[k] = g[k];
+      m[0] = fmaxf(m[0], fabsf(g[k]));
+    }
+    __syncwarp();
+    for (int j = lane; j < kH1; j += 32) {
+      float z = Wf.b[sp][0][j];
+      for (int k = 0; k < D; ++k) z = fmaf(x[k], Wf.W[sp][0][(size_t)k * kH1 + j], z);
+      const float h = z > 0.f ? z : al * (expf(z * inv_al) - 1.f);
+      y[j] = h;
+      m[1] = fmaxf(m[1], fabsf(h));
+    }
+    __syncwarp();
+    for (int j = lane; j < kH2; j += 32) {
+      float z = Wf.b[sp][1][j];
+      for (int k = 0; k < kH1; ++k) z = fmaf(y[k], Wf.W[sp][1][(size_t)k * kH2 + j], z);
+      const float h = z > 0.f ? z : al * (expf(z * inv_al) - 1.f);
+      m[2] = fmaxf(m[2], fabsf(h));
+    }
+  }
+  flush();
+}
+
+// ---------------------------------------------------------------------------
 // host side
 
 namespace {
 
 struct TcState {
-  uint8_t* blob = nullptr;   // pre-swizzled BF16 weights, all species
+  bool f8 = false;
+  uint8_t* blob = nullptr;   // pre-swizzled weights, all species
+  float* wsc = nullptr;      // FP8 per-column weight scales, all species
   size_t per_species = 0;
   size_t off[6] = {0, 0, 0, 0, 0, 0};
   MlpTcWeights w{};
 };
 
-// Swizzled K-major image of a logical [N][K] matrix (value(n, k)).
+// Byte offset of element (n, k) of a swizzled K-major [N][K] image with
+// elements of esize bytes (2: BF16, 64 per slab row; 1: E4M3, 128).
+inline size_t swz_off(int N, int n, int k, int esize) {
+  const int per = 128 / esize;  // elements per 128-byte row of a slab
+  const int slab = k / per, kk = k % per, ch = kk * esize / 16, e = kk * esize % 16;
+  return (size_t)slab * N * 128 + (size_t)n * 128 + (size_t)((ch ^ (n & 7)) << 4) + e;
+}
+
+// BF16 image of a logical [N][K] matrix (value(n, k)).
 template <class F>
 void swizzle_into(uint8_t* dst, int N, int K, F value) {
   memset(dst, 0, (size_t)mat_bytes(N, K));
   for (int n = 0; n < N; ++n)
     for (int k = 0; k < K; ++k) {
-      const int slab = k / 64, ch = (k % 64) / 8, e = k % 8;
-      const size_t off = (size_t)slab * N * 128 + (size_t)n * 128 + (size_t)((ch ^ (n & 7)) << 4) + e * 2;
       __nv_bfloat16 h = __float2bfloat16(value(n, k));
-      memcpy(dst + off, &h, 2);
+      memcpy(dst + swz_off(N, n, k, 2), &h, 2);
     }
+}
+
+// E4M3 image of value(n, k) / s[n] with one scale per output column n,
+// s[n] = max_k |value(n, k)| / 448 (1 for an all-zero column).
+template <class F>
+void swizzle_e4m3_into(uint8_t* dst, float* s, int N, int K, F value) {
+  memset(dst, 0, (size_t)mat8_bytes(N, K));
+  for (int n = 0; n < N; ++n) {
+    float amax = 0.f;
+    for (int k = 0; k < K; ++k) amax = std::max(amax, std::fabs(value(n, k)));
+    s[n] = amax > 0.f ? amax / kE4M3Max : 1.f;
+    for (int k = 0; k < K; ++k)
+      dst[swz_off(N, n, k, 1)] = (uint8_t)__nv_cvt_float_to_fp8(value(n, k) / s[n], __NV_SATFINITE, __NV_E4M3);
+  }
 }
 
 size_t smem_bytes(int D) {
   const int a = slabs_of(D > kH2 ? D : kH2) * kSlab, b = slabs_of(kH1) * kSlab, c = slabs_of(kH2) * kSlab;
   return 1024 + (size_t)a + b + c + 2 * 48 * 1024 + 4 * 8 + 8 + 4 * kTM * 4 +
-         (kH1 + kH2 + 2 * kH3 + 1) * 4 + 64;
+         (kH1 + kH2 + 2 * kH3 + 1) * 4 + (kH1 + kH2 + kH3) * 4 + 64;
+}
+
+template <int D, bool F8>
+cudaError_t set_smem(size_t sm) {
+  return cudaFuncSetAttribute(k_mlp_tc<D, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
 }
 
 }  // namespace
 
 int mlp_tc_init(nnp_ctx* ctx) {
-  if (ctx->cfg.precision != NNP_BF16)
-    return ctx->fail(NNP_ERR_UNSUPPORTED, "only the BF16 tensor-core form is built so far");
+  const bool f8 = ctx->cfg.precision == NNP_FP8;
   const int D = ctx->P.D;
-  if (D != 128 && D != 48)
-    return ctx->fail(NNP_ERR_UNSUPPORTED, "the tensor-core network supports 1 or 2 species (D = 48, 128)");
+  if (!f8 && D != 128 && D != 48)
+    return ctx->fail(NNP_ERR_UNSUPPORTED, "the BF16 tensor-core network supports 1 or 2 species (D = 48, 128)");
+  if (f8 && D != 128)
+    return ctx->fail(NNP_ERR_UNSUPPORTED, "the FP8 tensor-core network supports 2 species (D = 128)");
   TcState* st = new TcState();
+  st->f8 = f8;
   const int NW[6] = {kH1, kH2, kH3, kH2, kH1, D};
   const int KW[6] = {D, kH1, kH2, kH3, kH2, kH1};
   size_t o = 0;
   for (int i = 0; i < 6; ++i) {
     st->off[i] = o;
-    o += (size_t)mat_bytes(NW[i], KW[i]);
+    o += (size_t)((f8 && i < 3) ? mat8_bytes(NW[i], KW[i]) : mat_bytes(NW[i], KW[i]));
     o = (o + 1023) / 1024 * 1024;
   }
   st->per_species = o;
+  ctx->tc = st;
   cudaError_t e = cudaMalloc(&st->blob, o * ctx->P.S);
   if (e != cudaSuccess) {
-    delete st;
+    st->blob = nullptr;
     return ctx->cuda_fail(e, "cudaMalloc tensor-core weights");
   }
   cudaMemset(st->blob, 0, o * ctx->P.S);
   for (int s = 0; s < ctx->P.S; ++s)
     for (int i = 0; i < 6; ++i) st->w.m[s][i] = st->blob + o * s + st->off[i];
-  ctx->tc = st;
+  if (f8) {
+    e = cudaMalloc(&st->wsc, sizeof(float) * (kH1 + kH2 + kH3) * ctx->P.S);
+    if (e != cudaSuccess) {
+      st->wsc = nullptr;
+      return ctx->cuda_fail(e, "cudaMalloc FP8 weight scales");
+    }
+    for (int s = 0; s < ctx->P.S; ++s) st->w.wsc[s] = st->wsc + (size_t)(kH1 + kH2 + kH3) * s;
+  }
+  e = cudaMalloc(&ctx->b_q8, sizeof(int) * 8 * kMaxS);
+  if (e != cudaSuccess) {
+    ctx->b_q8 = nullptr;
+    return ctx->cuda_fail(e, "cudaMalloc FP8 scales");
+  }
+  cudaMemset(ctx->b_q8, 0, sizeof(int) * 8 * kMaxS);
   const size_t sm = smem_bytes(D);
-  e = (D == 128) ? cudaFuncSetAttribute(k_mlp_bf16<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
-                 : cudaFuncSetAttribute(k_mlp_bf16<48>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaFuncSetAttribute(k_mlp_bf16)");
+  if (f8) e = set_smem<128, true>(sm);
+  else e = (D == 128) ? set_smem<128, false>(sm) : set_smem<48, false>(sm);
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaFuncSetAttribute(k_mlp_tc)");
   return NNP_OK;
 }
 
@@ -579,23 +739,43 @@ int mlp_tc_set_weights(nnp_ctx* ctx, int s, const float* hb) {
   const float* W2 = W1 + (size_t)D * kH1 + kH1;
   const float* W3 = W2 + (size_t)kH1 * kH2 + kH2;
   std::vector<uint8_t> img(st->per_species, 0);
-  swizzle_into(img.data() + st->off[0], kH1, D, [&](int n, int k) { return W1[(size_t)k * kH1 + n]; });
-  swizzle_into(img.data() + st->off[1], kH2, kH1, [&](int n, int k) { return W2[(size_t)k * kH2 + n]; });
-  swizzle_into(img.data() + st->off[2], kH3, kH2, [&](int n, int k) { return W3[(size_t)k * kH3 + n]; });
+  auto w1t = [&](int n, int k) { return W1[(size_t)k * kH1 + n]; };
+  auto w2t = [&](int n, int k) { return W2[(size_t)k * kH2 + n]; };
+  auto w3t = [&](int n, int k) { return W3[(size_t)k * kH3 + n]; };
+  std::vector<float> sw(kH1 + kH2 + kH3, 1.f);
+  if (st->f8) {
+    swizzle_e4m3_into(img.data() + st->off[0], sw.data(), kH1, D, w1t);
+    swizzle_e4m3_into(img.data() + st->off[1], sw.data() + kH1, kH2, kH1, w2t);
+    swizzle_e4m3_into(img.data() + st->off[2], sw.data() + kH1 + kH2, kH3, kH2, w3t);
+  } else {
+    swizzle_into(img.data() + st->off[0], kH1, D, w1t);
+    swizzle_into(img.data() + st->off[1], kH2, kH1, w2t);
+    swizzle_into(img.data() + st->off[2], kH3, kH2, w3t);
+  }
   swizzle_into(img.data() + st->off[3], kH2, kH3, [&](int n, int k) { return W3[(size_t)n * kH3 + k]; });
   swizzle_into(img.data() + st->off[4], kH1, kH2, [&](int n, int k) { return W2[(size_t)n * kH2 + k]; });
   swizzle_into(img.data() + st->off[5], D, kH1, [&](int n, int k) { return W1[(size_t)n * kH1 + k]; });
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e == cudaSuccess)
     e = cudaMemcpy(st->blob + st->per_species * s, img.data(), st->per_species, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && st->f8) {
+    // new weights: the weight scales of species s, and every activation range is re-calibrated
+    e = cudaMemcpy(st->wsc + sw.size() * s, sw.data(), sizeof(float) * sw.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(ctx->b_q8, 0, sizeof(int) * 8 * kMaxS);
+    ctx->fp8_calibrated = false;
+    for (int t = 0; t < kMaxS; ++t) ctx->fp8_seen[t] = false;
+  }
   if (e != cudaSuccess) return ctx->cuda_fail(e, "upload tensor-core weights");
   return NNP_OK;
 }
 
 void mlp_tc_free(nnp_ctx* ctx) {
   TcState* st = static_cast<TcState*>(ctx->tc);
+  if (ctx->b_q8) cudaFree(ctx->b_q8);
+  ctx->b_q8 = nullptr;
   if (!st) return;
   if (st->blob) cudaFree(st->blob);
+  if (st->wsc) cudaFree(st->wsc);
   delete st;
   ctx->tc = nullptr;
 }
@@ -608,10 +788,19 @@ int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t stream, long long rows) {
   const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, ctx->num_sms));
   const Workspace w = ctx->workspace();
   const size_t sm = smem_bytes(D);
-  if (D == 128)
-    k_mlp_bf16<128><<<grid, 256, sm, stream>>>(ctx->d_io, ctx->P, w, st->w, ctx->wf32);
+  if (st->f8)
+    k_mlp_tc<128, true><<<grid, 256, sm, stream>>>(ctx->d_io, ctx->P, w, st->w, ctx->wf32);
+  else if (D == 128)
+    k_mlp_tc<128, false><<<grid, 256, sm, stream>>>(ctx->d_io, ctx->P, w, st->w, ctx->wf32);
   else
-    k_mlp_bf16<48><<<grid, 256, sm, stream>>>(ctx->d_io, ctx->P, w, st->w, ctx->wf32);
+    k_mlp_tc<48, false><<<grid, 256, sm, stream>>>(ctx->d_io, ctx->P, w, st->w, ctx->wf32);
+  return NNP_OK;
+}
+
+int launch_fp8_calib(nnp_ctx* ctx, cudaStream_t stream, long long rows) {
+  if (ctx->P.D > kH1) return ctx->fail(NNP_ERR_UNSUPPORTED, "FP8 calibration needs D <= %d", kH1);
+  const int grid = (int)std::max<long long>(1, std::min<long long>((rows + 7) / 8, 8ll * ctx->num_sms));
+  k_fp8_calib<<<grid, 256, 0, stream>>>(ctx->P, ctx->workspace(), ctx->wf32);
   return NNP_OK;
 }
 

@@ -140,6 +140,7 @@ Workspace nnp_ctx::workspace() const {
   w.dEdG = b_dEdG;
   w.Ei = b_Ei;
   w.flags = b_flags;
+  w.q8 = b_q8;
   w.cap_r = cap_r;
   w.cap_a = cap_a;
   w.max_rows = (long long)c_rows1;
@@ -153,7 +154,7 @@ void nnp_ctx::invalidate_graph() {
 }
 
 // The kernel sequence of one evaluation (stream-ordered; capturable).
-int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows) {
+int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows, bool calib) {
   const Workspace w = workspace();
   const int nsm = num_sms;
   const int g_atoms = grid_for(n, 256, nsm * 8);
@@ -174,8 +175,15 @@ int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows)
   mark_stage(1, capturing);
   k_neighbors<<<g_rows, 256, neighbors_smem(cap_r), stream>>>(io, sys, P, w); ++launches;
   mark_stage(2, capturing);
-  const int bf16 = cfg.precision != NNP_FP32;
-  launch_aev_fwd(rows, nsm, stream, sys, P, w, bf16, tune.fwd); ++launches;
+  if (calib) {  // FP8 calibration: FP32 descriptor, then the activation ranges
+    launch_aev_fwd(rows, nsm, stream, sys, P, w, kGFp32, tune.fwd);
+    int rc = launch_fp8_calib(this, stream, rows);
+    if (rc) return rc;
+    CK(cudaGetLastError());
+    return NNP_OK;
+  }
+  const int gmode = cfg.precision == NNP_FP32 ? kGFp32 : (cfg.precision == NNP_BF16 ? kGBf16 : kGFp8);
+  launch_aev_fwd(rows, nsm, stream, sys, P, w, gmode, tune.fwd); ++launches;
   mark_stage(3, capturing);
   const int g_tiles = (int)std::min<long long>(rows / 64, (long long)nsm);
   if (cfg.precision == NNP_FP32) {
@@ -197,6 +205,36 @@ void nnp_ctx::mark_stage(int k, bool capturing) {
   if (!stage_ev[k]) return;
   if (capturing) cudaEventRecordWithFlags(stage_ev[k], stream, cudaEventRecordExternal);
   else cudaEventRecord(stage_ev[k], stream);
+}
+
+// FP8 form: one synchronous pass of the FP32 descriptor and network forward
+// over this input sets the activation ranges (Workspace::q8).  Runs before the
+// evaluation proper, outside any graph; the device flags accumulated by
+// earlier asynchronous evaluations are kept for nnp_sync.  Species absent
+// from this input stay uncalibrated, so a later input that has them is
+// calibrated again (the ranges only grow).  Returns -1 if the lists were regrown.
+int nnp_ctx::calibrate_fp8(long long n, int B, long long bins, long long rows) {
+  int saved[kNumFlags];
+  CK(cudaStreamSynchronize(stream));
+  CK(cudaMemcpy(saved, b_flags, sizeof saved, cudaMemcpyDeviceToHost));
+  CK(cudaMemsetAsync(b_flags, 0, sizeof saved, stream));
+  int rc = launch_pipeline(n, B, bins, rows, true);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(h_flags, b_flags, sizeof saved, cudaMemcpyDeviceToHost, stream));
+  int seg[kMaxS + 2];
+  CK(cudaMemcpyAsync(seg, b_seg, sizeof(int) * (P.S + 1), cudaMemcpyDeviceToHost, stream));
+  CK(cudaStreamSynchronize(stream));
+  CK(cudaMemcpy(b_flags, saved, sizeof saved, cudaMemcpyHostToDevice));
+  const int st = check_flags();
+  if (st) return st;
+  bool all = true;
+  for (int s = 0; s < P.S; ++s) {
+    // species segments are padded to whole tiles, so a non-empty one has atoms
+    if (seg[s + 1] > seg[s]) fp8_seen[s] = true;
+    all = all && fp8_seen[s];
+  }
+  fp8_calibrated = all;
+  return NNP_OK;
 }
 
 // Host-side set-up of the systems: cell grids, capacity, IO descriptor.
@@ -325,6 +363,11 @@ int nnp_ctx::evaluate(int B, const int64_t* offsets, const double* pos, const in
     // device flags accumulate over asynchronous evaluations until nnp_sync reads them;
     // a synchronous evaluation reports only its own
     if (sync) CK(cudaMemsetAsync(b_flags, 0, sizeof(int) * kNumFlags, stream));
+    if (cfg.precision == NNP_FP8 && !fp8_calibrated) {
+      rc = calibrate_fp8(n, B, bins, rows);
+      if (rc == -1) continue;  // lists regrown: evaluate again
+      if (rc) return rc;
+    }
     if ((cfg.flags & NNP_FLAG_AUTOTUNE) && sync) {
       rc = autotune(n, B, bins, rows);
       if (rc) return rc;
@@ -574,6 +617,7 @@ int nnp_query(nnp_ctx* ctx, int32_t key, int64_t* value) {
     case NNP_Q_TUNE_NEIGHBOURS: *value = ctx->tune.nbr; break;
     case NNP_Q_TUNE_DESCRIPTOR: *value = ctx->tune.fwd; break;
     case NNP_Q_TUNE_BACKWARD: *value = ctx->tune.bwd; break;
+    case NNP_Q_FP8_CALIBRATED: *value = ctx->fp8_calibrated ? 1 : 0; break;
     default: return ctx->fail(NNP_ERR_INVALID_ARG, "unknown query key %d", key);
   }
   return NNP_OK;

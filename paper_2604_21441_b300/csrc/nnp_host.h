@@ -22,7 +22,7 @@ cudaError_t neighbors_set_smem_limits();
 // rows: upper bound of the rows of the evaluation (grid sizing only)
 // per_sm: cap on resident blocks per SM of the grid (0 = built-in default)
 void launch_aev_fwd(long long rows, int nsm, cudaStream_t st, const SysDesc* sys, const DescParams& P,
-                    const Workspace& ws, int bf16, int per_sm = 0);
+                    const Workspace& ws, int mode /* GMode */, int per_sm = 0);
 void launch_aev_bwd(long long rows, int nsm, cudaStream_t st, const EvalIO* io, const SysDesc* sys,
                     const DescParams& P, const Workspace& ws, int per_sm = 0);
 cudaError_t aev_set_smem_limits();
@@ -47,6 +47,7 @@ namespace nnp {
 int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t st, long long rows);
 int mlp_tc_init(nnp_ctx* ctx);
 int mlp_tc_set_weights(nnp_ctx* ctx, int species, const float* host_blob);
+int launch_fp8_calib(nnp_ctx* ctx, cudaStream_t st, long long rows);
 void mlp_tc_free(nnp_ctx* ctx);
 }  // namespace nnp
 
@@ -96,6 +97,10 @@ struct nnp_ctx {
   bool has_weights[nnp::kMaxS] = {false, false, false, false};
   std::vector<float> host_weights;  // FP32 copy (layout of nnp_param_count), for re-quantisation
   void* tc = nullptr;           // tensor-core network state (k_mlp_tc.cu)
+  int* b_q8 = nullptr;          // FP8 scales (Workspace::q8)
+  bool fp8_calibrated = false;  // every species has been seen by a calibration pass
+  bool fp8_seen[nnp::kMaxS] = {false, false, false, false};
+  int calibrate_fp8(long long n, int B, long long bins, long long rows);
 
   // force-matching buffers (allocated on first use)
   float *fm_z = nullptr, *fm_dz = nullptr, *fm_t = nullptr, *fm_p = nullptr;
@@ -134,7 +139,7 @@ struct nnp_ctx {
   int ensure_capacity(long long n, int B, long long bins, long long rows);
   nnp::Workspace workspace() const;
   void invalidate_graph();
-  int launch_pipeline(long long n, int B, long long bins, long long rows);
+  int launch_pipeline(long long n, int B, long long bins, long long rows, bool calib = false);
   int prepare(int B, const int64_t* offsets, const double* pos_host, const double* boxes,
               long long& bins, long long& rows);
   int read_flags(int& fl);

@@ -20,6 +20,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 namespace nnp {
 
@@ -106,6 +107,8 @@ struct Workspace {
   float* dEdG;      // [max_rows * D]
   float* Ei;        // [max_rows]
   int* flags;       // [kNumFlags]
+  int* q8;          // FP8 form, [kMaxS * 8] per species: calibrated |max| of G, h1, h2 as
+                    // float bits at [0, 3) (raised by atomicMax); the rest unused
   int cap_r;        // radial list capacity per row
   int cap_a;        // angular neighbours per row that the descriptor kernels stage
   long long max_rows;
@@ -198,6 +201,28 @@ __device__ __forceinline__ size_t gh_offset(int row, int f, int D) {
   const int r = row & 127;
   return (size_t)(row >> 7) * gh_tile_bytes(D) + (size_t)(f >> 6) * (128 * 128) + (size_t)r * 128 +
          (size_t)((((f >> 3) & 7) ^ (r & 7)) << 4) + (size_t)(f & 7) * 2;
+}
+
+// FP8 (E4M3) copy of G for the FP8 form: the same tiling with 128 one-byte
+// features per slab, 16-byte chunks of 16 features swizzled the same way.
+__host__ __device__ __forceinline__ size_t gh8_tile_bytes(int D) {
+  return (size_t)((D + 127) / 128) * 128 * 128;
+}
+__device__ __forceinline__ size_t gh8_offset(int row, int f, int D) {
+  const int r = row & 127;
+  return (size_t)(row >> 7) * gh8_tile_bytes(D) + (size_t)(f >> 7) * (128 * 128) + (size_t)r * 128 +
+         (size_t)((((f >> 4) & 7) ^ (r & 7)) << 4) + (size_t)(f & 15);
+}
+
+// What the descriptor kernel writes: FP32 G, or the BF16 / FP8 tile copy.
+enum GMode { kGFp32 = 0, kGBf16 = 1, kGFp8 = 2 };
+
+// Largest finite E4M3 magnitude; a per-layer scale s = amax / kE4M3Max maps
+// the calibrated range onto the format's.
+constexpr float kE4M3Max = 448.f;
+__device__ __forceinline__ float fp8_step(int amax_bits) {
+  const float a = __int_as_float(amax_bits);
+  return a > 0.f ? a / kE4M3Max : 1.f;
 }
 
 __device__ __forceinline__ int pair_block(int S, int s1, int s2) {

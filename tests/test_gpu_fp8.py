@@ -1,0 +1,131 @@
+"""GPU tests of the FP8 form: the three forward GEMMs of the tcgen05 network
+in E4M3 (activations: one static scale per layer and species from the
+calibration pass; weights: one scale per output column), the backward in BF16.
+
+E4M3 keeps 3 mantissa bits against BF16's 7.  The error is dominated by the
+fixed rounding of the weights: it changes the network itself, so every E_i
+moves the same way and the relative energy error does not average out over
+atoms.  A NumPy emulation of the same quantisation (float8_e4m3fn casts)
+gives 1.4e-2 relative energy error and a per-atom RMS error of 8e-3 eV on
+1,536 atoms of water, against 4.6e-2 with one scale per weight matrix.  The
+bounds are about twice that: relative energy error <= 3e-2, force errors
+max <= 0.3 eV/A and RMS <= 0.05 eV/A for forces of RMS ~0.3 eV/A.
+"""
+import numpy as np
+import pytest
+
+import synth
+from common import box9, energy_error, weights32
+
+pytestmark = pytest.mark.gpu
+
+E_FP8 = 3e-2       # relative energy error (normalised by max(|E|, sum |E_i|))
+F_MAX_FP8 = 0.3    # eV/A, max-abs force error
+F_RMS_FP8 = 0.05   # eV/A
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2604_21441_b300 import build
+    build.build()
+    import paper_2604_21441_b300 as P
+    return P
+
+
+def _pot(P, w, prec, **kw):
+    pot = P.NNP(atomic_numbers=(1, 8), precision=prec, **kw)
+    pot.set_all_weights([[(W.astype(np.float32), b.astype(np.float32)) for W, b in sp] for sp in w])
+    return pot
+
+
+def test_fp8_water64_vs_oracle(P, oracle_mod):
+    s = synth.water_box(64, synth.GEOM_SEED[1])
+    w = weights32(2, 128, synth.WEIGHT_SEED[1], 7)
+    pot = _pot(P, w, "fp8")
+    assert pot.query("fp8_calibrated") == 0
+    E, F = pot.eval(s.pos, s.Z, box9(s.box))
+    assert pot.query("fp8_calibrated") == 1
+    p = oracle_mod.Params()
+    m = oracle_mod.Model(p, w)
+    Er, Eir, Fr, _ = oracle_mod.energy_forces(m, s.pos, p.species_of(s.Z), s.box)
+    ee = energy_error(E, Er, Eir)
+    dF = F - Fr
+    print(f"fp8 water-64: rel E err {ee:.2e}, max|dF| {np.abs(dF).max():.3e}, "
+          f"rms dF {np.sqrt((dF ** 2).mean()):.3e}, rms F {np.sqrt((Fr ** 2).mean()):.3f}")
+    assert ee <= E_FP8
+    assert np.abs(dF).max() <= F_MAX_FP8
+    assert np.sqrt((dF ** 2).mean()) <= F_RMS_FP8
+    Ei = pot.atom_energies(s.n)
+    assert abs(Ei.sum() - E) <= 1e-6 * np.abs(Ei).sum()
+
+
+def test_fp8_calibration_state(P):
+    """Scales are fixed after the first evaluation (repeats agree),
+    reset by new weights, and a species missing from the first input keeps
+    the form uncalibrated until an input has it."""
+    s = synth.water_box(216, 31)
+    w = weights32(2, 128, 32, 33)
+    pot = _pot(P, w, "fp8")
+    # oxygen only: hydrogen has not been seen
+    oxy = s.Z == 8
+    pos_o, Z_o = s.pos[oxy], s.Z[oxy]
+    pot.eval(pos_o, Z_o, box9(s.box))
+    assert pot.query("fp8_calibrated") == 0
+    E1, F1 = pot.eval(s.pos, s.Z, box9(s.box))
+    assert pot.query("fp8_calibrated") == 1
+    E2, F2 = pot.eval(s.pos, s.Z, box9(s.box))
+    # same scales: equal up to the order of the FP64 atomic sums
+    assert abs(E2 - E1) <= 1e-9 * abs(E1) and np.abs(F2 - F1).max() <= 1e-9
+    pot.set_all_weights([[(W.astype(np.float32), b.astype(np.float32)) for W, b in sp] for sp in w])
+    assert pot.query("fp8_calibrated") == 0
+    E3, F3 = pot.eval(s.pos, s.Z, box9(s.box))
+    assert pot.query("fp8_calibrated") == 1
+    # ranges now come from the full input alone: same scales as E1's pass or wider
+    assert np.isfinite(E3) and np.isfinite(F3).all()
+
+
+def test_fp8_close_to_bf16_and_fp32(P):
+    s = synth.water_box(512, 77)
+    w = weights32(2, 128, 78, 79)
+    a = _pot(P, w, "fp32")
+    b = _pot(P, w, "bf16")
+    c = _pot(P, w, "fp8")
+    Ea, Fa = a.eval(s.pos, s.Z, box9(s.box))
+    Eb, Fb = b.eval(s.pos, s.Z, box9(s.box))
+    Ec, Fc = c.eval(s.pos, s.Z, box9(s.box))
+    Ei = a.atom_energies(s.n)
+    norm = np.abs(Ei).sum()
+    print(f"fp8 vs fp32 (1536 atoms): |dE|/sum|Ei| {abs(Ec - Ea) / norm:.2e}, "
+          f"max|dF| {np.abs(Fc - Fa).max():.3e}, rms dF {np.sqrt(((Fc - Fa) ** 2).mean()):.3e}; "
+          f"bf16: {abs(Eb - Ea) / norm:.2e}, {np.abs(Fb - Fa).max():.3e}")
+    assert abs(Ec - Ea) <= E_FP8 * norm
+    assert np.abs(Fc - Fa).max() <= F_MAX_FP8
+    assert np.sqrt(((Fc - Fa) ** 2).mean()) <= F_RMS_FP8
+    # FP8 is the coarser form
+    assert np.sqrt(((Fc - Fa) ** 2).mean()) >= np.sqrt(((Fb - Fa) ** 2).mean())
+
+
+def test_fp8_full_size_sampled(P, oracle_mod):
+    """98,304 atoms (768 tiles over the persistent CTAs) against the oracle
+    on sampled atoms."""
+    import torch
+    wl = synth.workload(3)
+    s = wl["systems"][0]
+    w = weights32(2, 128, wl["weight_seed"])
+    pot = _pot(P, w, "fp8", max_atoms=s.n)
+    pos = torch.tensor(s.pos, device="cuda")
+    Z = torch.tensor(s.Z, device="cuda")
+    E, F = pot.eval(pos, Z, box9(s.box))
+    F = F.cpu().numpy()
+    Ei = pot.atom_energies(s.n)
+    rng = np.random.default_rng(6)
+    sel_e = np.sort(rng.choice(s.n, 64, replace=False))
+    sel_f = np.sort(rng.choice(s.n, 12, replace=False))
+    p = oracle_mod.Params()
+    m = oracle_mod.Model(p, w)
+    Eir, Fr = oracle_mod.energy_forces_subset(m, s.pos, p.species_of(s.Z), s.box, sel_e, sel_f)
+    print(f"fp8 water-32768 sampled: max|dEi| {np.abs(Ei[sel_e] - Eir).max():.2e}, "
+          f"max|dF| {np.abs(F[sel_f] - Fr).max():.3e}")
+    assert np.abs(Ei[sel_e] - Eir).max() <= E_FP8 * max(1.0, np.abs(Eir).max()) * 5
+    assert np.abs(F[sel_f] - Fr).max() <= F_MAX_FP8
+    assert abs(float(E) - Ei.sum()) <= 1e-6 * np.abs(Ei).sum()
