@@ -31,6 +31,7 @@ namespace {
 
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kPi = 3.14159265358979f;
+constexpr int kBwdWarps = 4;  // rows (warps) per k_aev_bwd block
 
 // fc = cos^2(y), dfc/dr = -2 k sin(y) cos(y), y = k r, k = pi / (2 rc), from
 // the Taylor series of cos and sin about 0 (truncation error < 1e-8 for
@@ -352,248 +353,415 @@ __global__ void __launch_bounds__(256) k_aev_fwd(const SysDesc* __restrict__ sys
 
 // --------------------------------------------------------------------------
 // backward: dE/dG -> forces (FP64 accumulation in the caller's array)
+//
+// Warp per row.  (1) Radial: lanes over all radial neighbours of the row
+// (every species in one flat range); each lane writes its neighbour's
+// radial force into the neighbour's slot and stages the angular neighbours
+// (unit vector, distance, cutoff).  (2) Angular: the neighbour pairs of all
+// species-pair blocks form one flat index space walked 32 at a time.  A pair
+// (u, v) of block (s1, s2) contributes -(A_u e_u + B_u e_v) to u,
+// -(A_v e_v + B_v e_u) to v and the negative sum to the centre; the lane
+// keeps the centre's share and writes (A_u, B_u) to entry (u, v) and
+// (A_v, B_v) to entry (v, u) of a per-row matrix in shared memory.
+// (3) The lane of angular neighbour m sums row m of the matrix (the partner's
+// unit vector comes from the staging) and adds the result to m's slot, so no
+// shared-memory atomics are needed.  (4) One FP64 add per slot and component.
+//
+// Pair order inside a block: diagonal blocks (n neighbours) use the
+// round-robin order (l, l + k mod n), k = 1..K, then (l, l + n/2) for l < n/2
+// if n is even; off-diagonal blocks with lists a (m1 entries) and b
+// (m2 >= m1 entries) use the wrapped diagonals (i, i + d mod m2), d-major.
+// The term is symmetric in (u, v), so either list may play u.  The eight
+// angular sectors (and the sixteen radial shifts) are evaluated in pairs with
+// packed FP32x2 arithmetic.
+
+namespace {
+
+// packed FP32 pair (fma/mul.rn.f32x2: one instruction for two lanes of arithmetic)
+struct f2 {
+  unsigned long long v;
+};
+__device__ __forceinline__ f2 f2_make(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 f2_split(f2 x) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(x.v));
+  return r;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+// 2^x (MUFU; results below the normal range flush to zero)
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ f2 f2_ex2(f2 x) {
+  const float2 h = f2_split(x);
+  return f2_make(ex2(h.x), ex2(h.y));
+}
+
+// One species-pair block of a row's angular pairs (per-warp table in shared memory).
+struct PairBlock {
+  int base, T;      // first flat index, pairs
+  int ma, mb;       // list lengths: a (u role), b (v role); diagonal: ma = mb = n
+  int oa, ob;       // staging offsets of the lists
+  int nK, half;     // diagonal: n K (round-robin part), n / 2 if n is even else 0
+  int sa, sb;       // species of the lists
+  int wo;           // offset of the block's 32 weights in dE/dG
+  float inv;        // 1 / n (diagonal) or 1 / ma (off-diagonal)
+};
+
+// q = t / n for 0 <= t < 2^22 (float reciprocal, one correction step)
+__device__ __forceinline__ int div_small(int t, int n, float inv) {
+  int q = (int)(((float)t + 0.5f) * inv);
+  if (q * n > t) --q;
+  else if ((q + 1) * n <= t) ++q;
+  return q;
+}
+
+}  // namespace
+
+// float4 units of one warp's shared memory; the pair matrix has rows of
+// cap_a + 1 float2 entries (the odd stride spreads a column over the banks)
+__host__ __device__ inline size_t bwd_mat_f4(int cap_a) { return ((size_t)cap_a * (cap_a + 1) * 2 + 3) / 4; }
+__host__ __device__ inline size_t bwd_warp_f4(int cap_a, int cap_r, int D) {
+  return 27 + 2 * (size_t)cap_a + bwd_mat_f4(cap_a) + (size_t)D / 4 + ((size_t)3 * cap_r + 3) / 4 +
+         ((size_t)cap_r + 3) / 4 + (sizeof(PairBlock) * (kMaxS * (kMaxS + 1) / 2) + 15) / 16;
+}
 
 template <int S, int ZSQ>
-__global__ void __launch_bounds__(128) k_aev_bwd(const EvalIO* __restrict__ io,
-                                                 const SysDesc* __restrict__ sys, DescParams P,
-                                                 Workspace ws) {
+__global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ io,
+                                                    const SysDesc* __restrict__ sys, DescParams P,
+                                                    Workspace ws) {
   constexpr int D = kNRad * S + kNAng * S * (S + 1) / 2;
+  constexpr int NB = S * (S + 1) / 2;
+  constexpr unsigned FM = 0xffffffffu;
   extern __shared__ float4 sm4[];
-  const int lane = threadIdx.x & 31, hl = lane & 15, half = lane >> 4;
-  const int hwb = threadIdx.x >> 4;  // 0..7
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int ca = ws.cap_a, cr = ws.cap_r;
-  // per half warp: geo[ca], aux[ca] (fc, dfc, 1/r, slot), sh[27] | fsl[3 cr] | origs[cr] | w[D] | counts
-  const size_t n4 = (size_t)2 * ca + 27;
-  float4* geo = sm4 + hwb * n4;
+  float4* sh = sm4 + (size_t)wib * bwd_warp_f4(ca, cr, D);
+  float4* geo = sh + 27;
   float4* aux = geo + ca;
-  float4* sh = aux + ca;
-  float* fbase = reinterpret_cast<float*>(sm4 + 8 * n4);
-  const size_t nf = (size_t)4 * cr + D;
-  float* fsl = fbase + hwb * nf;
-  int* origs = reinterpret_cast<int*>(fsl + 3 * cr);
-  float* wsm = fsl + 4 * cr;
-  RowCounts* rc = reinterpret_cast<RowCounts*>(fbase + 8 * nf) + hwb;
+  float2* mat = reinterpret_cast<float2*>(aux + ca);  // [ca][ca + 1]
+  const int ms = ca + 1;
+  float* wsm = reinterpret_cast<float*>(aux + ca + bwd_mat_f4(ca));
+  float* fsl = wsm + D;
+  int* origs = reinterpret_cast<int*>(reinterpret_cast<float4*>(fsl) + (3 * cr + 3) / 4);
+  PairBlock* blk = reinterpret_cast<PairBlock*>(reinterpret_cast<float4*>(origs) + (cr + 3) / 4);
+
   const float kr = -P.eta_r * kLog2e, ka = -P.eta_a * kLog2e;
   const float kfr = kPi / (2.f * P.rc_r), kfa = kPi / (2.f * P.rc_a);
   const float zeta = (float)(1 << P.zeta_sq);
+  // sector constants in pairs (z, z+1): base = 1/2 + uc hc + sn hs,
+  // d(base^zeta)/dc = base^(zeta-1) (Kc - (uc/sn) Ks) with K = 0.95 zeta h
+  f2 hc2[4], hs2[4], kc2[4], ks2[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    hc2[q] = f2_make(P.hcos_z[2 * q], P.hcos_z[2 * q + 1]);
+    hs2[q] = f2_make(P.hsin_z[2 * q], P.hsin_z[2 * q + 1]);
+    kc2[q] = f2_make(0.95f * zeta * P.hcos_z[2 * q], 0.95f * zeta * P.hcos_z[2 * q + 1]);
+    ks2[q] = f2_make(-0.95f * zeta * P.hsin_z[2 * q], -0.95f * zeta * P.hsin_z[2 * q + 1]);
+  }
+  const f2 half2 = f2_make(0.5f, 0.5f);
   double* F = io->forces;
   const int rows = ws.seg[S];
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int wpb = blockDim.x >> 5;
   int cached_sys = -1;
-  for (int pr = warp; 2 * pr < rows; pr += nwarps) {
-    const int row = 2 * pr + half;
-    const bool live = row < rows && ws.row_atom[row] >= 0;
-    float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (live) {
-      pi = ws.pos4[row];
-      const int sid = ws.row_info[row];
-      if (sid != cached_sys) {
-        const SysDesc& sd = sys[sid];
-        const float ell[3] = {sd.ellf[0], sd.ellf[1], sd.ellf[2]};
-        for (int c = hl; c < 27; c += 16) sh[c] = shift_vec(c, ell);
-        cached_sys = sid;
-      }
-      const float4* dg = reinterpret_cast<const float4*>(ws.dEdG + (size_t)row * D);
-      for (int f = hl; f < D / 4; f += 16) reinterpret_cast<float4*>(wsm)[f] = dg[f];
+  for (int row = blockIdx.x * wpb + wib; row < rows; row += gridDim.x * wpb) {
+    if (ws.row_atom[row] < 0) continue;  // padding row (warp-uniform)
+    const float4 pi = ws.pos4[row];
+    const int sid = ws.row_info[row];
+    __syncwarp();  // the previous row's shared data has been read
+    if (sid != cached_sys) {
+      const SysDesc& sd = sys[sid];
+      const float ell[3] = {sd.ellf[0], sd.ellf[1], sd.ellf[2]};
+      if (lane < 27) sh[lane] = shift_vec(lane, ell);
+      cached_sys = sid;
     }
-    load_counts(ws, S, row, live, ca, rc, hl);
-    __syncwarp();
+    {
+      const float4* dg = reinterpret_cast<const float4*>(ws.dEdG + (size_t)row * D);
+      for (int f = lane; f < D / 4; f += 32) reinterpret_cast<float4*>(wsm)[f] = dg[f];
+    }
+    // counts per species (angular ones clamped to the staging capacity)
+    int cnt_l = 0, cna_l = 0;
+    if (lane < S) {
+      cnt_l = ws.cnt_r[(size_t)row * kMaxS + lane];
+      cna_l = ws.cnt_a[(size_t)row * kMaxS + lane];
+    }
+    int nr[S], orr[S], na[S], oa[S];
+    int ntot = 0, nang = 0;
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+      nr[q] = __shfl_sync(FM, cnt_l, q);
+      orr[q] = ntot;
+      ntot += nr[q];
+      na[q] = min(__shfl_sync(FM, cna_l, q), max(0, ca - nang));
+      oa[q] = nang;
+      nang += na[q];
+    }
+    // pair blocks (every lane computes the same table; lanes < NB store it)
+    int Ttot = 0;
+    {
+      int b = 0;
+#pragma unroll
+      for (int s1 = 0; s1 < S; ++s1)
+#pragma unroll
+        for (int s2 = s1; s2 < S; ++s2, ++b) {
+          PairBlock pb;
+          pb.base = Ttot;
+          pb.wo = kNRad * S + b * kNAng;
+          if (s1 == s2) {
+            const int n = na[s1];
+            const int K = (n & 1) ? (n - 1) / 2 : max(0, n / 2 - 1);
+            pb.ma = pb.mb = n;
+            pb.oa = pb.ob = oa[s1];
+            pb.sa = pb.sb = s1;
+            pb.nK = n * K;
+            pb.half = (n & 1) ? 0 : n / 2;
+            pb.T = pb.nK + pb.half;
+            pb.inv = n > 0 ? 1.f / (float)n : 0.f;
+          } else {
+            const bool sw = na[s1] > na[s2];  // list a is the shorter one
+            pb.ma = sw ? na[s2] : na[s1];
+            pb.mb = sw ? na[s1] : na[s2];
+            pb.oa = sw ? oa[s2] : oa[s1];
+            pb.ob = sw ? oa[s1] : oa[s2];
+            pb.sa = sw ? s2 : s1;
+            pb.sb = sw ? s1 : s2;
+            pb.nK = 0;
+            pb.half = 0;
+            pb.T = pb.ma * pb.mb;
+            pb.inv = pb.ma > 0 ? 1.f / (float)pb.ma : 0.f;
+          }
+          if (lane == b) blk[b] = pb;
+          Ttot += pb.T;
+        }
+    }
     const int* lr = ws.nbr_r + (size_t)row * cr;
     float fix = 0.f, fiy = 0.f, fiz = 0.f;  // force on the centre atom
+    __syncwarp();
 
-    // ---------------- radial: every slot written once (initialises fsl)
-#pragma unroll 1
-    for (int s = 0; s < S; ++s) {
-      const int n_s = rc->nr[s], o_s = rc->orr[s];
-      const int nmax = max(n_s, __shfl_xor_sync(0xffffffffu, n_s, 16));
-      float w16[kNRad];
+    // ---------------- (1) radial, and staging of the angular neighbours
+    for (int k = lane; k < ntot; k += 32) {
+      int s = 0, o_s = 0, na_s = na[0], oa_s = 0;
 #pragma unroll
-      for (int m = 0; m < kNRad; m += 4) {
-        const float4 q = reinterpret_cast<const float4*>(wsm + s * kNRad)[m / 4];
-        w16[m] = q.x; w16[m + 1] = q.y; w16[m + 2] = q.z; w16[m + 3] = q.w;
-      }
-      for (int k0 = 0; k0 < nmax; k0 += 16) {
-        const int k = k0 + hl;
-        if (k < n_s) {
-          const int e = lr[o_s + k];
-          const float4 pj = ws.pos4[nbr_row(e)];
-          const float4 sv = sh[nbr_code(e)];
-          const float dx = (pj.x - pi.x) + sv.x, dy = (pj.y - pi.y) + sv.y, dz = (pj.z - pi.z) + sv.z;
-          const float r2 = dx * dx + dy * dy + dz * dz;
-          const float ir = rsqrtf(r2);
-          const float r = r2 * ir;
-          float fc, dfc;
-          cutoff(r, P.rc_r, kfr, fc, dfc);
-          float s0 = 0.f, s1 = 0.f;
+      for (int q = 1; q < S; ++q)
+        if (k >= orr[q]) {
+          s = q;
+          o_s = orr[q];
+          na_s = na[q];
+          oa_s = oa[q];
+        }
+      const int e = lr[k];
+      const float4 pj = ws.pos4[nbr_row(e)];
+      const float4 sv = sh[nbr_code(e)];
+      const float dx = (pj.x - pi.x) + sv.x, dy = (pj.y - pi.y) + sv.y, dz = (pj.z - pi.z) + sv.z;
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      const float ir = rsqrtf(r2);
+      const float r = r2 * ir;
+      float fc, dfc;
+      cutoff(r, P.rc_r, kfr, fc, dfc);
+      const float4* w4 = reinterpret_cast<const float4*>(wsm + s * kNRad);
+      const f2 r2v = f2_make(r, r), kr2 = f2_make(kr, kr);
+      f2 s02 = f2_make(0.f, 0.f), s12 = s02;
 #pragma unroll
-          for (int m = 0; m < kNRad; ++m) {
-            const float x = r - P.shf_r[m];
-            const float we = w16[m] * exp2f(kr * x * x);
-            s0 += we;
-            s1 = fmaf(we, x, s1);
-          }
-          // dE_i/dr_ij divided by r_ij; dE_i/dr_j = g d, dE_i/dr_i = -g d
-          const float g = 0.25f * fmaf(dfc, s0, -2.f * P.eta_r * fc * s1) * ir;
-          const int slot = o_s + k;
-          fsl[3 * slot] = -g * dx;
-          fsl[3 * slot + 1] = -g * dy;
-          fsl[3 * slot + 2] = -g * dz;
-          origs[slot] = pos4_orig(pj);
-          fix = fmaf(g, dx, fix);
-          fiy = fmaf(g, dy, fiy);
-          fiz = fmaf(g, dz, fiz);
+      for (int m4 = 0; m4 < kNRad / 4; ++m4) {
+        const float4 q = w4[m4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const f2 x = f2_add(r2v, f2_make(-P.shf_r[4 * m4 + 2 * h], -P.shf_r[4 * m4 + 2 * h + 1]));
+          const f2 we = f2_mul(h ? f2_make(q.z, q.w) : f2_make(q.x, q.y), f2_ex2(f2_mul(kr2, f2_mul(x, x))));
+          s02 = f2_add(s02, we);
+          s12 = f2_fma(we, x, s12);
         }
       }
-    }
-
-    // ---------------- angular: stage the neighbours inside rc_a
-#pragma unroll 1
-    for (int s = 0; s < S; ++s) {
-      const int n_a = rc->na[s], o_r = rc->orr[s], o_a = rc->oa[s];
-      for (int k = hl; k < n_a; k += 16) {
-        const int e = lr[o_r + k];
-        const float4 pj = ws.pos4[nbr_row(e)];
-        const float4 sv = sh[nbr_code(e)];
-        const float dx = (pj.x - pi.x) + sv.x, dy = (pj.y - pi.y) + sv.y, dz = (pj.z - pi.z) + sv.z;
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        const float ir = rsqrtf(r2);
-        const float r = r2 * ir;
-        float fc, dfc;
-        cutoff(r, P.rc_a, kfa, fc, dfc);
-        geo[o_a + k] = make_float4(dx * ir, dy * ir, dz * ir, r);
-        aux[o_a + k] = make_float4(fc, dfc, ir, __int_as_float(o_r + k));
+      const float2 s0h = f2_split(s02), s1h = f2_split(s12);
+      const float s0 = s0h.x + s0h.y, s1 = s1h.x + s1h.y;
+      // dE_i/dr_ij divided by r_ij; dE_i/dr_j = g d, dE_i/dr_i = -g d
+      const float g = 0.25f * fmaf(dfc, s0, -2.f * P.eta_r * fc * s1) * ir;
+      fsl[3 * k] = -g * dx;
+      fsl[3 * k + 1] = -g * dy;
+      fsl[3 * k + 2] = -g * dz;
+      origs[k] = pos4_orig(pj);
+      fix = fmaf(g, dx, fix);
+      fiy = fmaf(g, dy, fiy);
+      fiz = fmaf(g, dz, fiz);
+      const int kk = k - o_s;
+      if (kk < na_s) {  // the first na[s] entries of a species are the angular ones
+        float fca, dfca;
+        cutoff(r, P.rc_a, kfa, fca, dfca);
+        geo[oa_s + kk] = make_float4(dx * ir, dy * ir, dz * ir, r);
+        aux[oa_s + kk] = make_float4(fca, dfca, ir, __int_as_float(k));
       }
     }
     __syncwarp();
-#pragma unroll 1
-    for (int s1 = 0; s1 < S; ++s1) {
-#pragma unroll 1
-      for (int s2 = s1; s2 < S; ++s2) {
-        const bool diag = s1 == s2;
-        const int n1 = rc->na[s1], n2 = rc->na[s2];
-        const int T = diag ? n1 * (n1 - 1) / 2 : n1 * n2;
-        const int Tmax = max(T, __shfl_xor_sync(0xffffffffu, T, 16));
-        if (Tmax == 0) continue;
-        const PairMap pm = make_map(diag, n1, n2, rc->oa[s1], rc->oa[s2]);
-        float wr[kNAng];
-        const float4* wb = reinterpret_cast<const float4*>(wsm + kNRad * S + pair_block(S, s1, s2) * kNAng);
-#pragma unroll
-        for (int q = 0; q < kNAng / 4; ++q) {
-          const float4 x = wb[q];
-          wr[4 * q] = x.x; wr[4 * q + 1] = x.y; wr[4 * q + 2] = x.z; wr[4 * q + 3] = x.w;
+
+    // ---------------- (2) angular pairs, flat over the blocks
+    {
+      int b = 0;
+      PairBlock pb = blk[0];
+      for (int t = lane; t < Ttot; t += 32) {
+        while (b + 1 < NB && t >= pb.base + pb.T) pb = blk[++b];
+        const int tl = t - pb.base;
+        int u, v;
+        if (pb.sa == pb.sb) {
+          const int n = pb.ma;
+          if (tl < pb.nK) {
+            const int q = div_small(tl, n, pb.inv);
+            u = tl - q * n;
+            v = u + q + 1;
+            if (v >= n) v -= n;
+          } else {
+            u = tl - pb.nK;
+            v = u + pb.half;
+          }
+        } else {
+          const int d = div_small(tl, pb.ma, pb.inv);
+          u = tl - d * pb.ma;
+          v = u + d;
+          if (v >= pb.mb) v -= pb.mb;
         }
-        // each lane walks a contiguous chunk of the pair index: the first
-        // neighbour u stays fixed over runs, so its force is summed in
-        // registers and flushed once per run; only v needs an atomic per pair
-        const int chunk = (T + 15) >> 4;
-        const int cmax = max(chunk, __shfl_xor_sync(0xffffffffu, chunk, 16));
-        int cur_u = -1;
-        float aux_ = 0.f, auy = 0.f, auz = 0.f;
-        for (int j = 0; j < cmax; ++j) {
-          const int t = hl * chunk + j;
-          if (j < chunk && t < T) {
-            int u, v;
-            map_pair(pm, t, u, v);
-            const float4 gu = geo[u], gv = geo[v], au = aux[u], av = aux[v];
-            const float c = gu.x * gv.x + gu.y * gv.y + gu.z * gv.z;
-            const float uc = 0.95f * c;
-            const float s2q = fmaxf(1.f - uc * uc, 1e-12f);
-            const float isn = rsqrtf(s2q);
-            const float sn = s2q * isn;
-            const float ucisn = uc * isn;
-            const float rbar = 0.5f * (gu.w + gv.w);
-            float Be[kNAngR], Bq[kNAngR], X[kNAngR], Y[kNAngR];
+        u += pb.oa;
+        v += pb.ob;
+        const float4 gu = geo[u], gv = geo[v], au = aux[u], av = aux[v];
+        const float c = gu.x * gv.x + gu.y * gv.y + gu.z * gv.z;
+        const float uc = 0.95f * c;
+        const float s2q = fmaxf(1.f - uc * uc, 1e-12f);
+        const float isn = rsqrtf(s2q);
+        const float sn = s2q * isn;
+        const float ucisn = uc * isn;
+        const float rbar = 0.5f * (gu.w + gv.w);
+        float Be[kNAngR], Bq[kNAngR];
 #pragma unroll
-            for (int a = 0; a < kNAngR; ++a) {
-              const float x = rbar - P.shf_a[a];
-              Be[a] = exp2f(ka * x * x);
-              Bq[a] = -2.f * P.eta_a * x * Be[a];
-              X[a] = 0.f;
-              Y[a] = 0.f;
-            }
+        for (int a = 0; a < kNAngR; ++a) {
+          const float x = rbar - P.shf_a[a];
+          Be[a] = ex2(ka * x * x);
+          Bq[a] = -2.f * P.eta_a * x * Be[a];
+        }
+        const f2 uc2 = f2_make(uc, uc), sn2 = f2_make(sn, sn), ucisn2 = f2_make(ucisn, ucisn);
+        const float* wb = wsm + pb.wo;
+        f2 X2[kNAngR], Y2[kNAngR];
 #pragma unroll
-            for (int z = 0; z < kNAngZ; ++z) {
-              const float base = fmaf(sn, P.hsin_z[z], fmaf(uc, P.hcos_z[z], 0.5f));
-              float bz, bzm1;
-              pow_zeta<ZSQ>(base, P.zeta_sq, bz, bzm1);
-              // d base / d cos(theta) = 0.95 (cos(theta_z) - sin(theta_z) u / sqrt(1-u^2)) / 2
-              const float dbase = 0.95f * fmaf(-ucisn, P.hsin_z[z], P.hcos_z[z]);
-              const float dA = zeta * bzm1 * dbase;
+        for (int zp = 0; zp < kNAngZ / 2; ++zp) {
+          const f2 base = f2_fma(sn2, hs2[zp], f2_fma(uc2, hc2[zp], half2));
+          // base^(zeta-1) and base^zeta
+          f2 pw = base, pm1;
+          if (ZSQ >= 1) {
+            f2 prod = base;
+            pw = f2_mul(base, base);
 #pragma unroll
-              for (int a = 0; a < kNAngR; ++a) {
-                X[a] = fmaf(wr[a * kNAngZ + z], bz, X[a]);
-                Y[a] = fmaf(wr[a * kNAngZ + z], dA, Y[a]);
-              }
+            for (int i = 1; i < (ZSQ >= 1 ? ZSQ : 1); ++i) {
+              prod = f2_mul(prod, pw);
+              pw = f2_mul(pw, pw);
             }
-            float Pv = 0.f, Qv = 0.f, Rv = 0.f;
+            pm1 = prod;
+          } else {
+            const float2 bb = f2_split(base);
+            float b0z, b0m, b1z, b1m;
+            pow_zeta<ZSQ>(bb.x, P.zeta_sq, b0z, b0m);
+            pow_zeta<ZSQ>(bb.y, P.zeta_sq, b1z, b1m);
+            pw = f2_make(b0z, b1z);
+            pm1 = f2_make(b0m, b1m);
+          }
+          const f2 dA = f2_mul(pm1, f2_fma(ucisn2, ks2[zp], kc2[zp]));
 #pragma unroll
-            for (int a = 0; a < kNAngR; ++a) {
-              Pv = fmaf(Be[a], X[a], Pv);
-              Qv = fmaf(Bq[a], X[a], Qv);
-              Rv = fmaf(Be[a], Y[a], Rv);
+          for (int a = 0; a < kNAngR; ++a) {
+            const float4 w4 = reinterpret_cast<const float4*>(wb + a * kNAngZ)[zp >> 1];
+            const f2 w2 = (zp & 1) ? f2_make(w4.z, w4.w) : f2_make(w4.x, w4.y);
+            if (zp == 0) {
+              X2[a] = f2_mul(w2, pw);
+              Y2[a] = f2_mul(w2, dA);
+            } else {
+              X2[a] = f2_fma(w2, pw, X2[a]);
+              Y2[a] = f2_fma(w2, dA, Y2[a]);
             }
-            // the angular term carries a factor 2 (2 ((1 + cos)/2)^zeta)
-            const float fu = au.x, fv = av.x;
-            const float fuv = fu * fv;
-            const float dEdru = 2.f * fmaf(au.y * fv, Pv, 0.5f * fuv * Qv);
-            const float dEdrv = 2.f * fmaf(fu * av.y, Pv, 0.5f * fuv * Qv);
-            const float dEdc = 2.f * fuv * Rv;
-            // d cos/d d_u = (e_v - c e_u)/r_u ; d cos/d d_v = (e_u - c e_v)/r_v
-            const float Au = fmaf(-dEdc * c, au.z, dEdru), Bu = dEdc * au.z;
-            const float Av = fmaf(-dEdc * c, av.z, dEdrv), Bv = dEdc * av.z;
-            const float gux = fmaf(Au, gu.x, Bu * gv.x), guy = fmaf(Au, gu.y, Bu * gv.y),
-                        guz = fmaf(Au, gu.z, Bu * gv.z);
-            const float gvx = fmaf(Av, gv.x, Bv * gu.x), gvy = fmaf(Av, gv.y, Bv * gu.y),
-                        gvz = fmaf(Av, gv.z, Bv * gu.z);
-            const int su = __float_as_int(au.w), svs = __float_as_int(av.w);
-            if (su != cur_u) {
-              if (cur_u >= 0) {
-                atomicAdd(&fsl[3 * cur_u], aux_);
-                atomicAdd(&fsl[3 * cur_u + 1], auy);
-                atomicAdd(&fsl[3 * cur_u + 2], auz);
-              }
-              cur_u = su;
-              aux_ = auy = auz = 0.f;
-            }
-            aux_ -= gux;
-            auy -= guy;
-            auz -= guz;
-            atomicAdd(&fsl[3 * svs], -gvx);
-            atomicAdd(&fsl[3 * svs + 1], -gvy);
-            atomicAdd(&fsl[3 * svs + 2], -gvz);
-            fix += gux + gvx;
-            fiy += guy + gvy;
-            fiz += guz + gvz;
           }
         }
-        if (cur_u >= 0) {
-          atomicAdd(&fsl[3 * cur_u], aux_);
-          atomicAdd(&fsl[3 * cur_u + 1], auy);
-          atomicAdd(&fsl[3 * cur_u + 2], auz);
+        float Pv = 0.f, Qv = 0.f, Rv = 0.f;
+#pragma unroll
+        for (int a = 0; a < kNAngR; ++a) {
+          const float2 xs = f2_split(X2[a]), ys = f2_split(Y2[a]);
+          const float X = xs.x + xs.y, Y = ys.x + ys.y;
+          Pv = fmaf(Be[a], X, Pv);
+          Qv = fmaf(Bq[a], X, Qv);
+          Rv = fmaf(Be[a], Y, Rv);
         }
+        // the angular term carries a factor 2 (2 ((1 + cos)/2)^zeta)
+        const float fu = au.x, fv = av.x;
+        const float fuv = fu * fv;
+        const float dEdru = 2.f * fmaf(au.y * fv, Pv, 0.5f * fuv * Qv);
+        const float dEdrv = 2.f * fmaf(fu * av.y, Pv, 0.5f * fuv * Qv);
+        const float dEdc = 2.f * fuv * Rv;
+        // d cos/d d_u = (e_v - c e_u)/r_u ; d cos/d d_v = (e_u - c e_v)/r_v
+        const float Au = fmaf(-dEdc * c, au.z, dEdru), Bu = dEdc * au.z;
+        const float Av = fmaf(-dEdc * c, av.z, dEdrv), Bv = dEdc * av.z;
+        mat[u * ms + v] = make_float2(Au, Bu);
+        mat[v * ms + u] = make_float2(Av, Bv);
+        const float ca_ = Au + Bv, cb_ = Bu + Av;  // centre: g_u + g_v = (Au + Bv) e_u + (Bu + Av) e_v
+        fix += ca_ * gu.x + cb_ * gv.x;
+        fiy += ca_ * gu.y + cb_ * gv.y;
+        fiz += ca_ * gu.z + cb_ * gv.z;
       }
     }
     __syncwarp();
-    // one FP64 add per neighbour slot and component
-    int ntot = 0;
-    for (int s = 0; s < S; ++s) ntot += rc->nr[s];
-    for (int k = hl; k < ntot; k += 16) {
+
+    // ---------------- (3) each angular neighbour sums its row of the pair matrix
+    for (int m = lane; m < nang; m += 32) {
+      const float4 gm = geo[m];
+      float sa = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+      const float2* row_m = mat + m * ms;
+      for (int p = 0; p < nang; ++p) {
+        if (p == m) continue;
+        const float2 c = row_m[p];
+        const float4 gp = geo[p];
+        sa += c.x;
+        fx = fmaf(c.y, gp.x, fx);
+        fy = fmaf(c.y, gp.y, fy);
+        fz = fmaf(c.y, gp.z, fz);
+      }
+      const int slot = __float_as_int(aux[m].w);
+      fsl[3 * slot] -= fmaf(sa, gm.x, fx);
+      fsl[3 * slot + 1] -= fmaf(sa, gm.y, fy);
+      fsl[3 * slot + 2] -= fmaf(sa, gm.z, fz);
+    }
+    __syncwarp();
+
+    // ---------------- (4) one FP64 add per neighbour slot and component
+    for (int k = lane; k < ntot; k += 32) {
       const int oj = origs[k];
       atomicAdd(&F[3 * oj], (double)fsl[3 * k]);
       atomicAdd(&F[3 * oj + 1], (double)fsl[3 * k + 1]);
       atomicAdd(&F[3 * oj + 2], (double)fsl[3 * k + 2]);
     }
-    fix = hw_sum(fix);
-    fiy = hw_sum(fiy);
-    fiz = hw_sum(fiz);
-    if (live && hl == 0) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      fix += __shfl_xor_sync(FM, fix, o);
+      fiy += __shfl_xor_sync(FM, fiy, o);
+      fiz += __shfl_xor_sync(FM, fiz, o);
+    }
+    if (lane == 0) {
       const int oi = pos4_orig(pi);
       atomicAdd(&F[3 * oi], (double)fix);
       atomicAdd(&F[3 * oi + 1], (double)fiy);
       atomicAdd(&F[3 * oi + 2], (double)fiz);
     }
-    __syncwarp();
   }
 }
 
@@ -804,8 +972,7 @@ size_t aev_fwd_smem(int cap_a) {
   return 16 * ((size_t)(cap_a + 27) * sizeof(float4) + (size_t)cap_a * sizeof(float) + sizeof(RowCounts));
 }
 size_t aev_bwd_smem(int cap_a, int cap_r, int D) {
-  return 8 * ((size_t)(2 * cap_a + 27) * sizeof(float4) + ((size_t)4 * cap_r + D) * sizeof(float) +
-              sizeof(RowCounts));
+  return (size_t)kBwdWarps * bwd_warp_f4(cap_a, cap_r, D) * sizeof(float4);
 }
 
 static int warps_grid(long long rows, int warps_per_block, int nsm, int per_sm) {
@@ -827,7 +994,9 @@ static void fwd_t(long long rows, int nsm, cudaStream_t st, const SysDesc* sys, 
 template <int S, int ZSQ>
 static void bwd_t(long long rows, int nsm, cudaStream_t st, const EvalIO* io, const SysDesc* sys,
                   const DescParams& P, const Workspace& ws) {
-  k_aev_bwd<S, ZSQ><<<warps_grid(rows, 4, nsm, g_bwd_per_sm), 128, aev_bwd_smem(ws.cap_a, ws.cap_r, P.D),
+  long long g = (rows + kBwdWarps - 1) / kBwdWarps;
+  if (g > (long long)nsm * g_bwd_per_sm) g = (long long)nsm * g_bwd_per_sm;
+  k_aev_bwd<S, ZSQ><<<(int)(g < 1 ? 1 : g), 32 * kBwdWarps, aev_bwd_smem(ws.cap_a, ws.cap_r, P.D),
                       st>>>(io, sys, P, ws);
 }
 

@@ -8,8 +8,8 @@
 //   k_scan     bin counts -> row starts; species segments padded to 128 rows
 //   k_scatter  atom -> row (slot order, not yet deterministic)
 //   k_binsort  order each bin by input index; write the row arrays
-//   k_neighbors  warp per row: 27 neighbour cells x S species, lists grouped
-//                by neighbour species
+//   k_neighbors  warp per cell, lane per row: the 27-cell neighbourhood
+//                staged in shared memory; lists grouped by neighbour species
 #include "nnp_internal.cuh"
 
 namespace nnp {
@@ -139,6 +139,10 @@ __global__ void __launch_bounds__(1024) k_scan(const EvalIO* __restrict__ io, in
       ws.pos4[r] = make_float4(0.f, 0.f, 0.f, __int_as_float(s));
       ws.row_info[r] = 0;
       ws.row_cell[r] = 0;
+      for (int sp = 0; sp < kMaxS; ++sp) {
+        ws.cnt_r[(size_t)r * kMaxS + sp] = 0;
+        ws.cnt_a[(size_t)r * kMaxS + sp] = 0;
+      }
     }
   }
 }
@@ -192,127 +196,192 @@ __global__ void __launch_bounds__(256) k_binsort(const EvalIO* __restrict__ io, 
   }
 }
 
-// Warp per row.  Candidates: for each neighbour species s', the atoms of the
-// 27 virtual cells around the row's cell, flattened into one index space so
-// that all 32 lanes test candidates.  A candidate (j, image m) is kept if
-// |off_j - off_i + m*ell| < rc_r and it is not the atom itself.  Entries
-// within rc_a go straight to the row's list; radial-only entries wait in a
-// per-warp shared buffer and are appended after the species' angular ones.
-__global__ void __launch_bounds__(256) k_neighbors(const EvalIO* __restrict__ io,
-                                                   const SysDesc* __restrict__ sys,
-                                                   DescParams P, Workspace ws) {
-  __shared__ int s_start[8][32];
-  __shared__ int s_excl[8][33];
-  extern __shared__ int s_stage[];  // [8][cap_r]
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int* stage = s_stage + (size_t)w * ws.cap_r;
-  const int rows = ws.seg[P.S];
-  const int TC = io->total_cells;
+// Warp per cell (grid-stride over the cells of every system), lane per row
+// of the cell (in groups of 32).  For each neighbour species, the atoms of the
+// 27 virtual cells around the cell (periodic images by the virtual cell offset
+// m in {-1,0,1}^3) are staged in the warp's shared window as positions
+// relative to the cell's corner plus their list entry; every lane then walks
+// the window (a broadcast read) and tests its own row.  A candidate (j, m) is
+// kept if |off_j + m*ell - off_i| < rc_r and it is not the atom itself.
+// Within a species, entries inside rc_a go to the front of the row's
+// segment; radial-only entries are parked at the end of the row's list and
+// moved behind the angular ones once the species is done (their order is
+// free).  Counts are clamped to what the list holds, so readers never run
+// past it; the unclamped maxima raise the overflow flags (one update per
+// CTA).  Padding rows get zero counts from k_scan.
+__global__ void __launch_bounds__(kNbrThreads, 6) k_neighbors(const EvalIO* __restrict__ io,
+                                                          const SysDesc* __restrict__ sys,
+                                                          DescParams P, Workspace ws) {
+  constexpr unsigned F = 0xffffffffu;
+  __shared__ int s_mx[2];
+  extern __shared__ float4 s_dyn[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float4* cand = s_dyn + (size_t)wib * kNbrWin;
+  const int TC = io->total_cells, nsys = io->n_sys, S = P.S, cap = ws.cap_r;
   const float rcr2 = P.rc_r * P.rc_r, rca2 = P.rc_a * P.rc_a;
-  for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows;
-       row += (gridDim.x * blockDim.x) >> 5) {
-    int* cr = ws.cnt_r + (size_t)row * kMaxS;
-    int* ca = ws.cnt_a + (size_t)row * kMaxS;
-    if (ws.row_atom[row] < 0) {
-      if (lane < kMaxS) { cr[lane] = 0; ca[lane] = 0; }
-      continue;
+  int mx_r = 0, mx_a = 0;  // largest unclamped row counts seen by this lane
+  const int wpb = blockDim.x >> 5;
+  for (int g = blockIdx.x * wpb + wib; g < TC; g += gridDim.x * wpb) {
+    int lo = 0, hi = nsys - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (sys[mid].cell_base <= g) lo = mid; else hi = mid - 1;
     }
-    const float4 pi = ws.pos4[row];
-    const SysDesc& sd = sys[ws.row_info[row]];
-    const int pc = ws.row_cell[row];
-    const int cx = pc & 1023, cy = (pc >> 10) & 1023, cz = (pc >> 20) & 1023;
-    const float ell[3] = {sd.ellf[0], sd.ellf[1], sd.ellf[2]};
-    int* lr = ws.nbr_r + (size_t)row * ws.cap_r;
-    int nr = 0, na = 0;  // entries found so far (all species), may exceed capacity
-    for (int sp = 0; sp < P.S; ++sp) {
-      int len = 0, st = 0;
-      if (lane < 27) {
-        int v[3] = {cx + lane / 9 - 1, cy + (lane / 3) % 3 - 1, cz + lane % 3 - 1};
-        bool ok = true;
+    const SysDesc& sd = sys[lo];
+    const int nc0 = sd.nc[0], nc1 = sd.nc[1], nc2 = sd.nc[2];
+    const int lc = g - sd.cell_base;
+    const int cz = lc % nc2, cy = (lc / nc2) % nc1, cx = lc / (nc1 * nc2);
+    // rows of this cell: lane s < S holds species s's bin (first row, length)
+    int rst = 0, rln = 0;
+    if (lane < S) {
+      const int b = lane * TC + g;
+      rst = ws.bin_start[b];
+      rln = ws.bin_len[b];
+    }
+    int rpre = rln;  // inclusive prefix over species
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          if (v[c] < 0 || v[c] >= sd.nc[c]) {
-            if (sd.periodic) v[c] = (v[c] + sd.nc[c]) % sd.nc[c];
-            else ok = false;
+    for (int o = 1; o < kMaxS; o <<= 1) {
+      const int y = __shfl_up_sync(F, rpre, o);
+      if (lane >= o) rpre += y;
+    }
+    const int nrows = __shfl_sync(F, rpre, kMaxS - 1);
+    if (nrows == 0) continue;
+    // virtual cell v = lane (< 27): local index of the real cell, or -1 outside an open boundary
+    int vcell = -1;
+    if (lane < 27) {
+      int v[3] = {cx + lane / 9 - 1, cy + (lane / 3) % 3 - 1, cz + lane % 3 - 1};
+      const int ncv[3] = {nc0, nc1, nc2};
+      bool ok = true;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (v[c] < 0 || v[c] >= ncv[c]) {
+          if (sd.periodic) v[c] = (v[c] + ncv[c]) % ncv[c];
+          else ok = false;
+        }
+      }
+      if (ok) vcell = (v[0] * nc1 + v[1]) * nc2 + v[2];
+    }
+    const float ell0 = sd.ellf[0], ell1 = sd.ellf[1], ell2 = sd.ellf[2];
+    for (int r0 = 0; r0 < nrows; r0 += 32) {
+      const int q = r0 + lane;
+      const bool has = q < nrows;
+      int row = 0;
+#pragma unroll
+      for (int s = 0; s < kMaxS; ++s) {
+        const int inc = __shfl_sync(F, rpre, s), len = __shfl_sync(F, rln, s), st = __shfl_sync(F, rst, s);
+        if (q >= inc - len && q < inc) row = st + (q - (inc - len));
+      }
+      const float4 pi = has ? ws.pos4[row] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const int self = pack_nbr(row, 13);
+      int* lr = ws.nbr_r + (size_t)row * cap;
+      int nr = 0, tot_r = 0, tot_a = 0;  // written entries; all entries found
+      for (int sp = 0; sp < S; ++sp) {
+        int bst = 0, bln = 0;
+        if (vcell >= 0) {
+          const int b = sp * TC + sd.cell_base + vcell;
+          bst = ws.bin_start[b];
+          bln = ws.bin_len[b];
+        }
+        int incl = bln;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(F, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(F, incl, 31);
+        const int bex = incl - bln;
+        int wa = 0, wro = 0, ka = 0, kro = 0;  // written / found: angular, radial-only
+        for (int w0 = 0; w0 < total; w0 += kNbrWin) {
+          const int wn = min(kNbrWin, total - w0);
+          __syncwarp();  // the previous window has been read
+          for (int v = 0; v < 27; ++v) {
+            const int len_v = __shfl_sync(F, bln, v);
+            const int ex_v = __shfl_sync(F, bex, v), st_v = __shfl_sync(F, bst, v);
+            const int k0 = max(0, w0 - ex_v), k1 = min(len_v, w0 + wn - ex_v);
+            const float sx = (float)(v / 9 - 1) * ell0, sy = (float)((v / 3) % 3 - 1) * ell1,
+                        sz = (float)(v % 3 - 1) * ell2;
+            for (int k = k0 + lane; k < k1; k += 32) {
+              const float4 pj = ws.pos4[st_v + k];
+              cand[ex_v + k - w0] = make_float4(pj.x + sx, pj.y + sy, pj.z + sz,
+                                                __int_as_float(pack_nbr(st_v + k, v)));
+            }
+          }
+          __syncwarp();
+          if (has) {
+            // 32 candidates at a time: hit masks first (no branches), then the hits
+            for (int k0 = 0; k0 < wn; k0 += 32) {
+              unsigned hr = 0u, ha = 0u;
+#pragma unroll
+              for (int k = 0; k < 32; ++k) {
+                const float4 c = cand[k0 + k];  // past wn: stale window data, masked below
+                const float dx = c.x - pi.x, dy = c.y - pi.y, dz = c.z - pi.z;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                hr |= (r2 < rcr2 ? 1u : 0u) << k;
+                ha |= (r2 < rca2 ? 1u : 0u) << k;
+              }
+              if (wn - k0 < 32) hr &= (1u << (wn - k0)) - 1u;
+              while (hr) {
+                const int k = __ffs(hr) - 1;
+                hr &= hr - 1u;
+                const int e = __float_as_int(cand[k0 + k].w);
+                if (e == self) continue;
+                const bool room = nr + wa + wro < cap;
+                if ((ha >> k) & 1u) {
+                  if (room) lr[nr + wa++] = e;
+                  ++ka;
+                } else {
+                  if (room) lr[cap - 1 - wro++] = e;
+                  ++kro;
+                }
+              }
+            }
           }
         }
-        if (ok) {
-          const int bin = sp * TC + sd.cell_base + (v[0] * sd.nc[1] + v[1]) * sd.nc[2] + v[2];
-          st = ws.bin_start[bin];
-          len = ws.bin_len[bin];
+        if (has) {
+          // bring the parked radial-only entries down behind the angular ones
+          const int m = min(wro, cap - wro - (nr + wa));
+          for (int k = 0; k < m; ++k) lr[nr + wa + k] = lr[cap - 1 - k];
+          ws.cnt_r[(size_t)row * kMaxS + sp] = wa + wro;
+          ws.cnt_a[(size_t)row * kMaxS + sp] = wa;
         }
+        nr += wa + wro;
+        tot_r += ka + kro;
+        tot_a += ka;
       }
-      int incl = len;
+      if (has) {
+        for (int sp = S; sp < kMaxS; ++sp) {
+          ws.cnt_r[(size_t)row * kMaxS + sp] = 0;
+          ws.cnt_a[(size_t)row * kMaxS + sp] = 0;
+        }
+        mx_r = max(mx_r, tot_r);
+        mx_a = max(mx_a, tot_a);
+      }
+    }
+  }
+  if (threadIdx.x == 0) { s_mx[0] = 0; s_mx[1] = 0; }
+  __syncthreads();
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      const int total = __shfl_sync(0xffffffffu, incl, 31);
-      s_start[w][lane] = st;
-      s_excl[w][lane] = incl - len;
-      if (lane == 31) s_excl[w][32] = total;
-      __syncwarp();
-      int n_ang = 0, n_ro = 0;  // this species: angular entries, radial-only entries
-      for (int t0 = 0; t0 < total; t0 += 32) {
-        const int t = t0 + lane;
-        bool is_a = false, is_ro = false;
-        int entry = 0;
-        if (t < total) {
-          int lo = 0, hi = 26;
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_excl[w][mid] <= t) lo = mid; else hi = mid - 1;
-          }
-          const int j = s_start[w][lo] + (t - s_excl[w][lo]);
-          const float4 pj = ws.pos4[j];
-          const float dx = (pj.x - pi.x) + (float)(lo / 9 - 1) * ell[0];
-          const float dy = (pj.y - pi.y) + (float)((lo / 3) % 3 - 1) * ell[1];
-          const float dz = (pj.z - pi.z) + (float)(lo % 3 - 1) * ell[2];
-          const float r2 = dx * dx + dy * dy + dz * dz;
-          const bool is_r = r2 < rcr2 && !(j == row && lo == 13);
-          is_a = is_r && r2 < rca2;
-          is_ro = is_r && !is_a;
-          entry = pack_nbr(j, lo);
-        }
-        const unsigned ba = __ballot_sync(0xffffffffu, is_a);
-        const unsigned bro = __ballot_sync(0xffffffffu, is_ro);
-        const unsigned below = (1u << lane) - 1u;
-        if (is_a) {
-          const int pos = nr + n_ang + __popc(ba & below);
-          if (pos < ws.cap_r) lr[pos] = entry;
-        }
-        if (is_ro) {
-          const int pos = n_ro + __popc(bro & below);
-          if (pos < ws.cap_r) stage[pos] = entry;
-        }
-        n_ang += __popc(ba);
-        n_ro += __popc(bro);
-      }
-      __syncwarp();
-      // append the radial-only entries after this species' angular ones
-      const int base = nr + n_ang;
-      for (int k = lane; k < n_ro; k += 32)
-        if (base + k < ws.cap_r && k < ws.cap_r) lr[base + k] = stage[k];
-      __syncwarp();
-      // counts clamped to what the list holds, so readers never run past it
-      const int keep = max(0, min(n_ang + n_ro, ws.cap_r - nr));
-      const int keep_a = min(n_ang, keep);
-      if (lane == 0) { cr[sp] = keep; ca[sp] = keep_a; }
-      nr += n_ang + n_ro;
-      na += n_ang;
-    }
-    if (lane == 0) {
-      for (int sp = P.S; sp < kMaxS; ++sp) { cr[sp] = 0; ca[sp] = 0; }
-      atomicMax(&ws.flags[kFlagMaxNbrR], nr);
-      atomicMax(&ws.flags[kFlagMaxNbrA], na);
-      if (nr > ws.cap_r) atomicOr(&ws.flags[kFlagOverflowR], 1);
-      if (na > ws.cap_a) atomicOr(&ws.flags[kFlagOverflowA], 1);
-    }
+  for (int o = 16; o; o >>= 1) {
+    mx_r = max(mx_r, __shfl_xor_sync(F, mx_r, o));
+    mx_a = max(mx_a, __shfl_xor_sync(F, mx_a, o));
+  }
+  if (lane == 0) {
+    atomicMax(&s_mx[0], mx_r);
+    atomicMax(&s_mx[1], mx_a);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && (s_mx[0] | s_mx[1])) {
+    atomicMax(&ws.flags[kFlagMaxNbrR], s_mx[0]);
+    atomicMax(&ws.flags[kFlagMaxNbrA], s_mx[1]);
+    if (s_mx[0] > ws.cap_r) atomicOr(&ws.flags[kFlagOverflowR], 1);
+    if (s_mx[1] > ws.cap_a) atomicOr(&ws.flags[kFlagOverflowA], 1);
   }
 }
 
-size_t neighbors_smem(int cap_r) { return 8 * sizeof(int) * (size_t)cap_r; }
+size_t neighbors_smem(int cap_r) {
+  (void)cap_r;
+  return sizeof(float4) * kNbrWin * (kNbrThreads / 32);
+}
 
 cudaError_t neighbors_set_smem_limits() {
   return cudaFuncSetAttribute(k_neighbors, cudaFuncAttributeMaxDynamicSharedMemorySize,

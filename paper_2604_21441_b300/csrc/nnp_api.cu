@@ -158,7 +158,7 @@ int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows,
   const Workspace w = workspace();
   const int nsm = num_sms;
   const int g_atoms = grid_for(n, 256, nsm * 8);
-  const int g_rows = grid_for(rows * 32, 256, nsm * tune.nbr);
+  const int g_cells = grid_for(total_cells, kNbrThreads / 32, nsm * tune.nbr);
   const int g_bins = grid_for(bins * 32, 256, nsm * 16);
   const EvalIO* io = d_io;
   const SysDesc* sys = b_sys;
@@ -173,7 +173,7 @@ int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows,
   k_binsort<<<g_bins, 256, 0, stream>>>(io, P.S, (cfg.flags & NNP_FLAG_NONDETERMINISTIC_BINS) ? 0 : 1,
                                         w); ++launches;
   mark_stage(1, capturing);
-  k_neighbors<<<g_rows, 256, neighbors_smem(cap_r), stream>>>(io, sys, P, w); ++launches;
+  k_neighbors<<<g_cells, kNbrThreads, neighbors_smem(cap_r), stream>>>(io, sys, P, w); ++launches;
   mark_stage(2, capturing);
   if (calib) {  // FP8 calibration: FP32 descriptor, then the activation ranges
     launch_aev_fwd(rows, nsm, stream, sys, P, w, kGFp32, tune.fwd);
@@ -417,7 +417,8 @@ int nnp_ctx::check_flags() {
   if (f[kFlagOverflowR] || f[kFlagOverflowA]) {
     if (f[kFlagOverflowR]) cap_r = ((int)(f[kFlagMaxNbrR] * 1.25) + 31) / 32 * 32;
     if (f[kFlagOverflowA]) cap_a = ((int)(f[kFlagMaxNbrA] * 1.25) + 15) / 16 * 16;
-    if (cap_r > 4096 || cap_a > 1024)
+    // the descriptor backward parks every angular pair of a row in shared memory
+    if (cap_r > 4096 || cap_a > kMaxCapA)
       return fail(NNP_ERR_CAPACITY, "neighbour counts too large (%d radial, %d angular)",
                   f[kFlagMaxNbrR], f[kFlagMaxNbrA]);
     invalidate_graph();

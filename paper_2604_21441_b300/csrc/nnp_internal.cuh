@@ -31,6 +31,9 @@ constexpr int kNAng = kNAngR * kNAngZ;  // 32 features per species pair
 constexpr int kH1 = 160, kH2 = 128, kH3 = 96;
 constexpr int kMaxS = 4;       // species supported by the kernels
 constexpr int kTileRows = 128; // species segments are padded to this
+constexpr int kMaxCapA = 64;     // largest angular-neighbour capacity (staged per row)
+constexpr int kNbrThreads = 128;  // k_neighbors: warp per cell, lane per row
+constexpr int kNbrWin = 512;      // neighbourhood atoms one warp stages per window
 constexpr int kMaxD = kNRad * kMaxS + kNAng * kMaxS * (kMaxS + 1) / 2;  // 384
 
 // Error flag words (device): set by kernels, read by the host after sync.

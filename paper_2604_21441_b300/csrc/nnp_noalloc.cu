@@ -202,7 +202,7 @@ extern "C" int nnp_eval_noalloc(nnp_ctx* ctx, int64_t n, const double* pos, cons
   const DescParams& P = ctx->P;
   const int nsm = ctx->num_sms;
   const int g_atoms = grid_cap(n, 256, nsm * 8);
-  const int g_rows = grid_cap(rows * 32, 256, nsm * 16);
+  const int g_cells = grid_cap(bins / P.S, kNbrThreads / 32, nsm * 16);
   const int g_bins = grid_cap(bins * 32, 256, nsm * 16);
   const int g_tiles = (int)((rows / 64) < nsm ? (rows / 64) : nsm);
   int hflags[kNumFlags];
@@ -221,7 +221,7 @@ extern "C" int nnp_eval_noalloc(nnp_ctx* ctx, int64_t n, const double* pos, cons
   k_scan<<<1, 1024, 0, st>>>(d_io, P.S, w);
   k_scatter<<<g_atoms, 256, 0, st>>>(d_io, w);
   k_binsort<<<g_bins, 256, 0, st>>>(d_io, P.S, 1, w);
-  k_neighbors<<<g_rows, 256, neighbors_smem(w.cap_r), st>>>(d_io, d_sys, P, w);
+  k_neighbors<<<g_cells, kNbrThreads, neighbors_smem(w.cap_r), st>>>(d_io, d_sys, P, w);
   launch_aev_fwd(rows, nsm, st, d_sys, P, w, 0);
   launch_mlp_f32(g_tiles > 0 ? g_tiles : 1, st, d_io, P, w, ctx->wf32);
   launch_aev_bwd(rows, nsm, st, d_io, d_sys, P, w);
