@@ -157,6 +157,54 @@ __device__ __forceinline__ void map_pair(const PairMap& m, int t, int& u, int& v
   }
 }
 
+// packed FP32 pair (fma/mul.rn.f32x2: one instruction for two lanes of arithmetic)
+struct f2 {
+  unsigned long long v;
+};
+__device__ __forceinline__ f2 f2_make(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 f2_split(f2 x) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(x.v));
+  return r;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+// 2^x (MUFU; results below the normal range flush to zero)
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ f2 f2_ex2(f2 x) {
+  const float2 h = f2_split(x);
+  return f2_make(ex2(h.x), ex2(h.y));
+}
+
+// q = t / n for 0 <= t < 2^22 (float reciprocal, one correction step)
+__device__ __forceinline__ int div_small(int t, int n, float inv) {
+  int q = (int)(((float)t + 0.5f) * inv);
+  if (q * n > t) --q;
+  else if ((q + 1) * n <= t) ++q;
+  return q;
+}
+
 __device__ __forceinline__ float4 shift_vec(int code, const float* ell) {
   const int mx = code / 9 - 1, my = (code / 3) % 3 - 1, mz = code % 3 - 1;
   return make_float4(mx * ell[0], my * ell[1], mz * ell[2], 0.f);
@@ -192,20 +240,28 @@ __device__ __forceinline__ void load_counts(const Workspace& ws, int S, int row,
 // forward
 
 template <int S, int ZSQ>
-__global__ void __launch_bounds__(256) k_aev_fwd(const SysDesc* __restrict__ sys, DescParams P,
+__global__ void __launch_bounds__(256, 2) k_aev_fwd(const SysDesc* __restrict__ sys, DescParams P,
                                                  Workspace ws, int mode) {
   constexpr int D = kNRad * S + kNAng * S * (S + 1) / 2;
   extern __shared__ float4 sm4[];
   const int lane = threadIdx.x & 31, hl = lane & 15, half = lane >> 4;
   const int hwb = threadIdx.x >> 4;  // half warp in block, 0..15
-  const int ca = ws.cap_a;
-  float4* geo = sm4 + (size_t)hwb * (ca + 27);
+  const int ca = ws.cap_a, cr = ws.cap_r;
+  float4* geo = sm4 + (size_t)hwb * (ca + 27 + cr);
   float4* sh = geo + ca;
-  float* fcs = reinterpret_cast<float*>(sm4 + 16 * (size_t)(ca + 27)) + (size_t)hwb * ca;
-  RowCounts* rc = reinterpret_cast<RowCounts*>(reinterpret_cast<float*>(sm4 + 16 * (size_t)(ca + 27)) +
+  float4* rad = sh + 27;  // [cr]: displacement and r^2 of every radial neighbour
+  float* fcs = reinterpret_cast<float*>(sm4 + 16 * (size_t)(ca + 27 + cr)) + (size_t)hwb * ca;
+  RowCounts* rc = reinterpret_cast<RowCounts*>(reinterpret_cast<float*>(sm4 + 16 * (size_t)(ca + 27 + cr)) +
                                                16 * (size_t)ca) + hwb;
   const float kr = -P.eta_r * kLog2e, ka = -P.eta_a * kLog2e;
   const float kfr = kPi / (2.f * P.rc_r), kfa = kPi / (2.f * P.rc_a);
+  f2 hc2[4], hs2[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    hc2[q] = f2_make(P.hcos_z[2 * q], P.hcos_z[2 * q + 1]);
+    hs2[q] = f2_make(P.hsin_z[2 * q], P.hsin_z[2 * q + 1]);
+  }
+  const f2 half2 = f2_make(0.5f, 0.5f), kr2 = f2_make(kr, kr);
   const int rows = ws.seg[S];
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -250,32 +306,48 @@ __global__ void __launch_bounds__(256) k_aev_fwd(const SysDesc* __restrict__ sys
     load_counts(ws, S, row, live, ca, rc, hl);
     __syncwarp();
     const int* lr = ws.nbr_r + (size_t)row * ws.cap_r;
+    // gather every radial neighbour once (independent loads, all in flight)
+    {
+      const int ntot = rc->orr[S - 1] + rc->nr[S - 1];
+#pragma unroll 4
+      for (int k = hl; k < ntot; k += 16) {
+        const int e = lr[k];
+        const float4 pj = ws.pos4[nbr_row(e)];
+        const float4 sv = sh[nbr_code(e)];
+        const float dx = (pj.x - pi.x) + sv.x, dy = (pj.y - pi.y) + sv.y, dz = (pj.z - pi.z) + sv.z;
+        rad[k] = make_float4(dx, dy, dz, dx * dx + dy * dy + dz * dz);
+      }
+    }
+    __syncwarp();
 
     // ---------------- radial
 #pragma unroll 1
     for (int s = 0; s < S; ++s) {
       const int n_s = rc->nr[s], o_s = rc->orr[s];
       const int nmax = max(n_s, __shfl_xor_sync(0xffffffffu, n_s, 16));
-      float acc[kNRad];
+      f2 acc2[kNRad / 2];
 #pragma unroll
-      for (int m = 0; m < kNRad; ++m) acc[m] = 0.f;
+      for (int m = 0; m < kNRad / 2; ++m) acc2[m] = f2_make(0.f, 0.f);
       for (int k0 = 0; k0 < nmax; k0 += 16) {
         const int k = k0 + hl;
         if (k < n_s) {
-          const int e = lr[o_s + k];
-          const float4 pj = ws.pos4[nbr_row(e)];
-          const float4 sv = sh[nbr_code(e)];
-          const float dx = (pj.x - pi.x) + sv.x, dy = (pj.y - pi.y) + sv.y, dz = (pj.z - pi.z) + sv.z;
-          const float r = sqrtf(dx * dx + dy * dy + dz * dz);
+          const float r = sqrtf(rad[o_s + k].w);
           float fc, dfc;
           cutoff(r, P.rc_r, kfr, fc, dfc);
-          const float f = 0.25f * fc;
+          const f2 f = f2_make(0.25f * fc, 0.25f * fc), rr = f2_make(r, r);
 #pragma unroll
-          for (int m = 0; m < kNRad; ++m) {
-            const float x = r - P.shf_r[m];
-            acc[m] = fmaf(f, exp2f(kr * x * x), acc[m]);
+          for (int m = 0; m < kNRad / 2; ++m) {
+            const f2 x = f2_add(rr, f2_make(-P.shf_r[2 * m], -P.shf_r[2 * m + 1]));
+            acc2[m] = f2_fma(f, f2_ex2(f2_mul(kr2, f2_mul(x, x))), acc2[m]);
           }
         }
+      }
+      float acc[kNRad];
+#pragma unroll
+      for (int m = 0; m < kNRad / 2; ++m) {
+        const float2 h = f2_split(acc2[m]);
+        acc[2 * m] = h.x;
+        acc[2 * m + 1] = h.y;
       }
       hw_reduce_scatter<kNRad>(acc, hl);
       if (live) put1(s * kNRad + hl, acc[0]);
@@ -286,11 +358,8 @@ __global__ void __launch_bounds__(256) k_aev_fwd(const SysDesc* __restrict__ sys
     for (int s = 0; s < S; ++s) {
       const int n_a = rc->na[s], o_r = rc->orr[s], o_a = rc->oa[s];
       for (int k = hl; k < n_a; k += 16) {
-        const int e = lr[o_r + k];
-        const float4 pj = ws.pos4[nbr_row(e)];
-        const float4 sv = sh[nbr_code(e)];
-        const float dx = (pj.x - pi.x) + sv.x, dy = (pj.y - pi.y) + sv.y, dz = (pj.z - pi.z) + sv.z;
-        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float4 d = rad[o_r + k];
+        const float dx = d.x, dy = d.y, dz = d.z, r2 = d.w;
         const float ir = rsqrtf(r2);
         const float r = r2 * ir;
         float fc, dfc;
@@ -314,9 +383,11 @@ __global__ void __launch_bounds__(256) k_aev_fwd(const SysDesc* __restrict__ sys
           continue;
         }
         const PairMap pm = make_map(diag, n1, n2, rc->oa[s1], rc->oa[s2]);
-        float acc[kNAng];
+        f2 acc2[kNAngR][kNAngZ / 2];
 #pragma unroll
-        for (int q = 0; q < kNAng; ++q) acc[q] = 0.f;
+        for (int a = 0; a < kNAngR; ++a)
+#pragma unroll
+          for (int zp = 0; zp < kNAngZ / 2; ++zp) acc2[a][zp] = f2_make(0.f, 0.f);
         for (int t0 = 0; t0 < Tmax; t0 += 16) {
           const int t = t0 + hl;
           if (t < T) {
@@ -328,21 +399,37 @@ __global__ void __launch_bounds__(256) k_aev_fwd(const SysDesc* __restrict__ sys
             const float sn = sqrtf(fmaxf(1.f - uc * uc, 0.f));
             const float fp = fcs[u] * fcs[v];
             const float rbar = 0.5f * (gu.w + gv.w);
-            float B[kNAngR];
+            f2 B2[kNAngR];
 #pragma unroll
             for (int a = 0; a < kNAngR; ++a) {
               const float x = rbar - P.shf_a[a];
-              B[a] = fp * exp2f(ka * x * x);
+              const float Bv = fp * ex2(ka * x * x);
+              B2[a] = f2_make(Bv, Bv);
             }
+            const f2 uc2 = f2_make(uc, uc), sn2 = f2_make(sn, sn);
 #pragma unroll
-            for (int z = 0; z < kNAngZ; ++z) {
-              const float base = fmaf(sn, P.hsin_z[z], fmaf(uc, P.hcos_z[z], 0.5f));
-              const float A = pow_zeta1<ZSQ>(base, P.zeta_sq);
+            for (int zp = 0; zp < kNAngZ / 2; ++zp) {
+              f2 bz = f2_fma(sn2, hs2[zp], f2_fma(uc2, hc2[zp], half2));
+              if (ZSQ >= 0) {
 #pragma unroll
-              for (int a = 0; a < kNAngR; ++a) acc[a * kNAngZ + z] = fmaf(A, B[a], acc[a * kNAngZ + z]);
+                for (int i = 0; i < (ZSQ >= 0 ? ZSQ : 0); ++i) bz = f2_mul(bz, bz);
+              } else {
+                for (int i = 0; i < P.zeta_sq; ++i) bz = f2_mul(bz, bz);
+              }
+#pragma unroll
+              for (int a = 0; a < kNAngR; ++a) acc2[a][zp] = f2_fma(B2[a], bz, acc2[a][zp]);
             }
           }
         }
+        float acc[kNAng];
+#pragma unroll
+        for (int a = 0; a < kNAngR; ++a)
+#pragma unroll
+          for (int zp = 0; zp < kNAngZ / 2; ++zp) {
+            const float2 h = f2_split(acc2[a][zp]);
+            acc[a * kNAngZ + 2 * zp] = h.x;
+            acc[a * kNAngZ + 2 * zp + 1] = h.y;
+          }
         hw_reduce_scatter<kNAng>(acc, hl);
         if (live) put2(f0, 2.f * acc[0], 2.f * acc[1]);
       }
@@ -377,46 +464,6 @@ __global__ void __launch_bounds__(256) k_aev_fwd(const SysDesc* __restrict__ sys
 
 namespace {
 
-// packed FP32 pair (fma/mul.rn.f32x2: one instruction for two lanes of arithmetic)
-struct f2 {
-  unsigned long long v;
-};
-__device__ __forceinline__ f2 f2_make(float a, float b) {
-  f2 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ float2 f2_split(f2 x) {
-  float2 r;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(x.v));
-  return r;
-}
-__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
-  f2 r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
-  return r;
-}
-__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
-  f2 r;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
-  return r;
-}
-__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
-  f2 r;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
-  return r;
-}
-// 2^x (MUFU; results below the normal range flush to zero)
-__device__ __forceinline__ float ex2(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ f2 f2_ex2(f2 x) {
-  const float2 h = f2_split(x);
-  return f2_make(ex2(h.x), ex2(h.y));
-}
-
 // One species-pair block of a row's angular pairs (per-warp table in shared memory).
 struct PairBlock {
   int base, T;      // first flat index, pairs
@@ -428,13 +475,6 @@ struct PairBlock {
   float inv;        // 1 / n (diagonal) or 1 / ma (off-diagonal)
 };
 
-// q = t / n for 0 <= t < 2^22 (float reciprocal, one correction step)
-__device__ __forceinline__ int div_small(int t, int n, float inv) {
-  int q = (int)(((float)t + 0.5f) * inv);
-  if (q * n > t) --q;
-  else if ((q + 1) * n <= t) ++q;
-  return q;
-}
 
 }  // namespace
 
@@ -968,8 +1008,8 @@ static void jvp_t(long long rows, int nsm, cudaStream_t st, const SysDesc* sys, 
 // --------------------------------------------------------------------------
 // launchers
 
-size_t aev_fwd_smem(int cap_a) {
-  return 16 * ((size_t)(cap_a + 27) * sizeof(float4) + (size_t)cap_a * sizeof(float) + sizeof(RowCounts));
+size_t aev_fwd_smem(int cap_a, int cap_r) {
+  return 16 * ((size_t)(cap_a + 27 + cap_r) * sizeof(float4) + (size_t)cap_a * sizeof(float) + sizeof(RowCounts));
 }
 size_t aev_bwd_smem(int cap_a, int cap_r, int D) {
   return (size_t)kBwdWarps * bwd_warp_f4(cap_a, cap_r, D) * sizeof(float4);
@@ -988,7 +1028,7 @@ static int g_fwd_per_sm = 8, g_bwd_per_sm = 16;  // set per launch by the caller
 template <int S, int ZSQ>
 static void fwd_t(long long rows, int nsm, cudaStream_t st, const SysDesc* sys, const DescParams& P,
                   const Workspace& ws, int mode) {
-  k_aev_fwd<S, ZSQ><<<warps_grid(rows, 8, nsm, g_fwd_per_sm), 256, aev_fwd_smem(ws.cap_a), st>>>(sys, P, ws,
+  k_aev_fwd<S, ZSQ><<<warps_grid(rows, 8, nsm, g_fwd_per_sm), 256, aev_fwd_smem(ws.cap_a, ws.cap_r), st>>>(sys, P, ws,
                                                                                                   mode);
 }
 template <int S, int ZSQ>

@@ -418,7 +418,7 @@ int nnp_ctx::check_flags() {
     if (f[kFlagOverflowR]) cap_r = ((int)(f[kFlagMaxNbrR] * 1.25) + 31) / 32 * 32;
     if (f[kFlagOverflowA]) cap_a = ((int)(f[kFlagMaxNbrA] * 1.25) + 15) / 16 * 16;
     // the descriptor backward parks every angular pair of a row in shared memory
-    if (cap_r > 4096 || cap_a > kMaxCapA)
+    if (cap_r > kMaxCapR || cap_a > kMaxCapA)
       return fail(NNP_ERR_CAPACITY, "neighbour counts too large (%d radial, %d angular)",
                   f[kFlagMaxNbrR], f[kFlagMaxNbrA]);
     invalidate_graph();
