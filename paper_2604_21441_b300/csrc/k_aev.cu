@@ -464,6 +464,12 @@ __global__ void __launch_bounds__(256, 2) k_aev_fwd(const SysDesc* __restrict__ 
 
 namespace {
 
+// acc.xyz += (x, y, z): one vector reduction in global memory (L2)
+__device__ __forceinline__ void red_add_f3(float4* acc, float x, float y, float z) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(acc), "f"(x), "f"(y), "f"(z), "f"(0.f)
+               : "memory");
+}
+
 // One species-pair block of a row's angular pairs (per-warp table in shared memory).
 struct PairBlock {
   int base, T;      // first flat index, pairs
@@ -520,7 +526,6 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
     ks2[q] = f2_make(-0.95f * zeta * P.hsin_z[2 * q], -0.95f * zeta * P.hsin_z[2 * q + 1]);
   }
   const f2 half2 = f2_make(0.5f, 0.5f);
-  double* F = io->forces;
   const int rows = ws.seg[S];
   const int wpb = blockDim.x >> 5;
   int cached_sys = -1;
@@ -783,25 +788,29 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
     }
     __syncwarp();
 
-    // ---------------- (4) one FP64 add per neighbour slot and component
-    for (int k = lane; k < ntot; k += 32) {
-      const int oj = origs[k];
-      atomicAdd(&F[3 * oj], (double)fsl[3 * k]);
-      atomicAdd(&F[3 * oj + 1], (double)fsl[3 * k + 1]);
-      atomicAdd(&F[3 * oj + 2], (double)fsl[3 * k + 2]);
-    }
+    // ---------------- (4) one vector reduction per neighbour slot
+    for (int k = lane; k < ntot; k += 32)
+      red_add_f3(ws.facc + origs[k], fsl[3 * k], fsl[3 * k + 1], fsl[3 * k + 2]);
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
       fix += __shfl_xor_sync(FM, fix, o);
       fiy += __shfl_xor_sync(FM, fiy, o);
       fiz += __shfl_xor_sync(FM, fiz, o);
     }
-    if (lane == 0) {
-      const int oi = pos4_orig(pi);
-      atomicAdd(&F[3 * oi], (double)fix);
-      atomicAdd(&F[3 * oi + 1], (double)fiy);
-      atomicAdd(&F[3 * oi + 2], (double)fiz);
-    }
+    if (lane == 0) red_add_f3(ws.facc + pos4_orig(pi), fix, fiy, fiz);
+  }
+}
+
+// FP32 accumulators -> the caller's FP64 forces (input order).
+__global__ void k_forces_out(const EvalIO* __restrict__ io, Workspace ws) {
+  const long long n = io->n_atoms;
+  double* F = io->forces;
+  for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < n;
+       a += (long long)gridDim.x * blockDim.x) {
+    const float4 f = ws.facc[a];
+    F[3 * a] = (double)f.x;
+    F[3 * a + 1] = (double)f.y;
+    F[3 * a + 2] = (double)f.z;
   }
 }
 
@@ -1062,6 +1071,9 @@ void launch_aev_bwd(long long rows, int nsm, cudaStream_t st, const EvalIO* io, 
     case 3: z5 ? bwd_t<3, 5>(rows, nsm, st, io, sys, P, ws) : bwd_t<3, -1>(rows, nsm, st, io, sys, P, ws); break;
     default: z5 ? bwd_t<4, 5>(rows, nsm, st, io, sys, P, ws) : bwd_t<4, -1>(rows, nsm, st, io, sys, P, ws); break;
   }
+  long long g = (rows + 255) / 256;
+  if (g > (long long)nsm * 4) g = (long long)nsm * 4;
+  k_forces_out<<<(int)(g < 1 ? 1 : g), 256, 0, st>>>(io, ws);
 }
 
 template <class K>

@@ -32,14 +32,17 @@ def test_batch_256(oracle_mod):
     E, F = E.cpu().numpy(), F.cpu().numpy()
     assert pot.query("tune_backward") in (4, 8, 16, 32)
     # every system against its own single-system evaluation: the same kernels
-    # on the same neighbour lists; only the grouping of FP32 per-warp energy
-    # partial sums differs (rows of a system start at other warp offsets)
+    # on the same neighbour lists; only the order of the FP32 sums differs
+    # (energy partial sums per warp start at other row offsets; forces are
+    # accumulated by FP32 atomic reductions in launch order).  Force sums
+    # run over ~10^2 terms of up to ~1 eV/A, so 1e-5 eV/A bounds their
+    # rounding with margin (the parity bound against the oracle is 1e-4).
     single = P.NNP(atomic_numbers=(1, 8), max_atoms=int(max(s.n for s in systems)))
     single.set_all_weights(w32)
     for b, s in enumerate(systems):
         e1, f1 = single.eval(s.pos, s.Z, s.box)
         assert abs(E[b] - e1) <= 1e-7 * (abs(e1) + s.n), b
-        assert np.abs(F[off[b]:off[b + 1]] - f1).max() <= 1e-8, b
+        assert np.abs(F[off[b]:off[b + 1]] - f1).max() <= 1e-5, b
     # sampled systems against the oracle
     p = oracle_mod.Params()
     m = oracle_mod.Model(p, w)

@@ -74,8 +74,8 @@ def test_fp8_calibration_state(P):
     E1, F1 = pot.eval(s.pos, s.Z, box9(s.box))
     assert pot.query("fp8_calibrated") == 1
     E2, F2 = pot.eval(s.pos, s.Z, box9(s.box))
-    # same scales: equal up to the order of the FP64 atomic sums
-    assert abs(E2 - E1) <= 1e-9 * abs(E1) and np.abs(F2 - F1).max() <= 1e-9
+    # same scales: equal up to the order of the atomic sums (FP64 energies, FP32 forces)
+    assert abs(E2 - E1) <= 1e-9 * abs(E1) and np.abs(F2 - F1).max() <= 1e-5
     pot.set_all_weights([[(W.astype(np.float32), b.astype(np.float32)) for W, b in sp] for sp in w])
     assert pot.query("fp8_calibrated") == 0
     E3, F3 = pot.eval(s.pos, s.Z, box9(s.box))
