@@ -6,9 +6,9 @@
 //   z_l = h_{l-1} W_l + b_l, h_l = CELU(z_l), E_i = h_3 w_4 + b_4
 //   g_3 = w_4 * CELU'(z_3), g_{l-1} = (g_l W_l^T) * CELU'(z_{l-1}), dE/dG = g_1 W_1^T
 //
-// One CTA (8 warps) per SM, persistent over 128-row tiles (one species per
-// tile).  Row r of a tile is TMEM lane r; warps w and w+4 share the lanes of
-// quarter w and split each epilogue's 16-column chunks.  Thread 0 issues the
+// One CTA (16 warps) per SM, persistent over 128-row tiles (one species per
+// tile).  Row r of a tile is TMEM lane r; warps w, w+4, w+8 and w+12 share the
+// lanes of quarter w and split each epilogue's 16-column chunks.  Thread 0 issues the
 // bulk (TMA) copies and the MMAs; all threads run the epilogues, reading
 // biases from shared memory and keeping two TMEM loads in flight.
 // Shared memory holds three activation buffers and two weight buffers, every
@@ -19,9 +19,12 @@
 // streams in while the current layer runs.
 //
 // TMEM columns (512 allocated): z1 [0,160)  z2 [160,288)  z3 [288,384)
-// g2' [384,512)  g1' [160,320)  dE/dG [0, D).  CELU' comes from the FP32
-// pre-activations kept in TMEM, so the backward does not lose precision to
-// the BF16 activations.
+// g2' [384,512)  g1' [160,320)  dE/dG [384, 384 + D).  The forward epilogues
+// overwrite z1 and z2 with CELU'(z1), CELU'(z2) in FP32, which the backward
+// epilogues multiply in; the backward does not lose precision to the BF16
+// activations and does not evaluate the exponential again.  Because dE/dG
+// sits above column 384, the next tile's layer-1 MMA (into [0,160)) is issued
+// as soon as this tile's last MMA is done and runs under the dE/dG epilogue.
 //
 // FP8 form: the three forward GEMMs take E4M3 operands (kind::f8f6f4, twice
 // the BF16 rate) with static scales: activations x_q = x / s_x with one s_x
@@ -45,6 +48,8 @@ namespace nnp {
 namespace {
 
 constexpr int kTM = 128;                 // rows per tile (MMA M)
+constexpr int kTcThreads = 512;          // 16 warps: 4 per TMEM lane quarter
+constexpr int kG = kTcThreads / 128;     // column groups of the epilogues
 constexpr int kSlab = kTM * 128;         // bytes of one 64-column slab
 constexpr uint32_t kTmemCols = 512;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any wait
@@ -82,6 +87,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 // Wait for the phase of the given parity; false after kWaitNs nanoseconds.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int i = 0; i < 64; ++i)  // short waits without reading the timer
+    if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   while (!mbar_try(bar, parity))
     if (global_ns() - t0 > kWaitNs) return false;
@@ -183,10 +190,17 @@ __device__ __forceinline__ void issue_gemm(uint32_t d_tmem, const uint8_t* A, co
 }
 
 // CELU and its derivative; k = log2(e) / alpha, so exp(z / alpha) = exp2(k z).
-__device__ __forceinline__ float celu_f(float z, float al, float k) {
-  return z > 0.f ? z : al * (exp2f(z * k) - 1.f);
+// 2^x on the MUFU unit; results below the normal range flush to zero, which
+// moves CELU(z) = alpha (e^(z/alpha) - 1) by less than alpha 2^-126.
+__device__ __forceinline__ float ex2f(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
-__device__ __forceinline__ float dcelu_f(float z, float k) { return z > 0.f ? 1.f : exp2f(z * k); }
+__device__ __forceinline__ float celu_f(float z, float al, float k) {
+  return z > 0.f ? z : al * (ex2f(z * k) - 1.f);
+}
+__device__ __forceinline__ float dcelu_f(float z, float k) { return z > 0.f ? 1.f : ex2f(z * k); }
 
 // Store 16 values of row r, columns [c0, c0+16), as BF16 into a swizzled buffer.
 __device__ __forceinline__ void store_row16(uint8_t* buf, int r, int c0, const float (&v)[16]) {
@@ -260,17 +274,31 @@ __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[1
       : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// Store 16 columns of the warp's 32 lanes to TMEM (completion: tmem_wait_st).
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+      "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+      "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-// Epilogue skeleton: the warp's half h handles 16-column chunks h, h+2, ...;
-// two chunks are loaded from TMEM per wait.  f(chunk_col0, values[16]).
+// Epilogue skeleton: the warp's column group h handles 16-column chunks
+// h, h + kG, ...; two chunks are loaded from TMEM per wait.
+// f(chunk_col0, values[16]).
 template <int N, class F>
 __device__ __forceinline__ void for_chunks(uint32_t tcol, int h, F f) {
   constexpr int NCH = N / 16;
-  for (int c = h; c < NCH; c += 4) {
+  for (int c = h; c < NCH; c += 2 * kG) {
     uint32_t a[16], b[16];
-    const bool two = c + 2 < NCH;
+    const bool two = c + kG < NCH;
     tmem_ld16_nowait(tcol + c * 16, a);
-    if (two) tmem_ld16_nowait(tcol + (c + 2) * 16, b);
+    if (two) tmem_ld16_nowait(tcol + (c + kG) * 16, b);
     tmem_wait_ld();
     float v[16];
 #pragma unroll
@@ -279,7 +307,7 @@ __device__ __forceinline__ void for_chunks(uint32_t tcol, int h, F f) {
     if (two) {
 #pragma unroll
       for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(b[j]);
-      f((c + 2) * 16, v);
+      f((c + kG) * 16, v);
     }
   }
 }
@@ -288,7 +316,7 @@ __device__ __forceinline__ void for_chunks(uint32_t tcol, int h, F f) {
 template <int N, class F>
 __device__ __forceinline__ void for_chunks2(uint32_t tcol, uint32_t tcol2, int h, F f) {
   constexpr int NCH = N / 16;
-  for (int c = h; c < NCH; c += 2) {
+  for (int c = h; c < NCH; c += kG) {
     uint32_t a[16], b[16];
     tmem_ld16_nowait(tcol + c * 16, a);
     tmem_ld16_nowait(tcol2 + c * 16, b);
@@ -304,7 +332,7 @@ __device__ __forceinline__ void for_chunks2(uint32_t tcol, uint32_t tcol2, int h
 }
 
 template <int D, bool F8>
-__global__ void __launch_bounds__(256, 1) k_mlp_tc(const EvalIO* __restrict__ io, DescParams P,
+__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(const EvalIO* __restrict__ io, DescParams P,
                                                   Workspace ws, MlpTcWeights Wt, MlpF32Weights Wf) {
   constexpr int kBufA = slabs_of(D > kH2 ? D : kH2) * kSlab;  // G, later g2
   constexpr int kBufB = slabs_of(kH1) * kSlab;                // h1, later g1
@@ -322,11 +350,12 @@ __global__ void __launch_bounds__(256, 1) k_mlp_tc(const EvalIO* __restrict__ io
   uint8_t* bufB = bufA + kBufA;
   uint8_t* bufC = bufB + kBufB;
   uint8_t* wbuf[2] = {bufC + kBufC, bufC + kBufC + kWBuf};
-  uint64_t* bars = reinterpret_cast<uint64_t*>(wbuf[1] + kWBuf);  // [0,1] weights, [2] tile, [3] mma
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
+  // [0,1] weights, [2] tile, [3] MMAs, [4] layer-1 MMAs (may be issued one tile ahead)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wbuf[1] + kWBuf);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 5);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
-  float* sE = reinterpret_cast<float*>(abort_flag + 1);  // [2][kTM] partial energies
-  float* sb = sE + 2 * kTM;  // [kNB] biases and w4 of the tile's species
+  float* sE = reinterpret_cast<float*>(abort_flag + 1);  // [kG][kTM] partial energies
+  float* sb = sE + kG * kTM;  // [kNB] biases and w4 of the tile's species
   float* sb1 = sb;
   float* sb2 = sb1 + kH1;
   float* sb3 = sb2 + kH2;
@@ -338,7 +367,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_tc(const EvalIO* __restrict__ io
   float* ssc3 = ssc2 + kH2;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int quarter = warp & 3, h = warp >> 2;  // TMEM lane quarter; column half
+  const int quarter = warp & 3, h = warp >> 2;  // TMEM lane quarter; column group
   const int r = quarter * 32 + lane;            // row of the tile (TMEM lane)
   const float al = P.celu_alpha, kexp = 1.4426950408889634f / P.celu_alpha;
   const int rows = ws.seg[P.S];
@@ -349,6 +378,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_tc(const EvalIO* __restrict__ io
     mbar_init(&bars[1], 1);
     mbar_init(&bars[2], 1);
     mbar_init(&bars[3], 1);
+    mbar_init(&bars[4], 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -359,11 +389,12 @@ __global__ void __launch_bounds__(256, 1) k_mlp_tc(const EvalIO* __restrict__ io
   const uint32_t tmem = *tmem_slot;
   const uint32_t lb = (uint32_t)(quarter * 32) << 16;
   const uint32_t tz1 = tmem + lb + 0, tz2 = tmem + lb + 160, tz3 = tmem + lb + 288,
-                 tg2 = tmem + lb + 384, tg1 = tmem + lb + 160, tdg = tmem + lb + 0;
+                 tg2 = tmem + lb + 384, tg1 = tmem + lb + 160, tdg = tmem + lb + 384;
   const uint32_t mz1 = tmem + 0, mz2 = tmem + 160, mz3 = tmem + 288, mg2 = tmem + 384, mg1 = tmem + 160,
-                 mdg = tmem + 0;  // MMA destinations (lane 0)
+                 mdg = tmem + 384;  // MMA destinations (lane 0)
 
-  // barrier parities and outstanding work (thread 0): bars 0,1 weights, 2 tile, 3 MMA
+  // barrier parities and outstanding work: bars 0,1 weights, 2 tile (thread 0
+  // waits on these); bar 3 MMA completion (every thread waits on it)
   uint32_t ph[4] = {0, 0, 0, 0};
   bool pend[4] = {false, false, false, false};
 
@@ -383,24 +414,52 @@ __global__ void __launch_bounds__(256, 1) k_mlp_tc(const EvalIO* __restrict__ io
     mma_commit(&bars[3]);
     pend[3] = true;
   };
-  auto sync_wait = [&](int i) -> bool {
+  auto wait0 = [&](int i) {  // thread 0: copies into buffer i have landed
+    if (!pend[i]) return;
+    if (mbar_wait(&bars[i], ph[i])) {
+      ph[i] ^= 1u;
+      pend[i] = false;
+    } else {
+      *abort_flag = 1;
+      atomicOr(&ws.flags[kFlagTimeout], 1);
+    }
+  };
+  // Phase boundary: the epilogue's shared-memory writes (generic proxy) and
+  // TMEM reads are ordered before the next MMA; thread 0 has seen buffers i
+  // and j (-1: none) land; one block barrier publishes both.
+  auto phase = [&](int i, int j) -> bool {
+    tmem_wait_st();
+    fence_proxy_async();
+    tc_fence_before();
     if (tid == 0) {
-      if (mbar_wait(&bars[i], ph[i])) {
-        ph[i] ^= 1u;
-        pend[i] = false;
-      } else {
-        *abort_flag = 1;
-        atomicOr(&ws.flags[kFlagTimeout], 1);
-      }
+      if (i >= 0) wait0(i);
+      if (j >= 0) wait0(j);
     }
     __syncthreads();
     return *abort_flag == 0;
   };
-  // epilogue writes (generic proxy) -> next MMA (async proxy); TMEM reads -> next MMA
-  auto end_epilogue = [&]() {
-    fence_proxy_async();
-    tc_fence_before();
-    __syncthreads();
+  // every thread waits for the MMAs committed to barrier b (3, or 4 for
+  // layer 1); a timeout raises the abort flag and the next phase boundary
+  // then ends the loop for all threads
+  uint32_t ph4 = 0;
+  bool pend4 = false, l1_issued = false;  // thread 0: layer-1 MMA of the current tile in flight
+  auto commit4 = [&]() {
+    mma_commit(&bars[4]);
+    pend4 = true;
+  };
+  auto wait_mma = [&](int b) {
+    uint32_t& p = b == 4 ? ph4 : ph[3];
+    if (mbar_wait(&bars[b], p)) {
+      p ^= 1u;
+      if (tid == 0) {
+        if (b == 4) pend4 = false;
+        else pend[3] = false;
+      }
+    } else {
+      *abort_flag = 1;
+      atomicOr(&ws.flags[kFlagTimeout], 1);
+    }
+    tc_fence_after();
   };
 
   int tile = blockIdx.x;
@@ -411,6 +470,8 @@ __global__ void __launch_bounds__(256, 1) k_mlp_tc(const EvalIO* __restrict__ io
   for (; tile < ntiles; tile += gridDim.x) {
     const int row0 = tile * kTM;
     const int sp = pos4_species(ws.pos4[row0]);
+    const int next = tile + gridDim.x;
+    const int sp_next = next < ntiles ? pos4_species(ws.pos4[next * kTM]) : 0;
     const int row = row0 + r;
     const int my_atom = ws.row_atom[row];  // consumed by the energy epilogue
     const int my_sys = ws.row_info[row];
@@ -434,50 +495,61 @@ __global__ void __launch_bounds__(256, 1) k_mlp_tc(const EvalIO* __restrict__ io
       sb[i] = v;
     }
     // ---------------- layer 1: z1 = G W1
-    if (!sync_wait(2)) break;                        // G tile (also publishes sb)
-    if (!sync_wait(0)) break;                        // W1^T in wbuf[0]
+    if (!phase(2, 0)) break;                         // G tile, W1^T in wbuf[0] (also publishes sb)
     if (tid == 0) {
       load_w(sp, 1, 1);                              // W2^T -> wbuf[1]
-      tc_fence_after();
-      issue_gemm<F8>(mz1, bufA, wbuf[0], kH1, D);
-      commit();
+      if (!l1_issued) {
+        tc_fence_after();
+        issue_gemm<F8>(mz1, bufA, wbuf[0], kH1, D);
+        commit4();
+      }
+      l1_issued = false;
     }
-    if (!sync_wait(3)) break;
-    tc_fence_after();
+    wait_mma(4);
     for_chunks<kH1>(tz1, h, [&](int c0, float (&v)[16]) {
+      float d[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = celu_f(fmaf(v[j], F8 ? ssc1[c0 + j] : 1.f, sb1[c0 + j]), al, kexp);
+      for (int j = 0; j < 16; ++j) {
+        const float z = fmaf(v[j], F8 ? ssc1[c0 + j] : 1.f, sb1[c0 + j]);
+        const float ez = ex2f(z * kexp);
+        v[j] = z > 0.f ? z : al * (ez - 1.f);
+        d[j] = z > 0.f ? 1.f : ez;
+      }
+      tmem_st16(tz1 + c0, d);  // CELU'(z1) for the backward
       if (F8) store_row16_e4m3(bufB, r, c0, v, q1);
       else store_row16(bufB, r, c0, v);
     });
-    end_epilogue();
     // ---------------- layer 2: z2 = h1 W2
-    if (!sync_wait(1)) break;
+    if (!phase(1, -1)) break;
     if (tid == 0) {
       load_w(sp, 2, 0);                              // W3^T -> wbuf[0]
       tc_fence_after();
       issue_gemm<F8>(mz2, bufB, wbuf[1], kH2, kH1);
       commit();
     }
-    if (!sync_wait(3)) break;
-    tc_fence_after();
+    wait_mma(3);
     for_chunks<kH2>(tz2, h, [&](int c0, float (&v)[16]) {
+      float d[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = celu_f(fmaf(v[j], F8 ? ssc2[c0 + j] : 1.f, sb2[c0 + j]), al, kexp);
+      for (int j = 0; j < 16; ++j) {
+        const float z = fmaf(v[j], F8 ? ssc2[c0 + j] : 1.f, sb2[c0 + j]);
+        const float ez = ex2f(z * kexp);
+        v[j] = z > 0.f ? z : al * (ez - 1.f);
+        d[j] = z > 0.f ? 1.f : ez;
+      }
+      tmem_st16(tz2 + c0, d);  // CELU'(z2) for the backward
       if (F8) store_row16_e4m3(bufC, r, c0, v, q2);
       else store_row16(bufC, r, c0, v);
     });
-    end_epilogue();
     // ---------------- layer 3: z3 = h2 W3; energy and g3 = w4 CELU'(z3)
-    if (!sync_wait(0)) break;
+    if (!phase(0, -1)) break;
     if (tid == 0) {
       load_w(sp, 3, 1);                              // W3 (backward) -> wbuf[1]
       tc_fence_after();
       issue_gemm<F8>(mz3, bufC, wbuf[0], kH3, kH2);
       commit();
     }
-    if (!sync_wait(3)) break;
-    tc_fence_after();
+    wait_mma(3);
     {
       float e = 0.f;
       for_chunks<kH3>(tz3, h, [&](int c0, float (&v)[16]) {
@@ -485,66 +557,72 @@ __global__ void __launch_bounds__(256, 1) k_mlp_tc(const EvalIO* __restrict__ io
         for (int j = 0; j < 16; ++j) {
           const float z = fmaf(v[j], F8 ? ssc3[c0 + j] : 1.f, sb3[c0 + j]);
           const float ww = sw4[c0 + j];
-          e = fmaf(celu_f(z, al, kexp), ww, e);
-          v[j] = ww * dcelu_f(z, kexp);
+          const float ez = ex2f(z * kexp);
+          e = fmaf(z > 0.f ? z : al * (ez - 1.f), ww, e);
+          v[j] = ww * (z > 0.f ? 1.f : ez);
         }
         store_row16(bufC, r, c0, v);  // h2 no longer needed: the layer-3 MMA is done
       });
       sE[h * kTM + r] = e;
     }
-    end_epilogue();
-    if (h == 0) {  // warps 0-3: one row per thread
-      const float e = sE[r] + sE[kTM + r] + *sb4;
-      const bool valid = my_atom >= 0;
-      ws.Ei[row] = valid ? e : 0.f;
-      tile_energy_sums(valid ? e : 0.f, valid, my_sys, lane, io->energies);
-    }
     // ---------------- backward 3: g2' = g3 W3^T
-    if (!sync_wait(1)) break;
+    if (!phase(1, -1)) break;
     if (tid == 0) {
       load_w(sp, 4, 0);                              // W2 (backward) -> wbuf[0]
       tc_fence_after();
       issue_gemm<false>(mg2, bufC, wbuf[1], kH2, kH3);
       commit();
     }
-    if (!sync_wait(3)) break;
-    tc_fence_after();
-    for_chunks2<kH2>(tg2, tz2, h, [&](int c0, float (&g)[16], float (&z)[16]) {
+    if (h == 0) {  // warps 0-3, one row per thread, while the MMA runs
+      float e = *sb4;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) g[j] *= dcelu_f(fmaf(z[j], F8 ? ssc2[c0 + j] : 1.f, sb2[c0 + j]), kexp);
+      for (int g = 0; g < kG; ++g) e += sE[g * kTM + r];
+      const bool valid = my_atom >= 0;
+      ws.Ei[row] = valid ? e : 0.f;
+      tile_energy_sums(valid ? e : 0.f, valid, my_sys, lane, io->energies);
+    }
+    wait_mma(3);
+    for_chunks2<kH2>(tg2, tz2, h, [&](int c0, float (&g)[16], float (&d)[16]) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) g[j] *= d[j];
       store_row16(bufA, r, c0, g);  // the G tile is no longer needed
     });
-    end_epilogue();
     // ---------------- backward 2: g1' = g2 W2^T
-    if (!sync_wait(0)) break;
+    if (!phase(0, -1)) break;
     if (tid == 0) {
       load_w(sp, 5, 1);                              // W1 (backward) -> wbuf[1]
       tc_fence_after();
       issue_gemm<false>(mg1, bufA, wbuf[0], kH1, kH2);
       commit();
     }
-    if (!sync_wait(3)) break;
-    tc_fence_after();
-    for_chunks2<kH1>(tg1, tz1, h, [&](int c0, float (&g)[16], float (&z)[16]) {
+    wait_mma(3);
+    if (tid == 0 && next < ntiles) {  // bufA and wbuf[0] are free: prefetch the next tile
+      load_tile(next);
+      load_w(sp_next, 0, 0);
+    }
+    for_chunks2<kH1>(tg1, tz1, h, [&](int c0, float (&g)[16], float (&d)[16]) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) g[j] *= dcelu_f(fmaf(z[j], F8 ? ssc1[c0 + j] : 1.f, sb1[c0 + j]), kexp);
+      for (int j = 0; j < 16; ++j) g[j] *= d[j];
       store_row16(bufB, r, c0, g);
     });
-    end_epilogue();
     // ---------------- backward 1: dE/dG = g1 W1^T
-    if (!sync_wait(1)) break;
-    const int next = tile + gridDim.x;
+    if (!phase(1, -1)) break;
     if (tid == 0) {
       tc_fence_after();
       issue_gemm<false>(mdg, bufB, wbuf[1], D, kH1);
       commit();
-      if (next < ntiles) {  // bufA and wbuf[0] are free: prefetch the next tile
-        load_tile(next);
-        load_w(pos4_species(ws.pos4[next * kTM]), 0, 0);
+    }
+    wait_mma(3);
+    if (tid == 0 && next < ntiles) {  // next tile's layer 1 into [0,160), under the dE/dG epilogue
+      wait0(2);
+      wait0(0);
+      if (*abort_flag == 0) {
+        tc_fence_after();
+        issue_gemm<F8>(mz1, bufA, wbuf[0], kH1, D);
+        commit4();
+        l1_issued = true;
       }
     }
-    if (!sync_wait(3)) break;
-    tc_fence_after();
     {
       float* out = ws.dEdG + (size_t)row * D;
       for_chunks<D>(tdg, h, [&](int c0, float (&v)[16]) {
@@ -553,13 +631,12 @@ __global__ void __launch_bounds__(256, 1) k_mlp_tc(const EvalIO* __restrict__ io
           *reinterpret_cast<float4*>(out + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
       });
     }
-    tc_fence_before();
-    __syncthreads();
   }
   // on abort: give this CTA's outstanding copies and MMAs a bounded chance to land
   if (tid == 0 && *abort_flag) {
     for (int i = 0; i < 4; ++i)
       if (pend[i]) mbar_wait(&bars[i], ph[i]);
+    if (pend4) mbar_wait(&bars[4], ph4);
   }
   tc_fence_before();
   __syncthreads();
@@ -671,7 +748,7 @@ void swizzle_e4m3_into(uint8_t* dst, float* s, int N, int K, F value) {
 
 size_t smem_bytes(int D) {
   const int a = slabs_of(D > kH2 ? D : kH2) * kSlab, b = slabs_of(kH1) * kSlab, c = slabs_of(kH2) * kSlab;
-  return 1024 + (size_t)a + b + c + 2 * 48 * 1024 + 4 * 8 + 8 + 4 * kTM * 4 +
+  return 1024 + (size_t)a + b + c + 2 * 48 * 1024 + 5 * 8 + 8 + kG * kTM * 4 +
          (kH1 + kH2 + 2 * kH3 + 1) * 4 + (kH1 + kH2 + kH3) * 4 + 64;
 }
 
@@ -789,11 +866,11 @@ int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t stream, long long rows) {
   const Workspace w = ctx->workspace();
   const size_t sm = smem_bytes(D);
   if (st->f8)
-    k_mlp_tc<128, true><<<grid, 256, sm, stream>>>(ctx->d_io, ctx->P, w, st->w, ctx->wf32);
+    k_mlp_tc<128, true><<<grid, kTcThreads, sm, stream>>>(ctx->d_io, ctx->P, w, st->w, ctx->wf32);
   else if (D == 128)
-    k_mlp_tc<128, false><<<grid, 256, sm, stream>>>(ctx->d_io, ctx->P, w, st->w, ctx->wf32);
+    k_mlp_tc<128, false><<<grid, kTcThreads, sm, stream>>>(ctx->d_io, ctx->P, w, st->w, ctx->wf32);
   else
-    k_mlp_tc<48, false><<<grid, 256, sm, stream>>>(ctx->d_io, ctx->P, w, st->w, ctx->wf32);
+    k_mlp_tc<48, false><<<grid, kTcThreads, sm, stream>>>(ctx->d_io, ctx->P, w, st->w, ctx->wf32);
   return NNP_OK;
 }
 
