@@ -240,7 +240,7 @@ __device__ __forceinline__ void load_counts(const Workspace& ws, int S, int row,
 // forward
 
 template <int S, int ZSQ>
-__global__ void __launch_bounds__(256, 2) k_aev_fwd(const SysDesc* __restrict__ sys, DescParams P,
+__global__ void __launch_bounds__(256, 3) k_aev_fwd(const SysDesc* __restrict__ sys, DescParams P,
                                                  Workspace ws, int mode) {
   constexpr int D = kNRad * S + kNAng * S * (S + 1) / 2;
   extern __shared__ float4 sm4[];
@@ -528,11 +528,33 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
   const f2 half2 = f2_make(0.5f, 0.5f);
   const int rows = ws.seg[S];
   const int wpb = blockDim.x >> 5;
+  const int rstride = gridDim.x * wpb;
   int cached_sys = -1;
-  for (int row = blockIdx.x * wpb + wib; row < rows; row += gridDim.x * wpb) {
-    if (ws.row_atom[row] < 0) continue;  // padding row (warp-uniform)
-    const float4 pi = ws.pos4[row];
-    const int sid = ws.row_info[row];
+  // the next row's metadata, counts and first 64 list entries are loaded one
+  // row ahead, so their latency hides behind the current row's arithmetic
+  int p_atom = -1, p_info = 0, p_cnt = 0, p_cna = 0, p_e0 = 0, p_e1 = 0;
+  float4 p_pos = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto prefetch = [&](int rw) {
+    if (rw >= rows) return;
+    p_atom = ws.row_atom[rw];
+    p_pos = ws.pos4[rw];
+    p_info = ws.row_info[rw];
+    if (lane < S) {
+      p_cnt = ws.cnt_r[(size_t)rw * kMaxS + lane];
+      p_cna = ws.cnt_a[(size_t)rw * kMaxS + lane];
+    }
+    const int* l = ws.nbr_r + (size_t)rw * cr;
+    p_e0 = lane < cr ? l[lane] : 0;
+    p_e1 = lane + 32 < cr ? l[lane + 32] : 0;
+  };
+  prefetch(blockIdx.x * wpb + wib);
+  for (int row = blockIdx.x * wpb + wib; row < rows; row += rstride) {
+    const bool live_row = p_atom >= 0;
+    const float4 pi = p_pos;
+    const int sid = p_info;
+    const int cnt_l = p_cnt, cna_l = p_cna, e0 = p_e0, e1 = p_e1;
+    prefetch(row + rstride);
+    if (!live_row) continue;  // padding row (warp-uniform)
     __syncwarp();  // the previous row's shared data has been read
     if (sid != cached_sys) {
       const SysDesc& sd = sys[sid];
@@ -545,11 +567,6 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
       for (int f = lane; f < D / 4; f += 32) reinterpret_cast<float4*>(wsm)[f] = dg[f];
     }
     // counts per species (angular ones clamped to the staging capacity)
-    int cnt_l = 0, cna_l = 0;
-    if (lane < S) {
-      cnt_l = ws.cnt_r[(size_t)row * kMaxS + lane];
-      cna_l = ws.cnt_a[(size_t)row * kMaxS + lane];
-    }
     int nr[S], orr[S], na[S], oa[S];
     int ntot = 0, nang = 0;
 #pragma unroll
@@ -614,7 +631,7 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
           na_s = na[q];
           oa_s = oa[q];
         }
-      const int e = lr[k];
+      const int e = k < 32 ? e0 : (k < 64 ? e1 : lr[k]);
       const float4 pj = ws.pos4[nbr_row(e)];
       const float4 sv = sh[nbr_code(e)];
       const float dx = (pj.x - pi.x) + sv.x, dy = (pj.y - pi.y) + sv.y, dz = (pj.z - pi.z) + sv.z;
