@@ -207,11 +207,11 @@ __global__ void __launch_bounds__(256) k_binsort(const EvalIO* __restrict__ io, 
 // free).  Counts are clamped to what the list holds, so readers never run
 // past it; the unclamped maxima raise the overflow flags (one update per
 // CTA).  Padding rows get zero counts from k_scan.
-__global__ void __launch_bounds__(kNbrThreads, 6) k_neighbors(const EvalIO* __restrict__ io,
+__global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __restrict__ io,
                                                           const SysDesc* __restrict__ sys,
                                                           DescParams P, Workspace ws) {
   constexpr unsigned F = 0xffffffffu;
-  __shared__ int s_mx[2];
+  __shared__ int s_mx[3];  // maxima of the CTA's row counts; warps done
   extern __shared__ float4 s_dyn[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   float4* cand = s_dyn + (size_t)wib * kNbrWin;
@@ -219,6 +219,8 @@ __global__ void __launch_bounds__(kNbrThreads, 6) k_neighbors(const EvalIO* __re
   const float rcr2 = P.rc_r * P.rc_r, rca2 = P.rc_a * P.rc_a;
   int mx_r = 0, mx_a = 0;  // largest unclamped row counts seen by this lane
   const int wpb = blockDim.x >> 5;
+  if (threadIdx.x < 3) s_mx[threadIdx.x] = 0;
+  __syncthreads();
   for (int g = blockIdx.x * wpb + wib; g < TC; g += gridDim.x * wpb) {
     int lo = 0, hi = nsys - 1;
     while (lo < hi) {
@@ -260,64 +262,193 @@ __global__ void __launch_bounds__(kNbrThreads, 6) k_neighbors(const EvalIO* __re
       if (ok) vcell = (v[0] * nc1 + v[1]) * nc2 + v[2];
     }
     const float ell0 = sd.ellf[0], ell1 = sd.ellf[1], ell2 = sd.ellf[2];
-    for (int r0 = 0; r0 < nrows; r0 += 32) {
-      const int q = r0 + lane;
-      const bool has = q < nrows;
+    // bins of the 27 virtual cells for every species (lane v), their exclusive
+    // offsets within the species' flattened neighbourhood, and its size
+    int bst[kMaxS], bln[kMaxS], bex[kMaxS], tot[kMaxS];
+    int max_tot = 0;
+#pragma unroll
+    for (int sp = 0; sp < kMaxS; ++sp) {
+      bst[sp] = 0;
+      bln[sp] = 0;
+      if (sp < S && vcell >= 0) {
+        const int b = sp * TC + sd.cell_base + vcell;
+        bst[sp] = ws.bin_start[b];
+        bln[sp] = ws.bin_len[b];
+      }
+      int incl = bln[sp];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(F, incl, o);
+        if (lane >= o) incl += y;
+      }
+      tot[sp] = __shfl_sync(F, incl, 31);
+      bex[sp] = incl - bln[sp];
+      max_tot = max(max_tot, tot[sp]);
+    }
+    // per-species register arrays are read with constant indices only
+    auto pick = [&](const int (&a)[kMaxS], int sp) {
+      int x = a[0];
+#pragma unroll
+      for (int t = 1; t < kMaxS; ++t)
+        if (sp == t) x = a[t];
+      return x;
+    };
+    // stage the window [w0, w0 + wn) of species sp's neighbourhood: lane t
+    // finds the virtual cell of candidate w0 + t by a binary search over the
+    // cells' offsets, so that all of its position loads are independent
+    auto stage = [&](int sp, int w0, int wn) {
+      const int bex_s = pick(bex, sp), bst_s = pick(bst, sp);
+      __syncwarp();  // the previous window has been read
+#pragma unroll 4
+      for (int t0 = 0; t0 < wn; t0 += 32) {
+        const int t = t0 + lane, tt = w0 + t;
+        int lo = 0, hi = 26;
+#pragma unroll
+        for (int it = 0; it < 5; ++it) {  // largest v with offset(v) <= tt
+          const int mid = (lo + hi + 1) >> 1;
+          const int om = __shfl_sync(F, bex_s, mid);
+          if (om <= tt) lo = mid;
+          else hi = mid - 1;
+        }
+        const int ex_v = __shfl_sync(F, bex_s, lo), st_v = __shfl_sync(F, bst_s, lo);
+        if (t < wn) {
+          const int k = tt - ex_v;
+          const float4 pj = ws.pos4[st_v + k];
+          const float sx = (float)(lo / 9 - 1) * ell0, sy = (float)((lo / 3) % 3 - 1) * ell1,
+                      sz = (float)(lo % 3 - 1) * ell2;
+          cand[t] = make_float4(pj.x + sx, pj.y + sy, pj.z + sz, __int_as_float(pack_nbr(st_v + k, lo)));
+        }
+      }
+      __syncwarp();
+    };
+    // row of lane position q (species-major within the cell)
+    auto row_of = [&](int q) {
       int row = 0;
 #pragma unroll
       for (int s = 0; s < kMaxS; ++s) {
         const int inc = __shfl_sync(F, rpre, s), len = __shfl_sync(F, rln, s), st = __shfl_sync(F, rst, s);
         if (q >= inc - len && q < inc) row = st + (q - (inc - len));
       }
+      return row;
+    };
+    // hit masks of 32 candidates starting at k0 (window holds wn)
+    auto masks = [&](const float4 pi, int k0, int wn, unsigned& hr, unsigned& ha) {
+      hr = 0u;
+      ha = 0u;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        const float4 c = cand[k0 + k];  // past wn: stale window data, masked below
+        const float dx = c.x - pi.x, dy = c.y - pi.y, dz = c.z - pi.z;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        hr |= (r2 < rcr2 ? 1u : 0u) << k;
+        ha |= (r2 < rca2 ? 1u : 0u) << k;
+      }
+      if (wn - k0 < 32) hr &= (1u << (wn - k0)) - 1u;
+      ha &= hr;
+    };
+
+    if (nrows <= 16 && max_tot <= kNbrWin) {
+      // ---- split path: lanes q and q + 16 test row q against the two halves
+      // of the window; counts are exchanged, so every entry goes straight to
+      // its final place (angular ones first, half 0 before half 1)
+      const int q = lane & 15, hh = lane >> 4;
+      const bool has = q < nrows;
+      const int row = row_of(q);
+      const float4 pi = has ? ws.pos4[row] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const int row_sp = pos4_species(pi);
+      int* lr = ws.nbr_r + (size_t)row * cap;
+      int nr = 0, tot_r = 0, tot_a = 0;
+      for (int sp = 0; sp < S; ++sp) {
+        const int wn = pick(tot, sp);
+        stage(sp, 0, wn);
+        const int nch = (wn + 31) >> 5, mid = (nch + 1) >> 1;
+        const int ch0 = hh ? mid : 0, ch1 = hh ? nch : mid;
+        // the row itself: image 0 in virtual cell 13 of its own species
+        const int ex13 = __shfl_sync(F, pick(bex, sp), 13), st13 = __shfl_sync(F, pick(bst, sp), 13);
+        const int self_k = (row_sp == sp) ? ex13 + (row - st13) : -1;
+        unsigned A[8], R[8];
+        int na_me = 0, nro_me = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int ch = ch0 + i;
+          A[i] = 0u;
+          R[i] = 0u;
+          if (has && ch < ch1) {
+            unsigned hr, ha;
+            masks(pi, ch * 32, wn, hr, ha);
+            if ((self_k >> 5) == ch) {
+              hr &= ~(1u << (self_k & 31));
+              ha &= hr;
+            }
+            A[i] = ha;
+            R[i] = hr & ~ha;
+            na_me += __popc(A[i]);
+            nro_me += __popc(R[i]);
+          }
+        }
+        const int na_o = __shfl_xor_sync(F, na_me, 16), nro_o = __shfl_xor_sync(F, nro_me, 16);
+        const int NA = na_me + na_o, NRO = nro_me + nro_o;
+        int apos = nr + (hh ? na_o : 0), rpos = nr + NA + (hh ? nro_o : 0);
+        if (has) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int kb = (ch0 + i) * 32;
+            unsigned a = A[i], r = R[i];
+            while (a) {
+              const int k = __ffs(a) - 1;
+              a &= a - 1u;
+              if (apos < cap) lr[apos] = __float_as_int(cand[kb + k].w);
+              ++apos;
+            }
+            while (r) {
+              const int k = __ffs(r) - 1;
+              r &= r - 1u;
+              if (rpos < cap) lr[rpos] = __float_as_int(cand[kb + k].w);
+              ++rpos;
+            }
+          }
+        }
+        // counts clamped to what the list holds, so readers never run past it
+        const int keep = max(0, min(NA + NRO, cap - nr));
+        if (has && hh == 0) {
+          ws.cnt_r[(size_t)row * kMaxS + sp] = keep;
+          ws.cnt_a[(size_t)row * kMaxS + sp] = min(NA, keep);
+        }
+        nr += keep;
+        tot_r += NA + NRO;
+        tot_a += NA;
+      }
+      if (has && hh == 0) {
+        for (int sp = S; sp < kMaxS; ++sp) {
+          ws.cnt_r[(size_t)row * kMaxS + sp] = 0;
+          ws.cnt_a[(size_t)row * kMaxS + sp] = 0;
+        }
+        mx_r = max(mx_r, tot_r);
+        mx_a = max(mx_a, tot_a);
+      }
+      continue;
+    }
+
+    // ---- lane per row, windows of kNbrWin candidates
+    for (int r0 = 0; r0 < nrows; r0 += 32) {
+      const int q = r0 + lane;
+      const bool has = q < nrows;
+      const int row = row_of(q);
       const float4 pi = has ? ws.pos4[row] : make_float4(0.f, 0.f, 0.f, 0.f);
       const int self = pack_nbr(row, 13);
       int* lr = ws.nbr_r + (size_t)row * cap;
       int nr = 0, tot_r = 0, tot_a = 0;  // written entries; all entries found
       for (int sp = 0; sp < S; ++sp) {
-        int bst = 0, bln = 0;
-        if (vcell >= 0) {
-          const int b = sp * TC + sd.cell_base + vcell;
-          bst = ws.bin_start[b];
-          bln = ws.bin_len[b];
-        }
-        int incl = bln;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(F, incl, o);
-          if (lane >= o) incl += y;
-        }
-        const int total = __shfl_sync(F, incl, 31);
-        const int bex = incl - bln;
+        const int total = pick(tot, sp);
         int wa = 0, wro = 0, ka = 0, kro = 0;  // written / found: angular, radial-only
         for (int w0 = 0; w0 < total; w0 += kNbrWin) {
           const int wn = min(kNbrWin, total - w0);
-          __syncwarp();  // the previous window has been read
-          for (int v = 0; v < 27; ++v) {
-            const int len_v = __shfl_sync(F, bln, v);
-            const int ex_v = __shfl_sync(F, bex, v), st_v = __shfl_sync(F, bst, v);
-            const int k0 = max(0, w0 - ex_v), k1 = min(len_v, w0 + wn - ex_v);
-            const float sx = (float)(v / 9 - 1) * ell0, sy = (float)((v / 3) % 3 - 1) * ell1,
-                        sz = (float)(v % 3 - 1) * ell2;
-            for (int k = k0 + lane; k < k1; k += 32) {
-              const float4 pj = ws.pos4[st_v + k];
-              cand[ex_v + k - w0] = make_float4(pj.x + sx, pj.y + sy, pj.z + sz,
-                                                __int_as_float(pack_nbr(st_v + k, v)));
-            }
-          }
-          __syncwarp();
+          stage(sp, w0, wn);
           if (has) {
             // 32 candidates at a time: hit masks first (no branches), then the hits
             for (int k0 = 0; k0 < wn; k0 += 32) {
-              unsigned hr = 0u, ha = 0u;
-#pragma unroll
-              for (int k = 0; k < 32; ++k) {
-                const float4 c = cand[k0 + k];  // past wn: stale window data, masked below
-                const float dx = c.x - pi.x, dy = c.y - pi.y, dz = c.z - pi.z;
-                const float r2 = dx * dx + dy * dy + dz * dz;
-                hr |= (r2 < rcr2 ? 1u : 0u) << k;
-                ha |= (r2 < rca2 ? 1u : 0u) << k;
-              }
-              if (wn - k0 < 32) hr &= (1u << (wn - k0)) - 1u;
+              unsigned hr, ha;
+              masks(pi, k0, wn, hr, ha);
               while (hr) {
                 const int k = __ffs(hr) - 1;
                 hr &= hr - 1u;
@@ -356,23 +487,26 @@ __global__ void __launch_bounds__(kNbrThreads, 6) k_neighbors(const EvalIO* __re
       }
     }
   }
-  if (threadIdx.x == 0) { s_mx[0] = 0; s_mx[1] = 0; }
-  __syncthreads();
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     mx_r = max(mx_r, __shfl_xor_sync(F, mx_r, o));
     mx_a = max(mx_a, __shfl_xor_sync(F, mx_a, o));
   }
+  // the CTA's last warp to finish publishes the maxima (no block barrier, so
+  // warps that finish early do not wait)
   if (lane == 0) {
     atomicMax(&s_mx[0], mx_r);
     atomicMax(&s_mx[1], mx_a);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0 && (s_mx[0] | s_mx[1])) {
-    atomicMax(&ws.flags[kFlagMaxNbrR], s_mx[0]);
-    atomicMax(&ws.flags[kFlagMaxNbrA], s_mx[1]);
-    if (s_mx[0] > ws.cap_r) atomicOr(&ws.flags[kFlagOverflowR], 1);
-    if (s_mx[1] > ws.cap_a) atomicOr(&ws.flags[kFlagOverflowA], 1);
+    __threadfence_block();
+    if (atomicAdd(&s_mx[2], 1) == wpb - 1) {
+      const int r = atomicMax(&s_mx[0], 0), a = atomicMax(&s_mx[1], 0);
+      if (r | a) {
+        atomicMax(&ws.flags[kFlagMaxNbrR], r);
+        atomicMax(&ws.flags[kFlagMaxNbrA], a);
+        if (r > ws.cap_r) atomicOr(&ws.flags[kFlagOverflowR], 1);
+        if (a > ws.cap_a) atomicOr(&ws.flags[kFlagOverflowA], 1);
+      }
+    }
   }
 }
 
