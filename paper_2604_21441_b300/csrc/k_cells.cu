@@ -47,11 +47,11 @@ __global__ void k_bin(const EvalIO* __restrict__ io, const SysDesc* __restrict__
     for (int c = 0; c < 3; ++c) {
       double x = p[c] - sd.origin[c];
       if (sd.periodic) {
-        x -= sd.L[c] * floor(x / sd.L[c]);
+        x -= sd.L[c] * floor(x * sd.inv_L[c]);
         if (x >= sd.L[c]) x -= sd.L[c];
         if (x < 0.0) x = 0.0;
       }
-      int kk = (int)floor(x / sd.ell[c]);
+      int kk = (int)floor(x * sd.inv_ell[c]);
       kk = kk < 0 ? 0 : (kk >= sd.nc[c] ? sd.nc[c] - 1 : kk);
       k[c] = kk;
       off[c] = (float)(x - kk * sd.ell[c]);
@@ -71,6 +71,7 @@ __global__ void k_bin(const EvalIO* __restrict__ io, const SysDesc* __restrict__
 // Single CTA of 1024 threads.  bin_start[b] = first row of bin b, with each
 // species segment starting on a multiple of kTileRows; bin_len keeps counts.
 __global__ void __launch_bounds__(1024) k_scan(const EvalIO* __restrict__ io, int S, Workspace ws) {
+  constexpr int kReg = 16;  // bins per thread held in registers (up to 16,384 bins)
   __shared__ int warp_tot[32];
   __shared__ long long seg_s[kMaxS + 2];
   __shared__ int raw_at_species[kMaxS + 1];
@@ -79,8 +80,17 @@ __global__ void __launch_bounds__(1024) k_scan(const EvalIO* __restrict__ io, in
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int chunk = (nb + 1023) / 1024;
   const int b0 = t * chunk, b1 = min(nb, b0 + chunk);
+  const bool in_regs = chunk <= kReg;
+  int cnt[kReg];
   int sum = 0;
-  for (int b = b0; b < b1; ++b) sum += ws.bin_count[b];
+  if (in_regs) {  // all loads of the thread's bins at once
+#pragma unroll
+    for (int i = 0; i < kReg; ++i) cnt[i] = (b0 + i < b1) ? ws.bin_count[b0 + i] : 0;
+#pragma unroll
+    for (int i = 0; i < kReg; ++i) sum += cnt[i];
+  } else {
+    for (int b = b0; b < b1; ++b) sum += ws.bin_count[b];
+  }
   // block exclusive scan of per-thread sums
   int incl = sum;
 #pragma unroll
@@ -101,32 +111,83 @@ __global__ void __launch_bounds__(1024) k_scan(const EvalIO* __restrict__ io, in
     warp_tot[lane] = iv - v;  // exclusive warp offsets
   }
   __syncthreads();
-  int run = warp_tot[wid] + incl - sum;
-  for (int b = b0; b < b1; ++b) {
-    int c = ws.bin_count[b];
-    ws.bin_start[b] = run;   // raw prefix (no padding yet)
-    ws.bin_len[b] = c;
-    run += c;
-    if (b % TC == 0) raw_at_species[b / TC] = ws.bin_start[b];
+  const int run0 = warp_tot[wid] + incl - sum;  // raw prefix (no padding yet) of bin b0
+  {
+    int run = run0;
+    // bins are species-major: species sp starts at bin sp * TC (no divisions per bin)
+    int sp = TC > 0 ? b0 / TC : 0, sp_start = sp * TC;
+    if (in_regs) {
+#pragma unroll
+      for (int i = 0; i < kReg; ++i) {
+        const int b = b0 + i;
+        if (b < b1) {
+          if (b == sp_start + TC) {
+            ++sp;
+            sp_start += TC;
+          }
+          if (b == sp_start) raw_at_species[sp] = run;
+        }
+        run += cnt[i];
+      }
+    } else {
+      for (int b = b0; b < b1; ++b) {
+        if (b == sp_start + TC) {
+          ++sp;
+          sp_start += TC;
+        }
+        if (b == sp_start) raw_at_species[sp] = run;
+        run += ws.bin_count[b];
+      }
+    }
+    if (b1 == nb && b0 < b1) raw_at_species[S] = run;
   }
-  if (b1 == nb && b0 < b1) raw_at_species[S] = run;
   if (nb == 0 && t == 0) raw_at_species[S] = 0;
   __syncthreads();
   if (t == 0) {
     long long start = 0;
     for (int s = 0; s < S; ++s) {
       seg_s[s] = start;
-      const int cnt = raw_at_species[s + 1] - raw_at_species[s];
-      start = ((start + cnt + kTileRows - 1) / kTileRows) * kTileRows;
+      const int c = raw_at_species[s + 1] - raw_at_species[s];
+      start = ((start + c + kTileRows - 1) / kTileRows) * kTileRows;
     }
     seg_s[S] = start;
     for (int s = 0; s <= S; ++s) ws.seg[s] = (int)seg_s[s];
     ws.seg[kMaxS + 1] = raw_at_species[S];  // real atoms
   }
   __syncthreads();
-  for (int b = t; b < nb; b += 1024) {
-    const int s = b / TC;
-    ws.bin_start[b] += (int)(seg_s[s] - raw_at_species[s]);
+  // bin_start = raw prefix + the padding of the preceding species segments
+  {
+    int run = run0;
+    int sp = TC > 0 ? b0 / TC : 0, sp_start = sp * TC;
+    int shift = (sp < S) ? (int)(seg_s[sp] - raw_at_species[sp]) : 0;
+    if (in_regs) {
+#pragma unroll
+      for (int i = 0; i < kReg; ++i) {
+        const int b = b0 + i;
+        if (b < b1) {
+          if (b == sp_start + TC) {
+            ++sp;
+            sp_start += TC;
+            shift = (int)(seg_s[sp] - raw_at_species[sp]);
+          }
+          ws.bin_start[b] = run + shift;
+          ws.bin_len[b] = cnt[i];
+        }
+        run += cnt[i];
+      }
+    } else {
+      for (int b = b0; b < b1; ++b) {
+        if (b == sp_start + TC) {
+          ++sp;
+          sp_start += TC;
+          shift = (int)(seg_s[sp] - raw_at_species[sp]);
+        }
+        const int c = ws.bin_count[b];
+        ws.bin_start[b] = run + shift;
+        ws.bin_len[b] = c;
+        run += c;
+      }
+    }
   }
   if (t == 0) ws.bin_start[nb] = (int)seg_s[S];
   // padding rows at the end of each species segment

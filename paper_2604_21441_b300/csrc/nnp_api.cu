@@ -300,6 +300,8 @@ int nnp_ctx::prepare(int B, const int64_t* offsets, const double* pos_host_or_nu
       sd.L[c] = L[c];
       sd.nc[c] = nc[c];
       sd.ell[c] = L[c] / nc[c];
+      sd.inv_L[c] = 1.0 / L[c];
+      sd.inv_ell[c] = 1.0 / sd.ell[c];
       sd.ellf[c] = (float)sd.ell[c];
     }
     sd.cell_base = (int)cell_base;

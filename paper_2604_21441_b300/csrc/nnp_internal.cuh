@@ -66,6 +66,7 @@ struct DescParams {
 struct SysDesc {
   double L[3];      // edges (isolated systems: padded bounding box)
   double ell[3];    // cell edges L / nc
+  double inv_L[3], inv_ell[3];  // reciprocals (the wrap multiplies: FP64 division is slow)
   double origin[3]; // subtracted before wrapping (isolated systems)
   float ellf[3];
   int nc[3];

@@ -150,6 +150,8 @@ extern "C" int nnp_eval_noalloc(nnp_ctx* ctx, int64_t n, const double* pos, cons
   for (int c = 0; c < 3; ++c) {
     sd.nc[c] = nc[c];
     sd.ell[c] = sd.L[c] / nc[c];
+    sd.inv_L[c] = 1.0 / sd.L[c];
+    sd.inv_ell[c] = 1.0 / sd.ell[c];
     sd.ellf[c] = (float)sd.ell[c];
   }
   sd.periodic = 1;
