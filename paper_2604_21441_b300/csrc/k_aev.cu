@@ -331,7 +331,8 @@ __global__ void __launch_bounds__(256, 3) k_aev_fwd(const SysDesc* __restrict__ 
       for (int k0 = 0; k0 < nmax; k0 += 16) {
         const int k = k0 + hl;
         if (k < n_s) {
-          const float r = sqrtf(rad[o_s + k].w);
+          const float r2 = rad[o_s + k].w;
+          const float r = r2 * rsqrtf(r2);
           float fc, dfc;
           cutoff(r, P.rc_r, kfr, fc, dfc);
           const f2 f = f2_make(0.25f * fc, 0.25f * fc), rr = f2_make(r, r);
@@ -396,7 +397,8 @@ __global__ void __launch_bounds__(256, 3) k_aev_fwd(const SysDesc* __restrict__ 
             const float4 gu = geo[u], gv = geo[v];
             const float c = gu.x * gv.x + gu.y * gv.y + gu.z * gv.z;
             const float uc = 0.95f * c;
-            const float sn = sqrtf(fmaxf(1.f - uc * uc, 0.f));
+            const float s2 = fmaxf(1.f - uc * uc, 1e-12f);  // >= 0.0975: |uc| <= 0.95
+            const float sn = s2 * rsqrtf(s2);
             const float fp = fcs[u] * fcs[v];
             const float rbar = 0.5f * (gu.w + gv.w);
             f2 B2[kNAngR];
