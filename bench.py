@@ -360,6 +360,21 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def aggregate_ranks(t_rank, units, world, device):
+    """Whole-job timing of independent replicas: the slowest rank's timed
+    seconds and the units (atom-steps) summed over ranks.  Any process group
+    backend (NCCL on GPUs, gloo on CPU)."""
+    if world <= 1:
+        return t_rank, float(units)
+    import torch
+    import torch.distributed as dist
+    tmax = torch.tensor([t_rank], dtype=torch.float64, device=device)
+    tsum = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax.item()), float(tsum.item())
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -386,15 +401,8 @@ def main():
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     r = run_ours(args, rank, world, local_rank)
-    t_rank = float(np.sum(r["ms"])) / 1e3
-    total_atoms = r["n"] * args.steps
-    if world > 1:
-        tt = torch.tensor([t_rank, float(total_atoms)], dtype=torch.float64, device="cuda")
-        tmax = tt[:1].clone()
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        tsum = tt[1:].clone()
-        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
-        t_rank, total_atoms = float(tmax.item()), float(tsum.item())
+    t_rank, total_atoms = aggregate_ranks(float(np.sum(r["ms"])) / 1e3, r["n"] * args.steps, world,
+                                          "cuda")
     value = total_atoms / t_rank
     if rank != 0:
         if world > 1:
@@ -423,7 +431,9 @@ def main():
                 "peak_source": (f"{pk_kind} bf16" if bound == "tensor" else
                                 "148 SMs x 128 FP32 lanes x 2 x max SM clock"),
                 "stage_ms": st}
-    cpu_v, cpu_desc, _, _ = oracle_sample(r["wl"], r["w"], seconds=args.cpu_seconds)
+    # the CPU baseline is timed at N = 1 only (rank 0 of a multi-GPU run skips it)
+    cpu_v, cpu_desc = (oracle_sample(r["wl"], r["w"], seconds=args.cpu_seconds)[:2] if world == 1
+                       else (None, None))
     ms_mean = float(np.mean(r["ms"]))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -442,8 +452,8 @@ def main():
         "autotuned_blocks_per_sm": r["tuned"],
         "clocks": r["clocks"],
         "roofline": roofline,
-        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": cpu_desc},
+        "cpu_baseline": ({"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                          "sample": cpu_desc} if cpu_v is not None else None),
     }
     if r["per_system_ms"] is not None:
         line["batch"] = {"systems": r["B"], "one_graph_launch_ms": ms_mean,
