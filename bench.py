@@ -305,6 +305,38 @@ def run_ours(args, rank, world, local_rank):
                 wl=wl, pot=pot, pos_h=pos_h, Z_h=Z_h, boxes=boxes, w=w)
 
 
+def nve_rate(precision, steps=400):
+    """Velocity-Verlet throughput on the 4,096-water box (12,288 atoms,
+    0.5 fs): library forces plus the four elementwise updates per step, all
+    on the library's stream, device-resident state; timed with CUDA events.
+    The network's output layer is scaled by 0.03 (as in the NVE test) so that
+    random weights give stable dynamics."""
+    import torch
+    import synth
+    import paper_2604_21441_b300 as P
+    from paper_2604_21441_b300 import torch_nnp as tn
+    wl = synth.workload(2)
+    s = wl["systems"][0]
+    w = synth.xavier_weights(2, 128, wl["weight_seed"], final_scale=0.03)
+    stream = torch.cuda.Stream()
+    pot = P.NNP(atomic_numbers=(1, 8), precision=precision, max_atoms=s.n, stream=stream,
+                nbr_capacity=128, ang_capacity=48)
+    pot.set_all_weights([[(W.astype(np.float32), b.astype(np.float32)) for W, b in x] for x in w])
+    md = tn.NVE(pot, s.pos, s.Z, s.box, synth.maxwell_boltzmann(s.Z, 300.0, 7), dt_fs=0.5)
+    md.step(50, check_every=50)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    md.step(steps, check_every=steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    pot.close()
+    return {"workload": "water-4096 (12,288 atoms, 49.7 A)", "precision": precision, "dt_fs": 0.5,
+            "steps": steps, "ms_per_step": ms, "ns_per_day": 0.5e-6 * 86400e3 / ms,
+            "rollbacks": md.retries}
+
+
 def oracle_sample(wl, w, seconds=20.0, seed=0):
     """Time the FP64 oracle on bounded samples of the workload: sampled atoms
     get E_i and F_i, which evaluates them and every atom within the radial
@@ -455,6 +487,8 @@ def main():
         "cpu_baseline": ({"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
                           "sample": cpu_desc} if cpu_v is not None else None),
     }
+    if args.workload == 3:  # the paper reports MD throughput in ns/day
+        line["nve"] = nve_rate(args.precision)
     if r["per_system_ms"] is not None:
         line["batch"] = {"systems": r["B"], "one_graph_launch_ms": ms_mean,
                          "one_launch_per_system_ms": r["per_system_ms"],

@@ -34,7 +34,12 @@ int nnp_ctx::init_device() {
   CK(cudaMalloc(&b_flags, sizeof(int) * kNumFlags));
   CK(cudaMemset(b_flags, 0, sizeof(int) * kNumFlags));
   CK(cudaMalloc(&d_io, sizeof(EvalIO)));
-  CK(cudaMallocHost(&h_io, sizeof(EvalIO)));
+  for (auto& sg : stages) {
+    CK(cudaMallocHost(&sg.io, sizeof(EvalIO)));
+    memset(sg.io, 0, sizeof(EvalIO));
+    CK(cudaEventCreateWithFlags(&sg.ev, cudaEventDisableTiming));
+  }
+  h_io = stages[0].io;
   CK(cudaMallocHost(&h_flags, sizeof(int) * kNumFlags));
   memset(h_flags, 0, sizeof(int) * kNumFlags);
   signed char lut[128];
@@ -90,7 +95,11 @@ nnp_ctx::~nnp_ctx() {
     if (p) cudaFree(p);
   for (auto& ev : stage_ev)
     if (ev) cudaEventDestroy(ev);
-  if (h_io) cudaFreeHost(h_io);
+  for (auto& sg : stages) {
+    if (sg.io) cudaFreeHost(sg.io);
+    if (sg.sys) cudaFreeHost(sg.sys);
+    if (sg.ev) cudaEventDestroy(sg.ev);
+  }
   if (h_flags) cudaFreeHost(h_flags);
   if (own_stream && stream) cudaStreamDestroy(stream);
 }

@@ -91,7 +91,18 @@ struct nnp_ctx {
   int* b_flags = nullptr;
   signed char* d_zlut = nullptr;
   nnp::EvalIO* d_io = nullptr;
-  nnp::EvalIO* h_io = nullptr;  // pinned
+  nnp::EvalIO* h_io = nullptr;  // pinned; the staging slot of the last evaluation
+  // Pinned staging slots for the per-call descriptors, used in turn: a slot is
+  // rewritten only after the copies that read it (event) have run, so
+  // asynchronous evaluations never wait for the stream.
+  static constexpr int kStages = 4;
+  struct Stage {
+    nnp::EvalIO* io = nullptr;
+    nnp::SysDesc* sys = nullptr;
+    size_t cap = 0;
+    cudaEvent_t ev = nullptr;
+  } stages[kStages];
+  int stage_next = 0;
   int* h_flags = nullptr;       // pinned
 
   // weights
