@@ -350,9 +350,20 @@ int nnp_ctx::evaluate(int B, const int64_t* offsets, const double* pos, const in
   for (int attempt = 0; attempt < 4; ++attempt) {
     rc = ensure_capacity(n, B, bins, rows);
     if (rc) return rc;
-    // IO descriptor
-    EvalIO& io = *h_io;
-    CK(cudaStreamSynchronize(stream));  // pinned descriptor buffers are reused
+    // IO and system descriptors through the next pinned staging slot
+    Stage& sg = stages[stage_next];
+    stage_next = (stage_next + 1) % kStages;
+    CK(cudaEventSynchronize(sg.ev));  // the copies that last read this slot have run
+    if (sg.cap < (size_t)B) {
+      if (sg.sys) cudaFreeHost(sg.sys);
+      sg.sys = nullptr;
+      sg.cap = 0;
+      CK(cudaMallocHost(&sg.sys, sizeof(SysDesc) * (size_t)B));
+      sg.cap = (size_t)B;
+    }
+    memcpy(sg.sys, sys_h.data(), sizeof(SysDesc) * (size_t)B);
+    h_io = sg.io;
+    EvalIO& io = *sg.io;
     io.pos = pos_dev ? pos : b_pos_stage;
     io.Z = Z_dev ? Z : b_Z_stage;
     io.forces = F_dev ? forces : b_F_stage;
@@ -362,8 +373,9 @@ int nnp_ctx::evaluate(int B, const int64_t* offsets, const double* pos, const in
     io.total_cells = total_cells;
     if (!pos_dev) CK(cudaMemcpyAsync(b_pos_stage, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, stream));
     if (!Z_dev) CK(cudaMemcpyAsync(b_Z_stage, Z, sizeof(int) * n, cudaMemcpyHostToDevice, stream));
-    CK(cudaMemcpyAsync(d_io, h_io, sizeof(EvalIO), cudaMemcpyHostToDevice, stream));
-    CK(cudaMemcpyAsync(b_sys, sys_h.data(), sizeof(SysDesc) * B, cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(d_io, sg.io, sizeof(EvalIO), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(b_sys, sg.sys, sizeof(SysDesc) * B, cudaMemcpyHostToDevice, stream));
+    CK(cudaEventRecord(sg.ev, stream));
     // device flags accumulate over asynchronous evaluations until nnp_sync reads them;
     // a synchronous evaluation reports only its own
     if (sync) CK(cudaMemsetAsync(b_flags, 0, sizeof(int) * kNumFlags, stream));
