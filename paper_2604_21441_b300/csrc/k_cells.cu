@@ -71,7 +71,8 @@ __global__ void k_bin(const EvalIO* __restrict__ io, const SysDesc* __restrict__
 // Single CTA of 1024 threads.  bin_start[b] = first row of bin b, with each
 // species segment starting on a multiple of kTileRows; bin_len keeps counts.
 __global__ void __launch_bounds__(1024) k_scan(const EvalIO* __restrict__ io, int S, Workspace ws) {
-  constexpr int kReg = 16;  // bins per thread held in registers (up to 16,384 bins)
+  constexpr int kReg = 16;  // bins per thread (up to kScanSmemBins bins go through shared memory)
+  extern __shared__ int s_bins[];  // [kScanSmemBins]: counts, then raw starts
   __shared__ int warp_tot[32];
   __shared__ long long seg_s[kMaxS + 2];
   __shared__ int raw_at_species[kMaxS + 1];
@@ -80,12 +81,22 @@ __global__ void __launch_bounds__(1024) k_scan(const EvalIO* __restrict__ io, in
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int chunk = (nb + 1023) / 1024;
   const int b0 = t * chunk, b1 = min(nb, b0 + chunk);
-  const bool in_regs = chunk <= kReg;
+  const bool in_smem = nb <= kScanSmemBins;
+  // coalesced loads into shared memory (and bin_len), then each thread scans
+  // its contiguous range from there
+  if (in_smem) {
+    for (int b = t; b < nb; b += 1024) {
+      const int c = ws.bin_count[b];
+      s_bins[b] = c;
+      ws.bin_len[b] = c;
+    }
+    __syncthreads();
+  }
   int cnt[kReg];
   int sum = 0;
-  if (in_regs) {  // all loads of the thread's bins at once
+  if (in_smem) {
 #pragma unroll
-    for (int i = 0; i < kReg; ++i) cnt[i] = (b0 + i < b1) ? ws.bin_count[b0 + i] : 0;
+    for (int i = 0; i < kReg; ++i) cnt[i] = (b0 + i < b1) ? s_bins[b0 + i] : 0;
 #pragma unroll
     for (int i = 0; i < kReg; ++i) sum += cnt[i];
   } else {
@@ -113,10 +124,10 @@ __global__ void __launch_bounds__(1024) k_scan(const EvalIO* __restrict__ io, in
   __syncthreads();
   const int run0 = warp_tot[wid] + incl - sum;  // raw prefix (no padding yet) of bin b0
   {
-    int run = run0;
     // bins are species-major: species sp starts at bin sp * TC (no divisions per bin)
+    int run = run0;
     int sp = TC > 0 ? b0 / TC : 0, sp_start = sp * TC;
-    if (in_regs) {
+    if (in_smem) {
 #pragma unroll
       for (int i = 0; i < kReg; ++i) {
         const int b = b0 + i;
@@ -126,6 +137,7 @@ __global__ void __launch_bounds__(1024) k_scan(const EvalIO* __restrict__ io, in
             sp_start += TC;
           }
           if (b == sp_start) raw_at_species[sp] = run;
+          s_bins[b] = run;  // raw start
         }
         run += cnt[i];
       }
@@ -156,37 +168,27 @@ __global__ void __launch_bounds__(1024) k_scan(const EvalIO* __restrict__ io, in
   }
   __syncthreads();
   // bin_start = raw prefix + the padding of the preceding species segments
-  {
+  if (in_smem) {
+    for (int b = t; b < nb; b += 1024) {  // coalesced
+      int sp = 0;
+#pragma unroll
+      for (int q = 1; q < kMaxS; ++q) sp += (q < S && b >= q * TC) ? 1 : 0;
+      ws.bin_start[b] = s_bins[b] + (int)(seg_s[sp] - raw_at_species[sp]);
+    }
+  } else {
     int run = run0;
     int sp = TC > 0 ? b0 / TC : 0, sp_start = sp * TC;
     int shift = (sp < S) ? (int)(seg_s[sp] - raw_at_species[sp]) : 0;
-    if (in_regs) {
-#pragma unroll
-      for (int i = 0; i < kReg; ++i) {
-        const int b = b0 + i;
-        if (b < b1) {
-          if (b == sp_start + TC) {
-            ++sp;
-            sp_start += TC;
-            shift = (int)(seg_s[sp] - raw_at_species[sp]);
-          }
-          ws.bin_start[b] = run + shift;
-          ws.bin_len[b] = cnt[i];
-        }
-        run += cnt[i];
+    for (int b = b0; b < b1; ++b) {
+      if (b == sp_start + TC) {
+        ++sp;
+        sp_start += TC;
+        shift = (int)(seg_s[sp] - raw_at_species[sp]);
       }
-    } else {
-      for (int b = b0; b < b1; ++b) {
-        if (b == sp_start + TC) {
-          ++sp;
-          sp_start += TC;
-          shift = (int)(seg_s[sp] - raw_at_species[sp]);
-        }
-        const int c = ws.bin_count[b];
-        ws.bin_start[b] = run + shift;
-        ws.bin_len[b] = c;
-        run += c;
-      }
+      const int c = ws.bin_count[b];
+      ws.bin_start[b] = run + shift;
+      ws.bin_len[b] = c;
+      run += c;
     }
   }
   if (t == 0) ws.bin_start[nb] = (int)seg_s[S];
@@ -577,6 +579,9 @@ size_t neighbors_smem(int cap_r) {
 }
 
 cudaError_t neighbors_set_smem_limits() {
+  cudaError_t e = cudaFuncSetAttribute(k_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(int) * kScanSmemBins));
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_neighbors, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)neighbors_smem(4096));
 }

@@ -170,7 +170,7 @@ int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows,
   const bool capturing = cs == cudaStreamCaptureStatusActive;
   mark_stage(0, capturing);
   k_bin<<<g_atoms, 256, 0, stream>>>(io, sys, d_zlut, w); ++launches;
-  k_scan<<<1, 1024, 0, stream>>>(io, P.S, w); ++launches;
+  k_scan<<<1, 1024, sizeof(int) * kScanSmemBins, stream>>>(io, P.S, w); ++launches;
   k_scatter<<<g_atoms, 256, 0, stream>>>(io, w); ++launches;
   k_binsort<<<g_bins, 256, 0, stream>>>(io, P.S, (cfg.flags & NNP_FLAG_NONDETERMINISTIC_BINS) ? 0 : 1,
                                         w); ++launches;

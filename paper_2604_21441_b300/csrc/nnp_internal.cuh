@@ -33,6 +33,7 @@ constexpr int kMaxS = 4;       // species supported by the kernels
 constexpr int kTileRows = 128; // species segments are padded to this
 constexpr int kMaxCapA = 64;     // largest angular-neighbour capacity (staged per row)
 constexpr int kMaxCapR = 512;    // largest radial-neighbour capacity (gathered per row)
+constexpr int kScanSmemBins = 16384;  // k_scan stages up to this many bins in shared memory
 constexpr int kNbrThreads = 128;  // k_neighbors: warp per cell, lane per row
 constexpr int kNbrWin = 512;      // neighbourhood atoms one warp stages per window
 constexpr int kMaxD = kNRad * kMaxS + kNAng * kMaxS * (kMaxS + 1) / 2;  // 384

@@ -222,7 +222,7 @@ extern "C" int nnp_eval_noalloc(nnp_ctx* ctx, int64_t n, const double* pos, cons
   NA_CK(cudaMemcpyAsync(d_io, &io, sizeof io, cudaMemcpyHostToDevice, st));
   NA_CK(cudaMemcpyAsync(d_sys, &sd, sizeof sd, cudaMemcpyHostToDevice, st));
   k_bin<<<g_atoms, 256, 0, st>>>(d_io, d_sys, ctx->d_zlut, w);
-  k_scan<<<1, 1024, 0, st>>>(d_io, P.S, w);
+  k_scan<<<1, 1024, sizeof(int) * kScanSmemBins, st>>>(d_io, P.S, w);
   k_scatter<<<g_atoms, 256, 0, st>>>(d_io, w);
   k_binsort<<<g_bins, 256, 0, st>>>(d_io, P.S, 1, w);
   k_neighbors<<<g_cells, kNbrThreads, neighbors_smem(w.cap_r), st>>>(d_io, d_sys, P, w);
