@@ -277,9 +277,18 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
   __shared__ int s_mx[3];  // maxima of the CTA's row counts; warps done
   extern __shared__ float4 s_dyn[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  float4* cand = s_dyn + (size_t)wib * kNbrWin;
+  // per warp: the candidate window as arrays of x, y, z (chunks of 32 at a
+  // stride of 36 floats, so that the lanes of a row, reading different
+  // chunks, hit different banks) and of list entries, then the 16 hit-mask
+  // slots of the group path
+  float* wx = reinterpret_cast<float*>(s_dyn) + (size_t)wib * kNbrWarpFloats;
+  float* wy = wx + kNbrChunks * kNbrChunkStride;
+  float* wz = wy + kNbrChunks * kNbrChunkStride;
+  int* we = reinterpret_cast<int*>(wz + kNbrChunks * kNbrChunkStride);
+  unsigned* hmask = reinterpret_cast<unsigned*>(we + kNbrWin);
   const int TC = io->total_cells, nsys = io->n_sys, S = P.S, cap = ws.cap_r;
   const float rcr2 = P.rc_r * P.rc_r, rca2 = P.rc_a * P.rc_a;
+  const f2 nrc2 = f2_make(-rcr2, -rcr2), nra2 = f2_make(-rca2, -rca2);
   int mx_r = 0, mx_a = 0;  // largest unclamped row counts seen by this lane
   const int wpb = blockDim.x >> 5;
   if (threadIdx.x < 3) s_mx[threadIdx.x] = 0;
@@ -328,7 +337,7 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
     // bins of the 27 virtual cells for every species (lane v), their exclusive
     // offsets within the species' flattened neighbourhood, and its size
     int bst[kMaxS], bln[kMaxS], bex[kMaxS], tot[kMaxS];
-    int max_tot = 0;
+    int max_tot = 0, sum_tot = 0;  // sum of the windows, each rounded up to whole chunks
 #pragma unroll
     for (int sp = 0; sp < kMaxS; ++sp) {
       bst[sp] = 0;
@@ -347,6 +356,7 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
       tot[sp] = __shfl_sync(F, incl, 31);
       bex[sp] = incl - bln[sp];
       max_tot = max(max_tot, tot[sp]);
+      sum_tot += (tot[sp] + 31) & ~31;
     }
     // per-species register arrays are read with constant indices only
     auto pick = [&](const int (&a)[kMaxS], int sp) {
@@ -359,7 +369,7 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
     // stage the window [w0, w0 + wn) of species sp's neighbourhood: lane t
     // finds the virtual cell of candidate w0 + t by a binary search over the
     // cells' offsets, so that all of its position loads are independent
-    auto stage = [&](int sp, int w0, int wn) {
+    auto stage = [&](int sp, int w0, int wn, int db) {
       const int bex_s = pick(bex, sp), bst_s = pick(bst, sp);
       __syncwarp();  // the previous window has been read
 #pragma unroll 4
@@ -379,7 +389,11 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
           const float4 pj = ws.pos4[st_v + k];
           const float sx = (float)(lo / 9 - 1) * ell0, sy = (float)((lo / 3) % 3 - 1) * ell1,
                       sz = (float)(lo % 3 - 1) * ell2;
-          cand[t] = make_float4(pj.x + sx, pj.y + sy, pj.z + sz, __int_as_float(pack_nbr(st_v + k, lo)));
+          const int gi = db + t, ci = (gi >> 5) * kNbrChunkStride + (gi & 31);
+          wx[ci] = pj.x + sx;
+          wy[ci] = pj.y + sy;
+          wz[ci] = pj.z + sz;
+          we[gi] = pack_nbr(st_v + k, lo);
         }
       }
       __syncwarp();
@@ -394,100 +408,156 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
       }
       return row;
     };
-    // hit masks of 32 candidates starting at k0 (window holds wn)
-    auto masks = [&](const float4 pi, int k0, int wn, unsigned& hr, unsigned& ha) {
-      hr = 0u;
-      ha = 0u;
+    // hit masks of the 32 candidates of the chunk starting at k0 (a multiple
+    // of 32; the window ends at wn) against the row at -(nx, ny, nz).  Bit k
+    // is the sign of r^2 - rc^2 (exact: both are near-equal normal floats
+    // or clearly ordered), shifted in by one funnel shift per candidate.
+    auto masks = [&](const f2 nx, const f2 ny, const f2 nz, int k0, int wn, unsigned& hr, unsigned& ha) {
+      const int cb = (k0 >> 5) * kNbrChunkStride;
+      unsigned r = 0u, a = 0u;
 #pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        const float4 c = cand[k0 + k];  // past wn: stale window data, masked below
-        const float dx = c.x - pi.x, dy = c.y - pi.y, dz = c.z - pi.z;
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        hr |= (r2 < rcr2 ? 1u : 0u) << k;
-        ha |= (r2 < rca2 ? 1u : 0u) << k;
+      for (int j = 0; j < 8; ++j) {  // past wn: stale window data, masked below
+        const float4 X = *reinterpret_cast<const float4*>(wx + cb + 4 * j);
+        const float4 Y = *reinterpret_cast<const float4*>(wy + cb + 4 * j);
+        const float4 Z = *reinterpret_cast<const float4*>(wz + cb + 4 * j);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const f2 dx = f2_add(u ? f2_make(X.z, X.w) : f2_make(X.x, X.y), nx);
+          const f2 dy = f2_add(u ? f2_make(Y.z, Y.w) : f2_make(Y.x, Y.y), ny);
+          const f2 dz = f2_add(u ? f2_make(Z.z, Z.w) : f2_make(Z.x, Z.y), nz);
+          const f2 r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
+          const float2 dr = f2_split(f2_add(r2, nrc2)), da = f2_split(f2_add(r2, nra2));
+          r = __funnelshift_l(__float_as_uint(dr.x), r, 1);
+          r = __funnelshift_l(__float_as_uint(dr.y), r, 1);
+          a = __funnelshift_l(__float_as_uint(da.x), a, 1);
+          a = __funnelshift_l(__float_as_uint(da.y), a, 1);
+        }
       }
+      hr = __brev(r);  // candidate k at bit k
+      ha = __brev(a);
       if (wn - k0 < 32) hr &= (1u << (wn - k0)) - 1u;
       ha &= hr;
     };
 
-    if (nrows <= 16 && max_tot <= kNbrWin) {
-      // ---- split path: lanes q and q + 16 test row q against the two halves
-      // of the window; counts are exchanged, so every entry goes straight to
-      // its final place (angular ones first, half 0 before half 1)
-      const int q = lane & 15, hh = lane >> 4;
-      const bool has = q < nrows;
-      const int row = row_of(q);
-      const float4 pi = has ? ws.pos4[row] : make_float4(0.f, 0.f, 0.f, 0.f);
-      const int row_sp = pos4_species(pi);
-      int* lr = ws.nbr_r + (size_t)row * cap;
-      int nr = 0, tot_r = 0, tot_a = 0;
-      for (int sp = 0; sp < S; ++sp) {
-        const int wn = pick(tot, sp);
-        stage(sp, 0, wn);
-        const int nch = (wn + 31) >> 5, mid = (nch + 1) >> 1;
-        const int ch0 = hh ? mid : 0, ch1 = hh ? nch : mid;
-        // the row itself: image 0 in virtual cell 13 of its own species
-        const int ex13 = __shfl_sync(F, pick(bex, sp), 13), st13 = __shfl_sync(F, pick(bst, sp), 13);
-        const int self_k = (row_sp == sp) ? ex13 + (row - st13) : -1;
-        unsigned A[8], R[8];
-        int na_me = 0, nro_me = 0;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int ch = ch0 + i;
-          A[i] = 0u;
-          R[i] = 0u;
-          if (has && ch < ch1) {
+    if (max_tot <= kNbrWin) {
+      // ---- group path: rows in groups of up to 16, h = 32 / 2^ceil(log2(rows))
+      // lanes per row (h >= 2), lane p of a row testing its share of the
+      // window's 32-candidate chunks.  Hit counts are scanned over the h
+      // lanes of the row, so every entry goes straight to its final place
+      // (angular ones first, both kinds in window order).  When the windows
+      // of all species fit, they are staged once for all groups.
+      const bool all_fit = sum_tot <= kNbrWin;
+      if (all_fit) {
+        int wb = 0;
+        for (int sp = 0; sp < S; ++sp) {
+          const int wn = pick(tot, sp);
+          stage(sp, 0, wn, wb);
+          wb += (wn + 31) & ~31;
+        }
+      }
+      for (int r0 = 0; r0 < nrows; r0 += 16) {
+        const int rg = min(16, nrows - r0);
+        const int lh = rg > 8 ? 1 : (rg > 4 ? 2 : (rg > 2 ? 3 : (rg > 1 ? 4 : 5)));  // log2 h
+        const int h = 1 << lh;
+        const int ql = lane >> lh, p = lane & (h - 1);
+        const bool has = ql < rg;
+        const int row = row_of(r0 + ql);
+        const float4 pi = has ? ws.pos4[row] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int row_sp = pos4_species(pi);
+        const f2 nx = f2_make(-pi.x, -pi.x), ny = f2_make(-pi.y, -pi.y), nz = f2_make(-pi.z, -pi.z);
+        int* lr = ws.nbr_r + (size_t)row * cap;
+        int nr = 0, tot_r = 0, tot_a = 0, wb = 0;
+        for (int sp = 0; sp < S; ++sp) {
+          const int wn = pick(tot, sp);
+          if (!all_fit) stage(sp, 0, wn, 0);
+          const int nch = (wn + 31) >> 5;
+          const int ch0 = (p * nch) >> lh, ch1 = ((p + 1) * nch) >> lh;
+          // the row itself: image 0 in virtual cell 13 of its own species
+          const int ex13 = __shfl_sync(F, pick(bex, sp), 13), st13 = __shfl_sync(F, pick(bst, sp), 13);
+          const int self_k = (row_sp == sp) ? ex13 + (row - st13) : -1;
+          // hit masks of the lane's chunks go to the warp's mask buffer, slot
+          // 2i for the angular hits of chunk ch0 + i and 2i + 1 for the
+          // radial-only ones, so one flat loop per lane then walks all of its
+          // hits (the warp pays the largest hit count of a lane, not the sum
+          // over chunks of the per-chunk largest)
+          int na_me = 0, nro_me = 0;
+          unsigned nzs = 0u;  // slots with hits
+#pragma unroll 1
+          for (int i = 0; i < (has ? ch1 - ch0 : 0); ++i) {
+            const int ch = ch0 + i;
             unsigned hr, ha;
-            masks(pi, ch * 32, wn, hr, ha);
+            masks(nx, ny, nz, wb + ch * 32, wb + wn, hr, ha);
             if ((self_k >> 5) == ch) {
               hr &= ~(1u << (self_k & 31));
               ha &= hr;
             }
-            A[i] = ha;
-            R[i] = hr & ~ha;
-            na_me += __popc(A[i]);
-            nro_me += __popc(R[i]);
+            hmask[(2 * i) * 32 + lane] = ha;
+            hmask[(2 * i + 1) * 32 + lane] = hr & ~ha;
+            nzs |= (ha ? 1u : 0u) << (2 * i);
+            nzs |= ((hr & ~ha) ? 1u : 0u) << (2 * i + 1);
+            na_me += __popc(ha);
+            nro_me += __popc(hr & ~ha);
           }
-        }
-        const int na_o = __shfl_xor_sync(F, na_me, 16), nro_o = __shfl_xor_sync(F, nro_me, 16);
-        const int NA = na_me + na_o, NRO = nro_me + nro_o;
-        int apos = nr + (hh ? na_o : 0), rpos = nr + NA + (hh ? nro_o : 0);
-        if (has) {
+          // offsets of the lane's hits within the row's segment
+          int ia = na_me, ir = nro_me;
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int kb = (ch0 + i) * 32;
-            unsigned a = A[i], r = R[i];
-            while (a) {
-              const int k = __ffs(a) - 1;
-              a &= a - 1u;
-              if (apos < cap) lr[apos] = __float_as_int(cand[kb + k].w);
-              ++apos;
-            }
-            while (r) {
-              const int k = __ffs(r) - 1;
-              r &= r - 1u;
-              if (rpos < cap) lr[rpos] = __float_as_int(cand[kb + k].w);
-              ++rpos;
+          for (int o = 1; o < 32; o <<= 1) {
+            if (o >= h) break;
+            const int ya = __shfl_up_sync(F, ia, o, h), yr = __shfl_up_sync(F, ir, o, h);
+            if (p >= o) {
+              ia += ya;
+              ir += yr;
             }
           }
+          const int NA = __shfl_sync(F, ia, h - 1, h), NRO = __shfl_sync(F, ir, h - 1, h);
+          int apos = nr + ia - na_me, rpos = nr + NA + ir - nro_me;
+          {
+            // one step per hit, the same step count for the whole warp (a
+            // nested data-dependent loop would let the lanes drift apart and
+            // run one after another); nz marks the lane's slots still holding hits
+            const int steps = __reduce_max_sync(F, (unsigned)(na_me + nro_me));
+            unsigned nz = has ? nzs : 0u, cur = 0u;
+            int base = 0;
+            bool ang = true;
+            for (int it = 0; it < steps; ++it) {
+              if (cur == 0u && nz != 0u) {
+                const int m = __ffs(nz) - 1;
+                nz &= nz - 1u;
+                cur = hmask[m * 32 + lane];
+                base = wb + (ch0 + (m >> 1)) * 32;
+                ang = (m & 1) == 0;
+              }
+              if (cur != 0u) {
+                const int k = __ffs(cur) - 1;
+                cur &= cur - 1u;
+                const int e = we[base + k];
+                const int q = ang ? apos : rpos;
+                if (q < cap) lr[q] = e;
+                apos += ang ? 1 : 0;
+                rpos += ang ? 0 : 1;
+              }
+            }
+          }
+          __syncwarp();  // the mask buffer and the window are rewritten next
+          // counts clamped to what the list holds, so readers never run past it
+          const int keep = max(0, min(NA + NRO, cap - nr));
+          if (has && p == 0) {
+            ws.cnt_r[(size_t)row * kMaxS + sp] = keep;
+            ws.cnt_a[(size_t)row * kMaxS + sp] = min(NA, keep);
+          }
+          nr += keep;
+          tot_r += NA + NRO;
+          tot_a += NA;
+          if (all_fit) wb += (wn + 31) & ~31;
         }
-        // counts clamped to what the list holds, so readers never run past it
-        const int keep = max(0, min(NA + NRO, cap - nr));
-        if (has && hh == 0) {
-          ws.cnt_r[(size_t)row * kMaxS + sp] = keep;
-          ws.cnt_a[(size_t)row * kMaxS + sp] = min(NA, keep);
+        if (has && p == 0) {
+          for (int sp = S; sp < kMaxS; ++sp) {
+            ws.cnt_r[(size_t)row * kMaxS + sp] = 0;
+            ws.cnt_a[(size_t)row * kMaxS + sp] = 0;
+          }
+          mx_r = max(mx_r, tot_r);
+          mx_a = max(mx_a, tot_a);
         }
-        nr += keep;
-        tot_r += NA + NRO;
-        tot_a += NA;
-      }
-      if (has && hh == 0) {
-        for (int sp = S; sp < kMaxS; ++sp) {
-          ws.cnt_r[(size_t)row * kMaxS + sp] = 0;
-          ws.cnt_a[(size_t)row * kMaxS + sp] = 0;
-        }
-        mx_r = max(mx_r, tot_r);
-        mx_a = max(mx_a, tot_a);
       }
       continue;
     }
@@ -498,6 +568,7 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
       const bool has = q < nrows;
       const int row = row_of(q);
       const float4 pi = has ? ws.pos4[row] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const f2 nx = f2_make(-pi.x, -pi.x), ny = f2_make(-pi.y, -pi.y), nz = f2_make(-pi.z, -pi.z);
       const int self = pack_nbr(row, 13);
       int* lr = ws.nbr_r + (size_t)row * cap;
       int nr = 0, tot_r = 0, tot_a = 0;  // written entries; all entries found
@@ -506,16 +577,16 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
         int wa = 0, wro = 0, ka = 0, kro = 0;  // written / found: angular, radial-only
         for (int w0 = 0; w0 < total; w0 += kNbrWin) {
           const int wn = min(kNbrWin, total - w0);
-          stage(sp, w0, wn);
+          stage(sp, w0, wn, 0);
           if (has) {
             // 32 candidates at a time: hit masks first (no branches), then the hits
             for (int k0 = 0; k0 < wn; k0 += 32) {
               unsigned hr, ha;
-              masks(pi, k0, wn, hr, ha);
+              masks(nx, ny, nz, k0, wn, hr, ha);
               while (hr) {
                 const int k = __ffs(hr) - 1;
                 hr &= hr - 1u;
-                const int e = __float_as_int(cand[k0 + k].w);
+                const int e = we[k0 + k];
                 if (e == self) continue;
                 const bool room = nr + wa + wro < cap;
                 if ((ha >> k) & 1u) {
@@ -575,7 +646,7 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
 
 size_t neighbors_smem(int cap_r) {
   (void)cap_r;
-  return sizeof(float4) * kNbrWin * (kNbrThreads / 32);
+  return sizeof(float) * kNbrWarpFloats * (kNbrThreads / 32);
 }
 
 cudaError_t neighbors_set_smem_limits() {

@@ -36,6 +36,10 @@ constexpr int kMaxCapR = 512;    // largest radial-neighbour capacity (gathered 
 constexpr int kScanSmemBins = 16384;  // k_scan stages up to this many bins in shared memory
 constexpr int kNbrThreads = 128;  // k_neighbors: warp per cell, lane per row
 constexpr int kNbrWin = 512;      // neighbourhood atoms one warp stages per window
+constexpr int kNbrChunks = kNbrWin / 32;  // window chunks of 32 candidates
+constexpr int kNbrChunkStride = 36;       // floats per chunk in shared memory (bank spread)
+// shared floats per k_neighbors warp: x, y, z chunks, entries, 16 x 32 hit masks
+constexpr int kNbrWarpFloats = 3 * kNbrChunks * kNbrChunkStride + kNbrWin + 16 * 32;
 constexpr int kMaxD = kNRad * kMaxS + kNAng * kMaxS * (kMaxS + 1) / 2;  // 384
 
 // Error flag words (device): set by kernels, read by the host after sync.
@@ -151,6 +155,35 @@ __device__ __forceinline__ float3 image_shift(int code, const float ell[3]) {
 
 __device__ __forceinline__ int nbr_row(int e) { return e & 0x07FFFFFF; }
 __device__ __forceinline__ int nbr_code(int e) { return (int)((unsigned)e >> 27); }
+// packed FP32 pair (fma/mul.rn.f32x2: one instruction for two lanes of arithmetic)
+struct f2 {
+  unsigned long long v;
+};
+__device__ __forceinline__ f2 f2_make(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 f2_split(f2 x) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(x.v));
+  return r;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
 __device__ __forceinline__ int pack_nbr(int row, int code) {
   return (int)((unsigned)row | ((unsigned)code << 27));
 }
