@@ -109,52 +109,52 @@ __device__ __forceinline__ float hw_sum(float x) {
 // angular neighbours.  Off-diagonal blocks: t = q n2 + r.  Diagonal blocks
 // (n atoms): each unordered pair once, as (q, q + k mod n) with k <= K for the
 // first n K indices (K = (n-1)/2, or n/2 - 1 for even n), then (q, q + n/2).
+//
+// The quotient q = t / K comes from one multiply by mg = ceil(2^31 / K):
+// for t < 2^15 and K <= 2^15 the error t (mg - 2^31 / K) / 2^31 stays below
+// 1 / K, so the floor is exact.  No branches: the wrap of a diagonal block
+// and its tail (even n) are selects.
 struct PairMap {
-  int n1, n2, o1, o2, K, nK;
-  float inv;
-  bool diag;
+  int K, nK, o1, vb, vq, n;  // off-diagonal: vq = 0, n = 0 (no wrap), nK = INT_MAX (no tail)
+  unsigned mg;
 };
+
+__device__ __forceinline__ unsigned div_magic(int K) { return (0x80000000u + (unsigned)K - 1u) / (unsigned)K; }
+__device__ __forceinline__ int div_by_magic(int t, unsigned mg) {
+  return (int)(((unsigned long long)(unsigned)t * mg) >> 31);
+}
 
 __device__ __forceinline__ PairMap make_map(bool diag, int n1, int n2, int o1, int o2) {
   PairMap m;
-  m.diag = diag;
-  m.n1 = n1;
-  m.n2 = n2;
   m.o1 = o1;
-  m.o2 = o2;
   if (diag) {
     m.K = (n1 & 1) ? (n1 - 1) / 2 : n1 / 2 - 1;
     if (m.K < 0) m.K = 0;
     m.nK = n1 * m.K;
-    m.inv = m.K > 0 ? 1.0f / (float)m.K : 0.f;
+    m.vb = 1;  // v = u + 1 + r, wrapped into the block
+    m.vq = 1;
+    m.n = n1;
   } else {
     m.K = n2;
-    m.nK = 0;
-    m.inv = n2 > 0 ? 1.0f / (float)n2 : 0.f;
+    m.nK = 0x7fffffff;
+    m.vb = o2;  // v = o2 + r
+    m.vq = 0;
+    m.n = 0;
   }
+  m.mg = div_magic(max(m.K, 1));
   return m;
 }
 
 __device__ __forceinline__ void map_pair(const PairMap& m, int t, int& u, int& v) {
-  if (!m.diag || t < m.nK) {
-    int q = (int)(((float)t + 0.5f) * m.inv);
-    if (q * m.K > t) --q;
-    else if ((q + 1) * m.K <= t) ++q;
-    const int r = t - q * m.K;
-    if (!m.diag) {
-      u = m.o1 + q;
-      v = m.o2 + r;
-    } else {
-      int vv = q + r + 1;
-      if (vv >= m.n1) vv -= m.n1;
-      u = m.o1 + q;
-      v = m.o1 + vv;
-    }
-  } else {
-    const int tt = t - m.nK;
-    u = m.o1 + tt;
-    v = m.o1 + tt + (m.n1 >> 1);
-  }
+  const int q = div_by_magic(t, m.mg);
+  const int r = t - q * m.K;
+  const int uu = m.o1 + q;
+  int vv = m.vb + r + m.vq * uu;
+  vv -= vv >= m.o1 + m.n ? m.n : 0;
+  const int tt = t - m.nK;
+  const bool tail = tt >= 0;  // diagonal, even n: (q, q + n/2)
+  u = tail ? m.o1 + tt : uu;
+  v = tail ? m.o1 + tt + (m.n >> 1) : vv;
 }
 
 // 2^x (MUFU; results below the normal range flush to zero)
