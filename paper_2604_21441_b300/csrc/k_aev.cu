@@ -168,14 +168,6 @@ __device__ __forceinline__ f2 f2_ex2(f2 x) {
   return f2_make(ex2(h.x), ex2(h.y));
 }
 
-// q = t / n for 0 <= t < 2^22 (float reciprocal, one correction step)
-__device__ __forceinline__ int div_small(int t, int n, float inv) {
-  int q = (int)(((float)t + 0.5f) * inv);
-  if (q * n > t) --q;
-  else if ((q + 1) * n <= t) ++q;
-  return q;
-}
-
 __device__ __forceinline__ float4 shift_vec(int code, const float* ell) {
   const int mx = code / 9 - 1, my = (code / 3) % 3 - 1, mz = code % 3 - 1;
   return make_float4(mx * ell[0], my * ell[1], mz * ell[2], 0.f);
@@ -443,15 +435,17 @@ __device__ __forceinline__ void red_add_f3(float4* acc, float x, float y, float 
                : "memory");
 }
 
-// One species-pair block of a row's angular pairs (per-warp table in shared memory).
+// One species-pair block of a row's angular pairs (per-warp table in shared
+// memory).  Pair tl of the block: q = tl / K (multiply by mg), u = tl - q K,
+// v = u + q + vq wrapped into [0, W); diagonal blocks of even n end with
+// (tl - nK, tl - nK + half).
 struct PairBlock {
   int base, T;      // first flat index, pairs
-  int ma, mb;       // list lengths: a (u role), b (v role); diagonal: ma = mb = n
-  int oa, ob;       // staging offsets of the lists
-  int nK, half;     // diagonal: n K (round-robin part), n / 2 if n is even else 0
-  int sa, sb;       // species of the lists
+  int K, W, vq;     // diagonal: K = W = n, vq = 1; off-diagonal: K = ma, W = mb, vq = 0
+  int oa, ob;       // staging offsets of the lists (a: u role, b: v role)
+  int nK, half;     // diagonal: n K (round-robin part), n / 2 if n is even else 0; off: INT_MAX, 0
   int wo;           // offset of the block's 32 weights in dE/dG
-  float inv;        // 1 / n (diagonal) or 1 / ma (off-diagonal)
+  unsigned mg;      // ceil(2^31 / K)
 };
 
 
@@ -565,26 +559,24 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
           if (s1 == s2) {
             const int n = na[s1];
             const int K = (n & 1) ? (n - 1) / 2 : max(0, n / 2 - 1);
-            pb.ma = pb.mb = n;
+            pb.K = pb.W = n;
+            pb.vq = 1;
             pb.oa = pb.ob = oa[s1];
-            pb.sa = pb.sb = s1;
             pb.nK = n * K;
             pb.half = (n & 1) ? 0 : n / 2;
             pb.T = pb.nK + pb.half;
-            pb.inv = n > 0 ? 1.f / (float)n : 0.f;
           } else {
             const bool sw = na[s1] > na[s2];  // list a is the shorter one
-            pb.ma = sw ? na[s2] : na[s1];
-            pb.mb = sw ? na[s1] : na[s2];
+            pb.K = sw ? na[s2] : na[s1];
+            pb.W = sw ? na[s1] : na[s2];
+            pb.vq = 0;
             pb.oa = sw ? oa[s2] : oa[s1];
             pb.ob = sw ? oa[s1] : oa[s2];
-            pb.sa = sw ? s2 : s1;
-            pb.sb = sw ? s1 : s2;
-            pb.nK = 0;
+            pb.nK = 0x7fffffff;
             pb.half = 0;
-            pb.T = pb.ma * pb.mb;
-            pb.inv = pb.ma > 0 ? 1.f / (float)pb.ma : 0.f;
+            pb.T = pb.K * pb.W;
           }
+          pb.mg = div_magic(max(pb.K, 1));
           if (lane == b) blk[b] = pb;
           Ttot += pb.T;
         }
@@ -655,23 +647,14 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
       for (int t = lane; t < Ttot; t += 32) {
         while (b + 1 < NB && t >= pb.base + pb.T) pb = blk[++b];
         const int tl = t - pb.base;
-        int u, v;
-        if (pb.sa == pb.sb) {
-          const int n = pb.ma;
-          if (tl < pb.nK) {
-            const int q = div_small(tl, n, pb.inv);
-            u = tl - q * n;
-            v = u + q + 1;
-            if (v >= n) v -= n;
-          } else {
-            u = tl - pb.nK;
-            v = u + pb.half;
-          }
-        } else {
-          const int d = div_small(tl, pb.ma, pb.inv);
-          u = tl - d * pb.ma;
-          v = u + d;
-          if (v >= pb.mb) v -= pb.mb;
+        const int q = div_by_magic(tl, pb.mg);
+        int u = tl - q * pb.K;
+        int v = u + q + pb.vq;
+        v -= v >= pb.W ? pb.W : 0;
+        const int tt = tl - pb.nK;
+        if (tt >= 0) {  // select: diagonal tail (u, u + n/2)
+          u = tt;
+          v = tt + pb.half;
         }
         u += pb.oa;
         v += pb.ob;
