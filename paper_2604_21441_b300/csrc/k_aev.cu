@@ -119,7 +119,15 @@ struct PairMap {
   unsigned mg;
 };
 
-__device__ __forceinline__ unsigned div_magic(int K) { return (0x80000000u + (unsigned)K - 1u) / (unsigned)K; }
+// ceil(2^31 / K) for the list lengths K <= kMaxCapA (entry 0 holds K = 1's)
+struct DivMagic {
+  unsigned v[kMaxCapA + 1];
+  constexpr DivMagic() : v() {
+    for (int k = 0; k <= kMaxCapA; ++k) v[k] = (0x80000000u + (unsigned)(k > 0 ? k : 1) - 1u) / (unsigned)(k > 0 ? k : 1);
+  }
+};
+__constant__ DivMagic c_div_magic = DivMagic();
+__device__ __forceinline__ unsigned div_magic(int K) { return c_div_magic.v[K]; }
 __device__ __forceinline__ int div_by_magic(int t, unsigned mg) {
   return (int)(((unsigned long long)(unsigned)t * mg) >> 31);
 }
@@ -141,7 +149,7 @@ __device__ __forceinline__ PairMap make_map(bool diag, int n1, int n2, int o1, i
     m.vq = 0;
     m.n = 0;
   }
-  m.mg = div_magic(max(m.K, 1));
+  m.mg = div_magic(m.K);
   return m;
 }
 
@@ -576,7 +584,7 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
             pb.half = 0;
             pb.T = pb.K * pb.W;
           }
-          pb.mg = div_magic(max(pb.K, 1));
+          pb.mg = div_magic(pb.K);
           if (lane == b) blk[b] = pb;
           Ttot += pb.T;
         }
