@@ -366,35 +366,23 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
         if (sp == t) x = a[t];
       return x;
     };
-    // stage the window [w0, w0 + wn) of species sp's neighbourhood: lane t
-    // finds the virtual cell of candidate w0 + t by a binary search over the
-    // cells' offsets, so that all of its position loads are independent
+    // stage the window [w0, w0 + wn) of species sp's neighbourhood: lane v <
+    // 27 copies the atoms of virtual cell v (shifted by its image offset) to
+    // their places bex[v] + k; the loads of the 27 cells are independent
+    const float vsx = (float)(lane / 9 - 1) * ell0, vsy = (float)((lane / 3) % 3 - 1) * ell1,
+                vsz = (float)(lane % 3 - 1) * ell2;
     auto stage = [&](int sp, int w0, int wn, int db) {
-      const int bex_s = pick(bex, sp), bst_s = pick(bst, sp);
+      const int bex_s = pick(bex, sp), bst_s = pick(bst, sp), bln_s = pick(bln, sp);
+      const int k0 = max(0, w0 - bex_s), k1 = min(bln_s, w0 + wn - bex_s);
       __syncwarp();  // the previous window has been read
 #pragma unroll 4
-      for (int t0 = 0; t0 < wn; t0 += 32) {
-        const int t = t0 + lane, tt = w0 + t;
-        int lo = 0, hi = 26;
-#pragma unroll
-        for (int it = 0; it < 5; ++it) {  // largest v with offset(v) <= tt
-          const int mid = (lo + hi + 1) >> 1;
-          const int om = __shfl_sync(F, bex_s, mid);
-          if (om <= tt) lo = mid;
-          else hi = mid - 1;
-        }
-        const int ex_v = __shfl_sync(F, bex_s, lo), st_v = __shfl_sync(F, bst_s, lo);
-        if (t < wn) {
-          const int k = tt - ex_v;
-          const float4 pj = ws.pos4[st_v + k];
-          const float sx = (float)(lo / 9 - 1) * ell0, sy = (float)((lo / 3) % 3 - 1) * ell1,
-                      sz = (float)(lo % 3 - 1) * ell2;
-          const int gi = db + t, ci = (gi >> 5) * kNbrChunkStride + (gi & 31);
-          wx[ci] = pj.x + sx;
-          wy[ci] = pj.y + sy;
-          wz[ci] = pj.z + sz;
-          we[gi] = pack_nbr(st_v + k, lo);
-        }
+      for (int k = k0; k < k1; ++k) {
+        const float4 pj = ws.pos4[bst_s + k];
+        const int gi = db + bex_s + k - w0, ci = (gi >> 5) * kNbrChunkStride + (gi & 31);
+        wx[ci] = pj.x + vsx;
+        wy[ci] = pj.y + vsy;
+        wz[ci] = pj.z + vsz;
+        we[gi] = pack_nbr(bst_s + k, lane);
       }
       __syncwarp();
     };
