@@ -491,16 +491,16 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
   const float kfr = kPi / (2.f * P.rc_r), kfa = kPi / (2.f * P.rc_a);
   const float zeta = (float)(1 << P.zeta_sq);
   // sector constants in pairs (z, z+1): base = 1/2 + uc hc + sn hs,
-  // d(base^zeta)/dc = base^(zeta-1) (Kc - (uc/sn) Ks) with K = 0.95 zeta h
-  f2 hc2[4], hs2[4], kc2[4], ks2[4];
+  // d(base^zeta)/dc = 0.95 zeta base^(zeta-1) (hc - (uc/sn) hs); the factor
+  // 0.95 zeta (times the angular term's 2) is applied once per pair (dcs)
+  f2 hc2[4], hs2[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     hc2[q] = f2_make(P.hcos_z[2 * q], P.hcos_z[2 * q + 1]);
     hs2[q] = f2_make(P.hsin_z[2 * q], P.hsin_z[2 * q + 1]);
-    kc2[q] = f2_make(0.95f * zeta * P.hcos_z[2 * q], 0.95f * zeta * P.hcos_z[2 * q + 1]);
-    ks2[q] = f2_make(-0.95f * zeta * P.hsin_z[2 * q], -0.95f * zeta * P.hsin_z[2 * q + 1]);
   }
   const f2 half2 = f2_make(0.5f, 0.5f);
+  const float dcs = 1.9f * zeta;
   const int rows = ws.seg[S];
   const int wpb = blockDim.x >> 5;
   const int rstride = gridDim.x * wpb;
@@ -681,7 +681,7 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
           Be[a] = ex2(ka * x * x);
           Bq[a] = -2.f * P.eta_a * x * Be[a];
         }
-        const f2 uc2 = f2_make(uc, uc), sn2 = f2_make(sn, sn), ucisn2 = f2_make(ucisn, ucisn);
+        const f2 uc2 = f2_make(uc, uc), sn2 = f2_make(sn, sn), nucisn2 = f2_make(-ucisn, -ucisn);
         const float* wb = wsm + pb.wo;
         f2 X2[kNAngR], Y2[kNAngR];
 #pragma unroll
@@ -706,7 +706,7 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
             pw = f2_make(b0z, b1z);
             pm1 = f2_make(b0m, b1m);
           }
-          const f2 dA = f2_mul(pm1, f2_fma(ucisn2, ks2[zp], kc2[zp]));
+          const f2 dA = f2_mul(pm1, f2_fma(nucisn2, hs2[zp], hc2[zp]));  // d(base^zeta)/dc / (0.95 zeta)
 #pragma unroll
           for (int a = 0; a < kNAngR; ++a) {
             const float4 w4 = reinterpret_cast<const float4*>(wb + a * kNAngZ)[zp >> 1];
@@ -734,7 +734,7 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
         const float fuv = fu * fv;
         const float dEdru = 2.f * fmaf(au.y * fv, Pv, 0.5f * fuv * Qv);
         const float dEdrv = 2.f * fmaf(fu * av.y, Pv, 0.5f * fuv * Qv);
-        const float dEdc = 2.f * fuv * Rv;
+        const float dEdc = dcs * fuv * Rv;
         // d cos/d d_u = (e_v - c e_u)/r_u ; d cos/d d_v = (e_u - c e_v)/r_v
         const float Au = fmaf(-dEdc * c, au.z, dEdru), Bu = dEdc * au.z;
         const float Av = fmaf(-dEdc * c, av.z, dEdrv), Bv = dEdc * av.z;
