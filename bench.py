@@ -337,6 +337,51 @@ def nve_rate(precision, steps=400):
             "rollbacks": md.retries}
 
 
+def mlmm_rate(precision, steps=50):
+    """ML/MM mechanical embedding through nnp_eval_mlmm (device buffers) on
+    the 4,096-water box: the first 2,048 waters form the ML group, and 64 of
+    them have one O-H bond cut (the H is MM, a link atom at 1 A replaces it).
+    Each call validates the index sets, gathers the subsystem, evaluates it
+    and scatters the forces to all 12,288 atoms; it is synchronous, so it is
+    timed by wall clock.  The plain evaluation of a subsystem of the same size
+    is timed beside it."""
+    import torch
+    import synth
+    import paper_2604_21441_b300 as P
+    wl = synth.workload(2)
+    s = wl["systems"][0]
+    w = synth.xavier_weights(2, 128, wl["weight_seed"])
+    pot = P.NNP(atomic_numbers=(1, 8), precision=precision, max_atoms=s.n)
+    pot.set_all_weights([[(W.astype(np.float32), b.astype(np.float32)) for W, b in x] for x in w])
+    cut = np.arange(0, 2048, 32)
+    group = np.setdiff1d(np.arange(3 * 2048), 3 * cut + 1)
+    dev = lambda a: torch.tensor(a, device="cuda")
+    pos, Z = dev(s.pos), dev(s.Z.astype(np.int32))
+    ml, lml, lmm = dev(group.astype(np.int64)), dev((3 * cut).astype(np.int64)), dev((3 * cut + 1).astype(np.int64))
+    box = np.diag(s.box)
+    for _ in range(5):
+        pot.eval_mlmm(pos, Z, ml, lml, lmm, None, 1, box=box)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        pot.eval_mlmm(pos, Z, ml, lml, lmm, None, 1, box=box)
+    ms = (time.perf_counter() - t0) * 1e3 / steps
+    n_sub = len(group) + len(cut)
+    sub_pos, sub_Z = pos[:n_sub].contiguous(), Z[:n_sub].contiguous()
+    for _ in range(5):
+        pot.eval(sub_pos, sub_Z, box)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        pot.eval(sub_pos, sub_Z, box)
+    ms_plain = (time.perf_counter() - t0) * 1e3 / steps
+    pot.close()
+    return {"workload": "water-4096 (12,288 atoms): 2,048-water ML group, 64 link atoms",
+            "precision": precision, "subsystem_atoms": n_sub, "links": len(cut), "steps": steps,
+            "ms_per_step": ms, "subsystem_atom_steps_per_s": n_sub / (ms * 1e-3),
+            "plain_eval_ms_same_size": ms_plain}
+
+
 def oracle_sample(wl, w, seconds=20.0, seed=0):
     """Time the FP64 oracle on bounded samples of the workload: sampled atoms
     get E_i and F_i, which evaluates them and every atom within the radial
@@ -489,6 +534,7 @@ def main():
     }
     if args.workload == 3:  # the paper reports MD throughput in ns/day
         line["nve"] = nve_rate(args.precision)
+        line["mlmm"] = mlmm_rate(args.precision)
     if r["per_system_ms"] is not None:
         line["batch"] = {"systems": r["B"], "one_graph_launch_ms": ms_mean,
                          "one_launch_per_system_ms": r["per_system_ms"],

@@ -227,6 +227,36 @@ int64_t nnp_param_count(const nnp_ctx *ctx);
 int nnp_force_match_grad(nnp_ctx *ctx, const double *v, const double *Fref, double *loss,
                          double *grad);
 
+/* ML/MM mechanical embedding (Sec. Methods, the nnpot interface and its
+ * link-atom equation).  The NNP sees the ML group plus one link atom per cut
+ * ML-MM bond; the rest of the n_total-atom system is MM and gets no force
+ * from here except through the links.
+ *   pos, Z     n_total x 3 doubles (A) and n_total atomic numbers of the whole
+ *              system (host or device);
+ *   box        as in nnp_eval (3 x 3 rows; orthorhombic only; NULL = open);
+ *   ml_index   n_ml distinct indices into [0, n_total) (host or device): the
+ *              group, in the order the NNP sees it;
+ *   link_ml, link_mm  n_link atom pairs of the cut bonds (host or device):
+ *              link_ml[l] in the group, link_mm[l] outside it;
+ *   link_d     n_link distances d (A) of the link atoms from their ML atoms,
+ *              or NULL for 1 A each; link_Z the link atoms' atomic number
+ *              (<= 0: hydrogen).
+ * Link atom l sits at r_L = r_ML + d (r_MM - r_ML) / |r_MM - r_ML| (minimum
+ * image of r_MM - r_ML in the box) and is evaluated as an ordinary ML atom,
+ * after the group's atoms.  Outputs: *energy (eV) of the subsystem and
+ * forces (n_total x 3, eV/A, host or device, overwritten): the group's atoms
+ * get their own NNP force, atoms outside the group zero, and each link
+ * atom's force F_L is passed on by the chain rule:
+ *   F_MM += (d / |R|) (F_L - u (u . F_L)),  F_ML += F_L - (that),  u = R / |R|.
+ * Errors: NNP_ERR_INVALID_ARG for an index out of range, a repeated group
+ * index, a link whose ML atom is outside the group or whose MM atom is
+ * inside it, d <= 0, or a zero-length bond; NNP_ERR_UNSUPPORTED for a
+ * non-orthorhombic box.  Synchronous on the context's stream. */
+int nnp_eval_mlmm(nnp_ctx *ctx, int64_t n_total, const double *pos, const int32_t *Z,
+                  const double *box, int64_t n_ml, const int64_t *ml_index, int32_t n_link,
+                  const int64_t *link_ml, const int64_t *link_mm, const double *link_d,
+                  int32_t link_Z, double *energy, double *forces);
+
 /* Per-atom energies E_i (eV) of the last evaluation, in input order
  * (n doubles for nnp_eval, offsets[B] for nnp_eval_batch), host pointer.
  * Synchronises the context's stream. */

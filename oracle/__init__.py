@@ -21,6 +21,9 @@ energy_forces              : pinned (finite differences, sum F = 0,
                              translation / rotation / permutation invariance)
 aev_jvp, force_match       : pinned (finite differences in positions and in
                              weights)
+mlmm_energy_forces         : pinned (finite differences of the embedded energy
+                             in the whole system's coordinates, zero net
+                             force, a link placed on its MM atom)
 """
 from __future__ import annotations
 
@@ -302,3 +305,50 @@ def force_match(model: Model, pos, species, box, Fref):
     lib().or_force_match(model.ref, n, _dp(pos), _ip(species), None if bx is None else _dp(bx),
                          _dp(Fref), _dp(L), PW, PB, _dp(F))
     return float(L[0]), dW, db, F
+
+
+def mlmm_energy_forces(model: Model, pos, species, box, ml_index, link_ml, link_mm, link_d,
+                       link_species):
+    """ML/MM mechanical embedding (Sec. Methods, the nnpot interface and its
+    link-atom equation): the NNP on the ML group (pos[ml_index], in that
+    order) followed by one link atom per cut bond at
+        r_L = r_ML + d (r_MM - r_ML) / |r_MM - r_ML|
+    (minimum image in the orthorhombic box), of species link_species.
+    Returns E, the forces on all atoms (group atoms their own, link forces
+    passed to the bonded pair by the chain rule of that equation, all other
+    atoms zero) and the subsystem's atom energies (group, then links)."""
+    pos = np.asarray(pos, dtype=np.float64)
+    species = np.asarray(species)
+    ml_index = np.asarray(ml_index, dtype=np.int64)
+    link_ml = np.asarray(link_ml, dtype=np.int64)
+    link_mm = np.asarray(link_mm, dtype=np.int64)
+    nl = len(link_ml)
+    d = np.ones(nl) if link_d is None else np.asarray(link_d, dtype=np.float64)
+    L = None if box is None else np.asarray(box, dtype=np.float64)
+
+    def bond(i, j):
+        R = pos[j] - pos[i]
+        if L is not None:
+            R = R - L * np.round(R / L)
+        return R
+
+    sub = [pos[a] for a in ml_index]
+    for l in range(nl):
+        R = bond(link_ml[l], link_mm[l])
+        sub.append(pos[link_ml[l]] + d[l] * R / np.linalg.norm(R))
+    sub = np.array(sub)
+    sub_species = np.concatenate([species[ml_index], np.full(nl, link_species)]).astype(np.int32)
+    E, Ei, Fs, _ = energy_forces(model, sub, sub_species, box)
+    F = np.zeros_like(pos)
+    F[ml_index] = Fs[:len(ml_index)]
+    for l in range(nl):
+        i, j = link_ml[l], link_mm[l]
+        R = bond(i, j)
+        r = np.linalg.norm(R)
+        u = R / r
+        FL = Fs[len(ml_index) + l]
+        # dr_L/dr_MM = (d/r)(I - u u^T) (symmetric); dr_L/dr_ML = I - dr_L/dr_MM
+        J = (d[l] / r) * (np.eye(3) - np.outer(u, u))
+        F[j] += J @ FL
+        F[i] += FL - J @ FL
+    return E, F, Ei

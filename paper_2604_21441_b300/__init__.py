@@ -39,7 +39,7 @@ STAGES = ("cells", "neighbours", "descriptor", "network", "descriptor_backward")
 ABI_FUNCTIONS = ("nnp_config_init", "nnp_create", "nnp_destroy", "nnp_last_error",
                  "nnp_set_weights", "nnp_eval", "nnp_eval_async", "nnp_sync",
                  "nnp_eval_batch", "nnp_param_count", "nnp_force_match_grad", "nnp_query",
-                 "nnp_profile_stages", "nnp_atom_energies", "nnp_eval_noalloc",
+                 "nnp_profile_stages", "nnp_atom_energies", "nnp_eval_noalloc", "nnp_eval_mlmm",
                  "nnp_eval_batch_async")
 
 QUERY = {"launches_per_eval": 0, "nbr_capacity": 1, "ang_capacity": 2, "max_nbr": 3,
@@ -125,6 +125,8 @@ def lib() -> ctypes.CDLL:
     L.nnp_atom_energies.restype = ctypes.c_int
     L.nnp_eval_noalloc.argtypes = [vp, i64, dp, dp, dp, dp, dp]
     L.nnp_eval_noalloc.restype = ctypes.c_int
+    L.nnp_eval_mlmm.argtypes = [vp, i64, dp, dp, dp, i64, dp, i32, dp, dp, dp, i32, dp, dp]
+    L.nnp_eval_mlmm.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -139,7 +141,8 @@ def _ptr(x, dtype):
         return None, None
     if _is_torch(x):
         import torch
-        tdt = {np.float64: torch.float64, np.int32: torch.int32, np.float32: torch.float32}[dtype]
+        tdt = {np.float64: torch.float64, np.int32: torch.int32, np.float32: torch.float32,
+               np.int64: torch.int64}[dtype]
         if x.dtype != tdt or not x.is_contiguous():
             x = x.to(tdt).contiguous()
         return ctypes.c_void_p(x.data_ptr()), x
@@ -273,6 +276,35 @@ class NNP:
         self._check(fn(self._h, int(pos.shape[0]), ctypes.c_void_p(pos.data_ptr()),
                        ctypes.c_void_p(Z.data_ptr()), ctypes.c_void_p(b9.ctypes.data),
                        ctypes.c_void_p(E_out.data_ptr()), ctypes.c_void_p(F_out.data_ptr())))
+
+    def eval_mlmm(self, pos, Z, ml_index, link_ml=(), link_mm=(), link_d=None, link_Z=1, box=None):
+        """ML/MM mechanical embedding: energy of the ML group plus link atoms,
+        and forces on all atoms of the system (same library/device as pos)."""
+        n = int(pos.shape[0])
+        pp, kp = _ptr(pos, np.float64)
+        pz, kz = _ptr(Z, np.int32)
+        mi, kmi = _ptr(ml_index, np.int64)
+        n_ml = int(ml_index.shape[0]) if hasattr(ml_index, "shape") else len(ml_index)
+        n_link = len(link_ml)
+        if n_link:
+            pl, kl = _ptr(link_ml, np.int64)
+            pm, km = _ptr(link_mm, np.int64)
+        else:
+            pl = pm = None
+        pd, kd = _ptr(link_d, np.float64) if link_d is not None else (None, None)
+        b9 = _box9(box)
+        pbox = None if b9 is None else ctypes.c_void_p(b9.ctypes.data)
+        if _is_torch(pos):
+            import torch
+            E = torch.zeros(1, dtype=torch.float64, device=pos.device)
+            F = torch.empty((n, 3), dtype=torch.float64, device=pos.device)
+            pE, pF = ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(F.data_ptr())
+        else:
+            E, F = np.zeros(1), np.empty((n, 3))
+            pE, pF = ctypes.c_void_p(E.ctypes.data), ctypes.c_void_p(F.ctypes.data)
+        self._check(self._L.nnp_eval_mlmm(self._h, n, pp, pz, pbox, n_ml, mi, n_link, pl, pm, pd,
+                                          int(link_Z), pE, pF))
+        return (float(E[0]) if not _is_torch(pos) else E[0]), F
 
     def sync(self):
         self._check(self._L.nnp_sync(self._h))

@@ -90,9 +90,11 @@ nnp_ctx::~nnp_ctx() {
                   b_atom_sys, b_atom_off, b_row_atom, b_row_info, b_row_cell, b_pos4, b_cnt_r,
                   b_cnt_a, b_nbr_r, b_G, b_dEdG, b_Ei, b_facc, b_Gh, b_sys, b_pos_stage,
                   b_Z_stage, b_F_stage, b_E_stage, b_seg, b_flags, d_zlut, d_io, b_wf32,
-                  fm_z, fm_dz, fm_t, fm_p, fm_v, fm_ref, fm_grad, fm_jobs};
+                  fm_z, fm_dz, fm_t, fm_p, fm_v, fm_ref, fm_grad, fm_jobs,
+                  mm.pos, mm.F, mm.sub_pos, mm.sub_F, mm.ld, mm.E, mm.Z, mm.sub_Z, mm.idx, mm.mark};
   for (void* p : bufs)
     if (p) cudaFree(p);
+  if (mm.h_bad) cudaFreeHost(mm.h_bad);
   for (auto& ev : stage_ev)
     if (ev) cudaEventDestroy(ev);
   for (auto& sg : stages) {

@@ -124,6 +124,19 @@ struct nnp_ctx {
   size_t fm_cap = 0, fm_cap2 = 0, fm_cap3 = 0, fm_cap4 = 0, fm_vcap = 0, fm_refcap = 0, fm_gcap = 0, fm_jcap = 0;
   static bool is_device(const void* p);
 
+  // ML/MM embedding buffers (nnp_mlmm.cu; allocated on first use)
+  struct MlmmBufs {
+    double *pos = nullptr, *F = nullptr, *sub_pos = nullptr, *sub_F = nullptr, *ld = nullptr, *E = nullptr;
+    int32_t *Z = nullptr, *sub_Z = nullptr;
+    int64_t* idx = nullptr;
+    int* mark = nullptr;   // group membership (device index sets)
+    int* h_bad = nullptr;  // pinned: validation bits of the last call
+    std::vector<unsigned char> mark_host;
+    std::vector<double> ld_host;
+    size_t c_pos = 0, c_F = 0, c_sub_pos = 0, c_sub_F = 0, c_ld = 0, c_E = 0, c_Z = 0, c_sub_Z = 0, c_idx = 0,
+           c_mark = 0;
+  } mm;
+
   // launch shape (blocks per SM caps), chosen by the autotuner (NNP_FLAG_AUTOTUNE)
   struct Tune { int nbr = 16, fwd = 8, bwd = 16; } tune;
   long long tuned_key = -1;
