@@ -382,6 +382,44 @@ def mlmm_rate(precision, steps=50):
             "plain_eval_ms_same_size": ms_plain}
 
 
+def pairs_rate(precision, steps=20):
+    """The pair-list path (nnp_eval_pairs) on the 32,768-water box: a buffered
+    half list (every pair within 5.6 A once, minimum-image shifts; built once
+    on the host with a k-d tree, resident on the device) replaces the cell
+    search.  Both paths are synchronous calls with device buffers, timed by
+    wall clock over the same number of calls."""
+    import torch
+    import synth
+    import paper_2604_21441_b300 as P
+    from scipy.spatial import cKDTree
+    wl = synth.workload(3)
+    s = wl["systems"][0]
+    w = synth.xavier_weights(2, 128, wl["weight_seed"])
+    L = s.box
+    ij = cKDTree(np.mod(s.pos, L), boxsize=L).query_pairs(5.6, output_type="ndarray")
+    shifts = -L * np.round((s.pos[ij[:, 1]] - s.pos[ij[:, 0]]) / L)
+    pot = P.NNP(atomic_numbers=(1, 8), precision=precision, max_atoms=s.n)
+    pot.set_all_weights([[(W.astype(np.float32), b.astype(np.float32)) for W, b in x] for x in w])
+    dev = lambda a: torch.tensor(a, device="cuda")
+    pos, Z, pr, sh = dev(s.pos), dev(s.Z.astype(np.int32)), dev(ij.astype(np.int32)), dev(shifts)
+    box = np.diag(L)
+    out = {}
+    for name, fn in (("pair_list", lambda: pot.eval_pairs(pos, Z, pr, sh, box)),
+                     ("cell_search", lambda: pot.eval(pos, Z, box))):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            fn()
+        out[name] = (time.perf_counter() - t0) * 1e3 / steps
+    pot.close()
+    return {"workload": "water-32768 (98,304 atoms), half list within 5.6 A", "precision": precision,
+            "pairs": int(len(ij)), "steps": steps, "ms_per_step_pair_list": out["pair_list"],
+            "ms_per_step_cell_search": out["cell_search"],
+            "atom_steps_per_s_pair_list": s.n / (out["pair_list"] * 1e-3)}
+
+
 def oracle_sample(wl, w, seconds=20.0, seed=0):
     """Time the FP64 oracle on bounded samples of the workload: sampled atoms
     get E_i and F_i, which evaluates them and every atom within the radial
@@ -535,6 +573,7 @@ def main():
     if args.workload == 3:  # the paper reports MD throughput in ns/day
         line["nve"] = nve_rate(args.precision)
         line["mlmm"] = mlmm_rate(args.precision)
+        line["pairs"] = pairs_rate(args.precision)
     if r["per_system_ms"] is not None:
         line["batch"] = {"systems": r["B"], "one_graph_launch_ms": ms_mean,
                          "one_launch_per_system_ms": r["per_system_ms"],

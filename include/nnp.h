@@ -157,6 +157,26 @@ int nnp_set_weights(nnp_ctx *ctx, int32_t species, const float *const W[4],
 int nnp_eval(nnp_ctx *ctx, int64_t n, const double *pos, const int32_t *Z,
              const double *box, double *energy, double *forces);
 
+/* As nnp_eval, with the neighbour pairs supplied by the caller instead of the
+ * library's cell search (Methods: the 2026 nnpot interface passes the MD
+ * engine's own pair list to the model).
+ *   pairs   n_pairs x 2 int32 atom indices (i, j), host or device: every
+ *           unordered pair, or periodic self-image (i, i) with a nonzero shift,
+ *           exactly once (a pair listed twice counts twice);
+ *   shifts  n_pairs x 3 doubles (A), host or device, or NULL for none: the
+ *           pair's displacement is r_j - r_i + shift.  With a box, a shift
+ *           must be a whole periodic image (integer multiples of the edges);
+ *           an isolated system (box NULL) takes no shifts.
+ * Pairs whose distance is at or beyond the radial cutoff are ignored, so a
+ * buffered list is fine; a pair inside it enters both atoms' neighbour lists.
+ * A complete list gives the cell search's neighbour sets, hence the same
+ * energy and forces up to the FP32 order of the sums (list order follows
+ * the fill's atomics).  NNP_ERR_INVALID_ARG for an index out of range or a
+ * shift that is not a whole image; list capacities grow as for nnp_eval. */
+int nnp_eval_pairs(nnp_ctx *ctx, int64_t n, const double *pos, const int32_t *Z,
+                   const double *box, int64_t n_pairs, const int32_t *pairs,
+                   const double *shifts, double *energy, double *forces);
+
 /* As nnp_eval, but pos, Z, energy and forces must be device pointers and
  * the call returns without synchronising; device-side flags (unknown species,
  * non-finite position, list overflow) are reported by the next nnp_sync(). */

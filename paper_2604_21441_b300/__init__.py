@@ -39,7 +39,7 @@ STAGES = ("cells", "neighbours", "descriptor", "network", "descriptor_backward")
 ABI_FUNCTIONS = ("nnp_config_init", "nnp_create", "nnp_destroy", "nnp_last_error",
                  "nnp_set_weights", "nnp_eval", "nnp_eval_async", "nnp_sync",
                  "nnp_eval_batch", "nnp_param_count", "nnp_force_match_grad", "nnp_query",
-                 "nnp_profile_stages", "nnp_atom_energies", "nnp_eval_noalloc", "nnp_eval_mlmm",
+                 "nnp_profile_stages", "nnp_atom_energies", "nnp_eval_noalloc", "nnp_eval_mlmm", "nnp_eval_pairs",
                  "nnp_eval_batch_async")
 
 QUERY = {"launches_per_eval": 0, "nbr_capacity": 1, "ang_capacity": 2, "max_nbr": 3,
@@ -127,6 +127,8 @@ def lib() -> ctypes.CDLL:
     L.nnp_eval_noalloc.restype = ctypes.c_int
     L.nnp_eval_mlmm.argtypes = [vp, i64, dp, dp, dp, i64, dp, i32, dp, dp, dp, i32, dp, dp]
     L.nnp_eval_mlmm.restype = ctypes.c_int
+    L.nnp_eval_pairs.argtypes = [vp, i64, dp, dp, dp, i64, dp, dp, dp, dp]
+    L.nnp_eval_pairs.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -304,6 +306,28 @@ class NNP:
             pE, pF = ctypes.c_void_p(E.ctypes.data), ctypes.c_void_p(F.ctypes.data)
         self._check(self._L.nnp_eval_mlmm(self._h, n, pp, pz, pbox, n_ml, mi, n_link, pl, pm, pd,
                                           int(link_Z), pE, pF))
+        return (float(E[0]) if not _is_torch(pos) else E[0]), F
+
+    def eval_pairs(self, pos, Z, pairs, shifts=None, box=None):
+        """Energy and forces with the caller's pair list (n_pairs x 2 atom
+        indices, each unordered pair once; optional n_pairs x 3 shifts)."""
+        n = int(pos.shape[0])
+        pp, kp = _ptr(pos, np.float64)
+        pz, kz = _ptr(Z, np.int32)
+        npairs = int(pairs.shape[0])
+        pq, kq = _ptr(pairs, np.int32)
+        ps, ks = _ptr(shifts, np.float64) if shifts is not None else (None, None)
+        b9 = _box9(box)
+        pbox = None if b9 is None else ctypes.c_void_p(b9.ctypes.data)
+        if _is_torch(pos):
+            import torch
+            E = torch.zeros(1, dtype=torch.float64, device=pos.device)
+            F = torch.empty((n, 3), dtype=torch.float64, device=pos.device)
+            pE, pF = ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(F.data_ptr())
+        else:
+            E, F = np.zeros(1), np.empty((n, 3))
+            pE, pF = ctypes.c_void_p(E.ctypes.data), ctypes.c_void_p(F.ctypes.data)
+        self._check(self._L.nnp_eval_pairs(self._h, n, pp, pz, pbox, npairs, pq, ps, pE, pF))
         return (float(E[0]) if not _is_torch(pos) else E[0]), F
 
     def sync(self):

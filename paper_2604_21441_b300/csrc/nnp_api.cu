@@ -113,6 +113,7 @@ int nnp_ctx::ensure_capacity(long long n, int B, long long bins, long long rows)
   GR(b_Z_stage, c_Z_stage, (size_t)n);
   GR(b_F_stage, c_F_stage, (size_t)n * 3);
   GR(b_E_stage, c_E_stage, (size_t)B);
+  if (ext_mode) GR(b_pair_cur, c_pair_cur, (size_t)rows * 2 * kMaxS);
 #undef GR
   if (changed) invalidate_graph();
   return NNP_OK;
@@ -175,7 +176,16 @@ int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows,
   k_binsort<<<g_bins, 256, 0, stream>>>(io, P.S, (cfg.flags & NNP_FLAG_NONDETERMINISTIC_BINS) ? 0 : 1,
                                         w); ++launches;
   mark_stage(1, capturing);
-  k_neighbors<<<g_cells, kNbrThreads, neighbors_smem(cap_r), stream>>>(io, sys, P, w); ++launches;
+  if (ext_mode) {  // the caller's pair list instead of the cell search
+    const int g_rows = grid_for(rows, 256, nsm * 8), g_pairs = nsm * 16;
+    k_pairs_prep<<<g_rows, 256, 0, stream>>>(P.S, w);
+    k_pairs_count<<<g_pairs, 256, 0, stream>>>(io, sys, P, w);
+    k_pairs_offsets<<<g_rows, 256, 0, stream>>>(io, P.S, w, b_pair_cur);
+    k_pairs_fill<<<g_pairs, 256, 0, stream>>>(io, sys, P, w, b_pair_cur);
+    launches += 4;
+  } else {
+    k_neighbors<<<g_cells, kNbrThreads, neighbors_smem(cap_r), stream>>>(io, sys, P, w); ++launches;
+  }
   mark_stage(2, capturing);
   if (calib) {  // FP8 calibration: FP32 descriptor, then the activation ranges
     launch_aev_fwd(rows, nsm, stream, sys, P, w, kGFp32, tune.fwd);
@@ -371,6 +381,9 @@ int nnp_ctx::evaluate(int B, const int64_t* offsets, const double* pos, const in
     io.n_atoms = n;
     io.n_sys = B;
     io.total_cells = total_cells;
+    io.pairs = ext_pairs;
+    io.shifts = ext_shifts;
+    io.n_pairs = ext_n_pairs;
     if (!pos_dev) CK(cudaMemcpyAsync(b_pos_stage, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, stream));
     if (!Z_dev) CK(cudaMemcpyAsync(b_Z_stage, Z, sizeof(int) * n, cudaMemcpyHostToDevice, stream));
     CK(cudaMemcpyAsync(d_io, sg.io, sizeof(EvalIO), cudaMemcpyHostToDevice, stream));
@@ -390,7 +403,8 @@ int nnp_ctx::evaluate(int B, const int64_t* offsets, const double* pos, const in
     }
     const bool use_graph = !(cfg.flags & NNP_FLAG_NO_GRAPH);
     if (use_graph) {
-      if (!gexec || g_key_n != n || g_key_B != B || g_key_bins != bins) {
+      const int ext = ext_mode ? 1 : 0;
+      if (!gexec || g_key_n != n || g_key_B != B || g_key_bins != bins || g_key_ext != ext) {
         invalidate_graph();
         cudaGraph_t graph;
         CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
@@ -401,7 +415,7 @@ int nnp_ctx::evaluate(int B, const int64_t* offsets, const double* pos, const in
         ce = cudaGraphInstantiate(&gexec, graph, 0);
         cudaGraphDestroy(graph);
         if (ce != cudaSuccess) { gexec = nullptr; return cuda_fail(ce, "cudaGraphInstantiate"); }
-        g_key_n = n; g_key_B = B; g_key_bins = bins;
+        g_key_n = n; g_key_B = B; g_key_bins = bins; g_key_ext = ext;
         ++graph_captures;
       }
       CK(cudaGraphLaunch(gexec, stream));
@@ -430,6 +444,8 @@ int nnp_ctx::check_flags() {
   max_nbr_a = f[kFlagMaxNbrA];
   if (f[kFlagNonFinite]) return fail(NNP_ERR_INVALID_ARG, "non-finite atom position");
   if (f[kFlagBadSpecies]) return fail(NNP_ERR_UNKNOWN_SPECIES, "atomic number outside the configured species");
+  if (f[kFlagBadPair])
+    return fail(NNP_ERR_INVALID_ARG, "pair list: an index is out of range or a shift is not a whole periodic image");
   if (f[kFlagOverflowR] || f[kFlagOverflowA]) {
     if (f[kFlagOverflowR]) cap_r = ((int)(f[kFlagMaxNbrR] * 1.25) + 31) / 32 * 32;
     if (f[kFlagOverflowA]) cap_a = ((int)(f[kFlagMaxNbrA] * 1.25) + 15) / 16 * 16;
@@ -565,6 +581,44 @@ int nnp_eval(nnp_ctx* ctx, int64_t n, const double* pos, const int32_t* Z, const
   if (n <= 0) return ctx->fail(NNP_ERR_INVALID_ARG, "n must be positive");
   int64_t off[2] = {0, n};
   return ctx->evaluate(1, off, pos, Z, box, energy, forces, true);
+}
+
+int nnp_eval_pairs(nnp_ctx* ctx, int64_t n, const double* pos, const int32_t* Z, const double* box,
+                   int64_t n_pairs, const int32_t* pairs, const double* shifts, double* energy, double* forces) {
+  if (!ctx) return NNP_ERR_INVALID_ARG;
+  if (n <= 0) return ctx->fail(NNP_ERR_INVALID_ARG, "n must be positive");
+  if (n_pairs < 0 || (n_pairs > 0 && !pairs)) return ctx->fail(NNP_ERR_INVALID_ARG, "null pair list");
+  if (!box && shifts) return ctx->fail(NNP_ERR_INVALID_ARG, "shifts need a periodic box");
+  const int* d_pairs = pairs;
+  const double* d_shifts = shifts;
+  cudaError_t e = cudaSuccess;
+  const size_t np = (size_t)(n_pairs > 0 ? n_pairs : 1);
+  if (n_pairs > 0 && !is_device_ptr(pairs)) {
+    e = grow(ctx->b_pairs_stage, ctx->c_pairs_stage, 2 * np);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ctx->b_pairs_stage, pairs, sizeof(int) * 2 * n_pairs, cudaMemcpyHostToDevice, ctx->stream);
+    d_pairs = ctx->b_pairs_stage;
+  }
+  if (e == cudaSuccess && shifts && n_pairs > 0 && !is_device_ptr(shifts)) {
+    e = grow(ctx->b_shifts_stage, ctx->c_shifts_stage, 3 * np);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ctx->b_shifts_stage, shifts, sizeof(double) * 3 * n_pairs, cudaMemcpyHostToDevice,
+                          ctx->stream);
+    d_shifts = ctx->b_shifts_stage;
+  }
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "nnp_eval_pairs staging");
+  // an empty list still selects the pair-list path (no neighbours at all)
+  ctx->ext_mode = true;
+  ctx->ext_pairs = n_pairs > 0 ? d_pairs : nullptr;
+  ctx->ext_shifts = n_pairs > 0 ? d_shifts : nullptr;
+  ctx->ext_n_pairs = n_pairs;
+  int64_t off[2] = {0, n};
+  const int rc = ctx->evaluate(1, off, pos, Z, box, energy, forces, true);
+  ctx->ext_mode = false;
+  ctx->ext_pairs = nullptr;
+  ctx->ext_shifts = nullptr;
+  ctx->ext_n_pairs = 0;
+  return rc;
 }
 
 int nnp_eval_async(nnp_ctx* ctx, int64_t n, const double* pos, const int32_t* Z, const double* box,

@@ -91,7 +91,8 @@ nnp_ctx::~nnp_ctx() {
                   b_cnt_a, b_nbr_r, b_G, b_dEdG, b_Ei, b_facc, b_Gh, b_sys, b_pos_stage,
                   b_Z_stage, b_F_stage, b_E_stage, b_seg, b_flags, d_zlut, d_io, b_wf32,
                   fm_z, fm_dz, fm_t, fm_p, fm_v, fm_ref, fm_grad, fm_jobs,
-                  mm.pos, mm.F, mm.sub_pos, mm.sub_F, mm.ld, mm.E, mm.Z, mm.sub_Z, mm.idx, mm.mark};
+                  mm.pos, mm.F, mm.sub_pos, mm.sub_F, mm.ld, mm.E, mm.Z, mm.sub_Z, mm.idx, mm.mark,
+                  b_pair_cur, b_pairs_stage, b_shifts_stage};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (mm.h_bad) cudaFreeHost(mm.h_bad);

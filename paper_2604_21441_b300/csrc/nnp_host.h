@@ -15,6 +15,10 @@ __global__ void k_scan(const EvalIO* io, int S, Workspace ws);
 __global__ void k_scatter(const EvalIO* io, Workspace ws);
 __global__ void k_binsort(const EvalIO* io, int S, int sort, Workspace ws);
 __global__ void k_neighbors(const EvalIO* io, const SysDesc* sys, DescParams P, Workspace ws);
+__global__ void k_pairs_prep(int S, Workspace ws);
+__global__ void k_pairs_count(const EvalIO* io, const SysDesc* sys, DescParams P, Workspace ws);
+__global__ void k_pairs_offsets(const EvalIO* io, int S, Workspace ws, int* cur);
+__global__ void k_pairs_fill(const EvalIO* io, const SysDesc* sys, DescParams P, Workspace ws, int* cur);
 size_t neighbors_smem(int cap_r);
 cudaError_t neighbors_set_smem_limits();
 
@@ -123,6 +127,18 @@ struct nnp_ctx {
   nnp::FmJob* fm_jobs = nullptr;
   size_t fm_cap = 0, fm_cap2 = 0, fm_cap3 = 0, fm_cap4 = 0, fm_vcap = 0, fm_refcap = 0, fm_gcap = 0, fm_jcap = 0;
   static bool is_device(const void* p);
+
+  // caller's pair list for the current evaluation (nnp_eval_pairs; device
+  // pointers, null otherwise) and the per-row fill cursors it needs
+  bool ext_mode = false;
+  const int* ext_pairs = nullptr;
+  const double* ext_shifts = nullptr;
+  long long ext_n_pairs = 0;
+  int* b_pair_cur = nullptr;
+  int* b_pairs_stage = nullptr;
+  double* b_shifts_stage = nullptr;
+  size_t c_pair_cur = 0, c_pairs_stage = 0, c_shifts_stage = 0;
+  int g_key_ext = -1;
 
   // ML/MM embedding buffers (nnp_mlmm.cu; allocated on first use)
   struct MlmmBufs {

@@ -52,7 +52,8 @@ enum FlagWord {
   kFlagMaxNbrA = 5,
   kFlagBinOverflow = 6, // a bin held more than the per-bin sort capacity
   kFlagTimeout = 7,
-  kNumFlags = 8
+  kFlagBadPair = 8,     // a caller's pair: index out of range or shift not a whole image
+  kNumFlags = 9
 };
 
 // Descriptor and network constants, passed by value to kernels.
@@ -90,6 +91,9 @@ struct EvalIO {
   long long n_atoms;
   int n_sys;
   int total_cells;     // sum of cells over systems
+  const int* pairs;     // caller's pair list (n_pairs x 2), or null: the cell search
+  const double* shifts; // n_pairs x 3, or null
+  long long n_pairs;
 };
 
 // Device workspace (all capacity-sized).

@@ -164,7 +164,7 @@ extern "C" int nnp_eval_noalloc(nnp_ctx* ctx, int64_t n, const double* pos, cons
   if (bins > kNAMaxBins || rows > kNAMaxRows)
     return ctx->fail(NNP_ERR_CAPACITY, "nnp_eval_noalloc: cell grid exceeds its scratch");
 
-  EvalIO io;
+  EvalIO io{};
   io.pos = pos;
   io.Z = Z;
   io.forces = forces;
