@@ -14,11 +14,15 @@ of the ANI descriptor (radial: 16 shifts 0.9 + 0.26875 m, eta 16, cutoff
 Parity status per function
 --------------------------
 pairs_brute / pairs_cells : pinned (lattice shell counts, brute force = cells)
+pairs_brute_cell           : pinned (shell counts of a triclinic lattice, equal
+                             to pairs_brute for a rectangular cell)
 aev                        : pinned (closed forms of special geometries,
                              invariances, block placement)
 mlp                        : pinned (torch.nn.functional library routines)
 energy_forces              : pinned (finite differences, sum F = 0,
-                             translation / rotation / permutation invariance)
+                             translation / rotation / permutation invariance;
+                             general cells: the same lattice in a sheared cell
+                             gives the same result)
 aev_jvp, force_match       : pinned (finite differences in positions and in
                              weights)
 mlmm_energy_forces         : pinned (finite differences of the embedded energy
@@ -87,6 +91,9 @@ def lib():
         L.or_pairs_brute.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_long, ip, ip, dp]
         L.or_pairs_cells.restype = ctypes.c_long
         L.or_pairs_cells.argtypes = L.or_pairs_brute.argtypes
+        L.or_pairs_brute_cell.restype = ctypes.c_long
+        L.or_pairs_brute_cell.argtypes = L.or_pairs_brute.argtypes
+        L.or_energy_forces_cell.argtypes = [ctypes.POINTER(_Model), ctypes.c_int, dp, ip, dp, dp, dp, dp, dp]
         L.or_aev_length.restype = ctypes.c_int
         L.or_aev.argtypes = [ctypes.POINTER(_Model), ctypes.c_int, ip, ctypes.c_long, ip, ip, dp, dp]
         L.or_mlp.restype = ctypes.c_double
@@ -212,6 +219,12 @@ def pairs_brute(pos, box, rc):
     return _pairs(lib().or_pairs_brute, pos, box, rc)
 
 
+def pairs_brute_cell(pos, cell, rc):
+    """(i, j, d) of every pair/image within rc in a general periodic cell
+    (3 x 3, rows = cell vectors), brute force over images."""
+    return _pairs(lib().or_pairs_brute_cell, pos, np.asarray(cell, dtype=np.float64).reshape(9), rc)
+
+
 def pairs_cells(pos, box, rc):
     """Same set as pairs_brute, through a cell list."""
     return _pairs(lib().or_pairs_cells, pos, box, rc)
@@ -239,7 +252,9 @@ def mlp(model: Model, s: int, x) -> tuple[float, np.ndarray]:
 
 
 def energy_forces(model: Model, pos, species, box):
-    """E (float), Ei (n,), F (n,3), G (n,D)."""
+    """E (float), Ei (n,), F (n,3), G (n,D).  box: None (isolated), 3 edge
+    lengths (orthorhombic) or a 3 x 3 cell whose rows are the cell vectors
+    (general periodic cell, pairs by brute force over images)."""
     pos = np.ascontiguousarray(pos, dtype=np.float64)
     species = np.ascontiguousarray(species, dtype=np.int32)
     n = pos.shape[0]
@@ -248,8 +263,12 @@ def energy_forces(model: Model, pos, species, box):
     Ei = np.zeros(n)
     F = np.zeros((n, 3))
     G = np.zeros((n, model.p.aev_length))
-    lib().or_energy_forces(model.ref, n, _dp(pos), _ip(species),
-                           None if bx is None else _dp(bx), _dp(E), _dp(Ei), _dp(F), _dp(G))
+    if bx is not None and bx.size == 9:
+        lib().or_energy_forces_cell(model.ref, n, _dp(pos), _ip(species), _dp(bx.reshape(9)),
+                                    _dp(E), _dp(Ei), _dp(F), _dp(G))
+    else:
+        lib().or_energy_forces(model.ref, n, _dp(pos), _ip(species),
+                               None if bx is None else _dp(bx), _dp(E), _dp(Ei), _dp(F), _dp(G))
     return float(E[0]), Ei, F, G
 
 

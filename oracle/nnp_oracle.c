@@ -110,6 +110,75 @@ static long emit(long cnt, long cap, int *pi, int *pj, double *pd,
     return cnt + 1;
 }
 
+/* General periodic cell (triclinic): rows of cell are the cell vectors a, b,
+ * c (right-handed).  Positions are wrapped through fractional coordinates
+ * s = r B^-1 into [0, 1); then every image n = (n0, n1, n2) with |n_d| <=
+ * ceil(rc / h_d) + 1 is tried, h_d the cell's height across the other two
+ * vectors (d = r_j + n0 a + n1 b + n2 c - r_i), which covers every pair of
+ * wrapped atoms within rc.  Returns the number of pairs; writes the first
+ * `cap`. */
+static double det3(const double *B) {
+    return B[0] * (B[4] * B[8] - B[5] * B[7]) - B[1] * (B[3] * B[8] - B[5] * B[6]) +
+           B[2] * (B[3] * B[7] - B[4] * B[6]);
+}
+
+static void cross3(const double *u, const double *v, double *w) {
+    w[0] = u[1] * v[2] - u[2] * v[1];
+    w[1] = u[2] * v[0] - u[0] * v[2];
+    w[2] = u[0] * v[1] - u[1] * v[0];
+}
+
+long or_pairs_brute_cell(int n, const double *pos, const double *cell, double rc,
+                         long cap, int *pi, int *pj, double *pd) {
+    const double V = det3(cell);
+    /* inverse by cofactors: Binv[c][d] with s_d = sum_c r_c Binv[c][d] */
+    double Binv[9];
+    {
+        const double *a = cell, *b = cell + 3, *c = cell + 6;
+        double bc[3], ca[3], ab[3];
+        cross3(b, c, bc); cross3(c, a, ca); cross3(a, b, ab);
+        for (int k = 0; k < 3; ++k) {
+            Binv[3 * k + 0] = bc[k] / V;
+            Binv[3 * k + 1] = ca[k] / V;
+            Binv[3 * k + 2] = ab[k] / V;
+        }
+    }
+    int nmax[3];
+    for (int d = 0; d < 3; ++d) {
+        double w[3];
+        cross3(cell + 3 * ((d + 1) % 3), cell + 3 * ((d + 2) % 3), w);
+        const double h = V / sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+        nmax[d] = (int)ceil(rc / h) + 1;
+    }
+    double *x = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) {
+        double sf[3];
+        for (int d = 0; d < 3; ++d) {
+            double t = 0.0;
+            for (int c = 0; c < 3; ++c) t += pos[3 * i + c] * Binv[3 * c + d];
+            t -= floor(t);
+            if (t >= 1.0) t -= 1.0;
+            sf[d] = t;
+        }
+        for (int c = 0; c < 3; ++c) x[3 * i + c] = sf[0] * cell[c] + sf[1] * cell[3 + c] + sf[2] * cell[6 + c];
+    }
+    long cnt = 0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            for (int n0 = -nmax[0]; n0 <= nmax[0]; ++n0)
+                for (int n1 = -nmax[1]; n1 <= nmax[1]; ++n1)
+                    for (int n2 = -nmax[2]; n2 <= nmax[2]; ++n2) {
+                        if (i == j && n0 == 0 && n1 == 0 && n2 == 0) continue;
+                        double d[3];
+                        for (int c = 0; c < 3; ++c)
+                            d[c] = x[3 * j + c] - x[3 * i + c] + n0 * cell[c] + n1 * cell[3 + c] + n2 * cell[6 + c];
+                        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                        if (r2 < rc * rc) cnt = emit(cnt, cap, pi, pj, pd, i, j, d);
+                    }
+    free(x);
+    return cnt;
+}
+
 /* All (i, j, image) with |d| < rc, d = r_j + n.L - r_i, by brute force over
  * every image n with |n_a L_a| < rc + L_a.  box = NULL: isolated system.
  * Returns the number of pairs; writes the first `cap` of them. */
@@ -431,12 +500,42 @@ static long build_pairs(int n, const double *pos, const double *box, double rc,
 
 /* E (sum), Ei (n, may be NULL), F (n x 3), G (n x D, may be NULL).
  * species[i] in [0, S); box: 3 edge lengths (orthorhombic) or NULL. */
+static int energy_forces_from_pairs(const oracle_model *m, int n, const int *species, long np,
+                                    int *pi, int *pj, double *pd, double *E, double *Ei, double *F,
+                                    double *Gout);
+
 int or_energy_forces(const oracle_model *m, int n, const double *pos, const int *species,
                      const double *box, double *E, double *Ei, double *F, double *Gout) {
-    int D = or_aev_length(m);
     double rmax = m->rc_r > m->rc_a ? m->rc_r : m->rc_a;
     int *pi, *pj; double *pd;
     long np = build_pairs(n, pos, box, rmax, &pi, &pj, &pd);
+    return energy_forces_from_pairs(m, n, species, np, pi, pj, pd, E, Ei, F, Gout);
+}
+
+/* As or_energy_forces for a general periodic cell (rows a, b, c; pairs by
+ * or_pairs_brute_cell). */
+int or_energy_forces_cell(const oracle_model *m, int n, const double *pos, const int *species,
+                          const double *cell, double *E, double *Ei, double *F, double *Gout) {
+    double rmax = m->rc_r > m->rc_a ? m->rc_r : m->rc_a;
+    long cap = 64;
+    int *pi, *pj; double *pd;
+    for (;;) {
+        pi = (int *)malloc(sizeof(int) * (size_t)cap);
+        pj = (int *)malloc(sizeof(int) * (size_t)cap);
+        pd = (double *)malloc(sizeof(double) * 3 * (size_t)cap);
+        long np = or_pairs_brute_cell(n, pos, cell, rmax, cap, pi, pj, pd);
+        if (np <= cap) return energy_forces_from_pairs(m, n, species, np, pi, pj, pd, E, Ei, F, Gout);
+        free(pi); free(pj); free(pd);
+        cap = np;
+    }
+}
+
+/* E, Ei, F and G from a pair list (every ordered pair/image within the
+ * largest cutoff); frees the pair arrays. */
+static int energy_forces_from_pairs(const oracle_model *m, int n, const int *species, long np,
+                                    int *pi, int *pj, double *pd, double *E, double *Ei, double *F,
+                                    double *Gout) {
+    int D = or_aev_length(m);
     nbr_csr rad, ang;
     csr_build(&rad, n, np, pi, pj, pd, m->rc_r);
     csr_build(&ang, n, np, pi, pj, pd, m->rc_a);
