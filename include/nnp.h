@@ -148,9 +148,10 @@ int nnp_set_weights(nnp_ctx *ctx, int32_t species, const float *const W[4],
 /* Energy and forces of one system of n atoms.
  *   pos    n x 3 positions (Angstrom), any values (wrapped into the box);
  *   Z      n atomic numbers;
- *   box    9 doubles (3 x 3 row-major cell vectors, host pointer); only
- *          orthorhombic cells (off-diagonals zero) with every edge >= rc_r
- *          are supported; NULL = isolated system (no periodic images);
+ *   box    9 doubles (3 x 3 row-major, rows = cell vectors a, b, c; host
+ *          pointer); orthorhombic or triclinic (right-handed), every height
+ *          of the cell across two of its vectors >= rc_r; NULL = isolated
+ *          system (no periodic images);
  *   energy 1 double (eV), forces n x 3 doubles (eV/Angstrom); either may be
  *          NULL to skip it.
  * Synchronous: returns after the results are written. */

@@ -176,9 +176,10 @@ __device__ __forceinline__ f2 f2_ex2(f2 x) {
   return f2_make(ex2(h.x), ex2(h.y));
 }
 
-__device__ __forceinline__ float4 shift_vec(int code, const float* ell) {
-  const int mx = code / 9 - 1, my = (code / 3) % 3 - 1, mz = code % 3 - 1;
-  return make_float4(mx * ell[0], my * ell[1], mz * ell[2], 0.f);
+// image shift of a list entry's virtual-cell code
+__device__ __forceinline__ float4 shift_vec(int code, const SysDesc& sd) {
+  const float3 v = cell_shift(code / 9 - 1, (code / 3) % 3 - 1, code % 3 - 1, sd);
+  return make_float4(v.x, v.y, v.z, 0.f);
 }
 
 // Per half-warp row bookkeeping in shared memory: counts and offsets per species.
@@ -269,8 +270,7 @@ __global__ void __launch_bounds__(256, 3) k_aev_fwd(const SysDesc* __restrict__ 
       const int sid = ws.row_info[row];
       if (sid != cached_sys) {
         const SysDesc& sd = sys[sid];
-        const float ell[3] = {sd.ellf[0], sd.ellf[1], sd.ellf[2]};
-        for (int c = hl; c < 27; c += 16) sh[c] = shift_vec(c, ell);
+        for (int c = hl; c < 27; c += 16) sh[c] = shift_vec(c, sd);
         cached_sys = sid;
       }
     }
@@ -533,8 +533,7 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
     __syncwarp();  // the previous row's shared data has been read
     if (sid != cached_sys) {
       const SysDesc& sd = sys[sid];
-      const float ell[3] = {sd.ellf[0], sd.ellf[1], sd.ellf[2]};
-      if (lane < 27) sh[lane] = shift_vec(lane, ell);
+      if (lane < 27) sh[lane] = shift_vec(lane, sd);
       cached_sys = sid;
     }
     {
@@ -852,8 +851,7 @@ __global__ void __launch_bounds__(256) k_aev_jvp(const SysDesc* __restrict__ sys
       const int sid = ws.row_info[row];
       if (sid != cached_sys) {
         const SysDesc& sd = sys[sid];
-        const float ell[3] = {sd.ellf[0], sd.ellf[1], sd.ellf[2]};
-        for (int c = hl; c < 27; c += 16) sh[c] = shift_vec(c, ell);
+        for (int c = hl; c < 27; c += 16) sh[c] = shift_vec(c, sd);
         cached_sys = sid;
       }
     }

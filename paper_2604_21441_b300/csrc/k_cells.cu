@@ -43,18 +43,38 @@ __global__ void k_bin(const EvalIO* __restrict__ io, const SysDesc* __restrict__
     }
     int k[3];
     float off[3];
+    if (sd.tric) {
+      // fractional coordinates, wrapped into [0, 1); the offset from the
+      // cell's corner is the fractional remainder times the cell steps
+      double f[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      double x = p[c] - sd.origin[c];
-      if (sd.periodic) {
-        x -= sd.L[c] * floor(x * sd.inv_L[c]);
-        if (x >= sd.L[c]) x -= sd.L[c];
-        if (x < 0.0) x = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        double t = p[0] * sd.Binv[d] + p[1] * sd.Binv[3 + d] + p[2] * sd.Binv[6 + d];
+        t -= floor(t);
+        if (t >= 1.0) t -= 1.0;
+        if (t < 0.0) t = 0.0;
+        const double u = t * sd.nc[d];
+        int kk = (int)floor(u);
+        kk = kk < 0 ? 0 : (kk >= sd.nc[d] ? sd.nc[d] - 1 : kk);
+        k[d] = kk;
+        f[d] = (u - kk) / sd.nc[d];
       }
-      int kk = (int)floor(x * sd.inv_ell[c]);
-      kk = kk < 0 ? 0 : (kk >= sd.nc[c] ? sd.nc[c] - 1 : kk);
-      k[c] = kk;
-      off[c] = (float)(x - kk * sd.ell[c]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) off[c] = (float)(f[0] * sd.B[c] + f[1] * sd.B[3 + c] + f[2] * sd.B[6 + c]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        double x = p[c] - sd.origin[c];
+        if (sd.periodic) {
+          x -= sd.L[c] * floor(x * sd.inv_L[c]);
+          if (x >= sd.L[c]) x -= sd.L[c];
+          if (x < 0.0) x = 0.0;
+        }
+        int kk = (int)floor(x * sd.inv_ell[c]);
+        kk = kk < 0 ? 0 : (kk >= sd.nc[c] ? sd.nc[c] - 1 : kk);
+        k[c] = kk;
+        off[c] = (float)(x - kk * sd.ell[c]);
+      }
     }
     const int cell = (k[0] * sd.nc[1] + k[1]) * sd.nc[2] + k[2];
     const int bin = s * TC + sd.cell_base + cell;
@@ -333,7 +353,6 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
       }
       if (ok) vcell = (v[0] * nc1 + v[1]) * nc2 + v[2];
     }
-    const float ell0 = sd.ellf[0], ell1 = sd.ellf[1], ell2 = sd.ellf[2];
     // bins of the 27 virtual cells for every species (lane v), their exclusive
     // offsets within the species' flattened neighbourhood, and its size
     int bst[kMaxS], bln[kMaxS], bex[kMaxS], tot[kMaxS];
@@ -369,8 +388,8 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
     // stage the window [w0, w0 + wn) of species sp's neighbourhood: lane v <
     // 27 copies the atoms of virtual cell v (shifted by its image offset) to
     // their places bex[v] + k; the loads of the 27 cells are independent
-    const float vsx = (float)(lane / 9 - 1) * ell0, vsy = (float)((lane / 3) % 3 - 1) * ell1,
-                vsz = (float)(lane % 3 - 1) * ell2;
+    const float3 vs = cell_shift(lane / 9 - 1, (lane / 3) % 3 - 1, lane % 3 - 1, sd);
+    const float vsx = vs.x, vsy = vs.y, vsz = vs.z;
     auto stage = [&](int sp, int w0, int wn, int db) {
       const int bex_s = pick(bex, sp), bst_s = pick(bst, sp), bln_s = pick(bln, sp);
       const int k0 = max(0, w0 - bex_s), k1 = min(bln_s, w0 + wn - bex_s);

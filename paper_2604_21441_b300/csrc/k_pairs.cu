@@ -73,11 +73,12 @@ __device__ __forceinline__ PairGeo pair_geo(const EvalIO* __restrict__ io, const
   g.si = pos4_species(pi);
   g.sj = pos4_species(pj);
   const SysDesc& sd = sys[ws.row_info[g.ri]];
-  const float off[3] = {pj.x - pi.x, pj.y - pi.y, pj.z - pi.z};
+  // the image in cell steps: m = (d - (off_j - off_i)) cv^-1
+  const float x[3] = {d[0] - (pj.x - pi.x), d[1] - (pj.y - pi.y), d[2] - (pj.z - pi.z)};
   int m[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const float q = (d[c] - off[c]) / sd.ellf[c];
+    const float q = x[0] * sd.cvinv[c] + x[1] * sd.cvinv[3 + c] + x[2] * sd.cvinv[6 + c];
     m[c] = __float2int_rn(q);
     if (m[c] < -1 || m[c] > 1 || fabsf(q - (float)m[c]) > 1e-3f) return g;
   }
@@ -89,9 +90,9 @@ __device__ __forceinline__ PairGeo pair_geo(const EvalIO* __restrict__ io, const
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
     const float4 a = side ? pj : pi, b = side ? pi : pj;
-    const float sg = side ? -1.f : 1.f;
-    const float cx = b.x + sg * (float)m[0] * sd.ellf[0], cy = b.y + sg * (float)m[1] * sd.ellf[1],
-                cz = b.z + sg * (float)m[2] * sd.ellf[2];
+    const int sg = side ? -1 : 1;
+    const float3 v = cell_shift(sg * m[0], sg * m[1], sg * m[2], sd);
+    const float cx = b.x + v.x, cy = b.y + v.y, cz = b.z + v.z;
     const float dx = cx - a.x, dy = cy - a.y, dz = cz - a.z;
     const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));  // the search's rounding order
     g.radial[side] = r2 < rcr2 && !self;

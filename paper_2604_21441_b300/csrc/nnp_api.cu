@@ -249,6 +249,31 @@ int nnp_ctx::calibrate_fp8(long long n, int B, long long bins, long long rows) {
   return NNP_OK;
 }
 
+static void cross3(const double* u, const double* v, double* w) {
+  w[0] = u[1] * v[2] - u[2] * v[1];
+  w[1] = u[2] * v[0] - u[0] * v[2];
+  w[2] = u[0] * v[1] - u[1] * v[0];
+}
+
+// Cell steps cv_d (rows: B_d / nc_d, or ell_d along axis d) and their inverse.
+void nnp::set_cell_steps(SysDesc& sd) {
+  double M[9];
+  for (int d = 0; d < 3; ++d)
+    for (int c = 0; c < 3; ++c)
+      M[3 * d + c] = sd.tric ? sd.B[3 * d + c] / sd.nc[d] : (c == d ? sd.ell[d] : 0.0);
+  double r1r2[3], r2r0[3], r0r1[3];
+  cross3(M + 3, M + 6, r1r2);
+  cross3(M + 6, M, r2r0);
+  cross3(M, M + 3, r0r1);
+  const double det = M[0] * r1r2[0] + M[1] * r1r2[1] + M[2] * r1r2[2];
+  const double* crs[3] = {r1r2, r2r0, r0r1};
+  for (int d = 0; d < 3; ++d)
+    for (int c = 0; c < 3; ++c) {
+      sd.cv[3 * d + c] = sd.tric ? (float)M[3 * d + c] : (c == d ? sd.ellf[d] : 0.f);
+      sd.cvinv[3 * c + d] = (float)(crs[d][c] / det);  // m_d = sum_c x_c cvinv[c][d]
+    }
+}
+
 // Host-side set-up of the systems: cell grids, capacity, IO descriptor.
 int nnp_ctx::prepare(int B, const int64_t* offsets, const double* pos_host_or_null,
                      const double* boxes, long long& bins, long long& rows) {
@@ -265,21 +290,46 @@ int nnp_ctx::prepare(int B, const int64_t* offsets, const double* pos_host_or_nu
     double L[3];
     if (boxes) {
       const double* bx = boxes + 9 * (size_t)b;
+      bool tric = false;
       for (int r = 0; r < 3; ++r)
         for (int c = 0; c < 3; ++c) {
           if (!std::isfinite(bx[3 * r + c]))
             return fail(NNP_ERR_INVALID_ARG, "system %d: non-finite box entry", b);
-          if (r != c && bx[3 * r + c] != 0.0)
-            return fail(NNP_ERR_UNSUPPORTED, "system %d: triclinic boxes are not supported", b);
+          if (r != c && bx[3 * r + c] != 0.0) tric = true;
         }
-      for (int c = 0; c < 3; ++c) {
-        L[c] = bx[4 * c];
-        if (!(L[c] > 0.0)) return fail(NNP_ERR_INVALID_ARG, "system %d: box edge %d is %g", b, c, L[c]);
-        if (L[c] < rc)
-          return fail(NNP_ERR_UNSUPPORTED, "system %d: box edge %g is shorter than the radial cutoff %g",
-                      b, L[c], rc);
-        sd.origin[c] = 0.0;
+      if (!tric) {
+        for (int c = 0; c < 3; ++c) {
+          L[c] = bx[4 * c];
+          if (!(L[c] > 0.0)) return fail(NNP_ERR_INVALID_ARG, "system %d: box edge %d is %g", b, c, L[c]);
+          if (L[c] < rc)
+            return fail(NNP_ERR_UNSUPPORTED, "system %d: box edge %g is shorter than the radial cutoff %g",
+                        b, L[c], rc);
+        }
+      } else {
+        // rows are the cell vectors; cells are sized by the heights across them
+        const double* u = bx;
+        const double* v = bx + 3;
+        const double* w = bx + 6;
+        double vw[3], wu[3], uv[3];
+        cross3(v, w, vw);
+        cross3(w, u, wu);
+        cross3(u, v, uv);
+        const double V = u[0] * vw[0] + u[1] * vw[1] + u[2] * vw[2];
+        if (!(V > 0.0)) return fail(NNP_ERR_INVALID_ARG, "system %d: the cell is not right-handed", b);
+        const double* crs[3] = {vw, wu, uv};
+        for (int d = 0; d < 3; ++d) {
+          L[d] = V / std::sqrt(crs[d][0] * crs[d][0] + crs[d][1] * crs[d][1] + crs[d][2] * crs[d][2]);
+          if (L[d] < rc)
+            return fail(NNP_ERR_UNSUPPORTED, "system %d: cell height %g is shorter than the radial cutoff %g",
+                        b, L[d], rc);
+          for (int c = 0; c < 3; ++c) {
+            sd.B[3 * d + c] = bx[3 * d + c];
+            sd.Binv[3 * c + d] = crs[d][c] / V;  // s_d = sum_c r_c Binv[c][d]
+          }
+        }
+        sd.tric = 1;
       }
+      for (int c = 0; c < 3; ++c) sd.origin[c] = 0.0;
       sd.periodic = 1;
     } else {
       if (!pos_host_or_null) return fail(NNP_ERR_INVALID_ARG, "isolated system needs positions on the host");
@@ -314,6 +364,7 @@ int nnp_ctx::prepare(int B, const int64_t* offsets, const double* pos_host_or_nu
       sd.inv_ell[c] = 1.0 / sd.ell[c];
       sd.ellf[c] = (float)sd.ell[c];
     }
+    set_cell_steps(sd);
     sd.cell_base = (int)cell_base;
     cell_base += (long long)nc[0] * nc[1] * nc[2];
   }

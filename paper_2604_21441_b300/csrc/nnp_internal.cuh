@@ -69,17 +69,36 @@ struct DescParams {
 };
 
 // One periodic system.  Filled on the host, copied to the device per eval.
+// Orthorhombic boxes and isolated systems use the edge form (L, ell); a
+// triclinic box (tric = 1) wraps through fractional coordinates s = r Binv
+// with B's rows the cell vectors a, b, c.  In both forms cell (k0, k1, k2)
+// has its corner at sum_d k_d cv_d and the image shift of virtual-cell offset
+// m is sum_d m_d cv_d (cv = B / nc row-wise; diagonal for the edge form).
 struct SysDesc {
   double L[3];      // edges (isolated systems: padded bounding box)
   double ell[3];    // cell edges L / nc
   double inv_L[3], inv_ell[3];  // reciprocals (the wrap multiplies: FP64 division is slow)
   double origin[3]; // subtracted before wrapping (isolated systems)
+  double B[9], Binv[9];  // triclinic: cell vectors (rows) and the inverse, s_d = sum_c r_c Binv[c][d]
   float ellf[3];
+  float cv[9];      // cell steps: rows cv_d = B_d / nc_d
+  float cvinv[9];   // inverse of cv (rows), for image codes of given displacements
   int nc[3];
   int cell_base;    // first global cell of this system
   int periodic;
+  int tric;
   long long atom_begin, atom_end;
 };
+
+// Image shift of virtual-cell offset (m0, m1, m2): sum_d m_d cv_d, in one
+// fixed FP32 order shared by every kernel (exactly m_d ell_d for the edge form).
+__device__ __forceinline__ float3 cell_shift(int m0, int m1, int m2, const SysDesc& sd) {
+  float3 v;
+  v.x = fmaf((float)m2, sd.cv[6], fmaf((float)m1, sd.cv[3], (float)m0 * sd.cv[0]));
+  v.y = fmaf((float)m2, sd.cv[7], fmaf((float)m1, sd.cv[4], (float)m0 * sd.cv[1]));
+  v.z = fmaf((float)m2, sd.cv[8], fmaf((float)m1, sd.cv[5], (float)m0 * sd.cv[2]));
+  return v;
+}
 
 // Per-evaluation IO descriptor (device memory, refreshed before each launch
 // so that captured graphs do not depend on caller pointers).

@@ -124,7 +124,7 @@ extern "C" int nnp_eval_noalloc(nnp_ctx* ctx, int64_t n, const double* pos, cons
   }
 
   // one periodic orthorhombic system (same cell rule as nnp_eval)
-  SysDesc sd;
+  SysDesc sd{};
   memset(&sd, 0, sizeof sd);
   const double rc = ctx->cfg.rc_r;
   for (int r = 0; r < 3; ++r)
@@ -154,6 +154,8 @@ extern "C" int nnp_eval_noalloc(nnp_ctx* ctx, int64_t n, const double* pos, cons
     sd.inv_ell[c] = 1.0 / sd.ell[c];
     sd.ellf[c] = (float)sd.ell[c];
   }
+  sd.tric = 0;
+  set_cell_steps(sd);
   sd.periodic = 1;
   sd.atom_begin = 0;
   sd.atom_end = n;

@@ -160,11 +160,15 @@ def test_error_codes(P):
     with pytest.raises(P.NNPError) as e:
         pot.eval(nanpos, s.Z, s.box)
     assert e.value.code == 1
-    tri = np.diag(s.box)
-    tri[1, 0] = 0.5
+    L = s.box[0]
+    thin = np.array([[L, 0.0, 0.0], [0.95 * L, 0.3 * L, 0.0], [0.0, 0.0, L]])  # a height of 0.3 L < rc
     with pytest.raises(P.NNPError) as e:
-        pot.eval(s.pos, s.Z, tri)
+        pot.eval(s.pos, s.Z, thin)
     assert e.value.code == 3
+    left = np.diag(s.box)[[1, 0, 2]]  # left-handed cell
+    with pytest.raises(P.NNPError) as e:
+        pot.eval(s.pos, s.Z, left)
+    assert e.value.code == 1
     with pytest.raises(P.NNPError) as e:
         pot.eval(s.pos, s.Z, [5.0, 9.3, 9.3])
     assert e.value.code == 3
