@@ -45,7 +45,8 @@ typedef enum {
     NNP_OK = 0,
     NNP_ERR_INVALID_ARG = 1,     /* null pointer, n <= 0, non-finite position, bad box */
     NNP_ERR_UNKNOWN_SPECIES = 2, /* an atomic number outside the configured species */
-    NNP_ERR_UNSUPPORTED = 3,     /* triclinic box, box edge < radial cutoff, layer sizes */
+    NNP_ERR_UNSUPPORTED = 3,     /* cell height < radial cutoff, layer sizes, a triclinic
+                                    box where only orthorhombic ones are taken */
     NNP_ERR_CAPACITY = 4,        /* neighbour lists overflowed (async path) or > max */
     NNP_ERR_CUDA = 5,            /* a CUDA runtime call failed */
     NNP_ERR_TIMEOUT = 6,         /* a bounded device wait expired */
