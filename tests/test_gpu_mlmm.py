@@ -140,3 +140,15 @@ def test_mlmm_open_cluster(P, oracle_mod):
     Er, Fr, Eir = oracle_mod.mlmm_energy_forces(m, pos, p.species_of(Z), None, ml, lml, lmm, None, 0)
     assert abs(E - Er) / max(abs(Er), float(np.abs(Eir).sum())) <= E_REL_TOL
     assert np.abs(F - Fr).max() <= F_ABS_TOL
+
+
+def test_mlmm_without_links_is_the_group(P):
+    """No cut bonds: the embedding is the plain evaluation of the group."""
+    w = weights32(2, 128, 55, 56)
+    s = synth.water_box(64, 57)
+    ml = np.arange(3 * 20, dtype=np.int64)  # 20 whole waters
+    pot = _pot(P, w)
+    E, F = pot.eval_mlmm(s.pos, s.Z, ml, (), (), None, 1, box=box9(s.box))
+    Eg, Fg = pot.eval(s.pos[ml], s.Z[ml], box9(s.box))
+    assert abs(E - Eg) <= 1e-9 * max(1.0, abs(Eg))
+    assert np.abs(F[ml] - Fg).max() <= 1e-5 and np.all(F[3 * 20:] == 0.0)

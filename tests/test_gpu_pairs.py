@@ -146,3 +146,32 @@ def test_pairs_rejects_bad_lists(P, oracle_mod):
     E, F = pot.eval_pairs(s.pos, s.Z, pairs, shifts, box9(s.box))
     Es, _ = pot.eval(s.pos, s.Z, box9(s.box))
     assert np.isfinite(E) and abs(E - Es) <= 1e-5 * max(1.0, abs(Es))
+
+
+def test_pairs_empty_list_is_isolated_atoms(P, oracle_mod):
+    """No pairs: every atom alone, G = 0, so E = sum over atoms of its
+    species' network at zero input, and all forces vanish."""
+    s = synth.water_box(27, 69)
+    w = weights32(2, 128, 70, 71)
+    pot = _pot(P, w)
+    E, F = pot.eval_pairs(s.pos, s.Z, np.zeros((0, 2), dtype=np.int32), None, box9(s.box))
+    p = oracle_mod.Params()
+    m = oracle_mod.Model(p, w)
+    e0 = [oracle_mod.mlp(m, sp, np.zeros(p.aev_length))[0] for sp in range(2)]
+    ref = sum(e0[sp] for sp in p.species_of(s.Z))
+    assert abs(E - ref) <= 1e-6 * max(1.0, abs(ref))
+    assert np.all(F == 0.0)
+
+
+def test_pairs_fp8_form(P, oracle_mod):
+    """The FP8 form calibrates through the same path (the caller's list)."""
+    s = synth.water_box(64, 72)
+    w = weights32(2, 128, 73, 74)
+    pairs, shifts = _half_list(oracle_mod, s.pos, s.box)
+    a = _pot(P, w, "fp8")
+    E, F = a.eval_pairs(s.pos, s.Z, pairs, shifts, box9(s.box))
+    b = _pot(P, w, "fp8")
+    Es, Fs = b.eval(s.pos, s.Z, box9(s.box))
+    Ei = b.atom_energies(s.n)
+    # same neighbour sets, so the same calibration and (up to sum order) the same result
+    assert abs(E - Es) <= 1e-3 * np.abs(Ei).sum() and np.abs(F - Fs).max() <= 0.05

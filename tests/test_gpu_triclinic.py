@@ -95,3 +95,20 @@ def test_skewed_box_pair_list(P, oracle_mod):
     Es, Fs = pot.eval(s.pos, s.Z, cell)
     Ei = pot.atom_energies(s.n)
     assert abs(E - Es) <= 1e-6 * np.abs(Ei).sum() and np.abs(F - Fs).max() <= 1e-5
+
+
+def test_triclinic_batch(P):
+    """Two skewed systems and one orthorhombic one in one batched launch equal
+    their separate evaluations."""
+    w = weights32(2, 128, 89, 90)
+    systems = [synth.water_box(64, 91), synth.water_box(27, 92), synth.water_box(125, 93)]
+    cells = [_skewed(systems[0].box), np.diag(systems[1].box), _sheared(systems[2].box)]
+    pot = _pot(P, w)
+    off = np.concatenate([[0], np.cumsum([s.n for s in systems])])
+    pos = np.concatenate([s.pos for s in systems])
+    Z = np.concatenate([s.Z for s in systems])
+    Eb, Fb = pot.eval_batch(off, pos, Z, np.stack(cells))
+    for k, (s, c) in enumerate(zip(systems, cells)):
+        E, F = pot.eval(s.pos, s.Z, c)
+        assert abs(Eb[k] - E) <= 1e-6 * max(1.0, abs(E))
+        assert np.abs(Fb[off[k]:off[k + 1]] - F).max() <= 1e-5
