@@ -460,10 +460,15 @@ struct PairBlock {
 }  // namespace
 
 // float4 units of one warp's shared memory; the pair matrix has rows of
-// cap_a + 1 float2 entries (the odd stride spreads a column over the banks)
-__host__ __device__ inline size_t bwd_mat_f4(int cap_a) { return ((size_t)cap_a * (cap_a + 1) * 2 + 3) / 4; }
+// mc + 1 float2 entries (the odd stride spreads a column over the banks).
+// Its capacity mc is at most kBwdMatCap angular neighbours, whatever the
+// staging capacity: a row with more adds its pair forces with shared-memory
+// atomics instead, so one crowded row does not cost every warp its occupancy.
+constexpr int kBwdMatCap = 32;
+__host__ __device__ inline int bwd_mat_cap(int cap_a) { return cap_a < kBwdMatCap ? cap_a : kBwdMatCap; }
+__host__ __device__ inline size_t bwd_mat_f4(int mc) { return ((size_t)mc * (mc + 1) * 2 + 3) / 4; }
 __host__ __device__ inline size_t bwd_warp_f4(int cap_a, int cap_r, int D) {
-  return 27 + 2 * (size_t)cap_a + bwd_mat_f4(cap_a) + (size_t)D / 4 + ((size_t)3 * cap_r + 3) / 4 +
+  return 27 + 2 * (size_t)cap_a + bwd_mat_f4(bwd_mat_cap(cap_a)) + (size_t)D / 4 + ((size_t)3 * cap_r + 3) / 4 +
          ((size_t)cap_r + 3) / 4 + (sizeof(PairBlock) * (kMaxS * (kMaxS + 1) / 2) + 15) / 16;
 }
 
@@ -481,8 +486,8 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
   float4* geo = sh + 27;
   float4* aux = geo + ca;
   float2* mat = reinterpret_cast<float2*>(aux + ca);  // [ca][ca + 1]
-  const int ms = ca + 1;
-  float* wsm = reinterpret_cast<float*>(aux + ca + bwd_mat_f4(ca));
+  const int mc = bwd_mat_cap(ca), ms = mc + 1;
+  float* wsm = reinterpret_cast<float*>(aux + ca + bwd_mat_f4(mc));
   float* fsl = wsm + D;
   int* origs = reinterpret_cast<int*>(reinterpret_cast<float4*>(fsl) + (3 * cr + 3) / 4);
   PairBlock* blk = reinterpret_cast<PairBlock*>(reinterpret_cast<float4*>(origs) + (cr + 3) / 4);
@@ -552,6 +557,7 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
       oa[q] = nang;
       nang += na[q];
     }
+    const bool use_mat = nang <= mc;  // warp-uniform
     // pair blocks (every lane computes the same table; lanes < NB store it)
     int Ttot = 0;
     {
@@ -737,8 +743,18 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
         // d cos/d d_u = (e_v - c e_u)/r_u ; d cos/d d_v = (e_u - c e_v)/r_v
         const float Au = fmaf(-dEdc * c, au.z, dEdru), Bu = dEdc * au.z;
         const float Av = fmaf(-dEdc * c, av.z, dEdrv), Bv = dEdc * av.z;
-        mat[u * ms + v] = make_float2(Au, Bu);
-        mat[v * ms + u] = make_float2(Av, Bv);
+        if (use_mat) {
+          mat[u * ms + v] = make_float2(Au, Bu);
+          mat[v * ms + u] = make_float2(Av, Bv);
+        } else {  // a row beyond the matrix capacity: its neighbours' shares directly
+          const int su = 3 * __float_as_int(au.w), sv = 3 * __float_as_int(av.w);
+          atomicAdd(&fsl[su], -fmaf(Au, gu.x, Bu * gv.x));
+          atomicAdd(&fsl[su + 1], -fmaf(Au, gu.y, Bu * gv.y));
+          atomicAdd(&fsl[su + 2], -fmaf(Au, gu.z, Bu * gv.z));
+          atomicAdd(&fsl[sv], -fmaf(Av, gv.x, Bv * gu.x));
+          atomicAdd(&fsl[sv + 1], -fmaf(Av, gv.y, Bv * gu.y));
+          atomicAdd(&fsl[sv + 2], -fmaf(Av, gv.z, Bv * gu.z));
+        }
         const float ca_ = Au + Bv, cb_ = Bu + Av;  // centre: g_u + g_v = (Au + Bv) e_u + (Bu + Av) e_v
         fix += ca_ * gu.x + cb_ * gv.x;
         fiy += ca_ * gu.y + cb_ * gv.y;
@@ -748,7 +764,7 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
     __syncwarp();
 
     // ---------------- (3) each angular neighbour sums its row of the pair matrix
-    for (int m = lane; m < nang; m += 32) {
+    for (int m = lane; m < (use_mat ? nang : 0); m += 32) {
       const float4 gm = geo[m];
       float sa = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
       const float2* row_m = mat + m * ms;

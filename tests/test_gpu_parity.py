@@ -206,3 +206,24 @@ def test_full_size_sampled(P, oracle_mod, k):
     assert np.abs(F[sel_f] - Fr).max() <= F_ABS_TOL
     assert abs(E - Ei.sum()) <= 1e-6 * np.abs(Ei).sum()
     assert np.abs(F.sum(0)).max() <= 1e-6 * np.abs(F).sum()
+
+
+def test_dense_water_rows_beyond_the_pair_matrix(P, oracle_mod):
+    """Water compressed to about twice its density: rows have more angular
+    neighbours than the backward's shared-memory pair matrix holds (32), so
+    those rows take the path that adds pair forces with shared-memory
+    atomics.  Checked atom by atom against the oracle, FP32 bounds."""
+    s = synth.water_box(64, 95)
+    scale = 0.8
+    pos, box = s.pos * scale, s.box * scale
+    w = weights32(2, 128, 96, 97)
+    pot = _pot(P, w)
+    E, F = pot.eval(pos, s.Z, box9(box))
+    assert pot.query("max_ang") > 32  # the path under test is taken
+    p = oracle_mod.Params()
+    m = oracle_mod.Model(p, w)
+    Er, Eir, Fr, _ = oracle_mod.energy_forces(m, pos, p.species_of(s.Z), box)
+    print(f"dense water: max angular {pot.query('max_ang')}, rel E err {energy_error(E, Er, Eir):.2e}, "
+          f"max|dF| {np.abs(F - Fr).max():.2e}")
+    assert energy_error(E, Er, Eir) <= E_REL_TOL
+    assert np.abs(F - Fr).max() <= F_ABS_TOL
