@@ -569,34 +569,67 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
       continue;
     }
 
-    // ---- lane per row, windows of kNbrWin candidates
+    // ---- lane per row (cells of many rows, or windows beyond kNbrWin): the
+    // species' neighbourhood in windows of kNbrWin candidates, each tested in
+    // halves of 8 chunks whose hit masks go to the mask slots, then written
+    // by one flat loop with a warp-uniform step count.  Angular entries go to
+    // the front of the row's segment, radial-only ones are parked at the end
+    // of the list and moved behind them once the species is done.
     for (int r0 = 0; r0 < nrows; r0 += 32) {
       const int q = r0 + lane;
       const bool has = q < nrows;
       const int row = row_of(q);
       const float4 pi = has ? ws.pos4[row] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const int row_sp = pos4_species(pi);
       const f2 nx = f2_make(-pi.x, -pi.x), ny = f2_make(-pi.y, -pi.y), nz = f2_make(-pi.z, -pi.z);
-      const int self = pack_nbr(row, 13);
       int* lr = ws.nbr_r + (size_t)row * cap;
       int nr = 0, tot_r = 0, tot_a = 0;  // written entries; all entries found
       for (int sp = 0; sp < S; ++sp) {
         const int total = pick(tot, sp);
+        const int ex13 = __shfl_sync(F, pick(bex, sp), 13), st13 = __shfl_sync(F, pick(bst, sp), 13);
+        const int self_k = (has && row_sp == sp) ? ex13 + (row - st13) : -1;
         int wa = 0, wro = 0, ka = 0, kro = 0;  // written / found: angular, radial-only
         for (int w0 = 0; w0 < total; w0 += kNbrWin) {
           const int wn = min(kNbrWin, total - w0);
           stage(sp, w0, wn, 0);
-          if (has) {
-            // 32 candidates at a time: hit masks first (no branches), then the hits
-            for (int k0 = 0; k0 < wn; k0 += 32) {
+          for (int h0 = 0; h0 < wn; h0 += 256) {
+            const int nch = (min(256, wn - h0) + 31) >> 5;
+            int n_me = 0;
+            unsigned nzs = 0u;
+#pragma unroll 1
+            for (int i = 0; i < (has ? nch : 0); ++i) {
+              const int k0 = h0 + 32 * i;
               unsigned hr, ha;
               masks(nx, ny, nz, k0, wn, hr, ha);
-              while (hr) {
-                const int k = __ffs(hr) - 1;
-                hr &= hr - 1u;
-                const int e = we[k0 + k];
-                if (e == self) continue;
+              const int sk = self_k - w0 - k0;  // the row itself, image 0
+              if (self_k >= 0 && sk >= 0 && sk < 32) {
+                hr &= ~(1u << sk);
+                ha &= hr;
+              }
+              hmask[(2 * i) * 32 + lane] = ha;
+              hmask[(2 * i + 1) * 32 + lane] = hr & ~ha;
+              nzs |= (ha ? 1u : 0u) << (2 * i);
+              nzs |= ((hr & ~ha) ? 1u : 0u) << (2 * i + 1);
+              n_me += __popc(hr);
+            }
+            const int steps = __reduce_max_sync(F, (unsigned)n_me);
+            unsigned nzl = has ? nzs : 0u, cur = 0u;
+            int base = 0;
+            bool ang = true;
+            for (int it = 0; it < steps; ++it) {
+              if (cur == 0u && nzl != 0u) {
+                const int m = __ffs(nzl) - 1;
+                nzl &= nzl - 1u;
+                cur = hmask[m * 32 + lane];
+                base = h0 + (m >> 1) * 32;
+                ang = (m & 1) == 0;
+              }
+              if (cur != 0u) {
+                const int k = __ffs(cur) - 1;
+                cur &= cur - 1u;
+                const int e = we[base + k];
                 const bool room = nr + wa + wro < cap;
-                if ((ha >> k) & 1u) {
+                if (ang) {
                   if (room) lr[nr + wa++] = e;
                   ++ka;
                 } else {
@@ -605,6 +638,7 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
                 }
               }
             }
+            __syncwarp();  // the mask slots are rewritten by the next half
           }
         }
         if (has) {
