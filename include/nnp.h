@@ -284,6 +284,15 @@ int nnp_eval_mlmm(nnp_ctx *ctx, int64_t n_total, const double *pos, const int32_
  * Synchronises the context's stream. */
 int nnp_atom_energies(nnp_ctx *ctx, double *out);
 
+/* Self-tests of the library's failure handling (no GPU fault is involved).
+ *   NNP_SELFTEST_WAIT_TIMEOUT: one kernel waits, with the same bounded wait as
+ *   the tensor-core network's, on a barrier that nothing completes; the wait
+ *   gives up after 2 ms, raises the device timeout flag and returns.  The call
+ *   then returns NNP_ERR_TIMEOUT (the expected outcome), clears the flag, and
+ *   the context stays usable; any other status means the bound failed. */
+#define NNP_SELFTEST_WAIT_TIMEOUT 1
+int nnp_selftest(nnp_ctx *ctx, int32_t test);
+
 /* Queries for tests and benchmarks. */
 typedef enum {
     NNP_Q_LAUNCHES_PER_EVAL = 0,  /* kernels launched by one nnp_eval */

@@ -39,7 +39,7 @@ STAGES = ("cells", "neighbours", "descriptor", "network", "descriptor_backward")
 ABI_FUNCTIONS = ("nnp_config_init", "nnp_create", "nnp_destroy", "nnp_last_error",
                  "nnp_set_weights", "nnp_eval", "nnp_eval_async", "nnp_sync",
                  "nnp_eval_batch", "nnp_param_count", "nnp_force_match_grad", "nnp_query",
-                 "nnp_profile_stages", "nnp_atom_energies", "nnp_eval_noalloc", "nnp_eval_mlmm", "nnp_eval_pairs",
+                 "nnp_profile_stages", "nnp_atom_energies", "nnp_eval_noalloc", "nnp_eval_mlmm", "nnp_eval_pairs", "nnp_selftest",
                  "nnp_eval_batch_async")
 
 QUERY = {"launches_per_eval": 0, "nbr_capacity": 1, "ang_capacity": 2, "max_nbr": 3,
@@ -129,6 +129,8 @@ def lib() -> ctypes.CDLL:
     L.nnp_eval_mlmm.restype = ctypes.c_int
     L.nnp_eval_pairs.argtypes = [vp, i64, dp, dp, dp, i64, dp, dp, dp, dp]
     L.nnp_eval_pairs.restype = ctypes.c_int
+    L.nnp_selftest.argtypes = [vp, i32]
+    L.nnp_selftest.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -329,6 +331,11 @@ class NNP:
             pE, pF = ctypes.c_void_p(E.ctypes.data), ctypes.c_void_p(F.ctypes.data)
         self._check(self._L.nnp_eval_pairs(self._h, n, pp, pz, pbox, npairs, pq, ps, pE, pF))
         return (float(E[0]) if not _is_torch(pos) else E[0]), F
+
+    def selftest_wait_timeout(self):
+        """Run the bounded-wait self-test; raises NNPError (code 6, timeout),
+        which is the expected outcome."""
+        self._check(self._L.nnp_selftest(self._h, 1))
 
     def sync(self):
         self._check(self._L.nnp_sync(self._h))

@@ -495,6 +495,7 @@ int nnp_ctx::check_flags() {
   max_nbr_a = f[kFlagMaxNbrA];
   if (f[kFlagNonFinite]) return fail(NNP_ERR_INVALID_ARG, "non-finite atom position");
   if (f[kFlagBadSpecies]) return fail(NNP_ERR_UNKNOWN_SPECIES, "atomic number outside the configured species");
+  if (f[kFlagTimeout]) return fail(NNP_ERR_TIMEOUT, "a bounded device wait expired (tensor-core network)");
   if (f[kFlagBadPair])
     return fail(NNP_ERR_INVALID_ARG, "pair list: an index is out of range or a shift is not a whole periodic image");
   if (f[kFlagOverflowR] || f[kFlagOverflowA]) {
@@ -762,6 +763,23 @@ int nnp_atom_energies(nnp_ctx* ctx, double* out) {
   for (long long r = 0; r < used && r < rows; ++r)
     if (ra[r] >= 0 && ra[r] < ctx->last_n) out[ra[r]] = (double)ei[r];
   return NNP_OK;
+}
+
+int nnp_selftest(nnp_ctx* ctx, int32_t test) {
+  if (!ctx) return NNP_ERR_INVALID_ARG;
+  if (test != NNP_SELFTEST_WAIT_TIMEOUT) return ctx->fail(NNP_ERR_INVALID_ARG, "unknown self-test %d", test);
+  int f[kNumFlags];
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->b_flags, 0, sizeof f, ctx->stream);
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "nnp_selftest");
+  launch_wait_selftest(ctx->stream, ctx->b_flags, 2000000ull);  // 2 ms
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f, ctx->b_flags, sizeof f, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->b_flags, 0, sizeof f, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "nnp_selftest");
+  if (f[kFlagTimeout]) return ctx->fail(NNP_ERR_TIMEOUT, "self-test: the bounded wait expired and returned, as designed");
+  return ctx->fail(NNP_ERR_CUDA, "self-test: a wait on a barrier that nothing completes did not time out");
 }
 
 int nnp_profile_stages(nnp_ctx* ctx, double* out, int32_t n_out) {

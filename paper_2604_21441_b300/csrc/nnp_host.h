@@ -16,6 +16,7 @@ __global__ void k_scatter(const EvalIO* io, Workspace ws);
 __global__ void k_binsort(const EvalIO* io, int S, int sort, Workspace ws);
 __global__ void k_neighbors(const EvalIO* io, const SysDesc* sys, DescParams P, Workspace ws);
 void set_cell_steps(SysDesc& sd);  // cell steps and their inverse from nc, ell or B
+void launch_wait_selftest(cudaStream_t st, int* flags, unsigned long long limit_ns);
 __global__ void k_pairs_prep(int S, Workspace ws);
 __global__ void k_pairs_count(const EvalIO* io, const SysDesc* sys, DescParams P, Workspace ws);
 __global__ void k_pairs_offsets(const EvalIO* io, int S, Workspace ws, int* cur);
