@@ -227,12 +227,17 @@ __global__ void __launch_bounds__(256, 3) k_aev_fwd(const SysDesc* __restrict__ 
                                                16 * (size_t)ca) + hwb;
   const float kr = -P.eta_r * kLog2e, ka = -P.eta_a * kLog2e;
   const float kfr = kPi / (2.f * P.rc_r), kfa = kPi / (2.f * P.rc_a);
-  f2 hc2[4], hs2[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    hc2[q] = f2_make(P.hcos_z[2 * q], P.hcos_z[2 * q + 1]);
-    hs2[q] = f2_make(P.hsin_z[2 * q], P.hsin_z[2 * q + 1]);
+  // sector constants (z, z+1) in shared memory, read with volatile loads in
+  // the pair loop: kept in registers they push the kernel past its register
+  // budget (80 at three blocks per SM) into spills and moves
+  __shared__ unsigned long long s_hcs[8];
+  if (threadIdx.x < 8) {
+    const int q = threadIdx.x & 3;
+    s_hcs[threadIdx.x] = threadIdx.x < 4 ? f2_make(P.hcos_z[2 * q], P.hcos_z[2 * q + 1]).v
+                                         : f2_make(P.hsin_z[2 * q], P.hsin_z[2 * q + 1]).v;
   }
+  __syncthreads();
+  const volatile unsigned long long* vhcs = s_hcs;
   const f2 half2 = f2_make(0.5f, 0.5f), kr2 = f2_make(kr, kr);
   const int rows = ws.seg[S];
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -382,7 +387,10 @@ __global__ void __launch_bounds__(256, 3) k_aev_fwd(const SysDesc* __restrict__ 
             const f2 uc2 = f2_make(uc, uc), sn2 = f2_make(sn, sn);
 #pragma unroll
             for (int zp = 0; zp < kNAngZ / 2; ++zp) {
-              f2 bz = f2_fma(sn2, hs2[zp], f2_fma(uc2, hc2[zp], half2));
+              f2 hcz, hsz;
+              hcz.v = vhcs[zp];
+              hsz.v = vhcs[4 + zp];
+              f2 bz = f2_fma(sn2, hsz, f2_fma(uc2, hcz, half2));
               if (ZSQ >= 0) {
 #pragma unroll
                 for (int i = 0; i < (ZSQ >= 0 ? ZSQ : 0); ++i) bz = f2_mul(bz, bz);
