@@ -99,12 +99,6 @@ __device__ __forceinline__ void hw_reduce_scatter(float (&v)[V], int hl) {
   }
 }
 
-__device__ __forceinline__ float hw_sum(float x) {
-#pragma unroll
-  for (int o = 8; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  return x;
-}
-
 // Flat pair index t of block (s1, s2) -> positions (u, v) in the staged
 // angular neighbours.  Off-diagonal blocks: t = q n2 + r.  Diagonal blocks
 // (n atoms): each unordered pair once, as (q, q + k mod n) with k <= K for the

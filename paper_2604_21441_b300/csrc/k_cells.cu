@@ -8,8 +8,9 @@
 //   k_scan     bin counts -> row starts; species segments padded to 128 rows
 //   k_scatter  atom -> row (slot order, not yet deterministic)
 //   k_binsort  order each bin by input index; write the row arrays
-//   k_neighbors  warp per cell, lane per row: the 27-cell neighbourhood
-//                staged in shared memory; lists grouped by neighbour species
+//   k_neighbors  warp per cell: the 27-cell neighbourhood staged in shared
+//                memory, rows in groups with 2-32 lanes per row; lists
+//                grouped by neighbour species, angular entries first
 #include "nnp_internal.cuh"
 
 namespace nnp {
@@ -277,19 +278,26 @@ __global__ void __launch_bounds__(256) k_binsort(const EvalIO* __restrict__ io, 
   }
 }
 
-// Warp per cell (grid-stride over the cells of every system), lane per row
-// of the cell (in groups of 32).  For each neighbour species, the atoms of the
-// 27 virtual cells around the cell (periodic images by the virtual cell offset
-// m in {-1,0,1}^3) are staged in the warp's shared window as positions
-// relative to the cell's corner plus their list entry; every lane then walks
-// the window (a broadcast read) and tests its own row.  A candidate (j, m) is
-// kept if |off_j + m*ell - off_i| < rc_r and it is not the atom itself.
-// Within a species, entries inside rc_a go to the front of the row's
-// segment; radial-only entries are parked at the end of the row's list and
-// moved behind the angular ones once the species is done (their order is
-// free).  Counts are clamped to what the list holds, so readers never run
-// past it; the unclamped maxima raise the overflow flags (one update per
-// CTA).  Padding rows get zero counts from k_scan.
+// Warp per cell (grid-stride over the cells of every system).  For each
+// neighbour species, the atoms of the 27 virtual cells around the cell
+// (periodic images by the virtual cell offset m in {-1,0,1}^3, shift
+// sum_d m_d cv_d) are staged in the warp's shared window as positions relative
+// to the cell's corner plus their list entry.  A candidate (j, m) is kept if
+// |off_j + shift(m) - off_i| < rc_r and it is not the atom itself; within a
+// species, entries inside rc_a come first in the row's segment, then the
+// radial-only ones (their order is free).  Counts are clamped to what the
+// list holds, so readers never run past it; the unclamped maxima raise the
+// overflow flags (one update per CTA).  Padding rows get zero counts from
+// k_scan.
+//
+// Two ways through a cell.  The group path (windows that fit kNbrWin): rows
+// in groups of up to 16 with 2-32 lanes per row, each lane testing a share of
+// the window's 32-candidate chunks; hit counts are scanned over a row's lanes
+// so every entry goes straight to its place.  The lane-per-row path (larger
+// windows): one lane per row over windows of kNbrWin, radial-only entries
+// parked at the end of the list and moved down once the species is done.
+// Both keep the hit masks of a lane in shared-memory slots and write the hits
+// with one loop whose step count is the same for the whole warp.
 __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __restrict__ io,
                                                           const SysDesc* __restrict__ sys,
                                                           DescParams P, Workspace ws) {

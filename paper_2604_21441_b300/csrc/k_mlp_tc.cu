@@ -142,19 +142,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                    smem_u32(bar))
                : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-      "[%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-        "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-}
 
 // K-major operand, 128-byte swizzle: start address, leading byte offset
 // (unused for this layout, 16 B), stride byte offset 1024 B between 8-row
@@ -198,10 +185,6 @@ __device__ __forceinline__ float ex2f(float x) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-__device__ __forceinline__ float celu_f(float z, float al, float k) {
-  return z > 0.f ? z : al * (ex2f(z * k) - 1.f);
-}
-__device__ __forceinline__ float dcelu_f(float z, float k) { return z > 0.f ? 1.f : ex2f(z * k); }
 
 // Store 16 values of row r, columns [c0, c0+16), as BF16 into a swizzled buffer.
 __device__ __forceinline__ void store_row16(uint8_t* buf, int r, int c0, const float (&v)[16]) {
