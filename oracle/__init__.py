@@ -25,6 +25,9 @@ energy_forces              : pinned (finite differences, sum F = 0,
                              gives the same result)
 aev_jvp, force_match       : pinned (finite differences in positions and in
                              weights)
+ensemble_energy_forces     : pinned (equals one wider network with
+                             block-diagonal hidden layers and the output layer
+                             divided by M; M copies of one network equal it)
 mlmm_energy_forces         : pinned (finite differences of the embedded energy
                              in the whole system's coordinates, zero net
                              force, a link placed on its MM atom)
@@ -324,6 +327,19 @@ def force_match(model: Model, pos, species, box, Fref):
     lib().or_force_match(model.ref, n, _dp(pos), _ip(species), None if bx is None else _dp(bx),
                          _dp(Fref), _dp(L), PW, PB, _dp(F))
     return float(L[0]), dW, db, F
+
+
+def ensemble_energy_forces(models, pos, species, box):
+    """Ensemble of M networks of one architecture over one descriptor (the
+    ANI-2x model of the performance-scaling study in the Results is an
+    ensemble of eight): energy, per-atom energies and forces are the means of
+    the members' values.  Returns E, Ei (n,), F (n, 3)."""
+    M = len(models)
+    E, Ei, F = 0.0, 0.0, 0.0
+    for m in models:
+        e, ei, f, _ = energy_forces(m, pos, species, box)
+        E, Ei, F = E + e, Ei + ei, F + f
+    return E / M, Ei / M, F / M
 
 
 def mlmm_energy_forces(model: Model, pos, species, box, ml_index, link_ml, link_mm, link_d,
