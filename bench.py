@@ -424,6 +424,74 @@ def pairs_rate(precision, steps=20):
             "atom_steps_per_s_pair_list": s.n / (out["pair_list"] * 1e-3)}
 
 
+def ensemble_rate(precision, members=8, steps=20):
+    """An ensemble of M networks (the ANI-2x model is eight networks over one
+    descriptor) on the 32,768-water box: synchronous calls with device
+    buffers, timed by wall clock beside the single network.  The descriptor,
+    its backward and the neighbour search run once; only the network stage
+    runs M times."""
+    import torch
+    import synth
+    import paper_2604_21441_b300 as P
+    wl = synth.workload(3)
+    s = wl["systems"][0]
+    dev = lambda a: torch.tensor(a, device="cuda")
+    pos, Z = dev(s.pos), dev(s.Z.astype(np.int32))
+    box = np.diag(s.box)
+    out = {}
+    for M in (1, members):
+        pot = P.NNP(atomic_numbers=(1, 8), precision=precision, max_atoms=s.n, n_members=M)
+        for m in range(M):
+            w = synth.xavier_weights(2, 128, wl["weight_seed"] + m)
+            pot.set_all_weights([[(W.astype(np.float32), b.astype(np.float32)) for W, b in x] for x in w], m)
+        for _ in range(3):
+            pot.eval(pos, Z, box)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            pot.eval(pos, Z, box)
+        out[M] = (time.perf_counter() - t0) * 1e3 / steps
+        pot.close()
+    return {"workload": "water-32768 (98,304 atoms)", "precision": precision, "members": members,
+            "steps": steps, "ms_per_step_single": out[1], "ms_per_step_ensemble": out[members],
+            "atom_steps_per_s_ensemble": s.n / (out[members] * 1e-3)}
+
+
+def seven_species_rate(members=8, steps=20):
+    """The seven-element model (H, C, N, O, F, S, Cl; D = 1008, the ANI-2x
+    element set) on HCNOFSCl-40A (2,000 cluster atoms + 1,349 waters), FP32
+    form: one network and an ensemble of M, synchronous calls with device
+    buffers, timed by wall clock."""
+    import torch
+    import synth
+    import paper_2604_21441_b300 as P
+    wl = synth.workload(6)
+    s = wl["systems"][0]
+    dev = lambda a: torch.tensor(a, device="cuda")
+    pos, Z = dev(s.pos), dev(s.Z.astype(np.int32))
+    box = np.diag(s.box)
+    S = len(wl["atomic_numbers"])
+    out = {}
+    for M in (1, members):
+        pot = P.NNP(atomic_numbers=wl["atomic_numbers"], precision="fp32", max_atoms=s.n, n_members=M)
+        for m in range(M):
+            w = synth.xavier_weights(S, synth.aev_length(S), wl["weight_seed"] + m)
+            pot.set_all_weights([[(W.astype(np.float32), b.astype(np.float32)) for W, b in x] for x in w], m)
+        for _ in range(3):
+            pot.eval(pos, Z, box)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            pot.eval(pos, Z, box)
+        out[M] = (time.perf_counter() - t0) * 1e3 / steps
+        pot.close()
+    return {"workload": wl["name"], "atoms": s.n, "species": S, "aev_length": synth.aev_length(S),
+            "precision": "fp32", "members": members, "steps": steps,
+            "ms_per_step_single": out[1], "ms_per_step_ensemble": out[members],
+            "atom_steps_per_s_single": s.n / (out[1] * 1e-3),
+            "atom_steps_per_s_ensemble": s.n / (out[members] * 1e-3)}
+
+
 def oracle_sample(wl, w, seconds=20.0, seed=0):
     """Time the FP64 oracle on bounded samples of the workload: sampled atoms
     get E_i and F_i, which evaluates them and every atom within the radial
@@ -578,6 +646,9 @@ def main():
         line["nve"] = nve_rate(args.precision)
         line["mlmm"] = mlmm_rate(args.precision)
         line["pairs"] = pairs_rate(args.precision)
+        if args.precision != "fp8":
+            line["ensemble"] = ensemble_rate(args.precision)
+        line["seven_species"] = seven_species_rate()
     if r["per_system_ms"] is not None:
         line["batch"] = {"systems": r["B"], "one_graph_launch_ms": ms_mean,
                          "one_launch_per_system_ms": r["per_system_ms"],

@@ -69,6 +69,7 @@ typedef enum {
 
 #define NNP_MAX_SPECIES 8
 #define NNP_MAX_SHIFTS 32
+#define NNP_MAX_MEMBERS 16
 
 /* Context flags */
 #define NNP_FLAG_NO_GRAPH 0x1u      /* launch kernels directly instead of a CUDA graph */
@@ -91,8 +92,10 @@ typedef enum {
  *   p(s1, s2) = row-major index of the unordered species pair (s1 <= s2).
  *
  * The kernels are specialised for n_rad = 16, n_ang_r = 4, n_ang_z = 8,
- * zeta a power of two (<= 64), hidden = {160, 128, 96}, 1 <= S <= 4;
- * other values give NNP_ERR_UNSUPPORTED.
+ * zeta a power of two (<= 64), hidden = {160, 128, 96}, 1 <= S <= 8
+ * (S = 7, D = 1008: the H, C, N, O, S, F, Cl element set of ANI-2x); other
+ * values give NNP_ERR_UNSUPPORTED.  The BF16 and FP8 forms take S <= 2
+ * (D <= 128); nnp_force_match_grad and nnp_eval_noalloc take S <= 4.
  */
 typedef struct {
     int32_t n_species;                        /* S */
@@ -114,6 +117,11 @@ typedef struct {
     int32_t ang_capacity;     /* angular neighbours per atom; 0 = 32; grows on overflow */
     void *stream;             /* cudaStream_t to run on; NULL = the library makes one */
     uint32_t flags;           /* NNP_FLAG_* */
+    int32_t n_members;        /* ensemble size M (0 or 1 = one network; at most
+                                 NNP_MAX_MEMBERS; FP32 or BF16 only): E_i is the
+                                 mean of M networks of the same shape over the
+                                 shared descriptor, as in the ANI-2x model, and
+                                 the forces are minus the gradient of that mean */
 } nnp_config;
 
 /* ANI-style defaults for n_species species with the given atomic numbers
@@ -145,6 +153,15 @@ const char *nnp_last_error(const nnp_ctx *ctx);
  * next evaluation). */
 int nnp_set_weights(nnp_ctx *ctx, int32_t species, const float *const W[4],
                     const float *const b[4]);
+
+/* Weights of species s in ensemble member m (0 <= m < n_members), laid out
+ * and owned as in nnp_set_weights; nnp_set_weights is member 0.  Every member
+ * of every species needs weights before the first evaluation.  The output
+ * layer is stored divided by M so that the members' contributions, added
+ * into the same per-atom energies and descriptor gradients, give the mean.
+ * NNP_ERR_INVALID_ARG for m or s out of range or a null array. */
+int nnp_set_member_weights(nnp_ctx *ctx, int32_t member, int32_t species,
+                           const float *const W[4], const float *const b[4]);
 
 /* Energy and forces of one system of n atoms.
  *   pos    n x 3 positions (Angstrom), any values (wrapped into the box);
@@ -197,7 +214,8 @@ int nnp_eval_async(nnp_ctx *ctx, int64_t n, const double *pos, const int32_t *Z,
  *   Same meaning as nnp_eval for one periodic system, with n <=
  *   NNP_NOALLOC_MAX_ATOMS (larger n: NNP_ERR_CAPACITY), pos, Z, energy and
  *   forces device pointers, box a host pointer (orthorhombic, edges >= rc_r),
- *   FP32 contexts only (else NNP_ERR_UNSUPPORTED).  At most 128 radial and 48
+ *   FP32 contexts of at most 4 species only (else NNP_ERR_UNSUPPORTED;
+ *   ensembles are fine).  At most 128 radial and 48
  *   angular neighbours per atom (more: NNP_ERR_CAPACITY, lists do not grow).
  *   Synchronous; runs on the context's stream and leaves the context's own
  *   buffers, graph and last-evaluation state untouched.
@@ -245,7 +263,8 @@ int64_t nnp_param_count(const nnp_ctx *ctx);
  *          2 (F - Fref) / (3n), and *loss (if non-NULL) receives L.
  * F and the gradient are computed in the FP32 form (whatever the context's
  * precision) with FP64 sums: directional derivative of the descriptors along
- * v, then forward-over-reverse through the per-element networks. */
+ * v, then forward-over-reverse through the per-element networks.
+ * NNP_ERR_UNSUPPORTED for ensembles and for more than 4 species. */
 int nnp_force_match_grad(nnp_ctx *ctx, const double *v, const double *Fref, double *loss,
                          double *grad);
 

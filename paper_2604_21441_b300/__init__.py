@@ -40,7 +40,7 @@ ABI_FUNCTIONS = ("nnp_config_init", "nnp_create", "nnp_destroy", "nnp_last_error
                  "nnp_set_weights", "nnp_eval", "nnp_eval_async", "nnp_sync",
                  "nnp_eval_batch", "nnp_param_count", "nnp_force_match_grad", "nnp_query",
                  "nnp_profile_stages", "nnp_atom_energies", "nnp_eval_noalloc", "nnp_eval_mlmm", "nnp_eval_pairs", "nnp_selftest",
-                 "nnp_eval_batch_async")
+                 "nnp_eval_batch_async", "nnp_set_member_weights")
 
 QUERY = {"launches_per_eval": 0, "nbr_capacity": 1, "ang_capacity": 2, "max_nbr": 3,
          "max_ang": 4, "rows": 5, "graph_captures": 6,
@@ -77,6 +77,7 @@ class Config(ctypes.Structure):
         ("ang_capacity", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
         ("flags", ctypes.c_uint32),
+        ("n_members", ctypes.c_int32),
     ]
 
 
@@ -103,6 +104,8 @@ def lib() -> ctypes.CDLL:
     L.nnp_last_error.restype = ctypes.c_char_p
     L.nnp_set_weights.argtypes = [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(vp)]
     L.nnp_set_weights.restype = ctypes.c_int
+    L.nnp_set_member_weights.argtypes = [vp, i32, i32, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    L.nnp_set_member_weights.restype = ctypes.c_int
     L.nnp_eval.argtypes = [vp, i64, dp, dp, dp, dp, dp]
     L.nnp_eval.restype = ctypes.c_int
     L.nnp_eval_async.argtypes = [vp, i64, dp, dp, dp, dp, dp]
@@ -169,7 +172,7 @@ class NNP:
     """One libnnp context (one CUDA stream)."""
 
     def __init__(self, atomic_numbers=(1, 8), precision: str = "fp32", max_atoms: int = 4096,
-                 max_systems: int = 1, stream=None, flags: int = 0, **overrides):
+                 max_systems: int = 1, stream=None, flags: int = 0, n_members: int = 1, **overrides):
         L = lib()
         self._L = L
         zs = (ctypes.c_int32 * NNP_MAX_SPECIES)(*atomic_numbers)
@@ -181,6 +184,8 @@ class NNP:
         cfg.max_atoms = int(max_atoms)
         cfg.max_systems = int(max_systems)
         cfg.flags = int(flags)
+        cfg.n_members = int(n_members)
+        self.n_members = int(n_members)
         self.torch_stream = None
         if stream is not None:
             handle = stream if isinstance(stream, int) else stream.cuda_stream
@@ -237,7 +242,7 @@ class NNP:
         return int(v.value)
 
     # -- weights
-    def set_weights(self, species: int, layers):
+    def set_weights(self, species: int, layers, member: int = 0):
         """layers = [(W1, b1), ..., (W4, b4)], W_l (fan_in x fan_out)."""
         keep, Wp, bp = [], (ctypes.c_void_p * 4)(), (ctypes.c_void_p * 4)()
         for l, (W, b) in enumerate(layers):
@@ -245,11 +250,21 @@ class NNP:
             pb, kb = _ptr(b, np.float32)
             keep += [kw, kb]
             Wp[l], bp[l] = pw.value, pb.value
-        self._check(self._L.nnp_set_weights(self._h, int(species), Wp, bp))
+        if member == 0:
+            self._check(self._L.nnp_set_weights(self._h, int(species), Wp, bp))
+        else:
+            self._check(self._L.nnp_set_member_weights(self._h, int(member), int(species), Wp, bp))
 
-    def set_all_weights(self, weights):
+    def set_all_weights(self, weights, member: int = 0):
         for s, layers in enumerate(weights):
-            self.set_weights(s, layers)
+            self.set_weights(s, layers, member)
+
+    def set_member_weights(self, members):
+        """members[m] = per-species layers of ensemble member m (len = n_members)."""
+        if len(members) != self.n_members:
+            raise ValueError(f"expected {self.n_members} members, got {len(members)}")
+        for m, weights in enumerate(members):
+            self.set_all_weights(weights, m)
 
     # -- evaluation
     def eval(self, pos, Z, box=None, forces=True):

@@ -186,9 +186,9 @@ __device__ __forceinline__ void load_counts(const Workspace& ws, int S, int row,
                                             RowCounts* rc, int hl) {
   if (hl == 0) {
     int o = 0, oa = 0;
-    for (int s = 0; s < kMaxS; ++s) {
-      const int n = (live && s < S) ? ws.cnt_r[(size_t)row * kMaxS + s] : 0;
-      int a = (live && s < S) ? ws.cnt_a[(size_t)row * kMaxS + s] : 0;
+    for (int s = 0; s < S; ++s) {
+      const int n = live ? ws.cnt_r[(size_t)row * kMaxS + s] : 0;
+      int a = live ? ws.cnt_a[(size_t)row * kMaxS + s] : 0;
       a = min(a, max(0, cap_a - oa));  // never stage past the buffer
       rc->nr[s] = n;
       rc->orr[s] = o;
@@ -469,9 +469,9 @@ struct PairBlock {
 constexpr int kBwdMatCap = 32;
 __host__ __device__ inline int bwd_mat_cap(int cap_a) { return cap_a < kBwdMatCap ? cap_a : kBwdMatCap; }
 __host__ __device__ inline size_t bwd_mat_f4(int mc) { return ((size_t)mc * (mc + 1) * 2 + 3) / 4; }
-__host__ __device__ inline size_t bwd_warp_f4(int cap_a, int cap_r, int D) {
-  return 27 + 2 * (size_t)cap_a + bwd_mat_f4(bwd_mat_cap(cap_a)) + (size_t)D / 4 + ((size_t)3 * cap_r + 3) / 4 +
-         ((size_t)cap_r + 3) / 4 + (sizeof(PairBlock) * (kMaxS * (kMaxS + 1) / 2) + 15) / 16;
+__host__ __device__ inline size_t bwd_warp_f4(int cap_a, int cap_r, int S) {
+  return 27 + 2 * (size_t)cap_a + bwd_mat_f4(bwd_mat_cap(cap_a)) + (size_t)desc_len(S) / 4 +
+         ((size_t)3 * cap_r + 3) / 4 + ((size_t)cap_r + 3) / 4 + (sizeof(PairBlock) * (S * (S + 1) / 2) + 15) / 16;
 }
 
 template <int S, int ZSQ>
@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
   extern __shared__ float4 sm4[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int ca = ws.cap_a, cr = ws.cap_r;
-  float4* sh = sm4 + (size_t)wib * bwd_warp_f4(ca, cr, D);
+  float4* sh = sm4 + (size_t)wib * bwd_warp_f4(ca, cr, S);
   float4* geo = sh + 27;
   float4* aux = geo + ca;
   float2* mat = reinterpret_cast<float2*>(aux + ca);  // [ca][ca + 1]
@@ -1017,8 +1017,8 @@ static void jvp_t(long long rows, int nsm, cudaStream_t st, const SysDesc* sys, 
 size_t aev_fwd_smem(int cap_a, int cap_r) {
   return 16 * ((size_t)(cap_a + 27 + cap_r) * sizeof(float4) + (size_t)cap_a * sizeof(float) + sizeof(RowCounts));
 }
-size_t aev_bwd_smem(int cap_a, int cap_r, int D) {
-  return (size_t)kBwdWarps * bwd_warp_f4(cap_a, cap_r, D) * sizeof(float4);
+size_t aev_bwd_smem(int cap_a, int cap_r, int S) {
+  return (size_t)kBwdWarps * bwd_warp_f4(cap_a, cap_r, S) * sizeof(float4);
 }
 
 static int warps_grid(long long rows, int warps_per_block, int nsm, int per_sm) {
@@ -1042,7 +1042,7 @@ static void bwd_t(long long rows, int nsm, cudaStream_t st, const EvalIO* io, co
                   const DescParams& P, const Workspace& ws) {
   long long g = (rows + kBwdWarps - 1) / kBwdWarps;
   if (g > (long long)nsm * g_bwd_per_sm) g = (long long)nsm * g_bwd_per_sm;
-  k_aev_bwd<S, ZSQ><<<(int)(g < 1 ? 1 : g), 32 * kBwdWarps, aev_bwd_smem(ws.cap_a, ws.cap_r, P.D),
+  k_aev_bwd<S, ZSQ><<<(int)(g < 1 ? 1 : g), 32 * kBwdWarps, aev_bwd_smem(ws.cap_a, ws.cap_r, S),
                       st>>>(io, sys, P, ws);
 }
 
@@ -1050,24 +1050,18 @@ void launch_aev_fwd(long long rows, int nsm, cudaStream_t st, const SysDesc* sys
                     const Workspace& ws, int mode, int per_sm) {
   g_fwd_per_sm = per_sm > 0 ? per_sm : 8;
   const bool z5 = P.zeta_sq == 5;
-  switch (P.S) {
-    case 1: z5 ? fwd_t<1, 5>(rows, nsm, st, sys, P, ws, mode) : fwd_t<1, -1>(rows, nsm, st, sys, P, ws, mode); break;
-    case 2: z5 ? fwd_t<2, 5>(rows, nsm, st, sys, P, ws, mode) : fwd_t<2, -1>(rows, nsm, st, sys, P, ws, mode); break;
-    case 3: z5 ? fwd_t<3, 5>(rows, nsm, st, sys, P, ws, mode) : fwd_t<3, -1>(rows, nsm, st, sys, P, ws, mode); break;
-    default: z5 ? fwd_t<4, 5>(rows, nsm, st, sys, P, ws, mode) : fwd_t<4, -1>(rows, nsm, st, sys, P, ws, mode); break;
-  }
+#define FWD(s) z5 ? fwd_t<s, 5>(rows, nsm, st, sys, P, ws, mode) : fwd_t<s, -1>(rows, nsm, st, sys, P, ws, mode)
+  switch (P.S) { NNP_SPECIES_CASES(FWD) }
+#undef FWD
 }
 
 void launch_aev_bwd(long long rows, int nsm, cudaStream_t st, const EvalIO* io, const SysDesc* sys,
                     const DescParams& P, const Workspace& ws, int per_sm) {
   g_bwd_per_sm = per_sm > 0 ? per_sm : 16;
   const bool z5 = P.zeta_sq == 5;
-  switch (P.S) {
-    case 1: z5 ? bwd_t<1, 5>(rows, nsm, st, io, sys, P, ws) : bwd_t<1, -1>(rows, nsm, st, io, sys, P, ws); break;
-    case 2: z5 ? bwd_t<2, 5>(rows, nsm, st, io, sys, P, ws) : bwd_t<2, -1>(rows, nsm, st, io, sys, P, ws); break;
-    case 3: z5 ? bwd_t<3, 5>(rows, nsm, st, io, sys, P, ws) : bwd_t<3, -1>(rows, nsm, st, io, sys, P, ws); break;
-    default: z5 ? bwd_t<4, 5>(rows, nsm, st, io, sys, P, ws) : bwd_t<4, -1>(rows, nsm, st, io, sys, P, ws); break;
-  }
+#define BWD(s) z5 ? bwd_t<s, 5>(rows, nsm, st, io, sys, P, ws) : bwd_t<s, -1>(rows, nsm, st, io, sys, P, ws)
+  switch (P.S) { NNP_SPECIES_CASES(BWD) }
+#undef BWD
   long long g = (rows + 255) / 256;
   if (g > (long long)nsm * 4) g = (long long)nsm * 4;
   k_forces_out<<<(int)(g < 1 ? 1 : g), 256, 0, st>>>(io, ws);
@@ -1081,23 +1075,20 @@ static cudaError_t big_smem(K k) {
 void launch_aev_jvp(long long rows, int nsm, cudaStream_t st, const SysDesc* sys, const DescParams& P,
                     const Workspace& ws, const double* v, float* dG) {
   const bool z5 = P.zeta_sq == 5;
-  switch (P.S) {
-    case 1: z5 ? jvp_t<1, 5>(rows, nsm, st, sys, P, ws, v, dG) : jvp_t<1, -1>(rows, nsm, st, sys, P, ws, v, dG); break;
-    case 2: z5 ? jvp_t<2, 5>(rows, nsm, st, sys, P, ws, v, dG) : jvp_t<2, -1>(rows, nsm, st, sys, P, ws, v, dG); break;
-    case 3: z5 ? jvp_t<3, 5>(rows, nsm, st, sys, P, ws, v, dG) : jvp_t<3, -1>(rows, nsm, st, sys, P, ws, v, dG); break;
-    default: z5 ? jvp_t<4, 5>(rows, nsm, st, sys, P, ws, v, dG) : jvp_t<4, -1>(rows, nsm, st, sys, P, ws, v, dG); break;
-  }
+#define JVP(s) z5 ? jvp_t<s, 5>(rows, nsm, st, sys, P, ws, v, dG) : jvp_t<s, -1>(rows, nsm, st, sys, P, ws, v, dG)
+  switch (P.S) { NNP_SPECIES_CASES_FM(JVP) }
+#undef JVP
 }
 
 cudaError_t aev_set_smem_limits() {
   cudaError_t e = cudaSuccess;
 #define BS(k) if ((e = big_smem(k)) != cudaSuccess) return e
-  BS((k_aev_fwd<1, 5>)); BS((k_aev_fwd<2, 5>)); BS((k_aev_fwd<3, 5>)); BS((k_aev_fwd<4, 5>));
-  BS((k_aev_fwd<1, -1>)); BS((k_aev_fwd<2, -1>)); BS((k_aev_fwd<3, -1>)); BS((k_aev_fwd<4, -1>));
-  BS((k_aev_bwd<1, 5>)); BS((k_aev_bwd<2, 5>)); BS((k_aev_bwd<3, 5>)); BS((k_aev_bwd<4, 5>));
-  BS((k_aev_bwd<1, -1>)); BS((k_aev_bwd<2, -1>)); BS((k_aev_bwd<3, -1>)); BS((k_aev_bwd<4, -1>));
-  BS((k_aev_jvp<1, 5>)); BS((k_aev_jvp<2, 5>)); BS((k_aev_jvp<3, 5>)); BS((k_aev_jvp<4, 5>));
-  BS((k_aev_jvp<1, -1>)); BS((k_aev_jvp<2, -1>)); BS((k_aev_jvp<3, -1>)); BS((k_aev_jvp<4, -1>));
+#define FB(s) BS((k_aev_fwd<s, 5>)); BS((k_aev_fwd<s, -1>)); BS((k_aev_bwd<s, 5>)); BS((k_aev_bwd<s, -1>))
+  FB(1); FB(2); FB(3); FB(4); FB(5); FB(6); FB(7); FB(8);
+#define JB(s) BS((k_aev_jvp<s, 5>)); BS((k_aev_jvp<s, -1>))
+  JB(1); JB(2); JB(3); JB(4);
+#undef JB
+#undef FB
 #undef BS
   return e;
 }

@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(1024) k_scan(const EvalIO* __restrict__ io, in
       ws.pos4[r] = make_float4(0.f, 0.f, 0.f, __int_as_float(s));
       ws.row_info[r] = 0;
       ws.row_cell[r] = 0;
-      for (int sp = 0; sp < kMaxS; ++sp) {
+      for (int sp = 0; sp < S; ++sp) {
         ws.cnt_r[(size_t)r * kMaxS + sp] = 0;
         ws.cnt_a[(size_t)r * kMaxS + sp] = 0;
       }
@@ -297,7 +297,9 @@ __global__ void __launch_bounds__(256) k_binsort(const EvalIO* __restrict__ io, 
 // windows): one lane per row over windows of kNbrWin, radial-only entries
 // parked at the end of the list and moved down once the species is done.
 // Both keep the hit masks of a lane in shared-memory slots and write the hits
-// with one loop whose step count is the same for the whole warp.
+// with one loop whose step count is the same for the whole warp.  SB >= S
+// bounds the per-species register arrays and scans (2, 4 or 8).
+template <int SB>
 __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __restrict__ io,
                                                           const SysDesc* __restrict__ sys,
                                                           DescParams P, Workspace ws) {
@@ -340,11 +342,11 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
     }
     int rpre = rln;  // inclusive prefix over species
 #pragma unroll
-    for (int o = 1; o < kMaxS; o <<= 1) {
+    for (int o = 1; o < SB; o <<= 1) {
       const int y = __shfl_up_sync(F, rpre, o);
       if (lane >= o) rpre += y;
     }
-    const int nrows = __shfl_sync(F, rpre, kMaxS - 1);
+    const int nrows = __shfl_sync(F, rpre, SB - 1);
     if (nrows == 0) continue;
     // virtual cell v = lane (< 27): local index of the real cell, or -1 outside an open boundary
     int vcell = -1;
@@ -363,10 +365,10 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
     }
     // bins of the 27 virtual cells for every species (lane v), their exclusive
     // offsets within the species' flattened neighbourhood, and its size
-    int bst[kMaxS], bln[kMaxS], bex[kMaxS], tot[kMaxS];
+    int bst[SB], bln[SB], bex[SB], tot[SB];
     int max_tot = 0, sum_tot = 0;  // sum of the windows, each rounded up to whole chunks
 #pragma unroll
-    for (int sp = 0; sp < kMaxS; ++sp) {
+    for (int sp = 0; sp < SB; ++sp) {
       bst[sp] = 0;
       bln[sp] = 0;
       if (sp < S && vcell >= 0) {
@@ -386,10 +388,10 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
       sum_tot += (tot[sp] + 31) & ~31;
     }
     // per-species register arrays are read with constant indices only
-    auto pick = [&](const int (&a)[kMaxS], int sp) {
+    auto pick = [&](const int (&a)[SB], int sp) {
       int x = a[0];
 #pragma unroll
-      for (int t = 1; t < kMaxS; ++t)
+      for (int t = 1; t < SB; ++t)
         if (sp == t) x = a[t];
       return x;
     };
@@ -417,7 +419,7 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
     auto row_of = [&](int q) {
       int row = 0;
 #pragma unroll
-      for (int s = 0; s < kMaxS; ++s) {
+      for (int s = 0; s < SB; ++s) {
         const int inc = __shfl_sync(F, rpre, s), len = __shfl_sync(F, rln, s), st = __shfl_sync(F, rst, s);
         if (q >= inc - len && q < inc) row = st + (q - (inc - len));
       }
@@ -566,10 +568,6 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
           if (all_fit) wb += (wn + 31) & ~31;
         }
         if (has && p == 0) {
-          for (int sp = S; sp < kMaxS; ++sp) {
-            ws.cnt_r[(size_t)row * kMaxS + sp] = 0;
-            ws.cnt_a[(size_t)row * kMaxS + sp] = 0;
-          }
           mx_r = max(mx_r, tot_r);
           mx_a = max(mx_a, tot_a);
         }
@@ -661,10 +659,6 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
         tot_a += ka;
       }
       if (has) {
-        for (int sp = S; sp < kMaxS; ++sp) {
-          ws.cnt_r[(size_t)row * kMaxS + sp] = 0;
-          ws.cnt_a[(size_t)row * kMaxS + sp] = 0;
-        }
         mx_r = max(mx_r, tot_r);
         mx_a = max(mx_a, tot_a);
       }
@@ -701,9 +695,19 @@ size_t neighbors_smem(int cap_r) {
 cudaError_t neighbors_set_smem_limits() {
   cudaError_t e = cudaFuncSetAttribute(k_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(sizeof(int) * kScanSmemBins));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_neighbors, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)neighbors_smem(4096));
+  const int sm = (int)neighbors_smem(4096);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_neighbors<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_neighbors<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_neighbors<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  return e;
+}
+
+void launch_neighbors(int grid, cudaStream_t st, const EvalIO* io, const SysDesc* sys, const DescParams& P,
+                      const Workspace& ws) {
+  const size_t sm = neighbors_smem(ws.cap_r);
+  if (P.S <= 2) k_neighbors<2><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws);
+  else if (P.S <= 4) k_neighbors<4><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws);
+  else k_neighbors<8><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws);
 }
 
 }  // namespace nnp

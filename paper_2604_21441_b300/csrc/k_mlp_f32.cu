@@ -7,7 +7,9 @@
 //   g_3 = w_4 * CELU'(z_3),  g_{l-1} = (g_l W_l^T) * CELU'(z_{l-1}),
 //   dE/dG = g_1 W_1^T,   CELU'(z) = 1 (z > 0), h/alpha + 1 (z <= 0)
 //
-// One CTA of 256 threads per 64-row tile (one species per tile).  Thread
+// One CTA of 256 threads per 64-row tile (one species per tile).  Above
+// kF32WholeD descriptor features the last product (dE/dG) runs in column
+// blocks of kF32ColBlock, so the accumulators and the weight chunk stay small.  Thread
 // (warp ty, lane tx) owns rows 8ty..8ty+7 and columns tx + 32j.  The tile's
 // activations stay in shared memory, transposed (feature-major, padded
 // leading dimension) so that a thread's 8 rows are two float4 loads;
@@ -19,19 +21,34 @@ namespace nnp {
 constexpr int kTM = 64;          // rows per tile
 constexpr int kLDX = kTM + 4;    // padded leading dim of transposed activations
 constexpr int kKC = 32;          // streamed k-chunk
+constexpr int kF32WholeD = 384;  // widest descriptor whose dE/dG is one product
+constexpr int kF32ColBlock = 128;
+__host__ __device__ constexpr int f32_bsn(int D) {  // columns of the weight chunk buffer
+  return (D <= kF32WholeD ? (D > kH1 ? D : kH1) : (kF32ColBlock > kH1 ? kF32ColBlock : kH1));
+}
 
 // acc[8][NJ] += A(64 x K) * B(K x N).  A is either transposed in shared
 // memory (AT[k][kLDX]) or, if Ag != nullptr, rows of global memory (lda).
-template <int N>
+// CH: B is a column block of a wider matrix (leading dimension ldb) whose
+// columns from ncol on are absent (read as zero).
+template <int N, bool CH = false>
 __device__ __forceinline__ void gemm_tile(float (&acc)[8][(N + 31) / 32], const float* AT,
                                           const float* __restrict__ Ag, int lda, int K,
-                                          const float* __restrict__ Bg, float* Bs, float* As) {
+                                          const float* __restrict__ Bg, float* Bs, float* As,
+                                          int ldb = N, int ncol = N) {
   constexpr int NJ = (N + 31) / 32;
   const int tid = threadIdx.x, ty = tid >> 5, tx = tid & 31;
   for (int k0 = 0; k0 < K; k0 += kKC) {
     const int kc = min(kKC, K - k0);
     __syncthreads();
-    for (int i = tid; i < kc * N; i += 256) Bs[i] = Bg[(size_t)k0 * N + i];
+    if (CH) {
+      for (int i = tid; i < kc * N; i += 256) {
+        const int kk = i / N, c = i - kk * N;
+        Bs[i] = c < ncol ? Bg[(size_t)(k0 + kk) * ldb + c] : 0.f;
+      }
+    } else {
+      for (int i = tid; i < kc * N; i += 256) Bs[i] = Bg[(size_t)k0 * N + i];
+    }
     if (Ag) {
       for (int i = tid; i < kTM * kc; i += 256) {
         const int r = i / kc, kk = i - r * kc;
@@ -113,16 +130,17 @@ __device__ __forceinline__ void store_bwd(const float (&acc)[8][(N + 31) / 32], 
   }
 }
 
+// acc = 1: add E_i and dE/dG to what an earlier ensemble member left there
 template <int S>
 __global__ void __launch_bounds__(256, 1) k_mlp_f32(const EvalIO* __restrict__ io,
-                                                    DescParams P, Workspace ws, MlpF32Weights Wt) {
+                                                    DescParams P, Workspace ws, MlpF32Weights Wt, int acc) {
   constexpr int D = kNRad * S + kNAng * S * (S + 1) / 2;
   extern __shared__ float smf[];
   float* H1T = smf;                       // [160][kLDX]
   float* H2T = H1T + kH1 * kLDX;          // [128][kLDX]
   float* H3T = H2T + kH2 * kLDX;          // [96][kLDX]
-  float* Bs = H3T + kH3 * kLDX;           // [kKC][max N = max(160, D)]
-  constexpr int kBsN = (D > kH1 ? D : kH1);
+  float* Bs = H3T + kH3 * kLDX;           // [kKC][widest N of a product]
+  constexpr int kBsN = f32_bsn(D);
   float* As = Bs + kKC * kBsN;            // [kKC][kLDX]
   const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
   const float al = P.celu_alpha, inv_al = 1.f / P.celu_alpha;
@@ -175,7 +193,10 @@ __global__ void __launch_bounds__(256, 1) k_mlp_f32(const EvalIO* __restrict__ i
       const bool valid = tx < 8 && ws.row_atom[row] >= 0;
       const int sys = ws.row_info[row];
       ev += Wt.b[sp][3][0];
-      if (tx < 8) ws.Ei[row] = valid ? ev : 0.f;
+      if (tx < 8) {
+        const float v = valid ? ev : 0.f;
+        ws.Ei[row] = acc ? ws.Ei[row] + v : v;
+      }
       unsigned todo = __ballot_sync(0xffffffffu, valid);
       while (todo) {  // per-system runs: shuffle sum, one FP64 add each
         const int leader = __ffs(todo) - 1;
@@ -197,15 +218,37 @@ __global__ void __launch_bounds__(256, 1) k_mlp_f32(const EvalIO* __restrict__ i
     zero_acc<kH1>(accb1);
     gemm_tile<kH1>(accb1, H2T, nullptr, 0, kH2, Wt.WT[sp][1], Bs, As);
     store_bwd<kH1>(accb1, H1T, inv_al);
-    float accg[8][(D + 31) / 32];
-    zero_acc<D>(accg);
-    gemm_tile<D>(accg, H1T, nullptr, 0, kH1, Wt.WT[sp][0], Bs, As);
+    if (D <= kF32WholeD) {
+      float accg[8][(D + 31) / 32];
+      zero_acc<D>(accg);
+      gemm_tile<D>(accg, H1T, nullptr, 0, kH1, Wt.WT[sp][0], Bs, As);
 #pragma unroll
-    for (int j = 0; j < (D + 31) / 32; ++j) {
-      const int col = tx + 32 * j;
-      if (D % 32 != 0 && col >= D) continue;
+      for (int j = 0; j < (D + 31) / 32; ++j) {
+        const int col = tx + 32 * j;
+        if (D % 32 != 0 && col >= D) continue;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) ws.dEdG[(size_t)(row0 + ty * 8 + i) * D + col] = accg[i][j];
+        for (int i = 0; i < 8; ++i) {
+          float* o = ws.dEdG + (size_t)(row0 + ty * 8 + i) * D + col;
+          *o = acc ? *o + accg[i][j] : accg[i][j];
+        }
+      }
+    } else {
+      for (int c0 = 0; c0 < D; c0 += kF32ColBlock) {
+        const int nc = min(kF32ColBlock, D - c0);
+        float accg[8][kF32ColBlock / 32];
+        zero_acc<kF32ColBlock>(accg);
+        gemm_tile<kF32ColBlock, true>(accg, H1T, nullptr, 0, kH1, Wt.WT[sp][0] + c0, Bs, As, D, nc);
+#pragma unroll
+        for (int j = 0; j < kF32ColBlock / 32; ++j) {
+          const int col = tx + 32 * j;
+          if (col >= nc) continue;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            float* o = ws.dEdG + (size_t)(row0 + ty * 8 + i) * D + c0 + col;
+            *o = acc ? *o + accg[i][j] : accg[i][j];
+          }
+        }
+      }
     }
     __syncthreads();
   }
@@ -480,12 +523,9 @@ size_t fm_rev_smem() {
 void launch_fm(int grid, cudaStream_t st, const DescParams& P, const Workspace& ws, const MlpF32Weights& W,
                const float* dG, float* z, float* dz, float* t, float* p) {
   const size_t sf = fm_fwd_smem(P.D), sr = fm_rev_smem();
-  switch (P.S) {
-    case 1: k_fm_fwd<1><<<grid, 256, sf, st>>>(P, ws, W, dG, z, dz); k_fm_rev<1><<<grid, 256, sr, st>>>(P, ws, W, z, dz, t, p); break;
-    case 2: k_fm_fwd<2><<<grid, 256, sf, st>>>(P, ws, W, dG, z, dz); k_fm_rev<2><<<grid, 256, sr, st>>>(P, ws, W, z, dz, t, p); break;
-    case 3: k_fm_fwd<3><<<grid, 256, sf, st>>>(P, ws, W, dG, z, dz); k_fm_rev<3><<<grid, 256, sr, st>>>(P, ws, W, z, dz, t, p); break;
-    default: k_fm_fwd<4><<<grid, 256, sf, st>>>(P, ws, W, dG, z, dz); k_fm_rev<4><<<grid, 256, sr, st>>>(P, ws, W, z, dz, t, p); break;
-  }
+#define FM(s) k_fm_fwd<s><<<grid, 256, sf, st>>>(P, ws, W, dG, z, dz); k_fm_rev<s><<<grid, 256, sr, st>>>(P, ws, W, z, dz, t, p)
+  switch (P.S) { NNP_SPECIES_CASES_FM(FM) }  // at most kMaxSFm species (checked by the caller)
+#undef FM
 }
 
 void launch_fm_wgrad(int grid, cudaStream_t st, const DescParams& P, const FmJob* jobs, int njobs,
@@ -495,27 +535,23 @@ void launch_fm_wgrad(int grid, cudaStream_t st, const DescParams& P, const FmJob
 }
 
 size_t mlp_f32_smem(int D) {
-  const int bsn = D > kH1 ? D : kH1;
-  return sizeof(float) * ((size_t)(kH1 + kH2 + kH3) * kLDX + (size_t)kKC * bsn + (size_t)kKC * kLDX);
+  return sizeof(float) * ((size_t)(kH1 + kH2 + kH3) * kLDX + (size_t)kKC * f32_bsn(D) + (size_t)kKC * kLDX);
 }
 
 void launch_mlp_f32(int grid, cudaStream_t st, const EvalIO* io, const DescParams& P,
-                    const Workspace& ws, const MlpF32Weights& W) {
+                    const Workspace& ws, const MlpF32Weights& W, int acc) {
   const size_t sm = mlp_f32_smem(P.D);
-  switch (P.S) {
-    case 1: k_mlp_f32<1><<<grid, 256, sm, st>>>(io, P, ws, W); break;
-    case 2: k_mlp_f32<2><<<grid, 256, sm, st>>>(io, P, ws, W); break;
-    case 3: k_mlp_f32<3><<<grid, 256, sm, st>>>(io, P, ws, W); break;
-    default: k_mlp_f32<4><<<grid, 256, sm, st>>>(io, P, ws, W); break;
-  }
+#define MLP(s) k_mlp_f32<s><<<grid, 256, sm, st>>>(io, P, ws, W, acc)
+  switch (P.S) { NNP_SPECIES_CASES(MLP) }
+#undef MLP
 }
 
 cudaError_t mlp_f32_set_smem_limits() {
   cudaError_t e;
-  e = cudaFuncSetAttribute(k_mlp_f32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_f32_smem(48)); if (e) return e;
-  e = cudaFuncSetAttribute(k_mlp_f32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_f32_smem(128)); if (e) return e;
-  e = cudaFuncSetAttribute(k_mlp_f32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_f32_smem(240)); if (e) return e;
-  e = cudaFuncSetAttribute(k_mlp_f32<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_f32_smem(384)); if (e) return e;
+#define MSM(s) e = cudaFuncSetAttribute(k_mlp_f32<s>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                    (int)mlp_f32_smem(desc_len(s))); if (e) return e
+  MSM(1); MSM(2); MSM(3); MSM(4); MSM(5); MSM(6); MSM(7); MSM(8);
+#undef MSM
   const int Ds[4] = {48, 128, 240, 384};
   const void* fwd[4] = {(const void*)k_fm_fwd<1>, (const void*)k_fm_fwd<2>, (const void*)k_fm_fwd<3>, (const void*)k_fm_fwd<4>};
   const void* rev[4] = {(const void*)k_fm_rev<1>, (const void*)k_fm_rev<2>, (const void*)k_fm_rev<3>, (const void*)k_fm_rev<4>};

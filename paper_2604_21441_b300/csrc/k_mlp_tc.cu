@@ -316,8 +316,9 @@ __device__ __forceinline__ void for_chunks2(uint32_t tcol, uint32_t tcol2, int h
 }
 
 template <int D, bool F8>
+// acc = 1: add E_i and dE/dG to what an earlier ensemble member left there
 __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(const EvalIO* __restrict__ io, DescParams P,
-                                                  Workspace ws, MlpTcWeights Wt, MlpF32Weights Wf) {
+                                                  Workspace ws, MlpTcWeights Wt, MlpF32Weights Wf, int acc) {
   constexpr int kBufA = slabs_of(D > kH2 ? D : kH2) * kSlab;  // G, later g2
   constexpr int kBufB = slabs_of(kH1) * kSlab;                // h1, later g1
   constexpr int kBufC = slabs_of(kH2) * kSlab;                // h2, later g3
@@ -562,8 +563,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(const EvalIO* __restri
 #pragma unroll
       for (int g = 0; g < kG; ++g) e += sE[g * kTM + r];
       const bool valid = my_atom >= 0;
-      ws.Ei[row] = valid ? e : 0.f;
-      tile_energy_sums(valid ? e : 0.f, valid, my_sys, lane, io->energies);
+      const float ev = valid ? e : 0.f;
+      ws.Ei[row] = acc ? ws.Ei[row] + ev : ev;
+      tile_energy_sums(ev, valid, my_sys, lane, io->energies);
     }
     wait_mma(3);
     for_chunks2<kH2>(tg2, tz2, h, [&](int c0, float (&g)[16], float (&d)[16]) {
@@ -611,8 +613,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(const EvalIO* __restri
       float* out = ws.dEdG + (size_t)row * D;
       for_chunks<D>(tdg, h, [&](int c0, float (&v)[16]) {
 #pragma unroll
-        for (int j = 0; j < 16; j += 4)
-          *reinterpret_cast<float4*>(out + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        for (int j = 0; j < 16; j += 4) {
+          float4* o = reinterpret_cast<float4*>(out + c0 + j);
+          float4 x = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+          if (acc) {
+            const float4 y = *o;
+            x.x += y.x;
+            x.y += y.y;
+            x.z += y.z;
+            x.w += y.w;
+          }
+          *o = x;
+        }
       });
     }
   }
@@ -708,11 +720,11 @@ namespace {
 
 struct TcState {
   bool f8 = false;
-  uint8_t* blob = nullptr;   // pre-swizzled weights, all species
+  uint8_t* blob = nullptr;   // pre-swizzled weights, all members and species
   float* wsc = nullptr;      // FP8 per-column weight scales, all species
   size_t per_species = 0;
   size_t off[6] = {0, 0, 0, 0, 0, 0};
-  MlpTcWeights w{};
+  std::vector<MlpTcWeights> wm;  // one set of image pointers per ensemble member
 };
 
 // Byte offset of element (n, k) of a swizzled K-major [N][K] image with
@@ -780,21 +792,24 @@ int mlp_tc_init(nnp_ctx* ctx) {
   }
   st->per_species = o;
   ctx->tc = st;
-  cudaError_t e = cudaMalloc(&st->blob, o * ctx->P.S);
+  const size_t images = (size_t)ctx->n_members * ctx->P.S;
+  cudaError_t e = cudaMalloc(&st->blob, o * images);
   if (e != cudaSuccess) {
     st->blob = nullptr;
     return ctx->cuda_fail(e, "cudaMalloc tensor-core weights");
   }
-  cudaMemset(st->blob, 0, o * ctx->P.S);
-  for (int s = 0; s < ctx->P.S; ++s)
-    for (int i = 0; i < 6; ++i) st->w.m[s][i] = st->blob + o * s + st->off[i];
+  cudaMemset(st->blob, 0, o * images);
+  st->wm.assign((size_t)ctx->n_members, MlpTcWeights{});
+  for (int m = 0; m < ctx->n_members; ++m)
+    for (int s = 0; s < ctx->P.S; ++s)
+      for (int i = 0; i < 6; ++i) st->wm[(size_t)m].m[s][i] = st->blob + o * ((size_t)m * ctx->P.S + s) + st->off[i];
   if (f8) {
     e = cudaMalloc(&st->wsc, sizeof(float) * (kH1 + kH2 + kH3) * ctx->P.S);
     if (e != cudaSuccess) {
       st->wsc = nullptr;
       return ctx->cuda_fail(e, "cudaMalloc FP8 weight scales");
     }
-    for (int s = 0; s < ctx->P.S; ++s) st->w.wsc[s] = st->wsc + (size_t)(kH1 + kH2 + kH3) * s;
+    for (int s = 0; s < ctx->P.S; ++s) st->wm[0].wsc[s] = st->wsc + (size_t)(kH1 + kH2 + kH3) * s;
   }
   e = cudaMalloc(&ctx->b_q8, sizeof(int) * 8 * kMaxS);
   if (e != cudaSuccess) {
@@ -809,7 +824,7 @@ int mlp_tc_init(nnp_ctx* ctx) {
   return NNP_OK;
 }
 
-int mlp_tc_set_weights(nnp_ctx* ctx, int s, const float* hb) {
+int mlp_tc_set_weights(nnp_ctx* ctx, int member, int s, const float* hb) {
   TcState* st = static_cast<TcState*>(ctx->tc);
   if (!st) return ctx->fail(NNP_ERR_UNSUPPORTED, "tensor-core state missing");
   const int D = ctx->P.D;
@@ -836,7 +851,8 @@ int mlp_tc_set_weights(nnp_ctx* ctx, int s, const float* hb) {
   swizzle_into(img.data() + st->off[5], D, kH1, [&](int n, int k) { return W1[(size_t)n * kH1 + k]; });
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpy(st->blob + st->per_species * s, img.data(), st->per_species, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(st->blob + st->per_species * ((size_t)member * ctx->P.S + s), img.data(), st->per_species,
+                   cudaMemcpyHostToDevice);
   if (e == cudaSuccess && st->f8) {
     // new weights: the weight scales of species s, and every activation range is re-calibrated
     e = cudaMemcpy(st->wsc + sw.size() * s, sw.data(), sizeof(float) * sw.size(), cudaMemcpyHostToDevice);
@@ -859,7 +875,7 @@ void mlp_tc_free(nnp_ctx* ctx) {
   ctx->tc = nullptr;
 }
 
-int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t stream, long long rows) {
+int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t stream, long long rows, int member, int acc) {
   TcState* st = static_cast<TcState*>(ctx->tc);
   if (!st) return ctx->fail(NNP_ERR_UNSUPPORTED, "tensor-core state missing");
   const int D = ctx->P.D;
@@ -867,12 +883,14 @@ int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t stream, long long rows) {
   const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, ctx->num_sms));
   const Workspace w = ctx->workspace();
   const size_t sm = smem_bytes(D);
+  const MlpTcWeights& tw = st->wm[(size_t)member];
+  const MlpF32Weights& fw = ctx->wf32m[(size_t)member];
   if (st->f8)
-    k_mlp_tc<128, true><<<grid, kTcThreads, sm, stream>>>(ctx->d_io, ctx->P, w, st->w, ctx->wf32);
+    k_mlp_tc<128, true><<<grid, kTcThreads, sm, stream>>>(ctx->d_io, ctx->P, w, tw, fw, acc);
   else if (D == 128)
-    k_mlp_tc<128, false><<<grid, kTcThreads, sm, stream>>>(ctx->d_io, ctx->P, w, st->w, ctx->wf32);
+    k_mlp_tc<128, false><<<grid, kTcThreads, sm, stream>>>(ctx->d_io, ctx->P, w, tw, fw, acc);
   else
-    k_mlp_tc<48, false><<<grid, kTcThreads, sm, stream>>>(ctx->d_io, ctx->P, w, st->w, ctx->wf32);
+    k_mlp_tc<48, false><<<grid, kTcThreads, sm, stream>>>(ctx->d_io, ctx->P, w, tw, fw, acc);
   return NNP_OK;
 }
 

@@ -27,8 +27,7 @@ namespace nnp {
 __global__ void k_pairs_prep(int S, Workspace ws) {
   const int rows = ws.seg[S];
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
-#pragma unroll
-    for (int s = 0; s < kMaxS; ++s) {
+    for (int s = 0; s < S; ++s) {
       ws.cnt_r[(size_t)r * kMaxS + s] = 0;
       ws.cnt_a[(size_t)r * kMaxS + s] = 0;
     }
@@ -110,7 +109,7 @@ __device__ __forceinline__ PairGeo pair_geo(const EvalIO* __restrict__ io, const
 // part in the match.
 namespace {
 __device__ __forceinline__ unsigned key_of(int row, int s, bool ang) {
-  return ((unsigned)row << 3) | ((unsigned)s << 1) | (ang ? 0u : 1u);
+  return ((unsigned)row << 4) | ((unsigned)s << 1) | (ang ? 0u : 1u);  // s < 8, rows < 2^28
 }
 }  // namespace
 

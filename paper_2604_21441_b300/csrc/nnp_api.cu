@@ -184,7 +184,7 @@ int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows,
     k_pairs_fill<<<g_pairs, 256, 0, stream>>>(io, sys, P, w, b_pair_cur);
     launches += 4;
   } else {
-    k_neighbors<<<g_cells, kNbrThreads, neighbors_smem(cap_r), stream>>>(io, sys, P, w); ++launches;
+    launch_neighbors(g_cells, stream, io, sys, P, w); ++launches;
   }
   mark_stage(2, capturing);
   if (calib) {  // FP8 calibration: FP32 descriptor, then the activation ranges
@@ -199,11 +199,16 @@ int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows,
   mark_stage(3, capturing);
   const int g_tiles = (int)std::min<long long>(rows / 64, (long long)nsm);
   if (cfg.precision == NNP_FP32) {
-    launch_mlp_f32(std::max(1, g_tiles), stream, io, P, w, wf32); ++launches;
+    for (int m = 0; m < n_members; ++m) {  // ensemble members add up (mean by the stored 1/M)
+      launch_mlp_f32(std::max(1, g_tiles), stream, io, P, w, wf32m[(size_t)m], m > 0 ? 1 : 0);
+      ++launches;
+    }
   } else {
-    int rc = launch_mlp_tc(this, stream, rows);
-    if (rc) return rc;
-    ++launches;
+    for (int m = 0; m < n_members; ++m) {
+      int rc = launch_mlp_tc(this, stream, rows, m, m > 0 ? 1 : 0);
+      if (rc) return rc;
+      ++launches;
+    }
   }
   mark_stage(4, capturing);
   launch_aev_bwd(rows, nsm, stream, io, sys, P, w, tune.bwd); launches += 2;
@@ -513,7 +518,8 @@ int nnp_ctx::check_flags() {
 
 bool nnp_ctx::weights_ready() const {
   for (int s = 0; s < P.S; ++s)
-    if (!has_weights[s]) return false;
+    for (int m = 0; m < n_members; ++m)
+      if (!has_w[(size_t)m * kMaxS + s]) return false;
   return true;
 }
 
@@ -561,7 +567,7 @@ int nnp_create(const nnp_config* cfg, nnp_ctx** out) {
   auto bad = [&](int code, const char* msg) { g_create_error = msg; return code; };
   const int S = cfg->n_species;
   if (S < 1 || S > NNP_MAX_SPECIES) return bad(NNP_ERR_INVALID_ARG, "n_species outside 1..8");
-  if (S > kMaxS) return bad(NNP_ERR_UNSUPPORTED, "the kernels support at most 4 species");
+  if (S > kMaxS) return bad(NNP_ERR_UNSUPPORTED, "the kernels support at most 8 species");
   for (int s = 0; s < S; ++s) {
     if (cfg->atomic_numbers[s] < 1 || cfg->atomic_numbers[s] > 127)
       return bad(NNP_ERR_INVALID_ARG, "atomic numbers must lie in 1..127");
@@ -581,6 +587,11 @@ int nnp_create(const nnp_config* cfg, nnp_ctx** out) {
   if (!(cfg->celu_alpha > 0)) return bad(NNP_ERR_INVALID_ARG, "celu_alpha must be positive");
   if (cfg->precision < NNP_FP32 || cfg->precision > NNP_FP8)
     return bad(NNP_ERR_INVALID_ARG, "unknown precision");
+  if (cfg->n_members < 0) return bad(NNP_ERR_INVALID_ARG, "negative ensemble size");
+  const int members = cfg->n_members > 0 ? cfg->n_members : 1;
+  if (members > NNP_MAX_MEMBERS) return bad(NNP_ERR_INVALID_ARG, "at most NNP_MAX_MEMBERS ensemble members");
+  if (members > 1 && cfg->precision == NNP_FP8)
+    return bad(NNP_ERR_UNSUPPORTED, "the FP8 form takes one network per species");
 
   nnp_ctx* c = new nnp_ctx();
   c->cfg = *cfg;
@@ -601,6 +612,7 @@ int nnp_create(const nnp_config* cfg, nnp_ctx** out) {
   P.celu_alpha = (float)cfg->celu_alpha;
   c->cap_r = cfg->nbr_capacity > 0 ? cfg->nbr_capacity : 96;
   c->cap_a = cfg->ang_capacity > 0 ? cfg->ang_capacity : 32;
+  c->n_members = members;
   int rc = c->init_device();
   if (rc) {
     g_create_error = c->err;
@@ -624,7 +636,18 @@ int nnp_set_weights(nnp_ctx* ctx, int32_t species, const float* const W[4], cons
   if (!W || !b) return ctx->fail(NNP_ERR_INVALID_ARG, "null weight arrays");
   for (int l = 0; l < 4; ++l)
     if (!W[l] || !b[l]) return ctx->fail(NNP_ERR_INVALID_ARG, "null weight or bias of layer %d", l);
-  return ctx->set_weights(species, W, b);
+  return ctx->set_weights(0, species, W, b);
+}
+
+int nnp_set_member_weights(nnp_ctx* ctx, int32_t member, int32_t species, const float* const W[4],
+                           const float* const b[4]) {
+  if (!ctx) return NNP_ERR_INVALID_ARG;
+  if (member < 0 || member >= ctx->n_members) return ctx->fail(NNP_ERR_INVALID_ARG, "member index %d", member);
+  if (species < 0 || species >= ctx->P.S) return ctx->fail(NNP_ERR_INVALID_ARG, "species index %d", species);
+  if (!W || !b) return ctx->fail(NNP_ERR_INVALID_ARG, "null weight arrays");
+  for (int l = 0; l < 4; ++l)
+    if (!W[l] || !b[l]) return ctx->fail(NNP_ERR_INVALID_ARG, "null weight or bias of layer %d", l);
+  return ctx->set_weights(member, species, W, b);
 }
 
 int nnp_eval(nnp_ctx* ctx, int64_t n, const double* pos, const int32_t* Z, const double* box,

@@ -52,22 +52,29 @@ int nnp_ctx::init_device() {
   wf32_stride = D * kH1 + kH1 * kH2 + kH2 * kH3 + kH3 + kH1 + kH2 + kH3 + 1 + kH1 * D + kH2 * kH1 +
                 kH3 * kH2;
   wf32_stride = (wf32_stride + 63) / 64 * 64;
-  CK(cudaMalloc(&b_wf32, sizeof(float) * wf32_stride * P.S));
-  CK(cudaMemset(b_wf32, 0, sizeof(float) * wf32_stride * P.S));
-  for (int s = 0; s < P.S; ++s) {
-    float* p = b_wf32 + wf32_stride * s;
-    wf32.W[s][0] = p; p += D * kH1;
-    wf32.W[s][1] = p; p += kH1 * kH2;
-    wf32.W[s][2] = p; p += kH2 * kH3;
-    wf32.W[s][3] = p; p += kH3;
-    wf32.b[s][0] = p; p += kH1;
-    wf32.b[s][1] = p; p += kH2;
-    wf32.b[s][2] = p; p += kH3;
-    wf32.b[s][3] = p; p += 1;
-    wf32.WT[s][0] = p; p += kH1 * D;
-    wf32.WT[s][1] = p; p += kH2 * kH1;
-    wf32.WT[s][2] = p; p += kH3 * kH2;
-  }
+  // one table per ensemble member (member m, species s at (m S + s) strides)
+  const size_t tables = (size_t)n_members * P.S;
+  CK(cudaMalloc(&b_wf32, sizeof(float) * wf32_stride * tables));
+  CK(cudaMemset(b_wf32, 0, sizeof(float) * wf32_stride * tables));
+  wf32m.assign((size_t)n_members, MlpF32Weights{});
+  for (int m = 0; m < n_members; ++m)
+    for (int s = 0; s < P.S; ++s) {
+      MlpF32Weights& t = wf32m[(size_t)m];
+      float* p = b_wf32 + wf32_stride * ((size_t)m * P.S + s);
+      t.W[s][0] = p; p += D * kH1;
+      t.W[s][1] = p; p += kH1 * kH2;
+      t.W[s][2] = p; p += kH2 * kH3;
+      t.W[s][3] = p; p += kH3;
+      t.b[s][0] = p; p += kH1;
+      t.b[s][1] = p; p += kH2;
+      t.b[s][2] = p; p += kH3;
+      t.b[s][3] = p; p += 1;
+      t.WT[s][0] = p; p += kH1 * D;
+      t.WT[s][1] = p; p += kH2 * kH1;
+      t.WT[s][2] = p; p += kH3 * kH2;
+    }
+  wf32 = wf32m[0];
+  has_w.assign((size_t)n_members * kMaxS, 0);
   host_weights.assign((size_t)nnp_param_count(this), 0.f);
   if (cfg.precision != NNP_FP32) {
     int rc = mlp_tc_init(this);
@@ -116,7 +123,10 @@ bool nnp_ctx::is_device(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-int nnp_ctx::set_weights(int s, const float* const W[4], const float* const b[4]) {
+// Member m's weights.  With an ensemble of M members, the output layer (W4,
+// b4) is stored divided by M, so that the networks' sum over members is
+// their mean: energies and dE/dG add up member by member.
+int nnp_ctx::set_weights(int m, int s, const float* const W[4], const float* const b[4]) {
   const int D = P.D;
   const int fin[4] = {D, kH1, kH2, kH3}, fout[4] = {kH1, kH2, kH3, 1};
   std::vector<float> w[4], bb[4];
@@ -136,29 +146,35 @@ int nnp_ctx::set_weights(int s, const float* const W[4], const float* const b[4]
   std::vector<float> blob(wf32_stride, 0.f);
   float* p = blob.data();
   auto put = [&](const std::vector<float>& v) { memcpy(p, v.data(), sizeof(float) * v.size()); p += v.size(); };
-  put(w[0]); put(w[1]); put(w[2]); put(w[3]);
-  put(bb[0]); put(bb[1]); put(bb[2]); put(bb[3]);
+  std::vector<float> w4 = w[3], b4 = bb[3];
+  for (float& x : w4) x /= (float)n_members;
+  for (float& x : b4) x /= (float)n_members;
+  put(w[0]); put(w[1]); put(w[2]); put(w4);
+  put(bb[0]); put(bb[1]); put(bb[2]); put(b4);
   for (int l = 0; l < 3; ++l) {  // transposed copies (fan_out x fan_in)
     for (int o = 0; o < fout[l]; ++o)
       for (int i = 0; i < fin[l]; ++i) p[(size_t)o * fin[l] + i] = w[l][(size_t)i * fout[l] + o];
     p += (size_t)fin[l] * fout[l];
   }
   CK(cudaStreamSynchronize(stream));
-  CK(cudaMemcpy(b_wf32 + wf32_stride * s, blob.data(), sizeof(float) * wf32_stride,
+  CK(cudaMemcpy(b_wf32 + wf32_stride * ((size_t)m * P.S + s), blob.data(), sizeof(float) * wf32_stride,
                 cudaMemcpyHostToDevice));
   // packed FP32 copy in the nnp_param_count layout: W1 b1 W2 b2 W3 b3 W4 b4
+  // (member 0 keeps it for force matching and FP8 re-quantisation)
   size_t per = 0;
   for (int l = 0; l < 4; ++l) per += (size_t)fin[l] * fout[l] + fout[l];
-  float* hp = host_weights.data() + per * s;
+  std::vector<float> packed(per);
+  float* hp = packed.data();
   for (int l = 0; l < 4; ++l) {
     memcpy(hp, w[l].data(), sizeof(float) * w[l].size()); hp += w[l].size();
     memcpy(hp, bb[l].data(), sizeof(float) * bb[l].size()); hp += bb[l].size();
   }
+  if (m == 0) memcpy(host_weights.data() + per * s, packed.data(), sizeof(float) * per);
   if (cfg.precision != NNP_FP32) {
-    int rc = mlp_tc_set_weights(this, s, host_weights.data() + per * s);
+    int rc = mlp_tc_set_weights(this, m, s, packed.data());
     if (rc) return rc;
   }
-  has_weights[s] = true;
+  has_w[(size_t)m * kMaxS + s] = 1;
   return NNP_OK;
 }
 
@@ -188,6 +204,8 @@ static cudaError_t grow_buf(T*& p, size_t& cap, size_t need) {
 }
 
 int nnp_ctx::force_match_grad(const double* v, const double* Fref, double* loss, double* grad) {
+  if (n_members > 1) return fail(NNP_ERR_UNSUPPORTED, "force matching takes one network per species");
+  if (P.S > kMaxSFm) return fail(NNP_ERR_UNSUPPORTED, "force matching supports at most %d species", kMaxSFm);
   if (!has_state) return fail(NNP_ERR_NO_STATE, "nnp_force_match_grad needs a previous nnp_eval");
   if (!grad) return fail(NNP_ERR_INVALID_ARG, "null gradient output");
   if (!v && !Fref) return fail(NNP_ERR_INVALID_ARG, "pass v = dL/dF or the reference forces");

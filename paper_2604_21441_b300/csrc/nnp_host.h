@@ -14,7 +14,8 @@ __global__ void k_bin(const EvalIO* io, const SysDesc* sys, const signed char* z
 __global__ void k_scan(const EvalIO* io, int S, Workspace ws);
 __global__ void k_scatter(const EvalIO* io, Workspace ws);
 __global__ void k_binsort(const EvalIO* io, int S, int sort, Workspace ws);
-__global__ void k_neighbors(const EvalIO* io, const SysDesc* sys, DescParams P, Workspace ws);
+void launch_neighbors(int grid, cudaStream_t st, const EvalIO* io, const SysDesc* sys, const DescParams& P,
+                      const Workspace& ws);
 void set_cell_steps(SysDesc& sd);  // cell steps and their inverse from nc, ell or B
 void launch_wait_selftest(cudaStream_t st, int* flags, unsigned long long limit_ns);
 __global__ void k_pairs_prep(int S, Workspace ws);
@@ -37,7 +38,7 @@ cudaError_t aev_set_smem_limits();
 
 // k_mlp_f32.cu
 void launch_mlp_f32(int grid, cudaStream_t st, const EvalIO* io, const DescParams& P,
-                    const Workspace& ws, const MlpF32Weights& W);
+                    const Workspace& ws, const MlpF32Weights& W, int acc = 0);
 cudaError_t mlp_f32_set_smem_limits();
 void launch_fm(int grid, cudaStream_t st, const DescParams& P, const Workspace& ws, const MlpF32Weights& W,
                const float* dG, float* z, float* dz, float* t, float* p);
@@ -52,9 +53,9 @@ void launch_aev_jvp(long long rows, int nsm, cudaStream_t st, const SysDesc* sys
 struct nnp_ctx;
 namespace nnp {
 // k_mlp_tc.cu (tensor-core network); returns an nnp_status
-int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t st, long long rows);
+int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t st, long long rows, int member, int acc);
 int mlp_tc_init(nnp_ctx* ctx);
-int mlp_tc_set_weights(nnp_ctx* ctx, int species, const float* host_blob);
+int mlp_tc_set_weights(nnp_ctx* ctx, int member, int species, const float* host_blob);
 int launch_fp8_calib(nnp_ctx* ctx, cudaStream_t st, long long rows);
 void mlp_tc_free(nnp_ctx* ctx);
 }  // namespace nnp
@@ -114,13 +115,15 @@ struct nnp_ctx {
   // weights
   float* b_wf32 = nullptr;      // FP32 blob, all species
   size_t wf32_stride = 0;       // floats per species
-  nnp::MlpF32Weights wf32{};
-  bool has_weights[nnp::kMaxS] = {false, false, false, false};
+  nnp::MlpF32Weights wf32{};                 // ensemble member 0 (every single-network path)
+  int n_members = 1;                         // networks averaged per species (ensemble)
+  std::vector<nnp::MlpF32Weights> wf32m;     // per member; wf32m[0] == wf32
+  std::vector<unsigned char> has_w;          // [member * kMaxS + species]
   std::vector<float> host_weights;  // FP32 copy (layout of nnp_param_count), for re-quantisation
   void* tc = nullptr;           // tensor-core network state (k_mlp_tc.cu)
   int* b_q8 = nullptr;          // FP8 scales (Workspace::q8)
   bool fp8_calibrated = false;  // every species has been seen by a calibration pass
-  bool fp8_seen[nnp::kMaxS] = {false, false, false, false};
+  bool fp8_seen[nnp::kMaxS] = {};
   int calibrate_fp8(long long n, int B, long long bins, long long rows);
 
   // force-matching buffers (allocated on first use)
@@ -193,7 +196,7 @@ struct nnp_ctx {
                const double* boxes, double* energies, double* forces, bool sync);
   int check_flags();
   bool weights_ready() const;
-  int set_weights(int species, const float* const W[4], const float* const b[4]);
+  int set_weights(int member, int species, const float* const W[4], const float* const b[4]);
   int force_match_grad(const double* v, const double* Fref, double* loss, double* grad);
   int profile_stages(double* out, int n_out);
 };

@@ -29,7 +29,7 @@ constexpr int kNAngR = 4;      // angular radial shifts
 constexpr int kNAngZ = 8;      // angular sectors
 constexpr int kNAng = kNAngR * kNAngZ;  // 32 features per species pair
 constexpr int kH1 = 160, kH2 = 128, kH3 = 96;
-constexpr int kMaxS = 4;       // species supported by the kernels
+constexpr int kMaxS = 8;       // species supported by the kernels (stride of the per-row counts)
 constexpr int kTileRows = 128; // species segments are padded to this
 constexpr int kMaxCapA = 64;     // largest angular-neighbour capacity (staged per row)
 constexpr int kMaxCapR = 512;    // largest radial-neighbour capacity (gathered per row)
@@ -40,7 +40,25 @@ constexpr int kNbrChunks = kNbrWin / 32;  // window chunks of 32 candidates
 constexpr int kNbrChunkStride = 36;       // floats per chunk in shared memory (bank spread)
 // shared floats per k_neighbors warp: x, y, z chunks, entries, 16 x 32 hit masks
 constexpr int kNbrWarpFloats = 3 * kNbrChunks * kNbrChunkStride + kNbrWin + 16 * 32;
-constexpr int kMaxD = kNRad * kMaxS + kNAng * kMaxS * (kMaxS + 1) / 2;  // 384
+constexpr int kMaxD = kNRad * kMaxS + kNAng * kMaxS * (kMaxS + 1) / 2;  // 1280
+__host__ __device__ constexpr int desc_len(int S) { return kNRad * S + kNAng * S * (S + 1) / 2; }
+constexpr int kMaxSFm = 4;     // species of the force-matching (second-order) kernels
+
+// switch cases over the species count, CALL(s) with s a constant 1..kMaxS
+#define NNP_SPECIES_CASES(CALL)                                                      \
+  case 1: CALL(1); break;                                                            \
+  case 2: CALL(2); break;                                                            \
+  case 3: CALL(3); break;                                                            \
+  case 4: CALL(4); break;                                                            \
+  case 5: CALL(5); break;                                                            \
+  case 6: CALL(6); break;                                                            \
+  case 7: CALL(7); break;                                                            \
+  default: CALL(8); break;
+#define NNP_SPECIES_CASES_FM(CALL)                                                   \
+  case 1: CALL(1); break;                                                            \
+  case 2: CALL(2); break;                                                            \
+  case 3: CALL(3); break;                                                            \
+  default: CALL(4); break;
 
 // Error flag words (device): set by kernels, read by the host after sync.
 enum FlagWord {

@@ -35,9 +35,11 @@ namespace {
 constexpr long long kNAMaxAtoms = NNP_NOALLOC_MAX_ATOMS;
 constexpr int kNACapR = 128;  // radial neighbours per atom
 constexpr int kNACapA = 48;   // angular neighbours per atom
-constexpr long long kNAMaxRows = kNAMaxAtoms + (long long)kTileRows * kMaxS;
+constexpr int kNAMaxS = 4;    // species (the scratch array is sized for D <= 384)
+constexpr long long kNAMaxRows = kNAMaxAtoms + (long long)kTileRows * kNAMaxS;
 constexpr long long kNAMaxCells = 2 * kNAMaxAtoms;  // cell cap per system (>= 27)
-constexpr long long kNAMaxBins = kMaxS * kNAMaxCells;
+constexpr long long kNAMaxBins = kNAMaxS * kNAMaxCells;
+constexpr int kNAMaxD = desc_len(kNAMaxS);
 
 constexpr size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -59,8 +61,8 @@ constexpr size_t o_cnt_r = o_row_cell + al256(sizeof(int) * kNAMaxRows);
 constexpr size_t o_cnt_a = o_cnt_r + al256(sizeof(int) * kNAMaxRows * kMaxS);
 constexpr size_t o_nbr_r = o_cnt_a + al256(sizeof(int) * kNAMaxRows * kMaxS);
 constexpr size_t o_G = o_nbr_r + al256(sizeof(int) * kNAMaxRows * kNACapR);
-constexpr size_t o_dEdG = o_G + al256(sizeof(float) * kNAMaxRows * kMaxD);
-constexpr size_t o_Ei = o_dEdG + al256(sizeof(float) * kNAMaxRows * kMaxD);
+constexpr size_t o_dEdG = o_G + al256(sizeof(float) * kNAMaxRows * kNAMaxD);
+constexpr size_t o_Ei = o_dEdG + al256(sizeof(float) * kNAMaxRows * kNAMaxD);
 constexpr size_t o_facc = o_Ei + al256(sizeof(float) * kNAMaxRows);
 constexpr size_t o_flags = o_facc + al256(sizeof(float4) * kNAMaxAtoms);
 constexpr size_t o_io = o_flags + al256(sizeof(int) * kNumFlags);
@@ -104,6 +106,8 @@ extern "C" int nnp_eval_noalloc(nnp_ctx* ctx, int64_t n, const double* pos, cons
     return ctx->fail(NNP_ERR_INVALID_ARG, "nnp_eval_noalloc needs device pointers for pos, Z, energy, forces");
   if (ctx->cfg.precision != NNP_FP32)
     return ctx->fail(NNP_ERR_UNSUPPORTED, "nnp_eval_noalloc supports FP32 contexts only");
+  if (ctx->P.S > kNAMaxS)
+    return ctx->fail(NNP_ERR_UNSUPPORTED, "nnp_eval_noalloc supports at most %d species", kNAMaxS);
   if (!ctx->weights_ready()) return ctx->fail(NNP_ERR_NO_WEIGHTS, "weights missing for some species");
 
   // device address of the scratch array (once per device, that device current)
@@ -227,9 +231,10 @@ extern "C" int nnp_eval_noalloc(nnp_ctx* ctx, int64_t n, const double* pos, cons
   k_scan<<<1, 1024, sizeof(int) * kScanSmemBins, st>>>(d_io, P.S, w);
   k_scatter<<<g_atoms, 256, 0, st>>>(d_io, w);
   k_binsort<<<g_bins, 256, 0, st>>>(d_io, P.S, 1, w);
-  k_neighbors<<<g_cells, kNbrThreads, neighbors_smem(w.cap_r), st>>>(d_io, d_sys, P, w);
+  launch_neighbors(g_cells, st, d_io, d_sys, P, w);
   launch_aev_fwd(rows, nsm, st, d_sys, P, w, 0);
-  launch_mlp_f32(g_tiles > 0 ? g_tiles : 1, st, d_io, P, w, ctx->wf32);
+  for (int m = 0; m < ctx->n_members; ++m)  // ensemble members add up
+    launch_mlp_f32(g_tiles > 0 ? g_tiles : 1, st, d_io, P, w, ctx->wf32m[(size_t)m], m > 0 ? 1 : 0);
   launch_aev_bwd(rows, nsm, st, d_io, d_sys, P, w);
   NA_CK(cudaGetLastError());
   NA_CK(cudaMemcpyAsync(hflags, w.flags, sizeof hflags, cudaMemcpyDeviceToHost, st));

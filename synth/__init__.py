@@ -23,6 +23,9 @@ hcno_box():        random covalent-like H/C/N/O trees (20-60 atoms, bond
                    lengths U(1.0, 1.5) A, element probabilities
                    H .45 / C .35 / N .10 / O .10) up to 2,000 atoms in a 40 A
                    box, then waters on the 1 g/cm^3 lattice filling the rest.
+                   With elements=ANI2X_Z, probs=ANI2X_P: the seven elements
+                   of the ANI-2x model (H .40 / C .30 / N .08 / O .08 / F .05
+                   / S .05 / Cl .04), same trees.
 xavier_weights():  per-species MLP weights, Xavier-uniform (gain 1), biases 0.
 """
 from __future__ import annotations
@@ -36,11 +39,11 @@ import numpy as np
 WATER_VOLUME_A3 = 29.915          # A^3 per molecule at 1 g/cm^3
 OH_BOND_A = 0.9572
 HOH_ANGLE_DEG = 104.52
-MASS_AMU = {1: 1.008, 6: 12.011, 7: 14.007, 8: 15.999}
+MASS_AMU = {1: 1.008, 6: 12.011, 7: 14.007, 8: 15.999, 9: 18.998, 16: 32.06, 17: 35.45}
 
 # Seeds per workload: geometry 1000 + k, weights 2000 + k.
-GEOM_SEED = {1: 1001, 2: 1002, 3: 1003, 4: 1004, 5: 1005}
-WEIGHT_SEED = {1: 2001, 2: 2002, 3: 2003, 4: 2004, 5: 2005}
+GEOM_SEED = {1: 1001, 2: 1002, 3: 1003, 4: 1004, 5: 1005, 6: 1006}
+WEIGHT_SEED = {1: 2001, 2: 2002, 3: 2003, 4: 2004, 5: 2005, 6: 2006}
 
 HIDDEN = (160, 128, 96)
 
@@ -144,12 +147,14 @@ def water_batch(n_systems: int, seed: int, lo: int = 16, hi: int = 2048
 
 HCNO_Z = np.array([1, 6, 7, 8], dtype=np.int32)
 HCNO_P = np.array([0.45, 0.35, 0.10, 0.10])
+ANI2X_Z = np.array([1, 6, 7, 8, 9, 16, 17], dtype=np.int32)
+ANI2X_P = np.array([0.40, 0.30, 0.08, 0.08, 0.05, 0.05, 0.04])
 
 
 def hcno_box(seed: int, L: float = 40.0, n_cluster_atoms: int = 2000,
              cluster_size: tuple[int, int] = (20, 60), max_waters: int = 3000,
              min_bonded: float = 0.95, min_between: float = 2.0,
-             water_excl: float = 2.5) -> System:
+             water_excl: float = 2.5, elements=HCNO_Z, probs=HCNO_P) -> System:
     """H/C/N/O clusters grown as random trees, solvated by lattice waters.
 
     Bonds: length U(1.0, 1.5) A along a uniform random direction from a
@@ -203,7 +208,7 @@ def hcno_box(seed: int, L: float = 40.0, n_cluster_atoms: int = 2000,
         else:
             raise RuntimeError("could not place a cluster seed")
         members = [len(pos)]
-        add(seedp, rng.choice(HCNO_Z, p=HCNO_P), c_id)
+        add(seedp, rng.choice(elements, p=probs), c_id)
         tries = 0
         while len(members) < size and tries < 20000:
             tries += 1
@@ -213,7 +218,7 @@ def hcno_box(seed: int, L: float = 40.0, n_cluster_atoms: int = 2000,
             p = parent + v * rng.uniform(1.0, 1.5)
             if ok(p, c_id):
                 members.append(len(pos))
-                add(p, rng.choice(HCNO_Z, p=HCNO_P), c_id)
+                add(p, rng.choice(elements, p=probs), c_id)
         c_id += 1
     n_clu = len(pos)
     cl = np.array(pos)
@@ -300,7 +305,7 @@ def aev_length(n_species: int, n_rad: int = 16, n_ang: int = 32) -> int:
 
 
 def workload(k: int) -> dict:
-    """The five named synthetic workloads (1..5) with their seeds."""
+    """The six named synthetic workloads (1..6) with their seeds."""
     if k == 1:
         s = water_box(64, GEOM_SEED[1])
         return dict(name="water-64 (192 atoms, 12.42 A)", systems=[s],
@@ -321,4 +326,8 @@ def workload(k: int) -> dict:
         s = hcno_box(GEOM_SEED[5])
         return dict(name="HCNO-40A (2,000 cluster atoms + waters)", systems=[s],
                     atomic_numbers=(1, 6, 7, 8), weight_seed=WEIGHT_SEED[5])
+    if k == 6:
+        s = hcno_box(GEOM_SEED[6], elements=ANI2X_Z, probs=ANI2X_P)
+        return dict(name="HCNOFSCl-40A (2,000 cluster atoms of 7 elements + waters)", systems=[s],
+                    atomic_numbers=tuple(int(z) for z in ANI2X_Z), weight_seed=WEIGHT_SEED[6])
     raise ValueError(k)

@@ -1,0 +1,164 @@
+"""GPU tests of the network ensemble (n_members = M: the per-atom energy is
+the mean of M networks over the shared descriptor, as in the eight-network
+ANI-2x model of the performance-scaling study in the Results).
+
+* M = 3, FP32: the FP64 oracle's ensemble mean within the FP32 bounds, on a
+  box and in the batched graph form;
+* M = 3, BF16: within the BF16 form's bounds;
+* M copies of one network give that network's result (the output layer is
+  stored divided by M, which rounds, so 1e-6 relative and 1e-5 eV/A);
+* M = 8 on the 12,288-atom box against the oracle on sampled atoms;
+* a missing member, FP8 with M > 1, M above the maximum and force matching
+  of an ensemble are refused, and the context keeps working.
+"""
+import numpy as np
+import pytest
+
+import synth
+from common import E_REL_TOL, F_ABS_TOL, box9, energy_error, weights32
+
+pytestmark = pytest.mark.gpu
+
+E_BF16 = 1e-2
+F_MAX_BF16 = 0.1
+F_RMS_BF16 = 0.02
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2604_21441_b300 import build
+    build.build()
+    import paper_2604_21441_b300 as P
+    return P
+
+
+def _members(M, seed):
+    return [weights32(2, 128, seed + 7 * m, seed + 7 * m + 1) for m in range(M)]
+
+
+def _f32(w):
+    return [[(W.astype(np.float32), b.astype(np.float32)) for W, b in sp] for sp in w]
+
+
+def _pot(P, mem, prec="fp32", **kw):
+    pot = P.NNP(atomic_numbers=(1, 8), precision=prec, n_members=len(mem), **kw)
+    pot.set_member_weights([_f32(w) for w in mem])
+    return pot
+
+
+def _oracle(oracle_mod, mem, pos, Z, box):
+    p = oracle_mod.Params()
+    models = [oracle_mod.Model(p, w) for w in mem]
+    return oracle_mod.ensemble_energy_forces(models, pos, p.species_of(Z), box)
+
+
+def test_ensemble3_fp32_vs_oracle(P, oracle_mod):
+    s = synth.water_box(64, 531)
+    mem = _members(3, 532)
+    pot = _pot(P, mem)
+    E, F = pot.eval(s.pos, s.Z, box9(s.box))
+    Er, Eir, Fr = _oracle(oracle_mod, mem, s.pos, s.Z, s.box)
+    print(f"ensemble-3 fp32 water-64: rel E err {energy_error(E, Er, Eir):.2e}, max|dF| {np.abs(F - Fr).max():.2e}")
+    assert energy_error(E, Er, Eir) <= E_REL_TOL
+    assert np.abs(F - Fr).max() <= F_ABS_TOL
+    Ei = pot.atom_energies(s.n)
+    assert np.abs(Ei - Eir).max() <= 1e-5 * max(1.0, np.abs(Eir).max())
+    # a second evaluation (captured graph replay) gives the same result up to
+    # the order of the FP32 atomic sums
+    E2, F2 = pot.eval(s.pos, s.Z, box9(s.box))
+    assert abs(E2 - E) <= 1e-7 * np.abs(Ei).sum() and np.abs(F2 - F).max() <= 1e-5
+
+
+def test_ensemble3_batch_vs_oracle(P, oracle_mod):
+    import torch
+    mem = _members(3, 541)
+    systems = [synth.water_box(n, 542 + n) for n in (27, 64, 125)]
+    off = np.cumsum([0] + [s.n for s in systems]).astype(np.int64)
+    pot = _pot(P, mem, max_atoms=int(off[-1]), max_systems=3)
+    pos = torch.tensor(np.concatenate([s.pos for s in systems]), device="cuda")
+    Z = torch.tensor(np.concatenate([s.Z for s in systems]), device="cuda")
+    E, F = pot.eval_batch(off, pos, Z, np.stack([s.box for s in systems]))
+    E, F = E.cpu().numpy(), F.cpu().numpy()
+    for b, s in enumerate(systems):
+        Er, Eir, Fr = _oracle(oracle_mod, mem, s.pos, s.Z, s.box)
+        assert energy_error(E[b], Er, Eir) <= E_REL_TOL, b
+        assert np.abs(F[off[b]:off[b + 1]] - Fr).max() <= F_ABS_TOL, b
+
+
+def test_ensemble3_bf16_vs_oracle(P, oracle_mod):
+    s = synth.water_box(64, 551)
+    mem = _members(3, 552)
+    pot = _pot(P, mem, "bf16")
+    E, F = pot.eval(s.pos, s.Z, box9(s.box))
+    Er, Eir, Fr = _oracle(oracle_mod, mem, s.pos, s.Z, s.box)
+    dF = F - Fr
+    print(f"ensemble-3 bf16 water-64: rel E err {energy_error(E, Er, Eir):.2e}, max|dF| {np.abs(dF).max():.3e},"
+          f" rms dF {np.sqrt((dF ** 2).mean()):.3e}")
+    assert energy_error(E, Er, Eir) <= E_BF16
+    assert np.abs(dF).max() <= F_MAX_BF16
+    assert np.sqrt((dF ** 2).mean()) <= F_RMS_BF16
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_copies_equal_single_network(P, prec):
+    s = synth.water_box(216, 561)
+    w = weights32(2, 128, 562, 563)
+    one = P.NNP(atomic_numbers=(1, 8), precision=prec)
+    one.set_all_weights(_f32(w))
+    E1, F1 = one.eval(s.pos, s.Z, box9(s.box))
+    Ei1 = one.atom_energies(s.n)
+    four = _pot(P, [w] * 4, prec)
+    E4, F4 = four.eval(s.pos, s.Z, box9(s.box))
+    assert abs(E4 - E1) <= 1e-6 * np.abs(Ei1).sum()
+    assert np.abs(F4 - F1).max() <= 1e-5
+
+
+def test_ensemble8_water4096_sampled(P, oracle_mod):
+    """M = 8 (the ANI-2x ensemble size) on 12,288 atoms, BF16: sampled atoms'
+    forces and energies against the oracle's ensemble on the same box."""
+    wl = synth.workload(2)
+    s = wl["systems"][0]
+    mem = _members(8, 571)
+    pot = _pot(P, mem, "bf16", max_atoms=s.n)
+    E, F = pot.eval(s.pos, s.Z, box9(s.box))
+    Ei = pot.atom_energies(s.n)
+    p = oracle_mod.Params()
+    models = [oracle_mod.Model(p, w) for w in mem]
+    sp = p.species_of(s.Z)
+    sel = np.random.default_rng(5).choice(s.n, 24, replace=False)
+    Eis, Fs = 0.0, 0.0
+    for m in models:
+        eis, fs = oracle_mod.energy_forces_subset(m, s.pos, sp, s.box, sel, sel)
+        Eis, Fs = Eis + eis, Fs + fs
+    Eis, Fs = Eis / 8, Fs / 8
+    dF = F[sel] - Fs
+    print(f"ensemble-8 bf16 water-4096 (24 sampled atoms): max|dEi| {np.abs(Ei[sel] - Eis).max():.2e},"
+          f" max|dF| {np.abs(dF).max():.3e}")
+    assert np.abs(Ei[sel] - Eis).max() <= E_BF16 * max(1.0, np.abs(Eis).max())
+    assert np.abs(dF).max() <= F_MAX_BF16
+    assert abs(Ei.sum() - E) <= 1e-6 * np.abs(Ei).sum()
+
+
+def test_ensemble_refusals(P):
+    s = synth.water_box(27, 581)
+    mem = _members(2, 582)
+    pot = P.NNP(atomic_numbers=(1, 8), n_members=2)
+    pot.set_all_weights(_f32(mem[0]))
+    with pytest.raises(P.NNPError) as e:
+        pot.eval(s.pos, s.Z, box9(s.box))
+    assert e.value.code == 7  # NO_WEIGHTS: member 1 has none
+    with pytest.raises(P.NNPError) as e:
+        pot.set_weights(0, _f32(mem[1])[0], member=2)
+    assert e.value.code == 1
+    pot.set_all_weights(_f32(mem[1]), member=1)
+    E, F = pot.eval(s.pos, s.Z, box9(s.box))
+    assert np.isfinite(E)
+    with pytest.raises(P.NNPError) as e:
+        pot.force_match_grad()
+    assert e.value.code == 3
+    with pytest.raises(P.NNPError) as e:
+        P.NNP(atomic_numbers=(1, 8), precision="fp8", n_members=2)
+    assert e.value.code == 3
+    with pytest.raises(P.NNPError) as e:
+        P.NNP(atomic_numbers=(1, 8), n_members=17)
+    assert e.value.code == 1

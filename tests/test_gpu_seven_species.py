@@ -1,0 +1,143 @@
+"""GPU tests at seven species (H, C, N, O, F, S, Cl; D = 1008: the element
+set of the ANI-2x model), FP32 form.
+
+* a small seven-element box and the full 6,047-atom workload against the FP64
+  oracle within the FP32 bounds;
+* water through a seven-species context equals water through a two-species
+  context with the mapped first-layer rows (the absent species' blocks are
+  zero);
+* an ensemble of two seven-species networks, the batched form and the
+  caller's pair list against the oracle;
+* the tensor-core forms, force matching and the no-allocation entry point
+  refuse more species than they take.
+"""
+import numpy as np
+import pytest
+
+import synth
+from common import E_REL_TOL, F_ABS_TOL, box9, energy_error, weights32
+
+pytestmark = pytest.mark.gpu
+
+Z7 = (1, 6, 7, 8, 9, 16, 17)
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2604_21441_b300 import build
+    build.build()
+    import paper_2604_21441_b300 as P
+    return P
+
+
+def _f32(w):
+    return [[(W.astype(np.float32), b.astype(np.float32)) for W, b in sp] for sp in w]
+
+
+def _pot(P, w, Zs=Z7, **kw):
+    pot = P.NNP(atomic_numbers=Zs, **kw)
+    pot.set_all_weights(_f32(w))
+    return pot
+
+
+def _small_box(seed):
+    return synth.hcno_box(seed, L=16.0, n_cluster_atoms=160, max_waters=60,
+                          elements=synth.ANI2X_Z, probs=synth.ANI2X_P)
+
+
+def test_seven_species_small_box(P, oracle_mod):
+    s = _small_box(701)
+    w = weights32(7, 1008, 702, 703)
+    pot = _pot(P, w)
+    E, F = pot.eval(s.pos, s.Z, box9(s.box))
+    p = oracle_mod.Params(atomic_numbers=Z7)
+    Er, Eir, Fr, _ = oracle_mod.energy_forces(oracle_mod.Model(p, w), s.pos, p.species_of(s.Z), s.box)
+    print(f"7 species, {s.n} atoms: rel E err {energy_error(E, Er, Eir):.2e}, max|dF| {np.abs(F - Fr).max():.2e}")
+    assert len(np.unique(s.Z)) == 7
+    assert energy_error(E, Er, Eir) <= E_REL_TOL
+    assert np.abs(F - Fr).max() <= F_ABS_TOL
+    Ei = pot.atom_energies(s.n)
+    assert np.abs(Ei - Eir).max() <= 1e-5 * max(1.0, np.abs(Eir).max())
+
+
+def test_seven_species_workload(P, oracle_mod):
+    """HCNOFSCl-40A: 2,000 cluster atoms of seven elements and 1,349 waters."""
+    wl = synth.workload(6)
+    s = wl["systems"][0]
+    w = weights32(7, 1008, wl["weight_seed"])
+    pot = _pot(P, w, max_atoms=s.n)
+    E, F = pot.eval(s.pos, s.Z, box9(s.box))
+    p = oracle_mod.Params(atomic_numbers=Z7)
+    Er, Eir, Fr, _ = oracle_mod.energy_forces(oracle_mod.Model(p, w), s.pos, p.species_of(s.Z), s.box)
+    print(f"HCNOFSCl-40A ({s.n} atoms): rel E err {energy_error(E, Er, Eir):.2e},"
+          f" max|dF| {np.abs(F - Fr).max():.2e}")
+    assert energy_error(E, Er, Eir) <= E_REL_TOL
+    assert np.abs(F - Fr).max() <= F_ABS_TOL
+
+
+def test_water_in_seven_species_context(P):
+    w7 = weights32(7, 1008, 711, 712)
+    pair = lambda a, b: a * 7 - a * (a - 1) // 2 + (b - a)
+    rows = np.concatenate([np.arange(0, 16), np.arange(48, 64)] +
+                          [112 + 32 * pair(a, b) + np.arange(32) for a, b in ((0, 0), (0, 3), (3, 3))])
+    w2 = [[(w7[s7][0][0][rows].copy(), w7[s7][0][1])] + list(w7[s7][1:]) for s7 in (0, 3)]
+    s = synth.water_box(216, 713)
+    E7, F7 = _pot(P, w7).eval(s.pos, s.Z, box9(s.box))
+    a2 = _pot(P, w2, Zs=(1, 8))
+    E2, F2 = a2.eval(s.pos, s.Z, box9(s.box))
+    Ei2 = a2.atom_energies(s.n)
+    assert abs(E7 - E2) <= 1e-6 * np.abs(Ei2).sum()
+    assert np.abs(F7 - F2).max() <= 1e-5
+
+
+def test_seven_species_ensemble_batch_pairs(P, oracle_mod):
+    import torch
+    mem = [weights32(7, 1008, 721 + 3 * m, 722 + 3 * m) for m in range(2)]
+    systems = [_small_box(731), _small_box(732)]
+    off = np.cumsum([0] + [s.n for s in systems]).astype(np.int64)
+    pot = P.NNP(atomic_numbers=Z7, n_members=2, max_atoms=int(off[-1]), max_systems=2)
+    pot.set_member_weights([_f32(w) for w in mem])
+    p = oracle_mod.Params(atomic_numbers=Z7)
+    models = [oracle_mod.Model(p, w) for w in mem]
+    pos = torch.tensor(np.concatenate([s.pos for s in systems]), device="cuda")
+    Z = torch.tensor(np.concatenate([s.Z for s in systems]), device="cuda")
+    E, F = pot.eval_batch(off, pos, Z, np.stack([s.box for s in systems]))
+    E, F = E.cpu().numpy(), F.cpu().numpy()
+    for b, s in enumerate(systems):
+        Er, Eir, Fr = oracle_mod.ensemble_energy_forces(models, s.pos, p.species_of(s.Z), s.box)
+        assert energy_error(E[b], Er, Eir) <= E_REL_TOL, b
+        assert np.abs(F[off[b]:off[b + 1]] - Fr).max() <= F_ABS_TOL, b
+    # the caller's pair list (half list within 6 A) for the first box
+    s = systems[0]
+    pi, pj, pd = oracle_mod.pairs_brute(s.pos, s.box, 6.0)
+    keep = pi < pj
+    pairs = np.stack([pi[keep], pj[keep]], axis=1).astype(np.int32)
+    shifts = pd[keep] - (s.pos[pj[keep]] - s.pos[pi[keep]])
+    Ep, Fp = pot.eval_pairs(s.pos, s.Z, pairs, shifts, box9(s.box))
+    Er, Eir, Fr = oracle_mod.ensemble_energy_forces(models, s.pos, p.species_of(s.Z), s.box)
+    assert energy_error(Ep, Er, Eir) <= E_REL_TOL
+    assert np.abs(Fp - Fr).max() <= F_ABS_TOL
+
+
+def test_seven_species_refusals(P):
+    w = weights32(7, 1008, 741)
+    for prec in ("bf16", "fp8"):
+        with pytest.raises(P.NNPError) as e:
+            P.NNP(atomic_numbers=Z7, precision=prec)
+        assert e.value.code == 3
+    pot = _pot(P, w)
+    s = _small_box(742)
+    E, _ = pot.eval(s.pos, s.Z, box9(s.box))
+    assert np.isfinite(E)
+    with pytest.raises(P.NNPError) as e:
+        pot.force_match_grad(Fref=np.zeros((s.n, 3)))
+    assert e.value.code == 3
+    import ctypes
+    import torch
+    pos, Z = torch.tensor(s.pos, device="cuda"), torch.tensor(s.Z, device="cuda")
+    E1 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    F1 = torch.zeros((s.n, 3), dtype=torch.float64, device="cuda")
+    box = np.ascontiguousarray(np.diag(s.box))
+    p_ = lambda t: ctypes.c_void_p(t.data_ptr())
+    rc = P.lib().nnp_eval_noalloc(pot._h, s.n, p_(pos), p_(Z), ctypes.c_void_p(box.ctypes.data), p_(E1), p_(F1))
+    assert rc == 3
