@@ -460,8 +460,8 @@ def ensemble_rate(precision, members=8, steps=20):
 def seven_species_rate(members=8, steps=20):
     """The seven-element model (H, C, N, O, F, S, Cl; D = 1008, the ANI-2x
     element set) on HCNOFSCl-40A (2,000 cluster atoms + 1,349 waters), FP32
-    form: one network and an ensemble of M, synchronous calls with device
-    buffers, timed by wall clock."""
+    and BF16 forms: one network and an ensemble of M, synchronous calls with
+    device buffers, timed by wall clock."""
     import torch
     import synth
     import paper_2604_21441_b300 as P
@@ -472,8 +472,8 @@ def seven_species_rate(members=8, steps=20):
     box = np.diag(s.box)
     S = len(wl["atomic_numbers"])
     out = {}
-    for M in (1, members):
-        pot = P.NNP(atomic_numbers=wl["atomic_numbers"], precision="fp32", max_atoms=s.n, n_members=M)
+    for prec, M in (("fp32", 1), ("fp32", members), ("bf16", 1), ("bf16", members)):
+        pot = P.NNP(atomic_numbers=wl["atomic_numbers"], precision=prec, max_atoms=s.n, n_members=M)
         for m in range(M):
             w = synth.xavier_weights(S, synth.aev_length(S), wl["weight_seed"] + m)
             pot.set_all_weights([[(W.astype(np.float32), b.astype(np.float32)) for W, b in x] for x in w], m)
@@ -483,13 +483,15 @@ def seven_species_rate(members=8, steps=20):
         t0 = time.perf_counter()
         for _ in range(steps):
             pot.eval(pos, Z, box)
-        out[M] = (time.perf_counter() - t0) * 1e3 / steps
+        out[prec, M] = (time.perf_counter() - t0) * 1e3 / steps
         pot.close()
-    return {"workload": wl["name"], "atoms": s.n, "species": S, "aev_length": synth.aev_length(S),
-            "precision": "fp32", "members": members, "steps": steps,
-            "ms_per_step_single": out[1], "ms_per_step_ensemble": out[members],
-            "atom_steps_per_s_single": s.n / (out[1] * 1e-3),
-            "atom_steps_per_s_ensemble": s.n / (out[members] * 1e-3)}
+    res = {"workload": wl["name"], "atoms": s.n, "species": S, "aev_length": synth.aev_length(S),
+           "members": members, "steps": steps}
+    for prec in ("fp32", "bf16"):
+        res[prec] = {"ms_per_step_single": out[prec, 1], "ms_per_step_ensemble": out[prec, members],
+                     "atom_steps_per_s_single": s.n / (out[prec, 1] * 1e-3),
+                     "atom_steps_per_s_ensemble": s.n / (out[prec, members] * 1e-3)}
+    return res
 
 
 def oracle_sample(wl, w, seconds=20.0, seed=0):

@@ -164,16 +164,18 @@ __host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
 // D[128 x N] = A[128 x K] B[N x K]^T.  One MMA covers 32 bytes of K (16 BF16
 // or 32 E4M3 values), so both types advance 32 bytes per MMA inside a
 // 128-byte swizzle row and one slab per four MMAs.
+// acc0 = 1: the first MMA adds to D as well (a later K chunk of one product).
 template <bool F8>
-__device__ __forceinline__ void issue_gemm(uint32_t d_tmem, const uint8_t* A, const uint8_t* B, int N, int K) {
+__device__ __forceinline__ void issue_gemm(uint32_t d_tmem, const uint8_t* A, const uint8_t* B, int N, int K,
+                                           uint32_t acc0 = 0u) {
   const uint32_t idesc = F8 ? idesc_e4m3(kTM, N) : idesc_bf16(kTM, N);
   const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
   const int nk = K / (F8 ? 32 : 16);
   for (int k = 0; k < nk; ++k) {
     const uint32_t a = a0 + (uint32_t)(k >> 2) * kSlab + (uint32_t)(k & 3) * 32;
     const uint32_t b = b0 + (uint32_t)(k >> 2) * (uint32_t)(N * 128) + (uint32_t)(k & 3) * 32;
-    if (F8) mma_e4m3(d_tmem, sw128_desc(a), sw128_desc(b), idesc, k > 0 ? 1u : 0u);
-    else mma_bf16(d_tmem, sw128_desc(a), sw128_desc(b), idesc, k > 0 ? 1u : 0u);
+    if (F8) mma_e4m3(d_tmem, sw128_desc(a), sw128_desc(b), idesc, (k > 0 || acc0) ? 1u : 0u);
+    else mma_bf16(d_tmem, sw128_desc(a), sw128_desc(b), idesc, (k > 0 || acc0) ? 1u : 0u);
   }
 }
 
@@ -641,6 +643,362 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(const EvalIO* __restri
 }
 
 // ---------------------------------------------------------------------------
+// Wide descriptors (three or more species, D > 128), BF16: the same network
+// and epilogues, with the two products that involve D split into pieces that
+// fit shared and tensor memory.
+//
+// * Layer 1, z1 = G W1: K in chunks of two slabs (128 features) through two
+//   stages, stage 0 = (bufA, wbuf[0]) and stage 1 = (bufC, wbuf[1]); each
+//   chunk's G slabs and W1^T slabs arrive on one barrier, and a stage is
+//   reloaded once the MMAs that read it have completed (their own barrier,
+//   bars 5 and 6, waited by thread 0 only).
+// * dE/dG = g1 W1^T: output columns in blocks of 128.  A block's weights are
+//   the matching 128 rows of each of the three K slabs of the backward W1
+//   image (three bulk copies); blocks alternate between wbuf[1] / wbuf[0] and
+//   between TMEM columns [384,512) / [256,384), and the next block's MMA runs
+//   under this block's epilogue.  Blocks complete on bars 7 and 8, which every
+//   thread waits on in turn.
+// The G tile is not fetched ahead of the tile, so layer 1 starts each tile
+// with the latency of its first chunk.
+// switch cases over the species counts with a wide descriptor (3..8)
+#define NNP_WIDE_CASES(CALL) \
+  case 3: CALL(3); break;    \
+  case 4: CALL(4); break;    \
+  case 5: CALL(5); break;    \
+  case 6: CALL(6); break;    \
+  case 7: CALL(7); break;    \
+  default: CALL(8); break;
+constexpr int kWideKC = 2;    // slabs per layer-1 chunk
+constexpr int kWideNC = 128;  // dE/dG columns per block
+
+template <int D>
+__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __restrict__ io, DescParams P,
+                                                       Workspace ws, MlpTcWeights Wt, MlpF32Weights Wf,
+                                                       int acc) {
+  constexpr int kBufA = kWideKC * kSlab;        // G chunk (stage 0), later g2
+  constexpr int kBufB = slabs_of(kH1) * kSlab;  // h1, later g1
+  constexpr int kBufC = slabs_of(kH2) * kSlab;  // G chunk (stage 1), h2, later g3
+  constexpr int kWBuf = 48 * 1024;
+  constexpr int kSl = slabs_of(D);                          // slabs of G and of W1^T
+  constexpr int kNC1 = (kSl + kWideKC - 1) / kWideKC;       // layer-1 chunks
+  constexpr int kNCB = (D + kWideNC - 1) / kWideNC;         // dE/dG blocks
+  static_assert(D % 16 == 0 && D > kH2, "wide descriptor");
+  static_assert(kBufA >= slabs_of(kH2) * kSlab && kBufC >= kWideKC * kSlab, "stage buffers");
+  static_assert(kWideKC * kH1 * 128 <= kWBuf && slabs_of(kH1) * kWideNC * 128 <= kWBuf, "weight buffers");
+  constexpr int kNB = kH1 + kH2 + kH3 + kH3 + 1;  // b1 b2 b3 w4 b4
+
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  uint8_t* bufA = sm;
+  uint8_t* bufB = bufA + kBufA;
+  uint8_t* bufC = bufB + kBufB;
+  uint8_t* wbuf[2] = {bufC + kBufC, bufC + kBufC + kWBuf};
+  // [0,1] stage / weight copies, [3] MMAs, [4] layer 1 done, [5,6] layer-1
+  // stage MMAs, [7,8] dE/dG blocks, [9] drain on abort ([2] unused)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wbuf[1] + kWBuf);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 10);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  float* sE = reinterpret_cast<float*>(abort_flag + 1);  // [kG][kTM] partial energies
+  float* sb = sE + kG * kTM;                             // [kNB] biases and w4 of the tile's species
+  float* sb1 = sb;
+  float* sb2 = sb1 + kH1;
+  float* sb3 = sb2 + kH2;
+  float* sw4 = sb3 + kH3;
+  float* sb4 = sw4 + kH3;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quarter = warp & 3, h = warp >> 2;
+  const int r = quarter * 32 + lane;
+  const float al = P.celu_alpha, kexp = 1.4426950408889634f / P.celu_alpha;
+  const int rows = ws.seg[P.S];
+  const int ntiles = rows / kTM;
+
+  if (tid == 0) {
+    for (int i = 0; i < 10; ++i) mbar_init(&bars[i], 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t lb = (uint32_t)(quarter * 32) << 16;
+  const uint32_t tz1 = tmem + lb + 0, tz2 = tmem + lb + 160, tz3 = tmem + lb + 288, tg2 = tmem + lb + 384,
+                 tg1 = tmem + lb + 160;
+  const uint32_t mz1 = tmem + 0, mz2 = tmem + 160, mz3 = tmem + 288, mg2 = tmem + 384, mg1 = tmem + 160;
+  auto dg_col = [](int q) -> uint32_t { return q ? 256u : 384u; };  // TMEM columns of even / odd dE/dG blocks
+
+  uint32_t ph[4] = {0, 0, 0, 0};
+  bool pend[4] = {false, false, false, false};
+  uint32_t ph56[2] = {0, 0}, ph78[2] = {0, 0}, ph4 = 0;
+  bool pend4 = false;
+
+  auto timeout = [&]() {
+    *abort_flag = 1;
+    atomicOr(&ws.flags[kFlagTimeout], 1);
+  };
+  auto load_w = [&](int sp, int which, int b) {  // a whole matrix (layers 2, 3 and backward 3, 2)
+    constexpr int NWt[6] = {kH1, kH2, kH3, kH2, kH1, D};
+    constexpr int KWt[6] = {D, kH1, kH2, kH3, kH2, kH1};
+    const int bytes = mat_bytes(NWt[which], KWt[which]);
+    mbar_expect_tx(&bars[b], (uint32_t)bytes);
+    bulk_g2s(wbuf[b], Wt.m[sp][which], (uint32_t)bytes, &bars[b]);
+    pend[b] = true;
+  };
+  auto load_chunk = [&](int t, int sp, int c) {  // layer-1 chunk c into stage c & 1
+    const int b = c & 1, s0 = c * kWideKC, ns = min(kWideKC, kSl - s0);
+    const uint32_t gb = (uint32_t)(ns * kSlab), wbytes = (uint32_t)(ns * kH1 * 128);
+    mbar_expect_tx(&bars[b], gb + wbytes);
+    bulk_g2s(b ? bufC : bufA, reinterpret_cast<const uint8_t*>(ws.Gh) + (size_t)t * gh_tile_bytes(D) +
+                                  (size_t)s0 * kSlab, gb, &bars[b]);
+    bulk_g2s(wbuf[b], Wt.m[sp][0] + (size_t)s0 * kH1 * 128, wbytes, &bars[b]);
+    pend[b] = true;
+  };
+  auto load_block = [&](int sp, int cb, int b) {  // dE/dG block cb's W1 rows into wbuf[b]
+    const int n0 = cb * kWideNC, nc = min(kWideNC, D - n0);
+    const uint32_t bytes = (uint32_t)(nc * 128);
+    mbar_expect_tx(&bars[b], (uint32_t)slabs_of(kH1) * bytes);
+    for (int k = 0; k < slabs_of(kH1); ++k)
+      bulk_g2s(wbuf[b] + (size_t)k * bytes, Wt.m[sp][5] + (size_t)k * D * 128 + (size_t)n0 * 128, bytes, &bars[b]);
+    pend[b] = true;
+  };
+  auto commit = [&]() {
+    mma_commit(&bars[3]);
+    pend[3] = true;
+  };
+  auto wait0 = [&](int i) {  // thread 0: copies into buffer i have landed
+    if (!pend[i]) return;
+    if (mbar_wait(&bars[i], ph[i])) {
+      ph[i] ^= 1u;
+      pend[i] = false;
+    } else {
+      timeout();
+    }
+  };
+  auto phase = [&](int i, int j) -> bool {
+    tmem_wait_st();
+    fence_proxy_async();
+    tc_fence_before();
+    if (tid == 0) {
+      if (i >= 0) wait0(i);
+      if (j >= 0) wait0(j);
+    }
+    __syncthreads();
+    return *abort_flag == 0;
+  };
+  auto wait_bar = [&](uint64_t* bar, uint32_t& p) {  // every thread: MMAs committed to bar
+    if (mbar_wait(bar, p)) p ^= 1u;
+    else timeout();
+    tc_fence_after();
+  };
+  auto wait_mma = [&]() {
+    wait_bar(&bars[3], ph[3]);
+    if (tid == 0) pend[3] = false;
+  };
+
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int row0 = tile * kTM;
+    const int sp = pos4_species(ws.pos4[row0]);
+    const int row = row0 + r;
+    const int my_atom = ws.row_atom[row];
+    const int my_sys = ws.row_info[row];
+    for (int i = tid; i < kNB; i += blockDim.x) {
+      float v;
+      if (i < kH1) v = Wf.b[sp][0][i];
+      else if (i < kH1 + kH2) v = Wf.b[sp][1][i - kH1];
+      else if (i < kH1 + kH2 + kH3) v = Wf.b[sp][2][i - kH1 - kH2];
+      else if (i < kH1 + kH2 + 2 * kH3) v = Wf.W[sp][3][i - kH1 - kH2 - kH3];
+      else v = Wf.b[sp][3][0];
+      sb[i] = v;
+    }
+    if (!phase(-1, -1)) break;  // biases published; every buffer of the last tile is free
+    // ---------------- layer 1: z1 = G W1, K in chunks through two stages
+    if (tid == 0) {
+      load_chunk(tile, sp, 0);
+      if (kNC1 > 1) load_chunk(tile, sp, 1);
+      for (int c = 0; c < kNC1 && *abort_flag == 0; ++c) {
+        const int b = c & 1;
+        wait0(b);
+        if (*abort_flag) break;
+        tc_fence_after();
+        const int kc = min(kWideKC * 64, D - c * kWideKC * 64);
+        issue_gemm<false>(mz1, b ? bufC : bufA, wbuf[b], kH1, kc, c > 0 ? 1u : 0u);
+        if (c + 2 < kNC1) mma_commit(&bars[5 + b]);  // stage b is reloaded once these MMAs are done
+        if (c >= 1 && c + 1 < kNC1) {                 // chunk c - 1 has been read: reload its stage
+          if (mbar_wait(&bars[5 + (b ^ 1)], ph56[b ^ 1])) ph56[b ^ 1] ^= 1u;
+          else timeout();
+          if (*abort_flag == 0) load_chunk(tile, sp, c + 1);
+        }
+      }
+      mma_commit(&bars[4]);
+      pend4 = true;
+    }
+    wait_bar(&bars[4], ph4);
+    if (tid == 0) {
+      pend4 = false;
+      if (*abort_flag == 0) {
+        load_w(sp, 1, 1);  // W2^T -> wbuf[1]
+        load_w(sp, 2, 0);  // W3^T -> wbuf[0]
+      }
+    }
+    for_chunks<kH1>(tz1, h, [&](int c0, float (&v)[16]) {
+      float d[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float z = v[j] + sb1[c0 + j];
+        const float ez = ex2f(z * kexp);
+        v[j] = z > 0.f ? z : al * (ez - 1.f);
+        d[j] = z > 0.f ? 1.f : ez;
+      }
+      tmem_st16(tz1 + c0, d);
+      store_row16(bufB, r, c0, v);
+    });
+    // ---------------- layer 2: z2 = h1 W2
+    if (!phase(1, -1)) break;
+    if (tid == 0) {
+      tc_fence_after();
+      issue_gemm<false>(mz2, bufB, wbuf[1], kH2, kH1);
+      commit();
+    }
+    wait_mma();
+    for_chunks<kH2>(tz2, h, [&](int c0, float (&v)[16]) {
+      float d[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float z = v[j] + sb2[c0 + j];
+        const float ez = ex2f(z * kexp);
+        v[j] = z > 0.f ? z : al * (ez - 1.f);
+        d[j] = z > 0.f ? 1.f : ez;
+      }
+      tmem_st16(tz2 + c0, d);
+      store_row16(bufC, r, c0, v);
+    });
+    // ---------------- layer 3: z3 = h2 W3; energy and g3 = w4 CELU'(z3)
+    if (!phase(0, -1)) break;
+    if (tid == 0) {
+      load_w(sp, 3, 1);  // W3 (backward) -> wbuf[1]
+      tc_fence_after();
+      issue_gemm<false>(mz3, bufC, wbuf[0], kH3, kH2);
+      commit();
+    }
+    wait_mma();
+    {
+      float e = 0.f;
+      for_chunks<kH3>(tz3, h, [&](int c0, float (&v)[16]) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float z = v[j] + sb3[c0 + j];
+          const float ww = sw4[c0 + j];
+          const float ez = ex2f(z * kexp);
+          e = fmaf(z > 0.f ? z : al * (ez - 1.f), ww, e);
+          v[j] = ww * (z > 0.f ? 1.f : ez);
+        }
+        store_row16(bufC, r, c0, v);
+      });
+      sE[h * kTM + r] = e;
+    }
+    // ---------------- backward 3: g2' = g3 W3^T
+    if (!phase(1, -1)) break;
+    if (tid == 0) {
+      load_w(sp, 4, 0);  // W2 (backward) -> wbuf[0]
+      tc_fence_after();
+      issue_gemm<false>(mg2, bufC, wbuf[1], kH2, kH3);
+      commit();
+    }
+    if (h == 0) {
+      float e = *sb4;
+#pragma unroll
+      for (int g = 0; g < kG; ++g) e += sE[g * kTM + r];
+      const bool valid = my_atom >= 0;
+      const float ev = valid ? e : 0.f;
+      ws.Ei[row] = acc ? ws.Ei[row] + ev : ev;
+      tile_energy_sums(ev, valid, my_sys, lane, io->energies);
+    }
+    wait_mma();
+    for_chunks2<kH2>(tg2, tz2, h, [&](int c0, float (&g)[16], float (&d)[16]) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) g[j] *= d[j];
+      store_row16(bufA, r, c0, g);
+    });
+    // ---------------- backward 2: g1' = g2 W2^T
+    if (!phase(0, -1)) break;
+    if (tid == 0) {
+      load_block(sp, 0, 1);  // dE/dG block 0 -> wbuf[1]
+      tc_fence_after();
+      issue_gemm<false>(mg1, bufA, wbuf[0], kH1, kH2);
+      commit();
+    }
+    wait_mma();
+    if (tid == 0 && kNCB > 1) load_block(sp, 1, 0);  // wbuf[0] is free: block 1
+    for_chunks2<kH1>(tg1, tz1, h, [&](int c0, float (&g)[16], float (&d)[16]) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) g[j] *= d[j];
+      store_row16(bufB, r, c0, g);
+    });
+    // ---------------- backward 1: dE/dG = g1 W1^T in column blocks
+    if (!phase(1, -1)) break;
+    if (tid == 0) {
+      tc_fence_after();
+      issue_gemm<false>(tmem + dg_col(0), bufB, wbuf[1], min(kWideNC, D), kH1);
+      mma_commit(&bars[7]);
+    }
+    bool ok = true;
+    for (int cb = 0; cb < kNCB; ++cb) {
+      const int q = cb & 1, wb = q ? 0 : 1;  // block cb: weights in wbuf[wb], accumulator dg_col(q)
+      const int n0 = cb * kWideNC, nc = min(kWideNC, D - n0);
+      if (tid == 0 && cb + 1 < kNCB) {  // the next block's MMA runs under this block's epilogue
+        wait0(wb ^ 1);
+        if (*abort_flag == 0) {
+          tc_fence_after();
+          issue_gemm<false>(tmem + dg_col(q ^ 1), bufB, wbuf[wb ^ 1], min(kWideNC, D - n0 - kWideNC), kH1);
+        }
+        mma_commit(&bars[7 + (q ^ 1)]);
+      }
+      wait_bar(&bars[7 + q], ph78[q]);
+      if (tid == 0 && cb + 2 < kNCB && *abort_flag == 0) load_block(sp, cb + 2, wb);
+      float* out = ws.dEdG + (size_t)row * D + n0;
+      const uint32_t tb = tmem + lb + dg_col(q);
+      for (int c = h; c < nc / 16; c += kG) {
+        uint32_t a[16];
+        tmem_ld16_nowait(tb + c * 16, a);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; j += 4) {
+          float4* o = reinterpret_cast<float4*>(out + c * 16 + j);
+          float4 x = make_float4(__uint_as_float(a[j]), __uint_as_float(a[j + 1]), __uint_as_float(a[j + 2]),
+                                 __uint_as_float(a[j + 3]));
+          if (acc) {
+            const float4 y = *o;
+            x.x += y.x;
+            x.y += y.y;
+            x.z += y.z;
+            x.w += y.w;
+          }
+          *o = x;
+        }
+      }
+      if (!phase(-1, -1)) {  // this block's TMEM columns have been read before block cb + 2 reuses them
+        ok = false;
+        break;
+      }
+    }
+    if (!ok) break;
+  }
+  // on abort: let this CTA's copies and MMAs land (bounded) before freeing TMEM
+  if (tid == 0 && *abort_flag) {
+    for (int i = 0; i < 2; ++i)
+      if (pend[i]) mbar_wait(&bars[i], ph[i]);
+    mma_commit(&bars[9]);
+    mbar_wait(&bars[9], 0);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// ---------------------------------------------------------------------------
 // Self-test of the bounded waits: a barrier that nothing completes.  Thread 0
 // waits on it with the network kernel's own wait, gives up after limit_ns,
 // raises the timeout flag and returns; the context stays usable.
@@ -771,13 +1129,24 @@ cudaError_t set_smem(size_t sm) {
   return cudaFuncSetAttribute(k_mlp_tc<D, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
 }
 
+size_t smem_bytes_wide() {
+  return 1024 + (size_t)kWideKC * kSlab + slabs_of(kH1) * kSlab + slabs_of(kH2) * kSlab + 2 * 48 * 1024 +
+         10 * 8 + 8 + kG * kTM * 4 + (kH1 + kH2 + 2 * kH3 + 1) * 4 + 64;
+}
+
+template <int S>
+cudaError_t set_smem_wide() {
+  return cudaFuncSetAttribute(k_mlp_tc_wide<desc_len(S)>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_bytes_wide());
+}
+
 }  // namespace
 
 int mlp_tc_init(nnp_ctx* ctx) {
   const bool f8 = ctx->cfg.precision == NNP_FP8;
   const int D = ctx->P.D;
-  if (!f8 && D != 128 && D != 48)
-    return ctx->fail(NNP_ERR_UNSUPPORTED, "the BF16 tensor-core network supports 1 or 2 species (D = 48, 128)");
+  if (!f8 && D != 128 && D != 48 && D != desc_len(ctx->P.S))
+    return ctx->fail(NNP_ERR_UNSUPPORTED, "the BF16 tensor-core network takes the standard descriptor");
   if (f8 && D != 128)
     return ctx->fail(NNP_ERR_UNSUPPORTED, "the FP8 tensor-core network supports 2 species (D = 128)");
   TcState* st = new TcState();
@@ -819,7 +1188,13 @@ int mlp_tc_init(nnp_ctx* ctx) {
   cudaMemset(ctx->b_q8, 0, sizeof(int) * 8 * kMaxS);
   const size_t sm = smem_bytes(D);
   if (f8) e = set_smem<128, true>(sm);
-  else e = (D == 128) ? set_smem<128, false>(sm) : set_smem<48, false>(sm);
+  else if (D == 128) e = set_smem<128, false>(sm);
+  else if (D == 48) e = set_smem<48, false>(sm);
+  else {
+#define WSM(s) e = set_smem_wide<s>()
+    switch (ctx->P.S) { NNP_WIDE_CASES(WSM) }
+#undef WSM
+  }
   if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaFuncSetAttribute(k_mlp_tc)");
   return NNP_OK;
 }
@@ -889,8 +1264,14 @@ int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t stream, long long rows, int member,
     k_mlp_tc<128, true><<<grid, kTcThreads, sm, stream>>>(ctx->d_io, ctx->P, w, tw, fw, acc);
   else if (D == 128)
     k_mlp_tc<128, false><<<grid, kTcThreads, sm, stream>>>(ctx->d_io, ctx->P, w, tw, fw, acc);
-  else
+  else if (D == 48)
     k_mlp_tc<48, false><<<grid, kTcThreads, sm, stream>>>(ctx->d_io, ctx->P, w, tw, fw, acc);
+  else {
+    const size_t smw = smem_bytes_wide();
+#define WIDE(s) k_mlp_tc_wide<desc_len(s)><<<grid, kTcThreads, smw, stream>>>(ctx->d_io, ctx->P, w, tw, fw, acc)
+    switch (ctx->P.S) { NNP_WIDE_CASES(WIDE) }
+#undef WIDE
+  }
   return NNP_OK;
 }
 

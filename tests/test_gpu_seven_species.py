@@ -1,5 +1,5 @@
 """GPU tests at seven species (H, C, N, O, F, S, Cl; D = 1008: the element
-set of the ANI-2x model), FP32 form.
+set of the ANI-2x model), and of the wide-descriptor tensor-core network.
 
 * a small seven-element box and the full 6,047-atom workload against the FP64
   oracle within the FP32 bounds;
@@ -8,8 +8,11 @@ set of the ANI-2x model), FP32 form.
   zero);
 * an ensemble of two seven-species networks, the batched form and the
   caller's pair list against the oracle;
-* the tensor-core forms, force matching and the no-allocation entry point
-  refuse more species than they take.
+* BF16 (tcgen05 network with layer 1 streamed in K chunks and dE/dG in
+  column blocks) at three, four and seven species against the oracle within
+  the BF16 form's bounds, and against the FP32 form on the 6,047-atom box;
+* the FP8 form, force matching and the no-allocation entry point refuse more
+  species than they take.
 """
 import numpy as np
 import pytest
@@ -20,6 +23,9 @@ from common import E_REL_TOL, F_ABS_TOL, box9, energy_error, weights32
 pytestmark = pytest.mark.gpu
 
 Z7 = (1, 6, 7, 8, 9, 16, 17)
+E_BF16 = 1e-2
+F_MAX_BF16 = 0.1
+F_RMS_BF16 = 0.02
 
 
 @pytest.fixture(scope="module")
@@ -119,12 +125,56 @@ def test_seven_species_ensemble_batch_pairs(P, oracle_mod):
     assert np.abs(Fp - Fr).max() <= F_ABS_TOL
 
 
+@pytest.mark.parametrize("Zs", [(1, 6, 8), (1, 6, 7, 8), Z7])
+def test_bf16_wide_descriptor(P, oracle_mod, Zs):
+    S = len(Zs)
+    D = 16 * S + 32 * S * (S + 1) // 2
+    s = synth.hcno_box(751 + S, L=16.0, n_cluster_atoms=160, max_waters=60,
+                       elements=np.array(Zs, dtype=np.int32), probs=np.full(S, 1.0 / S))
+    w = weights32(S, D, 752 + S, 753 + S)
+    pot = _pot(P, w, Zs=Zs, precision="bf16")
+    E, F = pot.eval(s.pos, s.Z, box9(s.box))
+    p = oracle_mod.Params(atomic_numbers=Zs)
+    Er, Eir, Fr, _ = oracle_mod.energy_forces(oracle_mod.Model(p, w), s.pos, p.species_of(s.Z), s.box)
+    dF = F - Fr
+    print(f"bf16 {S} species (D = {D}), {s.n} atoms: rel E err {energy_error(E, Er, Eir):.2e},"
+          f" max|dF| {np.abs(dF).max():.3e}, rms dF {np.sqrt((dF ** 2).mean()):.3e}")
+    assert energy_error(E, Er, Eir) <= E_BF16
+    assert np.abs(dF).max() <= F_MAX_BF16
+    assert np.sqrt((dF ** 2).mean()) <= F_RMS_BF16
+    Ei = pot.atom_energies(s.n)
+    assert abs(Ei.sum() - E) <= 1e-6 * np.abs(Ei).sum()
+
+
+def test_bf16_seven_species_workload_and_ensemble(P):
+    """HCNOFSCl-40A: the BF16 form against the FP32 form (one network and a
+    two-member ensemble, the BF16 ensemble against the FP32 ensemble)."""
+    wl = synth.workload(6)
+    s = wl["systems"][0]
+    mem = [weights32(7, 1008, wl["weight_seed"] + m) for m in range(2)]
+    out = {}
+    for prec in ("fp32", "bf16"):
+        for M in (1, 2):
+            pot = P.NNP(atomic_numbers=Z7, precision=prec, n_members=M, max_atoms=s.n)
+            pot.set_member_weights([_f32(w) for w in mem[:M]])
+            E, F = pot.eval(s.pos, s.Z, box9(s.box))
+            out[prec, M] = (E, F, pot.atom_energies(s.n))
+    for M in (1, 2):
+        E32, F32, Ei32 = out["fp32", M]
+        E16, F16, _ = out["bf16", M]
+        dF = F16 - F32
+        print(f"HCNOFSCl-40A M={M}: bf16 vs fp32 rel E {abs(E16 - E32) / np.abs(Ei32).sum():.2e},"
+              f" max|dF| {np.abs(dF).max():.3e}, rms dF {np.sqrt((dF ** 2).mean()):.3e}")
+        assert abs(E16 - E32) <= E_BF16 * np.abs(Ei32).sum()
+        assert np.abs(dF).max() <= F_MAX_BF16
+        assert np.sqrt((dF ** 2).mean()) <= F_RMS_BF16
+
+
 def test_seven_species_refusals(P):
     w = weights32(7, 1008, 741)
-    for prec in ("bf16", "fp8"):
-        with pytest.raises(P.NNPError) as e:
-            P.NNP(atomic_numbers=Z7, precision=prec)
-        assert e.value.code == 3
+    with pytest.raises(P.NNPError) as e:
+        P.NNP(atomic_numbers=Z7, precision="fp8")
+    assert e.value.code == 3
     pot = _pot(P, w)
     s = _small_box(742)
     E, _ = pot.eval(s.pos, s.Z, box9(s.box))
