@@ -575,6 +575,9 @@ def main():
     ap.add_argument("--workload", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
+    ap.add_argument("--extras", type=int, default=1,
+                    help="0: leave out the auxiliary measurements after the JSON line's main step "
+                         "(NVE, ML/MM, pair list, ensembles, seven species), e.g. under a profiler")
     args = ap.parse_args()
     args.compare = args.compare.split(",")
     args.warmup = max(args.warmup, 3)
@@ -644,7 +647,7 @@ def main():
         "cpu_baseline": ({"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
                           "sample": cpu_desc} if cpu_v is not None else None),
     }
-    if args.workload == 3:  # the paper reports MD throughput in ns/day
+    if args.workload == 3 and args.extras:  # the paper reports MD throughput in ns/day
         line["nve"] = nve_rate(args.precision)
         line["mlmm"] = mlmm_rate(args.precision)
         line["pairs"] = pairs_rate(args.precision)
