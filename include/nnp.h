@@ -172,7 +172,8 @@ int nnp_set_member_weights(nnp_ctx *ctx, int32_t member, int32_t species,
  *          system (no periodic images);
  *   energy 1 double (eV), forces n x 3 doubles (eV/Angstrom); either may be
  *          NULL to skip it.
- * Synchronous: returns after the results are written. */
+ * Synchronous: returns after the results are written.  After an error
+ * return the contents of energy and forces are unspecified. */
 int nnp_eval(nnp_ctx *ctx, int64_t n, const double *pos, const int32_t *Z,
              const double *box, double *energy, double *forces);
 

@@ -482,12 +482,16 @@ int nnp_ctx::evaluate(int B, const int64_t* offsets, const double* pos, const in
     last_n = n; last_B = B; last_rows = rows; has_state = true;
     CK(cudaMemcpyAsync(h_flags, b_flags, sizeof(int) * kNumFlags, cudaMemcpyDeviceToHost, stream));
     if (!sync) return NNP_OK;
+    // results to host buffers on the stream, so that one synchronisation
+    // covers them; if the flags ask for a regrow they are overwritten below
+    if (forces && !F_dev)
+      CK(cudaMemcpyAsync(forces, b_F_stage, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, stream));
+    if (energies && !E_dev)
+      CK(cudaMemcpyAsync(energies, b_E_stage, sizeof(double) * B, cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
     int st = check_flags();
     if (st == -1) continue;  // lists regrown: evaluate again
     if (st) return st;
-    if (forces && !F_dev) CK(cudaMemcpy(forces, b_F_stage, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost));
-    if (energies && !E_dev) CK(cudaMemcpy(energies, b_E_stage, sizeof(double) * B, cudaMemcpyDeviceToHost));
     return NNP_OK;
   }
   return fail(NNP_ERR_CAPACITY, "neighbour lists still overflow after regrowing");
