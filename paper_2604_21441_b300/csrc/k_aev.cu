@@ -439,12 +439,6 @@ __global__ void __launch_bounds__(256, 3) k_aev_fwd(const SysDesc* __restrict__ 
 
 namespace {
 
-// acc.xyz += (x, y, z): one vector reduction in global memory (L2)
-__device__ __forceinline__ void red_add_f3(float4* acc, float x, float y, float z) {
-  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(acc), "f"(x), "f"(y), "f"(z), "f"(0.f)
-               : "memory");
-}
-
 // One species-pair block of a row's angular pairs (per-warp table in shared
 // memory).  Pair tl of the block: q = tl / K (multiply by mg), u = tl - q K,
 // v = u + q + vq wrapped into [0, W); diagonal blocks of even n end with
@@ -484,6 +478,7 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
   extern __shared__ float4 sm4[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int ca = ws.cap_a, cr = ws.cap_r;
+  double* const Fout = io->forces;  // FP64 forces in input order, zeroed by k_bin
   float4* sh = sm4 + (size_t)wib * bwd_warp_f4(ca, cr, S);
   float4* geo = sh + 27;
   float4* aux = geo + ca;
@@ -786,32 +781,24 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
     }
     __syncwarp();
 
-    // ---------------- (4) one vector reduction per neighbour slot
-    for (int k = lane; k < ntot; k += 32)
-      red_add_f3(ws.facc + origs[k], fsl[3 * k], fsl[3 * k + 1], fsl[3 * k + 2]);
+    // ---------------- (4) FP64 reductions of the slots' forces: lane t takes
+    // component t % 3 of slot t / 3, so the lanes of one instruction cover
+    // about eleven atoms' contiguous x, y, z (few L2 sectors per instruction)
+    for (int t = lane; t < 3 * ntot; t += 32) {
+      const int k = t / 3;
+      atomicAdd(Fout + 3 * (size_t)origs[k] + (t - 3 * k), (double)fsl[t]);
+    }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
       fix += __shfl_xor_sync(FM, fix, o);
       fiy += __shfl_xor_sync(FM, fiy, o);
       fiz += __shfl_xor_sync(FM, fiz, o);
     }
-    if (lane == 0) red_add_f3(ws.facc + pos4_orig(pi), fix, fiy, fiz);
+    if (lane < 3) atomicAdd(Fout + 3 * (size_t)pos4_orig(pi) + lane, (double)(lane == 0 ? fix : (lane == 1 ? fiy : fiz)));
   }
 }
 
 // FP32 accumulators -> the caller's FP64 forces (input order).
-__global__ void k_forces_out(const EvalIO* __restrict__ io, Workspace ws) {
-  const long long n = io->n_atoms;
-  double* F = io->forces;
-  for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < n;
-       a += (long long)gridDim.x * blockDim.x) {
-    const float4 f = ws.facc[a];
-    F[3 * a] = (double)f.x;
-    F[3 * a + 1] = (double)f.y;
-    F[3 * a + 2] = (double)f.z;
-  }
-}
-
 // --------------------------------------------------------------------------
 // directional derivative: dG_i = sum_j (dG_i / dr_j) . v_j (force-matching
 // gradients).  Same mapping as the forward; v is per atom in input order.
@@ -1062,9 +1049,6 @@ void launch_aev_bwd(long long rows, int nsm, cudaStream_t st, const EvalIO* io, 
 #define BWD(s) z5 ? bwd_t<s, 5>(rows, nsm, st, io, sys, P, ws) : bwd_t<s, -1>(rows, nsm, st, io, sys, P, ws)
   switch (P.S) { NNP_SPECIES_CASES(BWD) }
 #undef BWD
-  long long g = (rows + 255) / 256;
-  if (g > (long long)nsm * 4) g = (long long)nsm * 4;
-  k_forces_out<<<(int)(g < 1 ? 1 : g), 256, 0, st>>>(io, ws);
 }
 
 template <class K>

@@ -85,7 +85,9 @@ __global__ void k_bin(const EvalIO* __restrict__ io, const SysDesc* __restrict__
                                  __int_as_float((int)(((unsigned)a << 3) | (unsigned)s)));
     ws.atom_cell[a] = k[0] | (k[1] << 10) | (k[2] << 20);
     ws.atom_sys[a] = lo;
-    ws.facc[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+    io->forces[3 * a] = 0.0;  // the descriptor backward adds the forces here in FP64
+    io->forces[3 * a + 1] = 0.0;
+    io->forces[3 * a + 2] = 0.0;
   }
 }
 

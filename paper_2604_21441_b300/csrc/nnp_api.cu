@@ -107,7 +107,6 @@ int nnp_ctx::ensure_capacity(long long n, int B, long long bins, long long rows)
   GR(b_Gh, c_Gh, (size_t)rows * ((P.D + 63) / 64 * 64));  // swizzled BF16 tiles
   GR(b_dEdG, c_dEdG, (size_t)rows * P.D);
   GR(b_Ei, c_Ei, (size_t)rows);
-  GR(b_facc, c_facc, (size_t)n);
   GR(b_sys, c_sys, (size_t)B);
   GR(b_pos_stage, c_pos_stage, (size_t)n * 3);
   GR(b_Z_stage, c_Z_stage, (size_t)n);
@@ -141,7 +140,6 @@ Workspace nnp_ctx::workspace() const {
   w.Gh = b_Gh;
   w.dEdG = b_dEdG;
   w.Ei = b_Ei;
-  w.facc = b_facc;
   w.flags = b_flags;
   w.q8 = b_q8;
   w.cap_r = cap_r;
@@ -211,7 +209,7 @@ int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows,
     }
   }
   mark_stage(4, capturing);
-  launch_aev_bwd(rows, nsm, stream, io, sys, P, w, tune.bwd); launches += 2;
+  launch_aev_bwd(rows, nsm, stream, io, sys, P, w, tune.bwd); ++launches;
   mark_stage(5, capturing);
   CK(cudaGetLastError());
   launches_per_eval = launches;

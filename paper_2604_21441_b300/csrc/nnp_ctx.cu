@@ -95,7 +95,7 @@ nnp_ctx::~nnp_ctx() {
   mlp_tc_free(this);
   void* bufs[] = {b_bin_count, b_bin_start, b_bin_len, b_atom_bin, b_atom_slot, b_atom_cell,
                   b_atom_sys, b_atom_off, b_row_atom, b_row_info, b_row_cell, b_pos4, b_cnt_r,
-                  b_cnt_a, b_nbr_r, b_G, b_dEdG, b_Ei, b_facc, b_Gh, b_sys, b_pos_stage,
+                  b_cnt_a, b_nbr_r, b_G, b_dEdG, b_Ei, b_Gh, b_sys, b_pos_stage,
                   b_Z_stage, b_F_stage, b_E_stage, b_seg, b_flags, d_zlut, d_io, b_wf32,
                   fm_z, fm_dz, fm_t, fm_p, fm_v, fm_ref, fm_grad, fm_jobs,
                   mm.pos, mm.F, mm.sub_pos, mm.sub_F, mm.ld, mm.E, mm.Z, mm.sub_Z, mm.idx, mm.mark,
@@ -227,7 +227,7 @@ int nnp_ctx::force_match_grad(const double* v, const double* Fref, double* loss,
   io.energies = b_E_stage;
   *h_io = io;
   CK(cudaMemcpyAsync(d_io, h_io, sizeof(EvalIO), cudaMemcpyHostToDevice, stream));
-  CK(cudaMemsetAsync(b_facc, 0, sizeof(float4) * n, stream));
+  CK(cudaMemsetAsync(b_F_stage, 0, sizeof(double) * 3 * n, stream));
   CK(cudaMemsetAsync(b_E_stage, 0, sizeof(double) * last_B, stream));
   launch_aev_fwd(rows, num_sms, stream, b_sys, P, w, 0);
   const int g_tiles = (int)std::max<long long>(1, std::min<long long>(rows / 64, (long long)num_sms));

@@ -30,8 +30,8 @@ cudaError_t neighbors_set_smem_limits();
 // per_sm: cap on resident blocks per SM of the grid (0 = built-in default)
 void launch_aev_fwd(long long rows, int nsm, cudaStream_t st, const SysDesc* sys, const DescParams& P,
                     const Workspace& ws, int mode /* GMode */, int per_sm = 0);
-// k_aev_bwd, then k_forces_out (two launches): forces accumulate in
-// ws.facc (zeroed by k_bin) and are written to io->forces in FP64
+// k_aev_bwd: forces accumulate in FP64 straight into io->forces (zeroed
+// by k_bin)
 void launch_aev_bwd(long long rows, int nsm, cudaStream_t st, const EvalIO* io, const SysDesc* sys,
                     const DescParams& P, const Workspace& ws, int per_sm = 0);
 cudaError_t aev_set_smem_limits();
@@ -84,8 +84,6 @@ struct nnp_ctx {
   int *b_cnt_r = nullptr, *b_cnt_a = nullptr, *b_nbr_r = nullptr;
   size_t c_nbr_r = 0;
   float *b_G = nullptr, *b_dEdG = nullptr, *b_Ei = nullptr;
-  float4* b_facc = nullptr;
-  size_t c_facc = 0;
   __nv_bfloat16* b_Gh = nullptr;
   size_t c_G = 0, c_Gh = 0, c_dEdG = 0, c_Ei = 0;
   nnp::SysDesc* b_sys = nullptr;

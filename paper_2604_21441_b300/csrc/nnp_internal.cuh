@@ -157,7 +157,6 @@ struct Workspace {
   __nv_bfloat16* Gh;  // [max_rows * D]
   float* dEdG;      // [max_rows * D]
   float* Ei;        // [max_rows]
-  float4* facc;     // [max_atoms] force accumulators in input order (x, y, z, unused)
   int* flags;       // [kNumFlags]
   int* q8;          // FP8 form, [kMaxS * 8] per species: calibrated |max| of G, h1, h2 as
                     // float bits at [0, 3) (raised by atomicMax); the rest unused

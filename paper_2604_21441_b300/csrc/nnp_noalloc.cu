@@ -63,8 +63,7 @@ constexpr size_t o_nbr_r = o_cnt_a + al256(sizeof(int) * kNAMaxRows * kMaxS);
 constexpr size_t o_G = o_nbr_r + al256(sizeof(int) * kNAMaxRows * kNACapR);
 constexpr size_t o_dEdG = o_G + al256(sizeof(float) * kNAMaxRows * kNAMaxD);
 constexpr size_t o_Ei = o_dEdG + al256(sizeof(float) * kNAMaxRows * kNAMaxD);
-constexpr size_t o_facc = o_Ei + al256(sizeof(float) * kNAMaxRows);
-constexpr size_t o_flags = o_facc + al256(sizeof(float4) * kNAMaxAtoms);
+constexpr size_t o_flags = o_Ei + al256(sizeof(float) * kNAMaxRows);
 constexpr size_t o_io = o_flags + al256(sizeof(int) * kNumFlags);
 constexpr size_t o_sys = o_io + al256(sizeof(EvalIO));
 constexpr size_t kScratchBytes = o_sys + al256(sizeof(SysDesc));
@@ -200,7 +199,6 @@ extern "C" int nnp_eval_noalloc(nnp_ctx* ctx, int64_t n, const double* pos, cons
   w.Gh = reinterpret_cast<__nv_bfloat16*>(base + o_G);  // unused: FP32 form writes no BF16 copy
   w.dEdG = reinterpret_cast<float*>(base + o_dEdG);
   w.Ei = reinterpret_cast<float*>(base + o_Ei);
-  w.facc = reinterpret_cast<float4*>(base + o_facc);
   w.flags = reinterpret_cast<int*>(base + o_flags);
   w.cap_r = kNACapR;
   w.cap_a = kNACapA;
