@@ -28,6 +28,11 @@ aev_jvp, force_match       : pinned (finite differences in positions and in
 ensemble_energy_forces     : pinned (equals one wider network with
                              block-diagonal hidden layers and the output layer
                              divided by M; M copies of one network equal it)
+ee_energy_forces           : pinned (one ML atom and one MM charge: the
+                             closed-form Coulomb pair; zero MM charges give
+                             the plain NNP; total charge conserved; the total
+                             force on ML and MM atoms vanishes; finite
+                             differences in ML and MM coordinates)
 mlmm_energy_forces         : pinned (finite differences of the embedded energy
                              in the whole system's coordinates, zero net
                              force, a link placed on its MM atom)
@@ -107,6 +112,7 @@ def lib():
         L.or_aev_jvp.argtypes = [ctypes.POINTER(_Model), ctypes.c_int, dp, ip, dp, dp, dp]
         L.or_force_match.argtypes = [ctypes.POINTER(_Model), ctypes.c_int, dp, ip, dp, dp, dp,
                                      ctypes.POINTER(dp), ctypes.POINTER(dp), dp]
+        L.or_weighted_energy_forces.argtypes = [ctypes.POINTER(_Model), ctypes.c_int, dp, ip, dp, dp, dp, dp, dp]
         L.or_pair_index.restype = ctypes.c_int
         L.or_pair_index.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
         _lib = L
@@ -340,6 +346,64 @@ def ensemble_energy_forces(models, pos, species, box):
         e, ei, f, _ = energy_forces(m, pos, species, box)
         E, Ei, F = E + e, Ei + ei, F + f
     return E / M, Ei / M, F / M
+
+
+def weighted_energy_forces(model: Model, pos, species, box, wt):
+    """E = sum_i wt_i E_i and F = -dE/dr with the weights held fixed
+    (orthorhombic box or None).  Returns E, Ei (unweighted), F."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    species = np.ascontiguousarray(species, dtype=np.int32)
+    wt = np.ascontiguousarray(wt, dtype=np.float64)
+    n = pos.shape[0]
+    bx = None if box is None else np.ascontiguousarray(box, dtype=np.float64)
+    E, Ei, F = np.zeros(1), np.zeros(n), np.zeros((n, 3))
+    lib().or_weighted_energy_forces(model.ref, n, _dp(pos), _ip(species), None if bx is None else _dp(bx),
+                                    _dp(wt), _dp(E), _dp(Ei), _dp(F))
+    return float(E[0]), Ei, F
+
+
+COULOMB_EV_A = 14.3996454784  # e^2 / (4 pi eps0) in eV A
+
+
+def ee_energy_forces(model: Model, charge_model: Model, pos, species, box, mm_pos, mm_q,
+                     total_charge: float = 0.0):
+    """Electrostatic embedding (Methods, the nnpot interface: the model
+    predicts in vacuo charges of the ML atoms, which interact with the MM
+    point charges; the MM atoms receive forces).  Readings:
+
+    * charges: q_i = charge_model's per-element network on the same
+      descriptor, shifted so that they sum to total_charge,
+      q'_i = q_i - (sum_k q_k - Q) / n;
+    * E = E_NNP + E_es, E_es = k_e sum_i sum_J q'_i Q_J / |r_iJ|, over every
+      MM charge J; with a box (edge lengths) r_iJ is the minimum image;
+    * no polarisation term.
+
+    Returns E, F (ML atoms, n x 3), F_mm (MM atoms, m x 3), q' (n)."""
+    pos = np.asarray(pos, dtype=np.float64)
+    mm_pos = np.asarray(mm_pos, dtype=np.float64).reshape(-1, 3)
+    mm_q = np.asarray(mm_q, dtype=np.float64).reshape(-1)
+    n = pos.shape[0]
+    E_nnp, _, F_nnp, _ = energy_forces(model, pos, species, box)
+    _, q_raw, _, _ = energy_forces(charge_model, pos, species, box)
+    q = q_raw - (q_raw.sum() - total_charge) / n
+    V = np.zeros(n)
+    field = np.zeros((n, 3))  # -grad V at the ML atom
+    F_mm = np.zeros_like(mm_pos)
+    for i in range(n):
+        d = mm_pos - pos[i]  # r_J - r_i
+        if box is not None:
+            L = np.asarray(box, dtype=np.float64)
+            d -= L * np.round(d / L)
+        r = np.sqrt((d * d).sum(axis=1))
+        V[i] = COULOMB_EV_A * np.sum(mm_q / r)
+        pair = COULOMB_EV_A * (mm_q / r ** 3)[:, None] * d  # k Q_J (r_J - r_i) / r^3
+        field[i] = -pair.sum(axis=0)
+        F_mm += q[i] * pair
+    E_es = float(np.sum(q * V))
+    # charge dependence: dE_es/dq_raw_i = V_i - mean(V) (neutrality shift)
+    _, _, F_q = weighted_energy_forces(charge_model, pos, species, box, V - V.mean())
+    F = F_nnp + q[:, None] * field + F_q
+    return E_nnp + E_es, F, F_mm, q
 
 
 def mlmm_energy_forces(model: Model, pos, species, box, ml_index, link_ml, link_mm, link_d,

@@ -499,17 +499,29 @@ static long build_pairs(int n, const double *pos, const double *box, double rc,
 }
 
 /* E (sum), Ei (n, may be NULL), F (n x 3), G (n x D, may be NULL).
- * species[i] in [0, S); box: 3 edge lengths (orthorhombic) or NULL. */
+ * species[i] in [0, S); box: 3 edge lengths (orthorhombic) or NULL.
+ * wt (may be NULL = all ones): E = sum_i wt[i] E_i and F = -dE/dr with the
+ * weights held fixed. */
 static int energy_forces_from_pairs(const oracle_model *m, int n, const int *species, long np,
                                     int *pi, int *pj, double *pd, double *E, double *Ei, double *F,
-                                    double *Gout);
+                                    double *Gout, const double *wt);
 
 int or_energy_forces(const oracle_model *m, int n, const double *pos, const int *species,
                      const double *box, double *E, double *Ei, double *F, double *Gout) {
     double rmax = m->rc_r > m->rc_a ? m->rc_r : m->rc_a;
     int *pi, *pj; double *pd;
     long np = build_pairs(n, pos, box, rmax, &pi, &pj, &pd);
-    return energy_forces_from_pairs(m, n, species, np, pi, pj, pd, E, Ei, F, Gout);
+    return energy_forces_from_pairs(m, n, species, np, pi, pj, pd, E, Ei, F, Gout, NULL);
+}
+
+/* As or_energy_forces with fixed per-atom weights: E = sum_i wt[i] E_i,
+ * F = -dE/dr (Ei unweighted). */
+int or_weighted_energy_forces(const oracle_model *m, int n, const double *pos, const int *species,
+                              const double *box, const double *wt, double *E, double *Ei, double *F) {
+    double rmax = m->rc_r > m->rc_a ? m->rc_r : m->rc_a;
+    int *pi, *pj; double *pd;
+    long np = build_pairs(n, pos, box, rmax, &pi, &pj, &pd);
+    return energy_forces_from_pairs(m, n, species, np, pi, pj, pd, E, Ei, F, NULL, wt);
 }
 
 /* As or_energy_forces for a general periodic cell (rows a, b, c; pairs by
@@ -524,7 +536,7 @@ int or_energy_forces_cell(const oracle_model *m, int n, const double *pos, const
         pj = (int *)malloc(sizeof(int) * (size_t)cap);
         pd = (double *)malloc(sizeof(double) * 3 * (size_t)cap);
         long np = or_pairs_brute_cell(n, pos, cell, rmax, cap, pi, pj, pd);
-        if (np <= cap) return energy_forces_from_pairs(m, n, species, np, pi, pj, pd, E, Ei, F, Gout);
+        if (np <= cap) return energy_forces_from_pairs(m, n, species, np, pi, pj, pd, E, Ei, F, Gout, NULL);
         free(pi); free(pj); free(pd);
         cap = np;
     }
@@ -534,7 +546,7 @@ int or_energy_forces_cell(const oracle_model *m, int n, const double *pos, const
  * largest cutoff); frees the pair arrays. */
 static int energy_forces_from_pairs(const oracle_model *m, int n, const int *species, long np,
                                     int *pi, int *pj, double *pd, double *E, double *Ei, double *F,
-                                    double *Gout) {
+                                    double *Gout, const double *wt) {
     int D = or_aev_length(m);
     nbr_csr rad, ang;
     csr_build(&rad, n, np, pi, pj, pd, m->rc_r);
@@ -546,7 +558,10 @@ static int energy_forces_from_pairs(const oracle_model *m, int n, const int *spe
     for (int i = 0; i < n; ++i) {
         double e = or_mlp(m, species[i], G + (size_t)i * D, dG + (size_t)i * D);
         if (Ei) Ei[i] = e;
-        Etot += e;
+        const double w = wt ? wt[i] : 1.0;
+        if (wt)
+            for (int k = 0; k < D; ++k) dG[(size_t)i * D + k] *= w;
+        Etot += w * e;
     }
     *E = Etot;
     /* dE/dr by the chain rule through the AEV; F = -dE/dr */
