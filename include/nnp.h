@@ -75,6 +75,8 @@ typedef enum {
 #define NNP_FLAG_NO_GRAPH 0x1u      /* launch kernels directly instead of a CUDA graph */
 #define NNP_FLAG_NONDETERMINISTIC_BINS 0x2u /* skip the per-cell ordering pass */
 #define NNP_FLAG_STAGE_EVENTS 0x4u  /* record CUDA events between pipeline stages */
+#define NNP_FLAG_CHARGES 0x10u      /* reserve a charge network (nnp_set_charge_weights) for
+                                       the electrostatic embedding, nnp_eval_ee; not FP8 */
 #define NNP_FLAG_AUTOTUNE 0x8u      /* pick launch shapes by timing them (cached per shape bucket;
                                        file cache: environment NNP_AUTOTUNE_CACHE) */
 
@@ -298,6 +300,35 @@ int nnp_eval_mlmm(nnp_ctx *ctx, int64_t n_total, const double *pos, const int32_
                   const double *box, int64_t n_ml, const int64_t *ml_index, int32_t n_link,
                   const int64_t *link_ml, const int64_t *link_mm, const double *link_d,
                   int32_t link_Z, double *energy, double *forces);
+
+/* Charge network of species s for the electrostatic embedding (context
+ * created with NNP_FLAG_CHARGES; else NNP_ERR_UNSUPPORTED): a per-element
+ * network of the energy network's shape on the same descriptor whose output
+ * is the atom's in vacuo charge (e).  Layout and ownership as in
+ * nnp_set_weights; not averaged over an ensemble. */
+int nnp_set_charge_weights(nnp_ctx *ctx, int32_t species, const float *const W[4],
+                           const float *const b[4]);
+
+/* Electrostatic embedding (Methods, the nnpot interface: the model predicts
+ * in vacuo charges of the ML region, which interact with the MM point
+ * charges, and the MM atoms receive forces).  Readings of what the paper
+ * leaves open:
+ *   q_i  = charge network of atom i's species on G_i, shifted to the total
+ *          charge: q'_i = q_i - (sum_k q_k - total_charge) / n;
+ *   E    = E_NNP + k_e sum_i sum_J q'_i Q_J / |r_J - r_i| over every MM charge
+ *          J (k_e = 14.3996454784 eV A / e^2; with a box, the minimum image);
+ *   no polarisation term.
+ *   pos, Z, box, energy, forces  the ML atoms, as in nnp_eval (one system;
+ *          box orthorhombic or NULL; forces include the embedding's);
+ *   mm_pos n_mm x 3 doubles (A), mm_q n_mm charges (e), host or device
+ *          (n_mm = 0 allowed);
+ *   mm_forces n_mm x 3 doubles (eV/A), charges n doubles (q'), host or
+ *          device, either may be NULL.
+ * NNP_ERR_NO_WEIGHTS if a species lacks charge weights, NNP_ERR_UNSUPPORTED
+ * for a triclinic box.  Synchronous on the context's stream. */
+int nnp_eval_ee(nnp_ctx *ctx, int64_t n, const double *pos, const int32_t *Z, const double *box,
+                int64_t n_mm, const double *mm_pos, const double *mm_q, double total_charge,
+                double *energy, double *forces, double *mm_forces, double *charges);
 
 /* Per-atom energies E_i (eV) of the last evaluation, in input order
  * (n doubles for nnp_eval, offsets[B] for nnp_eval_batch), host pointer.

@@ -33,6 +33,7 @@ FLAG_NO_GRAPH = 0x1
 FLAG_NONDETERMINISTIC_BINS = 0x2
 FLAG_STAGE_EVENTS = 0x4
 FLAG_AUTOTUNE = 0x8
+FLAG_CHARGES = 0x10
 STAGES = ("cells", "neighbours", "descriptor", "network", "descriptor_backward")
 
 # Every entry point declared in include/nnp.h.
@@ -40,7 +41,7 @@ ABI_FUNCTIONS = ("nnp_config_init", "nnp_create", "nnp_destroy", "nnp_last_error
                  "nnp_set_weights", "nnp_eval", "nnp_eval_async", "nnp_sync",
                  "nnp_eval_batch", "nnp_param_count", "nnp_force_match_grad", "nnp_query",
                  "nnp_profile_stages", "nnp_atom_energies", "nnp_eval_noalloc", "nnp_eval_mlmm", "nnp_eval_pairs", "nnp_selftest",
-                 "nnp_eval_batch_async", "nnp_set_member_weights")
+                 "nnp_eval_batch_async", "nnp_set_member_weights", "nnp_set_charge_weights", "nnp_eval_ee")
 
 QUERY = {"launches_per_eval": 0, "nbr_capacity": 1, "ang_capacity": 2, "max_nbr": 3,
          "max_ang": 4, "rows": 5, "graph_captures": 6,
@@ -131,6 +132,10 @@ def lib() -> ctypes.CDLL:
     L.nnp_eval_mlmm.argtypes = [vp, i64, dp, dp, dp, i64, dp, i32, dp, dp, dp, i32, dp, dp]
     L.nnp_eval_mlmm.restype = ctypes.c_int
     L.nnp_eval_pairs.argtypes = [vp, i64, dp, dp, dp, i64, dp, dp, dp, dp]
+    L.nnp_set_charge_weights.argtypes = [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    L.nnp_set_charge_weights.restype = ctypes.c_int
+    L.nnp_eval_ee.argtypes = [vp, i64, dp, dp, dp, i64, dp, dp, ctypes.c_double, dp, dp, dp, dp]
+    L.nnp_eval_ee.restype = ctypes.c_int
     L.nnp_eval_pairs.restype = ctypes.c_int
     L.nnp_selftest.argtypes = [vp, i32]
     L.nnp_selftest.restype = ctypes.c_int
@@ -258,6 +263,40 @@ class NNP:
     def set_all_weights(self, weights, member: int = 0):
         for s, layers in enumerate(weights):
             self.set_weights(s, layers, member)
+
+    def set_charge_weights(self, weights):
+        """Charge network (context created with FLAG_CHARGES): per-species layers."""
+        for s_, layers in enumerate(weights):
+            keep, Wp, bp = [], (ctypes.c_void_p * 4)(), (ctypes.c_void_p * 4)()
+            for l, (W, b) in enumerate(layers):
+                pw, kw = _ptr(W, np.float32)
+                pb, kb = _ptr(b, np.float32)
+                keep += [kw, kb]
+                Wp[l], bp[l] = pw.value, pb.value
+            self._check(self._L.nnp_set_charge_weights(self._h, int(s_), Wp, bp))
+
+    def eval_ee(self, pos, Z, mm_pos, mm_q, box=None, total_charge=0.0):
+        """Electrostatic embedding: (E, F of the ML atoms, F of the MM charges,
+        ML charges), on the library/device of pos."""
+        n = int(pos.shape[0])
+        m = int(mm_pos.shape[0])
+        pp, kp = _ptr(pos, np.float64)
+        pz, kz = _ptr(Z, np.int32)
+        px, kx = _ptr(mm_pos, np.float64) if m else (None, None)
+        pq, kq = _ptr(mm_q, np.float64) if m else (None, None)
+        b9 = _box9(box)
+        pbox = None if b9 is None else ctypes.c_void_p(b9.ctypes.data)
+        if _is_torch(pos):
+            import torch
+            mk = lambda *shape: torch.zeros(shape, dtype=torch.float64, device=pos.device)
+            E, F, Fm, q = mk(1), mk(n, 3), mk(max(m, 1), 3), mk(n)
+            ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+        else:
+            E, F, Fm, q = np.zeros(1), np.zeros((n, 3)), np.zeros((max(m, 1), 3)), np.zeros(n)
+            ptr = lambda a: ctypes.c_void_p(a.ctypes.data)
+        self._check(self._L.nnp_eval_ee(self._h, n, pp, pz, pbox, m, px, pq, float(total_charge),
+                                        ptr(E), ptr(F), ptr(Fm), ptr(q)))
+        return (float(E[0]) if not _is_torch(pos) else E[0]), F, Fm[:m], q
 
     def set_member_weights(self, members):
         """members[m] = per-species layers of ensemble member m (len = n_members)."""

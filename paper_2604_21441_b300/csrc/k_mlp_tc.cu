@@ -1161,15 +1161,16 @@ int mlp_tc_init(nnp_ctx* ctx) {
   }
   st->per_species = o;
   ctx->tc = st;
-  const size_t images = (size_t)ctx->n_members * ctx->P.S;
+  const int sets = ctx->n_members + (ctx->has_charges ? 1 : 0);  // ensemble, then the charge network
+  const size_t images = (size_t)sets * ctx->P.S;
   cudaError_t e = cudaMalloc(&st->blob, o * images);
   if (e != cudaSuccess) {
     st->blob = nullptr;
     return ctx->cuda_fail(e, "cudaMalloc tensor-core weights");
   }
   cudaMemset(st->blob, 0, o * images);
-  st->wm.assign((size_t)ctx->n_members, MlpTcWeights{});
-  for (int m = 0; m < ctx->n_members; ++m)
+  st->wm.assign((size_t)sets, MlpTcWeights{});
+  for (int m = 0; m < sets; ++m)
     for (int s = 0; s < ctx->P.S; ++s)
       for (int i = 0; i < 6; ++i) st->wm[(size_t)m].m[s][i] = st->blob + o * ((size_t)m * ctx->P.S + s) + st->off[i];
   if (f8) {
@@ -1250,25 +1251,27 @@ void mlp_tc_free(nnp_ctx* ctx) {
   ctx->tc = nullptr;
 }
 
-int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t stream, long long rows, int member, int acc) {
+int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t stream, long long rows, int member, int acc, const EvalIO* io_o,
+                  const Workspace* ws_o) {
   TcState* st = static_cast<TcState*>(ctx->tc);
   if (!st) return ctx->fail(NNP_ERR_UNSUPPORTED, "tensor-core state missing");
   const int D = ctx->P.D;
   const long long tiles = (rows + kTM - 1) / kTM;
   const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, ctx->num_sms));
-  const Workspace w = ctx->workspace();
+  const Workspace w = ws_o ? *ws_o : ctx->workspace();
+  const EvalIO* io = io_o ? io_o : ctx->d_io;
   const size_t sm = smem_bytes(D);
   const MlpTcWeights& tw = st->wm[(size_t)member];
   const MlpF32Weights& fw = ctx->wf32m[(size_t)member];
   if (st->f8)
-    k_mlp_tc<128, true><<<grid, kTcThreads, sm, stream>>>(ctx->d_io, ctx->P, w, tw, fw, acc);
+    k_mlp_tc<128, true><<<grid, kTcThreads, sm, stream>>>(io, ctx->P, w, tw, fw, acc);
   else if (D == 128)
-    k_mlp_tc<128, false><<<grid, kTcThreads, sm, stream>>>(ctx->d_io, ctx->P, w, tw, fw, acc);
+    k_mlp_tc<128, false><<<grid, kTcThreads, sm, stream>>>(io, ctx->P, w, tw, fw, acc);
   else if (D == 48)
-    k_mlp_tc<48, false><<<grid, kTcThreads, sm, stream>>>(ctx->d_io, ctx->P, w, tw, fw, acc);
+    k_mlp_tc<48, false><<<grid, kTcThreads, sm, stream>>>(io, ctx->P, w, tw, fw, acc);
   else {
     const size_t smw = smem_bytes_wide();
-#define WIDE(s) k_mlp_tc_wide<desc_len(s)><<<grid, kTcThreads, smw, stream>>>(ctx->d_io, ctx->P, w, tw, fw, acc)
+#define WIDE(s) k_mlp_tc_wide<desc_len(s)><<<grid, kTcThreads, smw, stream>>>(io, ctx->P, w, tw, fw, acc)
     switch (ctx->P.S) { NNP_WIDE_CASES(WIDE) }
 #undef WIDE
   }

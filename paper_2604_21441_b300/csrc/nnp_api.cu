@@ -208,8 +208,13 @@ int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows,
       ++launches;
     }
   }
+  if (ee_mode) {  // embedding: potentials, charge network, dE/dG of the charges
+    int rc = launch_ee_pre(rows, w, launches);
+    if (rc) return rc;
+  }
   mark_stage(4, capturing);
   launch_aev_bwd(rows, nsm, stream, io, sys, P, w, tune.bwd); ++launches;
+  if (ee_mode) launch_ee_post(launches);  // charges, embedding energy, ML and MM forces
   mark_stage(5, capturing);
   CK(cudaGetLastError());
   launches_per_eval = launches;
@@ -458,7 +463,8 @@ int nnp_ctx::evaluate(int B, const int64_t* offsets, const double* pos, const in
     const bool use_graph = !(cfg.flags & NNP_FLAG_NO_GRAPH);
     if (use_graph) {
       const int ext = ext_mode ? 1 : 0;
-      if (!gexec || g_key_n != n || g_key_B != B || g_key_bins != bins || g_key_ext != ext) {
+      const long long eek = ee_mode ? ee_n_mm : -1;
+      if (!gexec || g_key_n != n || g_key_B != B || g_key_bins != bins || g_key_ext != ext || g_key_ee != eek) {
         invalidate_graph();
         cudaGraph_t graph;
         CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
@@ -469,7 +475,7 @@ int nnp_ctx::evaluate(int B, const int64_t* offsets, const double* pos, const in
         ce = cudaGraphInstantiate(&gexec, graph, 0);
         cudaGraphDestroy(graph);
         if (ce != cudaSuccess) { gexec = nullptr; return cuda_fail(ce, "cudaGraphInstantiate"); }
-        g_key_n = n; g_key_B = B; g_key_bins = bins; g_key_ext = ext;
+        g_key_n = n; g_key_B = B; g_key_bins = bins; g_key_ext = ext; g_key_ee = eek;
         ++graph_captures;
       }
       CK(cudaGraphLaunch(gexec, stream));
@@ -516,6 +522,13 @@ int nnp_ctx::check_flags() {
     return -1;
   }
   return NNP_OK;
+}
+
+bool nnp_ctx::charges_ready() const {
+  if (!has_charges) return false;
+  for (int s = 0; s < P.S; ++s)
+    if (!has_w[(size_t)n_members * kMaxS + s]) return false;
+  return true;
 }
 
 bool nnp_ctx::weights_ready() const {
@@ -594,6 +607,8 @@ int nnp_create(const nnp_config* cfg, nnp_ctx** out) {
   if (members > NNP_MAX_MEMBERS) return bad(NNP_ERR_INVALID_ARG, "at most NNP_MAX_MEMBERS ensemble members");
   if (members > 1 && cfg->precision == NNP_FP8)
     return bad(NNP_ERR_UNSUPPORTED, "the FP8 form takes one network per species");
+  if ((cfg->flags & NNP_FLAG_CHARGES) && cfg->precision == NNP_FP8)
+    return bad(NNP_ERR_UNSUPPORTED, "the FP8 form has no charge network");
 
   nnp_ctx* c = new nnp_ctx();
   c->cfg = *cfg;
@@ -615,6 +630,7 @@ int nnp_create(const nnp_config* cfg, nnp_ctx** out) {
   c->cap_r = cfg->nbr_capacity > 0 ? cfg->nbr_capacity : 96;
   c->cap_a = cfg->ang_capacity > 0 ? cfg->ang_capacity : 32;
   c->n_members = members;
+  c->has_charges = (cfg->flags & NNP_FLAG_CHARGES) != 0;
   int rc = c->init_device();
   if (rc) {
     g_create_error = c->err;

@@ -52,12 +52,14 @@ int nnp_ctx::init_device() {
   wf32_stride = D * kH1 + kH1 * kH2 + kH2 * kH3 + kH3 + kH1 + kH2 + kH3 + 1 + kH1 * D + kH2 * kH1 +
                 kH3 * kH2;
   wf32_stride = (wf32_stride + 63) / 64 * 64;
-  // one table per ensemble member (member m, species s at (m S + s) strides)
-  const size_t tables = (size_t)n_members * P.S;
+  // one table per ensemble member (member m, species s at (m S + s) strides),
+  // then the charge network's (set n_members) with NNP_FLAG_CHARGES
+  const int sets = n_members + (has_charges ? 1 : 0);
+  const size_t tables = (size_t)sets * P.S;
   CK(cudaMalloc(&b_wf32, sizeof(float) * wf32_stride * tables));
   CK(cudaMemset(b_wf32, 0, sizeof(float) * wf32_stride * tables));
-  wf32m.assign((size_t)n_members, MlpF32Weights{});
-  for (int m = 0; m < n_members; ++m)
+  wf32m.assign((size_t)sets, MlpF32Weights{});
+  for (int m = 0; m < sets; ++m)
     for (int s = 0; s < P.S; ++s) {
       MlpF32Weights& t = wf32m[(size_t)m];
       float* p = b_wf32 + wf32_stride * ((size_t)m * P.S + s);
@@ -74,7 +76,7 @@ int nnp_ctx::init_device() {
       t.WT[s][2] = p; p += kH3 * kH2;
     }
   wf32 = wf32m[0];
-  has_w.assign((size_t)n_members * kMaxS, 0);
+  has_w.assign((size_t)sets * kMaxS, 0);
   host_weights.assign((size_t)nnp_param_count(this), 0.f);
   if (cfg.precision != NNP_FP32) {
     int rc = mlp_tc_init(this);
@@ -99,10 +101,13 @@ nnp_ctx::~nnp_ctx() {
                   b_Z_stage, b_F_stage, b_E_stage, b_seg, b_flags, d_zlut, d_io, b_wf32,
                   fm_z, fm_dz, fm_t, fm_p, fm_v, fm_ref, fm_grad, fm_jobs,
                   mm.pos, mm.F, mm.sub_pos, mm.sub_F, mm.ld, mm.E, mm.Z, mm.sub_Z, mm.idx, mm.mark,
-                  b_pair_cur, b_pairs_stage, b_shifts_stage};
+                  b_pair_cur, b_pairs_stage, b_shifts_stage, d_ee, d_io_q, b_ee_mmhi, b_ee_mmlo,
+                  b_ee_mlhi, b_ee_mllo, b_ee_V, b_ee_field, b_ee_qatom, b_ee_qout, b_ee_mmF, b_ee_mmpos,
+                  b_ee_mmq, b_ee_sums, b_ee_qrows, b_ee_dqdG};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (mm.h_bad) cudaFreeHost(mm.h_bad);
+  if (h_ee) cudaFreeHost(h_ee);
   for (auto& ev : stage_ev)
     if (ev) cudaEventDestroy(ev);
   for (auto& sg : stages) {
@@ -147,8 +152,10 @@ int nnp_ctx::set_weights(int m, int s, const float* const W[4], const float* con
   float* p = blob.data();
   auto put = [&](const std::vector<float>& v) { memcpy(p, v.data(), sizeof(float) * v.size()); p += v.size(); };
   std::vector<float> w4 = w[3], b4 = bb[3];
-  for (float& x : w4) x /= (float)n_members;
-  for (float& x : b4) x /= (float)n_members;
+  if (m < n_members) {  // ensemble members: the mean (the charge network is not averaged)
+    for (float& x : w4) x /= (float)n_members;
+    for (float& x : b4) x /= (float)n_members;
+  }
   put(w[0]); put(w[1]); put(w[2]); put(w4);
   put(bb[0]); put(bb[1]); put(bb[2]); put(b4);
   for (int l = 0; l < 3; ++l) {  // transposed copies (fan_out x fan_in)

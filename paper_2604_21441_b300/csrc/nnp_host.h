@@ -53,7 +53,9 @@ void launch_aev_jvp(long long rows, int nsm, cudaStream_t st, const SysDesc* sys
 struct nnp_ctx;
 namespace nnp {
 // k_mlp_tc.cu (tensor-core network); returns an nnp_status
-int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t st, long long rows, int member, int acc);
+// io / ws: the network's I/O block and workspace (null: the context's own)
+int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t st, long long rows, int member, int acc,
+                  const EvalIO* io = nullptr, const Workspace* ws = nullptr);
 int mlp_tc_init(nnp_ctx* ctx);
 int mlp_tc_set_weights(nnp_ctx* ctx, int member, int species, const float* host_blob);
 int launch_fp8_calib(nnp_ctx* ctx, cudaStream_t st, long long rows);
@@ -142,6 +144,25 @@ struct nnp_ctx {
   double* b_shifts_stage = nullptr;
   size_t c_pair_cur = 0, c_pairs_stage = 0, c_shifts_stage = 0;
   int g_key_ext = -1;
+
+  // electrostatic embedding (nnp_ee.cu; NNP_FLAG_CHARGES): the charge
+  // network is weight set n_members; buffers are allocated on first use
+  bool has_charges = false;
+  bool ee_mode = false;          // the current evaluation embeds
+  long long ee_n_ml = 0, ee_n_mm = 0;
+  long long g_key_ee = -1;
+  nnp::EeIO* h_ee = nullptr;     // pinned
+  nnp::EeIO* d_ee = nullptr;
+  nnp::EvalIO* d_io_q = nullptr; // the charge pass's I/O block
+  float4 *b_ee_mmhi = nullptr, *b_ee_mmlo = nullptr, *b_ee_mlhi = nullptr, *b_ee_mllo = nullptr;
+  double *b_ee_V = nullptr, *b_ee_field = nullptr, *b_ee_qatom = nullptr, *b_ee_qout = nullptr;
+  double *b_ee_mmF = nullptr, *b_ee_mmpos = nullptr, *b_ee_mmq = nullptr, *b_ee_sums = nullptr;
+  float *b_ee_qrows = nullptr, *b_ee_dqdG = nullptr;
+  size_t c_ee_n = 0, c_ee_m = 0, c_ee_rows = 0;
+  cudaError_t ee_reserve(long long n, long long m);
+  bool charges_ready() const;
+  int launch_ee_pre(long long rows, const nnp::Workspace& w, int& launches);
+  void launch_ee_post(int& launches);
 
   // ML/MM embedding buffers (nnp_mlmm.cu; allocated on first use)
   struct MlmmBufs {

@@ -133,6 +133,28 @@ struct EvalIO {
   long long n_pairs;
 };
 
+// Electrostatic embedding parameters and buffers of one evaluation (device
+// copy read by the embedding kernels; see nnp_ee.cu).
+struct EeIO {
+  const double* mm_pos;   // n_mm x 3
+  const double* mm_q;     // n_mm
+  long long n_mm;
+  double Q;               // total charge of the ML atoms
+  int S;                  // species (rows = seg[S])
+  int periodic;           // orthorhombic minimum image
+  float Lhi[3], Llo[3], invL[3];
+  float4 *mm_hi, *mm_lo;  // MM coordinates as FP32 hi + lo, charge in mm_hi.w
+  float4 *ml_hi, *ml_lo;  // ML coordinates, input order
+  double* V;              // n: potential of the MM charges at each ML atom (eV / e)
+  double* field;          // n x 3: -grad V
+  float* q_rows;          // [rows] raw charges from the charge network
+  float* dqdG;            // [rows][D] their descriptor gradients
+  double* q_atom;         // n: raw charges in input order
+  double* q_out;          // n: charges shifted to the total charge (output)
+  double* mm_forces;      // n_mm x 3 (output)
+  double* sums;           // [0] scratch, [1] sum of V, [2] sum of raw charges
+};
+
 // Device workspace (all capacity-sized).
 struct Workspace {
   // binning
