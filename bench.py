@@ -494,6 +494,44 @@ def seven_species_rate(members=8, steps=20):
     return res
 
 
+def ee_rate(precision, steps=50, n_ml_waters=64):
+    """Electrostatic embedding (nnp_eval_ee) on the 32,768-water box: the
+    first 64 waters (192 atoms) are the ML region, the other 98,112 atoms are
+    MM point charges (O -0.834 e, H +0.417 e).  Synchronous calls with device
+    buffers, timed by wall clock beside the plain evaluation of the ML atoms."""
+    import torch
+    import synth
+    import paper_2604_21441_b300 as P
+    wl = synth.workload(3)
+    s = wl["systems"][0]
+    k = 3 * n_ml_waters
+    dev = lambda a: torch.tensor(a, device="cuda")
+    pos, Z = dev(s.pos[:k]), dev(s.Z[:k].astype(np.int32))
+    mm_pos = dev(s.pos[k:])
+    mm_q = dev(np.tile([-0.834, 0.417, 0.417], (s.n - k) // 3))
+    box = np.diag(s.box)
+    w = synth.xavier_weights(2, 128, wl["weight_seed"])
+    wq = synth.xavier_weights(2, 128, wl["weight_seed"] + 100, final_scale=0.2)
+    f32 = lambda ws: [[(W.astype(np.float32), b.astype(np.float32)) for W, b in x] for x in ws]
+    pot = P.NNP(atomic_numbers=(1, 8), precision=precision, max_atoms=k, flags=P.FLAG_CHARGES)
+    pot.set_all_weights(f32(w))
+    pot.set_charge_weights(f32(wq))
+    out = {}
+    for name, fn in (("ee", lambda: pot.eval_ee(pos, Z, mm_pos, mm_q, box=box)),
+                     ("plain", lambda: pot.eval(pos, Z, box))):
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            fn()
+        out[name] = (time.perf_counter() - t0) * 1e3 / steps
+    pot.close()
+    return {"workload": "water-32768: 64 ML waters (192 atoms), 98,112 MM point charges", "precision": precision,
+            "steps": steps, "ms_per_step_ee": out["ee"], "ms_per_step_plain_ml": out["plain"],
+            "ml_mm_pairs": k * (s.n - k)}
+
+
 def oracle_sample(wl, w, seconds=20.0, seed=0):
     """Time the FP64 oracle on bounded samples of the workload: sampled atoms
     get E_i and F_i, which evaluates them and every atom within the radial
@@ -654,6 +692,8 @@ def main():
         if args.precision != "fp8":
             line["ensemble"] = ensemble_rate(args.precision)
         line["seven_species"] = seven_species_rate()
+        if args.precision != "fp8":
+            line["ee"] = ee_rate(args.precision)
     if r["per_system_ms"] is not None:
         line["batch"] = {"systems": r["B"], "one_graph_launch_ms": ms_mean,
                          "one_launch_per_system_ms": r["per_system_ms"],
