@@ -532,6 +532,51 @@ def ee_rate(precision, steps=50, n_ml_waters=64):
             "ml_mm_pairs": k * (s.n - k)}
 
 
+PAPER_SIZES = (3, 9, 21, 30, 90, 210, 300, 900, 2100, 3000, 9000, 21000, 30000)  # atoms (Table S3)
+
+
+def size_scan(steps=30, sizes=PAPER_SIZES):
+    """ms per synchronous evaluation (device buffers, wall clock, as one MD
+    step would call it) of water boxes at the sizes of the paper's
+    performance table, for (a) the two-species water model, one network,
+    BF16, and (b) the ANI-2x-scale model: seven species (D = 1008) and an
+    ensemble of eight networks, BF16.  Boxes shorter than the 5.2 A radial
+    cutoff (1 and 3 waters) are run as isolated clusters."""
+    import torch
+    import synth
+    import paper_2604_21441_b300 as P
+    Z7 = tuple(int(z) for z in synth.ANI2X_Z)
+    f32 = lambda ws: [[(W.astype(np.float32), b.astype(np.float32)) for W, b in x] for x in ws]
+    models = {"water_bf16": ((1, 8), 1), "ani2x_scale_bf16": (Z7, 8)}
+    pots = {}
+    for name, (zs, M) in models.items():
+        S = len(zs)
+        pot = P.NNP(atomic_numbers=zs, precision="bf16", max_atoms=max(sizes), n_members=M)
+        for m in range(M):
+            pot.set_all_weights(f32(synth.xavier_weights(S, synth.aev_length(S), 3000 + 17 * m + S)), m)
+        pots[name] = pot
+    rows = []
+    for n_atoms in sizes:
+        s = synth.water_box(n_atoms // 3, 4000 + n_atoms)
+        periodic = s.box[0] >= 5.2
+        box = np.diag(s.box) if periodic else None
+        pos = torch.tensor(s.pos if periodic else s.pos - s.pos.mean(axis=0), device="cuda")
+        Z = torch.tensor(s.Z.astype(np.int32), device="cuda")
+        row = {"atoms": n_atoms, "periodic": bool(periodic)}
+        for name, pot in pots.items():
+            for _ in range(5):
+                pot.eval(pos, Z, box)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                pot.eval(pos, Z, box)
+            row[name + "_ms"] = (time.perf_counter() - t0) * 1e3 / steps
+        rows.append(row)
+    for pot in pots.values():
+        pot.close()
+    return rows
+
+
 def oracle_sample(wl, w, seconds=20.0, seed=0):
     """Time the FP64 oracle on bounded samples of the workload: sampled atoms
     get E_i and F_i, which evaluates them and every atom within the radial
@@ -694,6 +739,7 @@ def main():
         line["seven_species"] = seven_species_rate()
         if args.precision != "fp8":
             line["ee"] = ee_rate(args.precision)
+        line["size_scan"] = size_scan()
     if r["per_system_ms"] is not None:
         line["batch"] = {"systems": r["B"], "one_graph_launch_ms": ms_mean,
                          "one_launch_per_system_ms": r["per_system_ms"],

@@ -249,6 +249,12 @@ __device__ __forceinline__ void tile_energy_sums(float e, bool valid, int sys, i
   }
 }
 
+// *o += (x, y, z, w): one vector reduction in global memory (L2)
+__device__ __forceinline__ void red_add_v4(float4* o, float x, float y, float z, float w) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(o), "f"(x), "f"(y), "f"(z), "f"(w)
+               : "memory");
+}
+
 // Issue the TMEM load of 16 columns (no wait).
 __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
@@ -317,10 +323,15 @@ __device__ __forceinline__ void for_chunks2(uint32_t tcol, uint32_t tcol2, int h
   }
 }
 
+// Work items are (tile, member) pairs for members m0 .. m0 + nm - 1 of the
+// weight sets Wts / Wfs (device arrays), tile-major within a member.  accm =
+// 1: E_i and dE/dG are added with reductions into buffers the caller zeroed
+// (members running side by side); 0: written.
 template <int D, bool F8>
-// acc = 1: add E_i and dE/dG to what an earlier ensemble member left there
 __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(const EvalIO* __restrict__ io, DescParams P,
-                                                  Workspace ws, MlpTcWeights Wt, MlpF32Weights Wf, int acc) {
+                                                  Workspace ws, const MlpTcWeights* __restrict__ Wts,
+                                                  const MlpF32Weights* __restrict__ Wfs, int m0, int nm,
+                                                  int accm) {
   constexpr int kBufA = slabs_of(D > kH2 ? D : kH2) * kSlab;  // G, later g2
   constexpr int kBufB = slabs_of(kH1) * kSlab;                // h1, later g1
   constexpr int kBufC = slabs_of(kH2) * kSlab;                // h2, later g3
@@ -385,12 +396,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(const EvalIO* __restri
   uint32_t ph[4] = {0, 0, 0, 0};
   bool pend[4] = {false, false, false, false};
 
-  auto load_w = [&](int sp, int which, int b) {
+  const MlpTcWeights* cur_w = Wts + m0;  // the current work item's member
+  const MlpF32Weights* cur_f = Wfs + m0;
+  auto load_wm = [&](const MlpTcWeights& W, int sp, int which, int b) {
     const int bytes = (F8 && which < 3) ? mat8_bytes(NW[which], KW[which]) : mat_bytes(NW[which], KW[which]);
     mbar_expect_tx(&bars[b], (uint32_t)bytes);
-    bulk_g2s(wbuf[b], Wt.m[sp][which], (uint32_t)bytes, &bars[b]);
+    bulk_g2s(wbuf[b], W.m[sp][which], (uint32_t)bytes, &bars[b]);
     pend[b] = true;
   };
+  auto load_w = [&](int sp, int which, int b) { load_wm(*cur_w, sp, which, b); };
   auto load_tile = [&](int t) {
     const uint32_t bytes = (uint32_t)(F8 ? gh8_tile_bytes(D) : gh_tile_bytes(D));
     mbar_expect_tx(&bars[2], bytes);
@@ -449,16 +463,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(const EvalIO* __restri
     tc_fence_after();
   };
 
-  int tile = blockIdx.x;
-  if (tile < ntiles && tid == 0) {
-    load_tile(tile);
-    load_w(pos4_species(ws.pos4[tile * kTM]), 0, 0);
+  const int nwork = ntiles * nm;
+  int wi = blockIdx.x;
+  if (wi < nwork && tid == 0) {
+    const int t0 = wi % ntiles;
+    load_tile(t0);
+    load_wm(Wts[m0 + wi / ntiles], pos4_species(ws.pos4[t0 * kTM]), 0, 0);
   }
-  for (; tile < ntiles; tile += gridDim.x) {
+  for (; wi < nwork; wi += gridDim.x) {
+    const int tile = wi % ntiles;
+    cur_w = Wts + m0 + wi / ntiles;
+    cur_f = Wfs + m0 + wi / ntiles;
     const int row0 = tile * kTM;
     const int sp = pos4_species(ws.pos4[row0]);
-    const int next = tile + gridDim.x;
-    const int sp_next = next < ntiles ? pos4_species(ws.pos4[next * kTM]) : 0;
+    const int nwi = wi + gridDim.x;
+    const bool has_next = nwi < nwork;
+    const int next = has_next ? nwi % ntiles : 0;
+    const MlpTcWeights& next_w = Wts[m0 + (has_next ? nwi / ntiles : 0)];
+    const int sp_next = has_next ? pos4_species(ws.pos4[next * kTM]) : 0;
     const int row = row0 + r;
     const int my_atom = ws.row_atom[row];  // consumed by the energy epilogue
     const int my_sys = ws.row_info[row];
@@ -470,15 +492,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(const EvalIO* __restri
       q1 = 1.f / sx1;
       q2 = 1.f / sx2;
       for (int i = tid; i < kH1 + kH2 + kH3; i += blockDim.x)
-        ssc[i] = Wt.wsc[sp][i] * (i < kH1 ? sx0 : (i < kH1 + kH2 ? sx1 : sx2));
+        ssc[i] = cur_w->wsc[sp][i] * (i < kH1 ? sx0 : (i < kH1 + kH2 ? sx1 : sx2));
     }
     for (int i = tid; i < kNB; i += blockDim.x) {
       float v;
-      if (i < kH1) v = Wf.b[sp][0][i];
-      else if (i < kH1 + kH2) v = Wf.b[sp][1][i - kH1];
-      else if (i < kH1 + kH2 + kH3) v = Wf.b[sp][2][i - kH1 - kH2];
-      else if (i < kH1 + kH2 + 2 * kH3) v = Wf.W[sp][3][i - kH1 - kH2 - kH3];
-      else v = Wf.b[sp][3][0];
+      if (i < kH1) v = cur_f->b[sp][0][i];
+      else if (i < kH1 + kH2) v = cur_f->b[sp][1][i - kH1];
+      else if (i < kH1 + kH2 + kH3) v = cur_f->b[sp][2][i - kH1 - kH2];
+      else if (i < kH1 + kH2 + 2 * kH3) v = cur_f->W[sp][3][i - kH1 - kH2 - kH3];
+      else v = cur_f->b[sp][3][0];
       sb[i] = v;
     }
     // ---------------- layer 1: z1 = G W1
@@ -566,7 +588,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(const EvalIO* __restri
       for (int g = 0; g < kG; ++g) e += sE[g * kTM + r];
       const bool valid = my_atom >= 0;
       const float ev = valid ? e : 0.f;
-      ws.Ei[row] = acc ? ws.Ei[row] + ev : ev;
+      if (accm) atomicAdd(&ws.Ei[row], ev);
+      else ws.Ei[row] = ev;
       tile_energy_sums(ev, valid, my_sys, lane, io->energies);
     }
     wait_mma(3);
@@ -584,9 +607,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(const EvalIO* __restri
       commit();
     }
     wait_mma(3);
-    if (tid == 0 && next < ntiles) {  // bufA and wbuf[0] are free: prefetch the next tile
+    if (tid == 0 && has_next) {  // bufA and wbuf[0] are free: prefetch the next work item
       load_tile(next);
-      load_w(sp_next, 0, 0);
+      load_wm(next_w, sp_next, 0, 0);
     }
     for_chunks2<kH1>(tg1, tz1, h, [&](int c0, float (&g)[16], float (&d)[16]) {
 #pragma unroll
@@ -601,7 +624,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(const EvalIO* __restri
       commit();
     }
     wait_mma(3);
-    if (tid == 0 && next < ntiles) {  // next tile's layer 1 into [0,160), under the dE/dG epilogue
+    if (tid == 0 && has_next) {  // next work item's layer 1 into [0,160), under the dE/dG epilogue
       wait0(2);
       wait0(0);
       if (*abort_flag == 0) {
@@ -617,15 +640,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(const EvalIO* __restri
 #pragma unroll
         for (int j = 0; j < 16; j += 4) {
           float4* o = reinterpret_cast<float4*>(out + c0 + j);
-          float4 x = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-          if (acc) {
-            const float4 y = *o;
-            x.x += y.x;
-            x.y += y.y;
-            x.z += y.z;
-            x.w += y.w;
-          }
-          *o = x;
+          if (accm) red_add_v4(o, v[j], v[j + 1], v[j + 2], v[j + 3]);
+          else *o = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
         }
       });
     }
@@ -673,8 +689,9 @@ constexpr int kWideNC = 128;  // dE/dG columns per block
 
 template <int D>
 __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __restrict__ io, DescParams P,
-                                                       Workspace ws, MlpTcWeights Wt, MlpF32Weights Wf,
-                                                       int acc) {
+                                                       Workspace ws, const MlpTcWeights* __restrict__ Wts,
+                                                       const MlpF32Weights* __restrict__ Wfs, int m0, int nm,
+                                                       int accm) {
   constexpr int kBufA = kWideKC * kSlab;        // G chunk (stage 0), later g2
   constexpr int kBufB = slabs_of(kH1) * kSlab;  // h1, later g1
   constexpr int kBufC = slabs_of(kH2) * kSlab;  // G chunk (stage 1), h2, later g3
@@ -734,6 +751,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
   uint32_t ph56[2] = {0, 0}, ph78[2] = {0, 0}, ph4 = 0;
   bool pend4 = false;
 
+  const MlpTcWeights* cur_w = Wts + m0;  // the current work item's member
+  const MlpF32Weights* cur_f = Wfs + m0;
   auto timeout = [&]() {
     *abort_flag = 1;
     atomicOr(&ws.flags[kFlagTimeout], 1);
@@ -743,7 +762,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
     constexpr int KWt[6] = {D, kH1, kH2, kH3, kH2, kH1};
     const int bytes = mat_bytes(NWt[which], KWt[which]);
     mbar_expect_tx(&bars[b], (uint32_t)bytes);
-    bulk_g2s(wbuf[b], Wt.m[sp][which], (uint32_t)bytes, &bars[b]);
+    bulk_g2s(wbuf[b], cur_w->m[sp][which], (uint32_t)bytes, &bars[b]);
     pend[b] = true;
   };
   auto load_chunk = [&](int t, int sp, int c) {  // layer-1 chunk c into stage c & 1
@@ -752,7 +771,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
     mbar_expect_tx(&bars[b], gb + wbytes);
     bulk_g2s(b ? bufC : bufA, reinterpret_cast<const uint8_t*>(ws.Gh) + (size_t)t * gh_tile_bytes(D) +
                                   (size_t)s0 * kSlab, gb, &bars[b]);
-    bulk_g2s(wbuf[b], Wt.m[sp][0] + (size_t)s0 * kH1 * 128, wbytes, &bars[b]);
+    bulk_g2s(wbuf[b], cur_w->m[sp][0] + (size_t)s0 * kH1 * 128, wbytes, &bars[b]);
     pend[b] = true;
   };
   auto load_block = [&](int sp, int cb, int b) {  // dE/dG block cb's W1 rows into wbuf[b]
@@ -760,7 +779,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
     const uint32_t bytes = (uint32_t)(nc * 128);
     mbar_expect_tx(&bars[b], (uint32_t)slabs_of(kH1) * bytes);
     for (int k = 0; k < slabs_of(kH1); ++k)
-      bulk_g2s(wbuf[b] + (size_t)k * bytes, Wt.m[sp][5] + (size_t)k * D * 128 + (size_t)n0 * 128, bytes, &bars[b]);
+      bulk_g2s(wbuf[b] + (size_t)k * bytes, cur_w->m[sp][5] + (size_t)k * D * 128 + (size_t)n0 * 128, bytes,
+               &bars[b]);
     pend[b] = true;
   };
   auto commit = [&]() {
@@ -797,7 +817,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
     if (tid == 0) pend[3] = false;
   };
 
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int wi = blockIdx.x; wi < ntiles * nm; wi += gridDim.x) {
+    const int tile = wi % ntiles;
+    cur_w = Wts + m0 + wi / ntiles;
+    cur_f = Wfs + m0 + wi / ntiles;
     const int row0 = tile * kTM;
     const int sp = pos4_species(ws.pos4[row0]);
     const int row = row0 + r;
@@ -805,11 +828,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
     const int my_sys = ws.row_info[row];
     for (int i = tid; i < kNB; i += blockDim.x) {
       float v;
-      if (i < kH1) v = Wf.b[sp][0][i];
-      else if (i < kH1 + kH2) v = Wf.b[sp][1][i - kH1];
-      else if (i < kH1 + kH2 + kH3) v = Wf.b[sp][2][i - kH1 - kH2];
-      else if (i < kH1 + kH2 + 2 * kH3) v = Wf.W[sp][3][i - kH1 - kH2 - kH3];
-      else v = Wf.b[sp][3][0];
+      if (i < kH1) v = cur_f->b[sp][0][i];
+      else if (i < kH1 + kH2) v = cur_f->b[sp][1][i - kH1];
+      else if (i < kH1 + kH2 + kH3) v = cur_f->b[sp][2][i - kH1 - kH2];
+      else if (i < kH1 + kH2 + 2 * kH3) v = cur_f->W[sp][3][i - kH1 - kH2 - kH3];
+      else v = cur_f->b[sp][3][0];
       sb[i] = v;
     }
     if (!phase(-1, -1)) break;  // biases published; every buffer of the last tile is free
@@ -912,7 +935,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
       for (int g = 0; g < kG; ++g) e += sE[g * kTM + r];
       const bool valid = my_atom >= 0;
       const float ev = valid ? e : 0.f;
-      ws.Ei[row] = acc ? ws.Ei[row] + ev : ev;
+      if (accm) atomicAdd(&ws.Ei[row], ev);
+      else ws.Ei[row] = ev;
       tile_energy_sums(ev, valid, my_sys, lane, io->energies);
     }
     wait_mma();
@@ -966,16 +990,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
 #pragma unroll
         for (int j = 0; j < 16; j += 4) {
           float4* o = reinterpret_cast<float4*>(out + c * 16 + j);
-          float4 x = make_float4(__uint_as_float(a[j]), __uint_as_float(a[j + 1]), __uint_as_float(a[j + 2]),
-                                 __uint_as_float(a[j + 3]));
-          if (acc) {
-            const float4 y = *o;
-            x.x += y.x;
-            x.y += y.y;
-            x.z += y.z;
-            x.w += y.w;
-          }
-          *o = x;
+          const float4 x = make_float4(__uint_as_float(a[j]), __uint_as_float(a[j + 1]), __uint_as_float(a[j + 2]),
+                                       __uint_as_float(a[j + 3]));
+          if (accm) red_add_v4(o, x.x, x.y, x.z, x.w);
+          else *o = x;
         }
       }
       if (!phase(-1, -1)) {  // this block's TMEM columns have been read before block cb + 2 reuses them
@@ -1083,6 +1101,8 @@ struct TcState {
   size_t per_species = 0;
   size_t off[6] = {0, 0, 0, 0, 0, 0};
   std::vector<MlpTcWeights> wm;  // one set of image pointers per ensemble member
+  MlpTcWeights* d_wm = nullptr;  // device copies of wm and of the context's FP32 sets (biases)
+  MlpF32Weights* d_wf = nullptr;
 };
 
 // Byte offset of element (n, k) of a swizzled K-major [N][K] image with
@@ -1181,6 +1201,12 @@ int mlp_tc_init(nnp_ctx* ctx) {
     }
     for (int s = 0; s < ctx->P.S; ++s) st->wm[0].wsc[s] = st->wsc + (size_t)(kH1 + kH2 + kH3) * s;
   }
+  e = cudaMalloc(&st->d_wm, sizeof(MlpTcWeights) * sets);
+  if (e == cudaSuccess) e = cudaMemcpy(st->d_wm, st->wm.data(), sizeof(MlpTcWeights) * sets, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&st->d_wf, sizeof(MlpF32Weights) * sets);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(st->d_wf, ctx->wf32m.data(), sizeof(MlpF32Weights) * sets, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "weight tables");
   e = cudaMalloc(&ctx->b_q8, sizeof(int) * 8 * kMaxS);
   if (e != cudaSuccess) {
     ctx->b_q8 = nullptr;
@@ -1247,31 +1273,33 @@ void mlp_tc_free(nnp_ctx* ctx) {
   if (!st) return;
   if (st->blob) cudaFree(st->blob);
   if (st->wsc) cudaFree(st->wsc);
+  if (st->d_wm) cudaFree(st->d_wm);
+  if (st->d_wf) cudaFree(st->d_wf);
   delete st;
   ctx->tc = nullptr;
 }
 
-int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t stream, long long rows, int member, int acc, const EvalIO* io_o,
+int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t stream, long long rows, int m0, int nm, int accm, const EvalIO* io_o,
                   const Workspace* ws_o) {
   TcState* st = static_cast<TcState*>(ctx->tc);
   if (!st) return ctx->fail(NNP_ERR_UNSUPPORTED, "tensor-core state missing");
   const int D = ctx->P.D;
   const long long tiles = (rows + kTM - 1) / kTM;
-  const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, ctx->num_sms));
+  const int grid = (int)std::max<long long>(1, std::min<long long>(tiles * nm, ctx->num_sms));
   const Workspace w = ws_o ? *ws_o : ctx->workspace();
   const EvalIO* io = io_o ? io_o : ctx->d_io;
   const size_t sm = smem_bytes(D);
-  const MlpTcWeights& tw = st->wm[(size_t)member];
-  const MlpF32Weights& fw = ctx->wf32m[(size_t)member];
+  const MlpTcWeights* tw = st->d_wm;
+  const MlpF32Weights* fw = st->d_wf;
   if (st->f8)
-    k_mlp_tc<128, true><<<grid, kTcThreads, sm, stream>>>(io, ctx->P, w, tw, fw, acc);
+    k_mlp_tc<128, true><<<grid, kTcThreads, sm, stream>>>(io, ctx->P, w, tw, fw, m0, nm, accm);
   else if (D == 128)
-    k_mlp_tc<128, false><<<grid, kTcThreads, sm, stream>>>(io, ctx->P, w, tw, fw, acc);
+    k_mlp_tc<128, false><<<grid, kTcThreads, sm, stream>>>(io, ctx->P, w, tw, fw, m0, nm, accm);
   else if (D == 48)
-    k_mlp_tc<48, false><<<grid, kTcThreads, sm, stream>>>(io, ctx->P, w, tw, fw, acc);
+    k_mlp_tc<48, false><<<grid, kTcThreads, sm, stream>>>(io, ctx->P, w, tw, fw, m0, nm, accm);
   else {
     const size_t smw = smem_bytes_wide();
-#define WIDE(s) k_mlp_tc_wide<desc_len(s)><<<grid, kTcThreads, smw, stream>>>(io, ctx->P, w, tw, fw, acc)
+#define WIDE(s) k_mlp_tc_wide<desc_len(s)><<<grid, kTcThreads, smw, stream>>>(io, ctx->P, w, tw, fw, m0, nm, accm)
     switch (ctx->P.S) { NNP_WIDE_CASES(WIDE) }
 #undef WIDE
   }

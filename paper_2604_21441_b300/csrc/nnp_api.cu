@@ -201,12 +201,14 @@ int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows,
       launch_mlp_f32(std::max(1, g_tiles), stream, io, P, w, wf32m[(size_t)m], m > 0 ? 1 : 0);
       ++launches;
     }
-  } else {
-    for (int m = 0; m < n_members; ++m) {
-      int rc = launch_mlp_tc(this, stream, rows, m, m > 0 ? 1 : 0);
-      if (rc) return rc;
-      ++launches;
+  } else {  // ensemble members side by side in one launch, outputs added with reductions
+    if (n_members > 1) {
+      CK(cudaMemsetAsync(b_Ei, 0, sizeof(float) * (size_t)rows, stream));
+      CK(cudaMemsetAsync(b_dEdG, 0, sizeof(float) * (size_t)rows * P.D, stream));
     }
+    int rc = launch_mlp_tc(this, stream, rows, 0, n_members, n_members > 1 ? 1 : 0);
+    if (rc) return rc;
+    ++launches;
   }
   if (ee_mode) {  // embedding: potentials, charge network, dE/dG of the charges
     int rc = launch_ee_pre(rows, w, launches);

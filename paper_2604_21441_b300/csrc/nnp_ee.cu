@@ -247,7 +247,7 @@ int nnp_ctx::launch_ee_pre(long long rows, const Workspace& w, int& launches) {
     const int g_tiles = (int)std::min<long long>(rows / 64, (long long)nsm);
     launch_mlp_f32(std::max(1, g_tiles), stream, d_io_q, P, wq, wf32m[(size_t)qm], 0);
   } else {
-    int rc = launch_mlp_tc(this, stream, rows, qm, 0, d_io_q, &wq);
+    int rc = launch_mlp_tc(this, stream, rows, qm, 1, 0, d_io_q, &wq);
     if (rc) return rc;
   }
   ++launches;

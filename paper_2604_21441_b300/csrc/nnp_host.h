@@ -54,7 +54,9 @@ struct nnp_ctx;
 namespace nnp {
 // k_mlp_tc.cu (tensor-core network); returns an nnp_status
 // io / ws: the network's I/O block and workspace (null: the context's own)
-int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t st, long long rows, int member, int acc,
+// Members m0 .. m0 + nm - 1 side by side; accm = 1 adds E_i and dE/dG with
+// reductions (the caller zeroes them first), 0 writes them.
+int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t st, long long rows, int m0, int nm, int accm,
                   const EvalIO* io = nullptr, const Workspace* ws = nullptr);
 int mlp_tc_init(nnp_ctx* ctx);
 int mlp_tc_set_weights(nnp_ctx* ctx, int member, int species, const float* host_blob);
