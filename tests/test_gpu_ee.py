@@ -14,6 +14,7 @@ network bounds of the BF16 tests (1e-2 relative energy, 0.1 eV/A).
   cluster, against the FP64 oracle, host and device buffers;
 * a four-species box (H/C/N/O clusters as ML, waters as MM), FP32 and BF16;
 * no MM charges reproduces nnp_eval and conserves the total charge;
+* an ensemble of two energy networks with the charge network, FP32 and BF16;
 * refusals: no FLAG_CHARGES, missing charge weights, FP8.
 """
 import numpy as np
@@ -57,13 +58,18 @@ def _oracle(oracle_mod, w, wq, Zs, pos, Z, box, mm_pos, mm_q, Q):
     sp = p.species_of(Z)
     E, F, Fmm, q = oracle_mod.ee_energy_forces(m, mq, pos, sp, box, mm_pos, mm_q, total_charge=Q)
     _, Ei, _, _ = oracle_mod.energy_forces(m, pos, sp, box)
-    scale = np.abs(Ei).sum()
+    return E, F, Fmm, q, max(abs(E), np.abs(Ei).sum() + _coulomb_scale(pos, q, mm_pos, mm_q, box))
+
+
+def _coulomb_scale(pos, q, mm_pos, mm_q, box):
+    """k_e sum_i sum_J |q_i Q_J| / r_iJ: the magnitude of the Coulomb sum's terms."""
+    total = 0.0
     for i in range(len(pos)):
         d = mm_pos - pos[i]
         if box is not None:
             d -= box * np.round(d / box)
-        scale += K_E * np.sum(np.abs(q[i] * mm_q) / np.sqrt((d * d).sum(axis=1)))
-    return E, F, Fmm, q, max(abs(E), scale)
+        total += K_E * np.sum(np.abs(q[i] * mm_q) / np.sqrt((d * d).sum(axis=1)))
+    return total
 
 
 def _water_split(seed, n_ml=6, n=27):
@@ -152,3 +158,32 @@ def test_ee_refusals(P):
     with pytest.raises(P.NNPError) as e:
         P.NNP(atomic_numbers=(1, 8), precision="fp8", flags=P.FLAG_CHARGES)
     assert e.value.code == 3
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_ee_with_ensemble(P, oracle_mod, prec):
+    """Two energy networks (their mean) plus the charge network: the charge
+    network is the weight set after the ensemble's and stays out of the
+    members' launch.  Oracle: the embedding terms with member 0, its NNP part
+    replaced by the ensemble's."""
+    s, pos, Z, mm_pos, mm_q = _water_split(941)
+    mem = [weights32(2, 128, 942 + 5 * m, 943 + 5 * m) for m in range(2)]
+    wq = _charge_weights(2, 128, 951)
+    pot = P.NNP(atomic_numbers=(1, 8), precision=prec, flags=P.FLAG_CHARGES, n_members=2)
+    pot.set_member_weights([_f32(w) for w in mem])
+    pot.set_charge_weights(_f32(wq))
+    E, F, Fmm, q = pot.eval_ee(pos, Z, mm_pos, mm_q, box=box9(s.box), total_charge=0.0)
+    p = oracle_mod.Params()
+    sp = p.species_of(Z)
+    models = [oracle_mod.Model(p, w) for w in mem]
+    Ee, Fe, Fmr, qr = oracle_mod.ee_energy_forces(models[0], oracle_mod.Model(p, wq), pos, sp, s.box, mm_pos, mm_q)
+    E0, _, F0, _ = oracle_mod.energy_forces(models[0], pos, sp, s.box)
+    Em, Eim, Fm = oracle_mod.ensemble_energy_forces(models, pos, sp, s.box)
+    Er, Fr = Ee - E0 + Em, Fe - F0 + Fm
+    scale = max(abs(Er), np.abs(Eim).sum() + _coulomb_scale(pos, qr, mm_pos, mm_q, s.box))
+    tolE, tolF = (1e-6, F_ABS_TOL) if prec == "fp32" else (1e-2, 0.1)
+    print(f"ee + ensemble {prec}: rel E {abs(E - Er) / scale:.2e}, max|dF| {np.abs(F - Fr).max():.2e},"
+          f" max|dFmm| {np.abs(Fmm - Fmr).max():.2e}")
+    assert abs(E - Er) <= tolE * scale
+    assert np.abs(F - Fr).max() <= tolF and np.abs(Fmm - Fmr).max() <= tolF
+    assert np.abs(q - qr).max() <= (1e-6 if prec == "fp32" else 1e-2)
