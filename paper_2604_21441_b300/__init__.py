@@ -330,9 +330,10 @@ class NNP:
     def eval_into(self, pos, Z, box, E_out, F_out, sync: bool = True):
         """Device-pointer evaluation into caller buffers (torch CUDA tensors)."""
         b9 = _box9(box)
+        pbox = None if b9 is None else ctypes.c_void_p(b9.ctypes.data)
         fn = self._L.nnp_eval if sync else self._L.nnp_eval_async
         self._check(fn(self._h, int(pos.shape[0]), ctypes.c_void_p(pos.data_ptr()),
-                       ctypes.c_void_p(Z.data_ptr()), ctypes.c_void_p(b9.ctypes.data),
+                       ctypes.c_void_p(Z.data_ptr()), pbox,
                        ctypes.c_void_p(E_out.data_ptr()), ctypes.c_void_p(F_out.data_ptr())))
 
     def eval_mlmm(self, pos, Z, ml_index, link_ml=(), link_mm=(), link_d=None, link_Z=1, box=None):
