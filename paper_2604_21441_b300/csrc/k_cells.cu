@@ -300,11 +300,17 @@ __global__ void __launch_bounds__(256) k_binsort(const EvalIO* __restrict__ io, 
 // parked at the end of the list and moved down once the species is done.
 // Both keep the hit masks of a lane in shared-memory slots and write the hits
 // with one loop whose step count is the same for the whole warp.  SB >= S
-// bounds the per-species register arrays and scans (2, 4 or 8).
-template <int SB>
+// bounds the per-species register arrays and scans (2, 4 or 8).  WIN is the
+// window (512; 1024 for small systems, with row groups of at most 8 so that a
+// lane still tests at most 8 chunks).  split > 1 spreads a cell's row groups
+// over that many warps, for systems with fewer cells than the GPU has warps.
+template <int SB, int WIN>
 __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __restrict__ io,
                                                           const SysDesc* __restrict__ sys,
-                                                          DescParams P, Workspace ws) {
+                                                          DescParams P, Workspace ws, int split) {
+  constexpr int NCH = WIN / 32;                                       // window chunks
+  constexpr int WF = 3 * NCH * kNbrChunkStride + WIN + 16 * 32;       // shared floats per warp
+  constexpr int GR = WIN > 512 ? 8 : 16;                              // rows per group
   constexpr unsigned F = 0xffffffffu;
   __shared__ int s_mx[3];  // maxima of the CTA's row counts; warps done
   extern __shared__ float4 s_dyn[];
@@ -313,11 +319,11 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
   // stride of 36 floats, so that the lanes of a row, reading different
   // chunks, hit different banks) and of list entries, then the 16 hit-mask
   // slots of the group path
-  float* wx = reinterpret_cast<float*>(s_dyn) + (size_t)wib * kNbrWarpFloats;
-  float* wy = wx + kNbrChunks * kNbrChunkStride;
-  float* wz = wy + kNbrChunks * kNbrChunkStride;
-  int* we = reinterpret_cast<int*>(wz + kNbrChunks * kNbrChunkStride);
-  unsigned* hmask = reinterpret_cast<unsigned*>(we + kNbrWin);
+  float* wx = reinterpret_cast<float*>(s_dyn) + (size_t)wib * WF;
+  float* wy = wx + NCH * kNbrChunkStride;
+  float* wz = wy + NCH * kNbrChunkStride;
+  int* we = reinterpret_cast<int*>(wz + NCH * kNbrChunkStride);
+  unsigned* hmask = reinterpret_cast<unsigned*>(we + WIN);
   const int TC = io->total_cells, nsys = io->n_sys, S = P.S, cap = ws.cap_r;
   const float rcr2 = P.rc_r * P.rc_r, rca2 = P.rc_a * P.rc_a;
   const f2 nrc2 = f2_make(-rcr2, -rcr2), nra2 = f2_make(-rca2, -rca2);
@@ -325,7 +331,8 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
   const int wpb = blockDim.x >> 5;
   if (threadIdx.x < 3) s_mx[threadIdx.x] = 0;
   __syncthreads();
-  for (int g = blockIdx.x * wpb + wib; g < TC; g += gridDim.x * wpb) {
+  for (int vg = blockIdx.x * wpb + wib; vg < TC * split; vg += gridDim.x * wpb) {
+    const int g = vg / split, part = vg - g * split;
     int lo = 0, hi = nsys - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
@@ -458,14 +465,14 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
       ha &= hr;
     };
 
-    if (max_tot <= kNbrWin) {
+    if (max_tot <= WIN) {
       // ---- group path: rows in groups of up to 16, h = 32 / 2^ceil(log2(rows))
       // lanes per row (h >= 2), lane p of a row testing its share of the
       // window's 32-candidate chunks.  Hit counts are scanned over the h
       // lanes of the row, so every entry goes straight to its final place
       // (angular ones first, both kinds in window order).  When the windows
       // of all species fit, they are staged once for all groups.
-      const bool all_fit = sum_tot <= kNbrWin;
+      const bool all_fit = sum_tot <= WIN;
       if (all_fit) {
         int wb = 0;
         for (int sp = 0; sp < S; ++sp) {
@@ -474,8 +481,8 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
           wb += (wn + 31) & ~31;
         }
       }
-      for (int r0 = 0; r0 < nrows; r0 += 16) {
-        const int rg = min(16, nrows - r0);
+      for (int r0 = GR * part; r0 < nrows; r0 += GR * split) {
+        const int rg = min(GR, nrows - r0);
         const int lh = rg > 8 ? 1 : (rg > 4 ? 2 : (rg > 2 ? 3 : (rg > 1 ? 4 : 5)));  // log2 h
         const int h = 1 << lh;
         const int ql = lane >> lh, p = lane & (h - 1);
@@ -583,7 +590,7 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
     // by one flat loop with a warp-uniform step count.  Angular entries go to
     // the front of the row's segment, radial-only ones are parked at the end
     // of the list and moved behind them once the species is done.
-    for (int r0 = 0; r0 < nrows; r0 += 32) {
+    for (int r0 = 32 * part; r0 < nrows; r0 += 32 * split) {
       const int q = r0 + lane;
       const bool has = q < nrows;
       const int row = row_of(q);
@@ -597,8 +604,8 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
         const int ex13 = __shfl_sync(F, pick(bex, sp), 13), st13 = __shfl_sync(F, pick(bst, sp), 13);
         const int self_k = (has && row_sp == sp) ? ex13 + (row - st13) : -1;
         int wa = 0, wro = 0, ka = 0, kro = 0;  // written / found: angular, radial-only
-        for (int w0 = 0; w0 < total; w0 += kNbrWin) {
-          const int wn = min(kNbrWin, total - w0);
+        for (int w0 = 0; w0 < total; w0 += WIN) {
+          const int wn = min(WIN, total - w0);
           stage(sp, w0, wn, 0);
           for (int h0 = 0; h0 < wn; h0 += 256) {
             const int nch = (min(256, wn - h0) + 31) >> 5;
@@ -689,27 +696,42 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
   }
 }
 
-size_t neighbors_smem(int cap_r) {
-  (void)cap_r;
-  return sizeof(float) * kNbrWarpFloats * (kNbrThreads / 32);
+size_t neighbors_smem(int win) {
+  return sizeof(float) * (size_t)(3 * (win / 32) * kNbrChunkStride + win + 16 * 32) * (kNbrThreads / 32);
 }
 
 cudaError_t neighbors_set_smem_limits() {
   cudaError_t e = cudaFuncSetAttribute(k_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(sizeof(int) * kScanSmemBins));
-  const int sm = (int)neighbors_smem(4096);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_neighbors<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_neighbors<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_neighbors<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  const int s1 = (int)neighbors_smem(kNbrWin), s2 = (int)neighbors_smem(kNbrWinSmall);
+#define NSM(sb)                                                                                                   \
+  if (e == cudaSuccess)                                                                                           \
+    e = cudaFuncSetAttribute(k_neighbors<sb, kNbrWin>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1);          \
+  if (e == cudaSuccess)                                                                                           \
+    e = cudaFuncSetAttribute(k_neighbors<sb, kNbrWinSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2);
+  NSM(2) NSM(4) NSM(8)
+#undef NSM
   return e;
 }
 
 void launch_neighbors(int grid, cudaStream_t st, const EvalIO* io, const SysDesc* sys, const DescParams& P,
-                      const Workspace& ws) {
-  const size_t sm = neighbors_smem(ws.cap_r);
-  if (P.S <= 2) k_neighbors<2><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws);
-  else if (P.S <= 4) k_neighbors<4><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws);
-  else k_neighbors<8><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws);
+                      const Workspace& ws, long long rows, long long cells, int nsm) {
+  if (rows > kNbrRowsSmall) {  // warp per cell, 512-candidate windows
+    const size_t sm = neighbors_smem(kNbrWin);
+    if (P.S <= 2) k_neighbors<2, kNbrWin><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws, 1);
+    else if (P.S <= 4) k_neighbors<4, kNbrWin><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws, 1);
+    else k_neighbors<8, kNbrWin><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws, 1);
+    return;
+  }
+  // small systems: 1024-candidate windows, each cell's row groups over up to 8 warps
+  const long long target = 8LL * nsm;  // warps to aim for
+  const int split = (int)std::max(1LL, std::min(8LL, (target + cells - 1) / std::max(1LL, cells)));
+  const long long warps = cells * split;
+  const int g = (int)std::max(1LL, (warps + kNbrThreads / 32 - 1) / (kNbrThreads / 32));
+  const size_t sm = neighbors_smem(kNbrWinSmall);
+  if (P.S <= 2) k_neighbors<2, kNbrWinSmall><<<g, kNbrThreads, sm, st>>>(io, sys, P, ws, split);
+  else if (P.S <= 4) k_neighbors<4, kNbrWinSmall><<<g, kNbrThreads, sm, st>>>(io, sys, P, ws, split);
+  else k_neighbors<8, kNbrWinSmall><<<g, kNbrThreads, sm, st>>>(io, sys, P, ws, split);
 }
 
 }  // namespace nnp

@@ -182,7 +182,7 @@ int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows,
     k_pairs_fill<<<g_pairs, 256, 0, stream>>>(io, sys, P, w, b_pair_cur);
     launches += 4;
   } else {
-    launch_neighbors(g_cells, stream, io, sys, P, w); ++launches;
+    launch_neighbors(g_cells, stream, io, sys, P, w, rows, total_cells, nsm); ++launches;
   }
   mark_stage(2, capturing);
   if (calib) {  // FP8 calibration: FP32 descriptor, then the activation ranges

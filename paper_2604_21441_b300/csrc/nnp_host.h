@@ -14,15 +14,17 @@ __global__ void k_bin(const EvalIO* io, const SysDesc* sys, const signed char* z
 __global__ void k_scan(const EvalIO* io, int S, Workspace ws);
 __global__ void k_scatter(const EvalIO* io, Workspace ws);
 __global__ void k_binsort(const EvalIO* io, int S, int sort, Workspace ws);
+// grid: blocks for a warp per cell (systems above kNbrRowsSmall rows); rows and
+// cells (totals over systems) choose the small-system form and its split
 void launch_neighbors(int grid, cudaStream_t st, const EvalIO* io, const SysDesc* sys, const DescParams& P,
-                      const Workspace& ws);
+                      const Workspace& ws, long long rows, long long cells, int nsm);
 void set_cell_steps(SysDesc& sd);  // cell steps and their inverse from nc, ell or B
 void launch_wait_selftest(cudaStream_t st, int* flags, unsigned long long limit_ns);
 __global__ void k_pairs_prep(int S, Workspace ws);
 __global__ void k_pairs_count(const EvalIO* io, const SysDesc* sys, DescParams P, Workspace ws);
 __global__ void k_pairs_offsets(const EvalIO* io, int S, Workspace ws, int* cur);
 __global__ void k_pairs_fill(const EvalIO* io, const SysDesc* sys, DescParams P, Workspace ws, int* cur);
-size_t neighbors_smem(int cap_r);
+size_t neighbors_smem(int win);
 cudaError_t neighbors_set_smem_limits();
 
 // k_aev.cu

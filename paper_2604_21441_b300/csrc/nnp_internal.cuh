@@ -36,10 +36,9 @@ constexpr int kMaxCapR = 512;    // largest radial-neighbour capacity (gathered 
 constexpr int kScanSmemBins = 16384;  // k_scan stages up to this many bins in shared memory
 constexpr int kNbrThreads = 128;  // k_neighbors: warp per cell, lane per row
 constexpr int kNbrWin = 512;      // neighbourhood atoms one warp stages per window
-constexpr int kNbrChunks = kNbrWin / 32;  // window chunks of 32 candidates
+constexpr int kNbrWinSmall = 1024;          // the same for small systems (at most kNbrRowsSmall rows)
+constexpr long long kNbrRowsSmall = 8192;
 constexpr int kNbrChunkStride = 36;       // floats per chunk in shared memory (bank spread)
-// shared floats per k_neighbors warp: x, y, z chunks, entries, 16 x 32 hit masks
-constexpr int kNbrWarpFloats = 3 * kNbrChunks * kNbrChunkStride + kNbrWin + 16 * 32;
 constexpr int kMaxD = kNRad * kMaxS + kNAng * kMaxS * (kMaxS + 1) / 2;  // 1280
 __host__ __device__ constexpr int desc_len(int S) { return kNRad * S + kNAng * S * (S + 1) / 2; }
 constexpr int kMaxSFm = 4;     // species of the force-matching (second-order) kernels

@@ -229,7 +229,7 @@ extern "C" int nnp_eval_noalloc(nnp_ctx* ctx, int64_t n, const double* pos, cons
   k_scan<<<1, 1024, sizeof(int) * kScanSmemBins, st>>>(d_io, P.S, w);
   k_scatter<<<g_atoms, 256, 0, st>>>(d_io, w);
   k_binsort<<<g_bins, 256, 0, st>>>(d_io, P.S, 1, w);
-  launch_neighbors(g_cells, st, d_io, d_sys, P, w);
+  launch_neighbors(g_cells, st, d_io, d_sys, P, w, rows, bins / P.S, nsm);
   launch_aev_fwd(rows, nsm, st, d_sys, P, w, 0);
   for (int m = 0; m < ctx->n_members; ++m)  // ensemble members add up
     launch_mlp_f32(g_tiles > 0 ? g_tiles : 1, st, d_io, P, w, ctx->wf32m[(size_t)m], m > 0 ? 1 : 0);
