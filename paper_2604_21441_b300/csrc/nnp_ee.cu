@@ -40,17 +40,29 @@ __device__ __forceinline__ void split2(double x, float& hi, float& lo) {
   lo = (float)(x - (double)hi);
 }
 
-// d = (b - a) with minimum image, from hi/lo parts; L, Lhi, Llo per axis
+// d = (b - a) with minimum image, from hi/lo parts of coordinates wrapped
+// into [0, L) (so |d| < L and one shift at most; selects, no rounding)
 __device__ __forceinline__ float3 disp(float4 ah, float4 al, float4 bh, float4 bl, const EeIO& e) {
   float d[3] = {(bh.x - ah.x) + (bl.x - al.x), (bh.y - ah.y) + (bl.y - al.y), (bh.z - ah.z) + (bl.z - al.z)};
   if (e.periodic) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const float s = rintf(d[c] * e.invL[c]);
+      const float half = 0.5f * e.Lhi[c];
+      const float s = d[c] > half ? 1.f : (d[c] < -half ? -1.f : 0.f);
       d[c] = fmaf(-s, e.Llo[c], fmaf(-s, e.Lhi[c], d[c]));
     }
   }
   return make_float3(d[0], d[1], d[2]);
+}
+
+// x wrapped into [0, L) in FP64 (periodic axes), then split into hi + lo
+__device__ __forceinline__ void wrap_split(double x, int c, const EeIO& e, float& hi, float& lo) {
+  if (e.periodic) {
+    x -= e.L[c] * floor(x * e.invL[c]);
+    if (x < 0.0) x += e.L[c];
+    if (x >= e.L[c]) x -= e.L[c];
+  }
+  split2(x, hi, lo);
 }
 
 }  // namespace
@@ -69,14 +81,14 @@ __global__ void k_ee_prep(const EvalIO* __restrict__ io, EvalIO* __restrict__ io
   for (long long j = tid; j < m; j += stride) {
     float h[3], l[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) split2(e.mm_pos[3 * j + c], h[c], l[c]);
+    for (int c = 0; c < 3; ++c) wrap_split(e.mm_pos[3 * j + c], c, e, h[c], l[c]);
     e.mm_hi[j] = make_float4(h[0], h[1], h[2], (float)e.mm_q[j]);
     e.mm_lo[j] = make_float4(l[0], l[1], l[2], 0.f);
   }
   for (long long a = tid; a < n; a += stride) {
     float h[3], l[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) split2(io->pos[3 * a + c], h[c], l[c]);
+    for (int c = 0; c < 3; ++c) wrap_split(io->pos[3 * a + c], c, e, h[c], l[c]);
     e.ml_hi[a] = make_float4(h[0], h[1], h[2], 0.f);
     e.ml_lo[a] = make_float4(l[0], l[1], l[2], 0.f);
     e.V[a] = 0.0;
@@ -109,6 +121,7 @@ __global__ void __launch_bounds__(kEeThreads) k_ee_potential(const EvalIO* __res
     }
     __syncthreads();
     if (live) {
+#pragma unroll 4
       for (int k = 0; k < nt; ++k) {
         const float3 d = disp(ah, al, sh[k], sl[k], e);
         const float r2 = fmaf(d.z, d.z, fmaf(d.y, d.y, d.x * d.x));
@@ -127,7 +140,17 @@ __global__ void __launch_bounds__(kEeThreads) k_ee_potential(const EvalIO* __res
     atomicAdd(&e.field[3 * a], kCoulomb * (double)fx);
     atomicAdd(&e.field[3 * a + 1], kCoulomb * (double)fy);
     atomicAdd(&e.field[3 * a + 2], kCoulomb * (double)fz);
-    atomicAdd(&e.sums[1], kCoulomb * (double)v);
+  }
+  // sum of V over the block, then one add per block (one address is shared by all blocks)
+  __shared__ double red[kEeThreads / 32];
+  double vs = (live && j1 > j0) ? kCoulomb * (double)v : 0.0;
+  for (int o = 16; o; o >>= 1) vs += __shfl_xor_sync(0xffffffffu, vs, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = vs;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < kEeThreads / 32; ++k) t += red[k];
+    if (t != 0.0) atomicAdd(&e.sums[1], t);
   }
 }
 
@@ -139,6 +162,7 @@ __global__ void k_ee_combine(const EvalIO* __restrict__ io, const EeIO* __restri
   const int rows = ws.seg[e.S];
   const double vbar = e.sums[1] / (double)n;
   const long long total = (long long)rows * D;
+  double qsum = 0.0;  // this thread's raw charges; one add per block below
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const int row = (int)(t / D), f = (int)(t - (long long)row * D);
@@ -149,8 +173,17 @@ __global__ void k_ee_combine(const EvalIO* __restrict__ io, const EeIO* __restri
     if (f == 0) {
       const double q = (double)e.q_rows[row];
       e.q_atom[a] = q;
-      atomicAdd(&e.sums[2], q);
+      qsum += q;
     }
+  }
+  __shared__ double red[32];
+  for (int o = 16; o; o >>= 1) qsum += __shfl_xor_sync(0xffffffffu, qsum, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = qsum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    if (t != 0.0) atomicAdd(&e.sums[2], t);
   }
 }
 
@@ -204,6 +237,7 @@ __global__ void __launch_bounds__(kEeThreads) k_ee_mm_forces(const EvalIO* __res
     }
     __syncthreads();
     if (live) {
+#pragma unroll 4
       for (int k = 0; k < nt; ++k) {
         const float3 d = disp(sh[k], sl[k], bh, bl, e);  // r_J - r_i
         const float r2 = fmaf(d.z, d.z, fmaf(d.y, d.y, d.x * d.x));
@@ -235,7 +269,7 @@ int nnp_ctx::launch_ee_pre(long long rows, const Workspace& w, int& launches) {
   const long long n = ee_n_ml, m = ee_n_mm;
   k_ee_prep<<<ee_grid(std::max(n, m), 256, nsm * 4), 256, 0, stream>>>(d_io, d_io_q, d_ee); ++launches;
   const int bx = (int)((n + kEeThreads - 1) / kEeThreads);
-  long long by = (2LL * nsm + bx - 1) / bx;
+  long long by = (8LL * nsm + bx - 1) / bx;  // enough blocks to hide the pair loop's latency
   by = std::max(1LL, std::min(by, (m + kEeTile - 1) / kEeTile));
   k_ee_potential<<<dim3(bx, (unsigned)by), kEeThreads, 0, stream>>>(d_io, d_ee); ++launches;
   // charge network: per-row outputs and dq/dG into the embedding's buffers
@@ -283,7 +317,8 @@ extern "C" int nnp_eval_ee(nnp_ctx* ctx, int64_t n, const double* pos, const int
   if (!std::isfinite(total_charge)) return ctx->fail(NNP_ERR_INVALID_ARG, "non-finite total charge");
   if (!ctx->charges_ready()) return ctx->fail(NNP_ERR_NO_WEIGHTS, "charge-network weights missing for some species");
   int periodic = 0;
-  float Lhi[3] = {0.f, 0.f, 0.f}, Llo[3] = {0.f, 0.f, 0.f}, invL[3] = {0.f, 0.f, 0.f};
+  float Lhi[3] = {0.f, 0.f, 0.f}, Llo[3] = {0.f, 0.f, 0.f};
+  double Ld[3] = {0.0, 0.0, 0.0}, invL[3] = {0.0, 0.0, 0.0};
   if (box) {
     for (int r = 0; r < 3; ++r)
       for (int c = 0; c < 3; ++c)
@@ -295,7 +330,8 @@ extern "C" int nnp_eval_ee(nnp_ctx* ctx, int64_t n, const double* pos, const int
       if (!(L > 0.0)) return ctx->fail(NNP_ERR_INVALID_ARG, "box edge %d is %g", c, L);
       Lhi[c] = (float)L;
       Llo[c] = (float)(L - (double)Lhi[c]);
-      invL[c] = (float)(1.0 / L);
+      Ld[c] = L;
+      invL[c] = 1.0 / L;
     }
   }
   const long long m = std::max<long long>(n_mm, 1);
@@ -306,6 +342,7 @@ extern "C" int nnp_eval_ee(nnp_ctx* ctx, int64_t n, const double* pos, const int
   for (int c = 0; c < 3; ++c) {
     h.Lhi[c] = Lhi[c];
     h.Llo[c] = Llo[c];
+    h.L[c] = Ld[c];
     h.invL[c] = invL[c];
   }
   cudaStream_t st = ctx->stream;

@@ -141,7 +141,8 @@ struct EeIO {
   double Q;               // total charge of the ML atoms
   int S;                  // species (rows = seg[S])
   int periodic;           // orthorhombic minimum image
-  float Lhi[3], Llo[3], invL[3];
+  float Lhi[3], Llo[3];    // box edges as FP32 hi + lo
+  double L[3], invL[3];    // and in FP64 (coordinates are wrapped into [0, L))
   float4 *mm_hi, *mm_lo;  // MM coordinates as FP32 hi + lo, charge in mm_hi.w
   float4 *ml_hi, *ml_lo;  // ML coordinates, input order
   double* V;              // n: potential of the MM charges at each ML atom (eV / e)
