@@ -15,14 +15,16 @@
 
 namespace nnp {
 
-__global__ void k_bin(const EvalIO* __restrict__ io, const SysDesc* __restrict__ sys,
-                      const signed char* __restrict__ zlut, Workspace ws) {
+// The four binning steps are device functions over (first thread, thread
+// stride), so that small systems run them in one block (k_cells_small) and
+// large ones as four grid-wide kernels.
+__device__ __forceinline__ void bin_atoms(const EvalIO* __restrict__ io, const SysDesc* __restrict__ sys,
+                                          const signed char* __restrict__ zlut, const Workspace& ws,
+                                          long long tid0, long long stride) {
   const long long n = io->n_atoms;
   const int TC = io->total_cells;
   const int nsys = io->n_sys;
-  const long long tid0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  if (tid0 < nsys) io->energies[tid0] = 0.0;
+  for (long long q = tid0; q < nsys; q += stride) io->energies[q] = 0.0;
   for (long long a = tid0; a < n; a += stride) {
     int lo = 0, hi = nsys - 1;
     while (lo < hi) {
@@ -91,11 +93,16 @@ __global__ void k_bin(const EvalIO* __restrict__ io, const SysDesc* __restrict__
   }
 }
 
-// Single CTA of 1024 threads.  bin_start[b] = first row of bin b, with each
+__global__ void k_bin(const EvalIO* __restrict__ io, const SysDesc* __restrict__ sys,
+                      const signed char* __restrict__ zlut, Workspace ws) {
+  bin_atoms(io, sys, zlut, ws, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+}
+
+// One block of 1024 threads.  bin_start[b] = first row of bin b, with each
 // species segment starting on a multiple of kTileRows; bin_len keeps counts.
-__global__ void __launch_bounds__(1024) k_scan(const EvalIO* __restrict__ io, int S, Workspace ws) {
+__device__ __forceinline__ void scan_bins(const EvalIO* __restrict__ io, int S, const Workspace& ws,
+                                          int* s_bins /* [kScanSmemBins] shared */) {
   constexpr int kReg = 16;  // bins per thread (up to kScanSmemBins bins go through shared memory)
-  extern __shared__ int s_bins[];  // [kScanSmemBins]: counts, then raw starts
   __shared__ int warp_tot[32];
   __shared__ long long seg_s[kMaxS + 2];
   __shared__ int raw_at_species[kMaxS + 1];
@@ -231,26 +238,35 @@ __global__ void __launch_bounds__(1024) k_scan(const EvalIO* __restrict__ io, in
   }
 }
 
-__global__ void k_scatter(const EvalIO* __restrict__ io, Workspace ws) {
+__global__ void __launch_bounds__(1024) k_scan(const EvalIO* __restrict__ io, int S, Workspace ws) {
+  extern __shared__ int s_bins[];  // [kScanSmemBins]: counts, then raw starts
+  scan_bins(io, S, ws, s_bins);
+}
+
+__device__ __forceinline__ void scatter_atoms(const EvalIO* __restrict__ io, const Workspace& ws, long long tid0,
+                                              long long stride) {
   const long long n = io->n_atoms;
-  for (long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x; a < n;
-       a += (long long)gridDim.x * blockDim.x) {
+  for (long long a = tid0; a < n; a += stride) {
     const int row = ws.bin_start[ws.atom_bin[a]] + ws.atom_slot[a];
     ws.row_atom[row] = (int)a;
   }
+}
+
+__global__ void k_scatter(const EvalIO* __restrict__ io, Workspace ws) {
+  scatter_atoms(io, ws, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
 // Warp per bin: order the bin's atoms by input index (ranks by comparison),
 // then write the row arrays.  Bins with more than kSortCap atoms keep slot
 // order (flagged; results stay correct, only summation order differs).
 constexpr int kSortCap = 256;
-__global__ void __launch_bounds__(256) k_binsort(const EvalIO* __restrict__ io, int S, int sort,
-                                                 Workspace ws) {
-  __shared__ int sm[8][kSortCap];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+// warp0: this warp's first bin, wstride: warps over all bins, sw: the warp's
+// kSortCap ints of shared memory
+__device__ __forceinline__ void sort_bins(const EvalIO* __restrict__ io, int S, int sort, const Workspace& ws,
+                                          int warp0, int wstride, int* sw) {
+  const int lane = threadIdx.x & 31;
   const int nb = S * io->total_cells;
-  for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb;
-       b += (gridDim.x * blockDim.x) >> 5) {
+  for (int b = warp0; b < nb; b += wstride) {
     const int start = ws.bin_start[b];
     const int cnt = ws.bin_len[b];
     if (lane == 0) ws.bin_count[b] = 0;  // ready for the next evaluation
@@ -258,12 +274,12 @@ __global__ void __launch_bounds__(256) k_binsort(const EvalIO* __restrict__ io, 
     const bool do_sort = sort && cnt <= kSortCap;
     if (sort && !do_sort && lane == 0) atomicOr(&ws.flags[kFlagBinOverflow], 1);
     if (do_sort) {
-      for (int k = lane; k < cnt; k += 32) sm[w][k] = ws.row_atom[start + k];
+      for (int k = lane; k < cnt; k += 32) sw[k] = ws.row_atom[start + k];
       __syncwarp();
       for (int k = lane; k < cnt; k += 32) {
-        const int a = sm[w][k];
+        const int a = sw[k];
         int rank = 0;
-        for (int q = 0; q < cnt; ++q) rank += sm[w][q] < a;
+        for (int q = 0; q < cnt; ++q) rank += sw[q] < a;
         const int row = start + rank;
         ws.row_atom[row] = a;
       }
@@ -278,6 +294,30 @@ __global__ void __launch_bounds__(256) k_binsort(const EvalIO* __restrict__ io, 
     }
     __syncwarp();
   }
+}
+
+__global__ void __launch_bounds__(256) k_binsort(const EvalIO* __restrict__ io, int S, int sort,
+                                                 Workspace ws) {
+  __shared__ int sm[8][kSortCap];
+  const int w = threadIdx.x >> 5;
+  sort_bins(io, S, sort, ws, (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5),
+            (int)((gridDim.x * blockDim.x) >> 5), sm[w]);
+}
+
+// Small systems: the four steps in one block of 1024 threads, block barriers
+// between them (global writes of the block are visible after a barrier).
+__global__ void __launch_bounds__(1024) k_cells_small(const EvalIO* __restrict__ io,
+                                                      const SysDesc* __restrict__ sys,
+                                                      const signed char* __restrict__ zlut, int S, int sort,
+                                                      Workspace ws) {
+  extern __shared__ int s_dyn_cells[];  // [kScanSmemBins] scan, then [32][kSortCap] sort
+  bin_atoms(io, sys, zlut, ws, threadIdx.x, 1024);
+  __syncthreads();
+  scan_bins(io, S, ws, s_dyn_cells);
+  __syncthreads();
+  scatter_atoms(io, ws, threadIdx.x, 1024);
+  __syncthreads();
+  sort_bins(io, S, sort, ws, threadIdx.x >> 5, 32, s_dyn_cells + (threadIdx.x >> 5) * kSortCap);
 }
 
 // Warp per cell (grid-stride over the cells of every system).  For each
@@ -703,6 +743,9 @@ size_t neighbors_smem(int win) {
 cudaError_t neighbors_set_smem_limits() {
   cudaError_t e = cudaFuncSetAttribute(k_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(sizeof(int) * kScanSmemBins));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cells_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(int) * kScanSmemBins));
   const int s1 = (int)neighbors_smem(kNbrWin), s2 = (int)neighbors_smem(kNbrWinSmall);
 #define NSM(sb)                                                                                                   \
   if (e == cudaSuccess)                                                                                           \

@@ -168,11 +168,15 @@ int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows,
   CK(cudaStreamIsCapturing(stream, &cs));
   const bool capturing = cs == cudaStreamCaptureStatusActive;
   mark_stage(0, capturing);
-  k_bin<<<g_atoms, 256, 0, stream>>>(io, sys, d_zlut, w); ++launches;
-  k_scan<<<1, 1024, sizeof(int) * kScanSmemBins, stream>>>(io, P.S, w); ++launches;
-  k_scatter<<<g_atoms, 256, 0, stream>>>(io, w); ++launches;
-  k_binsort<<<g_bins, 256, 0, stream>>>(io, P.S, (cfg.flags & NNP_FLAG_NONDETERMINISTIC_BINS) ? 0 : 1,
-                                        w); ++launches;
+  const int sort = (cfg.flags & NNP_FLAG_NONDETERMINISTIC_BINS) ? 0 : 1;
+  if (rows <= kCellsRowsSmall) {  // small systems: the four binning steps in one block
+    k_cells_small<<<1, 1024, sizeof(int) * kScanSmemBins, stream>>>(io, sys, d_zlut, P.S, sort, w); ++launches;
+  } else {
+    k_bin<<<g_atoms, 256, 0, stream>>>(io, sys, d_zlut, w); ++launches;
+    k_scan<<<1, 1024, sizeof(int) * kScanSmemBins, stream>>>(io, P.S, w); ++launches;
+    k_scatter<<<g_atoms, 256, 0, stream>>>(io, w); ++launches;
+    k_binsort<<<g_bins, 256, 0, stream>>>(io, P.S, sort, w); ++launches;
+  }
   mark_stage(1, capturing);
   if (ext_mode) {  // the caller's pair list instead of the cell search
     const int g_rows = grid_for(rows, 256, nsm * 8), g_pairs = nsm * 16;

@@ -14,6 +14,10 @@ __global__ void k_bin(const EvalIO* io, const SysDesc* sys, const signed char* z
 __global__ void k_scan(const EvalIO* io, int S, Workspace ws);
 __global__ void k_scatter(const EvalIO* io, Workspace ws);
 __global__ void k_binsort(const EvalIO* io, int S, int sort, Workspace ws);
+// the four above in one block of 1024 threads (at most kCellsRowsSmall rows);
+// dynamic shared memory sizeof(int) * kScanSmemBins
+__global__ void k_cells_small(const EvalIO* io, const SysDesc* sys, const signed char* zlut, int S, int sort,
+                              Workspace ws);
 // grid: blocks for a warp per cell (systems above kNbrRowsSmall rows); rows and
 // cells (totals over systems) choose the small-system form and its split
 void launch_neighbors(int grid, cudaStream_t st, const EvalIO* io, const SysDesc* sys, const DescParams& P,

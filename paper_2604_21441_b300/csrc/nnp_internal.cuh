@@ -38,6 +38,7 @@ constexpr int kNbrThreads = 128;  // k_neighbors: warp per cell, lane per row
 constexpr int kNbrWin = 512;      // neighbourhood atoms one warp stages per window
 constexpr int kNbrWinSmall = 1024;          // the same for small systems (at most kNbrRowsSmall rows)
 constexpr long long kNbrRowsSmall = 8192;
+constexpr long long kCellsRowsSmall = 1536;  // up to this many rows the binning runs in one block
 constexpr int kNbrChunkStride = 36;       // floats per chunk in shared memory (bank spread)
 constexpr int kMaxD = kNRad * kMaxS + kNAng * kMaxS * (kMaxS + 1) / 2;  // 1280
 __host__ __device__ constexpr int desc_len(int S) { return kNRad * S + kNAng * S * (S + 1) / 2; }

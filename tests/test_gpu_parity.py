@@ -136,14 +136,16 @@ def test_graph_and_direct_launches_agree(P):
     for _ in range(3):
         Eb, Fb = b.eval(s.pos, s.Z, s.box)
         Ea2, Fa2 = a.eval(s.pos, s.Z, s.box)
-        # energies: FP64 sums of per-warp partials; forces: FP32 atomic
-        # reductions, whose order (and last bits) vary from launch to launch
+        # energies: FP64 sums of per-warp partials; forces: FP64 reductions,
+        # whose order (and last bits) vary from launch to launch
         assert abs(Ea2 - Ea) <= 1e-12 * abs(Ea) and np.abs(Fa2 - Fa).max() < 1e-5
         assert abs(Eb - Ea) <= 1e-12 * abs(Ea) and np.abs(Fb - Fa).max() < 1e-5
     Ec, Fc = c.eval(s.pos, s.Z, s.box)
     assert abs(Ec - Ea) <= 1e-7 * abs(Ea) and np.abs(Fc - Fa).max() < 1e-5
     assert a.query("graph_captures") == 1
-    assert a.query("launches_per_eval") >= 8
+    # cells (one block for a system this small), neighbours, descriptor,
+    # network, descriptor backward
+    assert a.query("launches_per_eval") == 5
 
 
 def test_error_codes(P):
