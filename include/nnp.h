@@ -56,7 +56,8 @@ typedef enum {
 
 typedef enum {
     NNP_FP32 = 0, /* FP32 descriptors and FP32 SIMT network (reference form) */
-    NNP_BF16 = 1, /* FP32 descriptors, network on tcgen05 tensor cores in BF16 */
+    NNP_BF16 = 1, /* FP32 descriptors, network on tcgen05 tensor cores in BF16
+                     (ensemble members side by side in one launch) */
     NNP_FP8 = 2   /* as BF16, but the three forward GEMMs in FP8 E4M3 with one static
                      scale per layer and species for activations and one per output
                      column for weights: s_W[n] = max_k |W[k][n]| / 448 at
@@ -96,8 +97,9 @@ typedef enum {
  * The kernels are specialised for n_rad = 16, n_ang_r = 4, n_ang_z = 8,
  * zeta a power of two (<= 64), hidden = {160, 128, 96}, 1 <= S <= 8
  * (S = 7, D = 1008: the H, C, N, O, S, F, Cl element set of ANI-2x); other
- * values give NNP_ERR_UNSUPPORTED.  The BF16 and FP8 forms take S <= 2
- * (D <= 128); nnp_force_match_grad and nnp_eval_noalloc take S <= 4.
+ * values give NNP_ERR_UNSUPPORTED.  The BF16 form takes any S (above D = 128
+ * layer 1 and dE/dG are streamed in chunks); the FP8 form takes S = 2
+ * (D = 128); nnp_force_match_grad and nnp_eval_noalloc take S <= 4.
  */
 typedef struct {
     int32_t n_species;                        /* S */
