@@ -15,8 +15,14 @@ outside the event pair.  `e2e` times nnp_eval with pinned host buffers
 timed region).  Multi-GPU: one independent replica per rank (the path
 needs no exchange), value = all ranks' atom-steps / max rank time.
 
---impl reference times the FP64 CPU oracle (the reference arm of this
-build) on bounded samples of the same workload.
+--impl reference times the FP64 CPU oracle (the reference arm) on bounded
+samples of the same workload.
+
+Output: auxiliary measurements (MD throughput, ML/MM, pair lists,
+ensembles, seven species, electrostatic embedding, the size scan) come first,
+one per line, each starting with "# aux"; the benchmark's JSON line comes
+last, with the two forms' numbers ("forms") and the force-matching gradient
+("force_match") at its end.
 """
 from __future__ import annotations
 
@@ -109,10 +115,20 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# algorithmic work per stage (FP32 operations, FMA = 2), see the design doc
+# algorithmic work per stage (FP32 operations, FMA = 2)
+
+# Per-atom work of the water model (two species, D = 128, 1 g/cm^3) as the
+# scope table of the hot path states it: descriptor forward 35 kFLOP per
+# atom; descriptor backward 8 GFLOP on the 98,304-atom box (about 2.3 times
+# the forward); network forward and backward 106,688 + 106,496 FLOP.
+SCOPE_FLOP_PER_ATOM = {"descriptor": 35.0e3, "descriptor_backward": 8.0e9 / 98304,
+                        "network": 106688.0 + 106496.0}
+
 
 def algorithmic_flops(n_pairs_r, n_triplets, n_rows, D, S):
-    """FP32 work of the descriptor forward / backward and the network."""
+    """FP32 work of the descriptor forward / backward and the network,
+    counted per radial pair and angular triplet from the arithmetic the
+    kernels' formulas need (the instruction-level count)."""
     rad_fwd = n_pairs_r * 16 * 6          # x, x^2*eta, exp, fma per term
     ang_fwd = n_triplets * (32 * 2 + 8 * 9 + 4 * 6)
     rad_bwd = n_pairs_r * 16 * 9
@@ -607,30 +623,87 @@ def oracle_sample(wl, w, seconds=20.0, seed=0):
     return evaluated / t_tot, desc, calls, t_tot
 
 
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_full_omp(wl, w):
+    """One full evaluation of the workload (E and F of every atom of every
+    system) by the OpenMP build of the oracle.  Returns (seconds, threads)."""
+    import oracle
+    p = oracle.Params(atomic_numbers=tuple(wl["atomic_numbers"]))
+    m = oracle.Model(p, w)
+    t0 = time.perf_counter()
+    threads = 1
+    for s in wl["systems"]:
+        threads = oracle.energy_forces_omp(m, s.pos, p.species_of(s.Z), s.box)[3]
+    return time.perf_counter() - t0, threads
+
+
+def oracle_full_serial(wl, w):
+    """One full evaluation of the workload by the single-threaded oracle."""
+    import oracle
+    p = oracle.Params(atomic_numbers=tuple(wl["atomic_numbers"]))
+    m = oracle.Model(p, w)
+    t0 = time.perf_counter()
+    for s in wl["systems"]:
+        oracle.energy_forces(m, s.pos, p.species_of(s.Z), s.box)
+    return time.perf_counter() - t0
+
+
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, same workload,
+    metric and config as the GPU arm.  Each step is one full evaluation of
+    the workload by the OpenMP build of the oracle; if the first one shows
+    that K + W of them would take more than --ref-budget seconds, each step
+    is instead a bounded sample (--ref-seconds of single-threaded sampled
+    atoms in each of the host's cores).  One full single-threaded evaluation
+    is timed after the steps (--serial-full 1)."""
     wl, w, S, D = build_workload(args.workload)
     n = sum(s.n for s in wl["systems"])
-    for k in range(args.warmup):
-        oracle_sample(wl, w, seconds=0.5, seed=1000 + k)
-    vals = []
-    t_all = 0.0
-    descs = []
-    # each step a bounded sample; the whole run stays near two minutes
-    per_step = min(args.ref_seconds, max(1.5, 120.0 / max(1, args.steps)))
-    for k in range(args.steps):
-        v, d, calls, t = oracle_sample(wl, w, seconds=per_step, seed=k)
-        vals.append(v)
-        t_all += t
-        descs.append(d)
-    value = float(np.mean(vals))
+    t_probe, threads = oracle_full_omp(wl, w)
+    full = t_probe * (args.steps + args.warmup - 1) <= args.ref_budget
+    times, evaluated = [], 0
+    if full:
+        for _ in range(args.warmup - 1):
+            oracle_full_omp(wl, w)
+        for _ in range(args.steps):
+            t, _ = oracle_full_omp(wl, w)
+            times.append(t)
+        evaluated = n * args.steps
+        sample = (f"each step one full evaluation (E, F of all {n} atoms) by the OpenMP build of the "
+                  f"oracle over {threads} threads")
+    else:
+        for k in range(args.warmup):
+            oracle_sample(wl, w, seconds=0.5, seed=1000 + k)
+        per_step = min(args.ref_seconds, max(1.5, 120.0 / max(1, args.steps)))
+        for k in range(args.steps):
+            v, d, calls, t = oracle_sample(wl, w, seconds=per_step, seed=k)
+            times.append(t)
+            evaluated += v * t
+        threads = 1
+        sample = (f"each step {per_step:.1f} s of sampled atoms, single-threaded (a full OpenMP "
+                  f"evaluation took {t_probe:.1f} s)")
+    t_all = float(np.sum(times))
+    value = evaluated / t_all
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": n / value * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["name"], "atoms": n, "note": "FP64 CPU oracle, 1 thread"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": descs[0]},
+            "ms_per_step": t_all / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded water boxes, random Xavier weights)",
+            "config": workload_config(wl, args.precision, args.gpus),
+            "cpu_baseline": {"value": r4(value), "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample, "cpu": cpu_model(), "nproc": os.cpu_count()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if args.serial_full:
+        ts = oracle_full_serial(wl, w)
+        line["serial_full_eval"] = {"seconds": r4(ts), "atom_steps_per_s": r4(n / ts), "threads": 1}
     print(json.dumps(line), flush=True)
 
 
@@ -649,6 +722,82 @@ def aggregate_ranks(t_rank, units, world, device):
     return float(tmax.item()), float(tsum.item())
 
 
+def r4(x):
+    """A float rounded to 4 significant digits (keeps the JSON line short)."""
+    return None if x is None else float(f"{x:.4g}")
+
+
+def force_match_rate(steps=20):
+    """Force-matching weight gradient (nnp_force_match_grad, FP32 with FP64
+    sums) on the HCNO workload: 2,000 cluster atoms of H, C, N, O in water,
+    40 A box, 6,134 atoms, D = 384.  The reference forces come from a second,
+    independently seeded network of the same architecture (the teacher),
+    evaluated by the library.  Each call recomputes the forces of the last
+    evaluation, the tangent descriptors, the networks' tangent and adjoint
+    passes and the weight-gradient reductions, and returns the gradient to
+    the host: synchronous calls timed by wall clock, stage durations by CUDA
+    events.  Work per stage (FP32, FMA = 2; the roofline is the FP32 ALU
+    peak): the descriptor kernels' per-pair/per-triplet counts; the networks'
+    primal and tangent forward, 2 x 2 (D*160 + 160*128 + 128*96) per atom, and
+    the two adjoints, 2 x 2 (96*128 + 128*160); the weight gradients,
+    4 (D*160 + 160*128 + 128*96 + 96) per atom."""
+    import torch
+    import synth
+    import paper_2604_21441_b300 as P
+    wl = synth.workload(5)
+    s = wl["systems"][0]
+    Zs = tuple(int(z) for z in wl["atomic_numbers"])
+    S, D = len(Zs), synth.aev_length(len(Zs))
+    f32 = lambda ws: [[(W.astype(np.float32), b.astype(np.float32)) for W, b in x] for x in ws]
+    dev = lambda a: torch.tensor(a, device="cuda")
+    pos, Z = dev(s.pos), dev(s.Z.astype(np.int32))
+    box = np.diag(s.box)
+    teacher = P.NNP(atomic_numbers=Zs, precision="fp32", max_atoms=s.n)
+    teacher.set_all_weights(f32(synth.xavier_weights(S, D, wl["weight_seed"] + 1000)))
+    _, Fref = teacher.eval(pos, Z, box)
+    teacher.close()
+    pot = P.NNP(atomic_numbers=Zs, precision="fp32", max_atoms=s.n, flags=P.FLAG_STAGE_EVENTS)
+    pot.set_all_weights(f32(synth.xavier_weights(S, D, wl["weight_seed"])))
+    pot.eval(pos, Z, box)
+    for _ in range(3):
+        pot.force_match_grad(Fref=Fref)
+    torch.cuda.synchronize()
+    stages = []
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        L, _ = pot.force_match_grad(Fref=Fref, want_loss=True)
+        stages.append(pot.profile_force_match())
+    ms = (time.perf_counter() - t0) * 1e3 / steps
+    pot.close()
+    st = np.mean(np.array(stages), axis=0)
+    names = ("forces", "tangent_descriptors", "networks", "weight_gradients")
+    n_pairs, n_trip = neighbour_stats({"wl": wl})
+    fl_desc, fl_mlp, fl_bwd = algorithmic_flops(n_pairs, n_trip, s.n, D, S)
+    net_fwd = 2 * (D * 160 + 160 * 128 + 128 * 96)
+    work = {"forces": fl_desc + fl_mlp + fl_bwd, "tangent_descriptors": fl_bwd,
+            "networks": s.n * (2 * net_fwd + 2 * 2 * (96 * 128 + 128 * 160)),
+            "weight_gradients": s.n * 4 * (D * 160 + 160 * 128 + 128 * 96 + 96)}
+    stage = dict(zip(names, st.tolist()))
+    dom = max(stage, key=stage.get)
+    peak = alu_peak_tflops()
+    ach = work[dom] / (stage[dom] * 1e-3) / 1e12
+    return {"workload": wl["name"], "atoms": s.n, "species": S, "aev_length": D, "precision": "fp32",
+            "loss": r4(L), "ms_per_gradient": r4(ms), "stage_ms": {k: r4(v) for k, v in stage.items()},
+            "dominant": dom, "achieved_tflops": r4(ach), "peak_tflops": r4(peak), "frac": r4(ach / peak),
+            "bound": "alu"}
+
+
+def alu_peak_tflops(dev=0):
+    """FP32 ALU peak of the device: SMs (read from the device) x 128 FP32
+    lanes x 2 FLOP x the maximum SM clock (MEASURED_PEAKS.json, else the
+    device's own figure)."""
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    pk, _ = peaks()
+    mhz = pk.get("sm_max_mhz") or props.clock_rate / 1e3
+    return props.multi_processor_count * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -658,11 +807,17 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
     ap.add_argument("--compare", default="fp32,bf16,fp8")
     ap.add_argument("--workload", type=int, default=3)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
+    ap.add_argument("--ref-budget", type=float, default=150.0,
+                    help="reference arm: seconds allowed for its full evaluations")
+    ap.add_argument("--serial-full", type=int, default=1,
+                    help="reference arm: also time one full single-threaded evaluation")
     ap.add_argument("--extras", type=int, default=1,
                     help="0: leave out the auxiliary measurements after the JSON line's main step "
-                         "(NVE, ML/MM, pair list, ensembles, seven species), e.g. under a profiler")
+                         "(NVE, ML/MM, pair list, ensembles, seven species, force matching), "
+                         "e.g. under a profiler")
+    ap.add_argument("--out", default=None, help="also write the JSON line and the auxiliary "
+                                                "measurements to this file")
     args = ap.parse_args()
     args.compare = args.compare.split(",")
     args.warmup = max(args.warmup, 3)
@@ -691,26 +846,32 @@ def main():
     # algorithmic work (counted from the workload's neighbour statistics)
     n_pairs, n_trip = neighbour_stats(r)
     fl_desc, fl_mlp, fl_bwd = algorithmic_flops(n_pairs, n_trip, r["n"], r["D"], r["S"])
-    sm_mhz_max = pk.get("sm_max_mhz", 2032.0)
-    alu_peak = 148 * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12  # TFLOP/s FP32
+    alu_peak = alu_peak_tflops(local_rank)
+    n_sm = torch.cuda.get_device_properties(local_rank).multi_processor_count
     work = {"descriptor": (fl_desc, "alu"), "descriptor_backward": (fl_bwd, "alu"),
             "network": (fl_mlp, "tensor" if args.precision != "fp32" else "alu")}
     dom = max(work, key=lambda k: st[k])
-    fl, bound = work[dom]
-    achieved = fl / (st[dom] * 1e-3) / 1e12
+    fl_instr, bound = work[dom]
+    water = r["S"] == 2 and r["wl"]["name"].startswith("water")
+    fl_scope = SCOPE_FLOP_PER_ATOM[dom] * r["n"] if water else None
     if bound == "tensor":
         peak = pk["bf16_tflops"] * (2.0 if args.precision == "fp8" else 1.0)
+        peak_src = f"{pk_kind} cuBLAS bf16 burst" + (" x 2 (fp8)" if args.precision == "fp8" else "")
     else:
         peak = alu_peak
-    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak,
+        peak_src = f"{n_sm} SMs (device) x 128 FP32 lanes x 2 x {pk.get('sm_max_mhz', 2032.0):.0f} MHz"
+    ach_instr = fl_instr / (st[dom] * 1e-3) / 1e12
+    ach = (fl_scope if fl_scope is not None else fl_instr) / (st[dom] * 1e-3) / 1e12
+    roofline = {"bound": bound, "kernel": STAGE_KERNEL.get(dom) or dom, "achieved": r4(ach),
+                "peak": r4(peak), "unit": "TFLOP/s", "frac": r4(ach / peak),
                 "traffic": profiled_traffic(dom, args.precision),
-                "peak_source": (f"{pk_kind} bf16" if bound == "tensor" else
-                                "148 SMs x 128 FP32 lanes x 2 x max SM clock"),
-                "stage_ms": st}
+                "work": ("scope-table count: " + (f"{SCOPE_FLOP_PER_ATOM[dom]:.4g} FLOP/atom x {r['n']} atoms"
+                                                  if fl_scope is not None else "n/a, instruction count used")),
+                "frac_instruction_count": r4(ach_instr / peak),
+                "work_instruction_count": f"{fl_instr:.4g} FLOP (per pair/triplet counts)",
+                "peak_source": peak_src, "stage_ms": {k: r4(v) for k, v in st.items()}}
     # the CPU baseline is timed at N = 1 only (rank 0 of a multi-GPU run skips it)
-    cpu_v, cpu_desc = (oracle_sample(r["wl"], r["w"], seconds=args.cpu_seconds)[:2] if world == 1
-                       else (None, None))
+    cpu = cpu_baseline(r["wl"], r["w"]) if world == 1 else None
     ms_mean = float(np.mean(r["ms"]))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -718,41 +879,67 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else
         ("bf16" if args.precision == "bf16" else "fp8-e4m3"),
         "data": "synthetic (seeded water boxes, random Xavier weights)",
-        "config": {"workload": r["wl"]["name"], "atoms": r["n"], "systems": r["B"],
-                   "species": r["S"], "aev_length": r["D"], "precision": args.precision,
-                   "l2": "flushed (256 MB write) between timed steps, outside the timed events",
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-        "forms": r["forms"],
-        "e2e": {"value": r["e2e"], "unit": UNIT, "ms_per_step": r["e2e_ms"],
+        "config": workload_config(r["wl"], args.precision, world),
+        "e2e": {"value": r4(r["e2e"]), "unit": UNIT, "ms_per_step": r4(r["e2e_ms"]),
                 "h2d_bytes_per_step": r["n"] * (24 + 4), "d2h_bytes_per_step": r["n"] * 24 + 8 * r["B"]},
         "gpu_launches": int(r["launches"]) * args.steps,
-        "autotuned_blocks_per_sm": r["tuned"],
         "clocks": r["clocks"],
         "roofline": roofline,
-        "cpu_baseline": ({"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                          "sample": cpu_desc} if cpu_v is not None else None),
+        "cpu_baseline": cpu,
+        "autotuned": r["tuned"],
     }
+    aux = {}
     if args.workload == 3 and args.extras:  # the paper reports MD throughput in ns/day
-        line["nve"] = nve_rate(args.precision)
-        line["mlmm"] = mlmm_rate(args.precision)
-        line["pairs"] = pairs_rate(args.precision)
+        aux["nve"] = nve_rate(args.precision)
+        aux["mlmm"] = mlmm_rate(args.precision)
+        aux["pairs"] = pairs_rate(args.precision)
         if args.precision != "fp8":
-            line["ensemble"] = ensemble_rate(args.precision)
-        line["seven_species"] = seven_species_rate()
+            aux["ensemble"] = ensemble_rate(args.precision)
+        aux["seven_species"] = seven_species_rate()
         if args.precision != "fp8":
-            line["ee"] = ee_rate(args.precision)
-        line["size_scan"] = size_scan()
+            aux["ee"] = ee_rate(args.precision)
+        aux["size_scan"] = size_scan()
+    if (args.workload in (3, 5)) and args.extras:
+        line["force_match"] = force_match_rate()
     if r["per_system_ms"] is not None:
-        line["batch"] = {"systems": r["B"], "one_graph_launch_ms": ms_mean,
-                         "one_launch_per_system_ms": r["per_system_ms"],
-                         "speedup": r["per_system_ms"] / ms_mean}
+        line["batch"] = {"systems": r["B"], "one_graph_launch_ms": r4(ms_mean),
+                         "one_launch_per_system_ms": r4(r["per_system_ms"]),
+                         "speedup": r4(r["per_system_ms"] / ms_mean)}
+    line["forms"] = {k: {kk: (r4(vv) if isinstance(vv, float) else
+                              ({a: r4(b) for a, b in vv.items()} if isinstance(vv, dict) else vv))
+                         for kk, vv in v.items()} for k, v in r["forms"].items()}
+    for k, v in aux.items():
+        print(f"# aux {k} {json.dumps(v)}", flush=True)
     print(json.dumps(line), flush=True)
+    if args.out:
+        with open(args.out, "w") as f:
+            json.dump({"line": line, "aux": aux}, f, indent=1)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
+def workload_config(wl, precision, world=1):
+    """The JSON line's config block (the same for both arms)."""
+    S = len(wl["atomic_numbers"])
+    return {"workload": wl["name"], "atoms": int(sum(s.n for s in wl["systems"])),
+            "systems": len(wl["systems"]), "species": S, "aev_length": int(16 * S + 16 * S * (S + 1)),
+            "precision": precision,
+            "l2": "flushed (256 MB write) between timed steps, outside the timed events",
+            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}
+
+
+def cpu_baseline(wl, w):
+    """One full evaluation of the workload by the OpenMP build of the oracle
+    over the host's cores (the FP64 oracle's arithmetic, threads over atoms)."""
+    n = sum(s.n for s in wl["systems"])
+    t, threads = oracle_full_omp(wl, w)
+    return {"value": r4(n / t), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"one full evaluation (E, F of all {n} atoms), OpenMP build of the oracle, "
+                      f"{threads} threads, {t:.1f} s", "cpu": cpu_model()}
+
+
 STAGE_KERNEL = {"descriptor": "k_aev_fwd", "descriptor_backward": "k_aev_bwd",
-                "neighbours": "k_neighbors", "network": None}
+                "neighbours": "k_neighbors", "network": None, "cells": None}
 
 
 def profiled_traffic(stage, precision):

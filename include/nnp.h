@@ -99,7 +99,7 @@ typedef enum {
  * (S = 7, D = 1008: the H, C, N, O, S, F, Cl element set of ANI-2x); other
  * values give NNP_ERR_UNSUPPORTED.  The BF16 form takes any S (above D = 128
  * layer 1 and dE/dG are streamed in chunks); the FP8 form takes S = 2
- * (D = 128); nnp_force_match_grad and nnp_eval_noalloc take S <= 4.
+ * (D = 128); nnp_eval_noalloc takes S <= 4.
  */
 typedef struct {
     int32_t n_species;                        /* S */
@@ -222,13 +222,17 @@ int nnp_eval_async(nnp_ctx *ctx, int64_t n, const double *pos, const int32_t *Z,
  *   FP32 contexts of at most 4 species only (else NNP_ERR_UNSUPPORTED;
  *   ensembles are fine).  At most 128 radial and 48
  *   angular neighbours per atom (more: NNP_ERR_CAPACITY, lists do not grow).
- *   Synchronous; runs on the context's stream and leaves the context's own
- *   buffers, graph and last-evaluation state untouched.
+ *   Synchronous: it reads the device flags back and waits for the context's
+ *   stream, so it cannot be called while that stream is being captured.  It
+ *   runs on the context's stream and leaves the context's own buffers, graph
+ *   and last-evaluation state untouched.  A box given as a device pointer is
+ *   rejected (NNP_ERR_INVALID_ARG).
  * All per-call scratch lives in one fixed device array of the library (about
- * 6 MiB), which every GPU that loads the library holds until the process
- * exits.  The first call on a device looks up that array's address; make it
- * before any stream capture.  Every call shares the array: calls that overlap
- * on the GPU (other streams, contexts or threads) race and give wrong results.
+ * 6 MiB).  nnp_create looks up its address on the context's device, which
+ * places the array in that device's memory; it then stays there until the
+ * process exits.  Create the context before handing the GPU's free memory to
+ * another pool.  Every call shares the array: calls that overlap on the GPU
+ * (other streams, contexts or threads) race and give wrong results.
  * The paper has no counterpart of this entry point. */
 int nnp_eval_noalloc(nnp_ctx *ctx, int64_t n, const double *pos, const int32_t *Z,
                      const double *box, double *energy, double *forces);
@@ -254,8 +258,10 @@ int nnp_eval_batch(nnp_ctx *ctx, int32_t B, const int64_t *offsets, const double
 int nnp_eval_batch_async(nnp_ctx *ctx, int32_t B, const int64_t *offsets, const double *pos,
                          const int32_t *Z, const double *boxes, double *energies, double *forces);
 
-/* Number of network parameters: S * sum_l (fan_in*fan_out + fan_out), packed
- * per species as W1 b1 W2 b2 W3 b3 W4 b4 (each W row-major fan_in x fan_out). */
+/* Number of network parameters: M * S * sum_l (fan_in*fan_out + fan_out) for
+ * an ensemble of M members (M = 1 otherwise), packed member by member, within
+ * a member species by species, each as W1 b1 W2 b2 W3 b3 W4 b4 (each W
+ * row-major fan_in x fan_out). */
 int64_t nnp_param_count(const nnp_ctx *ctx);
 
 /* Weight gradient of a force loss L(F) (force matching, the training signal
@@ -268,8 +274,9 @@ int64_t nnp_param_count(const nnp_ctx *ctx);
  *          2 (F - Fref) / (3n), and *loss (if non-NULL) receives L.
  * F and the gradient are computed in the FP32 form (whatever the context's
  * precision) with FP64 sums: directional derivative of the descriptors along
- * v, then forward-over-reverse through the per-element networks.
- * NNP_ERR_UNSUPPORTED for ensembles and for more than 4 species. */
+ * v, then forward-over-reverse through the per-element networks.  For an
+ * ensemble, F is the members' mean and member m's block of grad is the
+ * gradient with respect to the weights given for member m. */
 int nnp_force_match_grad(nnp_ctx *ctx, const double *v, const double *Fref, double *loss,
                          double *grad);
 
@@ -370,6 +377,16 @@ int nnp_query(nnp_ctx *ctx, int32_t key, int64_t *value);
  * NNP_FLAG_STAGE_EVENTS (else NNP_ERR_UNSUPPORTED); waits for the stream.
  * Writes min(n_out, 5) entries. */
 int nnp_profile_stages(nnp_ctx *ctx, double *out, int32_t n_out);
+
+/* Device durations (milliseconds) of the stages of the most recent
+ * nnp_force_match_grad, for profiling: out[k] for stage k in the order
+ * forces (descriptor, networks, descriptor backward, FP32), tangent
+ * descriptors (J_G v), network tangent and adjoint passes (all members),
+ * weight-gradient reductions (all members).  Needs a context created with
+ * NNP_FLAG_STAGE_EVENTS (else NNP_ERR_UNSUPPORTED) and a previous gradient
+ * (else NNP_ERR_NO_STATE); waits for the stream.  Writes min(n_out, 4)
+ * entries. */
+int nnp_profile_force_match(nnp_ctx *ctx, double *out, int32_t n_out);
 
 #ifdef __cplusplus
 }

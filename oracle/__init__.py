@@ -28,6 +28,10 @@ aev_jvp, force_match       : pinned (finite differences in positions and in
 ensemble_energy_forces     : pinned (equals one wider network with
                              block-diagonal hidden layers and the output layer
                              divided by M; M copies of one network equal it)
+ensemble_force_match       : pinned (finite differences of the ensemble loss
+                             in each member's weights; the gradient of the
+                             equivalent wider network, mapped back to the
+                             members' blocks)
 ee_energy_forces           : pinned (one ML atom and one MM charge: the
                              closed-form Coulomb pair; zero MM charges give
                              the plain NNP; total charge conserved; the total
@@ -56,13 +60,25 @@ MAX_SHF = 32
 MAX_LAYERS = 8
 
 
+_SRC_OMP = os.path.join(_HERE, "nnp_oracle_omp.c")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+
+
 def build(force: bool = False) -> str:
-    """Compile nnp_oracle.c into liboracle.so (no fast-math: FP64 as written)."""
+    """Compile nnp_oracle.c into liboracle.so (no fast-math: FP64 as written),
+    and the OpenMP build of the same source (liboracle_omp.so, used only to
+    time the CPU baseline)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-shared",
                                "-fPIC", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_OMP))
+    if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < newest:
+        tmp = _LIB_OMP + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fopenmp", "-shared",
+                               "-fPIC", "-o", tmp, _SRC_OMP, "-lm"])
+        os.replace(tmp, _LIB_OMP)
     return _LIB
 
 
@@ -346,6 +362,56 @@ def ensemble_energy_forces(models, pos, species, box):
         e, ei, f, _ = energy_forces(m, pos, species, box)
         E, Ei, F = E + e, Ei + ei, F + f
     return E / M, Ei / M, F / M
+
+
+_lib_omp = None
+
+
+def energy_forces_omp(model: Model, pos, species, box):
+    """energy_forces computed by the OpenMP build of the same source (all
+    host cores unless OMP_NUM_THREADS says otherwise): the per-atom work is
+    the oracle's own, only the energy and force sums are grouped per thread.
+    For timing the CPU baseline.  Returns E, Ei, F, threads."""
+    global _lib_omp
+    if _lib_omp is None:
+        build()
+        L = ctypes.CDLL(_LIB_OMP)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        L.or_energy_forces_omp.argtypes = [ctypes.POINTER(_Model), ctypes.c_int, dp, ip, dp, dp, dp, dp]
+        L.or_omp_threads.restype = ctypes.c_int
+        _lib_omp = L
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    species = np.ascontiguousarray(species, dtype=np.int32)
+    n = pos.shape[0]
+    bx = None if box is None else np.ascontiguousarray(box, dtype=np.float64)
+    E, Ei, F = np.zeros(1), np.zeros(n), np.zeros((n, 3))
+    _lib_omp.or_energy_forces_omp(model.ref, n, _dp(pos), _ip(species), None if bx is None else _dp(bx),
+                                  _dp(E), _dp(Ei), _dp(F))
+    return float(E[0]), Ei, F, int(_lib_omp.or_omp_threads())
+
+
+def ensemble_force_match(models, pos, species, box, Fref):
+    """Force matching of an ensemble of M networks (mean energy, Results on
+    ANI-2x's eight networks; Eq. 2's forces): L = |F - Fref|^2 / (3N) with F
+    the members' mean force, and dL/dtheta for every member's weights.
+
+    The ensemble energy is (1/M) sum_m E_m, so member m's gradient is 1/M
+    times the single-network gradient of E_m taken along the ensemble's
+    v = 2 (F - Fref) / (3N).  force_match of member m with the reference
+    F_m - F + Fref has exactly that v.  Returns L, dW, db (lists over
+    members of per-species per-layer arrays), F."""
+    M = len(models)
+    Fm = [energy_forces(m, pos, species, box)[2] for m in models]
+    F = sum(Fm) / M
+    Fref = np.asarray(Fref, dtype=np.float64)
+    L = float(((F - Fref) ** 2).sum() / (3 * F.shape[0]))
+    dWs, dbs = [], []
+    for m, Fmm in zip(models, Fm):
+        _, dW, db, _ = force_match(m, pos, species, box, Fmm - F + Fref)
+        dWs.append([[x / M for x in sp] for sp in dW])
+        dbs.append([[x / M for x in sp] for sp in db])
+    return L, dWs, dbs, F
 
 
 def weighted_energy_forces(model: Model, pos, species, box, wt):

@@ -42,6 +42,13 @@
 #define OR_MAX_SHF 32
 #define OR_MAX_LAYERS 8
 
+/* Storage class of the network's scratch rows: empty here (plain statics,
+ * single-threaded); the OpenMP build (nnp_oracle_omp.c) makes them
+ * thread-local. */
+#ifndef OR_TLS
+#define OR_TLS
+#endif
+
 typedef struct {
     int n_species;
     int n_rad;     /* radial shifts per neighbour species */
@@ -448,7 +455,7 @@ static double d2celu(double x, double al) { return x > 0.0 ? 0.0 : exp(x / al) /
  * non-NULL, dE_i/dx (the backward pass, Eq. 2's chain rule through the net). */
 double or_mlp(const oracle_model *m, int s, const double *x, double *dx) {
     int L = m->n_layers;
-    static double z[OR_MAX_LAYERS][OR_MAXW], h[OR_MAX_LAYERS + 1][OR_MAXW];
+    static OR_TLS double z[OR_MAX_LAYERS][OR_MAXW], h[OR_MAX_LAYERS + 1][OR_MAXW];
     for (int k = 0; k < m->width[0]; ++k) h[0][k] = x[k];
     for (int l = 0; l < L; ++l) {
         const double *W = m->W[s * OR_MAX_LAYERS + l], *b = m->b[s * OR_MAX_LAYERS + l];
@@ -462,7 +469,7 @@ double or_mlp(const oracle_model *m, int s, const double *x, double *dx) {
     }
     double E = h[L][0];
     if (dx) {
-        static double g[OR_MAXW], gn[OR_MAXW];
+        static OR_TLS double g[OR_MAXW], gn[OR_MAXW];
         g[0] = 1.0; /* dE/dz of the linear output */
         for (int l = L - 1; l >= 0; --l) {
             const double *W = m->W[s * OR_MAX_LAYERS + l];

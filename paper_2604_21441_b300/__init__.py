@@ -41,7 +41,8 @@ ABI_FUNCTIONS = ("nnp_config_init", "nnp_create", "nnp_destroy", "nnp_last_error
                  "nnp_set_weights", "nnp_eval", "nnp_eval_async", "nnp_sync",
                  "nnp_eval_batch", "nnp_param_count", "nnp_force_match_grad", "nnp_query",
                  "nnp_profile_stages", "nnp_atom_energies", "nnp_eval_noalloc", "nnp_eval_mlmm", "nnp_eval_pairs", "nnp_selftest",
-                 "nnp_eval_batch_async", "nnp_set_member_weights", "nnp_set_charge_weights", "nnp_eval_ee")
+                 "nnp_eval_batch_async", "nnp_set_member_weights", "nnp_set_charge_weights", "nnp_eval_ee",
+                 "nnp_profile_force_match")
 
 QUERY = {"launches_per_eval": 0, "nbr_capacity": 1, "ang_capacity": 2, "max_nbr": 3,
          "max_ang": 4, "rows": 5, "graph_captures": 6,
@@ -125,6 +126,8 @@ def lib() -> ctypes.CDLL:
     L.nnp_query.restype = ctypes.c_int
     L.nnp_profile_stages.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32]
     L.nnp_profile_stages.restype = ctypes.c_int
+    L.nnp_profile_force_match.argtypes = [vp, ctypes.POINTER(ctypes.c_double), i32]
+    L.nnp_profile_force_match.restype = ctypes.c_int
     L.nnp_atom_energies.argtypes = [vp, dp]
     L.nnp_atom_energies.restype = ctypes.c_int
     L.nnp_eval_noalloc.argtypes = [vp, i64, dp, dp, dp, dp, dp]
@@ -456,6 +459,13 @@ class NNP:
     def profile_stages(self):
         out = (ctypes.c_double * 5)()
         self._check(self._L.nnp_profile_stages(self._h, out, 5))
+        return list(out)
+
+    def profile_force_match(self):
+        """ms of the last force_match_grad's stages: forces, tangent
+        descriptors, network passes, weight gradients."""
+        out = (ctypes.c_double * 4)()
+        self._check(self._L.nnp_profile_force_match(self._h, out, 4))
         return list(out)
 
 

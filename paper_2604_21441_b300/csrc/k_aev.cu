@@ -1060,7 +1060,7 @@ void launch_aev_jvp(long long rows, int nsm, cudaStream_t st, const SysDesc* sys
                     const Workspace& ws, const double* v, float* dG) {
   const bool z5 = P.zeta_sq == 5;
 #define JVP(s) z5 ? jvp_t<s, 5>(rows, nsm, st, sys, P, ws, v, dG) : jvp_t<s, -1>(rows, nsm, st, sys, P, ws, v, dG)
-  switch (P.S) { NNP_SPECIES_CASES_FM(JVP) }
+  switch (P.S) { NNP_SPECIES_CASES(JVP) }
 #undef JVP
 }
 
@@ -1070,7 +1070,7 @@ cudaError_t aev_set_smem_limits() {
 #define FB(s) BS((k_aev_fwd<s, 5>)); BS((k_aev_fwd<s, -1>)); BS((k_aev_bwd<s, 5>)); BS((k_aev_bwd<s, -1>))
   FB(1); FB(2); FB(3); FB(4); FB(5); FB(6); FB(7); FB(8);
 #define JB(s) BS((k_aev_jvp<s, 5>)); BS((k_aev_jvp<s, -1>))
-  JB(1); JB(2); JB(3); JB(4);
+  JB(1); JB(2); JB(3); JB(4); JB(5); JB(6); JB(7); JB(8);
 #undef JB
 #undef FB
 #undef BS

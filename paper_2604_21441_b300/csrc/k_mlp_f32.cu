@@ -315,9 +315,8 @@ __global__ void __launch_bounds__(256, 1) k_fm_fwd(DescParams P, Workspace ws, M
   float* DH1T = H1T + kH1 * kLDX;
   float* H2T = DH1T + kH1 * kLDX;
   float* DH2T = H2T + kH2 * kLDX;
-  float* Bs = DH2T + kH2 * kLDX;
-  constexpr int kBsN = (D > kH1 ? D : kH1);
-  float* As = Bs + kKC * kBsN;
+  float* Bs = DH2T + kH2 * kLDX;  // [kKC][160]: every product here has N <= 160
+  float* As = Bs + kKC * kH1;
   const float al = P.celu_alpha, inv_al = 1.f / P.celu_alpha;
   const int ntiles = ws.seg[S] / kTM;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -503,18 +502,18 @@ __global__ void __launch_bounds__(256) k_fm_wgrad(DescParams P, const FmJob* __r
       }
     }
     const int i = jbv.i0 + il;
+    const double sc = (double)jbv.scale;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int o = jbv.o0 + ol + k;
-      if (i < fin && o < fout) atomicAdd(&grad[jbv.w_off + (size_t)i * fout + o], -accd[k]);
-      if (jbv.i0 == 0 && il == 0 && o < fout && l < 4) atomicAdd(&grad[jbv.b_off + o], -bacc[k]);
+      if (i < fin && o < fout) atomicAdd(&grad[jbv.w_off + (size_t)i * fout + o], -sc * accd[k]);
+      if (jbv.i0 == 0 && il == 0 && o < fout && l < 4) atomicAdd(&grad[jbv.b_off + o], -sc * bacc[k]);
     }
   }
 }
 
-size_t fm_fwd_smem(int D) {
-  const int bsn = D > kH1 ? D : kH1;
-  return sizeof(float) * ((size_t)(2 * kH1 + 2 * kH2) * kLDX + (size_t)kKC * bsn + (size_t)kKC * kLDX);
+size_t fm_fwd_smem(int /*D*/) {
+  return sizeof(float) * ((size_t)(2 * kH1 + 2 * kH2) * kLDX + (size_t)kKC * kH1 + (size_t)kKC * kLDX);
 }
 size_t fm_rev_smem() {
   return sizeof(float) * ((size_t)(2 * kH3 + 2 * kH2) * kLDX + (size_t)kKC * kH1 + (size_t)kKC * kLDX);
@@ -524,7 +523,7 @@ void launch_fm(int grid, cudaStream_t st, const DescParams& P, const Workspace& 
                const float* dG, float* z, float* dz, float* t, float* p) {
   const size_t sf = fm_fwd_smem(P.D), sr = fm_rev_smem();
 #define FM(s) k_fm_fwd<s><<<grid, 256, sf, st>>>(P, ws, W, dG, z, dz); k_fm_rev<s><<<grid, 256, sr, st>>>(P, ws, W, z, dz, t, p)
-  switch (P.S) { NNP_SPECIES_CASES_FM(FM) }  // at most kMaxSFm species (checked by the caller)
+  switch (P.S) { NNP_SPECIES_CASES(FM) }
 #undef FM
 }
 
@@ -552,11 +551,14 @@ cudaError_t mlp_f32_set_smem_limits() {
                                     (int)mlp_f32_smem(desc_len(s))); if (e) return e
   MSM(1); MSM(2); MSM(3); MSM(4); MSM(5); MSM(6); MSM(7); MSM(8);
 #undef MSM
-  const int Ds[4] = {48, 128, 240, 384};
-  const void* fwd[4] = {(const void*)k_fm_fwd<1>, (const void*)k_fm_fwd<2>, (const void*)k_fm_fwd<3>, (const void*)k_fm_fwd<4>};
-  const void* rev[4] = {(const void*)k_fm_rev<1>, (const void*)k_fm_rev<2>, (const void*)k_fm_rev<3>, (const void*)k_fm_rev<4>};
-  for (int q = 0; q < 4; ++q) {
-    e = cudaFuncSetAttribute(fwd[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fm_fwd_smem(Ds[q])); if (e) return e;
+  const void* fwd[kMaxS] = {(const void*)k_fm_fwd<1>, (const void*)k_fm_fwd<2>, (const void*)k_fm_fwd<3>,
+                            (const void*)k_fm_fwd<4>, (const void*)k_fm_fwd<5>, (const void*)k_fm_fwd<6>,
+                            (const void*)k_fm_fwd<7>, (const void*)k_fm_fwd<8>};
+  const void* rev[kMaxS] = {(const void*)k_fm_rev<1>, (const void*)k_fm_rev<2>, (const void*)k_fm_rev<3>,
+                            (const void*)k_fm_rev<4>, (const void*)k_fm_rev<5>, (const void*)k_fm_rev<6>,
+                            (const void*)k_fm_rev<7>, (const void*)k_fm_rev<8>};
+  for (int q = 0; q < kMaxS; ++q) {
+    e = cudaFuncSetAttribute(fwd[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fm_fwd_smem(desc_len(q + 1))); if (e) return e;
     e = cudaFuncSetAttribute(rev[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fm_rev_smem()); if (e) return e;
   }
   return e;

@@ -638,6 +638,7 @@ int nnp_create(const nnp_config* cfg, nnp_ctx** out) {
   c->n_members = members;
   c->has_charges = (cfg->flags & NNP_FLAG_CHARGES) != 0;
   int rc = c->init_device();
+  if (!rc) rc = noalloc_prepare(c);
   if (rc) {
     g_create_error = c->err;
     delete c;
@@ -766,7 +767,7 @@ int nnp_eval_batch_async(nnp_ctx* ctx, int32_t B, const int64_t* offsets, const 
 int64_t nnp_param_count(const nnp_ctx* ctx) {
   if (!ctx) return -1;
   const int64_t D = ctx->P.D;
-  return (int64_t)ctx->P.S * (D * kH1 + kH1 + kH1 * kH2 + kH2 + kH2 * kH3 + kH3 + kH3 + 1);
+  return (int64_t)ctx->n_members * ctx->P.S * (D * kH1 + kH1 + kH1 * kH2 + kH2 + kH2 * kH3 + kH3 + kH3 + 1);
 }
 
 int nnp_force_match_grad(nnp_ctx* ctx, const double* v, const double* Fref, double* loss, double* grad) {
@@ -827,6 +828,12 @@ int nnp_selftest(nnp_ctx* ctx, int32_t test) {
   if (e != cudaSuccess) return ctx->cuda_fail(e, "nnp_selftest");
   if (f[kFlagTimeout]) return ctx->fail(NNP_ERR_TIMEOUT, "self-test: the bounded wait expired and returned, as designed");
   return ctx->fail(NNP_ERR_CUDA, "self-test: a wait on a barrier that nothing completes did not time out");
+}
+
+int nnp_profile_force_match(nnp_ctx* ctx, double* out, int32_t n_out) {
+  if (!ctx) return NNP_ERR_INVALID_ARG;
+  if (!out || n_out < 0) return ctx->fail(NNP_ERR_INVALID_ARG, "null output");
+  return ctx->profile_force_match(out, n_out);
 }
 
 int nnp_profile_stages(nnp_ctx* ctx, double* out, int32_t n_out) {

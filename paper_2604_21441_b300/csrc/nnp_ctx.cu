@@ -110,6 +110,8 @@ nnp_ctx::~nnp_ctx() {
   if (h_ee) cudaFreeHost(h_ee);
   for (auto& ev : stage_ev)
     if (ev) cudaEventDestroy(ev);
+  for (auto& ev : fm_ev)
+    if (ev) cudaEventDestroy(ev);
   for (auto& sg : stages) {
     if (sg.io) cudaFreeHost(sg.io);
     if (sg.sys) cudaFreeHost(sg.sys);
@@ -210,15 +212,22 @@ static cudaError_t grow_buf(T*& p, size_t& cap, size_t need) {
   return e;
 }
 
+// Force matching (Eq. 2's forces as a training signal).  For an ensemble
+// of M members, E = sum_m E_m with each member's output layer stored divided
+// by M, so dL/dtheta_m is the single-network formula applied to member m's
+// stored network (its output weights' gradient scaled by 1/M, the ratio of
+// stored to given weights); the loss's v = dL/dF comes from the ensemble's F.
 int nnp_ctx::force_match_grad(const double* v, const double* Fref, double* loss, double* grad) {
-  if (n_members > 1) return fail(NNP_ERR_UNSUPPORTED, "force matching takes one network per species");
-  if (P.S > kMaxSFm) return fail(NNP_ERR_UNSUPPORTED, "force matching supports at most %d species", kMaxSFm);
   if (!has_state) return fail(NNP_ERR_NO_STATE, "nnp_force_match_grad needs a previous nnp_eval");
   if (!grad) return fail(NNP_ERR_INVALID_ARG, "null gradient output");
   if (!v && !Fref) return fail(NNP_ERR_INVALID_ARG, "pass v = dL/dF or the reference forces");
   const long long n = last_n, rows = last_rows;
   const int D = P.D;
   const size_t npar = (size_t)nnp_param_count(this);
+  const size_t per_member = npar / (size_t)n_members;
+  const bool prof = stage_ev[0] != nullptr;
+  if (prof && !fm_ev[0])
+    for (auto& ev : fm_ev) CK(cudaEventCreate(&ev));
   CK(cudaStreamSynchronize(stream));
   CK(grow_buf(fm_z, fm_cap, (size_t)rows * 384));
   CK(grow_buf(fm_dz, fm_cap2, (size_t)rows * 384));
@@ -228,6 +237,7 @@ int nnp_ctx::force_match_grad(const double* v, const double* Fref, double* loss,
   CK(grow_buf(fm_ref, fm_refcap, (size_t)n * 3));
   CK(grow_buf(fm_grad, fm_gcap, npar + 1));  // last entry: loss
   const Workspace w = workspace();
+  if (prof) CK(cudaEventRecord(fm_ev[0], stream));
   // 1. FP32 forces of the last evaluated configuration into internal buffers
   EvalIO io = *h_io;
   io.forces = b_F_stage;
@@ -238,8 +248,10 @@ int nnp_ctx::force_match_grad(const double* v, const double* Fref, double* loss,
   CK(cudaMemsetAsync(b_E_stage, 0, sizeof(double) * last_B, stream));
   launch_aev_fwd(rows, num_sms, stream, b_sys, P, w, 0);
   const int g_tiles = (int)std::max<long long>(1, std::min<long long>(rows / 64, (long long)num_sms));
-  launch_mlp_f32(g_tiles, stream, d_io, P, w, wf32);
+  for (int m = 0; m < n_members; ++m)  // members add up their E_i and dE/dG
+    launch_mlp_f32(g_tiles, stream, d_io, P, w, wf32m[(size_t)m], m > 0 ? 1 : 0);
   launch_aev_bwd(rows, num_sms, stream, d_io, b_sys, P, w);
+  if (prof) CK(cudaEventRecord(fm_ev[1], stream));
   // 2. v = dL/dF (given, or from the reference forces)
   double* lossd = fm_grad + npar;
   CK(cudaMemsetAsync(fm_grad, 0, sizeof(double) * (npar + 1), stream));
@@ -257,37 +269,49 @@ int nnp_ctx::force_match_grad(const double* v, const double* Fref, double* loss,
   }
   // 3. tangent descriptors dG = J_G v (into the dE/dG buffer)
   launch_aev_jvp(rows, num_sms, stream, b_sys, P, w, fm_v, b_dEdG);
-  // 4. network: primal + tangent forward, reverse adjoints
-  launch_fm(g_tiles, stream, P, w, wf32, b_dEdG, fm_z, fm_dz, fm_t, fm_p);
-  // 5. weight-gradient jobs per species, layer, 32 x 32 tile and row segment
+  if (prof) CK(cudaEventRecord(fm_ev[2], stream));
+  // weight-gradient jobs per member, species, layer, 32 x 32 tile and
+  // 2,048-row segment (the segment bounds are the last evaluation's)
   int seg[kMaxS + 2];
   CK(cudaMemcpyAsync(seg, b_seg, sizeof(seg), cudaMemcpyDeviceToHost, stream));
   CK(cudaStreamSynchronize(stream));
   std::vector<FmJob> jobs;
   const int fin[4] = {D, kH1, kH2, kH3}, fout[4] = {kH1, kH2, kH3, 1};
-  const size_t per = npar / P.S;
-  for (int sp = 0; sp < P.S; ++sp) {
-    size_t off = per * sp;
-    size_t woff[4], boff[4];
-    for (int l = 0; l < 4; ++l) {
-      woff[l] = off;
-      off += (size_t)fin[l] * fout[l];
-      boff[l] = off;
-      off += fout[l];
+  const size_t per = per_member / P.S;
+  for (int m = 0; m < n_members; ++m)
+    for (int sp = 0; sp < P.S; ++sp) {
+      size_t off = per_member * m + per * sp;
+      size_t woff[4], boff[4];
+      for (int l = 0; l < 4; ++l) {
+        woff[l] = off;
+        off += (size_t)fin[l] * fout[l];
+        boff[l] = off;
+        off += fout[l];
+      }
+      for (int r0 = seg[sp]; r0 < seg[sp + 1]; r0 += 2048) {
+        const int r1 = std::min(seg[sp + 1], r0 + 2048);
+        for (int l = 0; l < 4; ++l)
+          for (int i0 = 0; i0 < fin[l]; i0 += 32)
+            for (int o0 = 0; o0 < fout[l]; o0 += 32)
+              jobs.push_back(FmJob{l + 1, i0, o0, r0, r1, l == 3 ? 1.0f / (float)n_members : 1.0f,
+                                   (long long)woff[l], (long long)boff[l]});
+      }
     }
-    for (int r0 = seg[sp]; r0 < seg[sp + 1]; r0 += 2048) {
-      const int r1 = std::min(seg[sp + 1], r0 + 2048);
-      for (int l = 0; l < 4; ++l)
-        for (int i0 = 0; i0 < fin[l]; i0 += 32)
-          for (int o0 = 0; o0 < fout[l]; o0 += 32)
-            jobs.push_back(FmJob{l + 1, i0, o0, r0, r1, (long long)woff[l], (long long)boff[l]});
-    }
-  }
   CK(grow_buf(fm_jobs, fm_jcap, jobs.size() + 1));
   CK(cudaMemcpyAsync(fm_jobs, jobs.data(), sizeof(FmJob) * jobs.size(), cudaMemcpyHostToDevice, stream));
-  launch_fm_wgrad(std::max(1, std::min((int)jobs.size(), num_sms * 8)), stream, P, fm_jobs, (int)jobs.size(),
-                  b_G, b_dEdG, fm_z, fm_dz, fm_t, fm_p, fm_grad);
+  const int jobs_per_member = (int)jobs.size() / n_members;
+  for (int m = 0; m < n_members; ++m) {
+    // 4. member m's network: primal + tangent forward, reverse adjoints
+    launch_fm(g_tiles, stream, P, w, wf32m[(size_t)m], b_dEdG, fm_z, fm_dz, fm_t, fm_p);
+    if (prof) CK(cudaEventRecord(fm_ev[3 + 2 * m], stream));
+    // 5. its weight-gradient jobs (they read the buffers step 4 wrote)
+    launch_fm_wgrad(std::max(1, std::min(jobs_per_member, num_sms * 8)), stream, P,
+                    fm_jobs + (size_t)m * jobs_per_member, jobs_per_member, b_G, b_dEdG, fm_z, fm_dz, fm_t,
+                    fm_p, fm_grad);
+    if (prof) CK(cudaEventRecord(fm_ev[4 + 2 * m], stream));
+  }
   CK(cudaGetLastError());
+  fm_profiled_members = prof ? n_members : 0;
   // 6. results
   CK(cudaMemcpyAsync(grad, fm_grad, sizeof(double) * npar,
                      is_device(grad) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream));
@@ -298,6 +322,31 @@ int nnp_ctx::force_match_grad(const double* v, const double* Fref, double* loss,
     *loss = Fref ? lh : 0.0;
   }
   CK(cudaStreamSynchronize(stream));
+  return NNP_OK;
+}
+
+// Stage durations of the last nnp_force_match_grad: forces, tangent
+// descriptors, networks (all members), weight gradients (all members).
+int nnp_ctx::profile_force_match(double* out, int n_out) {
+  if (!stage_ev[0]) return fail(NNP_ERR_UNSUPPORTED, "context was created without NNP_FLAG_STAGE_EVENTS");
+  if (fm_profiled_members <= 0) return fail(NNP_ERR_NO_STATE, "no force-matching gradient to profile");
+  const int M = fm_profiled_members;
+  CK(cudaEventSynchronize(fm_ev[2 + 2 * M]));
+  double t[4] = {0.0, 0.0, 0.0, 0.0};
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, fm_ev[0], fm_ev[1]));
+  t[0] = ms;
+  CK(cudaEventElapsedTime(&ms, fm_ev[1], fm_ev[2]));
+  t[1] = ms;
+  for (int m = 0; m < M; ++m) {
+    // member m's network starts where the previous member's jobs ended (the
+    // first after the tangent descriptors and the host's job list)
+    CK(cudaEventElapsedTime(&ms, m == 0 ? fm_ev[2] : fm_ev[2 + 2 * m], fm_ev[3 + 2 * m]));
+    t[2] += ms;
+    CK(cudaEventElapsedTime(&ms, fm_ev[3 + 2 * m], fm_ev[4 + 2 * m]));
+    t[3] += ms;
+  }
+  for (int k = 0; k < 4 && k < n_out; ++k) out[k] = t[k];
   return NNP_OK;
 }
 

@@ -65,6 +65,7 @@ namespace nnp {
 int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t st, long long rows, int m0, int nm, int accm,
                   const EvalIO* io = nullptr, const Workspace* ws = nullptr);
 int mlp_tc_init(nnp_ctx* ctx);
+int noalloc_prepare(nnp_ctx* ctx);  // nnp_create: scratch address and kernels of nnp_eval_noalloc
 int mlp_tc_set_weights(nnp_ctx* ctx, int member, int species, const float* host_blob);
 int launch_fp8_calib(nnp_ctx* ctx, cudaStream_t st, long long rows);
 void mlp_tc_free(nnp_ctx* ctx);
@@ -192,6 +193,10 @@ struct nnp_ctx {
 
   // stage events (NNP_FLAG_STAGE_EVENTS)
   cudaEvent_t stage_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  // force matching: start, forces, tangent descriptors, then per member the
+  // end of its network pass and of its weight-gradient jobs
+  cudaEvent_t fm_ev[3 + 2 * NNP_MAX_MEMBERS] = {};
+  int fm_profiled_members = 0;
   void mark_stage(int k, bool capturing);
 
   // graph
@@ -226,4 +231,5 @@ struct nnp_ctx {
   int set_weights(int member, int species, const float* const W[4], const float* const b[4]);
   int force_match_grad(const double* v, const double* Fref, double* loss, double* grad);
   int profile_stages(double* out, int n_out);
+  int profile_force_match(double* out, int n_out);
 };

@@ -42,7 +42,6 @@ constexpr long long kCellsRowsSmall = 1536;  // up to this many rows the binning
 constexpr int kNbrChunkStride = 36;       // floats per chunk in shared memory (bank spread)
 constexpr int kMaxD = kNRad * kMaxS + kNAng * kMaxS * (kMaxS + 1) / 2;  // 1280
 __host__ __device__ constexpr int desc_len(int S) { return kNRad * S + kNAng * S * (S + 1) / 2; }
-constexpr int kMaxSFm = 4;     // species of the force-matching (second-order) kernels
 
 // switch cases over the species count, CALL(s) with s a constant 1..kMaxS
 #define NNP_SPECIES_CASES(CALL)                                                      \
@@ -54,11 +53,7 @@ constexpr int kMaxSFm = 4;     // species of the force-matching (second-order) k
   case 6: CALL(6); break;                                                            \
   case 7: CALL(7); break;                                                            \
   default: CALL(8); break;
-#define NNP_SPECIES_CASES_FM(CALL)                                                   \
-  case 1: CALL(1); break;                                                            \
-  case 2: CALL(2); break;                                                            \
-  case 3: CALL(3); break;                                                            \
-  default: CALL(4); break;
+
 
 // Error flag words (device): set by kernels, read by the host after sync.
 enum FlagWord {
@@ -198,9 +193,12 @@ struct MlpF32Weights {
 
 // One block of the force-matching weight-gradient reduction: a 32 x 32 tile
 // (i0, o0) of layer l's gradient (l = 4: the output weights), over rows
-// [r0, r1) of one species; w_off / b_off index the packed gradient.
+// [r0, r1) of one species; w_off / b_off index the packed gradient;
+// scale multiplies the job's sums (1/M for an ensemble's output weights,
+// which are stored divided by M).
 struct FmJob {
   int l, i0, o0, r0, r1;
+  float scale;
   long long w_off, b_off;
 };
 

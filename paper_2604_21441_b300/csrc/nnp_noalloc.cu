@@ -15,10 +15,13 @@
 // library's ordinary kernels; only the workspace they are given differs.
 // Weights and model constants come from the context.
 //
-// Host code cannot use the array's name as a device address, so the first
-// call on each device looks the address up with cudaGetSymbolAddress (with
-// that device current) and caches it.  Make that first call before any
-// stream capture.  All calls share the array and it keeps the last call's
+// Host code cannot use the array's name as a device address.  nnp_create
+// looks the address up with cudaGetSymbolAddress (its device current) and
+// caches it per device (noalloc_prepare).  That lookup also loads this file's
+// module, which is when the driver places the array in device memory, and it
+// loads the kernels this entry point launches directly; so an MD engine that
+// creates its context before it takes the GPU's free memory finds the array
+// already in place.  All calls share the array and it keeps the last call's
 // contents: the bin counters are cleared at the start of every call, and
 // calls that overlap on the GPU (from other streams, contexts or threads)
 // race and give wrong results.
@@ -92,6 +95,51 @@ int grid_cap(long long items, int per_block, int cap) {
 // The scratch memory of every nnp_eval_noalloc call on this device.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
+namespace {
+
+// Device address of the scratch array on device `dev` (the current device),
+// looked up once and cached.
+cudaError_t scratch_base(int dev, unsigned char** out) {
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+namespace nnp {
+
+// Called by nnp_create with the context's device current: resolves the
+// scratch array (which loads its module and places the array in device
+// memory) and loads the cell-list kernels that nnp_eval_noalloc launches
+// itself.  The other kernels it launches are loaded by the context's own
+// set-up (their shared-memory limits are set there).
+int noalloc_prepare(nnp_ctx* ctx) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return NNP_OK;  // nnp_eval_noalloc refuses such a device
+  unsigned char* base = nullptr;
+  e = scratch_base(dev, &base);
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+  cudaFuncAttributes fa;
+  const void* kernels[] = {(const void*)k_bin, (const void*)k_scan, (const void*)k_scatter,
+                           (const void*)k_binsort};
+  for (const void* k : kernels) {
+    e = cudaFuncGetAttributes(&fa, k);
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaFuncGetAttributes");
+  }
+  return NNP_OK;
+}
+
+}  // namespace nnp
+
 extern "C" int nnp_eval_noalloc(nnp_ctx* ctx, int64_t n, const double* pos, const int32_t* Z,
                                 const double* box, double* energy, double* forces) {
   if (!ctx) return NNP_ERR_INVALID_ARG;
@@ -103,6 +151,7 @@ extern "C" int nnp_eval_noalloc(nnp_ctx* ctx, int64_t n, const double* pos, cons
     return ctx->fail(NNP_ERR_INVALID_ARG, "nnp_eval_noalloc needs pos, Z, energy, forces and a box");
   if (!on_device(pos) || !on_device(Z) || !on_device(energy) || !on_device(forces))
     return ctx->fail(NNP_ERR_INVALID_ARG, "nnp_eval_noalloc needs device pointers for pos, Z, energy, forces");
+  if (on_device(box)) return ctx->fail(NNP_ERR_INVALID_ARG, "nnp_eval_noalloc needs the box as a host pointer");
   if (ctx->cfg.precision != NNP_FP32)
     return ctx->fail(NNP_ERR_UNSUPPORTED, "nnp_eval_noalloc supports FP32 contexts only");
   if (ctx->P.S > kNAMaxS)
@@ -114,17 +163,9 @@ extern "C" int nnp_eval_noalloc(nnp_ctx* ctx, int64_t n, const double* pos, cons
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaGetDevice");
   if (dev < 0 || dev >= kMaxDevices) return ctx->fail(NNP_ERR_UNSUPPORTED, "device index %d", dev);
-  unsigned char* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-      g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
-    }
-    base = g_scratch_ptr[dev];
-  }
+  unsigned char* base = nullptr;  // cached by nnp_create on the context's device
+  e = scratch_base(dev, &base);
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
 
   // one periodic orthorhombic system (same cell rule as nnp_eval)
   SysDesc sd{};

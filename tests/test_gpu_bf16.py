@@ -3,21 +3,25 @@
 The BF16 form rounds descriptors, weights and activations to BF16 (8-bit
 mantissa) and accumulates in FP32, so it is not held to the FP32 bounds.
 Its measured error against the FP64 oracle is reported and must stay within
-bounds derived from that rounding: relative energy error <= 1e-2 (same
-normalisation as the FP32 form) and force errors max <= 0.1 eV/A, RMS <=
-0.02 eV/A for forces of RMS ~0.3 eV/A.
+about three times what it measures on water-64 (relative energy error 9.9e-4
+with the FP32 form's normalisation, max |dF| 6.8e-3 eV/A, RMS |dF| 2.0e-3
+eV/A for forces of RMS ~0.3 eV/A), so that a regression of the tensor-core
+path by a few times fails: relative energy error <= 3e-3, max |dF| <= 2e-2
+eV/A, RMS |dF| <= 6e-3 eV/A.  Per-atom energies on the full-size box:
+max |dE_i| <= 4e-3 of max(1 eV, max |E_i|).
 """
 import numpy as np
 import pytest
 
 import synth
-from common import box9, energy_error, weights32
+from common import box9, energy_error, oracle_subset, targeted_atoms, weights32
 
 pytestmark = pytest.mark.gpu
 
-E_BF16 = 1e-2
-F_MAX_BF16 = 0.1
-F_RMS_BF16 = 0.02
+E_BF16 = 3e-3
+F_MAX_BF16 = 2e-2
+F_RMS_BF16 = 6e-3
+EI_BF16 = 4e-3
 
 
 @pytest.fixture(scope="module")
@@ -66,12 +70,13 @@ def test_bf16_matches_fp32_form(P):
     Ei = a.atom_energies(s.n)
     assert abs(Eb - Ea) <= E_BF16 * np.abs(Ei).sum()
     assert np.abs(Fb - Fa).max() <= F_MAX_BF16
-    # FP32 force sums by atomic reductions: the order, and the last bits, vary
-    assert abs(Eb2 - Eb) <= 1e-9 * abs(Eb) and np.abs(Fb2 - Fb).max() <= 1e-5
+    # FP64 force reductions of FP32 terms: the order, and the last bits, vary
+    assert abs(Eb2 - Eb) <= 1e-9 * abs(Eb) and np.abs(Fb2 - Fb).max() <= 1e-11
 
 
 def test_bf16_full_size_sampled(P, oracle_mod):
-    """98,304 atoms: every SM runs several tiles (persistent loop)."""
+    """98,304 atoms: every SM runs several tiles (persistent loop).  Random,
+    face, corner and most-crowded atoms against the oracle."""
     import torch
     wl = synth.workload(3)
     s = wl["systems"][0]
@@ -82,14 +87,13 @@ def test_bf16_full_size_sampled(P, oracle_mod):
     E, F = pot.eval(pos, Z, box9(s.box))
     F = F.cpu().numpy()
     Ei = pot.atom_energies(s.n)
-    rng = np.random.default_rng(5)
-    sel_e = np.sort(rng.choice(s.n, 64, replace=False))
-    sel_f = np.sort(rng.choice(s.n, 12, replace=False))
-    p = oracle_mod.Params()
-    m = oracle_mod.Model(p, w)
-    Eir, Fr = oracle_mod.energy_forces_subset(m, s.pos, p.species_of(s.Z), s.box, sel_e, sel_f)
-    print(f"bf16 water-32768 sampled: max|dEi| {np.abs(Ei[sel_e] - Eir).max():.2e}, "
-          f"max|dF| {np.abs(F[sel_f] - Fr).max():.3e}")
-    assert np.abs(Ei[sel_e] - Eir).max() <= E_BF16 * max(1.0, np.abs(Eir).max()) * 5
-    assert np.abs(F[sel_f] - Fr).max() <= F_MAX_BF16
+    sel = targeted_atoms(s.pos, s.box, np.random.default_rng(5))
+    Eir, Fr = oracle_subset((1, 8), w, s.pos, s.Z, s.box, sel, sel)
+    dF = F[sel] - Fr
+    err_ei = np.abs(Ei[sel] - Eir).max()
+    print(f"bf16 water-32768, {len(sel)} atoms: max|dEi| {err_ei:.2e} (max|Ei| {np.abs(Eir).max():.2f}), "
+          f"max|dF| {np.abs(dF).max():.3e}, rms dF {np.sqrt((dF ** 2).mean()):.3e}")
+    assert err_ei <= EI_BF16 * max(1.0, np.abs(Eir).max())
+    assert np.abs(dF).max() <= F_MAX_BF16
+    assert np.sqrt((dF ** 2).mean()) <= F_RMS_BF16
     assert abs(float(E) - Ei.sum()) <= 1e-6 * np.abs(Ei).sum()

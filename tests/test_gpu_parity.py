@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import synth
-from common import E_REL_TOL, F_ABS_TOL, box9, energy_error, weights32
+from common import E_REL_TOL, F_ABS_TOL, box9, energy_error, oracle_subset, targeted_atoms, weights32
 
 pytestmark = pytest.mark.gpu
 
@@ -136,11 +136,12 @@ def test_graph_and_direct_launches_agree(P):
     for _ in range(3):
         Eb, Fb = b.eval(s.pos, s.Z, s.box)
         Ea2, Fa2 = a.eval(s.pos, s.Z, s.box)
-        # energies: FP64 sums of per-warp partials; forces: FP64 reductions,
-        # whose order (and last bits) vary from launch to launch
-        assert abs(Ea2 - Ea) <= 1e-12 * abs(Ea) and np.abs(Fa2 - Fa).max() < 1e-5
-        assert abs(Eb - Ea) <= 1e-12 * abs(Ea) and np.abs(Fb - Fa).max() < 1e-5
+        # energies: FP64 sums of per-warp partials; forces: FP64 reductions
+        # of FP32 terms, whose order (and last bits) vary from launch to launch
+        assert abs(Ea2 - Ea) <= 1e-12 * abs(Ea) and np.abs(Fa2 - Fa).max() < 1e-11
+        assert abs(Eb - Ea) <= 1e-12 * abs(Ea) and np.abs(Fb - Fa).max() < 1e-11
     Ec, Fc = c.eval(s.pos, s.Z, s.box)
+    # another row order changes the FP32 sums inside each descriptor
     assert abs(Ec - Ea) <= 1e-7 * abs(Ea) and np.abs(Fc - Fa).max() < 1e-5
     assert a.query("graph_captures") == 1
     # cells (one block for a system this small), neighbours, descriptor,
@@ -186,7 +187,10 @@ def test_error_codes(P):
 @pytest.mark.parametrize("k", [2, 3])
 def test_full_size_sampled(P, oracle_mod, k):
     """12,288 / 98,304 atoms, device-resident inputs, graph replay (the
-    benchmark's configuration): sampled E_i and F_j against the oracle."""
+    benchmark's configuration): E_i and F_j against the oracle on 128 random
+    atoms plus the atoms at the box faces and corners (neighbours through
+    periodic images, edge cells) and the 32 atoms with the most angular
+    neighbours."""
     import torch
     wl = synth.workload(k)
     s = wl["systems"][0]
@@ -200,12 +204,14 @@ def test_full_size_sampled(P, oracle_mod, k):
     F = F.cpu().numpy()
     Ei = pot.atom_energies(s.n)
     rng = np.random.default_rng(k)
-    sel_e = np.sort(rng.choice(s.n, 64, replace=False))
-    sel_f = np.sort(rng.choice(s.n, 12, replace=False))
-    p, m = _oracle(oracle_mod, w)
-    Eir, Fr = oracle_mod.energy_forces_subset(m, s.pos, p.species_of(s.Z), s.box, sel_e, sel_f)
-    assert np.abs(Ei[sel_e] - Eir).max() <= 1e-5 * max(1.0, np.abs(Eir).max())
-    assert np.abs(F[sel_f] - Fr).max() <= F_ABS_TOL
+    sel = targeted_atoms(s.pos, s.box, rng)
+    assert len(sel) >= 160
+    Eir, Fr = oracle_subset((1, 8), w, s.pos, s.Z, s.box, sel, sel)
+    err_ei = np.abs(Ei[sel] - Eir).max()
+    err_f = np.abs(F[sel] - Fr).max()
+    print(f"water k={k}: {len(sel)} atoms, max|dEi| {err_ei:.2e} eV, max|dF| {err_f:.2e} eV/A")
+    assert err_ei <= 1e-5 * max(1.0, np.abs(Eir).max())
+    assert err_f <= F_ABS_TOL
     assert abs(E - Ei.sum()) <= 1e-6 * np.abs(Ei).sum()
     assert np.abs(F.sum(0)).max() <= 1e-6 * np.abs(F).sum()
 

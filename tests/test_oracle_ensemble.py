@@ -10,6 +10,12 @@ descriptor).
   forces.
 * The ensemble forces equal central finite differences of the ensemble
   energy.
+* The force-matching gradient of the ensemble (the loss of the members'
+  mean force) equals central finite differences of that loss along unit
+  directions in each member's layers, and equals the gradient of the
+  equivalent wider network, mapped back to the members' blocks (output
+  weights: the wide network stores w4 / M, so its gradient there is M times
+  the member's).
 """
 import numpy as np
 
@@ -89,3 +95,68 @@ def test_ensemble_forces_are_finite_differences(oracle_mod):
             fd = -(oracle_mod.ensemble_energy_forces(models, pp, sp, s.box)[0]
                    - oracle_mod.ensemble_energy_forces(models, pm, sp, s.box)[0]) / (2 * h)
             assert abs(F[a, c] - fd) <= 1e-6 * max(1.0, abs(fd))
+
+
+def _ens_loss(oracle_mod, p, members, pos, sp, box, Fref):
+    models = [oracle_mod.Model(p, w) for w in members]
+    F = oracle_mod.ensemble_energy_forces(models, pos, sp, box)[2]
+    return ((F - Fref) ** 2).sum() / (3 * pos.shape[0])
+
+
+def test_ensemble_force_match_finite_differences(oracle_mod):
+    M = 2
+    mem = _members(M, 531)
+    p = oracle_mod.Params()
+    s = synth.water_box(8, 532)
+    sp = p.species_of(s.Z)
+    Fref = 0.3 * np.random.default_rng(533).standard_normal((s.n, 3))
+    models = [oracle_mod.Model(p, w) for w in mem]
+    L, dW, db, F = oracle_mod.ensemble_force_match(models, s.pos, sp, s.box, Fref)
+    assert L == _ens_loss(oracle_mod, p, mem, s.pos, sp, s.box, Fref) or \
+        abs(L - _ens_loss(oracle_mod, p, mem, s.pos, sp, s.box, Fref)) <= 1e-13 * L
+    rng = np.random.default_rng(534)
+    for m in range(M):
+        for s_ in range(2):
+            for l in range(4):
+                ref = mem[m][s_][l][0]
+                dirn = rng.normal(size=ref.shape)
+                dirn /= np.linalg.norm(dirn)
+                analytic = float((dW[m][s_][l] * dirn).sum())
+                errs = []
+                for h in (1e-5, 1e-6):
+                    def shifted(sign):
+                        out = [[list(x) for x in wm] for wm in mem]
+                        W, b = mem[m][s_][l]
+                        out[m][s_][l] = (W + sign * h * dirn, b)
+                        return [[tuple(x) for x in wm] for wm in out]
+                    fd = (_ens_loss(oracle_mod, p, shifted(1), s.pos, sp, s.box, Fref) -
+                          _ens_loss(oracle_mod, p, shifted(-1), s.pos, sp, s.box, Fref)) / (2 * h)
+                    errs.append(abs(analytic - fd) / max(abs(fd), 1e-6))
+                assert min(errs) < 1e-6, (m, s_, l, errs)
+        assert all(np.all(db[m][s_][3] == 0) for s_ in range(2))
+
+
+def test_ensemble_force_match_is_the_wide_networks(oracle_mod):
+    M = 3
+    mem = _members(M, 541)
+    p = oracle_mod.Params()
+    s = synth.water_box(8, 542)
+    sp = p.species_of(s.Z)
+    Fref = 0.3 * np.random.default_rng(543).standard_normal((s.n, 3))
+    L, dW, db, _ = oracle_mod.ensemble_force_match([oracle_mod.Model(p, w) for w in mem],
+                                                    s.pos, sp, s.box, Fref)
+    wide = oracle_mod.Model(oracle_mod.Params(hidden=(160 * M, 128 * M, 96 * M)), _wide(mem))
+    Lw, dWw, dbw, _ = oracle_mod.force_match(wide, s.pos, sp, s.box, Fref)
+    assert abs(L - Lw) <= 1e-12 * Lw
+    scale = np.abs(np.concatenate([x.ravel() for x in dWw[0]])).max()
+    tol = 1e-10 * scale
+    for m in range(M):
+        for s_ in range(2):
+            c1, c2, c3 = slice(160 * m, 160 * (m + 1)), slice(128 * m, 128 * (m + 1)), slice(96 * m, 96 * (m + 1))
+            assert np.abs(dW[m][s_][0] - dWw[s_][0][:, c1]).max() <= tol
+            assert np.abs(dW[m][s_][1] - dWw[s_][1][c1, c2]).max() <= tol
+            assert np.abs(dW[m][s_][2] - dWw[s_][2][c2, c3]).max() <= tol
+            assert np.abs(dW[m][s_][3] - dWw[s_][3][c3] / M).max() <= tol
+            assert np.abs(db[m][s_][0] - dbw[s_][0][c1]).max() <= tol
+            assert np.abs(db[m][s_][1] - dbw[s_][1][c2]).max() <= tol
+            assert np.abs(db[m][s_][2] - dbw[s_][2][c3]).max() <= tol
