@@ -660,20 +660,21 @@ def oracle_full_serial(wl, w):
 
 def run_reference(args):
     """The reference arm: the FP64 oracle on the host cores, same workload,
-    metric and config as the GPU arm.  Each step is one full evaluation of
-    the workload by the OpenMP build of the oracle; if the first one shows
-    that K + W of them would take more than --ref-budget seconds, each step
-    is instead a bounded sample (--ref-seconds of single-threaded sampled
-    atoms in each of the host's cores).  One full single-threaded evaluation
-    is timed after the steps (--serial-full 1)."""
+    metric and config as the GPU arm.  Each timed step is one full
+    evaluation of the workload by the OpenMP build of the oracle.  The first
+    warm-up step is one such evaluation (it also sizes the run); the oracle
+    keeps no state, so the other warm-up steps are short sampled calls.  If K
+    full evaluations would take more than --ref-budget seconds, each step is
+    instead a bounded sample (--ref-seconds of sampled atoms, single-threaded).
+    --serial-full 1 also times one full single-threaded evaluation."""
     wl, w, S, D = build_workload(args.workload)
     n = sum(s.n for s in wl["systems"])
     t_probe, threads = oracle_full_omp(wl, w)
-    full = t_probe * (args.steps + args.warmup - 1) <= args.ref_budget
+    full = t_probe * args.steps <= args.ref_budget
     times, evaluated = [], 0
     if full:
-        for _ in range(args.warmup - 1):
-            oracle_full_omp(wl, w)
+        for k in range(args.warmup - 1):
+            oracle_sample(wl, w, seconds=0.2, seed=1000 + k)
         for _ in range(args.steps):
             t, _ = oracle_full_omp(wl, w)
             times.append(t)
@@ -808,9 +809,9 @@ def main():
     ap.add_argument("--compare", default="fp32,bf16,fp8")
     ap.add_argument("--workload", type=int, default=3)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
-    ap.add_argument("--ref-budget", type=float, default=150.0,
-                    help="reference arm: seconds allowed for its full evaluations")
-    ap.add_argument("--serial-full", type=int, default=1,
+    ap.add_argument("--ref-budget", type=float, default=200.0,
+                    help="reference arm: seconds allowed for its timed full evaluations")
+    ap.add_argument("--serial-full", type=int, default=0,
                     help="reference arm: also time one full single-threaded evaluation")
     ap.add_argument("--extras", type=int, default=1,
                     help="0: leave out the auxiliary measurements after the JSON line's main step "

@@ -8,8 +8,9 @@ ANI-2x model of the performance-scaling study in the Results).
 * M copies of one network give that network's result (the output layer is
   stored divided by M, which rounds, so 1e-6 relative and 1e-5 eV/A);
 * M = 8 on the 12,288-atom box against the oracle on sampled atoms;
-* a missing member, FP8 with M > 1, M above the maximum and force matching
-  of an ensemble are refused, and the context keeps working.
+* a missing member, FP8 with M > 1, M above the maximum and a force-matching
+  call without v or reference forces are refused, and the context keeps
+  working (ensemble force matching itself: tests/test_gpu_force_match.py).
 """
 import numpy as np
 import pytest
@@ -19,9 +20,11 @@ from common import E_REL_TOL, F_ABS_TOL, box9, energy_error, weights32
 
 pytestmark = pytest.mark.gpu
 
-E_BF16 = 1e-2
-F_MAX_BF16 = 0.1
-F_RMS_BF16 = 0.02
+# about three times the measured BF16 errors of the three-member ensemble on
+# water-64 (relative energy 9.6e-4, max |dF| 6.2e-3, RMS 1.6e-3 eV/A)
+E_BF16 = 3e-3
+F_MAX_BF16 = 2e-2
+F_RMS_BF16 = 6e-3
 
 
 @pytest.fixture(scope="module")
@@ -153,9 +156,9 @@ def test_ensemble_refusals(P):
     pot.set_all_weights(_f32(mem[1]), member=1)
     E, F = pot.eval(s.pos, s.Z, box9(s.box))
     assert np.isfinite(E)
-    with pytest.raises(P.NNPError) as e:
+    with pytest.raises(P.NNPError) as e:  # neither v nor reference forces
         pot.force_match_grad()
-    assert e.value.code == 3
+    assert e.value.code == 1
     with pytest.raises(P.NNPError) as e:
         P.NNP(atomic_numbers=(1, 8), precision="fp8", n_members=2)
     assert e.value.code == 3

@@ -3,10 +3,15 @@
 L = |F - Fref|^2 / (3N) with Fref from an independently seeded teacher
 network (oracle), or seeded random reference forces on the full-size box.
 The GPU computes F and dL/dtheta in FP32 (with FP64 sums over 64-row chunks
-and 2,048-row segments); bounds: relative loss error <= 1e-5, gradient
-max-abs error <= 2e-3 of the largest gradient entry and relative L2 error
-<= 1e-3.
+and 2,048-row segments).  Bounds, about three times the measured errors:
+relative loss error <= 2e-6; gradient max-abs error, relative to the largest
+gradient entry, <= 2e-5 on the small systems (measured <= 7e-6) and <= 2e-4
+on the 6,134-atom workload (measured 5.8e-5); relative L2 error <= 1.5e-5
+(small, measured <= 4.5e-6) and <= 1e-4 (full size, measured 2.4e-5).
 """
+GRAD_MAX, GRAD_L2 = 2e-5, 1.5e-5          # small systems
+GRAD_MAX_FULL, GRAD_L2_FULL = 2e-4, 1e-4  # the 6,134-atom workload
+LOSS_REL = 2e-6
 import numpy as np
 import pytest
 
@@ -57,8 +62,8 @@ def test_force_match_gradient(P, oracle_mod, kind):
     err_l2 = np.linalg.norm(g - gref) / np.linalg.norm(gref)
     print(f"{kind}: L {L:.6e} ref {Lr:.6e} (rel {abs(L - Lr) / Lr:.2e}); grad max err {err_max:.2e}, "
           f"rel L2 {err_l2:.2e}")
-    assert abs(L - Lr) <= 1e-5 * Lr
-    assert err_max <= 2e-3 and err_l2 <= 1e-3
+    assert abs(L - Lr) <= LOSS_REL * Lr
+    assert err_max <= GRAD_MAX and err_l2 <= GRAD_L2
     # the v = dL/dF entry point gives the same gradient
     n = s.n
     F, _ = Fo, None
@@ -105,8 +110,8 @@ def test_force_match_workload5_full_size(P, oracle_mod):
           f"grad max err {err_max:.2e} of max entry, rel L2 {err_l2:.2e}")
     assert err_e <= E_REL_TOL and err_f <= F_ABS_TOL
     assert np.abs(Fo - Fr).max() <= 1e-10
-    assert err_l <= 1e-5
-    assert err_max <= 2e-3 and err_l2 <= 1e-3
+    assert err_l <= LOSS_REL
+    assert err_max <= GRAD_MAX_FULL and err_l2 <= GRAD_L2_FULL
 
 
 
@@ -137,8 +142,8 @@ def test_force_match_ensemble(P, oracle_mod):
         err_l2 = np.linalg.norm(g - gref) / np.linalg.norm(gref)
         print(f"ensemble M={M} ({prec} context): L rel {abs(L - Lr) / Lr:.2e}, grad max err {err_max:.2e}, "
               f"rel L2 {err_l2:.2e}")
-        assert abs(L - Lr) <= 1e-5 * Lr
-        assert err_max <= 2e-3 and err_l2 <= 1e-3
+        assert abs(L - Lr) <= LOSS_REL * Lr
+        assert err_max <= GRAD_MAX and err_l2 <= GRAD_L2
         pot.close()
 
 
@@ -164,8 +169,8 @@ def test_force_match_seven_species(P, oracle_mod):
     err_l2 = np.linalg.norm(g - gref) / np.linalg.norm(gref)
     print(f"seven species ({s.n} atoms): L rel {abs(L - Lr) / Lr:.2e}, grad max err {err_max:.2e}, "
           f"rel L2 {err_l2:.2e}")
-    assert abs(L - Lr) <= 1e-5 * Lr
-    assert err_max <= 2e-3 and err_l2 <= 1e-3
+    assert abs(L - Lr) <= LOSS_REL * Lr
+    assert err_max <= GRAD_MAX and err_l2 <= GRAD_L2
 
 
 def test_force_match_stage_profile(P):

@@ -11,8 +11,8 @@ set of the ANI-2x model), and of the wide-descriptor tensor-core network.
 * BF16 (tcgen05 network with layer 1 streamed in K chunks and dE/dG in
   column blocks) at three, four and seven species against the oracle within
   the BF16 form's bounds, and against the FP32 form on the 6,047-atom box;
-* the FP8 form, force matching and the no-allocation entry point refuse more
-  species than they take.
+* the FP8 form and the no-allocation entry point refuse more species than
+  they take (force matching takes all eight: tests/test_gpu_force_match.py).
 """
 import numpy as np
 import pytest
@@ -23,9 +23,11 @@ from common import E_REL_TOL, F_ABS_TOL, box9, energy_error, weights32
 pytestmark = pytest.mark.gpu
 
 Z7 = (1, 6, 7, 8, 9, 16, 17)
-E_BF16 = 1e-2
-F_MAX_BF16 = 0.1
-F_RMS_BF16 = 0.02
+# about three times the largest measured BF16 errors of the wide-descriptor
+# network (D = 240: relative energy 1.6e-3, max |dF| 2.9e-2, RMS 3.5e-3 eV/A)
+E_BF16 = 5e-3
+F_MAX_BF16 = 6e-2
+F_RMS_BF16 = 1e-2
 
 
 @pytest.fixture(scope="module")
@@ -179,9 +181,6 @@ def test_seven_species_refusals(P):
     s = _small_box(742)
     E, _ = pot.eval(s.pos, s.Z, box9(s.box))
     assert np.isfinite(E)
-    with pytest.raises(P.NNPError) as e:
-        pot.force_match_grad(Fref=np.zeros((s.n, 3)))
-    assert e.value.code == 3
     import ctypes
     import torch
     pos, Z = torch.tensor(s.pos, device="cuda"), torch.tensor(s.Z, device="cuda")
