@@ -365,7 +365,13 @@ typedef enum {
     NNP_Q_TUNE_NEIGHBOURS = 7,    /* blocks-per-SM cap of the neighbour kernel */
     NNP_Q_TUNE_DESCRIPTOR = 8,    /* ... of the descriptor kernel */
     NNP_Q_TUNE_BACKWARD = 9,      /* ... of the descriptor-backward kernel */
-    NNP_Q_FP8_CALIBRATED = 10     /* 1 once every species' FP8 activation scales are set */
+    NNP_Q_FP8_CALIBRATED = 10,    /* 1 once every species' FP8 activation scales are set */
+    NNP_Q_TUNE_DESCRIPTOR_TILE = 11, /* row pairs per work item of the descriptor kernel
+                                        (> 0: from the work queue; < 0: static order) */
+    NNP_Q_TUNE_BACKWARD_TILE = 12,   /* rows per work item of the descriptor-backward kernel
+                                        (sign as above) */
+    NNP_Q_TUNE_NEIGHBOURS_QUEUE = 13 /* 1: the neighbour kernel draws its cells from the work
+                                        queue; 0: static order */
 } nnp_query_key;
 
 int nnp_query(nnp_ctx *ctx, int32_t key, int64_t *value);

@@ -47,7 +47,8 @@ ABI_FUNCTIONS = ("nnp_config_init", "nnp_create", "nnp_destroy", "nnp_last_error
 QUERY = {"launches_per_eval": 0, "nbr_capacity": 1, "ang_capacity": 2, "max_nbr": 3,
          "max_ang": 4, "rows": 5, "graph_captures": 6,
          "tune_neighbours": 7, "tune_descriptor": 8, "tune_backward": 9,
-         "fp8_calibrated": 10}
+         "fp8_calibrated": 10, "tune_descriptor_tile": 11, "tune_backward_tile": 12,
+         "tune_neighbours_queue": 13}
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNKNOWN_SPECIES", 3: "UNSUPPORTED", 4: "CAPACITY",
           5: "CUDA", 6: "TIMEOUT", 7: "NO_WEIGHTS", 8: "NO_STATE"}

@@ -207,7 +207,7 @@ __device__ __forceinline__ void load_counts(const Workspace& ws, int S, int row,
 
 template <int S, int ZSQ>
 __global__ void __launch_bounds__(256, 3) k_aev_fwd(const SysDesc* __restrict__ sys, DescParams P,
-                                                 Workspace ws, int mode) {
+                                                 Workspace ws, int mode, int tile_rows, int dyn) {
   constexpr int D = kNRad * S + kNAng * S * (S + 1) / 2;
   extern __shared__ float4 sm4[];
   const int lane = threadIdx.x & 31, hl = lane & 15, half = lane >> 4;
@@ -234,10 +234,11 @@ __global__ void __launch_bounds__(256, 3) k_aev_fwd(const SysDesc* __restrict__ 
   const volatile unsigned long long* vhcs = s_hcs;
   const f2 half2 = f2_make(0.5f, 0.5f), kr2 = f2_make(kr, kr);
   const int rows = ws.seg[S];
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
   int cached_sys = -1;
-  for (int pr = warp; 2 * pr < rows; pr += nwarps) {
+  // tiles of tile_rows row pairs from the work queue
+  WorkQueue wq(ws.queue + kQFwd, dyn != 0);
+  int pr = wq.first() * tile_rows, tile_end = pr + tile_rows;
+  for (; 2 * pr < rows;) {
     const int row = 2 * pr + half;
     const bool inrow = row < rows;
     const bool live = inrow && ws.row_atom[row] >= 0;
@@ -410,7 +411,12 @@ __global__ void __launch_bounds__(256, 3) k_aev_fwd(const SysDesc* __restrict__ 
       }
     }
     __syncwarp();
+    if (++pr >= tile_end) {  // warp-uniform
+      pr = wq.next(lane) * tile_rows;
+      tile_end = pr + tile_rows;
+    }
   }
+  queue_warp_done(wq, lane);
 }
 
 // --------------------------------------------------------------------------
@@ -471,7 +477,7 @@ __host__ __device__ inline size_t bwd_warp_f4(int cap_a, int cap_r, int S) {
 template <int S, int ZSQ>
 __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ io,
                                                     const SysDesc* __restrict__ sys, DescParams P,
-                                                    Workspace ws) {
+                                                    Workspace ws, int tile_rows, int dyn) {
   constexpr int D = kNRad * S + kNAng * S * (S + 1) / 2;
   constexpr int NB = S * (S + 1) / 2;
   constexpr unsigned FM = 0xffffffffu;
@@ -504,8 +510,6 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
   const f2 half2 = f2_make(0.5f, 0.5f);
   const float dcs = 1.9f * zeta;
   const int rows = ws.seg[S];
-  const int wpb = blockDim.x >> 5;
-  const int rstride = gridDim.x * wpb;
   int cached_sys = -1;
   // the next row's metadata, counts and first 64 list entries are loaded one
   // row ahead, so their latency hides behind the current row's arithmetic
@@ -524,13 +528,22 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
     p_e0 = lane < cr ? l[lane] : 0;
     p_e1 = lane + 32 < cr ? l[lane + 32] : 0;
   };
-  prefetch(blockIdx.x * wpb + wib);
-  for (int row = blockIdx.x * wpb + wib; row < rows; row += rstride) {
+  // tiles of tile_rows consecutive rows from the work queue, so that a
+  // warp's rows are neighbours in space and share their gathers
+  WorkQueue wq(ws.queue + kQBwd, dyn != 0);
+  int row = wq.first() * tile_rows, tile_end = row + tile_rows, nrow = row;
+  prefetch(row);
+  for (; row < rows; row = nrow) {
     const bool live_row = p_atom >= 0;
     const float4 pi = p_pos;
     const int sid = p_info;
     const int cnt_l = p_cnt, cna_l = p_cna, e0 = p_e0, e1 = p_e1;
-    prefetch(row + rstride);
+    nrow = row + 1;
+    if (nrow >= tile_end) {  // warp-uniform
+      nrow = wq.next(lane) * tile_rows;
+      tile_end = nrow + tile_rows;
+    }
+    prefetch(nrow);
     if (!live_row) continue;  // padding row (warp-uniform)
     __syncwarp();  // the previous row's shared data has been read
     if (sid != cached_sys) {
@@ -796,6 +809,7 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
     }
     if (lane < 3) atomicAdd(Fout + 3 * (size_t)pos4_orig(pi) + lane, (double)(lane == 0 ? fix : (lane == 1 ? fiy : fiz)));
   }
+  queue_warp_done(wq, lane);
 }
 
 // FP32 accumulators -> the caller's FP64 forces (input order).
@@ -1008,45 +1022,53 @@ size_t aev_bwd_smem(int cap_a, int cap_r, int S) {
   return (size_t)kBwdWarps * bwd_warp_f4(cap_a, cap_r, S) * sizeof(float4);
 }
 
-static int warps_grid(long long rows, int warps_per_block, int nsm, int per_sm) {
-  const long long warps = (rows + 1) / 2;
-  long long g = (warps + warps_per_block - 1) / warps_per_block;
+// Persistent grids: no more blocks than the work needs (items of tile rows
+// per warp), capped at per_sm blocks per SM; the warps draw their tiles from
+// the stage's work queue.
+static int queue_grid(long long items, int warps_per_block, int nsm, int per_sm) {
+  long long g = (items + warps_per_block - 1) / warps_per_block;
   const long long cap = (long long)nsm * per_sm;
   if (g > cap) g = cap;
   return (int)(g < 1 ? 1 : g);
 }
 
-static int g_fwd_per_sm = 8, g_bwd_per_sm = 16;  // set per launch by the callers
-
+// tile > 0: dynamic (work queue) with tiles of that many items; tile < 0:
+// static order with tiles of -tile items; 0: the default
 template <int S, int ZSQ>
 static void fwd_t(long long rows, int nsm, cudaStream_t st, const SysDesc* sys, const DescParams& P,
-                  const Workspace& ws, int mode) {
-  k_aev_fwd<S, ZSQ><<<warps_grid(rows, 8, nsm, g_fwd_per_sm), 256, aev_fwd_smem(ws.cap_a, ws.cap_r), st>>>(sys, P, ws,
-                                                                                                  mode);
+                  const Workspace& ws, int mode, int per_sm, int tile) {
+  const int t = tile < 0 ? -tile : tile;
+  const long long items = ((rows + 1) / 2 + t - 1) / t;
+  k_aev_fwd<S, ZSQ><<<queue_grid(items, 8, nsm, per_sm), 256, aev_fwd_smem(ws.cap_a, ws.cap_r), st>>>(
+      sys, P, ws, mode, t, tile > 0 ? 1 : 0);
 }
 template <int S, int ZSQ>
 static void bwd_t(long long rows, int nsm, cudaStream_t st, const EvalIO* io, const SysDesc* sys,
-                  const DescParams& P, const Workspace& ws) {
-  long long g = (rows + kBwdWarps - 1) / kBwdWarps;
-  if (g > (long long)nsm * g_bwd_per_sm) g = (long long)nsm * g_bwd_per_sm;
-  k_aev_bwd<S, ZSQ><<<(int)(g < 1 ? 1 : g), 32 * kBwdWarps, aev_bwd_smem(ws.cap_a, ws.cap_r, S),
-                      st>>>(io, sys, P, ws);
+                  const DescParams& P, const Workspace& ws, int per_sm, int tile) {
+  const int t = tile < 0 ? -tile : tile;
+  const long long items = (rows + t - 1) / t;
+  k_aev_bwd<S, ZSQ><<<queue_grid(items, kBwdWarps, nsm, per_sm), 32 * kBwdWarps,
+                      aev_bwd_smem(ws.cap_a, ws.cap_r, S), st>>>(io, sys, P, ws, t, tile > 0 ? 1 : 0);
 }
 
 void launch_aev_fwd(long long rows, int nsm, cudaStream_t st, const SysDesc* sys, const DescParams& P,
-                    const Workspace& ws, int mode, int per_sm) {
-  g_fwd_per_sm = per_sm > 0 ? per_sm : 8;
+                    const Workspace& ws, int mode, int per_sm, int tile) {
+  per_sm = per_sm > 0 ? per_sm : 8;
+  tile = tile != 0 ? tile : -1;
   const bool z5 = P.zeta_sq == 5;
-#define FWD(s) z5 ? fwd_t<s, 5>(rows, nsm, st, sys, P, ws, mode) : fwd_t<s, -1>(rows, nsm, st, sys, P, ws, mode)
+#define FWD(s) z5 ? fwd_t<s, 5>(rows, nsm, st, sys, P, ws, mode, per_sm, tile) \
+                  : fwd_t<s, -1>(rows, nsm, st, sys, P, ws, mode, per_sm, tile)
   switch (P.S) { NNP_SPECIES_CASES(FWD) }
 #undef FWD
 }
 
 void launch_aev_bwd(long long rows, int nsm, cudaStream_t st, const EvalIO* io, const SysDesc* sys,
-                    const DescParams& P, const Workspace& ws, int per_sm) {
-  g_bwd_per_sm = per_sm > 0 ? per_sm : 16;
+                    const DescParams& P, const Workspace& ws, int per_sm, int tile) {
+  per_sm = per_sm > 0 ? per_sm : 16;
+  tile = tile != 0 ? tile : -1;
   const bool z5 = P.zeta_sq == 5;
-#define BWD(s) z5 ? bwd_t<s, 5>(rows, nsm, st, io, sys, P, ws) : bwd_t<s, -1>(rows, nsm, st, io, sys, P, ws)
+#define BWD(s) z5 ? bwd_t<s, 5>(rows, nsm, st, io, sys, P, ws, per_sm, tile) \
+                  : bwd_t<s, -1>(rows, nsm, st, io, sys, P, ws, per_sm, tile)
   switch (P.S) { NNP_SPECIES_CASES(BWD) }
 #undef BWD
 }

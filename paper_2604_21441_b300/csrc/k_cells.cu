@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(1024) k_cells_small(const EvalIO* __restrict__
 template <int SB, int WIN>
 __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __restrict__ io,
                                                           const SysDesc* __restrict__ sys,
-                                                          DescParams P, Workspace ws, int split) {
+                                                          DescParams P, Workspace ws, int split, int dyn) {
   constexpr int NCH = WIN / 32;                                       // window chunks
   constexpr int WF = 3 * NCH * kNbrChunkStride + WIN + 16 * 32;       // shared floats per warp
   constexpr int GR = WIN > 512 ? 8 : 16;                              // rows per group
@@ -369,9 +369,12 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
   const f2 nrc2 = f2_make(-rcr2, -rcr2), nra2 = f2_make(-rca2, -rca2);
   int mx_r = 0, mx_a = 0;  // largest unclamped row counts seen by this lane
   const int wpb = blockDim.x >> 5;
+  (void)wib;
   if (threadIdx.x < 3) s_mx[threadIdx.x] = 0;
   __syncthreads();
-  for (int vg = blockIdx.x * wpb + wib; vg < TC * split; vg += gridDim.x * wpb) {
+  // cells (each split into `split` parts) from the work queue
+  WorkQueue wq(ws.queue + kQNbr, dyn != 0);
+  for (int vg = wq.first(); vg < TC * split; vg = wq.next(lane)) {
     const int g = vg / split, part = vg - g * split;
     int lo = 0, hi = nsys - 1;
     while (lo < hi) {
@@ -718,6 +721,7 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
     mx_r = max(mx_r, __shfl_xor_sync(F, mx_r, o));
     mx_a = max(mx_a, __shfl_xor_sync(F, mx_a, o));
   }
+  queue_warp_done(wq, lane);
   // the CTA's last warp to finish publishes the maxima (no block barrier, so
   // warps that finish early do not wait)
   if (lane == 0) {
@@ -758,12 +762,12 @@ cudaError_t neighbors_set_smem_limits() {
 }
 
 void launch_neighbors(int grid, cudaStream_t st, const EvalIO* io, const SysDesc* sys, const DescParams& P,
-                      const Workspace& ws, long long rows, long long cells, int nsm) {
+                      const Workspace& ws, long long rows, long long cells, int nsm, int dyn) {
   if (rows > kNbrRowsSmall) {  // warp per cell, 512-candidate windows
     const size_t sm = neighbors_smem(kNbrWin);
-    if (P.S <= 2) k_neighbors<2, kNbrWin><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws, 1);
-    else if (P.S <= 4) k_neighbors<4, kNbrWin><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws, 1);
-    else k_neighbors<8, kNbrWin><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws, 1);
+    if (P.S <= 2) k_neighbors<2, kNbrWin><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws, 1, dyn);
+    else if (P.S <= 4) k_neighbors<4, kNbrWin><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws, 1, dyn);
+    else k_neighbors<8, kNbrWin><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws, 1, dyn);
     return;
   }
   // small systems: 1024-candidate windows, each cell's row groups over up to 8 warps
@@ -772,9 +776,9 @@ void launch_neighbors(int grid, cudaStream_t st, const EvalIO* io, const SysDesc
   const long long warps = cells * split;
   const int g = (int)std::max(1LL, (warps + kNbrThreads / 32 - 1) / (kNbrThreads / 32));
   const size_t sm = neighbors_smem(kNbrWinSmall);
-  if (P.S <= 2) k_neighbors<2, kNbrWinSmall><<<g, kNbrThreads, sm, st>>>(io, sys, P, ws, split);
-  else if (P.S <= 4) k_neighbors<4, kNbrWinSmall><<<g, kNbrThreads, sm, st>>>(io, sys, P, ws, split);
-  else k_neighbors<8, kNbrWinSmall><<<g, kNbrThreads, sm, st>>>(io, sys, P, ws, split);
+  if (P.S <= 2) k_neighbors<2, kNbrWinSmall><<<g, kNbrThreads, sm, st>>>(io, sys, P, ws, split, dyn);
+  else if (P.S <= 4) k_neighbors<4, kNbrWinSmall><<<g, kNbrThreads, sm, st>>>(io, sys, P, ws, split, dyn);
+  else k_neighbors<8, kNbrWinSmall><<<g, kNbrThreads, sm, st>>>(io, sys, P, ws, split, dyn);
 }
 
 }  // namespace nnp

@@ -141,6 +141,7 @@ Workspace nnp_ctx::workspace() const {
   w.dEdG = b_dEdG;
   w.Ei = b_Ei;
   w.flags = b_flags;
+  w.queue = b_queue;
   w.q8 = b_q8;
   w.cap_r = cap_r;
   w.cap_a = cap_a;
@@ -186,18 +187,18 @@ int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows,
     k_pairs_fill<<<g_pairs, 256, 0, stream>>>(io, sys, P, w, b_pair_cur);
     launches += 4;
   } else {
-    launch_neighbors(g_cells, stream, io, sys, P, w, rows, total_cells, nsm); ++launches;
+    launch_neighbors(g_cells, stream, io, sys, P, w, rows, total_cells, nsm, tune.nbr_dyn); ++launches;
   }
   mark_stage(2, capturing);
   if (calib) {  // FP8 calibration: FP32 descriptor, then the activation ranges
-    launch_aev_fwd(rows, nsm, stream, sys, P, w, kGFp32, tune.fwd);
+    launch_aev_fwd(rows, nsm, stream, sys, P, w, kGFp32, tune.fwd, tune.fwd_tile);
     int rc = launch_fp8_calib(this, stream, rows);
     if (rc) return rc;
     CK(cudaGetLastError());
     return NNP_OK;
   }
   const int gmode = cfg.precision == NNP_FP32 ? kGFp32 : (cfg.precision == NNP_BF16 ? kGBf16 : kGFp8);
-  launch_aev_fwd(rows, nsm, stream, sys, P, w, gmode, tune.fwd); ++launches;
+  launch_aev_fwd(rows, nsm, stream, sys, P, w, gmode, tune.fwd, tune.fwd_tile); ++launches;
   mark_stage(3, capturing);
   const int g_tiles = (int)std::min<long long>(rows / 64, (long long)nsm);
   if (cfg.precision == NNP_FP32) {
@@ -219,7 +220,7 @@ int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows,
     if (rc) return rc;
   }
   mark_stage(4, capturing);
-  launch_aev_bwd(rows, nsm, stream, io, sys, P, w, tune.bwd); ++launches;
+  launch_aev_bwd(rows, nsm, stream, io, sys, P, w, tune.bwd, tune.bwd_tile); ++launches;
   if (ee_mode) launch_ee_post(launches);  // charges, embedding energy, ML and MM forces
   mark_stage(5, capturing);
   CK(cudaGetLastError());
@@ -789,6 +790,9 @@ int nnp_query(nnp_ctx* ctx, int32_t key, int64_t* value) {
     case NNP_Q_TUNE_DESCRIPTOR: *value = ctx->tune.fwd; break;
     case NNP_Q_TUNE_BACKWARD: *value = ctx->tune.bwd; break;
     case NNP_Q_FP8_CALIBRATED: *value = ctx->fp8_calibrated ? 1 : 0; break;
+    case NNP_Q_TUNE_DESCRIPTOR_TILE: *value = ctx->tune.fwd_tile; break;
+    case NNP_Q_TUNE_BACKWARD_TILE: *value = ctx->tune.bwd_tile; break;
+    case NNP_Q_TUNE_NEIGHBOURS_QUEUE: *value = ctx->tune.nbr_dyn; break;
     default: return ctx->fail(NNP_ERR_INVALID_ARG, "unknown query key %d", key);
   }
   return NNP_OK;

@@ -33,6 +33,8 @@ int nnp_ctx::init_device() {
   CK(cudaMalloc(&b_seg, sizeof(int) * (kMaxS + 2)));
   CK(cudaMalloc(&b_flags, sizeof(int) * kNumFlags));
   CK(cudaMemset(b_flags, 0, sizeof(int) * kNumFlags));
+  CK(cudaMalloc(&b_queue, sizeof(int) * kQueueWords));
+  CK(cudaMemset(b_queue, 0, sizeof(int) * kQueueWords));
   CK(cudaMalloc(&d_io, sizeof(EvalIO)));
   for (auto& sg : stages) {
     CK(cudaMallocHost(&sg.io, sizeof(EvalIO)));
@@ -98,7 +100,7 @@ nnp_ctx::~nnp_ctx() {
   void* bufs[] = {b_bin_count, b_bin_start, b_bin_len, b_atom_bin, b_atom_slot, b_atom_cell,
                   b_atom_sys, b_atom_off, b_row_atom, b_row_info, b_row_cell, b_pos4, b_cnt_r,
                   b_cnt_a, b_nbr_r, b_G, b_dEdG, b_Ei, b_Gh, b_sys, b_pos_stage,
-                  b_Z_stage, b_F_stage, b_E_stage, b_seg, b_flags, d_zlut, d_io, b_wf32,
+                  b_Z_stage, b_F_stage, b_E_stage, b_seg, b_flags, b_queue, d_zlut, d_io, b_wf32,
                   fm_z, fm_dz, fm_t, fm_p, fm_v, fm_ref, fm_grad, fm_jobs,
                   mm.pos, mm.F, mm.sub_pos, mm.sub_F, mm.ld, mm.E, mm.Z, mm.sub_Z, mm.idx, mm.mark,
                   b_pair_cur, b_pairs_stage, b_shifts_stage, d_ee, d_io_q, b_ee_mmhi, b_ee_mmlo,

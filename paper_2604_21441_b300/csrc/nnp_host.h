@@ -21,7 +21,7 @@ __global__ void k_cells_small(const EvalIO* io, const SysDesc* sys, const signed
 // grid: blocks for a warp per cell (systems above kNbrRowsSmall rows); rows and
 // cells (totals over systems) choose the small-system form and its split
 void launch_neighbors(int grid, cudaStream_t st, const EvalIO* io, const SysDesc* sys, const DescParams& P,
-                      const Workspace& ws, long long rows, long long cells, int nsm);
+                      const Workspace& ws, long long rows, long long cells, int nsm, int dyn = 0);
 void set_cell_steps(SysDesc& sd);  // cell steps and their inverse from nc, ell or B
 void launch_wait_selftest(cudaStream_t st, int* flags, unsigned long long limit_ns);
 __global__ void k_pairs_prep(int S, Workspace ws);
@@ -35,11 +35,11 @@ cudaError_t neighbors_set_smem_limits();
 // rows: upper bound of the rows of the evaluation (grid sizing only)
 // per_sm: cap on resident blocks per SM of the grid (0 = built-in default)
 void launch_aev_fwd(long long rows, int nsm, cudaStream_t st, const SysDesc* sys, const DescParams& P,
-                    const Workspace& ws, int mode /* GMode */, int per_sm = 0);
+                    const Workspace& ws, int mode /* GMode */, int per_sm = 0, int tile = 0);
 // k_aev_bwd: forces accumulate in FP64 straight into io->forces (zeroed
 // by k_bin)
 void launch_aev_bwd(long long rows, int nsm, cudaStream_t st, const EvalIO* io, const SysDesc* sys,
-                    const DescParams& P, const Workspace& ws, int per_sm = 0);
+                    const DescParams& P, const Workspace& ws, int per_sm = 0, int tile = 0);
 cudaError_t aev_set_smem_limits();
 
 // k_mlp_f32.cu
@@ -105,6 +105,7 @@ struct nnp_ctx {
   size_t c_pos_stage = 0, c_Z_stage = 0, c_F_stage = 0, c_E_stage = 0;
   int* b_seg = nullptr;
   int* b_flags = nullptr;
+  int* b_queue = nullptr;       // work-queue counters (Workspace::queue)
   signed char* d_zlut = nullptr;
   nnp::EvalIO* d_io = nullptr;
   nnp::EvalIO* h_io = nullptr;  // pinned; the staging slot of the last evaluation
@@ -186,8 +187,12 @@ struct nnp_ctx {
            c_mark = 0;
   } mm;
 
-  // launch shape (blocks per SM caps), chosen by the autotuner (NNP_FLAG_AUTOTUNE)
-  struct Tune { int nbr = 16, fwd = 8, bwd = 16; } tune;
+  // launch shapes, chosen by the autotuner (NNP_FLAG_AUTOTUNE): blocks-per-SM
+  // caps of the persistent neighbour, descriptor and descriptor-backward
+  // grids; the row tiles of the two descriptor kernels (row pairs for the
+  // descriptor, rows for its backward), > 0 drawn from the work queue, < 0 in
+  // static order; nbr_dyn: the neighbour kernel draws its cells from the queue
+  struct Tune { int nbr = 16, fwd = 8, bwd = 16, fwd_tile = -1, bwd_tile = -1, nbr_dyn = 0; } tune;
   long long tuned_key = -1;
   int autotune(long long n, int B, long long bins, long long rows);
 

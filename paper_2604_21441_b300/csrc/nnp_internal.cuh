@@ -178,10 +178,59 @@ struct Workspace {
   int* flags;       // [kNumFlags]
   int* q8;          // FP8 form, [kMaxS * 8] per species: calibrated |max| of G, h1, h2 as
                     // float bits at [0, 3) (raised by atomicMax); the rest unused
+  int* queue;       // [kQueueWords] work-queue counters (zero between launches)
   int cap_r;        // radial list capacity per row
   int cap_a;        // angular neighbours per row that the descriptor kernels stage
   long long max_rows;
 };
+
+// Work distribution of the persistent kernels.  Static: warp w of the launch
+// takes items w, w + W, w + 2W, ... (W warps).  Dynamic: warp w takes item w
+// first, then the items after the first W from a queue, one atomic add each,
+// requested one item ahead once the warp has finished its first (so the
+// requests do not all arrive at the start of the launch).  Each stage has a
+// pair of counters (items handed out, warps done); the last warp of a
+// dynamic launch to finish puts both back to zero for the next launch.
+enum QueueSlot { kQNbr = 0, kQFwd = 2, kQBwd = 4, kQueueWords = 8 };
+
+struct WorkQueue {
+  int* q;
+  int base;       // warps of the launch
+  int cur;        // the warp's current item (static order)
+  int req;        // lane 0: the counter value requested ahead
+  bool pending;   // a request is in flight (warp-uniform)
+  bool dyn;
+  __device__ __forceinline__ WorkQueue(int* counters, bool dynamic)
+      : q(counters), base((int)(gridDim.x * (blockDim.x >> 5))), cur(0), req(0), pending(false),
+        dyn(dynamic) {}
+  // the warp's first item
+  __device__ __forceinline__ int first() {
+    cur = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    return cur;
+  }
+  // the next item after the one just finished
+  __device__ __forceinline__ int next(int lane) {
+    if (!dyn) return cur += base;
+    if (!pending && lane == 0) req = atomicAdd(q, 1);
+    const int it = __shfl_sync(0xffffffffu, req, 0);
+    if (lane == 0) req = atomicAdd(q, 1);  // one ahead
+    pending = true;
+    return base + it;
+  }
+};
+
+// every warp of a dynamic launch calls this once, after its last request
+__device__ __forceinline__ void queue_warp_done(const WorkQueue& wq, int lane) {
+  int* q = wq.q;
+  if (wq.dyn && lane == 0) {
+    __threadfence();
+    const int total = (int)(gridDim.x * (blockDim.x >> 5));
+    if (atomicAdd(q + 1, 1) == total - 1) {
+      atomicExch(q, 0);
+      atomicExch(q + 1, 0);
+    }
+  }
+}
 
 // FP32 network weights per species: W_l row-major (fan_in x fan_out) and the
 // transposed copies W_l^T used by the backward pass.

@@ -10,7 +10,8 @@
 //
 // How: every per-call scratch buffer of the evaluation (cell bins, sorted
 // rows, neighbour lists, descriptors, their gradients, per-atom energies,
-// flags and the small per-call descriptors) is carved out of one file-scope
+// flags, work-queue counters and the small per-call descriptors) is carved
+// out of one file-scope
 // static device array, g_noalloc_scratch, of fixed size.  The kernels are the
 // library's ordinary kernels; only the workspace they are given differs.
 // Weights and model constants come from the context.
@@ -67,7 +68,8 @@ constexpr size_t o_G = o_nbr_r + al256(sizeof(int) * kNAMaxRows * kNACapR);
 constexpr size_t o_dEdG = o_G + al256(sizeof(float) * kNAMaxRows * kNAMaxD);
 constexpr size_t o_Ei = o_dEdG + al256(sizeof(float) * kNAMaxRows * kNAMaxD);
 constexpr size_t o_flags = o_Ei + al256(sizeof(float) * kNAMaxRows);
-constexpr size_t o_io = o_flags + al256(sizeof(int) * kNumFlags);
+constexpr size_t o_queue = o_flags + al256(sizeof(int) * kNumFlags);
+constexpr size_t o_io = o_queue + al256(sizeof(int) * kQueueWords);
 constexpr size_t o_sys = o_io + al256(sizeof(EvalIO));
 constexpr size_t kScratchBytes = o_sys + al256(sizeof(SysDesc));
 static_assert(kScratchBytes <= 8u * 1024u * 1024u, "scratch must stay within 8 MiB");
@@ -241,6 +243,7 @@ extern "C" int nnp_eval_noalloc(nnp_ctx* ctx, int64_t n, const double* pos, cons
   w.dEdG = reinterpret_cast<float*>(base + o_dEdG);
   w.Ei = reinterpret_cast<float*>(base + o_Ei);
   w.flags = reinterpret_cast<int*>(base + o_flags);
+  w.queue = reinterpret_cast<int*>(base + o_queue);
   w.cap_r = kNACapR;
   w.cap_a = kNACapA;
   w.max_rows = kNAMaxRows;
@@ -264,6 +267,7 @@ extern "C" int nnp_eval_noalloc(nnp_ctx* ctx, int64_t n, const double* pos, cons
   // the array keeps the last call's contents: clear what must start at zero
   NA_CK(cudaMemsetAsync(w.bin_count, 0, sizeof(int) * bins, st));
   NA_CK(cudaMemsetAsync(w.flags, 0, sizeof(int) * kNumFlags, st));
+  NA_CK(cudaMemsetAsync(w.queue, 0, sizeof(int) * kQueueWords, st));
   NA_CK(cudaMemcpyAsync(d_io, &io, sizeof io, cudaMemcpyHostToDevice, st));
   NA_CK(cudaMemcpyAsync(d_sys, &sd, sizeof sd, cudaMemcpyHostToDevice, st));
   k_bin<<<g_atoms, 256, 0, st>>>(d_io, d_sys, ctx->d_zlut, w);

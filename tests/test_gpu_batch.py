@@ -1,7 +1,9 @@
 """The batched form on the full 256-box workload (16-2,048 waters per box,
-338,622 atoms): one graph launch over all systems, autotuned launch shapes.
-Sampled systems against the oracle (FP32 bounds), every system against a
-separate single-system evaluation."""
+338,622 atoms): one graph launch over all systems, whose persistent kernels
+draw (system, cell) and (system, row-tile) work items from their queues, with
+autotuned grid caps and tiles.  Sampled systems (the two smallest, the
+median, the largest) against the oracle (FP32 bounds), every system against
+a separate single-system evaluation."""
 import numpy as np
 import pytest
 
@@ -30,13 +32,21 @@ def test_batch_256(oracle_mod):
     pot.set_all_weights(w32)
     E, F = pot.eval_batch(off, pos, Z, boxes)
     E, F = E.cpu().numpy(), F.cpu().numpy()
-    assert pot.query("tune_backward") in (4, 8, 16, 32)
+    tuned = {k: pot.query("tune_" + k) for k in ("neighbours", "descriptor", "backward",
+                                                  "descriptor_tile", "backward_tile", "neighbours_queue")}
+    print("batch-256 tuned shapes:", tuned)
+    # one of the autotuner's candidates (tile < 0: static order, > 0: queue)
+    assert tuned["neighbours"] in (4, 8, 16, 32) and tuned["neighbours_queue"] in (0, 1)
+    assert (tuned["descriptor"], tuned["descriptor_tile"]) in {
+        (2, -1), (4, -1), (8, -1), (16, -1), (8, 1), (8, 2), (8, 4), (16, 2)}
+    assert (tuned["backward"], tuned["backward_tile"]) in {
+        (4, -1), (8, -1), (16, -1), (32, -1), (16, 2), (16, 4), (32, 4), (8, 8)}
     # every system against its own single-system evaluation: the same kernels
-    # on the same neighbour lists; only the order of the FP32 sums differs
-    # (energy partial sums per warp start at other row offsets; forces are
-    # accumulated by FP32 atomic reductions in launch order).  Force sums
-    # run over ~10^2 terms of up to ~1 eV/A, so 1e-5 eV/A bounds their
-    # rounding with margin (the parity bound against the oracle is 1e-4).
+    # on the same neighbour lists; only the order of the sums differs (energy
+    # partial sums per warp start at other row offsets; the FP64 force
+    # reductions add FP32 terms in launch order, and a system's row order
+    # inside its cells is the same).  1e-5 eV/A bounds that with margin (the
+    # parity bound against the oracle is 1e-4).
     single = P.NNP(atomic_numbers=(1, 8), max_atoms=int(max(s.n for s in systems)))
     single.set_all_weights(w32)
     for b, s in enumerate(systems):
@@ -47,7 +57,7 @@ def test_batch_256(oracle_mod):
     p = oracle_mod.Params()
     m = oracle_mod.Model(p, w)
     order = np.argsort([s.n for s in systems])
-    for b in (order[0], order[1], order[len(order) // 2]):
+    for b in (order[0], order[1], order[len(order) // 2], order[-1]):
         s = systems[b]
         Er, Eir, Fr, _ = oracle_mod.energy_forces(m, s.pos, p.species_of(s.Z), s.box)
         assert energy_error(E[b], Er, Eir) <= E_REL_TOL
