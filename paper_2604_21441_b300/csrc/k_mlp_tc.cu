@@ -256,6 +256,49 @@ __device__ __forceinline__ void red_add_v4(float4* o, float x, float y, float z,
 }
 
 // Issue the TMEM load of 16 columns (no wait).
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16]);
+__device__ __forceinline__ void tmem_wait_ld();
+
+// Epilogue of an accumulator block of ncols (<= 128, a multiple of 16)
+// columns: the warp's 32 rows (TMEM lanes) x columns [32 h, 32 h + 32) go
+// through a warp-private staging area of 32 x 8 float4 (4 KB; float4 k of row
+// r at r * 8 + (k ^ (r & 7)), so that neither the row-per-lane writes nor the
+// row-by-row reads conflict on banks) and leave as whole 128-byte lines:
+// eight lanes per row, four rows per instruction.  out points at column 0 of
+// the warp's first row, ld is the row stride; acc = 1 adds with FP32
+// vector reductions, 0 stores.
+__device__ __forceinline__ void store_block_staged(uint32_t tcol, int h, int lane, float* out, int ld,
+                                                   int ncols, float4* stage, int acc) {
+  const int c0 = 32 * h;
+  if (c0 >= ncols) return;  // warp-uniform
+  const bool two = c0 + 16 < ncols;
+  uint32_t a[16], b[16];
+  tmem_ld16_nowait(tcol + c0, a);
+  if (two) tmem_ld16_nowait(tcol + c0 + 16, b);
+  tmem_wait_ld();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    stage[lane * 8 + (k ^ (lane & 7))] = make_float4(__uint_as_float(a[4 * k]), __uint_as_float(a[4 * k + 1]),
+                                                     __uint_as_float(a[4 * k + 2]), __uint_as_float(a[4 * k + 3]));
+    if (two)
+      stage[lane * 8 + ((k + 4) ^ (lane & 7))] =
+          make_float4(__uint_as_float(b[4 * k]), __uint_as_float(b[4 * k + 1]), __uint_as_float(b[4 * k + 2]),
+                      __uint_as_float(b[4 * k + 3]));
+  }
+  __syncwarp();
+  const int kk = lane & 7, nk = two ? 8 : 4;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int row = 4 * j + (lane >> 3);
+    if (kk < nk) {
+      const float4 v = stage[row * 8 + (kk ^ (row & 7))];
+      float4* o = reinterpret_cast<float4*>(out + (size_t)row * ld + c0 + 4 * kk);
+      if (acc) red_add_v4(o, v.x, v.y, v.z, v.w);
+      else *o = v;
+    }
+  }
+  __syncwarp();  // the staging area is read before the warp writes it again
+}
 __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
@@ -324,7 +367,10 @@ __device__ __forceinline__ void for_chunks2(uint32_t tcol, uint32_t tcol2, int h
 }
 
 // Work items are (tile, member) pairs for members m0 .. m0 + nm - 1 of the
-// weight sets Wts / Wfs (device arrays), tile-major within a member.  accm =
+// weight sets Wts / Wfs (device arrays), member-minor: the members of one
+// tile are consecutive items, so they run at the same time on neighbouring
+// CTAs, which read the tile's descriptor rows from DRAM once between them
+// and whose dE/dG reductions meet in L2.  accm =
 // 1: E_i and dE/dG are added with reductions into buffers the caller zeroed
 // (members running side by side); 0: written.
 template <int D, bool F8>
@@ -466,20 +512,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(const EvalIO* __restri
   const int nwork = ntiles * nm;
   int wi = blockIdx.x;
   if (wi < nwork && tid == 0) {
-    const int t0 = wi % ntiles;
+    const int t0 = wi / nm;
     load_tile(t0);
-    load_wm(Wts[m0 + wi / ntiles], pos4_species(ws.pos4[t0 * kTM]), 0, 0);
+    load_wm(Wts[m0 + wi % nm], pos4_species(ws.pos4[t0 * kTM]), 0, 0);
   }
   for (; wi < nwork; wi += gridDim.x) {
-    const int tile = wi % ntiles;
-    cur_w = Wts + m0 + wi / ntiles;
-    cur_f = Wfs + m0 + wi / ntiles;
+    const int tile = wi / nm;
+    cur_w = Wts + m0 + wi % nm;
+    cur_f = Wfs + m0 + wi % nm;
     const int row0 = tile * kTM;
     const int sp = pos4_species(ws.pos4[row0]);
     const int nwi = wi + gridDim.x;
     const bool has_next = nwi < nwork;
-    const int next = has_next ? nwi % ntiles : 0;
-    const MlpTcWeights& next_w = Wts[m0 + (has_next ? nwi / ntiles : 0)];
+    const int next = has_next ? nwi / nm : 0;
+    const MlpTcWeights& next_w = Wts[m0 + (has_next ? nwi % nm : 0)];
     const int sp_next = has_next ? pos4_species(ws.pos4[next * kTM]) : 0;
     const int row = row0 + r;
     const int my_atom = ws.row_atom[row];  // consumed by the energy epilogue
@@ -634,16 +680,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(const EvalIO* __restri
         l1_issued = true;
       }
     }
-    {
-      float* out = ws.dEdG + (size_t)row * D;
-      for_chunks<D>(tdg, h, [&](int c0, float (&v)[16]) {
-#pragma unroll
-        for (int j = 0; j < 16; j += 4) {
-          float4* o = reinterpret_cast<float4*>(out + c0 + j);
-          if (accm) red_add_v4(o, v[j], v[j + 1], v[j + 2], v[j + 3]);
-          else *o = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-        }
-      });
+    {  // staged through bufC (h2 / g3, read) and wbuf[1] (W1 backward, read)
+      float4* stage = reinterpret_cast<float4*>(warp < 8 ? bufC + warp * 4096 : wbuf[1] + (warp - 8) * 4096);
+      store_block_staged(tdg, h, lane, ws.dEdG + (size_t)(row0 + quarter * 32) * D, D, D, stage, accm);
     }
   }
   // on abort: give this CTA's outstanding copies and MMAs a bounded chance to land
@@ -663,17 +702,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(const EvalIO* __restri
 // and epilogues, with the two products that involve D split into pieces that
 // fit shared and tensor memory.
 //
-// * Layer 1, z1 = G W1: K in chunks of two slabs (128 features) through two
-//   stages, stage 0 = (bufA, wbuf[0]) and stage 1 = (bufC, wbuf[1]); each
-//   chunk's G slabs and W1^T slabs arrive on one barrier, and a stage is
-//   reloaded once the MMAs that read it have completed (their own barrier,
-//   bars 5 and 6, waited by thread 0 only).
+// * Layer 1, z1 = G W1: K one slab (64 features) at a time through four
+//   stages; stage s takes G in bufA (s = 0, 1) or bufC (s = 2, 3) and W1^T in
+//   wbuf[s / 2] (two 20 KB halves).  A slab's G and W1^T arrive on one barrier
+//   (bars 10-13), and a stage is reloaded once the MMAs that read it have
+//   completed (bars 14-17, waited by thread 0 only), so three slabs are in
+//   flight while one is multiplied.
 // * dE/dG = g1 W1^T: output columns in blocks of 128.  A block's weights are
 //   the matching 128 rows of each of the three K slabs of the backward W1
-//   image (three bulk copies); blocks alternate between wbuf[1] / wbuf[0] and
-//   between TMEM columns [384,512) / [256,384), and the next block's MMA runs
-//   under this block's epilogue.  Blocks complete on bars 7 and 8, which every
-//   thread waits on in turn.
+//   image (three bulk copies).  Blocks alternate between wbuf[1] and wbuf[0];
+//   the four 128-column quarters of tensor memory (all free after the g1
+//   epilogue) take the accumulators in turn, and the next block's MMA runs
+//   under this block's epilogue.  Blocks complete on bars 7 and 8, which
+//   every thread waits on in turn.  The epilogue stages each warp's 32 rows x
+//   32 columns in bufA or bufC (free once the backward MMAs that read g2 and
+//   g3 are done) and writes whole 128-byte lines.
 // The G tile is not fetched ahead of the tile, so layer 1 starts each tile
 // with the latency of its first chunk.
 // switch cases over the species counts with a wide descriptor (3..8)
@@ -684,8 +727,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(const EvalIO* __restri
   case 6: CALL(6); break;    \
   case 7: CALL(7); break;    \
   default: CALL(8); break;
-constexpr int kWideKC = 2;    // slabs per layer-1 chunk
+constexpr int kWideKC = 2;    // slabs of G that bufA and bufC each hold
 constexpr int kWideNC = 128;  // dE/dG columns per block
+constexpr int kWideBars = 18; // mbarriers of k_mlp_tc_wide
 
 template <int D>
 __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __restrict__ io, DescParams P,
@@ -697,11 +741,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
   constexpr int kBufC = slabs_of(kH2) * kSlab;  // G chunk (stage 1), h2, later g3
   constexpr int kWBuf = 48 * 1024;
   constexpr int kSl = slabs_of(D);                          // slabs of G and of W1^T
-  constexpr int kNC1 = (kSl + kWideKC - 1) / kWideKC;       // layer-1 chunks
   constexpr int kNCB = (D + kWideNC - 1) / kWideNC;         // dE/dG blocks
   static_assert(D % 16 == 0 && D > kH2, "wide descriptor");
   static_assert(kBufA >= slabs_of(kH2) * kSlab && kBufC >= kWideKC * kSlab, "stage buffers");
-  static_assert(kWideKC * kH1 * 128 <= kWBuf && slabs_of(kH1) * kWideNC * 128 <= kWBuf, "weight buffers");
+  static_assert(2 * kH1 * 128 <= kWBuf && slabs_of(kH1) * kWideNC * 128 <= kWBuf, "weight buffers");
   constexpr int kNB = kH1 + kH2 + kH3 + kH3 + 1;  // b1 b2 b3 w4 b4
 
   extern __shared__ uint8_t smraw[];
@@ -710,10 +753,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
   uint8_t* bufB = bufA + kBufA;
   uint8_t* bufC = bufB + kBufB;
   uint8_t* wbuf[2] = {bufC + kBufC, bufC + kBufC + kWBuf};
-  // [0,1] stage / weight copies, [3] MMAs, [4] layer 1 done, [5,6] layer-1
-  // stage MMAs, [7,8] dE/dG blocks, [9] drain on abort ([2] unused)
+  // [0,1] weight copies, [3] MMAs, [4] layer 1 done, [7,8] dE/dG blocks,
+  // [9] drain on abort, [10-13] layer-1 stage copies, [14-17] layer-1 stage
+  // MMAs ([2], [5], [6] unused)
   uint64_t* bars = reinterpret_cast<uint64_t*>(wbuf[1] + kWBuf);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 10);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kWideBars);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
   float* sE = reinterpret_cast<float*>(abort_flag + 1);  // [kG][kTM] partial energies
   float* sb = sE + kG * kTM;                             // [kNB] biases and w4 of the tile's species
@@ -731,7 +775,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
   const int ntiles = rows / kTM;
 
   if (tid == 0) {
-    for (int i = 0; i < 10; ++i) mbar_init(&bars[i], 1);
+    for (int i = 0; i < kWideBars; ++i) mbar_init(&bars[i], 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -744,11 +788,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
   const uint32_t tz1 = tmem + lb + 0, tz2 = tmem + lb + 160, tz3 = tmem + lb + 288, tg2 = tmem + lb + 384,
                  tg1 = tmem + lb + 160;
   const uint32_t mz1 = tmem + 0, mz2 = tmem + 160, mz3 = tmem + 288, mg2 = tmem + 384, mg1 = tmem + 160;
-  auto dg_col = [](int q) -> uint32_t { return q ? 256u : 384u; };  // TMEM columns of even / odd dE/dG blocks
+  // dE/dG block cb: accumulator in TMEM columns [128 (cb & 3), + 128); weights
+  // in wbuf[1] (even cb, copies on bar 1) or wbuf[0] (odd cb, bar 0)
+  auto dg_col = [](int cb) -> uint32_t { return (uint32_t)(cb & 3) * 128u; };
+  auto dg_bar = [](int cb) -> int { return (cb & 1) ? 0 : 1; };
+  auto dg_slab = [&](int cb, int k) -> uint8_t* { return wbuf[dg_bar(cb)] + (size_t)k * kWideNC * 128; };
+  static_assert(8 * 4096 <= kBufA && 8 * 4096 <= kBufC, "dE/dG staging");
 
   uint32_t ph[4] = {0, 0, 0, 0};
   bool pend[4] = {false, false, false, false};
-  uint32_t ph56[2] = {0, 0}, ph78[2] = {0, 0}, ph4 = 0;
+  uint32_t ph78[2] = {0, 0}, ph4 = 0;
+  uint32_t phL[4] = {0, 0, 0, 0}, phM[4] = {0, 0, 0, 0};  // layer-1 stage copies / MMAs
+  bool pendL[4] = {false, false, false, false};
   bool pend4 = false;
 
   const MlpTcWeights* cur_w = Wts + m0;  // the current work item's member
@@ -765,23 +816,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
     bulk_g2s(wbuf[b], cur_w->m[sp][which], (uint32_t)bytes, &bars[b]);
     pend[b] = true;
   };
-  auto load_chunk = [&](int t, int sp, int c) {  // layer-1 chunk c into stage c & 1
-    const int b = c & 1, s0 = c * kWideKC, ns = min(kWideKC, kSl - s0);
-    const uint32_t gb = (uint32_t)(ns * kSlab), wbytes = (uint32_t)(ns * kH1 * 128);
-    mbar_expect_tx(&bars[b], gb + wbytes);
-    bulk_g2s(b ? bufC : bufA, reinterpret_cast<const uint8_t*>(ws.Gh) + (size_t)t * gh_tile_bytes(D) +
-                                  (size_t)s0 * kSlab, gb, &bars[b]);
-    bulk_g2s(wbuf[b], cur_w->m[sp][0] + (size_t)s0 * kH1 * 128, wbytes, &bars[b]);
-    pend[b] = true;
+  auto stage_g = [&](int st) { return (st < 2 ? bufA : bufC) + (size_t)(st & 1) * kSlab; };
+  auto stage_w = [&](int st) { return wbuf[st >> 1] + (size_t)(st & 1) * kH1 * 128; };
+  auto load_slab = [&](int t, int sp, int k) {  // G and W1^T slab k into stage k & 3
+    const int st = k & 3;
+    mbar_expect_tx(&bars[10 + st], (uint32_t)(kSlab + kH1 * 128));
+    bulk_g2s(stage_g(st), reinterpret_cast<const uint8_t*>(ws.Gh) + (size_t)t * gh_tile_bytes(D) +
+                              (size_t)k * kSlab, (uint32_t)kSlab, &bars[10 + st]);
+    bulk_g2s(stage_w(st), cur_w->m[sp][0] + (size_t)k * kH1 * 128, (uint32_t)(kH1 * 128), &bars[10 + st]);
+    pendL[st] = true;
   };
-  auto load_block = [&](int sp, int cb, int b) {  // dE/dG block cb's W1 rows into wbuf[b]
-    const int n0 = cb * kWideNC, nc = min(kWideNC, D - n0);
+  auto load_block = [&](int sp, int cb) {  // dE/dG block cb's W1 rows into its weight buffer
+    const int n0 = cb * kWideNC, nc = min(kWideNC, D - n0), b = dg_bar(cb);
     const uint32_t bytes = (uint32_t)(nc * 128);
     mbar_expect_tx(&bars[b], (uint32_t)slabs_of(kH1) * bytes);
     for (int k = 0; k < slabs_of(kH1); ++k)
-      bulk_g2s(wbuf[b] + (size_t)k * bytes, cur_w->m[sp][5] + (size_t)k * D * 128 + (size_t)n0 * 128, bytes,
-               &bars[b]);
+      bulk_g2s(dg_slab(cb, k), cur_w->m[sp][5] + (size_t)k * D * 128 + (size_t)n0 * 128, bytes, &bars[b]);
     pend[b] = true;
+  };
+  // D[128 x nc] = g1 (bufB, K = 160) x the block's weights (three slabs)
+  auto issue_block = [&](int cb) {
+    const int nc = min(kWideNC, D - cb * kWideNC);
+    const uint32_t idesc = idesc_bf16(kTM, nc), a0 = smem_u32(bufB);
+    for (int k = 0; k < kH1 / 16; ++k) {
+      const uint32_t a = a0 + (uint32_t)(k >> 2) * kSlab + (uint32_t)(k & 3) * 32;
+      const uint32_t b = smem_u32(dg_slab(cb, k >> 2)) + (uint32_t)(k & 3) * 32;
+      mma_bf16(tmem + dg_col(cb), sw128_desc(a), sw128_desc(b), idesc, k > 0 ? 1u : 0u);
+    }
   };
   auto commit = [&]() {
     mma_commit(&bars[3]);
@@ -818,9 +879,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
   };
 
   for (int wi = blockIdx.x; wi < ntiles * nm; wi += gridDim.x) {
-    const int tile = wi % ntiles;
-    cur_w = Wts + m0 + wi / ntiles;
-    cur_f = Wfs + m0 + wi / ntiles;
+    const int tile = wi / nm;  // member-minor, as in k_mlp_tc
+    cur_w = Wts + m0 + wi % nm;
+    cur_f = Wfs + m0 + wi % nm;
     const int row0 = tile * kTM;
     const int sp = pos4_species(ws.pos4[row0]);
     const int row = row0 + r;
@@ -836,22 +897,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
       sb[i] = v;
     }
     if (!phase(-1, -1)) break;  // biases published; every buffer of the last tile is free
-    // ---------------- layer 1: z1 = G W1, K in chunks through two stages
+    // ---------------- layer 1: z1 = G W1, K one slab at a time through four stages
     if (tid == 0) {
-      load_chunk(tile, sp, 0);
-      if (kNC1 > 1) load_chunk(tile, sp, 1);
-      for (int c = 0; c < kNC1 && *abort_flag == 0; ++c) {
-        const int b = c & 1;
-        wait0(b);
-        if (*abort_flag) break;
+      for (int k = 0; k < 4 && k < kSl; ++k) load_slab(tile, sp, k);
+      for (int c = 0; c < kSl && *abort_flag == 0; ++c) {
+        const int st = c & 3;
+        if (mbar_wait(&bars[10 + st], phL[st])) {
+          phL[st] ^= 1u;
+          pendL[st] = false;
+        } else {
+          timeout();
+          break;
+        }
         tc_fence_after();
-        const int kc = min(kWideKC * 64, D - c * kWideKC * 64);
-        issue_gemm<false>(mz1, b ? bufC : bufA, wbuf[b], kH1, kc, c > 0 ? 1u : 0u);
-        if (c + 2 < kNC1) mma_commit(&bars[5 + b]);  // stage b is reloaded once these MMAs are done
-        if (c >= 1 && c + 1 < kNC1) {                 // chunk c - 1 has been read: reload its stage
-          if (mbar_wait(&bars[5 + (b ^ 1)], ph56[b ^ 1])) ph56[b ^ 1] ^= 1u;
+        issue_gemm<false>(mz1, stage_g(st), stage_w(st), kH1, min(64, D - 64 * c), c > 0 ? 1u : 0u);
+        if (c + 4 < kSl) mma_commit(&bars[14 + st]);  // stage st is reloaded once these MMAs are done
+        if (c >= 1 && c + 3 < kSl) {                   // slab c - 1 has been read: its stage takes c + 3
+          const int sq = (c - 1) & 3;
+          if (mbar_wait(&bars[14 + sq], phM[sq])) phM[sq] ^= 1u;
           else timeout();
-          if (*abort_flag == 0) load_chunk(tile, sp, c + 1);
+          if (*abort_flag == 0) load_slab(tile, sp, c + 3);
         }
       }
       mma_commit(&bars[4]);
@@ -948,55 +1013,44 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
     // ---------------- backward 2: g1' = g2 W2^T
     if (!phase(0, -1)) break;
     if (tid == 0) {
-      load_block(sp, 0, 1);  // dE/dG block 0 -> wbuf[1]
+      load_block(sp, 0);  // dE/dG block 0 -> wbuf[1] (free since backward 3)
       tc_fence_after();
       issue_gemm<false>(mg1, bufA, wbuf[0], kH1, kH2);
       commit();
     }
     wait_mma();
-    if (tid == 0 && kNCB > 1) load_block(sp, 1, 0);  // wbuf[0] is free: block 1
+    if (tid == 0 && kNCB > 1) load_block(sp, 1);  // wbuf[0] is free: block 1
     for_chunks2<kH1>(tg1, tz1, h, [&](int c0, float (&g)[16], float (&d)[16]) {
 #pragma unroll
       for (int j = 0; j < 16; ++j) g[j] *= d[j];
       store_row16(bufB, r, c0, g);
     });
     // ---------------- backward 1: dE/dG = g1 W1^T in column blocks
-    if (!phase(1, -1)) break;
+    if (!phase(1, -1)) break;  // g1 written; block 0's weights have landed
     if (tid == 0) {
       tc_fence_after();
-      issue_gemm<false>(tmem + dg_col(0), bufB, wbuf[1], min(kWideNC, D), kH1);
+      issue_block(0);
       mma_commit(&bars[7]);
     }
     bool ok = true;
     for (int cb = 0; cb < kNCB; ++cb) {
-      const int q = cb & 1, wb = q ? 0 : 1;  // block cb: weights in wbuf[wb], accumulator dg_col(q)
+      const int q = cb & 1;  // block cb completes on bars[7 + q]
       const int n0 = cb * kWideNC, nc = min(kWideNC, D - n0);
       if (tid == 0 && cb + 1 < kNCB) {  // the next block's MMA runs under this block's epilogue
-        wait0(wb ^ 1);
+        wait0(dg_bar(cb + 1));
         if (*abort_flag == 0) {
           tc_fence_after();
-          issue_gemm<false>(tmem + dg_col(q ^ 1), bufB, wbuf[wb ^ 1], min(kWideNC, D - n0 - kWideNC), kH1);
+          issue_block(cb + 1);
         }
         mma_commit(&bars[7 + (q ^ 1)]);
       }
       wait_bar(&bars[7 + q], ph78[q]);
-      if (tid == 0 && cb + 2 < kNCB && *abort_flag == 0) load_block(sp, cb + 2, wb);
-      float* out = ws.dEdG + (size_t)row * D + n0;
-      const uint32_t tb = tmem + lb + dg_col(q);
-      for (int c = h; c < nc / 16; c += kG) {
-        uint32_t a[16];
-        tmem_ld16_nowait(tb + c * 16, a);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 16; j += 4) {
-          float4* o = reinterpret_cast<float4*>(out + c * 16 + j);
-          const float4 x = make_float4(__uint_as_float(a[j]), __uint_as_float(a[j + 1]), __uint_as_float(a[j + 2]),
-                                       __uint_as_float(a[j + 3]));
-          if (accm) red_add_v4(o, x.x, x.y, x.z, x.w);
-          else *o = x;
-        }
-      }
-      if (!phase(-1, -1)) {  // this block's TMEM columns have been read before block cb + 2 reuses them
+      // block cb's weights have been read: its buffer takes block cb + 2
+      if (tid == 0 && cb + 2 < kNCB && *abort_flag == 0) load_block(sp, cb + 2);
+      float4* stage = reinterpret_cast<float4*>(warp < 8 ? bufA + warp * 4096 : bufC + (warp - 8) * 4096);
+      store_block_staged(tmem + lb + dg_col(cb), h, lane, ws.dEdG + (size_t)(row0 + quarter * 32) * D + n0, D, nc,
+                         stage, accm);
+      if (!phase(-1, -1)) {  // this block's TMEM columns have been read before block cb + 4 reuses them
         ok = false;
         break;
       }
@@ -1007,6 +1061,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
   if (tid == 0 && *abort_flag) {
     for (int i = 0; i < 2; ++i)
       if (pend[i]) mbar_wait(&bars[i], ph[i]);
+    for (int i = 0; i < 4; ++i)
+      if (pendL[i]) mbar_wait(&bars[10 + i], phL[i]);
     mma_commit(&bars[9]);
     mbar_wait(&bars[9], 0);
   }
@@ -1151,7 +1207,7 @@ cudaError_t set_smem(size_t sm) {
 
 size_t smem_bytes_wide() {
   return 1024 + (size_t)kWideKC * kSlab + slabs_of(kH1) * kSlab + slabs_of(kH2) * kSlab + 2 * 48 * 1024 +
-         10 * 8 + 8 + kG * kTM * 4 + (kH1 + kH2 + 2 * kH3 + 1) * 4 + 64;
+         kWideBars * 8 + 8 + kG * kTM * 4 + (kH1 + kH2 + 2 * kH3 + 1) * 4 + 64;
 }
 
 template <int S>

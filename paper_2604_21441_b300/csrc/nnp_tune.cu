@@ -9,7 +9,7 @@
 // the first synchronous evaluation of a (species, precision, row-count
 // bucket, batch or single) the tuner runs the pipeline directly (no graph)
 // over eight candidate shapes per kernel, evaluated side by side (candidate
-// i of every kernel in the same run), times each stage with CUDA events (two
+// i of every kernel in the same run), times each stage with CUDA events (three
 // repetitions after a warm-up), keeps the fastest shape per stage, and caches
 // it in memory and, if the environment variable NNP_AUTOTUNE_CACHE names a
 // file, in that file ("key nbr fwd bwd fwd_tile bwd_tile nbr_queue" lines)
@@ -90,7 +90,7 @@ int nnp_ctx::autotune(long long n, int B, long long bins, long long rows) {
   Tune st_best = tune, dy_best = tune;
   int rc = launch_pipeline(n, B, bins, rows);  // warm-up
   if (rc) return rc;
-  for (int rep = 0; rep < 2 && !rc; ++rep)
+  for (int rep = 0; rep < 3 && !rc; ++rep)
     for (int i = 0; i < kC && !rc; ++i) {
       tune = Tune{cand_nbr[i][0], cand_fwd[i][0], cand_bwd[i][0], cand_fwd[i][1], cand_bwd[i][1], cand_nbr[i][1]};
       rc = launch_pipeline(n, B, bins, rows);
