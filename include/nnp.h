@@ -122,8 +122,9 @@ typedef struct {
     void *stream;             /* cudaStream_t to run on; NULL = the library makes one */
     uint32_t flags;           /* NNP_FLAG_* */
     int32_t n_members;        /* ensemble size M (0 or 1 = one network; at most
-                                 NNP_MAX_MEMBERS; FP32 or BF16 only): E_i is the
-                                 mean of M networks of the same shape over the
+                                 NNP_MAX_MEMBERS; any precision, FP8 with its own
+                                 activation and weight scales per member): E_i is
+                                 the mean of M networks of the same shape over the
                                  shared descriptor, as in the ANI-2x model, and
                                  the forces are minus the gradient of that mean */
 } nnp_config;

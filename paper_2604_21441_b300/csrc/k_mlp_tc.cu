@@ -28,9 +28,9 @@
 //
 // FP8 form: the three forward GEMMs take E4M3 operands (kind::f8f6f4, twice
 // the BF16 rate) with static scales: activations x_q = x / s_x with one s_x
-// per layer and species from a calibration pass of the FP32 form over the
-// first input; weights W_q[., n] = W[., n] / s_W[n] with one scale per output
-// column, s_W[n] = max_k |W[k, n]| / 448.  The accumulator of column n is
+// per layer, species and ensemble member from a calibration pass of the FP32
+// form over the first input; weights W_q[., n] = W[., n] / s_W[n] with one
+// scale per output column and member, s_W[n] = max_k |W[k, n]| / 448.  The accumulator of column n is
 // rescaled by s_x s_W[n] in the epilogue, before the bias.  The backward
 // GEMMs stay BF16; CELU' comes from the FP8 forward's z.
 //
@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(const EvalIO* __restri
     // FP8: z_l[n] = acc_l[n] * s_x s_W[n] + b_l[n]; q_l = 1 / s_{h_l} quantises h_l
     float q1 = 1.f, q2 = 1.f;
     if (F8) {
-      const int* qs = ws.q8 + 8 * sp;
+      const int* qs = ws.q8 + 8 * ((size_t)(m0 + wi % nm) * kMaxS + sp);  // this member's ranges
       const float sx0 = fp8_step(qs[0]), sx1 = fp8_step(qs[1]), sx2 = fp8_step(qs[2]);
       q1 = 1.f / sx1;
       q2 = 1.f / sx2;
@@ -1095,7 +1095,7 @@ void launch_wait_selftest(cudaStream_t st, int* flags, unsigned long long limit_
 // the FP32 descriptor and raises the species' |max| of G, h1 and h2 (float
 // bits, non-negative, so integer atomicMax orders them).  Rows are species
 // sorted, so a warp flushes its running maxima only when the species changes.
-__global__ void __launch_bounds__(256) k_fp8_calib(DescParams P, Workspace ws, MlpF32Weights Wf) {
+__global__ void __launch_bounds__(256) k_fp8_calib(DescParams P, Workspace ws, MlpF32Weights Wf, int member) {
   __shared__ float xs[8][kH1], ys[8][kH1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int D = P.D, rows = ws.seg[P.S];
@@ -1109,7 +1109,7 @@ __global__ void __launch_bounds__(256) k_fp8_calib(DescParams P, Workspace ws, M
     for (int l = 0; l < 3; ++l) {
       float v = m[l];
       for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-      if (lane == 0 && cur >= 0) atomicMax(&ws.q8[8 * cur + l], __float_as_int(v));
+      if (lane == 0 && cur >= 0) atomicMax(&ws.q8[8 * ((size_t)member * kMaxS + cur) + l], __float_as_int(v));
       m[l] = 0.f;
     }
   };
@@ -1250,12 +1250,14 @@ int mlp_tc_init(nnp_ctx* ctx) {
     for (int s = 0; s < ctx->P.S; ++s)
       for (int i = 0; i < 6; ++i) st->wm[(size_t)m].m[s][i] = st->blob + o * ((size_t)m * ctx->P.S + s) + st->off[i];
   if (f8) {
-    e = cudaMalloc(&st->wsc, sizeof(float) * (kH1 + kH2 + kH3) * ctx->P.S);
+    e = cudaMalloc(&st->wsc, sizeof(float) * (kH1 + kH2 + kH3) * ctx->P.S * sets);
     if (e != cudaSuccess) {
       st->wsc = nullptr;
       return ctx->cuda_fail(e, "cudaMalloc FP8 weight scales");
     }
-    for (int s = 0; s < ctx->P.S; ++s) st->wm[0].wsc[s] = st->wsc + (size_t)(kH1 + kH2 + kH3) * s;
+    for (int m = 0; m < sets; ++m)
+      for (int s = 0; s < ctx->P.S; ++s)
+        st->wm[(size_t)m].wsc[s] = st->wsc + (size_t)(kH1 + kH2 + kH3) * ((size_t)m * ctx->P.S + s);
   }
   e = cudaMalloc(&st->d_wm, sizeof(MlpTcWeights) * sets);
   if (e == cudaSuccess) e = cudaMemcpy(st->d_wm, st->wm.data(), sizeof(MlpTcWeights) * sets, cudaMemcpyHostToDevice);
@@ -1263,12 +1265,12 @@ int mlp_tc_init(nnp_ctx* ctx) {
   if (e == cudaSuccess)
     e = cudaMemcpy(st->d_wf, ctx->wf32m.data(), sizeof(MlpF32Weights) * sets, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return ctx->cuda_fail(e, "weight tables");
-  e = cudaMalloc(&ctx->b_q8, sizeof(int) * 8 * kMaxS);
+  e = cudaMalloc(&ctx->b_q8, sizeof(int) * 8 * kMaxS * sets);
   if (e != cudaSuccess) {
     ctx->b_q8 = nullptr;
     return ctx->cuda_fail(e, "cudaMalloc FP8 scales");
   }
-  cudaMemset(ctx->b_q8, 0, sizeof(int) * 8 * kMaxS);
+  cudaMemset(ctx->b_q8, 0, sizeof(int) * 8 * kMaxS * sets);
   const size_t sm = smem_bytes(D);
   if (f8) e = set_smem<128, true>(sm);
   else if (D == 128) e = set_smem<128, false>(sm);
@@ -1313,8 +1315,9 @@ int mlp_tc_set_weights(nnp_ctx* ctx, int member, int s, const float* hb) {
                    cudaMemcpyHostToDevice);
   if (e == cudaSuccess && st->f8) {
     // new weights: the weight scales of species s, and every activation range is re-calibrated
-    e = cudaMemcpy(st->wsc + sw.size() * s, sw.data(), sizeof(float) * sw.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(ctx->b_q8, 0, sizeof(int) * 8 * kMaxS);
+    e = cudaMemcpy(st->wsc + sw.size() * ((size_t)member * ctx->P.S + s), sw.data(), sizeof(float) * sw.size(),
+                   cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(ctx->b_q8, 0, sizeof(int) * 8 * kMaxS * ctx->n_members);
     ctx->fp8_calibrated = false;
     for (int t = 0; t < kMaxS; ++t) ctx->fp8_seen[t] = false;
   }
@@ -1365,7 +1368,8 @@ int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t stream, long long rows, int m0, int
 int launch_fp8_calib(nnp_ctx* ctx, cudaStream_t stream, long long rows) {
   if (ctx->P.D > kH1) return ctx->fail(NNP_ERR_UNSUPPORTED, "FP8 calibration needs D <= %d", kH1);
   const int grid = (int)std::max<long long>(1, std::min<long long>((rows + 7) / 8, 8ll * ctx->num_sms));
-  k_fp8_calib<<<grid, 256, 0, stream>>>(ctx->P, ctx->workspace(), ctx->wf32);
+  for (int m = 0; m < ctx->n_members; ++m)  // every member's activation ranges
+    k_fp8_calib<<<grid, 256, 0, stream>>>(ctx->P, ctx->workspace(), ctx->wf32m[(size_t)m], m);
   return NNP_OK;
 }
 

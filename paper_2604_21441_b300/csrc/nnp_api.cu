@@ -612,8 +612,6 @@ int nnp_create(const nnp_config* cfg, nnp_ctx** out) {
   if (cfg->n_members < 0) return bad(NNP_ERR_INVALID_ARG, "negative ensemble size");
   const int members = cfg->n_members > 0 ? cfg->n_members : 1;
   if (members > NNP_MAX_MEMBERS) return bad(NNP_ERR_INVALID_ARG, "at most NNP_MAX_MEMBERS ensemble members");
-  if (members > 1 && cfg->precision == NNP_FP8)
-    return bad(NNP_ERR_UNSUPPORTED, "the FP8 form takes one network per species");
   if ((cfg->flags & NNP_FLAG_CHARGES) && cfg->precision == NNP_FP8)
     return bad(NNP_ERR_UNSUPPORTED, "the FP8 form has no charge network");
 

@@ -8,9 +8,11 @@ ANI-2x model of the performance-scaling study in the Results).
 * M copies of one network give that network's result (the output layer is
   stored divided by M, which rounds, so 1e-6 relative and 1e-5 eV/A);
 * M = 8 on the 12,288-atom box against the oracle on sampled atoms;
-* a missing member, FP8 with M > 1, M above the maximum and a force-matching
-  call without v or reference forces are refused, and the context keeps
-  working (ensemble force matching itself: tests/test_gpu_force_match.py).
+* M = 3, FP8 (per-member activation and weight scales): within the FP8
+  form's bounds against the oracle's ensemble mean;
+* a missing member, M above the maximum and a force-matching call without v
+  or reference forces are refused, and the context keeps working (ensemble
+  force matching itself: tests/test_gpu_force_match.py).
 """
 import numpy as np
 import pytest
@@ -160,8 +162,34 @@ def test_ensemble_refusals(P):
         pot.force_match_grad()
     assert e.value.code == 1
     with pytest.raises(P.NNPError) as e:
-        P.NNP(atomic_numbers=(1, 8), precision="fp8", n_members=2)
-    assert e.value.code == 3
-    with pytest.raises(P.NNPError) as e:
         P.NNP(atomic_numbers=(1, 8), n_members=17)
     assert e.value.code == 1
+
+
+def test_ensemble_fp8_vs_oracle(P, oracle_mod):
+    """Three FP8 networks (E4M3 forward GEMMs, each member with its own
+    calibrated activation scales and per-column weight scales): the
+    ensemble's error against the FP64 oracle stays within the FP8 form's
+    single-network bounds (relative energy 3e-2, max |dF| 0.3, RMS 0.05
+    eV/A)."""
+    s = synth.water_box(64, 591)
+    mem = _members(3, 592)
+    pot = P.NNP(atomic_numbers=(1, 8), precision="fp8", n_members=3)
+    for m, w in enumerate(mem):
+        pot.set_all_weights(_f32(w), member=m)
+    E, F = pot.eval(s.pos, s.Z, box9(s.box))
+    assert pot.query("fp8_calibrated") == 1
+    p = oracle_mod.Params()
+    Er, Eir, Fr = oracle_mod.ensemble_energy_forces([oracle_mod.Model(p, w) for w in mem], s.pos,
+                                                    p.species_of(s.Z), s.box)
+    dF = F - Fr
+    ee = energy_error(E, Er, Eir)
+    print(f"ensemble-3 fp8 water-64: rel E err {ee:.2e}, max|dF| {np.abs(dF).max():.3e}, "
+          f"rms dF {np.sqrt((dF ** 2).mean()):.3e}")
+    assert ee <= 3e-2 and np.abs(dF).max() <= 0.3 and np.sqrt((dF ** 2).mean()) <= 0.05
+    # each member is quantised with its own scales: the ensemble differs from
+    # member 0 alone by more than the FP8 rounding
+    solo = P.NNP(atomic_numbers=(1, 8), precision="fp8")
+    solo.set_all_weights(_f32(mem[0]))
+    E0, _ = solo.eval(s.pos, s.Z, box9(s.box))
+    assert abs(E0 - E) > 1e-3 * np.abs(Eir).sum()
