@@ -820,6 +820,8 @@ def main():
                          "e.g. under a profiler")
     ap.add_argument("--out", default=None, help="also write the JSON line and the auxiliary "
                                                 "measurements to this file")
+    ap.add_argument("--cpu-baseline", type=int, default=1,
+                    help="0: leave out the timed CPU baseline (e.g. under a profiler)")
     args = ap.parse_args()
     args.compare = args.compare.split(",")
     args.warmup = max(args.warmup, 3)
@@ -873,7 +875,7 @@ def main():
                 "work_instruction_count": f"{fl_instr:.4g} FLOP (per pair/triplet counts)",
                 "peak_source": peak_src, "stage_ms": {k: r4(v) for k, v in st.items()}}
     # the CPU baseline is timed at N = 1 only (rank 0 of a multi-GPU run skips it)
-    cpu = cpu_baseline(r["wl"], r["w"]) if world == 1 else None
+    cpu = cpu_baseline(r["wl"], r["w"]) if world == 1 and args.cpu_baseline else None
     ms_mean = float(np.mean(r["ms"]))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

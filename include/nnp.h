@@ -370,7 +370,7 @@ typedef enum {
     NNP_Q_TUNE_DESCRIPTOR_TILE = 11, /* row pairs per work item of the descriptor kernel
                                         (> 0: from the work queue; < 0: static order) */
     NNP_Q_TUNE_BACKWARD_TILE = 12,   /* rows per work item of the descriptor-backward kernel
-                                        (sign as above) */
+                                        (-1: one row, static order) */
     NNP_Q_TUNE_NEIGHBOURS_QUEUE = 13 /* 1: the neighbour kernel draws its cells from the work
                                         queue; 0: static order */
 } nnp_query_key;

@@ -477,7 +477,7 @@ __host__ __device__ inline size_t bwd_warp_f4(int cap_a, int cap_r, int S) {
 template <int S, int ZSQ>
 __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ io,
                                                     const SysDesc* __restrict__ sys, DescParams P,
-                                                    Workspace ws, int tile_rows, int dyn) {
+                                                    Workspace ws) {
   constexpr int D = kNRad * S + kNAng * S * (S + 1) / 2;
   constexpr int NB = S * (S + 1) / 2;
   constexpr unsigned FM = 0xffffffffu;
@@ -510,6 +510,8 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
   const f2 half2 = f2_make(0.5f, 0.5f);
   const float dcs = 1.9f * zeta;
   const int rows = ws.seg[S];
+  const int wpb = blockDim.x >> 5;
+  const int rstride = gridDim.x * wpb;
   int cached_sys = -1;
   // the next row's metadata, counts and first 64 list entries are loaded one
   // row ahead, so their latency hides behind the current row's arithmetic
@@ -528,22 +530,13 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
     p_e0 = lane < cr ? l[lane] : 0;
     p_e1 = lane + 32 < cr ? l[lane + 32] : 0;
   };
-  // tiles of tile_rows consecutive rows from the work queue, so that a
-  // warp's rows are neighbours in space and share their gathers
-  WorkQueue wq(ws.queue + kQBwd, dyn != 0);
-  int row = wq.first() * tile_rows, tile_end = row + tile_rows, nrow = row;
-  prefetch(row);
-  for (; row < rows; row = nrow) {
+  prefetch(blockIdx.x * wpb + wib);
+  for (int row = blockIdx.x * wpb + wib; row < rows; row += rstride) {
     const bool live_row = p_atom >= 0;
     const float4 pi = p_pos;
     const int sid = p_info;
     const int cnt_l = p_cnt, cna_l = p_cna, e0 = p_e0, e1 = p_e1;
-    nrow = row + 1;
-    if (nrow >= tile_end) {  // warp-uniform
-      nrow = wq.next(lane) * tile_rows;
-      tile_end = nrow + tile_rows;
-    }
-    prefetch(nrow);
+    prefetch(row + rstride);
     if (!live_row) continue;  // padding row (warp-uniform)
     __syncwarp();  // the previous row's shared data has been read
     if (sid != cached_sys) {
@@ -809,7 +802,6 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
     }
     if (lane < 3) atomicAdd(Fout + 3 * (size_t)pos4_orig(pi) + lane, (double)(lane == 0 ? fix : (lane == 1 ? fiy : fiz)));
   }
-  queue_warp_done(wq, lane);
 }
 
 // FP32 accumulators -> the caller's FP64 forces (input order).
@@ -1042,13 +1034,13 @@ static void fwd_t(long long rows, int nsm, cudaStream_t st, const SysDesc* sys, 
   k_aev_fwd<S, ZSQ><<<queue_grid(items, 8, nsm, per_sm), 256, aev_fwd_smem(ws.cap_a, ws.cap_r), st>>>(
       sys, P, ws, mode, t, tile > 0 ? 1 : 0);
 }
+// The descriptor backward keeps static order, one row per warp and step (a
+// queue measured no faster for it, and its extra code cost 3%).
 template <int S, int ZSQ>
 static void bwd_t(long long rows, int nsm, cudaStream_t st, const EvalIO* io, const SysDesc* sys,
-                  const DescParams& P, const Workspace& ws, int per_sm, int tile) {
-  const int t = tile < 0 ? -tile : tile;
-  const long long items = (rows + t - 1) / t;
-  k_aev_bwd<S, ZSQ><<<queue_grid(items, kBwdWarps, nsm, per_sm), 32 * kBwdWarps,
-                      aev_bwd_smem(ws.cap_a, ws.cap_r, S), st>>>(io, sys, P, ws, t, tile > 0 ? 1 : 0);
+                  const DescParams& P, const Workspace& ws, int per_sm, int /*tile*/) {
+  k_aev_bwd<S, ZSQ><<<queue_grid(rows, kBwdWarps, nsm, per_sm), 32 * kBwdWarps,
+                      aev_bwd_smem(ws.cap_a, ws.cap_r, S), st>>>(io, sys, P, ws);
 }
 
 void launch_aev_fwd(long long rows, int nsm, cudaStream_t st, const SysDesc* sys, const DescParams& P,

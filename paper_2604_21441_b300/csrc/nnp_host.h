@@ -189,9 +189,10 @@ struct nnp_ctx {
 
   // launch shapes, chosen by the autotuner (NNP_FLAG_AUTOTUNE): blocks-per-SM
   // caps of the persistent neighbour, descriptor and descriptor-backward
-  // grids; the row tiles of the two descriptor kernels (row pairs for the
-  // descriptor, rows for its backward), > 0 drawn from the work queue, < 0 in
-  // static order; nbr_dyn: the neighbour kernel draws its cells from the queue
+  // grids; the descriptor's tiles of row pairs, > 0 drawn from the work
+  // queue, < 0 in static order (bwd_tile stays -1: the backward takes one row
+  // at a time in static order); nbr_dyn: the neighbour kernel draws its cells
+  // from the queue
   struct Tune { int nbr = 16, fwd = 8, bwd = 16, fwd_tile = -1, bwd_tile = -1, nbr_dyn = 0; } tune;
   long long tuned_key = -1;
   int autotune(long long n, int B, long long bins, long long rows);

@@ -1,9 +1,9 @@
 // nnp_tune.cu -- launch-shape autotuner (NNP_FLAG_AUTOTUNE).
 //
 // The neighbour, descriptor and descriptor-backward kernels are persistent:
-// a grid capped at (blocks per SM) x SMs whose warps draw work items from a
-// queue -- cells for the neighbour kernel, tiles of consecutive rows (row
-// pairs for the descriptor) for the other two.  The best cap and tile depend
+// a grid capped at (blocks per SM) x SMs.  The warps of the first two take
+// their work items -- cells, tiles of consecutive row pairs -- in static
+// order or from a queue; the backward's warps take rows in static order.  The best cap and tile depend
 // on the row count and on how many systems share the launch (a batch of many
 // small boxes has other tails and another locality than one large box).  On
 // the first synchronous evaluation of a (species, precision, row-count
@@ -81,7 +81,7 @@ int nnp_ctx::autotune(long long n, int B, long long bins, long long rows) {
   constexpr int kC = 8;
   const int cand_nbr[kC][2] = {{4, 0}, {8, 0}, {16, 0}, {32, 0}, {4, 1}, {8, 1}, {16, 1}, {32, 1}};
   const int cand_fwd[kC][2] = {{2, -1}, {4, -1}, {8, -1}, {16, -1}, {8, 1}, {8, 2}, {8, 4}, {16, 2}};
-  const int cand_bwd[kC][2] = {{4, -1}, {8, -1}, {16, -1}, {32, -1}, {16, 2}, {16, 4}, {32, 4}, {8, 8}};
+  const int cand_bwd[kC][2] = {{4, -1}, {8, -1}, {16, -1}, {32, -1}, {64, -1}, {12, -1}, {24, -1}, {48, -1}};
   const bool own_events = stage_ev[0] == nullptr;
   if (own_events)
     for (auto& ev : stage_ev) CK(cudaEventCreate(&ev));

@@ -39,8 +39,7 @@ def test_batch_256(oracle_mod):
     assert tuned["neighbours"] in (4, 8, 16, 32) and tuned["neighbours_queue"] in (0, 1)
     assert (tuned["descriptor"], tuned["descriptor_tile"]) in {
         (2, -1), (4, -1), (8, -1), (16, -1), (8, 1), (8, 2), (8, 4), (16, 2)}
-    assert (tuned["backward"], tuned["backward_tile"]) in {
-        (4, -1), (8, -1), (16, -1), (32, -1), (16, 2), (16, 4), (32, 4), (8, 8)}
+    assert tuned["backward"] in (4, 8, 12, 16, 24, 32, 48, 64) and tuned["backward_tile"] == -1
     # every system against its own single-system evaluation: the same kernels
     # on the same neighbour lists; only the order of the sums differs (energy
     # partial sums per warp start at other row offsets; the FP64 force
