@@ -736,9 +736,10 @@ def force_match_rate(steps=20):
     independently seeded network of the same architecture (the teacher),
     evaluated by the library.  Each call recomputes the forces of the last
     evaluation, the tangent descriptors, the networks' tangent and adjoint
-    passes and the weight-gradient reductions, and returns the gradient to
-    the host: synchronous calls timed by wall clock, stage durations by CUDA
-    events.  Work per stage (FP32, FMA = 2; the roofline is the FP32 ALU
+    passes and the weight-gradient reductions, and leaves the gradient in a
+    device buffer (as an optimiser on the GPU would use it): synchronous
+    calls timed by wall clock, stage durations by CUDA events (separate
+    calls).  Work per stage (FP32, FMA = 2; the roofline is the FP32 ALU
     peak): the descriptor kernels' per-pair/per-triplet counts; the networks'
     primal and tangent forward, 2 x 2 (D*160 + 160*128 + 128*96) per atom, and
     the two adjoints, 2 x 2 (96*128 + 128*160); the weight gradients,
@@ -761,15 +762,18 @@ def force_match_rate(steps=20):
     pot = P.NNP(atomic_numbers=Zs, precision="fp32", max_atoms=s.n, flags=P.FLAG_STAGE_EVENTS)
     pot.set_all_weights(f32(synth.xavier_weights(S, D, wl["weight_seed"])))
     pot.eval(pos, Z, box)
+    grad = torch.zeros(pot.param_count(), dtype=torch.float64, device="cuda")  # stays on the device
     for _ in range(3):
-        pot.force_match_grad(Fref=Fref)
+        pot.force_match_grad(Fref=Fref, out=grad)
     torch.cuda.synchronize()
-    stages = []
     t0 = time.perf_counter()
     for _ in range(steps):
-        L, _ = pot.force_match_grad(Fref=Fref, want_loss=True)
-        stages.append(pot.profile_force_match())
+        L, _ = pot.force_match_grad(Fref=Fref, want_loss=True, out=grad)
     ms = (time.perf_counter() - t0) * 1e3 / steps
+    stages = []
+    for _ in range(5):
+        pot.force_match_grad(Fref=Fref, out=grad)
+        stages.append(pot.profile_force_match())
     pot.close()
     st = np.mean(np.array(stages), axis=0)
     names = ("forces", "tangent_descriptors", "networks", "weight_gradients")

@@ -440,16 +440,28 @@ class NNP:
                        ctypes.c_void_p(bx.ctypes.data), ctypes.c_void_p(E_out.data_ptr()),
                        ctypes.c_void_p(F_out.data_ptr())))
 
-    def force_match_grad(self, v=None, Fref=None, want_loss: bool = False):
-        """dL/dtheta (packed, nnp_param_count doubles) for the last eval."""
-        g = np.zeros(self.param_count())
+    def force_match_grad(self, v=None, Fref=None, want_loss: bool = False, out=None):
+        """dL/dtheta (packed, nnp_param_count doubles) for the last eval.
+        out: optional contiguous float64 buffer of that size (NumPy array or
+        torch tensor, host or device) to write into; by default a new NumPy
+        array."""
+        npar = self.param_count()
+        if out is None:
+            out = np.zeros(npar)
+        if _is_torch(out):
+            if str(out.dtype) != "torch.float64" or not out.is_contiguous() or out.numel() != npar:
+                raise ValueError("out must be a contiguous float64 tensor of param_count() entries")
+            pg = ctypes.c_void_p(out.data_ptr())
+        else:
+            if out.dtype != np.float64 or not out.flags["C_CONTIGUOUS"] or out.size != npar:
+                raise ValueError("out must be a contiguous float64 array of param_count() entries")
+            pg = ctypes.c_void_p(out.ctypes.data)
         pv, kv = _ptr(v, np.float64)
         pr, kr = _ptr(Fref, np.float64)
         loss = np.zeros(1)
         self._check(self._L.nnp_force_match_grad(
-            self._h, pv, pr, ctypes.c_void_p(loss.ctypes.data) if want_loss else None,
-            ctypes.c_void_p(g.ctypes.data)))
-        return (float(loss[0]), g) if want_loss else g
+            self._h, pv, pr, ctypes.c_void_p(loss.ctypes.data) if want_loss else None, pg))
+        return (float(loss[0]), out) if want_loss else out
 
     def atom_energies(self, n: int) -> np.ndarray:
         """Per-atom energies of the last evaluation (input order)."""

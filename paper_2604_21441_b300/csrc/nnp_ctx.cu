@@ -230,7 +230,11 @@ int nnp_ctx::force_match_grad(const double* v, const double* Fref, double* loss,
   const bool prof = stage_ev[0] != nullptr;
   if (prof && !fm_ev[0])
     for (auto& ev : fm_ev) CK(cudaEventCreate(&ev));
-  CK(cudaStreamSynchronize(stream));
+  CK(cudaStreamSynchronize(stream));  // the staging slot below is rewritten
+  // species segments of the last evaluation (rows per species), for the
+  // weight-gradient jobs; the stream is idle, so this copy waits for nothing
+  int seg[kMaxS + 2];
+  CK(cudaMemcpy(seg, b_seg, sizeof(seg), cudaMemcpyDeviceToHost));
   CK(grow_buf(fm_z, fm_cap, (size_t)rows * 384));
   CK(grow_buf(fm_dz, fm_cap2, (size_t)rows * 384));
   CK(grow_buf(fm_t, fm_cap3, (size_t)rows * 384));
@@ -273,14 +277,14 @@ int nnp_ctx::force_match_grad(const double* v, const double* Fref, double* loss,
   launch_aev_jvp(rows, num_sms, stream, b_sys, P, w, fm_v, b_dEdG);
   if (prof) CK(cudaEventRecord(fm_ev[2], stream));
   // weight-gradient jobs per member, species, layer, 32 x 32 tile and
-  // 2,048-row segment (the segment bounds are the last evaluation's)
-  int seg[kMaxS + 2];
-  CK(cudaMemcpyAsync(seg, b_seg, sizeof(seg), cudaMemcpyDeviceToHost, stream));
-  CK(cudaStreamSynchronize(stream));
-  std::vector<FmJob> jobs;
+  // 2,048-row segment (the segment bounds are the last evaluation's); the
+  // device list is kept while the segments stay the same
+  std::vector<FmJob>& jobs = fm_job_list;
   const int fin[4] = {D, kH1, kH2, kH3}, fout[4] = {kH1, kH2, kH3, 1};
   const size_t per = per_member / P.S;
-  for (int m = 0; m < n_members; ++m)
+  const bool same_jobs = !jobs.empty() && std::equal(seg, seg + P.S + 1, fm_job_seg);
+  if (!same_jobs) jobs.clear();
+  for (int m = 0; m < n_members && !same_jobs; ++m)
     for (int sp = 0; sp < P.S; ++sp) {
       size_t off = per_member * m + per * sp;
       size_t woff[4], boff[4];
@@ -299,8 +303,11 @@ int nnp_ctx::force_match_grad(const double* v, const double* Fref, double* loss,
                                    (long long)woff[l], (long long)boff[l]});
       }
     }
-  CK(grow_buf(fm_jobs, fm_jcap, jobs.size() + 1));
-  CK(cudaMemcpyAsync(fm_jobs, jobs.data(), sizeof(FmJob) * jobs.size(), cudaMemcpyHostToDevice, stream));
+  if (!same_jobs) {
+    CK(grow_buf(fm_jobs, fm_jcap, jobs.size() + 1));
+    CK(cudaMemcpyAsync(fm_jobs, jobs.data(), sizeof(FmJob) * jobs.size(), cudaMemcpyHostToDevice, stream));
+    std::copy(seg, seg + P.S + 1, fm_job_seg);
+  }
   const int jobs_per_member = (int)jobs.size() / n_members;
   for (int m = 0; m < n_members; ++m) {
     // 4. member m's network: primal + tangent forward, reverse adjoints
@@ -317,13 +324,10 @@ int nnp_ctx::force_match_grad(const double* v, const double* Fref, double* loss,
   // 6. results
   CK(cudaMemcpyAsync(grad, fm_grad, sizeof(double) * npar,
                      is_device(grad) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream));
-  if (loss) {
-    double lh = 0.0;
-    CK(cudaMemcpyAsync(&lh, lossd, sizeof(double), cudaMemcpyDeviceToHost, stream));
-    CK(cudaStreamSynchronize(stream));
-    *loss = Fref ? lh : 0.0;
-  }
+  double lh = 0.0;
+  if (loss) CK(cudaMemcpyAsync(&lh, lossd, sizeof(double), cudaMemcpyDeviceToHost, stream));
   CK(cudaStreamSynchronize(stream));
+  if (loss) *loss = Fref ? lh : 0.0;
   return NNP_OK;
 }
 

@@ -140,6 +140,8 @@ struct nnp_ctx {
   float *fm_z = nullptr, *fm_dz = nullptr, *fm_t = nullptr, *fm_p = nullptr;
   double *fm_v = nullptr, *fm_ref = nullptr, *fm_grad = nullptr;
   nnp::FmJob* fm_jobs = nullptr;
+  std::vector<nnp::FmJob> fm_job_list;  // host copy of fm_jobs, built for the segments fm_job_seg
+  int fm_job_seg[nnp::kMaxS + 2] = {};
   size_t fm_cap = 0, fm_cap2 = 0, fm_cap3 = 0, fm_cap4 = 0, fm_vcap = 0, fm_refcap = 0, fm_gcap = 0, fm_jcap = 0;
   static bool is_device(const void* p);
 

@@ -174,7 +174,8 @@ def test_force_match_seven_species(P, oracle_mod):
 
 
 def test_force_match_stage_profile(P):
-    """nnp_profile_force_match reports four positive stage durations."""
+    """nnp_profile_force_match reports four positive stage durations; the
+    gradient written into a caller's device buffer equals the host one."""
     s = synth.water_box(64, 1001)
     w = weights32(2, 128, 81, 82)
     pot = P.NNP(atomic_numbers=(1, 8), flags=P.FLAG_STAGE_EVENTS)
@@ -182,6 +183,13 @@ def test_force_match_stage_profile(P):
     pot.eval(s.pos, s.Z, box9(s.box))
     with pytest.raises(P.NNPError):
         pot.profile_force_match()
-    pot.force_match_grad(Fref=np.zeros((s.n, 3)))
+    g_host = pot.force_match_grad(Fref=np.zeros((s.n, 3)))
     t = pot.profile_force_match()
     assert len(t) == 4 and all(x > 0 for x in t), t
+    # into a caller's device buffer, twice (the job list is reused): the same gradient
+    import torch
+    out = torch.zeros(pot.param_count(), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        g_dev = pot.force_match_grad(Fref=np.zeros((s.n, 3)), out=out)
+        assert g_dev is out
+        assert np.abs(out.cpu().numpy() - g_host).max() <= 1e-12 * np.abs(g_host).max()
