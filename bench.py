@@ -288,7 +288,7 @@ def run_ours(args, rank, world, local_rank):
     t_e2e = time.perf_counter() - t0
     launches = pot.query("launches_per_eval")
     tuned = {k: pot.query("tune_" + k) for k in ("neighbours", "descriptor", "backward",
-                                                  "descriptor_tile", "backward_tile", "neighbours_queue")}
+                                                  "descriptor_tile", "backward_tile", "neighbours_form")}
     per_system = None
     if B > 1:  # the same batch as one graph launch per system (one context each)
         pots = [P.NNP(atomic_numbers=wl["atomic_numbers"], precision=args.precision,

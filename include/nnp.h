@@ -371,8 +371,9 @@ typedef enum {
                                         (> 0: from the work queue; < 0: static order) */
     NNP_Q_TUNE_BACKWARD_TILE = 12,   /* rows per work item of the descriptor-backward kernel
                                         (-1: one row, static order) */
-    NNP_Q_TUNE_NEIGHBOURS_QUEUE = 13 /* 1: the neighbour kernel draws its cells from the work
-                                        queue; 0: static order */
+    NNP_Q_TUNE_NEIGHBOURS_QUEUE = 13 /* the neighbour kernel's form: bit 0 cells from the work
+                                        queue (else static order), bit 1 each cell's groups of
+                                        16 rows alternate between two warps */
 } nnp_query_key;
 
 int nnp_query(nnp_ctx *ctx, int32_t key, int64_t *value);

@@ -515,6 +515,7 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
       // lanes of the row, so every entry goes straight to its final place
       // (angular ones first, both kinds in window order).  When the windows
       // of all species fit, they are staged once for all groups.
+      if (GR * part >= nrows) continue;  // split > 1: this part has no row group
       const bool all_fit = sum_tot <= WIN;
       if (all_fit) {
         int wb = 0;
@@ -762,12 +763,14 @@ cudaError_t neighbors_set_smem_limits() {
 }
 
 void launch_neighbors(int grid, cudaStream_t st, const EvalIO* io, const SysDesc* sys, const DescParams& P,
-                      const Workspace& ws, long long rows, long long cells, int nsm, int dyn) {
-  if (rows > kNbrRowsSmall) {  // warp per cell, 512-candidate windows
+                      const Workspace& ws, long long rows, long long cells, int nsm, int mode) {
+  const int dyn = mode & 1;
+  if (rows > kNbrRowsSmall) {  // warp per cell (mode & 2: per half cell), 512-candidate windows
     const size_t sm = neighbors_smem(kNbrWin);
-    if (P.S <= 2) k_neighbors<2, kNbrWin><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws, 1, dyn);
-    else if (P.S <= 4) k_neighbors<4, kNbrWin><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws, 1, dyn);
-    else k_neighbors<8, kNbrWin><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws, 1, dyn);
+    const int sp = (mode & 2) ? 2 : 1;
+    if (P.S <= 2) k_neighbors<2, kNbrWin><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws, sp, dyn);
+    else if (P.S <= 4) k_neighbors<4, kNbrWin><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws, sp, dyn);
+    else k_neighbors<8, kNbrWin><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws, sp, dyn);
     return;
   }
   // small systems: 1024-candidate windows, each cell's row groups over up to 8 warps

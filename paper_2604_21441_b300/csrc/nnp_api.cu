@@ -160,7 +160,7 @@ int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows,
   const Workspace w = workspace();
   const int nsm = num_sms;
   const int g_atoms = grid_for(n, 256, nsm * 8);
-  const int g_cells = grid_for(total_cells, kNbrThreads / 32, nsm * tune.nbr);
+  const int g_cells = grid_for(total_cells * ((tune.nbr_dyn & 2) ? 2 : 1), kNbrThreads / 32, nsm * tune.nbr);
   const int g_bins = grid_for(bins * 32, 256, nsm * 16);
   const EvalIO* io = d_io;
   const SysDesc* sys = b_sys;

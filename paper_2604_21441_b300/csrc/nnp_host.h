@@ -18,10 +18,13 @@ __global__ void k_binsort(const EvalIO* io, int S, int sort, Workspace ws);
 // dynamic shared memory sizeof(int) * kScanSmemBins
 __global__ void k_cells_small(const EvalIO* io, const SysDesc* sys, const signed char* zlut, int S, int sort,
                               Workspace ws);
-// grid: blocks for a warp per cell (systems above kNbrRowsSmall rows); rows and
-// cells (totals over systems) choose the small-system form and its split
+// grid: blocks for a warp per cell, or (mode & 2) per half cell, for systems
+// above kNbrRowsSmall rows; rows and cells (totals over systems) choose the
+// small-system form and its split.  mode bit 0: items from the work queue
+// instead of static order; bit 1: each cell's row groups of 16 alternate
+// between two warps (large systems only; cells of many rows)
 void launch_neighbors(int grid, cudaStream_t st, const EvalIO* io, const SysDesc* sys, const DescParams& P,
-                      const Workspace& ws, long long rows, long long cells, int nsm, int dyn = 0);
+                      const Workspace& ws, long long rows, long long cells, int nsm, int mode = 0);
 void set_cell_steps(SysDesc& sd);  // cell steps and their inverse from nc, ell or B
 void launch_wait_selftest(cudaStream_t st, int* flags, unsigned long long limit_ns);
 __global__ void k_pairs_prep(int S, Workspace ws);
@@ -193,8 +196,8 @@ struct nnp_ctx {
   // caps of the persistent neighbour, descriptor and descriptor-backward
   // grids; the descriptor's tiles of row pairs, > 0 drawn from the work
   // queue, < 0 in static order (bwd_tile stays -1: the backward takes one row
-  // at a time in static order); nbr_dyn: the neighbour kernel draws its cells
-  // from the queue
+  // at a time in static order); nbr_dyn: the neighbour kernel's form, bit 0
+  // items from the queue, bit 1 each cell's row groups over two warps
   struct Tune { int nbr = 16, fwd = 8, bwd = 16, fwd_tile = -1, bwd_tile = -1, nbr_dyn = 0; } tune;
   long long tuned_key = -1;
   int autotune(long long n, int B, long long bins, long long rows);

@@ -3,7 +3,8 @@
 // The neighbour, descriptor and descriptor-backward kernels are persistent:
 // a grid capped at (blocks per SM) x SMs.  The warps of the first two take
 // their work items -- cells, tiles of consecutive row pairs -- in static
-// order or from a queue; the backward's warps take rows in static order.  The best cap and tile depend
+// order or from a queue; the backward's warps take rows in static order.  The
+// neighbour kernel can also split each cell's row groups over two warps.  The best cap and tile depend
 // on the row count and on how many systems share the launch (a batch of many
 // small boxes has other tails and another locality than one large box).  On
 // the first synchronous evaluation of a (species, precision, row-count
@@ -76,10 +77,11 @@ int nnp_ctx::autotune(long long n, int B, long long bins, long long rows) {
     }
   }
   // candidates, column i of each list timed in the same pipeline run: the
-  // neighbour kernel's (blocks per SM, queue), the descriptor kernels' (blocks
-  // per SM, tile; tile < 0: static order).  Columns 0-3 are the static shapes.
+  // neighbour kernel's (blocks per SM, form: bit 0 items from the queue, bit
+  // 1 each cell's row groups over two warps), the descriptor kernels' (blocks
+  // per SM, tile; tile < 0: static order).
   constexpr int kC = 8;
-  const int cand_nbr[kC][2] = {{4, 0}, {8, 0}, {16, 0}, {32, 0}, {4, 1}, {8, 1}, {16, 1}, {32, 1}};
+  const int cand_nbr[kC][2] = {{4, 0}, {8, 0}, {16, 0}, {16, 2}, {8, 1}, {16, 1}, {32, 1}, {16, 3}};
   const int cand_fwd[kC][2] = {{2, -1}, {4, -1}, {8, -1}, {16, -1}, {8, 1}, {8, 2}, {8, 4}, {16, 2}};
   const int cand_bwd[kC][2] = {{4, -1}, {8, -1}, {16, -1}, {32, -1}, {64, -1}, {12, -1}, {24, -1}, {48, -1}};
   const bool own_events = stage_ev[0] == nullptr;
@@ -100,11 +102,11 @@ int nnp_ctx::autotune(long long n, int B, long long bins, long long rows) {
       CK(cudaEventElapsedTime(&t_nbr, stage_ev[1], stage_ev[2]));
       CK(cudaEventElapsedTime(&t_fwd, stage_ev[2], stage_ev[3]));
       CK(cudaEventElapsedTime(&t_bwd, stage_ev[4], stage_ev[5]));
-      const int qn = cand_nbr[i][1], qf = cand_fwd[i][1] > 0, qb = cand_bwd[i][1] > 0;
+      const int qn = cand_nbr[i][1] & 1, qf = cand_fwd[i][1] > 0, qb = cand_bwd[i][1] > 0;
       Tune& tn = qn ? dy_best : st_best;
       Tune& tf = qf ? dy_best : st_best;
       Tune& tb = qb ? dy_best : st_best;
-      if (t_nbr < best[qn][0]) { best[qn][0] = t_nbr; tn.nbr = cand_nbr[i][0]; tn.nbr_dyn = qn; }
+      if (t_nbr < best[qn][0]) { best[qn][0] = t_nbr; tn.nbr = cand_nbr[i][0]; tn.nbr_dyn = cand_nbr[i][1]; }
       if (t_fwd < best[qf][1]) { best[qf][1] = t_fwd; tf.fwd = cand_fwd[i][0]; tf.fwd_tile = cand_fwd[i][1]; }
       if (t_bwd < best[qb][2]) { best[qb][2] = t_bwd; tb.bwd = cand_bwd[i][0]; tb.bwd_tile = cand_bwd[i][1]; }
     }
@@ -113,7 +115,7 @@ int nnp_ctx::autotune(long long n, int B, long long bins, long long rows) {
   // replays, and their caches are warm)
   constexpr float kQueueGain = 0.97f;
   Tune chosen = st_best;
-  if (best[1][0] < kQueueGain * best[0][0]) { chosen.nbr = dy_best.nbr; chosen.nbr_dyn = 1; }
+  if (best[1][0] < kQueueGain * best[0][0]) { chosen.nbr = dy_best.nbr; chosen.nbr_dyn = dy_best.nbr_dyn; }
   if (best[1][1] < kQueueGain * best[0][1]) { chosen.fwd = dy_best.fwd; chosen.fwd_tile = dy_best.fwd_tile; }
   if (best[1][2] < kQueueGain * best[0][2]) { chosen.bwd = dy_best.bwd; chosen.bwd_tile = dy_best.bwd_tile; }
   if (own_events)

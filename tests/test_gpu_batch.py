@@ -33,10 +33,12 @@ def test_batch_256(oracle_mod):
     E, F = pot.eval_batch(off, pos, Z, boxes)
     E, F = E.cpu().numpy(), F.cpu().numpy()
     tuned = {k: pot.query("tune_" + k) for k in ("neighbours", "descriptor", "backward",
-                                                  "descriptor_tile", "backward_tile", "neighbours_queue")}
+                                                  "descriptor_tile", "backward_tile", "neighbours_form")}
     print("batch-256 tuned shapes:", tuned)
-    # one of the autotuner's candidates (tile < 0: static order, > 0: queue)
-    assert tuned["neighbours"] in (4, 8, 16, 32) and tuned["neighbours_queue"] in (0, 1)
+    # one of the autotuner's candidates (tile < 0: static order, > 0: queue;
+    # neighbour form: bit 0 queue, bit 1 row groups over two warps)
+    assert (tuned["neighbours"], tuned["neighbours_form"]) in {
+        (4, 0), (8, 0), (16, 0), (16, 2), (8, 1), (16, 1), (32, 1), (16, 3)}
     assert (tuned["descriptor"], tuned["descriptor_tile"]) in {
         (2, -1), (4, -1), (8, -1), (16, -1), (8, 1), (8, 2), (8, 4), (16, 2)}
     assert tuned["backward"] in (4, 8, 12, 16, 24, 32, 48, 64) and tuned["backward_tile"] == -1
