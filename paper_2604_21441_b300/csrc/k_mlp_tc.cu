@@ -731,11 +731,14 @@ constexpr int kWideKC = 2;    // slabs of G that bufA and bufC each hold
 constexpr int kWideNC = 128;  // dE/dG columns per block
 constexpr int kWideBars = 18; // mbarriers of k_mlp_tc_wide
 
+// g1out (ensembles): instead of the dE/dG blocks, each work item writes its
+// g1 tile (the three swizzled slabs, as the MMA reads them) to slot
+// tile * nm + member of g1out, and k_dedg_ens forms dE/dG from all members.
 template <int D>
 __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __restrict__ io, DescParams P,
                                                        Workspace ws, const MlpTcWeights* __restrict__ Wts,
                                                        const MlpF32Weights* __restrict__ Wfs, int m0, int nm,
-                                                       int accm) {
+                                                       int accm, uint8_t* __restrict__ g1out) {
   constexpr int kBufA = kWideKC * kSlab;        // G chunk (stage 0), later g2
   constexpr int kBufB = slabs_of(kH1) * kSlab;  // h1, later g1
   constexpr int kBufC = slabs_of(kH2) * kSlab;  // G chunk (stage 1), h2, later g3
@@ -794,6 +797,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
   auto dg_bar = [](int cb) -> int { return (cb & 1) ? 0 : 1; };
   auto dg_slab = [&](int cb, int k) -> uint8_t* { return wbuf[dg_bar(cb)] + (size_t)k * kWideNC * 128; };
   static_assert(8 * 4096 <= kBufA && 8 * 4096 <= kBufC, "dE/dG staging");
+  static_assert((size_t)kBufB == kG1TileBytes, "g1 tile");
 
   uint32_t ph[4] = {0, 0, 0, 0};
   bool pend[4] = {false, false, false, false};
@@ -1013,13 +1017,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
     // ---------------- backward 2: g1' = g2 W2^T
     if (!phase(0, -1)) break;
     if (tid == 0) {
-      load_block(sp, 0);  // dE/dG block 0 -> wbuf[1] (free since backward 3)
+      if (!g1out) load_block(sp, 0);  // dE/dG block 0 -> wbuf[1] (free since backward 3)
       tc_fence_after();
       issue_gemm<false>(mg1, bufA, wbuf[0], kH1, kH2);
       commit();
     }
     wait_mma();
-    if (tid == 0 && kNCB > 1) load_block(sp, 1);  // wbuf[0] is free: block 1
+    if (tid == 0 && kNCB > 1 && !g1out) load_block(sp, 1);  // wbuf[0] is free: block 1
     for_chunks2<kH1>(tg1, tz1, h, [&](int c0, float (&g)[16], float (&d)[16]) {
 #pragma unroll
       for (int j = 0; j < 16; ++j) g[j] *= d[j];
@@ -1027,6 +1031,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
     });
     // ---------------- backward 1: dE/dG = g1 W1^T in column blocks
     if (!phase(1, -1)) break;  // g1 written; block 0's weights have landed
+    if (g1out) {  // ensemble: the g1 tile to its (tile, member) slot
+      const uint4* src = reinterpret_cast<const uint4*>(bufB);
+      uint4* dst = reinterpret_cast<uint4*>(g1out + ((size_t)tile * nm + wi % nm) * kG1TileBytes);
+      for (int i = tid; i < (int)(kG1TileBytes / 16); i += blockDim.x) dst[i] = src[i];
+      continue;  // the next item's first barrier comes before bufB is written again
+    }
     if (tid == 0) {
       tc_fence_after();
       issue_block(0);
@@ -1070,6 +1080,128 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
   __syncthreads();
   tc_fence_after();
   if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// dE/dG of an ensemble of wide networks, as one product over the members:
+//   dE/dG[tile, block cb] = sum_m g1_m W1_m^T[:, block cb]  (K = 160 per member)
+// Work items are (tile, 128-column block).  Thread 0 streams each member's g1
+// tile (written by k_mlp_tc_wide) and W1 rows of the block through two 96 KB
+// stages of shared memory and issues the MMAs, which accumulate in one TMEM
+// block; the block is written once, as whole 128-byte lines
+// (store_block_staged), so the members' shares meet in tensor memory instead
+// of in L2 reductions, in a fixed order.  (Six 32 KB stages of single K slabs,
+// with or without a separate producer thread, measured slower: 1.2-1.9x.)
+constexpr int kEnsStage = 2 * (int)kG1TileBytes;  // one member's g1 tile and W1 block (48 KB each)
+constexpr int kEnsBars = 5;                       // [0,1] stage copies, [2,3] stage MMAs, [4] block done
+size_t smem_bytes_dedg() { return 1024 + 2 * (size_t)kEnsStage + kEnsBars * 8 + 16; }
+
+template <int D>
+__global__ void __launch_bounds__(kTcThreads, 1) k_dedg_ens(DescParams P, Workspace ws,
+                                                    const MlpTcWeights* __restrict__ Wts,
+                                                    const uint8_t* __restrict__ g1, int nm) {
+  constexpr int kNCB = (D + kWideNC - 1) / kWideNC;
+  constexpr uint32_t kCols = 128;
+  static_assert(kTcThreads / 32 * 4096 <= kEnsStage, "epilogue staging");
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  uint8_t* stg[2] = {sm, sm + kEnsStage};
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * kEnsStage);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kEnsBars);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quarter = warp & 3, h = warp >> 2;
+  const int ntiles = ws.seg[P.S] / kTM;
+  if (tid == 0) {
+    for (int i = 0; i < kEnsBars; ++i) mbar_init(&bars[i], 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, kCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t lb = (uint32_t)(quarter * 32) << 16;
+  uint32_t pc[2] = {0, 0}, pm[2] = {0, 0}, p4 = 0;
+  bool pendc[2] = {false, false}, pendm[2] = {false, false};
+  auto timeout = [&]() {
+    *abort_flag = 1;
+    atomicOr(&ws.flags[kFlagTimeout], 1);
+  };
+  for (int it = blockIdx.x; it < ntiles * kNCB; it += gridDim.x) {
+    const int tile = it / kNCB, cb = it - tile * kNCB;
+    const int row0 = tile * kTM, n0 = cb * kWideNC, nc = min(kWideNC, D - n0);
+    if (tid == 0) {
+      const int sp = pos4_species(ws.pos4[row0]);
+      const uint32_t wbytes = (uint32_t)(nc * 128);
+      auto load = [&](int m, int st) {  // member m's g1 tile and W1 rows [n0, n0 + nc) into stage st
+        mbar_expect_tx(&bars[st], (uint32_t)kG1TileBytes + (uint32_t)slabs_of(kH1) * wbytes);
+        bulk_g2s(stg[st], g1 + ((size_t)tile * nm + m) * kG1TileBytes, (uint32_t)kG1TileBytes, &bars[st]);
+        for (int k = 0; k < slabs_of(kH1); ++k)
+          bulk_g2s(stg[st] + kG1TileBytes + (size_t)k * kWideNC * 128,
+                   Wts[m].m[sp][5] + (size_t)k * D * 128 + (size_t)n0 * 128, wbytes, &bars[st]);
+        pendc[st] = true;
+      };
+      load(0, 0);
+      if (nm > 1) load(1, 1);
+      const uint32_t idesc = idesc_bf16(kTM, nc);
+      for (int m = 0; m < nm && *abort_flag == 0; ++m) {
+        const int st = m & 1;
+        if (mbar_wait(&bars[st], pc[st])) {
+          pc[st] ^= 1u;
+          pendc[st] = false;
+        } else {
+          timeout();
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(stg[st]), b0 = smem_u32(stg[st] + kG1TileBytes);
+        for (int k = 0; k < kH1 / 16; ++k) {
+          const uint32_t a = a0 + (uint32_t)(k >> 2) * kSlab + (uint32_t)(k & 3) * 32;
+          const uint32_t b = b0 + (uint32_t)(k >> 2) * (uint32_t)(kWideNC * 128) + (uint32_t)(k & 3) * 32;
+          mma_bf16(tmem, sw128_desc(a), sw128_desc(b), idesc, (m > 0 || k > 0) ? 1u : 0u);
+        }
+        if (m + 2 < nm) {  // stage st takes member m + 2 once these MMAs have read it
+          mma_commit(&bars[2 + st]);
+          pendm[st] = true;
+          if (mbar_wait(&bars[2 + st], pm[st])) {
+            pm[st] ^= 1u;
+            pendm[st] = false;
+          } else {
+            timeout();
+            break;
+          }
+          load(m + 2, st);
+        }
+      }
+      mma_commit(&bars[4]);
+    }
+    if (mbar_wait(&bars[4], p4)) p4 ^= 1u;
+    else timeout();
+    tc_fence_after();
+    __syncthreads();
+    if (*abort_flag) break;
+    // every MMA is done: the stages take the epilogue's staging (4 KB per warp)
+    float4* stage = reinterpret_cast<float4*>(sm + (size_t)warp * 4096);
+    store_block_staged(tmem + lb, h, lane, ws.dEdG + (size_t)(row0 + quarter * 32) * D + n0, D, nc, stage, 0);
+    fence_proxy_async();  // generic writes to the stages before the next item's copies
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
+  // on abort: let this CTA's copies and MMAs land (bounded) before freeing TMEM
+  if (tid == 0 && *abort_flag) {
+    for (int i = 0; i < 2; ++i) {
+      if (pendc[i]) mbar_wait(&bars[i], pc[i]);
+      if (pendm[i]) mbar_wait(&bars[2 + i], pm[i]);
+    }
+    mma_commit(&bars[4]);
+    mbar_wait(&bars[4], p4);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, kCols);
 }
 
 // ---------------------------------------------------------------------------
@@ -1212,8 +1344,12 @@ size_t smem_bytes_wide() {
 
 template <int S>
 cudaError_t set_smem_wide() {
-  return cudaFuncSetAttribute(k_mlp_tc_wide<desc_len(S)>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem_bytes_wide());
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_tc_wide<desc_len(S)>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes_wide());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_dedg_ens<desc_len(S)>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes_dedg());
+  return e;
 }
 
 }  // namespace
@@ -1358,9 +1494,21 @@ int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t stream, long long rows, int m0, int
     k_mlp_tc<48, false><<<grid, kTcThreads, sm, stream>>>(io, ctx->P, w, tw, fw, m0, nm, accm);
   else {
     const size_t smw = smem_bytes_wide();
-#define WIDE(s) k_mlp_tc_wide<desc_len(s)><<<grid, kTcThreads, smw, stream>>>(io, ctx->P, w, tw, fw, m0, nm, accm)
+    // an ensemble run side by side (all members, outputs added): g1 tiles,
+    // then dE/dG as one product over the members
+    uint8_t* g1 = (accm && m0 == 0 && nm == ctx->n_members && ctx->ens_wide()) ? ctx->b_g1 : nullptr;
+#define WIDE(s) \
+  k_mlp_tc_wide<desc_len(s)><<<grid, kTcThreads, smw, stream>>>(io, ctx->P, w, tw, fw, m0, nm, accm, g1)
     switch (ctx->P.S) { NNP_WIDE_CASES(WIDE) }
 #undef WIDE
+    if (g1) {
+      const long long items = tiles * ((D + kWideNC - 1) / kWideNC);
+      const int gd = (int)std::max<long long>(1, std::min<long long>(items, ctx->num_sms));
+      const size_t smd = smem_bytes_dedg();
+#define DEDG(s) k_dedg_ens<desc_len(s)><<<gd, kTcThreads, smd, stream>>>(ctx->P, w, tw, g1, nm)
+      switch (ctx->P.S) { NNP_WIDE_CASES(DEDG) }
+#undef DEDG
+    }
   }
   return NNP_OK;
 }

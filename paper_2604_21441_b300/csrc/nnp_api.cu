@@ -107,6 +107,7 @@ int nnp_ctx::ensure_capacity(long long n, int B, long long bins, long long rows)
   GR(b_Gh, c_Gh, (size_t)rows * ((P.D + 63) / 64 * 64));  // swizzled BF16 tiles
   GR(b_dEdG, c_dEdG, (size_t)rows * P.D);
   GR(b_Ei, c_Ei, (size_t)rows);
+  if (ens_wide()) GR(b_g1, c_g1, (size_t)((rows + 127) / 128) * n_members * kG1TileBytes);
   GR(b_sys, c_sys, (size_t)B);
   GR(b_pos_stage, c_pos_stage, (size_t)n * 3);
   GR(b_Z_stage, c_Z_stage, (size_t)n);
@@ -209,11 +210,12 @@ int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows,
   } else {  // ensemble members side by side in one launch, outputs added with reductions
     if (n_members > 1) {
       CK(cudaMemsetAsync(b_Ei, 0, sizeof(float) * (size_t)rows, stream));
-      CK(cudaMemsetAsync(b_dEdG, 0, sizeof(float) * (size_t)rows * P.D, stream));
+      // wide networks write dE/dG once, from one product over the members
+      if (!ens_wide()) CK(cudaMemsetAsync(b_dEdG, 0, sizeof(float) * (size_t)rows * P.D, stream));
     }
     int rc = launch_mlp_tc(this, stream, rows, 0, n_members, n_members > 1 ? 1 : 0);
     if (rc) return rc;
-    ++launches;
+    launches += ens_wide() ? 2 : 1;
   }
   if (ee_mode) {  // embedding: potentials, charge network, dE/dG of the charges
     int rc = launch_ee_pre(rows, w, launches);

@@ -99,7 +99,7 @@ nnp_ctx::~nnp_ctx() {
   mlp_tc_free(this);
   void* bufs[] = {b_bin_count, b_bin_start, b_bin_len, b_atom_bin, b_atom_slot, b_atom_cell,
                   b_atom_sys, b_atom_off, b_row_atom, b_row_info, b_row_cell, b_pos4, b_cnt_r,
-                  b_cnt_a, b_nbr_r, b_G, b_dEdG, b_Ei, b_Gh, b_sys, b_pos_stage,
+                  b_cnt_a, b_nbr_r, b_G, b_dEdG, b_Ei, b_Gh, b_g1, b_sys, b_pos_stage,
                   b_Z_stage, b_F_stage, b_E_stage, b_seg, b_flags, b_queue, d_zlut, d_io, b_wf32,
                   fm_z, fm_dz, fm_t, fm_p, fm_v, fm_ref, fm_grad, fm_jobs,
                   mm.pos, mm.F, mm.sub_pos, mm.sub_F, mm.ld, mm.E, mm.Z, mm.sub_Z, mm.idx, mm.mark,

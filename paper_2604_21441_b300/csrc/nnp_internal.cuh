@@ -40,6 +40,7 @@ constexpr int kNbrWinSmall = 1024;          // the same for small systems (at mo
 constexpr long long kNbrRowsSmall = 8192;
 constexpr long long kCellsRowsSmall = 1536;  // up to this many rows the binning runs in one block
 constexpr int kNbrChunkStride = 36;       // floats per chunk in shared memory (bank spread)
+constexpr size_t kG1TileBytes = 3 * 128 * 128;  // one 128-row g1 tile (K = 160 in three swizzled slabs), BF16
 constexpr int kMaxD = kNRad * kMaxS + kNAng * kMaxS * (kMaxS + 1) / 2;  // 1280
 __host__ __device__ constexpr int desc_len(int S) { return kNRad * S + kNAng * S * (S + 1) / 2; }
 

@@ -10,6 +10,10 @@ ANI-2x model of the performance-scaling study in the Results).
 * M = 8 on the 12,288-atom box against the oracle on sampled atoms;
 * M = 3, FP8 (per-member activation and weight scales): within the FP8
   form's bounds against the oracle's ensemble mean;
+* wide descriptors (3 and 7 species), BF16: dE/dG of the ensemble is one
+  product over the members (k_dedg_ens); M = 4 against the mean of the four
+  networks evaluated one at a time, which differ only in FP32 summation
+  order (1e-6 relative energy, 1e-5 eV/A);
 * a missing member, M above the maximum and a force-matching call without v
   or reference forces are refused, and the context keeps working (ensemble
   force matching itself: tests/test_gpu_force_match.py).
@@ -116,6 +120,38 @@ def test_copies_equal_single_network(P, prec):
     E4, F4 = four.eval(s.pos, s.Z, box9(s.box))
     assert abs(E4 - E1) <= 1e-6 * np.abs(Ei1).sum()
     assert np.abs(F4 - F1).max() <= 1e-5
+
+
+@pytest.mark.parametrize("Zs", [(1, 6, 8), (1, 6, 7, 8, 9, 16, 17)])
+def test_bf16_wide_ensemble_matches_members(P, Zs):
+    """Four members over a 3-species (D = 240: two dE/dG column blocks, the
+    last 112 wide) or 7-species (D = 1,008) descriptor.  The output layers are
+    stored divided by M = 4 (exact in binary), so every member's BF16 path is
+    the single network's scaled by 1/4, and the ensemble differs from the
+    mean of single evaluations only in the order of the FP32 sums of dE/dG."""
+    S = len(Zs)
+    D = 16 * S + 32 * S * (S + 1) // 2
+    s = synth.hcno_box(771 + S, L=18.0, n_cluster_atoms=300, max_waters=120,
+                       elements=np.array(Zs, dtype=np.int32), probs=np.full(S, 1.0 / S))
+    mem = [weights32(S, D, 772 + 5 * m, 773 + 5 * m) for m in range(4)]
+    Es, Fs = [], []
+    for w in mem:
+        one = P.NNP(atomic_numbers=Zs, precision="bf16", max_atoms=s.n)
+        one.set_all_weights(_f32(w))
+        E, F = one.eval(s.pos, s.Z, box9(s.box))
+        Es.append(E)
+        Fs.append(F)
+        one.close()
+    ens = P.NNP(atomic_numbers=Zs, precision="bf16", n_members=4, max_atoms=s.n)
+    ens.set_member_weights([_f32(w) for w in mem])
+    for _ in range(2):  # direct, then the graph replay
+        E4, F4 = ens.eval(s.pos, s.Z, box9(s.box))
+        Ei4 = ens.atom_energies(s.n)
+        Em, Fm = np.mean(Es), np.mean(Fs, axis=0)
+        print(f"{S} species, {s.n} atoms: |dE| {abs(E4 - Em):.2e} of {np.abs(Ei4).sum():.1f}, "
+              f"max|dF| {np.abs(F4 - Fm).max():.2e}")
+        assert abs(E4 - Em) <= 1e-6 * np.abs(Ei4).sum()
+        assert np.abs(F4 - Fm).max() <= 1e-5
 
 
 def test_ensemble8_water4096_sampled(P, oracle_mod):
