@@ -51,7 +51,11 @@ typedef enum {
     NNP_ERR_CUDA = 5,            /* a CUDA runtime call failed */
     NNP_ERR_TIMEOUT = 6,         /* a bounded device wait expired */
     NNP_ERR_NO_WEIGHTS = 7,      /* nnp_eval before every species had weights */
-    NNP_ERR_NO_STATE = 8         /* nnp_force_match_grad before any nnp_eval */
+    NNP_ERR_NO_STATE = 8,        /* nnp_force_match_grad before any nnp_eval */
+    NNP_ERR_BOUNDS = 9           /* bounds-checked build only (NNP_CHECKED): an index read from
+                                    device data was out of range; the access was skipped and the
+                                    results of the call are not valid (the message names the
+                                    source line and the value) */
 } nnp_status;
 
 typedef enum {
@@ -352,6 +356,12 @@ int nnp_atom_energies(nnp_ctx *ctx, double *out);
  *   then returns NNP_ERR_TIMEOUT (the expected outcome), clears the flag, and
  *   the context stays usable; any other status means the bound failed. */
 #define NNP_SELFTEST_WAIT_TIMEOUT 1
+/*   NNP_SELFTEST_BOUNDS: one kernel checks an index that is out of range with
+ *   the bounds-checked build's check.  A library built with NNP_CHECKED
+ *   returns NNP_ERR_BOUNDS (the expected outcome) and clears the flag; the
+ *   ordinary build, whose checks compile to nothing, returns
+ *   NNP_ERR_UNSUPPORTED. */
+#define NNP_SELFTEST_BOUNDS 2
 int nnp_selftest(nnp_ctx *ctx, int32_t test);
 
 /* Queries for tests and benchmarks. */
@@ -371,9 +381,11 @@ typedef enum {
                                         (> 0: from the work queue; < 0: static order) */
     NNP_Q_TUNE_BACKWARD_TILE = 12,   /* rows per work item of the descriptor-backward kernel
                                         (-1: one row, static order) */
-    NNP_Q_TUNE_NEIGHBOURS_QUEUE = 13 /* the neighbour kernel's form: bit 0 cells from the work
-                                        queue (else static order), bit 1 each cell's groups of
-                                        16 rows alternate between two warps */
+    NNP_Q_TUNE_NEIGHBOURS_QUEUE = 13, /* the neighbour kernel's form: bit 0 cells from the work
+                                         queue (else static order), bit 1 each cell's groups of
+                                         16 rows alternate between two warps */
+    NNP_Q_CHECKED_BUILD = 14         /* 1: the library was built with NNP_CHECKED (indices read
+                                        from device data are bounds-checked) */
 } nnp_query_key;
 
 int nnp_query(nnp_ctx *ctx, int32_t key, int64_t *value);

@@ -20,7 +20,8 @@ import os
 
 import numpy as np
 
-__all__ = ["NNP", "NNPError", "lib", "LIB_PATH", "PRECISIONS", "ABI_FUNCTIONS"]
+__all__ = ["NNP", "NNPError", "lib", "LIB_PATH", "PRECISIONS", "ABI_FUNCTIONS", "write_weights",
+           "read_weights"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libnnp.so")
@@ -48,10 +49,10 @@ QUERY = {"launches_per_eval": 0, "nbr_capacity": 1, "ang_capacity": 2, "max_nbr"
          "max_ang": 4, "rows": 5, "graph_captures": 6,
          "tune_neighbours": 7, "tune_descriptor": 8, "tune_backward": 9,
          "fp8_calibrated": 10, "tune_descriptor_tile": 11, "tune_backward_tile": 12,
-         "tune_neighbours_form": 13, "tune_neighbours_queue": 13}
+         "tune_neighbours_form": 13, "tune_neighbours_queue": 13, "checked_build": 14}
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNKNOWN_SPECIES", 3: "UNSUPPORTED", 4: "CAPACITY",
-          5: "CUDA", 6: "TIMEOUT", 7: "NO_WEIGHTS", 8: "NO_STATE"}
+          5: "CUDA", 6: "TIMEOUT", 7: "NO_WEIGHTS", 8: "NO_STATE", 9: "BOUNDS"}
 
 
 class NNPError(RuntimeError):
@@ -85,6 +86,48 @@ class Config(ctypes.Structure):
 
 
 _lib = None
+
+# Weight files (checkpoints of a model): one .npz with the species list, the
+# member count and, per member m, species s and layer l, the arrays
+# m{m}_s{s}_W{l} (fan_in x fan_out, float32) and m{m}_s{s}_b{l}.
+WEIGHTS_FORMAT = 1
+
+
+def write_weights(path, atomic_numbers, members):
+    """members[m][s] = [(W1, b1), ..., (W4, b4)] of member m, species s."""
+    arrays = {"format": np.int64(WEIGHTS_FORMAT),
+              "atomic_numbers": np.asarray(atomic_numbers, dtype=np.int32),
+              "n_members": np.int64(len(members))}
+    for m, species in enumerate(members):
+        if len(species) != len(atomic_numbers):
+            raise ValueError(f"member {m}: {len(species)} species, expected {len(atomic_numbers)}")
+        for sp, layers in enumerate(species):
+            for l, (W, b) in enumerate(layers):
+                arrays[f"m{m}_s{sp}_W{l}"] = np.ascontiguousarray(W, dtype=np.float32)
+                arrays[f"m{m}_s{sp}_b{l}"] = np.ascontiguousarray(b, dtype=np.float32).reshape(-1)
+    np.savez(path, **arrays)
+
+
+def read_weights(path):
+    """(atomic_numbers, members) from a file of write_weights."""
+    with np.load(path) as f:
+        if int(f["format"]) != WEIGHTS_FORMAT:
+            raise ValueError(f"{path}: weight file format {int(f['format'])}, expected {WEIGHTS_FORMAT}")
+        zs = tuple(int(z) for z in f["atomic_numbers"])
+        members = []
+        for m in range(int(f["n_members"])):
+            species = []
+            for sp in range(len(zs)):
+                layers = []
+                l = 0
+                while f"m{m}_s{sp}_W{l}" in f.files:
+                    layers.append((f[f"m{m}_s{sp}_W{l}"], f[f"m{m}_s{sp}_b{l}"]))
+                    l += 1
+                if not layers:
+                    raise ValueError(f"{path}: no layers for member {m}, species {sp}")
+                species.append(layers)
+            members.append(species)
+    return zs, members
 
 
 def lib() -> ctypes.CDLL:
@@ -215,6 +258,7 @@ class NNP:
         self.atomic_numbers = tuple(atomic_numbers)
         self.n_species = len(atomic_numbers)
         self.precision = precision
+        self._host_weights = {}  # (member, species) -> layers as set, for save_weights
         h = ctypes.c_void_p()
         rc = L.nnp_create(ctypes.byref(cfg), ctypes.byref(h))
         if rc:
@@ -263,6 +307,36 @@ class NNP:
             self._check(self._L.nnp_set_weights(self._h, int(species), Wp, bp))
         else:
             self._check(self._L.nnp_set_member_weights(self._h, int(member), int(species), Wp, bp))
+        self._host_weights[int(member), int(species)] = [
+            (np.array(W, dtype=np.float32, copy=True), np.array(b, dtype=np.float32, copy=True)) for W, b in layers]
+
+    def save_weights(self, path):
+        """Write every member's weights, as set, to a weight file (write_weights)."""
+        members = []
+        for m in range(self.n_members):
+            species = []
+            for sp in range(self.n_species):
+                if (m, sp) not in self._host_weights:
+                    raise ValueError(f"weights of member {m}, species {sp} were never set")
+                species.append(self._host_weights[m, sp])
+            members.append(species)
+        write_weights(path, self.atomic_numbers, members)
+
+    def load_weights(self, path):
+        """Set every member's weights from a weight file; its species list and
+        member count must be this context's."""
+        zs, members = read_weights(path)
+        if zs != self.atomic_numbers:
+            raise ValueError(f"{path}: species {zs}, this context has {self.atomic_numbers}")
+        self.set_member_weights(members)
+
+    @classmethod
+    def from_weights(cls, path, **kw):
+        """A context for the species and member count of a weight file, with its weights."""
+        zs, members = read_weights(path)
+        pot = cls(atomic_numbers=zs, n_members=len(members), **kw)
+        pot.set_member_weights(members)
+        return pot
 
     def set_all_weights(self, weights, member: int = 0):
         for s, layers in enumerate(weights):
@@ -395,6 +469,11 @@ class NNP:
         """Run the bounded-wait self-test; raises NNPError (code 6, timeout),
         which is the expected outcome."""
         self._check(self._L.nnp_selftest(self._h, 1))
+
+    def selftest_bounds(self) -> int:
+        """Run the bounds-check self-test; returns its status: 9 (BOUNDS) from
+        the bounds-checked library, 3 (UNSUPPORTED) from the ordinary one."""
+        return int(self._L.nnp_selftest(self._h, 2))
 
     def sync(self):
         self._check(self._L.nnp_sync(self._h))

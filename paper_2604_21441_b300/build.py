@@ -1,10 +1,13 @@
 """Build libnnp.so (all CUDA sources under csrc/) for sm_103a, in-tree.
 
-    python -m paper_2604_21441_b300.build [--verbose]
+    python -m paper_2604_21441_b300.build [--verbose] [--checked]
 
 Each .cu is compiled to an object under _build/ (in parallel), then linked
 into paper_2604_21441_b300/libnnp.so.  Sources are rebuilt when they or any
-header changed.
+header changed.  --checked builds the bounds-checked library instead
+(-DNNP_CHECKED: indices read from device data are checked before use and a
+bad one makes the call return NNP_ERR_BOUNDS), as libnnp_checked.so from
+objects under _build_checked/.
 """
 from __future__ import annotations
 
@@ -19,6 +22,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libnnp.so")
+LIB_CHECKED = os.path.join(HERE, "libnnp_checked.so")
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -31,12 +35,12 @@ def _headers():
         [os.path.join(ROOT, "include", "nnp.h")]
 
 
-def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src: str, verbose: bool, checked: bool = False) -> str:
+    obj = os.path.join(BUILD + ("_checked" if checked else ""), os.path.basename(src) + ".o")
     newest = max(os.path.getmtime(p) for p in [src] + _headers())
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest:
         return obj
-    cmd = [NVCC, *ARCH, *FLAGS, "-c", src, "-o", obj]
+    cmd = [NVCC, *ARCH, *FLAGS, *(["-DNNP_CHECKED"] if checked else []), "-c", src, "-o", obj]
     if verbose:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -47,21 +51,22 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
-def build(verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, checked: bool = False) -> str:
+    lib = LIB_CHECKED if checked else LIB
+    os.makedirs(BUILD + ("_checked" if checked else ""), exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
-    if os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs):
-        return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, verbose, checked), srcs))
+    if os.path.exists(lib) and os.path.getmtime(lib) >= max(os.path.getmtime(o) for o in objs):
+        return lib
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose="--verbose" in sys.argv))
+    print(build(verbose="--verbose" in sys.argv, checked="--checked" in sys.argv))

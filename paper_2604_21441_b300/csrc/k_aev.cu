@@ -282,7 +282,9 @@ __global__ void __launch_bounds__(256, 3) k_aev_fwd(const SysDesc* __restrict__ 
       const int ntot = rc->orr[S - 1] + rc->nr[S - 1];
 #pragma unroll 4
       for (int k = hl; k < ntot; k += 16) {
+        if (!NNP_IN(k, cr, ws.flags)) break;
         const int e = lr[k];
+        if (!(NNP_IN(nbr_row(e), rows, ws.flags) && NNP_IN(nbr_code(e), 27, ws.flags))) continue;
         const float4 pj = ws.pos4[nbr_row(e)];
         const float4 sv = sh[nbr_code(e)];
         const float dx = (pj.x - pi.x) + sv.x, dy = (pj.y - pi.y) + sv.y, dz = (pj.z - pi.z) + sv.z;
@@ -612,7 +614,9 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
           na_s = na[q];
           oa_s = oa[q];
         }
+      if (!NNP_IN(k, cr, ws.flags)) break;
       const int e = k < 32 ? e0 : (k < 64 ? e1 : lr[k]);
+      if (!(NNP_IN(nbr_row(e), rows, ws.flags) && NNP_IN(nbr_code(e), 27, ws.flags))) continue;
       const float4 pj = ws.pos4[nbr_row(e)];
       const float4 sv = sh[nbr_code(e)];
       const float dx = (pj.x - pi.x) + sv.x, dy = (pj.y - pi.y) + sv.y, dz = (pj.z - pi.z) + sv.z;
@@ -792,6 +796,7 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
     // about eleven atoms' contiguous x, y, z (few L2 sectors per instruction)
     for (int t = lane; t < 3 * ntot; t += 32) {
       const int k = t / 3;
+      if (!(NNP_IN(k, cr, ws.flags) && NNP_IN(origs[k], io->n_atoms, ws.flags))) continue;
       atomicAdd(Fout + 3 * (size_t)origs[k] + (t - 3 * k), (double)fsl[t]);
     }
 #pragma unroll
@@ -800,7 +805,8 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
       fiy += __shfl_xor_sync(FM, fiy, o);
       fiz += __shfl_xor_sync(FM, fiz, o);
     }
-    if (lane < 3) atomicAdd(Fout + 3 * (size_t)pos4_orig(pi) + lane, (double)(lane == 0 ? fix : (lane == 1 ? fiy : fiz)));
+    if (lane < 3 && NNP_IN(pos4_orig(pi), io->n_atoms, ws.flags))
+      atomicAdd(Fout + 3 * (size_t)pos4_orig(pi) + lane, (double)(lane == 0 ? fix : (lane == 1 ? fiy : fiz)));
   }
 }
 
@@ -882,6 +888,7 @@ __global__ void __launch_bounds__(256) k_aev_jvp(const SysDesc* __restrict__ sys
         const int k = k0 + hl;
         if (k < n_s) {
           const int e = lr[o_s + k];
+          if (!(NNP_IN(nbr_row(e), rows, ws.flags) && NNP_IN(nbr_code(e), 27, ws.flags))) continue;
           const float4 pj = ws.pos4[nbr_row(e)];
           const float4 sv = sh[nbr_code(e)];
           const float dx = (pj.x - pi.x) + sv.x, dy = (pj.y - pi.y) + sv.y, dz = (pj.z - pi.z) + sv.z;
@@ -911,6 +918,7 @@ __global__ void __launch_bounds__(256) k_aev_jvp(const SysDesc* __restrict__ sys
       const int n_a = rc->na[s], o_r = rc->orr[s], o_a = rc->oa[s];
       for (int k = hl; k < n_a; k += 16) {
         const int e = lr[o_r + k];
+        if (!(NNP_IN(nbr_row(e), rows, ws.flags) && NNP_IN(nbr_code(e), 27, ws.flags))) continue;
         const float4 pj = ws.pos4[nbr_row(e)];
         const float4 sv = sh[nbr_code(e)];
         const float dx = (pj.x - pi.x) + sv.x, dy = (pj.y - pi.y) + sv.y, dz = (pj.z - pi.z) + sv.z;

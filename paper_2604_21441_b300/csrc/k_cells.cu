@@ -248,7 +248,7 @@ __device__ __forceinline__ void scatter_atoms(const EvalIO* __restrict__ io, con
   const long long n = io->n_atoms;
   for (long long a = tid0; a < n; a += stride) {
     const int row = ws.bin_start[ws.atom_bin[a]] + ws.atom_slot[a];
-    ws.row_atom[row] = (int)a;
+    if (NNP_IN(row, ws.max_rows, ws.flags)) ws.row_atom[row] = (int)a;
   }
 }
 
@@ -458,6 +458,7 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
       __syncwarp();  // the previous window has been read
 #pragma unroll 4
       for (int k = k0; k < k1; ++k) {
+        if (!(NNP_IN(bst_s + k, ws.max_rows, ws.flags) && NNP_IN(db + bex_s + k - w0, WIN, ws.flags))) break;
         const float4 pj = ws.pos4[bst_s + k];
         const int gi = db + bex_s + k - w0, ci = (gi >> 5) * kNbrChunkStride + (gi & 31);
         wx[ci] = pj.x + vsx;

@@ -148,7 +148,8 @@ __global__ void __launch_bounds__(256, 1) k_mlp_f32(const EvalIO* __restrict__ i
   const int ntiles = rows / kTM;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int row0 = tile * kTM;
-    const int sp = pos4_species(ws.pos4[row0]);
+    int sp = pos4_species(ws.pos4[row0]);
+    if (!NNP_IN(sp, P.S, ws.flags)) sp = 0;
     // ---- forward
     float acc1[8][kH1 / 32];
     zero_acc<kH1>(acc1);
@@ -321,7 +322,8 @@ __global__ void __launch_bounds__(256, 1) k_fm_fwd(DescParams P, Workspace ws, M
   const int ntiles = ws.seg[S] / kTM;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int row0 = tile * kTM;
-    const int sp = pos4_species(ws.pos4[row0]);
+    int sp = pos4_species(ws.pos4[row0]);
+    if (!NNP_IN(sp, P.S, ws.flags)) sp = 0;
     {
       float acc[8][kH1 / 32], accd[8][kH1 / 32];
       zero_acc<kH1>(acc);
@@ -396,7 +398,8 @@ __global__ void __launch_bounds__(256, 1) k_fm_rev(DescParams P, Workspace ws, M
   const int ntiles = ws.seg[S] / kTM;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int row0 = tile * kTM;
-    const int sp = pos4_species(ws.pos4[row0]);
+    int sp = pos4_species(ws.pos4[row0]);
+    if (!NNP_IN(sp, P.S, ws.flags)) sp = 0;
     int valid[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) valid[i] = ws.row_atom[row0 + ty * 8 + i] >= 0;

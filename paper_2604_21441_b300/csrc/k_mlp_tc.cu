@@ -521,7 +521,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(const EvalIO* __restri
     cur_w = Wts + m0 + wi % nm;
     cur_f = Wfs + m0 + wi % nm;
     const int row0 = tile * kTM;
-    const int sp = pos4_species(ws.pos4[row0]);
+    int sp = pos4_species(ws.pos4[row0]);
+    if (!NNP_IN(sp, P.S, ws.flags)) sp = 0;
     const int nwi = wi + gridDim.x;
     const bool has_next = nwi < nwork;
     const int next = has_next ? nwi / nm : 0;
@@ -887,7 +888,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
     cur_w = Wts + m0 + wi % nm;
     cur_f = Wfs + m0 + wi % nm;
     const int row0 = tile * kTM;
-    const int sp = pos4_species(ws.pos4[row0]);
+    int sp = pos4_species(ws.pos4[row0]);
+    if (!NNP_IN(sp, P.S, ws.flags)) sp = 0;
     const int row = row0 + r;
     const int my_atom = ws.row_atom[row];
     const int my_sys = ws.row_info[row];
@@ -1132,7 +1134,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dedg_ens(DescParams P, Worksp
     const int tile = it / kNCB, cb = it - tile * kNCB;
     const int row0 = tile * kTM, n0 = cb * kWideNC, nc = min(kWideNC, D - n0);
     if (tid == 0) {
-      const int sp = pos4_species(ws.pos4[row0]);
+      int sp = pos4_species(ws.pos4[row0]);
+    if (!NNP_IN(sp, P.S, ws.flags)) sp = 0;
       const uint32_t wbytes = (uint32_t)(nc * 128);
       auto load = [&](int m, int st) {  // member m's g1 tile and W1 rows [n0, n0 + nc) into stage st
         mbar_expect_tx(&bars[st], (uint32_t)kG1TileBytes + (uint32_t)slabs_of(kH1) * wbytes);

@@ -520,6 +520,9 @@ int nnp_ctx::check_flags() {
   if (f[kFlagTimeout]) return fail(NNP_ERR_TIMEOUT, "a bounded device wait expired (tensor-core network)");
   if (f[kFlagBadPair])
     return fail(NNP_ERR_INVALID_ARG, "pair list: an index is out of range or a shift is not a whole periodic image");
+  if (f[kFlagChecked])
+    return fail(NNP_ERR_BOUNDS, "bounds check: index %d out of range at source line %d", f[kFlagCheckedValue],
+                f[kFlagCheckedLine]);
   if (f[kFlagOverflowR] || f[kFlagOverflowA]) {
     if (f[kFlagOverflowR]) cap_r = ((int)(f[kFlagMaxNbrR] * 1.25) + 31) / 32 * 32;
     if (f[kFlagOverflowA]) cap_a = ((int)(f[kFlagMaxNbrA] * 1.25) + 15) / 16 * 16;
@@ -549,6 +552,13 @@ bool nnp_ctx::weights_ready() const {
 
 // ---------------------------------------------------------------------------
 // C ABI
+
+namespace nnp {
+// NNP_SELFTEST_BOUNDS: one index that is out of range, through the checked build's check
+__global__ void k_bounds_selftest(int* flags) {
+  if (threadIdx.x == 0) (void)NNP_IN(7, 3, flags);  // the check records the index
+}
+}  // namespace nnp
 
 extern "C" {
 
@@ -793,6 +803,11 @@ int nnp_query(nnp_ctx* ctx, int32_t key, int64_t* value) {
     case NNP_Q_TUNE_DESCRIPTOR_TILE: *value = ctx->tune.fwd_tile; break;
     case NNP_Q_TUNE_BACKWARD_TILE: *value = ctx->tune.bwd_tile; break;
     case NNP_Q_TUNE_NEIGHBOURS_QUEUE: *value = ctx->tune.nbr_dyn; break;
+#ifdef NNP_CHECKED
+    case NNP_Q_CHECKED_BUILD: *value = 1; break;
+#else
+    case NNP_Q_CHECKED_BUILD: *value = 0; break;
+#endif
     default: return ctx->fail(NNP_ERR_INVALID_ARG, "unknown query key %d", key);
   }
   return NNP_OK;
@@ -819,11 +834,24 @@ int nnp_atom_energies(nnp_ctx* ctx, double* out) {
 
 int nnp_selftest(nnp_ctx* ctx, int32_t test) {
   if (!ctx) return NNP_ERR_INVALID_ARG;
-  if (test != NNP_SELFTEST_WAIT_TIMEOUT) return ctx->fail(NNP_ERR_INVALID_ARG, "unknown self-test %d", test);
+  if (test != NNP_SELFTEST_WAIT_TIMEOUT && test != NNP_SELFTEST_BOUNDS)
+    return ctx->fail(NNP_ERR_INVALID_ARG, "unknown self-test %d", test);
   int f[kNumFlags];
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->b_flags, 0, sizeof f, ctx->stream);
   if (e != cudaSuccess) return ctx->cuda_fail(e, "nnp_selftest");
+  if (test == NNP_SELFTEST_BOUNDS) {
+    k_bounds_selftest<<<1, 32, 0, ctx->stream>>>(ctx->b_flags);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f, ctx->b_flags, sizeof f, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->b_flags, 0, sizeof f, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "nnp_selftest");
+    if (f[kFlagChecked])
+      return ctx->fail(NNP_ERR_BOUNDS, "self-test: index %d out of range was caught (line %d), as designed",
+                       f[kFlagCheckedValue], f[kFlagCheckedLine]);
+    return ctx->fail(NNP_ERR_UNSUPPORTED, "self-test: the library was built without NNP_CHECKED");
+  }
   launch_wait_selftest(ctx->stream, ctx->b_flags, 2000000ull);  // 2 ms
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(f, ctx->b_flags, sizeof f, cudaMemcpyDeviceToHost, ctx->stream);

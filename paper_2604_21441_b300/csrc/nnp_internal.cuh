@@ -67,7 +67,10 @@ enum FlagWord {
   kFlagBinOverflow = 6, // a bin held more than the per-bin sort capacity
   kFlagTimeout = 7,
   kFlagBadPair = 8,     // a caller's pair: index out of range or shift not a whole image
-  kNumFlags = 9
+  kFlagChecked = 9,     // bounds-checked build: an index read from device data was out of range
+  kFlagCheckedLine = 10,  // its source line and value (the first one recorded)
+  kFlagCheckedValue = 11,
+  kNumFlags = 12
 };
 
 // Descriptor and network constants, passed by value to kernels.
@@ -193,6 +196,25 @@ struct Workspace {
 // pair of counters (items handed out, warps done); the last warp of a
 // dynamic launch to finish puts both back to zero for the next launch.
 enum QueueSlot { kQNbr = 0, kQFwd = 2, kQueueWords = 8 };
+
+// Bounds-checked build (compiled with -DNNP_CHECKED): an index read from
+// device data (a neighbour-list entry, a bin, a slot, a species) is checked
+// before it addresses memory.  A bad one raises kFlagChecked, records the
+// first source line and value, and the access is skipped; the host then
+// returns NNP_ERR_BOUNDS.  In the ordinary build the checks are constant true.
+__device__ __forceinline__ bool checked_in(long long i, long long n, int* flags, int line) {
+  if (i >= 0 && i < n) return true;
+  if (atomicOr(&flags[kFlagChecked], 1) == 0) {
+    flags[kFlagCheckedLine] = line;
+    flags[kFlagCheckedValue] = (int)i;
+  }
+  return false;
+}
+#ifdef NNP_CHECKED
+#define NNP_IN(i, n, flags) ::nnp::checked_in((long long)(i), (long long)(n), (flags), __LINE__)
+#else
+#define NNP_IN(i, n, flags) true
+#endif
 
 struct WorkQueue {
   int* q;

@@ -148,8 +148,25 @@ class NVE:
         self.box = np.diag(np.asarray(box, dtype=np.float64))
         self.E = torch.zeros(1, dtype=torch.float64, device=device)
         self.F = torch.zeros_like(self.r)
+        self.steps_done = 0
         torch.cuda.synchronize()
         self.pot.eval_into(self.r, self.Z, self.box, self.E, self.F, sync=True)
+
+    def save(self, path):
+        """Checkpoint of the state: positions, velocities, steps done, time
+        step, atomic numbers and box (one .npz).  Forces are recomputed on
+        restore, from the same positions."""
+        self.stream.synchronize()
+        np.savez(path, r=self.r.cpu().numpy(), v=self.v.cpu().numpy(), steps_done=np.int64(self.steps_done),
+                 dt_fs=np.float64(self.dt), Z=self.Z.cpu().numpy(), box=np.diag(self.box))
+
+    @classmethod
+    def restore(cls, path, pot: NNP, device="cuda"):
+        """An integrator that continues from a checkpoint of save()."""
+        with np.load(path) as f:
+            nve = cls(pot, f["r"], f["Z"], f["box"], f["v"], dt_fs=float(f["dt_fs"]), device=device)
+            nve.steps_done = int(f["steps_done"])
+        return nve
 
     def kinetic(self) -> torch.Tensor:
         with torch.cuda.stream(self.stream):
@@ -187,6 +204,7 @@ class NVE:
                             t.copy_(s)
                     self.stream.synchronize()
             done += k
+            self.steps_done += k
 
     def total_energy(self) -> float:
         ek = self.kinetic()
