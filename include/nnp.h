@@ -102,8 +102,8 @@ typedef enum {
  * zeta a power of two (<= 64), hidden = {160, 128, 96}, 1 <= S <= 8
  * (S = 7, D = 1008: the H, C, N, O, S, F, Cl element set of ANI-2x); other
  * values give NNP_ERR_UNSUPPORTED.  The BF16 form takes any S (above D = 128
- * layer 1 and dE/dG are streamed in chunks); the FP8 form takes S = 2
- * (D = 128); nnp_eval_noalloc takes S <= 4.
+ * layer 1 and dE/dG are streamed in chunks); the FP8 form takes S >= 2
+ * (D >= 128); nnp_eval_noalloc takes S <= 4.
  */
 typedef struct {
     int32_t n_species;                        /* S */

@@ -735,7 +735,12 @@ constexpr int kWideBars = 18; // mbarriers of k_mlp_tc_wide
 // g1out (ensembles): instead of the dE/dG blocks, each work item writes its
 // g1 tile (the three swizzled slabs, as the MMA reads them) to slot
 // tile * nm + member of g1out, and k_dedg_ens forms dE/dG from all members.
-template <int D>
+//
+// F8: the three forward GEMMs in E4M3, as in k_mlp_tc: G arrives as E4M3
+// (slabs of 128 columns; with D not a multiple of 32 the last MMA reads
+// zeros past D in both operands), and the epilogues rescale by s_x s_W[n]
+// and quantise h1 and h2 for the next layer; the backward stays BF16.
+template <int D, bool F8>
 __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __restrict__ io, DescParams P,
                                                        Workspace ws, const MlpTcWeights* __restrict__ Wts,
                                                        const MlpF32Weights* __restrict__ Wfs, int m0, int nm,
@@ -744,7 +749,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
   constexpr int kBufB = slabs_of(kH1) * kSlab;  // h1, later g1
   constexpr int kBufC = slabs_of(kH2) * kSlab;  // G chunk (stage 1), h2, later g3
   constexpr int kWBuf = 48 * 1024;
-  constexpr int kSl = slabs_of(D);                          // slabs of G and of W1^T
+  constexpr int kSl = F8 ? slabs8_of(D) : slabs_of(D);      // slabs of G and of W1^T
   constexpr int kNCB = (D + kWideNC - 1) / kWideNC;         // dE/dG blocks
   static_assert(D % 16 == 0 && D > kH2, "wide descriptor");
   static_assert(kBufA >= slabs_of(kH2) * kSlab && kBufC >= kWideKC * kSlab, "stage buffers");
@@ -770,6 +775,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
   float* sb3 = sb2 + kH2;
   float* sw4 = sb3 + kH3;
   float* sb4 = sw4 + kH3;
+  float* ssc = sb + kNB;  // FP8: [kH1 + kH2 + kH3] per-column dequantisation s_x s_W[n]
+  float* ssc1 = ssc;
+  float* ssc2 = ssc1 + kH1;
+  float* ssc3 = ssc2 + kH2;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int quarter = warp & 3, h = warp >> 2;
@@ -816,7 +825,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
   auto load_w = [&](int sp, int which, int b) {  // a whole matrix (layers 2, 3 and backward 3, 2)
     constexpr int NWt[6] = {kH1, kH2, kH3, kH2, kH1, D};
     constexpr int KWt[6] = {D, kH1, kH2, kH3, kH2, kH1};
-    const int bytes = mat_bytes(NWt[which], KWt[which]);
+    const int bytes = (F8 && which < 3) ? mat8_bytes(NWt[which], KWt[which]) : mat_bytes(NWt[which], KWt[which]);
     mbar_expect_tx(&bars[b], (uint32_t)bytes);
     bulk_g2s(wbuf[b], cur_w->m[sp][which], (uint32_t)bytes, &bars[b]);
     pend[b] = true;
@@ -826,7 +835,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
   auto load_slab = [&](int t, int sp, int k) {  // G and W1^T slab k into stage k & 3
     const int st = k & 3;
     mbar_expect_tx(&bars[10 + st], (uint32_t)(kSlab + kH1 * 128));
-    bulk_g2s(stage_g(st), reinterpret_cast<const uint8_t*>(ws.Gh) + (size_t)t * gh_tile_bytes(D) +
+    bulk_g2s(stage_g(st), reinterpret_cast<const uint8_t*>(ws.Gh) + (size_t)t * (F8 ? gh8_tile_bytes(D) : gh_tile_bytes(D)) +
                               (size_t)k * kSlab, (uint32_t)kSlab, &bars[10 + st]);
     bulk_g2s(stage_w(st), cur_w->m[sp][0] + (size_t)k * kH1 * 128, (uint32_t)(kH1 * 128), &bars[10 + st]);
     pendL[st] = true;
@@ -893,6 +902,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
     const int row = row0 + r;
     const int my_atom = ws.row_atom[row];
     const int my_sys = ws.row_info[row];
+    // FP8: z_l[n] = acc_l[n] * s_x s_W[n] + b_l[n]; q_l = 1 / s_{h_l} quantises h_l
+    float q1 = 1.f, q2 = 1.f;
+    if (F8) {
+      const int* qs = ws.q8 + 8 * ((size_t)(m0 + wi % nm) * kMaxS + sp);  // this member's ranges
+      const float sx0 = fp8_step(qs[0]), sx1 = fp8_step(qs[1]), sx2 = fp8_step(qs[2]);
+      q1 = 1.f / sx1;
+      q2 = 1.f / sx2;
+      for (int i = tid; i < kH1 + kH2 + kH3; i += blockDim.x)
+        ssc[i] = cur_w->wsc[sp][i] * (i < kH1 ? sx0 : (i < kH1 + kH2 ? sx1 : sx2));
+    }
     for (int i = tid; i < kNB; i += blockDim.x) {
       float v;
       if (i < kH1) v = cur_f->b[sp][0][i];
@@ -916,7 +935,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
           break;
         }
         tc_fence_after();
-        issue_gemm<false>(mz1, stage_g(st), stage_w(st), kH1, min(64, D - 64 * c), c > 0 ? 1u : 0u);
+        // F8: K of the last slab rounded up to whole MMAs (zeros past D in both operands)
+        const int kc = F8 ? min(128, (D - 128 * c + 31) / 32 * 32) : min(64, D - 64 * c);
+        issue_gemm<F8>(mz1, stage_g(st), stage_w(st), kH1, kc, c > 0 ? 1u : 0u);
         if (c + 4 < kSl) mma_commit(&bars[14 + st]);  // stage st is reloaded once these MMAs are done
         if (c >= 1 && c + 3 < kSl) {                   // slab c - 1 has been read: its stage takes c + 3
           const int sq = (c - 1) & 3;
@@ -940,19 +961,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
       float d[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        const float z = v[j] + sb1[c0 + j];
+        const float z = fmaf(v[j], F8 ? ssc1[c0 + j] : 1.f, sb1[c0 + j]);
         const float ez = ex2f(z * kexp);
         v[j] = z > 0.f ? z : al * (ez - 1.f);
         d[j] = z > 0.f ? 1.f : ez;
       }
       tmem_st16(tz1 + c0, d);
-      store_row16(bufB, r, c0, v);
+      if (F8) store_row16_e4m3(bufB, r, c0, v, q1);
+      else store_row16(bufB, r, c0, v);
     });
     // ---------------- layer 2: z2 = h1 W2
     if (!phase(1, -1)) break;
     if (tid == 0) {
       tc_fence_after();
-      issue_gemm<false>(mz2, bufB, wbuf[1], kH2, kH1);
+      issue_gemm<F8>(mz2, bufB, wbuf[1], kH2, kH1);
       commit();
     }
     wait_mma();
@@ -960,20 +982,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
       float d[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        const float z = v[j] + sb2[c0 + j];
+        const float z = fmaf(v[j], F8 ? ssc2[c0 + j] : 1.f, sb2[c0 + j]);
         const float ez = ex2f(z * kexp);
         v[j] = z > 0.f ? z : al * (ez - 1.f);
         d[j] = z > 0.f ? 1.f : ez;
       }
       tmem_st16(tz2 + c0, d);
-      store_row16(bufC, r, c0, v);
+      if (F8) store_row16_e4m3(bufC, r, c0, v, q2);
+      else store_row16(bufC, r, c0, v);
     });
     // ---------------- layer 3: z3 = h2 W3; energy and g3 = w4 CELU'(z3)
     if (!phase(0, -1)) break;
     if (tid == 0) {
       load_w(sp, 3, 1);  // W3 (backward) -> wbuf[1]
       tc_fence_after();
-      issue_gemm<false>(mz3, bufC, wbuf[0], kH3, kH2);
+      issue_gemm<F8>(mz3, bufC, wbuf[0], kH3, kH2);
       commit();
     }
     wait_mma();
@@ -982,7 +1005,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
       for_chunks<kH3>(tz3, h, [&](int c0, float (&v)[16]) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const float z = v[j] + sb3[c0 + j];
+          const float z = fmaf(v[j], F8 ? ssc3[c0 + j] : 1.f, sb3[c0 + j]);
           const float ww = sw4[c0 + j];
           const float ez = ex2f(z * kexp);
           e = fmaf(z > 0.f ? z : al * (ez - 1.f), ww, e);
@@ -1231,7 +1254,7 @@ void launch_wait_selftest(cudaStream_t st, int* flags, unsigned long long limit_
 // bits, non-negative, so integer atomicMax orders them).  Rows are species
 // sorted, so a warp flushes its running maxima only when the species changes.
 __global__ void __launch_bounds__(256) k_fp8_calib(DescParams P, Workspace ws, MlpF32Weights Wf, int member) {
-  __shared__ float xs[8][kH1], ys[8][kH1];
+  __shared__ float xs[8][kMaxD], ys[8][kH1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int D = P.D, rows = ws.seg[P.S];
   const float al = P.celu_alpha, inv_al = 1.f / P.celu_alpha;
@@ -1342,13 +1365,16 @@ cudaError_t set_smem(size_t sm) {
 
 size_t smem_bytes_wide() {
   return 1024 + (size_t)kWideKC * kSlab + slabs_of(kH1) * kSlab + slabs_of(kH2) * kSlab + 2 * 48 * 1024 +
-         kWideBars * 8 + 8 + kG * kTM * 4 + (kH1 + kH2 + 2 * kH3 + 1) * 4 + 64;
+         kWideBars * 8 + 8 + kG * kTM * 4 + (kH1 + kH2 + 2 * kH3 + 1) * 4 + (kH1 + kH2 + kH3) * 4 + 64;
 }
 
 template <int S>
 cudaError_t set_smem_wide() {
-  cudaError_t e = cudaFuncSetAttribute(k_mlp_tc_wide<desc_len(S)>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_bytes_wide());
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_tc_wide<desc_len(S), false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes_wide());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_mlp_tc_wide<desc_len(S), true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes_wide());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_dedg_ens<desc_len(S)>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes_dedg());
@@ -1362,8 +1388,8 @@ int mlp_tc_init(nnp_ctx* ctx) {
   const int D = ctx->P.D;
   if (!f8 && D != 128 && D != 48 && D != desc_len(ctx->P.S))
     return ctx->fail(NNP_ERR_UNSUPPORTED, "the BF16 tensor-core network takes the standard descriptor");
-  if (f8 && D != 128)
-    return ctx->fail(NNP_ERR_UNSUPPORTED, "the FP8 tensor-core network supports 2 species (D = 128)");
+  if (f8 && ctx->P.S < 2)
+    return ctx->fail(NNP_ERR_UNSUPPORTED, "the FP8 tensor-core network needs at least 2 species (D >= 128)");
   TcState* st = new TcState();
   st->f8 = f8;
   const int NW[6] = {kH1, kH2, kH3, kH2, kH1, D};
@@ -1411,7 +1437,7 @@ int mlp_tc_init(nnp_ctx* ctx) {
   }
   cudaMemset(ctx->b_q8, 0, sizeof(int) * 8 * kMaxS * sets);
   const size_t sm = smem_bytes(D);
-  if (f8) e = set_smem<128, true>(sm);
+  if (f8 && D == 128) e = set_smem<128, true>(sm);
   else if (D == 128) e = set_smem<128, false>(sm);
   else if (D == 48) e = set_smem<48, false>(sm);
   else {
@@ -1489,7 +1515,7 @@ int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t stream, long long rows, int m0, int
   const size_t sm = smem_bytes(D);
   const MlpTcWeights* tw = st->d_wm;
   const MlpF32Weights* fw = st->d_wf;
-  if (st->f8)
+  if (st->f8 && D == 128)
     k_mlp_tc<128, true><<<grid, kTcThreads, sm, stream>>>(io, ctx->P, w, tw, fw, m0, nm, accm);
   else if (D == 128)
     k_mlp_tc<128, false><<<grid, kTcThreads, sm, stream>>>(io, ctx->P, w, tw, fw, m0, nm, accm);
@@ -1500,8 +1526,10 @@ int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t stream, long long rows, int m0, int
     // an ensemble run side by side (all members, outputs added): g1 tiles,
     // then dE/dG as one product over the members
     uint8_t* g1 = (accm && m0 == 0 && nm == ctx->n_members && ctx->ens_wide()) ? ctx->b_g1 : nullptr;
-#define WIDE(s) \
-  k_mlp_tc_wide<desc_len(s)><<<grid, kTcThreads, smw, stream>>>(io, ctx->P, w, tw, fw, m0, nm, accm, g1)
+#define WIDE(s)                                                                                           \
+  if (st->f8) k_mlp_tc_wide<desc_len(s), true><<<grid, kTcThreads, smw, stream>>>(io, ctx->P, w, tw, fw, m0, \
+                                                                                   nm, accm, g1);         \
+  else k_mlp_tc_wide<desc_len(s), false><<<grid, kTcThreads, smw, stream>>>(io, ctx->P, w, tw, fw, m0, nm, accm, g1)
     switch (ctx->P.S) { NNP_WIDE_CASES(WIDE) }
 #undef WIDE
     if (g1) {
@@ -1517,7 +1545,6 @@ int launch_mlp_tc(nnp_ctx* ctx, cudaStream_t stream, long long rows, int m0, int
 }
 
 int launch_fp8_calib(nnp_ctx* ctx, cudaStream_t stream, long long rows) {
-  if (ctx->P.D > kH1) return ctx->fail(NNP_ERR_UNSUPPORTED, "FP8 calibration needs D <= %d", kH1);
   const int grid = (int)std::max<long long>(1, std::min<long long>((rows + 7) / 8, 8ll * ctx->num_sms));
   for (int m = 0; m < ctx->n_members; ++m)  // every member's activation ranges
     k_fp8_calib<<<grid, 256, 0, stream>>>(ctx->P, ctx->workspace(), ctx->wf32m[(size_t)m], m);

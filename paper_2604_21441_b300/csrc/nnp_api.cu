@@ -104,7 +104,11 @@ int nnp_ctx::ensure_capacity(long long n, int B, long long bins, long long rows)
   GR(b_cnt_a, c_rows6, (size_t)rows * kMaxS);
   GR(b_nbr_r, c_nbr_r, (size_t)rows * cap_r);
   GR(b_G, c_G, (size_t)rows * P.D);
-  GR(b_Gh, c_Gh, (size_t)rows * ((P.D + 63) / 64 * 64));  // swizzled BF16 tiles
+  __nv_bfloat16* gh_old = b_Gh;
+  GR(b_Gh, c_Gh, (size_t)rows * ((P.D + 63) / 64 * 64));  // swizzled BF16 tiles (or E4M3 ones)
+  // E4M3 tiles: the columns past D up to the next 32 are read by the last MMA
+  // of layer 1 and never written, so they must hold zeros
+  if (b_Gh != gh_old) CK(cudaMemsetAsync(b_Gh, 0, sizeof(__nv_bfloat16) * c_Gh, stream));
   GR(b_dEdG, c_dEdG, (size_t)rows * P.D);
   GR(b_Ei, c_Ei, (size_t)rows);
   if (ens_wide()) GR(b_g1, c_g1, (size_t)((rows + 127) / 128) * n_members * kG1TileBytes);

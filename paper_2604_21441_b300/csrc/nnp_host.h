@@ -100,12 +100,12 @@ struct nnp_ctx {
   float *b_G = nullptr, *b_dEdG = nullptr, *b_Ei = nullptr;
   __nv_bfloat16* b_Gh = nullptr;
   size_t c_G = 0, c_Gh = 0, c_dEdG = 0, c_Ei = 0;
-  // BF16 ensembles of wide networks: every (tile, member)'s g1 tile, so that
+  // tensor-core ensembles of wide networks: every (tile, member)'s g1 tile, so that
   // dE/dG is one product over all members (ens_wide())
   uint8_t* b_g1 = nullptr;
   size_t c_g1 = 0;
   bool ens_wide() const {
-    return cfg.precision == NNP_BF16 && n_members > 1 && P.D != 128 && P.D != 48;
+    return cfg.precision != NNP_FP32 && n_members > 1 && P.D != 128 && P.D != 48;
   }
   nnp::SysDesc* b_sys = nullptr;
   size_t c_sys = 0;
