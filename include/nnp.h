@@ -50,7 +50,9 @@ typedef enum {
     NNP_ERR_CAPACITY = 4,        /* neighbour lists overflowed (async path) or > max */
     NNP_ERR_CUDA = 5,            /* a CUDA runtime call failed */
     NNP_ERR_TIMEOUT = 6,         /* a bounded device wait expired */
-    NNP_ERR_NO_WEIGHTS = 7,      /* nnp_eval before every species had weights */
+    NNP_ERR_NO_WEIGHTS = 7,      /* nnp_eval before every species had weights; FP8, from nnp_sync:
+                                    an asynchronous evaluation met a species that no calibration
+                                    pass had seen (the next evaluation calibrates) */
     NNP_ERR_NO_STATE = 8,        /* nnp_force_match_grad before any nnp_eval */
     NNP_ERR_BOUNDS = 9           /* bounds-checked build only (NNP_CHECKED): an index read from
                                     device data was out of range; the access was skipped and the
@@ -67,9 +69,10 @@ typedef enum {
                      column for weights: s_W[n] = max_k |W[k][n]| / 448 at
                      nnp_set_weights; activations s_x = max|x| / 448 from an FP32
                      calibration pass over the first evaluation's input (and again
-                     after new weights, or while a species has not been seen).  The
+                     after new weights, or when an input has a species that no pass
+                     has seen: that evaluation is then calibrated and redone).  The
                      calibration pass makes that evaluation synchronous.  The backward
-                     stays BF16.  Two species (D = 128) only. */
+                     stays BF16.  Two species or more (D >= 128). */
 } nnp_precision;
 
 #define NNP_MAX_SPECIES 8
@@ -384,8 +387,9 @@ typedef enum {
     NNP_Q_TUNE_NEIGHBOURS_QUEUE = 13, /* the neighbour kernel's form: bit 0 cells from the work
                                          queue (else static order), bit 1 each cell's groups of
                                          16 rows alternate between two warps */
-    NNP_Q_CHECKED_BUILD = 14         /* 1: the library was built with NNP_CHECKED (indices read
+    NNP_Q_CHECKED_BUILD = 14,        /* 1: the library was built with NNP_CHECKED (indices read
                                         from device data are bounds-checked) */
+    NNP_Q_FP8_PASSES = 15            /* FP8: calibration passes run so far */
 } nnp_query_key;
 
 int nnp_query(nnp_ctx *ctx, int32_t key, int64_t *value);

@@ -49,7 +49,7 @@ QUERY = {"launches_per_eval": 0, "nbr_capacity": 1, "ang_capacity": 2, "max_nbr"
          "max_ang": 4, "rows": 5, "graph_captures": 6,
          "tune_neighbours": 7, "tune_descriptor": 8, "tune_backward": 9,
          "fp8_calibrated": 10, "tune_descriptor_tile": 11, "tune_backward_tile": 12,
-         "tune_neighbours_form": 13, "tune_neighbours_queue": 13, "checked_build": 14}
+         "tune_neighbours_form": 13, "tune_neighbours_queue": 13, "checked_build": 14, "fp8_passes": 15}
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNKNOWN_SPECIES", 3: "UNSUPPORTED", 4: "CAPACITY",
           5: "CUDA", 6: "TIMEOUT", 7: "NO_WEIGHTS", 8: "NO_STATE", 9: "BOUNDS"}

@@ -535,6 +535,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(const EvalIO* __restri
     float q1 = 1.f, q2 = 1.f;
     if (F8) {
       const int* qs = ws.q8 + 8 * ((size_t)(m0 + wi % nm) * kMaxS + sp);  // this member's ranges
+      if (tid == 0 && qs[0] == 0) atomicOr(&ws.flags[kFlagFp8Uncal], 1);  // the host calibrates and redoes
       const float sx0 = fp8_step(qs[0]), sx1 = fp8_step(qs[1]), sx2 = fp8_step(qs[2]);
       q1 = 1.f / sx1;
       q2 = 1.f / sx2;
@@ -906,6 +907,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
     float q1 = 1.f, q2 = 1.f;
     if (F8) {
       const int* qs = ws.q8 + 8 * ((size_t)(m0 + wi % nm) * kMaxS + sp);  // this member's ranges
+      if (tid == 0 && qs[0] == 0) atomicOr(&ws.flags[kFlagFp8Uncal], 1);  // the host calibrates and redoes
       const float sx0 = fp8_step(qs[0]), sx1 = fp8_step(qs[1]), sx2 = fp8_step(qs[2]);
       q1 = 1.f / sx1;
       q2 = 1.f / sx2;
@@ -1484,6 +1486,7 @@ int mlp_tc_set_weights(nnp_ctx* ctx, int member, int s, const float* hb) {
                    cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(ctx->b_q8, 0, sizeof(int) * 8 * kMaxS * ctx->n_members);
     ctx->fp8_calibrated = false;
+    ctx->fp8_pass_done = false;
     for (int t = 0; t < kMaxS; ++t) ctx->fp8_seen[t] = false;
   }
   if (e != cudaSuccess) return ctx->cuda_fail(e, "upload tensor-core weights");

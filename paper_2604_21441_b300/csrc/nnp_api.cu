@@ -244,8 +244,10 @@ void nnp_ctx::mark_stage(int k, bool capturing) {
 // over this input sets the activation ranges (Workspace::q8).  Runs before the
 // evaluation proper, outside any graph; the device flags accumulated by
 // earlier asynchronous evaluations are kept for nnp_sync.  Species absent
-// from this input stay uncalibrated, so a later input that has them is
-// calibrated again (the ranges only grow).  Returns -1 if the lists were regrown.
+// from this input stay uncalibrated; a later input that has one makes the
+// network kernel raise kFlagFp8Uncal, and that evaluation is calibrated again
+// (the ranges only grow) and redone.  An input without the absent species
+// needs no new pass.  Returns -1 if the lists were regrown.
 int nnp_ctx::calibrate_fp8(long long n, int B, long long bins, long long rows) {
   int saved[kNumFlags];
   CK(cudaStreamSynchronize(stream));
@@ -267,6 +269,8 @@ int nnp_ctx::calibrate_fp8(long long n, int B, long long bins, long long rows) {
     all = all && fp8_seen[s];
   }
   fp8_calibrated = all;
+  fp8_pass_done = true;
+  ++fp8_passes;
   return NNP_OK;
 }
 
@@ -464,7 +468,7 @@ int nnp_ctx::evaluate(int B, const int64_t* offsets, const double* pos, const in
     // device flags accumulate over asynchronous evaluations until nnp_sync reads them;
     // a synchronous evaluation reports only its own
     if (sync) CK(cudaMemsetAsync(b_flags, 0, sizeof(int) * kNumFlags, stream));
-    if (cfg.precision == NNP_FP8 && !fp8_calibrated) {
+    if (cfg.precision == NNP_FP8 && !fp8_pass_done) {
       rc = calibrate_fp8(n, B, bins, rows);
       if (rc == -1) continue;  // lists regrown: evaluate again
       if (rc) return rc;
@@ -527,6 +531,10 @@ int nnp_ctx::check_flags() {
   if (f[kFlagChecked])
     return fail(NNP_ERR_BOUNDS, "bounds check: index %d out of range at source line %d", f[kFlagCheckedValue],
                 f[kFlagCheckedLine]);
+  if (f[kFlagFp8Uncal]) {  // FP8: a species without activation ranges: calibrate and evaluate again
+    fp8_pass_done = false;
+    return -1;
+  }
   if (f[kFlagOverflowR] || f[kFlagOverflowA]) {
     if (f[kFlagOverflowR]) cap_r = ((int)(f[kFlagMaxNbrR] * 1.25) + 31) / 32 * 32;
     if (f[kFlagOverflowA]) cap_a = ((int)(f[kFlagMaxNbrA] * 1.25) + 15) / 16 * 16;
@@ -753,7 +761,12 @@ int nnp_sync(nnp_ctx* ctx) {
   e = cudaMemcpy(ctx->h_flags, ctx->b_flags, sizeof(int) * kNumFlags, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemset(ctx->b_flags, 0, sizeof(int) * kNumFlags);
   if (e != cudaSuccess) return ctx->cuda_fail(e, "nnp_sync flags");
+  const bool uncal = ctx->h_flags[kFlagFp8Uncal] != 0;
   int st = ctx->check_flags();
+  if (st == -1 && uncal)
+    return ctx->fail(NNP_ERR_NO_WEIGHTS,
+                     "FP8: a species appeared that no calibration pass has seen; the next evaluation calibrates, "
+                     "evaluate again");
   if (st == -1)
     return ctx->fail(NNP_ERR_CAPACITY,
                      "neighbour lists overflowed since the last check; capacity grown, evaluate again");
@@ -812,6 +825,7 @@ int nnp_query(nnp_ctx* ctx, int32_t key, int64_t* value) {
 #else
     case NNP_Q_CHECKED_BUILD: *value = 0; break;
 #endif
+    case NNP_Q_FP8_PASSES: *value = ctx->fp8_passes; break;
     default: return ctx->fail(NNP_ERR_INVALID_ARG, "unknown query key %d", key);
   }
   return NNP_OK;

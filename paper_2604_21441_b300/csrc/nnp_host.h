@@ -143,6 +143,8 @@ struct nnp_ctx {
   void* tc = nullptr;           // tensor-core network state (k_mlp_tc.cu)
   int* b_q8 = nullptr;          // FP8 scales (Workspace::q8)
   bool fp8_calibrated = false;  // every species has been seen by a calibration pass
+  bool fp8_pass_done = false;   // a calibration pass has run since the weights were set
+  long long fp8_passes = 0;     // calibration passes run
   bool fp8_seen[nnp::kMaxS] = {};
   int calibrate_fp8(long long n, int B, long long bins, long long rows);
 

@@ -70,7 +70,8 @@ enum FlagWord {
   kFlagChecked = 9,     // bounds-checked build: an index read from device data was out of range
   kFlagCheckedLine = 10,  // its source line and value (the first one recorded)
   kFlagCheckedValue = 11,
-  kNumFlags = 12
+  kFlagFp8Uncal = 12,   // FP8: a tile's species has no calibrated activation range yet
+  kNumFlags = 13
 };
 
 // Descriptor and network constants, passed by value to kernels.

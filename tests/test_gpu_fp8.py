@@ -84,6 +84,33 @@ def test_fp8_calibration_state(P):
     assert np.isfinite(E3) and np.isfinite(F3).all()
 
 
+def test_fp8_absent_species_need_no_new_pass(P):
+    """A seven-species FP8 model on water (five species never present): one
+    calibration pass, then graph replays without new passes; an input with a
+    new species (carbon) raises the network's flag, is calibrated and redone,
+    and agrees with a fresh context calibrated on that input first."""
+    Z7 = (1, 6, 7, 8, 9, 16, 17)
+    w = [[(W.astype(np.float32), b.astype(np.float32)) for W, b in sp] for sp in weights32(7, 1008, 41, 42)]
+    s = synth.water_box(200, 43)
+    pot = P.NNP(atomic_numbers=Z7, precision="fp8", max_atoms=s.n)
+    pot.set_all_weights(w)
+    for _ in range(4):
+        pot.eval(s.pos, s.Z, box9(s.box))
+    assert pot.query("fp8_passes") == 1 and pot.query("fp8_calibrated") == 0
+    Zc = s.Z.copy()
+    oxy = np.flatnonzero(s.Z == 8)[:5]
+    Zc[oxy] = 6  # five oxygens become carbons
+    E1, F1 = pot.eval(s.pos, Zc, box9(s.box))
+    assert pot.query("fp8_passes") == 2
+    fresh = P.NNP(atomic_numbers=Z7, precision="fp8", max_atoms=s.n)
+    fresh.set_all_weights(w)
+    fresh.eval(s.pos, s.Z, box9(s.box))     # the same two passes in the same order
+    E2, F2 = fresh.eval(s.pos, Zc, box9(s.box))
+    assert abs(E1 - E2) <= 1e-9 * abs(E2) and np.abs(F1 - F2).max() <= 1e-5
+    pot.close()
+    fresh.close()
+
+
 def test_fp8_close_to_bf16_and_fp32(P):
     s = synth.water_box(512, 77)
     w = weights32(2, 128, 78, 79)
