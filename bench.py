@@ -169,10 +169,14 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     w32 = [[(W.astype(np.float32), b.astype(np.float32)) for W, b in sp] for sp in w]
 
+    import synth
+    f32 = lambda wm: [[(W.astype(np.float32), b.astype(np.float32)) for W, b in sp] for sp in wm]
+    members = [w32] + [f32(synth.xavier_weights(S, D, wl["weight_seed"] + m)) for m in range(1, args.members)]
+
     def make(prec, flags=0):
         pot = P.NNP(atomic_numbers=wl["atomic_numbers"], precision=prec, max_atoms=n,
-                    max_systems=B, stream=stream, flags=flags | P.FLAG_AUTOTUNE)
-        pot.set_all_weights(w32)
+                    max_systems=B, stream=stream, flags=flags | P.FLAG_AUTOTUNE, n_members=args.members)
+        pot.set_member_weights(members)
         return pot
 
     pos = torch.tensor(pos_h, device=dev)
@@ -693,13 +697,15 @@ def run_reference(args):
         threads = 1
         sample = (f"each step {per_step:.1f} s of sampled atoms, single-threaded (a full OpenMP "
                   f"evaluation took {t_probe:.1f} s)")
-    t_all = float(np.sum(times))
+    t_all = float(np.sum(times)) * args.members  # an ensemble: every member evaluated in full
     value = evaluated / t_all
+    if args.members > 1:
+        sample += f"; one member's time times {args.members} members"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_all / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded water boxes, random Xavier weights)",
-            "config": workload_config(wl, args.precision, args.gpus),
+            "config": workload_config(wl, args.precision, args.gpus, args.members),
             "cpu_baseline": {"value": r4(value), "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": sample, "cpu": cpu_model(), "nproc": os.cpu_count()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -813,6 +819,9 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
     ap.add_argument("--compare", default="fp32,bf16,fp8")
     ap.add_argument("--workload", type=int, default=3)
+    ap.add_argument("--members", type=int, default=1,
+                    help="networks in the ensemble (member m > 0 takes the weight seed + m); "
+                         "8 with --workload 6 is the ANI-2x architecture on the seven-element box")
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--ref-budget", type=float, default=200.0,
                     help="reference arm: seconds allowed for its timed full evaluations")
@@ -854,6 +863,7 @@ def main():
     # algorithmic work (counted from the workload's neighbour statistics)
     n_pairs, n_trip = neighbour_stats(r)
     fl_desc, fl_mlp, fl_bwd = algorithmic_flops(n_pairs, n_trip, r["n"], r["D"], r["S"])
+    fl_mlp *= args.members  # every member's network runs
     alu_peak = alu_peak_tflops(local_rank)
     n_sm = torch.cuda.get_device_properties(local_rank).multi_processor_count
     work = {"descriptor": (fl_desc, "alu"), "descriptor_backward": (fl_bwd, "alu"),
@@ -861,7 +871,7 @@ def main():
     dom = max(work, key=lambda k: st[k])
     fl_instr, bound = work[dom]
     water = r["S"] == 2 and r["wl"]["name"].startswith("water")
-    fl_scope = SCOPE_FLOP_PER_ATOM[dom] * r["n"] if water else None
+    fl_scope = SCOPE_FLOP_PER_ATOM[dom] * r["n"] * (args.members if dom == "network" else 1) if water else None
     if bound == "tensor":
         peak = pk["bf16_tflops"] * (2.0 if args.precision == "fp8" else 1.0)
         peak_src = f"{pk_kind} cuBLAS bf16 burst" + (" x 2 (fp8)" if args.precision == "fp8" else "")
@@ -879,7 +889,7 @@ def main():
                 "work_instruction_count": f"{fl_instr:.4g} FLOP (per pair/triplet counts)",
                 "peak_source": peak_src, "stage_ms": {k: r4(v) for k, v in st.items()}}
     # the CPU baseline is timed at N = 1 only (rank 0 of a multi-GPU run skips it)
-    cpu = cpu_baseline(r["wl"], r["w"]) if world == 1 and args.cpu_baseline else None
+    cpu = cpu_baseline(r["wl"], r["w"], args.members) if world == 1 and args.cpu_baseline else None
     ms_mean = float(np.mean(r["ms"]))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -887,7 +897,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else
         ("bf16" if args.precision == "bf16" else "fp8-e4m3"),
         "data": "synthetic (seeded water boxes, random Xavier weights)",
-        "config": workload_config(r["wl"], args.precision, world),
+        "config": workload_config(r["wl"], args.precision, world, args.members),
         "e2e": {"value": r4(r["e2e"]), "unit": UNIT, "ms_per_step": r4(r["e2e_ms"]),
                 "h2d_bytes_per_step": r["n"] * (24 + 4), "d2h_bytes_per_step": r["n"] * 24 + 8 * r["B"]},
         "gpu_launches": int(r["launches"]) * args.steps,
@@ -926,24 +936,30 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def workload_config(wl, precision, world=1):
+def workload_config(wl, precision, world=1, members=1):
     """The JSON line's config block (the same for both arms)."""
     S = len(wl["atomic_numbers"])
-    return {"workload": wl["name"], "atoms": int(sum(s.n for s in wl["systems"])),
-            "systems": len(wl["systems"]), "species": S, "aev_length": int(16 * S + 16 * S * (S + 1)),
-            "precision": precision,
-            "l2": "flushed (256 MB write) between timed steps, outside the timed events",
-            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}
+    cfg = {"workload": wl["name"], "atoms": int(sum(s.n for s in wl["systems"])),
+           "systems": len(wl["systems"]), "species": S, "aev_length": int(16 * S + 16 * S * (S + 1)),
+           "precision": precision,
+           "l2": "flushed (256 MB write) between timed steps, outside the timed events",
+           "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}
+    if members > 1:
+        cfg["members"] = members
+    return cfg
 
 
-def cpu_baseline(wl, w):
+def cpu_baseline(wl, w, members=1):
     """One full evaluation of the workload by the OpenMP build of the oracle
-    over the host's cores (the FP64 oracle's arithmetic, threads over atoms)."""
+    over the host's cores (the FP64 oracle's arithmetic, threads over atoms).
+    An ensemble of M networks is timed as one network's evaluation times M
+    (the oracle evaluates each member in full)."""
     n = sum(s.n for s in wl["systems"])
     t, threads = oracle_full_omp(wl, w)
-    return {"value": r4(n / t), "unit": UNIT, "cores": threads, "kind": "oracle",
+    ens = f"; one member's evaluation times {members} members" if members > 1 else ""
+    return {"value": r4(n / (t * members)), "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"one full evaluation (E, F of all {n} atoms), OpenMP build of the oracle, "
-                      f"{threads} threads, {t:.1f} s", "cpu": cpu_model()}
+                      f"{threads} threads, {t:.1f} s{ens}", "cpu": cpu_model()}
 
 
 STAGE_KERNEL = {"descriptor": "k_aev_fwd", "descriptor_backward": "k_aev_bwd",

@@ -95,6 +95,21 @@ __device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, un
   return true;
 }
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) { return mbar_wait_for(bar, parity, kWaitNs); }
+// The same bound for threads that only wait (epilogue threads while thread 0
+// streams operands and issues MMAs): they back off with nanosleep between
+// tries, so that their polling does not take issue slots from the thread
+// that does the work.
+__device__ __forceinline__ bool mbar_wait_idle(uint64_t* bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  unsigned ns = 32;
+  while (!mbar_try(bar, parity)) {
+    if (global_ns() - t0 > kWaitNs) return false;
+    __nanosleep(ns);
+    ns = ns < 256 ? 2 * ns : 256;
+  }
+  return true;
+}
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -496,6 +511,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc(const EvalIO* __restri
   };
   auto wait_mma = [&](int b) {
     uint32_t& p = b == 4 ? ph4 : ph[3];
+    if (warp == 0) __syncwarp();  // lanes 1-31 do not poll beside thread 0 while it issues
     if (mbar_wait(&bars[b], p)) {
       p ^= 1u;
       if (tid == 0) {
@@ -883,8 +899,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
     __syncthreads();
     return *abort_flag == 0;
   };
-  auto wait_bar = [&](uint64_t* bar, uint32_t& p) {  // every thread: MMAs committed to bar
-    if (mbar_wait(bar, p)) p ^= 1u;
+  // every thread: MMAs committed to bar; idle: threads other than 0 back off
+  // (layer 1, where thread 0 keeps streaming slabs while the others wait)
+  auto wait_bar = [&](uint64_t* bar, uint32_t& p, bool idle = false) {
+    if (warp == 0) __syncwarp();  // lanes 1-31 do not poll beside thread 0 while it issues
+    if ((idle && tid != 0) ? mbar_wait_idle(bar, p) : mbar_wait(bar, p)) p ^= 1u;
     else timeout();
     tc_fence_after();
   };
@@ -951,7 +970,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_tc_wide(const EvalIO* __r
       mma_commit(&bars[4]);
       pend4 = true;
     }
-    wait_bar(&bars[4], ph4);
+    wait_bar(&bars[4], ph4, true);  // lanes 1-31 of warp 0 wait for thread 0 at a warp barrier
     if (tid == 0) {
       pend4 = false;
       if (*abort_flag == 0) {
@@ -1204,7 +1223,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dedg_ens(DescParams P, Worksp
       }
       mma_commit(&bars[4]);
     }
-    if (mbar_wait(&bars[4], p4)) p4 ^= 1u;
+    if (warp == 0) __syncwarp();  // lanes 1-31 wait here, not polling beside thread 0
+    if (mbar_wait_idle(&bars[4], p4)) p4 ^= 1u;
     else timeout();
     tc_fence_after();
     __syncthreads();
