@@ -101,8 +101,8 @@ __global__ void k_bin(const EvalIO* __restrict__ io, const SysDesc* __restrict__
 // One block of 1024 threads.  bin_start[b] = first row of bin b, with each
 // species segment starting on a multiple of kTileRows; bin_len keeps counts.
 __device__ __forceinline__ void scan_bins(const EvalIO* __restrict__ io, int S, const Workspace& ws,
-                                          int* s_bins /* [kScanSmemBins] shared */) {
-  constexpr int kReg = 16;  // bins per thread (up to kScanSmemBins bins go through shared memory)
+                                          int* s_bins /* [cap_bins] shared */, int cap_bins) {
+  constexpr int kReg = 16;  // bins per thread held in registers (up to 16,384 bins)
   __shared__ int warp_tot[32];
   __shared__ long long seg_s[kMaxS + 2];
   __shared__ int raw_at_species[kMaxS + 1];
@@ -111,7 +111,8 @@ __device__ __forceinline__ void scan_bins(const EvalIO* __restrict__ io, int S, 
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int chunk = (nb + 1023) / 1024;
   const int b0 = t * chunk, b1 = min(nb, b0 + chunk);
-  const bool in_smem = nb <= kScanSmemBins;
+  const bool in_smem = nb <= cap_bins;
+  const bool in_reg = nb <= 1024 * kReg;  // else (up to kScanSmemBins) the ranges are read from shared memory
   // coalesced loads into shared memory (and bin_len), then each thread scans
   // its contiguous range from there
   if (in_smem) {
@@ -124,11 +125,13 @@ __device__ __forceinline__ void scan_bins(const EvalIO* __restrict__ io, int S, 
   }
   int cnt[kReg];
   int sum = 0;
-  if (in_smem) {
+  if (in_reg) {
 #pragma unroll
     for (int i = 0; i < kReg; ++i) cnt[i] = (b0 + i < b1) ? s_bins[b0 + i] : 0;
 #pragma unroll
     for (int i = 0; i < kReg; ++i) sum += cnt[i];
+  } else if (in_smem) {
+    for (int b = b0; b < b1; ++b) sum += s_bins[b];
   } else {
     for (int b = b0; b < b1; ++b) sum += ws.bin_count[b];
   }
@@ -157,7 +160,7 @@ __device__ __forceinline__ void scan_bins(const EvalIO* __restrict__ io, int S, 
     // bins are species-major: species sp starts at bin sp * TC (no divisions per bin)
     int run = run0;
     int sp = TC > 0 ? b0 / TC : 0, sp_start = sp * TC;
-    if (in_smem) {
+    if (in_reg) {
 #pragma unroll
       for (int i = 0; i < kReg; ++i) {
         const int b = b0 + i;
@@ -170,6 +173,17 @@ __device__ __forceinline__ void scan_bins(const EvalIO* __restrict__ io, int S, 
           s_bins[b] = run;  // raw start
         }
         run += cnt[i];
+      }
+    } else if (in_smem) {
+      for (int b = b0; b < b1; ++b) {
+        if (b == sp_start + TC) {
+          ++sp;
+          sp_start += TC;
+        }
+        if (b == sp_start) raw_at_species[sp] = run;
+        const int c = s_bins[b];
+        s_bins[b] = run;  // raw start
+        run += c;
       }
     } else {
       for (int b = b0; b < b1; ++b) {
@@ -240,7 +254,7 @@ __device__ __forceinline__ void scan_bins(const EvalIO* __restrict__ io, int S, 
 
 __global__ void __launch_bounds__(1024) k_scan(const EvalIO* __restrict__ io, int S, Workspace ws) {
   extern __shared__ int s_bins[];  // [kScanSmemBins]: counts, then raw starts
-  scan_bins(io, S, ws, s_bins);
+  scan_bins(io, S, ws, s_bins, kScanSmemBins);
 }
 
 __device__ __forceinline__ void scatter_atoms(const EvalIO* __restrict__ io, const Workspace& ws, long long tid0,
@@ -310,10 +324,10 @@ __global__ void __launch_bounds__(1024) k_cells_small(const EvalIO* __restrict__
                                                       const SysDesc* __restrict__ sys,
                                                       const signed char* __restrict__ zlut, int S, int sort,
                                                       Workspace ws) {
-  extern __shared__ int s_dyn_cells[];  // [kScanSmemBins] scan, then [32][kSortCap] sort
+  extern __shared__ int s_dyn_cells[];  // [kScanSmemBinsSmall] scan, then [32][kSortCap] sort
   bin_atoms(io, sys, zlut, ws, threadIdx.x, 1024);
   __syncthreads();
-  scan_bins(io, S, ws, s_dyn_cells);
+  scan_bins(io, S, ws, s_dyn_cells, kScanSmemBinsSmall);
   __syncthreads();
   scatter_atoms(io, ws, threadIdx.x, 1024);
   __syncthreads();
@@ -751,7 +765,7 @@ cudaError_t neighbors_set_smem_limits() {
                                        (int)(sizeof(int) * kScanSmemBins));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_cells_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(int) * kScanSmemBins));
+                             (int)(sizeof(int) * kScanSmemBinsSmall));
   const int s1 = (int)neighbors_smem(kNbrWin), s2 = (int)neighbors_smem(kNbrWinSmall);
 #define NSM(sb)                                                                                                   \
   if (e == cudaSuccess)                                                                                           \

@@ -176,7 +176,7 @@ int nnp_ctx::launch_pipeline(long long n, int B, long long bins, long long rows,
   mark_stage(0, capturing);
   const int sort = (cfg.flags & NNP_FLAG_NONDETERMINISTIC_BINS) ? 0 : 1;
   if (rows <= kCellsRowsSmall) {  // small systems: the four binning steps in one block
-    k_cells_small<<<1, 1024, sizeof(int) * kScanSmemBins, stream>>>(io, sys, d_zlut, P.S, sort, w); ++launches;
+    k_cells_small<<<1, 1024, sizeof(int) * kScanSmemBinsSmall, stream>>>(io, sys, d_zlut, P.S, sort, w); ++launches;
   } else {
     k_bin<<<g_atoms, 256, 0, stream>>>(io, sys, d_zlut, w); ++launches;
     k_scan<<<1, 1024, sizeof(int) * kScanSmemBins, stream>>>(io, P.S, w); ++launches;

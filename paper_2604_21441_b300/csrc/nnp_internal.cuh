@@ -33,7 +33,8 @@ constexpr int kMaxS = 8;       // species supported by the kernels (stride of th
 constexpr int kTileRows = 128; // species segments are padded to this
 constexpr int kMaxCapA = 64;     // largest angular-neighbour capacity (staged per row)
 constexpr int kMaxCapR = 512;    // largest radial-neighbour capacity (gathered per row)
-constexpr int kScanSmemBins = 16384;  // k_scan stages up to this many bins in shared memory
+constexpr int kScanSmemBins = 49152;  // k_scan stages up to this many bins in shared memory (192 KB)
+constexpr int kScanSmemBinsSmall = 16384;  // the same for k_cells_small (64 KB, also its sort buffers)
 constexpr int kNbrThreads = 128;  // k_neighbors: warp per cell, lane per row
 constexpr int kNbrWin = 512;      // neighbourhood atoms one warp stages per window
 constexpr int kNbrWinSmall = 1024;          // the same for small systems (at most kNbrRowsSmall rows)
