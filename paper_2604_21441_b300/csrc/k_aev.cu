@@ -294,6 +294,11 @@ __global__ void __launch_bounds__(256, 3) k_aev_fwd(const SysDesc* __restrict__ 
     __syncwarp();
 
     // ---------------- radial
+    // BF16 / FP8 forms with evenly spaced shifts: the 16 terms from two
+    // anchors (4 and 12) by the ratio of neighbouring terms (DescParams),
+    // 6 exponentials instead of 16; acc2[d] then holds terms (4 + d, 12 + d),
+    // d = 0..3, and acc2[3 + d] terms (4 - d, 12 - d), d = 1..4.
+    const bool rec = mode != kGFp32 && P.rad_even;
 #pragma unroll 1
     for (int s = 0; s < S; ++s) {
       const int n_s = rc->nr[s], o_s = rc->orr[s];
@@ -309,19 +314,49 @@ __global__ void __launch_bounds__(256, 3) k_aev_fwd(const SysDesc* __restrict__ 
           float fc, dfc;
           cutoff(r, P.rc_r, kfr, fc, dfc);
           const f2 f = f2_make(0.25f * fc, 0.25f * fc), rr = f2_make(r, r);
+          if (rec) {
+            const f2 xa = f2_add(rr, f2_make(-P.shf_r[4], -P.shf_r[12]));
+            const f2 ea = f2_ex2(f2_mul(kr2, f2_mul(xa, xa)));
+            const f2 gx = f2_mul(f2_make(P.rad_gk, P.rad_gk), xa);
+            const f2 G = f2_ex2(gx), Gi = f2_ex2(f2_mul(gx, f2_make(-1.f, -1.f)));
+            acc2[0] = f2_fma(f, ea, acc2[0]);
+            f2 u = ea, w = ea;
 #pragma unroll
-          for (int m = 0; m < kNRad / 2; ++m) {
-            const f2 x = f2_add(rr, f2_make(-P.shf_r[2 * m], -P.shf_r[2 * m + 1]));
-            acc2[m] = f2_fma(f, f2_ex2(f2_mul(kr2, f2_mul(x, x))), acc2[m]);
+            for (int d = 1; d <= 4; ++d) {
+              const f2 c = f2_make(P.rad_c[d - 1], P.rad_c[d - 1]);
+              if (d < 4) {
+                u = f2_mul(f2_mul(u, G), c);
+                acc2[d] = f2_fma(f, u, acc2[d]);
+              }
+              w = f2_mul(f2_mul(w, Gi), c);
+              acc2[3 + d] = f2_fma(f, w, acc2[3 + d]);
+            }
+          } else {
+#pragma unroll
+            for (int m = 0; m < kNRad / 2; ++m) {
+              const f2 x = f2_add(rr, f2_make(-P.shf_r[2 * m], -P.shf_r[2 * m + 1]));
+              acc2[m] = f2_fma(f, f2_ex2(f2_mul(kr2, f2_mul(x, x))), acc2[m]);
+            }
           }
         }
       }
       float acc[kNRad];
+      if (rec) {
 #pragma unroll
-      for (int m = 0; m < kNRad / 2; ++m) {
-        const float2 h = f2_split(acc2[m]);
-        acc[2 * m] = h.x;
-        acc[2 * m + 1] = h.y;
+        for (int d = 0; d < 4; ++d) {
+          const float2 hu = f2_split(acc2[d]), hd = f2_split(acc2[4 + d]);
+          acc[4 + d] = hu.x;
+          acc[12 + d] = hu.y;
+          acc[3 - d] = hd.x;
+          acc[11 - d] = hd.y;
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < kNRad / 2; ++m) {
+          const float2 h = f2_split(acc2[m]);
+          acc[2 * m] = h.x;
+          acc[2 * m + 1] = h.y;
+        }
       }
       hw_reduce_scatter<kNRad>(acc, hl);
       if (live) put1(s * kNRad + hl, acc[0]);

@@ -650,6 +650,15 @@ int nnp_create(const nnp_config* cfg, nnp_ctx** out) {
   P.rc_a = (float)cfg->rc_a;
   P.eta_a = (float)cfg->eta_a;
   for (int m = 0; m < kNRad; ++m) P.shf_r[m] = (float)cfg->shf_r[m];
+  {
+    const double dR = cfg->shf_r[1] - cfg->shf_r[0];
+    bool even = dR > 0.0;
+    for (int m = 0; m < kNRad; ++m)
+      even = even && std::fabs(cfg->shf_r[m] - (cfg->shf_r[0] + m * dR)) <= 1e-6 * (1.0 + std::fabs(cfg->shf_r[m]));
+    P.rad_even = even ? 1 : 0;
+    P.rad_gk = (float)(2.0 * cfg->eta_r * dR / std::log(2.0));
+    for (int d = 1; d <= 4; ++d) P.rad_c[d - 1] = (float)std::exp(-cfg->eta_r * dR * dR * (2 * d - 1));
+  }
   for (int a = 0; a < kNAngR; ++a) P.shf_a[a] = (float)cfg->shf_a[a];
   for (int z = 0; z < kNAngZ; ++z) {
     P.hcos_z[z] = (float)(0.5 * std::cos(cfg->shf_z[z]));

@@ -85,6 +85,14 @@ struct DescParams {
   float shf_a[kNAngR];
   float hcos_z[kNAngZ], hsin_z[kNAngZ];  // cos(theta_z)/2, sin(theta_z)/2
   float celu_alpha;
+  // evenly spaced radial shifts R_m = R_0 + m dR (rad_even = 1): the BF16
+  // and FP8 forms' descriptor kernel takes exp(-eta_r (r - R_m)^2) from the
+  // anchors m = 4 and 12 by the ratio of neighbouring terms,
+  //   e_{A+-d} = e_{A+-(d-1)} * exp(+-2 eta_r dR (r - R_A)) * exp(-eta_r dR^2 (2d - 1)),
+  // rad_gk = 2 eta_r dR log2(e), rad_c[d - 1] = exp(-eta_r dR^2 (2d - 1))
+  int rad_even;
+  float rad_gk;
+  float rad_c[4];
 };
 
 // One periodic system.  Filled on the host, copied to the device per eval.
