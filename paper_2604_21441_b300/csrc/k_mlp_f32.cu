@@ -435,33 +435,40 @@ __global__ void __launch_bounds__(256, 1) k_fm_rev(DescParams P, Workspace ws, M
   }
 }
 
-// Weight-gradient reduction over the rows of one species.  Job = a 32 x 32
+// Weight-gradient reduction over the rows of one species.  Job = a 64 x 64
 // tile (i0, o0) of layer l's (fan_in x fan_out) gradient, for rows [r0, r1);
-// l = 4 means w4 (tile of 32 x 1).  FP32 partials per 64-row chunk, FP64 sums,
-// FP64 atomic add into the packed gradient (zeroed before).
+// l = 4 means w4 (tile of 64 x 1).  The job's rows go through shared memory
+// 32 at a time (the inputs h, dh and the adjoints t, p of the tile); thread
+// (ti, to) keeps a 4 x 4 block of the tile (inputs 4 ti.., outputs 4 to..),
+// so each row costs it four 16-byte shared loads for 32 FMAs, and each staged
+// value serves 64 products.  FP32 partials over 64 rows, FP64 sums, one FP64
+// atomic add per entry into the packed gradient (zeroed before).
+constexpr int kWgT = 64;       // tile edge (inputs and outputs)
+constexpr int kWgRows = 32;    // rows staged at a time
+constexpr int kWgLd = kWgT + 4;  // floats per staged row (16-byte aligned 4-column reads)
 __global__ void __launch_bounds__(256) k_fm_wgrad(DescParams P, const FmJob* __restrict__ jobs, int njobs,
                                                   const float* __restrict__ G, const float* __restrict__ dG,
                                                   const float* __restrict__ z, const float* __restrict__ dz,
                                                   const float* __restrict__ t, const float* __restrict__ p,
                                                   double* grad) {
-  __shared__ float Hc[64][33], DHc[64][33], Tc[64][33], Pc[64][33];
+  __shared__ __align__(16) float Hc[kWgRows][kWgLd], DHc[kWgRows][kWgLd], Tc[kWgRows][kWgLd], Pc[kWgRows][kWgLd];
   const int D = P.D;
   const float al = P.celu_alpha, inv_al = 1.f / P.celu_alpha;
   const int tid = threadIdx.x;
-  const int il = tid >> 3;          // 0..31 : input index in the tile
-  const int ol = (tid & 7) * 4;     // 0..28 : first of four output indices
+  const int ti = tid >> 4, to = tid & 15;
   for (int jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
     const FmJob jbv = jobs[jb];
     const int l = jbv.l;
     const int fin = l == 1 ? D : (l == 2 ? kH1 : (l == 3 ? kH2 : kH3));
     const int fout = l == 1 ? kH1 : (l == 2 ? kH2 : (l == 3 ? kH3 : 1));
-    double accd[4] = {0.0, 0.0, 0.0, 0.0};
-    double bacc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int c0 = jbv.r0; c0 < jbv.r1; c0 += 64) {
-      const int nr = min(64, jbv.r1 - c0);
+    double accd[4][4] = {}, bacc[4] = {};
+    float a[4][4] = {}, b[4] = {};
+    int chunks = 0;
+    for (int c0 = jbv.r0; c0 < jbv.r1; c0 += kWgRows) {
+      const int nr = min(kWgRows, jbv.r1 - c0);
       __syncthreads();
-      for (int e = tid; e < 64 * 32; e += 256) {
-        const int rr = e >> 5, cc = e & 31;
+      for (int e = tid; e < kWgRows * kWgT; e += 256) {
+        const int rr = e / kWgT, cc = e % kWgT;
         const int r = c0 + rr, i = jbv.i0 + cc, o = jbv.o0 + cc;
         float hv = 0.f, dhv = 0.f, tv = 0.f, pv = 0.f;
         if (rr < nr) {
@@ -489,29 +496,52 @@ __global__ void __launch_bounds__(256) k_fm_wgrad(DescParams P, const FmJob* __r
         Pc[rr][cc] = pv;
       }
       __syncthreads();
-      float a[4] = {0.f, 0.f, 0.f, 0.f}, b[4] = {0.f, 0.f, 0.f, 0.f};
       for (int rr = 0; rr < nr; ++rr) {
-        const float hv = Hc[rr][il], dhv = DHc[rr][il];
+        const float4 h4 = *reinterpret_cast<const float4*>(&Hc[rr][4 * ti]);
+        const float4 d4 = *reinterpret_cast<const float4*>(&DHc[rr][4 * ti]);
+        const float4 t4 = *reinterpret_cast<const float4*>(&Tc[rr][4 * to]);
+        const float4 p4 = *reinterpret_cast<const float4*>(&Pc[rr][4 * to]);
+        const float hv[4] = {h4.x, h4.y, h4.z, h4.w}, dv[4] = {d4.x, d4.y, d4.z, d4.w};
+        const float tv[4] = {t4.x, t4.y, t4.z, t4.w}, pv[4] = {p4.x, p4.y, p4.z, p4.w};
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          a[k] = fmaf(dhv, Tc[rr][ol + k], fmaf(hv, Pc[rr][ol + k], a[k]));
-          b[k] += Pc[rr][ol + k];
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) a[x][y] = fmaf(dv[x], tv[y], fmaf(hv[x], pv[y], a[x][y]));
+#pragma unroll
+        for (int y = 0; y < 4; ++y) b[y] += pv[y];
+      }
+      if (++chunks == 2 || c0 + kWgRows >= jbv.r1) {  // 64 rows in FP32, then FP64
+        chunks = 0;
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) {
+            accd[x][y] += (double)a[x][y];
+            a[x][y] = 0.f;
+          }
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          bacc[y] += (double)b[y];
+          b[y] = 0.f;
         }
       }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        accd[k] += (double)a[k];
-        bacc[k] += (double)b[k];
-      }
     }
-    const int i = jbv.i0 + il;
     const double sc = (double)jbv.scale;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int o = jbv.o0 + ol + k;
-      if (i < fin && o < fout) atomicAdd(&grad[jbv.w_off + (size_t)i * fout + o], -sc * accd[k]);
-      if (jbv.i0 == 0 && il == 0 && o < fout && l < 4) atomicAdd(&grad[jbv.b_off + o], -sc * bacc[k]);
+    for (int x = 0; x < 4; ++x) {
+      const int i = jbv.i0 + 4 * ti + x;
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int o = jbv.o0 + 4 * to + y;
+        if (i < fin && o < fout) atomicAdd(&grad[jbv.w_off + (size_t)i * fout + o], -sc * accd[x][y]);
+      }
     }
+    if (ti == 0 && jbv.i0 == 0 && l < 4)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int o = jbv.o0 + 4 * to + y;
+        if (o < fout) atomicAdd(&grad[jbv.b_off + o], -sc * bacc[y]);
+      }
   }
 }
 

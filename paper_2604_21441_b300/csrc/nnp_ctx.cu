@@ -276,8 +276,8 @@ int nnp_ctx::force_match_grad(const double* v, const double* Fref, double* loss,
   // 3. tangent descriptors dG = J_G v (into the dE/dG buffer)
   launch_aev_jvp(rows, num_sms, stream, b_sys, P, w, fm_v, b_dEdG);
   if (prof) CK(cudaEventRecord(fm_ev[2], stream));
-  // weight-gradient jobs per member, species, layer, 32 x 32 tile and
-  // 2,048-row segment (the segment bounds are the last evaluation's); the
+  // weight-gradient jobs per member, species, layer, 64 x 64 tile and
+  // 512-row segment (the segment bounds are the last evaluation's); the
   // device list is kept while the segments stay the same
   std::vector<FmJob>& jobs = fm_job_list;
   const int fin[4] = {D, kH1, kH2, kH3}, fout[4] = {kH1, kH2, kH3, 1};
@@ -294,11 +294,11 @@ int nnp_ctx::force_match_grad(const double* v, const double* Fref, double* loss,
         boff[l] = off;
         off += fout[l];
       }
-      for (int r0 = seg[sp]; r0 < seg[sp + 1]; r0 += 2048) {
-        const int r1 = std::min(seg[sp + 1], r0 + 2048);
+      for (int r0 = seg[sp]; r0 < seg[sp + 1]; r0 += 512) {
+        const int r1 = std::min(seg[sp + 1], r0 + 512);
         for (int l = 0; l < 4; ++l)
-          for (int i0 = 0; i0 < fin[l]; i0 += 32)
-            for (int o0 = 0; o0 < fout[l]; o0 += 32)
+          for (int i0 = 0; i0 < fin[l]; i0 += 64)
+            for (int o0 = 0; o0 < fout[l]; o0 += 64)
               jobs.push_back(FmJob{l + 1, i0, o0, r0, r1, l == 3 ? 1.0f / (float)n_members : 1.0f,
                                    (long long)woff[l], (long long)boff[l]});
       }
