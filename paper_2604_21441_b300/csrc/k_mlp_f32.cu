@@ -7,13 +7,11 @@
 //   g_3 = w_4 * CELU'(z_3),  g_{l-1} = (g_l W_l^T) * CELU'(z_{l-1}),
 //   dE/dG = g_1 W_1^T,   CELU'(z) = 1 (z > 0), h/alpha + 1 (z <= 0)
 //
-// One CTA of 256 threads per 64-row tile (one species per tile).  Above
-// kF32WholeD descriptor features the last product (dE/dG) runs in column
-// blocks of kF32ColBlock, so the accumulators and the weight chunk stay small.  Thread
-// (warp ty, lane tx) owns rows 8ty..8ty+7 and columns tx + 32j.  The tile's
-// activations stay in shared memory, transposed (feature-major, padded
-// leading dimension) so that a thread's 8 rows are two float4 loads;
-// weights stream through a shared chunk buffer.
+// The evaluation kernel runs two CTAs of 256 threads per SM, one 64-row tile
+// (one species) at a time; its layout is described above k_mlp_f32.  The
+// force-matching kernels share the simpler helpers below: one CTA per SM,
+// activations transposed with a padded leading dimension, thread (warp ty,
+// lane tx) owning rows 8ty..8ty+7 and columns tx + 32j.
 #include "nnp_internal.cuh"
 
 namespace nnp {
@@ -21,11 +19,6 @@ namespace nnp {
 constexpr int kTM = 64;          // rows per tile
 constexpr int kLDX = kTM + 4;    // padded leading dim of transposed activations
 constexpr int kKC = 32;          // streamed k-chunk
-constexpr int kF32WholeD = 384;  // widest descriptor whose dE/dG is one product
-constexpr int kF32ColBlock = 128;
-__host__ __device__ constexpr int f32_bsn(int D) {  // columns of the weight chunk buffer
-  return (D <= kF32WholeD ? (D > kH1 ? D : kH1) : (kF32ColBlock > kH1 ? kF32ColBlock : kH1));
-}
 
 // acc[8][NJ] += A(64 x K) * B(K x N).  A is either transposed in shared
 // memory (AT[k][kLDX]) or, if Ag != nullptr, rows of global memory (lda).
@@ -130,18 +123,180 @@ __device__ __forceinline__ void store_bwd(const float (&acc)[8][(N + 31) / 32], 
   }
 }
 
+// ---- the evaluation kernel (k_mlp_f32) ----------------------------------
+// Two CTAs of 256 threads per SM.  A 64-row tile's activations stay in shared
+// memory transposed and unpadded: element (feature c, row r) sits at
+// c*64 + 4*((r>>2) ^ (c&7)) + (r&3).  A thread's eight rows at one feature are
+// then two float4 (the same address across the warp, a broadcast), and the
+// float4 stores of an epilogue from eight consecutive features land on all 32
+// banks.  Weights stream through one 16-row chunk that each thread fetches
+// into registers a chunk ahead, so the L2 latency hides behind the current
+// chunk's arithmetic.  Accumulators pair neighbouring rows for fma.rn.f32x2:
+// every lane still computes each output with one FP32 fma per k, in k order.
+constexpr int kNKC = 16;       // k-chunk of the streamed weights
+constexpr int kNBsN = 160;     // widest product (wider dE/dG: column blocks)
+constexpr int kNColBlock = 128;
+
+// offset of quad q (rows 4q..4q+3) of feature c
+__device__ __forceinline__ int hq(int c, int q) { return c * kTM + 4 * (q ^ (c & 7)); }
+
+// acc[p][j] += A(64 x K) B(K x N) for rows 8ty+2p, 8ty+2p+1 and column tx+32j.
+// A: transposed activations AT (layout above), or with Ag != nullptr rows of
+// global memory (lda), staged chunk by chunk in As.  B: rows of ldb floats;
+// CH: a column block whose columns from ncol on are absent (read as zero).
+template <int N, bool CH>
+__device__ __forceinline__ void net_gemm(f2 (&acc)[4][(N + 31) / 32], const float* AT,
+                                         const float* __restrict__ Ag, int lda, int K,
+                                         const float* __restrict__ Bg, int ldb, int ncol, float* Bs,
+                                         float* As) {
+  constexpr int NJ = (N + 31) / 32;
+  constexpr int NV = kNKC * N / 4;  // float4 of one weight chunk
+  constexpr int PV = (NV + 255) / 256;
+  const int tid = threadIdx.x, ty = tid >> 5, tx = tid & 31;
+  float4 pb[PV];
+  float4 pa = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int p = 0; p < PV; ++p) {
+      const int i = tid + 256 * p;
+      if (NV % 256 == 0 || i < NV) {
+        const int kk = i / (N / 4), c = 4 * (i - kk * (N / 4));
+        if (!CH || c < ncol)
+          pb[p] = __ldg(reinterpret_cast<const float4*>(Bg + (size_t)(k0 + kk) * ldb + c));
+        else
+          pb[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    if (Ag) pa = __ldg(reinterpret_cast<const float4*>(Ag + (size_t)(tid >> 2) * lda + k0 + 4 * (tid & 3)));
+  };
+  auto stash = [&]() {
+#pragma unroll
+    for (int p = 0; p < PV; ++p) {
+      const int i = tid + 256 * p;
+      if (NV % 256 == 0 || i < NV) reinterpret_cast<float4*>(Bs)[i] = pb[p];
+    }
+    if (Ag) {
+      const int r = tid >> 2, k4 = 4 * (tid & 3);
+      As[hq(k4, r >> 2) + (r & 3)] = pa.x;
+      As[hq(k4 + 1, r >> 2) + (r & 3)] = pa.y;
+      As[hq(k4 + 2, r >> 2) + (r & 3)] = pa.z;
+      As[hq(k4 + 3, r >> 2) + (r & 3)] = pa.w;
+    }
+  };
+  const int nch = K / kNKC;
+  fetch(0);
+  for (int ch = 0; ch < nch; ++ch) {
+    __syncthreads();  // every warp is done with the previous chunk
+    stash();
+    __syncthreads();
+    if (ch + 1 < nch) fetch((ch + 1) * kNKC);
+    // chunk offsets are multiples of 8 features, so (c & 7) is unchanged
+    const float* Ab = Ag ? As : AT + (size_t)ch * kNKC * kTM;
+#pragma unroll 8
+    for (int kk = 0; kk < kNKC; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(Ab + hq(kk, 2 * ty));
+      const float4 a1 = *reinterpret_cast<const float4*>(Ab + hq(kk, 2 * ty + 1));
+      const f2 ap[4] = {f2_make(a0.x, a0.y), f2_make(a0.z, a0.w), f2_make(a1.x, a1.y), f2_make(a1.z, a1.w)};
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        const int col = tx + 32 * j;
+        const float b = (N % 32 == 0 || col < N) ? Bs[kk * N + col] : 0.f;
+        const f2 bb = f2_make(b, b);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) acc[p][j] = f2_fma(ap[p], bb, acc[p][j]);
+      }
+    }
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void net_zero(f2 (&acc)[4][(N + 31) / 32]) {
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int j = 0; j < (N + 31) / 32; ++j) acc[p][j] = f2_make(0.f, 0.f);
+}
+
+// the eight values of column j, rows 8ty..8ty+7
+template <int NJ>
+__device__ __forceinline__ void net_col(const f2 (&acc)[4][NJ], int j, float (&v)[8]) {
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const float2 t = f2_split(acc[p][j]);
+    v[2 * p] = t.x;
+    v[2 * p + 1] = t.y;
+  }
+}
+
+// forward epilogue: HT(col, rows) = CELU(acc + b)
+template <int N>
+__device__ __forceinline__ void net_store_celu(const f2 (&acc)[4][N / 32], const float* bias, float* HT,
+                                               float al, float inv_al) {
+  const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < N / 32; ++j) {
+    const int col = tx + 32 * j;
+    const float bb = bias[col];
+    float h[8];
+    net_col<N / 32>(acc, j, h);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) h[i] = celu_f(h[i] + bb, al, inv_al);
+    *reinterpret_cast<float4*>(HT + hq(col, 2 * ty)) = make_float4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<float4*>(HT + hq(col, 2 * ty + 1)) = make_float4(h[4], h[5], h[6], h[7]);
+  }
+}
+
+// backward epilogue: HT(col, rows) <- acc * CELU'(h), h = HT(col, rows)
+template <int N>
+__device__ __forceinline__ void net_store_bwd(const f2 (&acc)[4][N / 32], float* HT, float inv_al) {
+  const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < N / 32; ++j) {
+    const int col = tx + 32 * j;
+    float4* p0 = reinterpret_cast<float4*>(HT + hq(col, 2 * ty));
+    float4* p1 = reinterpret_cast<float4*>(HT + hq(col, 2 * ty + 1));
+    const float4 h0 = *p0, h1 = *p1;
+    const float h[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+    float g[8];
+    net_col<N / 32>(acc, j, g);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) g[i] *= dcelu_from_h(h[i], inv_al);
+    *p0 = make_float4(g[0], g[1], g[2], g[3]);
+    *p1 = make_float4(g[4], g[5], g[6], g[7]);
+  }
+}
+
+// dE/dG columns [c0, c0 + ncol) of the tile's rows (acc = 1: added to what
+// an earlier ensemble member left there)
+template <int N>
+__device__ __forceinline__ void net_store_dedg(const f2 (&acc)[4][(N + 31) / 32], float* dEdG, int D, int row0,
+                                               int c0, int ncol, int add) {
+  const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < (N + 31) / 32; ++j) {
+    const int col = tx + 32 * j;
+    if (col >= ncol) continue;
+    float v[8];
+    net_col<(N + 31) / 32>(acc, j, v);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      float* o = dEdG + (size_t)(row0 + ty * 8 + i) * D + c0 + col;
+      *o = add ? *o + v[i] : v[i];
+    }
+  }
+}
+
 // acc = 1: add E_i and dE/dG to what an earlier ensemble member left there
 template <int S>
-__global__ void __launch_bounds__(256, 1) k_mlp_f32(const EvalIO* __restrict__ io,
+__global__ void __launch_bounds__(256, 2) k_mlp_f32(const EvalIO* __restrict__ io,
                                                     DescParams P, Workspace ws, MlpF32Weights Wt, int acc) {
   constexpr int D = kNRad * S + kNAng * S * (S + 1) / 2;
-  extern __shared__ float smf[];
-  float* H1T = smf;                       // [160][kLDX]
-  float* H2T = H1T + kH1 * kLDX;          // [128][kLDX]
-  float* H3T = H2T + kH2 * kLDX;          // [96][kLDX]
-  float* Bs = H3T + kH3 * kLDX;           // [kKC][widest N of a product]
-  constexpr int kBsN = f32_bsn(D);
-  float* As = Bs + kKC * kBsN;            // [kKC][kLDX]
+  extern __shared__ float4 smf4[];
+  float* H1T = reinterpret_cast<float*>(smf4);  // [160 features][64 rows]
+  float* H2T = H1T + kH1 * kTM;                 // [128][64]
+  float* H3T = H2T + kH2 * kTM;                 // [96][64]
+  float* Bs = H3T + kH3 * kTM;                  // [kNKC][<= 160]
+  float* As = Bs + kNKC * kNBsN;                // [kNKC][64]
   const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
   const float al = P.celu_alpha, inv_al = 1.f / P.celu_alpha;
   const int rows = ws.seg[S];
@@ -151,19 +306,23 @@ __global__ void __launch_bounds__(256, 1) k_mlp_f32(const EvalIO* __restrict__ i
     int sp = pos4_species(ws.pos4[row0]);
     if (!NNP_IN(sp, P.S, ws.flags)) sp = 0;
     // ---- forward
-    float acc1[8][kH1 / 32];
-    zero_acc<kH1>(acc1);
-    gemm_tile<kH1>(acc1, nullptr, ws.G + (size_t)row0 * D, D, D, Wt.W[sp][0], Bs, As);
-    store_celu<kH1>(acc1, Wt.b[sp][0], H1T, al, inv_al);
-    float acc2[8][kH2 / 32];
-    zero_acc<kH2>(acc2);
-    gemm_tile<kH2>(acc2, H1T, nullptr, 0, kH1, Wt.W[sp][1], Bs, As);
-    store_celu<kH2>(acc2, Wt.b[sp][1], H2T, al, inv_al);
-    float acc3[8][kH3 / 32];
-    zero_acc<kH3>(acc3);
-    gemm_tile<kH3>(acc3, H2T, nullptr, 0, kH2, Wt.W[sp][2], Bs, As);
-    // layer 3 epilogue: energy and g3 = w4 * CELU'(z3), stored in H3T
     {
+      f2 a1[4][kH1 / 32];
+      net_zero<kH1>(a1);
+      net_gemm<kH1, false>(a1, nullptr, ws.G + (size_t)row0 * D, D, D, Wt.W[sp][0], kH1, kH1, Bs, As);
+      net_store_celu<kH1>(a1, Wt.b[sp][0], H1T, al, inv_al);
+    }
+    {
+      f2 a2[4][kH2 / 32];
+      net_zero<kH2>(a2);
+      net_gemm<kH2, false>(a2, H1T, nullptr, 0, kH1, Wt.W[sp][1], kH2, kH2, Bs, As);
+      net_store_celu<kH2>(a2, Wt.b[sp][1], H2T, al, inv_al);
+    }
+    {
+      f2 a3[4][kH3 / 32];
+      net_zero<kH3>(a3);
+      net_gemm<kH3, false>(a3, H2T, nullptr, 0, kH2, Wt.W[sp][2], kH3, kH3, Bs, As);
+      // layer 3 epilogue: energy and g3 = w4 * CELU'(z3), stored in H3T
       const float* w4 = Wt.W[sp][3];
       const float* b3 = Wt.b[sp][2];
       float e[8];
@@ -173,16 +332,17 @@ __global__ void __launch_bounds__(256, 1) k_mlp_f32(const EvalIO* __restrict__ i
       for (int j = 0; j < kH3 / 32; ++j) {
         const int col = tx + 32 * j;
         const float ww = w4[col], bb = b3[col];
-        float g[8];
+        float z[8], g[8];
+        net_col<kH3 / 32>(a3, j, z);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const float z = acc3[i][j] + bb;
-          const float h = celu_f(z, al, inv_al);
+          const float zz = z[i] + bb;
+          const float h = celu_f(zz, al, inv_al);
           e[i] = fmaf(h, ww, e[i]);
-          g[i] = ww * (z > 0.f ? 1.f : expf(z * inv_al));
+          g[i] = ww * (zz > 0.f ? 1.f : expf(zz * inv_al));
         }
-        *reinterpret_cast<float4*>(H3T + col * kLDX + ty * 8) = make_float4(g[0], g[1], g[2], g[3]);
-        *reinterpret_cast<float4*>(H3T + col * kLDX + ty * 8 + 4) = make_float4(g[4], g[5], g[6], g[7]);
+        *reinterpret_cast<float4*>(H3T + hq(col, 2 * ty)) = make_float4(g[0], g[1], g[2], g[3]);
+        *reinterpret_cast<float4*>(H3T + hq(col, 2 * ty + 1)) = make_float4(g[4], g[5], g[6], g[7]);
       }
 #pragma unroll
       for (int i = 0; i < 8; ++i) e[i] = warp_sum(e[i]);
@@ -210,48 +370,35 @@ __global__ void __launch_bounds__(256, 1) k_mlp_f32(const EvalIO* __restrict__ i
         todo &= ~__ballot_sync(0xffffffffu, mine);
       }
     }
-    // ---- backward
-    float accb2[8][kH2 / 32];
-    zero_acc<kH2>(accb2);
-    gemm_tile<kH2>(accb2, H3T, nullptr, 0, kH3, Wt.WT[sp][2], Bs, As);
-    store_bwd<kH2>(accb2, H2T, inv_al);
-    float accb1[8][kH1 / 32];
-    zero_acc<kH1>(accb1);
-    gemm_tile<kH1>(accb1, H2T, nullptr, 0, kH2, Wt.WT[sp][1], Bs, As);
-    store_bwd<kH1>(accb1, H1T, inv_al);
-    if (D <= kF32WholeD) {
-      float accg[8][(D + 31) / 32];
-      zero_acc<D>(accg);
-      gemm_tile<D>(accg, H1T, nullptr, 0, kH1, Wt.WT[sp][0], Bs, As);
-#pragma unroll
-      for (int j = 0; j < (D + 31) / 32; ++j) {
-        const int col = tx + 32 * j;
-        if (D % 32 != 0 && col >= D) continue;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          float* o = ws.dEdG + (size_t)(row0 + ty * 8 + i) * D + col;
-          *o = acc ? *o + accg[i][j] : accg[i][j];
-        }
-      }
+    // ---- backward (each product's first chunk barrier orders the previous
+    // epilogue's stores before their reads)
+    {
+      f2 b2[4][kH2 / 32];
+      net_zero<kH2>(b2);
+      net_gemm<kH2, false>(b2, H3T, nullptr, 0, kH3, Wt.WT[sp][2], kH2, kH2, Bs, As);
+      net_store_bwd<kH2>(b2, H2T, inv_al);
+    }
+    {
+      f2 b1[4][kH1 / 32];
+      net_zero<kH1>(b1);
+      net_gemm<kH1, false>(b1, H2T, nullptr, 0, kH2, Wt.WT[sp][1], kH1, kH1, Bs, As);
+      net_store_bwd<kH1>(b1, H1T, inv_al);
+    }
+    if (D <= kNBsN) {
+      f2 g[4][(D + 31) / 32];
+      net_zero<D>(g);
+      net_gemm<D, false>(g, H1T, nullptr, 0, kH1, Wt.WT[sp][0], D, D, Bs, As);
+      net_store_dedg<D>(g, ws.dEdG, D, row0, 0, D, acc);
     } else {
-      for (int c0 = 0; c0 < D; c0 += kF32ColBlock) {
-        const int nc = min(kF32ColBlock, D - c0);
-        float accg[8][kF32ColBlock / 32];
-        zero_acc<kF32ColBlock>(accg);
-        gemm_tile<kF32ColBlock, true>(accg, H1T, nullptr, 0, kH1, Wt.WT[sp][0] + c0, Bs, As, D, nc);
-#pragma unroll
-        for (int j = 0; j < kF32ColBlock / 32; ++j) {
-          const int col = tx + 32 * j;
-          if (col >= nc) continue;
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            float* o = ws.dEdG + (size_t)(row0 + ty * 8 + i) * D + c0 + col;
-            *o = acc ? *o + accg[i][j] : accg[i][j];
-          }
-        }
+      for (int c0 = 0; c0 < D; c0 += kNColBlock) {
+        const int nc = min(kNColBlock, D - c0);
+        f2 g[4][kNColBlock / 32];
+        net_zero<kNColBlock>(g);
+        net_gemm<kNColBlock, true>(g, H1T, nullptr, 0, kH1, Wt.WT[sp][0] + c0, D, nc, Bs, As);
+        net_store_dedg<kNColBlock>(g, ws.dEdG, D, row0, c0, nc, acc);
       }
     }
-    __syncthreads();
+    __syncthreads();  // the next tile's first stores wait for this tile's reads
   }
 }
 
@@ -566,13 +713,15 @@ void launch_fm_wgrad(int grid, cudaStream_t st, const DescParams& P, const FmJob
   k_fm_wgrad<<<grid, 256, 0, st>>>(P, jobs, njobs, G, dG, z, dz, t, p, grad);
 }
 
-size_t mlp_f32_smem(int D) {
-  return sizeof(float) * ((size_t)(kH1 + kH2 + kH3) * kLDX + (size_t)kKC * f32_bsn(D) + (size_t)kKC * kLDX);
+size_t mlp_f32_smem(int) {
+  return sizeof(float) * ((size_t)(kH1 + kH2 + kH3) * kTM + (size_t)kNKC * kNBsN + (size_t)kNKC * kTM);
 }
 
 void launch_mlp_f32(int grid, cudaStream_t st, const EvalIO* io, const DescParams& P,
                     const Workspace& ws, const MlpF32Weights& W, int acc) {
   const size_t sm = mlp_f32_smem(P.D);
+  // grid: one CTA per SM (or per tile, if fewer); two are resident per SM
+  grid *= 2;
 #define MLP(s) k_mlp_f32<s><<<grid, 256, sm, st>>>(io, P, ws, W, acc)
   switch (P.S) { NNP_SPECIES_CASES(MLP) }
 #undef MLP

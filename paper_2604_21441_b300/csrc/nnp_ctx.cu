@@ -49,9 +49,10 @@ int nnp_ctx::init_device() {
   for (int s = 0; s < P.S; ++s) lut[cfg.atomic_numbers[s]] = (signed char)s;
   CK(cudaMalloc(&d_zlut, 128));
   CK(cudaMemcpy(d_zlut, lut, 128, cudaMemcpyHostToDevice));
-  // weights: W1 (D x 160), W2, W3, W4, b1..b4, W1T, W2T, W3T per species
+  // weights: W1 (D x 160), W2, W3, W4, b1..b4, W1T, W2T, W3T per species; b4
+  // takes four floats so that every array starts on 16 bytes (float4 loads)
   const size_t D = P.D;
-  wf32_stride = D * kH1 + kH1 * kH2 + kH2 * kH3 + kH3 + kH1 + kH2 + kH3 + 1 + kH1 * D + kH2 * kH1 +
+  wf32_stride = D * kH1 + kH1 * kH2 + kH2 * kH3 + kH3 + kH1 + kH2 + kH3 + 4 + kH1 * D + kH2 * kH1 +
                 kH3 * kH2;
   wf32_stride = (wf32_stride + 63) / 64 * 64;
   // one table per ensemble member (member m, species s at (m S + s) strides),
@@ -72,7 +73,7 @@ int nnp_ctx::init_device() {
       t.b[s][0] = p; p += kH1;
       t.b[s][1] = p; p += kH2;
       t.b[s][2] = p; p += kH3;
-      t.b[s][3] = p; p += 1;
+      t.b[s][3] = p; p += 4;
       t.WT[s][0] = p; p += kH1 * D;
       t.WT[s][1] = p; p += kH2 * kH1;
       t.WT[s][2] = p; p += kH3 * kH2;
@@ -162,6 +163,7 @@ int nnp_ctx::set_weights(int m, int s, const float* const W[4], const float* con
   }
   put(w[0]); put(w[1]); put(w[2]); put(w4);
   put(bb[0]); put(bb[1]); put(bb[2]); put(b4);
+  p += 3;  // b4 padded to four floats
   for (int l = 0; l < 3; ++l) {  // transposed copies (fan_out x fan_in)
     for (int o = 0; o < fout[l]; ++o)
       for (int i = 0; i < fin[l]; ++i) p[(size_t)o * fin[l] + i] = w[l][(size_t)i * fout[l] + o];
