@@ -125,24 +125,23 @@ __device__ __forceinline__ void store_bwd(const float (&acc)[8][(N + 31) / 32], 
 
 // ---- the evaluation kernel (k_mlp_f32) ----------------------------------
 // Two CTAs of 256 threads per SM.  A 64-row tile's activations stay in shared
-// memory transposed and unpadded: element (feature c, row r) sits at
-// c*64 + 4*((r>>2) ^ (c&7)) + (r&3).  A thread's eight rows at one feature are
-// then two float4 (the same address across the warp, a broadcast), and the
-// float4 stores of an epilogue from eight consecutive features land on all 32
-// banks.  Weights stream through one 16-row chunk that each thread fetches
-// into registers a chunk ahead, so the L2 latency hides behind the current
-// chunk's arithmetic.  Accumulators pair neighbouring rows for fma.rn.f32x2:
-// every lane still computes each output with one FP32 fma per k, in k order.
+// memory transposed with the padded leading dimension kLDX: a thread's eight
+// rows at one feature are two float4 at fixed offsets from the feature's row
+// (the same address across the warp, a broadcast), and the float4 stores of an
+// epilogue from eight consecutive features land on all 32 banks.  Weights
+// stream through one 16-row chunk that each thread fetches into registers a
+// chunk ahead, so the L2 latency hides behind the current chunk's arithmetic.
+// Accumulators pair neighbouring rows for fma.rn.f32x2: every lane still
+// computes each output with one FP32 fma per k, in k order.  Shared memory:
+// H1T | H2T | H3T | Bs = 114,688 bytes; the first layer's staged input chunk
+// lives in H2T, which is free until the second layer's epilogue.
 constexpr int kNKC = 16;       // k-chunk of the streamed weights
 constexpr int kNBsN = 160;     // widest product (wider dE/dG: column blocks)
 constexpr int kNColBlock = 128;
 
-// offset of quad q (rows 4q..4q+3) of feature c
-__device__ __forceinline__ int hq(int c, int q) { return c * kTM + 4 * (q ^ (c & 7)); }
-
 // acc[p][j] += A(64 x K) B(K x N) for rows 8ty+2p, 8ty+2p+1 and column tx+32j.
-// A: transposed activations AT (layout above), or with Ag != nullptr rows of
-// global memory (lda), staged chunk by chunk in As.  B: rows of ldb floats;
+// A: transposed activations AT[k][kLDX], or with Ag != nullptr rows of global
+// memory (lda), staged chunk by chunk in As[kNKC][kLDX].  B: rows of ldb floats;
 // CH: a column block whose columns from ncol on are absent (read as zero).
 template <int N, bool CH>
 __device__ __forceinline__ void net_gemm(f2 (&acc)[4][(N + 31) / 32], const float* AT,
@@ -177,10 +176,10 @@ __device__ __forceinline__ void net_gemm(f2 (&acc)[4][(N + 31) / 32], const floa
     }
     if (Ag) {
       const int r = tid >> 2, k4 = 4 * (tid & 3);
-      As[hq(k4, r >> 2) + (r & 3)] = pa.x;
-      As[hq(k4 + 1, r >> 2) + (r & 3)] = pa.y;
-      As[hq(k4 + 2, r >> 2) + (r & 3)] = pa.z;
-      As[hq(k4 + 3, r >> 2) + (r & 3)] = pa.w;
+      As[k4 * kLDX + r] = pa.x;
+      As[(k4 + 1) * kLDX + r] = pa.y;
+      As[(k4 + 2) * kLDX + r] = pa.z;
+      As[(k4 + 3) * kLDX + r] = pa.w;
     }
   };
   const int nch = K / kNKC;
@@ -190,12 +189,11 @@ __device__ __forceinline__ void net_gemm(f2 (&acc)[4][(N + 31) / 32], const floa
     stash();
     __syncthreads();
     if (ch + 1 < nch) fetch((ch + 1) * kNKC);
-    // chunk offsets are multiples of 8 features, so (c & 7) is unchanged
-    const float* Ab = Ag ? As : AT + (size_t)ch * kNKC * kTM;
-#pragma unroll 8
+    const float* Ab = (Ag ? As : AT + (size_t)ch * kNKC * kLDX) + ty * 8;
+#pragma unroll
     for (int kk = 0; kk < kNKC; ++kk) {
-      const float4 a0 = *reinterpret_cast<const float4*>(Ab + hq(kk, 2 * ty));
-      const float4 a1 = *reinterpret_cast<const float4*>(Ab + hq(kk, 2 * ty + 1));
+      const float4 a0 = *reinterpret_cast<const float4*>(Ab + kk * kLDX);
+      const float4 a1 = *reinterpret_cast<const float4*>(Ab + kk * kLDX + 4);
       const f2 ap[4] = {f2_make(a0.x, a0.y), f2_make(a0.z, a0.w), f2_make(a1.x, a1.y), f2_make(a1.z, a1.w)};
 #pragma unroll
       for (int j = 0; j < NJ; ++j) {
@@ -241,8 +239,8 @@ __device__ __forceinline__ void net_store_celu(const f2 (&acc)[4][N / 32], const
     net_col<N / 32>(acc, j, h);
 #pragma unroll
     for (int i = 0; i < 8; ++i) h[i] = celu_f(h[i] + bb, al, inv_al);
-    *reinterpret_cast<float4*>(HT + hq(col, 2 * ty)) = make_float4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<float4*>(HT + hq(col, 2 * ty + 1)) = make_float4(h[4], h[5], h[6], h[7]);
+    *reinterpret_cast<float4*>(HT + col * kLDX + ty * 8) = make_float4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<float4*>(HT + col * kLDX + ty * 8 + 4) = make_float4(h[4], h[5], h[6], h[7]);
   }
 }
 
@@ -253,8 +251,8 @@ __device__ __forceinline__ void net_store_bwd(const f2 (&acc)[4][N / 32], float*
 #pragma unroll
   for (int j = 0; j < N / 32; ++j) {
     const int col = tx + 32 * j;
-    float4* p0 = reinterpret_cast<float4*>(HT + hq(col, 2 * ty));
-    float4* p1 = reinterpret_cast<float4*>(HT + hq(col, 2 * ty + 1));
+    float4* p0 = reinterpret_cast<float4*>(HT + col * kLDX + ty * 8);
+    float4* p1 = p0 + 1;
     const float4 h0 = *p0, h1 = *p1;
     const float h[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
     float g[8];
@@ -292,11 +290,11 @@ __global__ void __launch_bounds__(256, 2) k_mlp_f32(const EvalIO* __restrict__ i
                                                     DescParams P, Workspace ws, MlpF32Weights Wt, int acc) {
   constexpr int D = kNRad * S + kNAng * S * (S + 1) / 2;
   extern __shared__ float4 smf4[];
-  float* H1T = reinterpret_cast<float*>(smf4);  // [160 features][64 rows]
-  float* H2T = H1T + kH1 * kTM;                 // [128][64]
-  float* H3T = H2T + kH2 * kTM;                 // [96][64]
-  float* Bs = H3T + kH3 * kTM;                  // [kNKC][<= 160]
-  float* As = Bs + kNKC * kNBsN;                // [kNKC][64]
+  float* H1T = reinterpret_cast<float*>(smf4);  // [160 features][kLDX]
+  float* H2T = H1T + kH1 * kLDX;                // [128][kLDX]
+  float* H3T = H2T + kH2 * kLDX;                // [96][kLDX]
+  float* Bs = H3T + kH3 * kLDX;                 // [kNKC][<= 160]
+  float* As = H2T;                              // [kNKC][kLDX], first layer only
   const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
   const float al = P.celu_alpha, inv_al = 1.f / P.celu_alpha;
   const int rows = ws.seg[S];
@@ -341,8 +339,8 @@ __global__ void __launch_bounds__(256, 2) k_mlp_f32(const EvalIO* __restrict__ i
           e[i] = fmaf(h, ww, e[i]);
           g[i] = ww * (zz > 0.f ? 1.f : expf(zz * inv_al));
         }
-        *reinterpret_cast<float4*>(H3T + hq(col, 2 * ty)) = make_float4(g[0], g[1], g[2], g[3]);
-        *reinterpret_cast<float4*>(H3T + hq(col, 2 * ty + 1)) = make_float4(g[4], g[5], g[6], g[7]);
+        *reinterpret_cast<float4*>(H3T + col * kLDX + ty * 8) = make_float4(g[0], g[1], g[2], g[3]);
+        *reinterpret_cast<float4*>(H3T + col * kLDX + ty * 8 + 4) = make_float4(g[4], g[5], g[6], g[7]);
       }
 #pragma unroll
       for (int i = 0; i < 8; ++i) e[i] = warp_sum(e[i]);
@@ -714,7 +712,7 @@ void launch_fm_wgrad(int grid, cudaStream_t st, const DescParams& P, const FmJob
 }
 
 size_t mlp_f32_smem(int) {
-  return sizeof(float) * ((size_t)(kH1 + kH2 + kH3) * kTM + (size_t)kNKC * kNBsN + (size_t)kNKC * kTM);
+  return sizeof(float) * ((size_t)(kH1 + kH2 + kH3) * kLDX + (size_t)kNKC * kNBsN);
 }
 
 void launch_mlp_f32(int grid, cudaStream_t st, const EvalIO* io, const DescParams& P,
