@@ -139,57 +139,78 @@ constexpr int kNKC = 16;       // k-chunk of the streamed weights
 constexpr int kNBsN = 160;     // widest product (wider dE/dG: column blocks)
 constexpr int kNColBlock = 128;
 
+// One weight chunk (and, for the first layer, one staged input chunk) in
+// flight in registers: kNKC x N floats of B as float4, at most three per thread.
+struct NetPf {
+  float4 b[3];
+  float4 a;
+};
+
+// Fetch chunk k0 of a product with N columns: B rows of ldb floats (CH: a
+// column block whose columns from ncol on are absent, read as zero); STAGED:
+// also the 64 x kNKC input chunk from rows of global memory (lda).
+template <int N, bool CH, bool STAGED>
+__device__ __forceinline__ void net_fetch(NetPf& pf, const float* __restrict__ Bg, int ldb, int ncol,
+                                          const float* __restrict__ Ag, int lda, int k0) {
+  constexpr int NV = kNKC * N / 4;
+  constexpr int PV = (NV + 255) / 256;
+  static_assert(PV <= 3, "weight chunk too wide");
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int p = 0; p < PV; ++p) {
+    const int i = tid + 256 * p;
+    if (NV % 256 == 0 || i < NV) {
+      const int kk = i / (N / 4), c = 4 * (i - kk * (N / 4));
+      if (!CH || c < ncol)
+        pf.b[p] = __ldg(reinterpret_cast<const float4*>(Bg + (size_t)(k0 + kk) * ldb + c));
+      else
+        pf.b[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  if (STAGED) pf.a = __ldg(reinterpret_cast<const float4*>(Ag + (size_t)(tid >> 2) * lda + k0 + 4 * (tid & 3)));
+}
+
+template <int N, bool STAGED>
+__device__ __forceinline__ void net_stash(const NetPf& pf, float* Bs, float* As) {
+  constexpr int NV = kNKC * N / 4;
+  constexpr int PV = (NV + 255) / 256;
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int p = 0; p < PV; ++p) {
+    const int i = tid + 256 * p;
+    if (NV % 256 == 0 || i < NV) reinterpret_cast<float4*>(Bs)[i] = pf.b[p];
+  }
+  if (STAGED) {
+    const int r = tid >> 2, k4 = 4 * (tid & 3);
+    As[k4 * kLDX + r] = pf.a.x;
+    As[(k4 + 1) * kLDX + r] = pf.a.y;
+    As[(k4 + 2) * kLDX + r] = pf.a.z;
+    As[(k4 + 3) * kLDX + r] = pf.a.w;
+  }
+}
+
 // acc[p][j] += A(64 x K) B(K x N) for rows 8ty+2p, 8ty+2p+1 and column tx+32j.
-// A: transposed activations AT[k][kLDX], or with Ag != nullptr rows of global
-// memory (lda), staged chunk by chunk in As[kNKC][kLDX].  B: rows of ldb floats;
-// CH: a column block whose columns from ncol on are absent (read as zero).
-template <int N, bool CH>
+// A: transposed activations AT[k][kLDX], or (STAGED) rows of global memory
+// (lda) staged chunk by chunk in As[kNKC][kLDX].  pf holds chunk 0 on entry
+// (fetched by the caller or by the previous product); during the last chunk
+// next(pf) fetches the following product's chunk 0.
+template <int N, bool CH, bool STAGED, class Next>
 __device__ __forceinline__ void net_gemm(f2 (&acc)[4][(N + 31) / 32], const float* AT,
                                          const float* __restrict__ Ag, int lda, int K,
                                          const float* __restrict__ Bg, int ldb, int ncol, float* Bs,
-                                         float* As) {
+                                         float* As, NetPf& pf, Next next) {
   constexpr int NJ = (N + 31) / 32;
-  constexpr int NV = kNKC * N / 4;  // float4 of one weight chunk
-  constexpr int PV = (NV + 255) / 256;
   const int tid = threadIdx.x, ty = tid >> 5, tx = tid & 31;
-  float4 pb[PV];
-  float4 pa = make_float4(0.f, 0.f, 0.f, 0.f);
-  auto fetch = [&](int k0) {
-#pragma unroll
-    for (int p = 0; p < PV; ++p) {
-      const int i = tid + 256 * p;
-      if (NV % 256 == 0 || i < NV) {
-        const int kk = i / (N / 4), c = 4 * (i - kk * (N / 4));
-        if (!CH || c < ncol)
-          pb[p] = __ldg(reinterpret_cast<const float4*>(Bg + (size_t)(k0 + kk) * ldb + c));
-        else
-          pb[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-    }
-    if (Ag) pa = __ldg(reinterpret_cast<const float4*>(Ag + (size_t)(tid >> 2) * lda + k0 + 4 * (tid & 3)));
-  };
-  auto stash = [&]() {
-#pragma unroll
-    for (int p = 0; p < PV; ++p) {
-      const int i = tid + 256 * p;
-      if (NV % 256 == 0 || i < NV) reinterpret_cast<float4*>(Bs)[i] = pb[p];
-    }
-    if (Ag) {
-      const int r = tid >> 2, k4 = 4 * (tid & 3);
-      As[k4 * kLDX + r] = pa.x;
-      As[(k4 + 1) * kLDX + r] = pa.y;
-      As[(k4 + 2) * kLDX + r] = pa.z;
-      As[(k4 + 3) * kLDX + r] = pa.w;
-    }
-  };
   const int nch = K / kNKC;
-  fetch(0);
   for (int ch = 0; ch < nch; ++ch) {
     __syncthreads();  // every warp is done with the previous chunk
-    stash();
+    net_stash<N, STAGED>(pf, Bs, As);
     __syncthreads();
-    if (ch + 1 < nch) fetch((ch + 1) * kNKC);
-    const float* Ab = (Ag ? As : AT + (size_t)ch * kNKC * kLDX) + ty * 8;
+    if (ch + 1 < nch)
+      net_fetch<N, CH, STAGED>(pf, Bg, ldb, ncol, Ag, lda, (ch + 1) * kNKC);
+    else
+      next(pf);
+    const float* Ab = (STAGED ? As : AT + (size_t)ch * kNKC * kLDX) + ty * 8;
 #pragma unroll
     for (int kk = 0; kk < kNKC; ++kk) {
       const float4 a0 = *reinterpret_cast<const float4*>(Ab + kk * kLDX);
@@ -299,27 +320,46 @@ __global__ void __launch_bounds__(256, 2) k_mlp_f32(const EvalIO* __restrict__ i
   const float al = P.celu_alpha, inv_al = 1.f / P.celu_alpha;
   const int rows = ws.seg[S];
   const int ntiles = rows / kTM;
+  auto tile_species = [&](int t) {
+    int s = pos4_species(ws.pos4[t * kTM]);
+    return NNP_IN(s, P.S, ws.flags) ? s : 0;
+  };
+  // every product's first chunk is fetched during the previous product's
+  // last one (the first layer of the next tile during the last dE/dG block)
+  NetPf pf;
+  int sp = 0;
+  if ((int)blockIdx.x < ntiles) {
+    sp = tile_species(blockIdx.x);
+    net_fetch<kH1, false, true>(pf, Wt.W[sp][0], kH1, kH1, ws.G + (size_t)blockIdx.x * kTM * D, D, 0);
+  }
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int row0 = tile * kTM;
-    int sp = pos4_species(ws.pos4[row0]);
-    if (!NNP_IN(sp, P.S, ws.flags)) sp = 0;
+    const int ntile = tile + gridDim.x;
+    const int sp_next = ntile < ntiles ? tile_species(ntile) : 0;
+    auto next_tile = [&](NetPf& q) {
+      if (ntile < ntiles)
+        net_fetch<kH1, false, true>(q, Wt.W[sp_next][0], kH1, kH1, ws.G + (size_t)ntile * kTM * D, D, 0);
+    };
     // ---- forward
     {
       f2 a1[4][kH1 / 32];
       net_zero<kH1>(a1);
-      net_gemm<kH1, false>(a1, nullptr, ws.G + (size_t)row0 * D, D, D, Wt.W[sp][0], kH1, kH1, Bs, As);
+      net_gemm<kH1, false, true>(a1, nullptr, ws.G + (size_t)row0 * D, D, D, Wt.W[sp][0], kH1, kH1, Bs, As, pf,
+                                 [&](NetPf& q) { net_fetch<kH2, false, false>(q, Wt.W[sp][1], kH2, kH2, nullptr, 0, 0); });
       net_store_celu<kH1>(a1, Wt.b[sp][0], H1T, al, inv_al);
     }
     {
       f2 a2[4][kH2 / 32];
       net_zero<kH2>(a2);
-      net_gemm<kH2, false>(a2, H1T, nullptr, 0, kH1, Wt.W[sp][1], kH2, kH2, Bs, As);
+      net_gemm<kH2, false, false>(a2, H1T, nullptr, 0, kH1, Wt.W[sp][1], kH2, kH2, Bs, As, pf,
+                                  [&](NetPf& q) { net_fetch<kH3, false, false>(q, Wt.W[sp][2], kH3, kH3, nullptr, 0, 0); });
       net_store_celu<kH2>(a2, Wt.b[sp][1], H2T, al, inv_al);
     }
     {
       f2 a3[4][kH3 / 32];
       net_zero<kH3>(a3);
-      net_gemm<kH3, false>(a3, H2T, nullptr, 0, kH2, Wt.W[sp][2], kH3, kH3, Bs, As);
+      net_gemm<kH3, false, false>(a3, H2T, nullptr, 0, kH2, Wt.W[sp][2], kH3, kH3, Bs, As, pf,
+                                  [&](NetPf& q) { net_fetch<kH2, false, false>(q, Wt.WT[sp][2], kH2, kH2, nullptr, 0, 0); });
       // layer 3 epilogue: energy and g3 = w4 * CELU'(z3), stored in H3T
       const float* w4 = Wt.W[sp][3];
       const float* b3 = Wt.b[sp][2];
@@ -373,30 +413,45 @@ __global__ void __launch_bounds__(256, 2) k_mlp_f32(const EvalIO* __restrict__ i
     {
       f2 b2[4][kH2 / 32];
       net_zero<kH2>(b2);
-      net_gemm<kH2, false>(b2, H3T, nullptr, 0, kH3, Wt.WT[sp][2], kH2, kH2, Bs, As);
+      net_gemm<kH2, false, false>(b2, H3T, nullptr, 0, kH3, Wt.WT[sp][2], kH2, kH2, Bs, As, pf,
+                                  [&](NetPf& q) { net_fetch<kH1, false, false>(q, Wt.WT[sp][1], kH1, kH1, nullptr, 0, 0); });
       net_store_bwd<kH2>(b2, H2T, inv_al);
     }
     {
       f2 b1[4][kH1 / 32];
       net_zero<kH1>(b1);
-      net_gemm<kH1, false>(b1, H2T, nullptr, 0, kH2, Wt.WT[sp][1], kH1, kH1, Bs, As);
+      net_gemm<kH1, false, false>(b1, H2T, nullptr, 0, kH2, Wt.WT[sp][1], kH1, kH1, Bs, As, pf, [&](NetPf& q) {
+        if constexpr (D <= kNBsN)
+          net_fetch<D, false, false>(q, Wt.WT[sp][0], D, D, nullptr, 0, 0);
+        else
+          net_fetch<kNColBlock, true, false>(q, Wt.WT[sp][0], D, min(kNColBlock, D), nullptr, 0, 0);
+      });
       net_store_bwd<kH1>(b1, H1T, inv_al);
     }
-    if (D <= kNBsN) {
+    if constexpr (D <= kNBsN) {
       f2 g[4][(D + 31) / 32];
       net_zero<D>(g);
-      net_gemm<D, false>(g, H1T, nullptr, 0, kH1, Wt.WT[sp][0], D, D, Bs, As);
+      net_gemm<D, false, false>(g, H1T, nullptr, 0, kH1, Wt.WT[sp][0], D, D, Bs, As, pf, next_tile);
       net_store_dedg<D>(g, ws.dEdG, D, row0, 0, D, acc);
     } else {
       for (int c0 = 0; c0 < D; c0 += kNColBlock) {
         const int nc = min(kNColBlock, D - c0);
         f2 g[4][kNColBlock / 32];
         net_zero<kNColBlock>(g);
-        net_gemm<kNColBlock, true>(g, H1T, nullptr, 0, kH1, Wt.WT[sp][0] + c0, D, nc, Bs, As);
+        const int c1 = c0 + kNColBlock;
+        net_gemm<kNColBlock, true, false>(g, H1T, nullptr, 0, kH1, Wt.WT[sp][0] + c0, D, nc, Bs, As, pf,
+                                          [&](NetPf& q) {
+                                            if (c1 < D)
+                                              net_fetch<kNColBlock, true, false>(q, Wt.WT[sp][0] + c1, D,
+                                                                                 min(kNColBlock, D - c1),
+                                                                                 nullptr, 0, 0);
+                                            else
+                                              next_tile(q);
+                                          });
         net_store_dedg<kNColBlock>(g, ws.dEdG, D, row0, c0, nc, acc);
       }
     }
-    __syncthreads();  // the next tile's first stores wait for this tile's reads
+    sp = sp_next;
   }
 }
 
