@@ -2,7 +2,8 @@
 set of the ANI-2x model), and of the wide-descriptor tensor-core network.
 
 * a small seven-element box and the full 6,047-atom workload against the FP64
-  oracle within the FP32 bounds;
+  oracle within the FP32 bounds, and small boxes of one, three and five
+  elements (the FP32 network's other product shapes);
 * water through a seven-species context equals water through a two-species
   context with the mapped first-layer rows (the absent species' blocks are
   zero);
@@ -138,6 +139,28 @@ def test_seven_species_ensemble_batch_pairs(P, oracle_mod):
     Er, Eir, Fr = oracle_mod.ensemble_energy_forces(models, s.pos, p.species_of(s.Z), s.box)
     assert energy_error(Ep, Er, Eir) <= E_REL_TOL
     assert np.abs(Fp - Fr).max() <= F_ABS_TOL
+
+
+@pytest.mark.parametrize("Zs", [(6,), (1, 6, 8), (1, 6, 7, 8, 9)])
+def test_fp32_species_counts(P, oracle_mod, Zs):
+    """The FP32 network's shapes besides two, four and seven species: D = 48
+    (one product with masked columns), 240 and 560 (dE/dG in 128-column
+    blocks with a ragged last block of 112 and 48 columns)."""
+    S = len(Zs)
+    D = 16 * S + 32 * S * (S + 1) // 2
+    s = synth.hcno_box(741 + S, L=16.0, n_cluster_atoms=160, max_waters=0 if S == 1 else 60,
+                       elements=np.array(Zs, dtype=np.int32), probs=np.full(S, 1.0 / S))
+    w = weights32(S, D, 742 + S, 743 + S)
+    pot = _pot(P, w, Zs=Zs)
+    E, F = pot.eval(s.pos, s.Z, box9(s.box))
+    p = oracle_mod.Params(atomic_numbers=Zs)
+    Er, Eir, Fr, _ = oracle_mod.energy_forces(oracle_mod.Model(p, w), s.pos, p.species_of(s.Z), s.box)
+    print(f"fp32 {S} species (D = {D}), {s.n} atoms: rel E err {energy_error(E, Er, Eir):.2e},"
+          f" max|dF| {np.abs(F - Fr).max():.3e}")
+    assert energy_error(E, Er, Eir) <= E_REL_TOL
+    assert np.abs(F - Fr).max() <= F_ABS_TOL
+    Ei = pot.atom_energies(s.n)
+    assert np.abs(Ei - Eir).max() <= 1e-5 * max(1.0, np.abs(Eir).max())
 
 
 @pytest.mark.parametrize("Zs", [(1, 6, 8), (1, 6, 7, 8), Z7])
