@@ -9,73 +9,14 @@
 //
 // The evaluation kernel runs two CTAs of 256 threads per SM, one 64-row tile
 // (one species) at a time; its layout is described above k_mlp_f32.  The
-// force-matching kernels share the simpler helpers below: one CTA per SM,
-// activations transposed with a padded leading dimension, thread (warp ty,
-// lane tx) owning rows 8ty..8ty+7 and columns tx + 32j.
+// force-matching passes (one CTA per SM) use the same layout, weight-chunk
+// pipeline and thread mapping with two products per weight chunk.
 #include "nnp_internal.cuh"
 
 namespace nnp {
 
 constexpr int kTM = 64;          // rows per tile
 constexpr int kLDX = kTM + 4;    // padded leading dim of transposed activations
-constexpr int kKC = 32;          // streamed k-chunk
-
-// acc[8][NJ] += A(64 x K) * B(K x N).  A is either transposed in shared
-// memory (AT[k][kLDX]) or, if Ag != nullptr, rows of global memory (lda).
-// CH: B is a column block of a wider matrix (leading dimension ldb) whose
-// columns from ncol on are absent (read as zero).
-template <int N, bool CH = false>
-__device__ __forceinline__ void gemm_tile(float (&acc)[8][(N + 31) / 32], const float* AT,
-                                          const float* __restrict__ Ag, int lda, int K,
-                                          const float* __restrict__ Bg, float* Bs, float* As,
-                                          int ldb = N, int ncol = N) {
-  constexpr int NJ = (N + 31) / 32;
-  const int tid = threadIdx.x, ty = tid >> 5, tx = tid & 31;
-  for (int k0 = 0; k0 < K; k0 += kKC) {
-    const int kc = min(kKC, K - k0);
-    __syncthreads();
-    if (CH) {
-      for (int i = tid; i < kc * N; i += 256) {
-        const int kk = i / N, c = i - kk * N;
-        Bs[i] = c < ncol ? Bg[(size_t)(k0 + kk) * ldb + c] : 0.f;
-      }
-    } else {
-      for (int i = tid; i < kc * N; i += 256) Bs[i] = Bg[(size_t)k0 * N + i];
-    }
-    if (Ag) {
-      for (int i = tid; i < kTM * kc; i += 256) {
-        const int r = i / kc, kk = i - r * kc;
-        As[kk * kLDX + r] = Ag[(size_t)r * lda + k0 + kk];
-      }
-    }
-    __syncthreads();
-    const float* Ab = Ag ? As : AT + (size_t)k0 * kLDX;
-#pragma unroll 4
-    for (int kk = 0; kk < kc; ++kk) {
-      const float4 a0 = *reinterpret_cast<const float4*>(Ab + kk * kLDX + ty * 8);
-      const float4 a1 = *reinterpret_cast<const float4*>(Ab + kk * kLDX + ty * 8 + 4);
-      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      float b[NJ];
-#pragma unroll
-      for (int j = 0; j < NJ; ++j) {
-        const int col = tx + 32 * j;
-        b[j] = (N % 32 == 0 || col < N) ? Bs[kk * N + col] : 0.f;
-      }
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-    }
-  }
-}
-
-template <int N>
-__device__ __forceinline__ void zero_acc(float (&acc)[8][(N + 31) / 32]) {
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int j = 0; j < (N + 31) / 32; ++j) acc[i][j] = 0.f;
-}
 
 __device__ __forceinline__ float celu_f(float z, float al, float inv_al) {
   return z > 0.f ? z : al * (expf(z * inv_al) - 1.f);
@@ -83,44 +24,6 @@ __device__ __forceinline__ float celu_f(float z, float al, float inv_al) {
 // CELU'(z) from h = CELU(z): 1 for h > 0, h/alpha + 1 otherwise
 __device__ __forceinline__ float dcelu_from_h(float h, float inv_al) {
   return h > 0.f ? 1.f : fmaf(h, inv_al, 1.f);
-}
-
-// Forward layer epilogue: H^T[col][row] = CELU(acc + b)
-template <int N>
-__device__ __forceinline__ void store_celu(const float (&acc)[8][(N + 31) / 32], const float* bias,
-                                           float* HT, float al, float inv_al) {
-  const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
-#pragma unroll
-  for (int j = 0; j < (N + 31) / 32; ++j) {
-    const int col = tx + 32 * j;
-    if (N % 32 != 0 && col >= N) continue;
-    const float bb = bias[col];
-    float h[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) h[i] = celu_f(acc[i][j] + bb, al, inv_al);
-    *reinterpret_cast<float4*>(HT + col * kLDX + ty * 8) = make_float4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<float4*>(HT + col * kLDX + ty * 8 + 4) = make_float4(h[4], h[5], h[6], h[7]);
-  }
-}
-
-// Backward epilogue: HT[col][row] <- acc * CELU'(h) where h = HT[col][row]
-template <int N>
-__device__ __forceinline__ void store_bwd(const float (&acc)[8][(N + 31) / 32], float* HT,
-                                          float inv_al) {
-  const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
-#pragma unroll
-  for (int j = 0; j < (N + 31) / 32; ++j) {
-    const int col = tx + 32 * j;
-    float4* p0 = reinterpret_cast<float4*>(HT + col * kLDX + ty * 8);
-    float4* p1 = p0 + 1;
-    const float4 h0 = *p0, h1 = *p1;
-    const float h[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
-    float g[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) g[i] = acc[i][j] * dcelu_from_h(h[i], inv_al);
-    *p0 = make_float4(g[0], g[1], g[2], g[3]);
-    *p1 = make_float4(g[4], g[5], g[6], g[7]);
-  }
 }
 
 // ---- the evaluation kernel (k_mlp_f32) ----------------------------------
@@ -468,6 +371,75 @@ __global__ void __launch_bounds__(256, 2) k_mlp_f32(const EvalIO* __restrict__ i
 //   dL/dw_4 = -sum_i dh_3,  dL/db_4 = 0.
 // Per-row buffers [rows][384]: z1 | z2 | z3 (160 | 128 | 96) and the same for dz, t, p.
 
+// Two products with the same B for the force-matching passes (primal and
+// tangent, or the two adjoints): acc += A B and acc2 += A2 B, one weight
+// chunk stream for both, fetched a chunk ahead, row-paired f32x2 FMAs (each
+// output still one FP32 fma per k, in k order).  A, A2: transposed in shared
+// memory (AT, AT2 [k][kLDX]) or (STAGED) rows of global memory (Ag, Ag2, lda)
+// staged in As, As2 [kNKC][kLDX].  B: rows of N floats.
+template <int N, bool STAGED>
+__device__ __forceinline__ void fm_gemm2(f2 (&acc)[4][N / 32], f2 (&acc2)[4][N / 32], const float* AT,
+                                         const float* AT2, const float* __restrict__ Ag,
+                                         const float* __restrict__ Ag2, int lda, int K,
+                                         const float* __restrict__ Bg, float* Bs, float* As, float* As2) {
+  constexpr int NJ = N / 32;
+  const int tid = threadIdx.x, ty = tid >> 5, tx = tid & 31;
+  NetPf pf;
+  float4 pa2 = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto fetch = [&](int k0) {
+    net_fetch<N, false, STAGED>(pf, Bg, N, N, Ag, lda, k0);
+    if (STAGED) pa2 = __ldg(reinterpret_cast<const float4*>(Ag2 + (size_t)(tid >> 2) * lda + k0 + 4 * (tid & 3)));
+  };
+  const int nch = K / kNKC;
+  fetch(0);
+  for (int ch = 0; ch < nch; ++ch) {
+    __syncthreads();
+    net_stash<N, STAGED>(pf, Bs, As);
+    if (STAGED) {
+      const int r = tid >> 2, k4 = 4 * (tid & 3);
+      As2[k4 * kLDX + r] = pa2.x;
+      As2[(k4 + 1) * kLDX + r] = pa2.y;
+      As2[(k4 + 2) * kLDX + r] = pa2.z;
+      As2[(k4 + 3) * kLDX + r] = pa2.w;
+    }
+    __syncthreads();
+    if (ch + 1 < nch) fetch((ch + 1) * kNKC);
+    const float* Ab = (STAGED ? As : AT + (size_t)ch * kNKC * kLDX) + ty * 8;
+    const float* Ab2 = (STAGED ? As2 : AT2 + (size_t)ch * kNKC * kLDX) + ty * 8;
+#pragma unroll
+    for (int kk = 0; kk < kNKC; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(Ab + kk * kLDX);
+      const float4 a1 = *reinterpret_cast<const float4*>(Ab + kk * kLDX + 4);
+      const float4 c0 = *reinterpret_cast<const float4*>(Ab2 + kk * kLDX);
+      const float4 c1 = *reinterpret_cast<const float4*>(Ab2 + kk * kLDX + 4);
+      const f2 ap[4] = {f2_make(a0.x, a0.y), f2_make(a0.z, a0.w), f2_make(a1.x, a1.y), f2_make(a1.z, a1.w)};
+      const f2 cp[4] = {f2_make(c0.x, c0.y), f2_make(c0.z, c0.w), f2_make(c1.x, c1.y), f2_make(c1.z, c1.w)};
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        const float b = Bs[kk * N + tx + 32 * j];
+        const f2 bb = f2_make(b, b);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          acc[p][j] = f2_fma(ap[p], bb, acc[p][j]);
+          acc2[p][j] = f2_fma(cp[p], bb, acc2[p][j]);
+        }
+      }
+    }
+  }
+}
+
+// f2 accumulators (row pairs) -> acc[row][column] for the epilogues
+template <int NJ>
+__device__ __forceinline__ void fm_rows(const f2 (&a)[4][NJ], float (&out)[8][NJ]) {
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    float v[8];
+    net_col<NJ>(a, j, v);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) out[i][j] = v[i];
+  }
+}
+
 constexpr int kFmW = kH1 + kH2 + kH3;  // 384
 __host__ __device__ constexpr int fm_off(int layer0) {  // z1 | z2 | z3 column offsets
   return layer0 == 0 ? 0 : (layer0 == 1 ? kH1 : kH1 + kH2);
@@ -516,8 +488,9 @@ __global__ void __launch_bounds__(256, 1) k_fm_fwd(DescParams P, Workspace ws, M
   float* DH1T = H1T + kH1 * kLDX;
   float* H2T = DH1T + kH1 * kLDX;
   float* DH2T = H2T + kH2 * kLDX;
-  float* Bs = DH2T + kH2 * kLDX;  // [kKC][160]: every product here has N <= 160
-  float* As = Bs + kKC * kH1;
+  float* Bs = DH2T + kH2 * kLDX;  // [kNKC][160]: every product here has N <= 160
+  float* As = Bs + kNKC * kH1;    // [kNKC][kLDX] each
+  float* As2 = As + kNKC * kLDX;
   const float al = P.celu_alpha, inv_al = 1.f / P.celu_alpha;
   const int ntiles = ws.seg[S] / kTM;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -525,27 +498,34 @@ __global__ void __launch_bounds__(256, 1) k_fm_fwd(DescParams P, Workspace ws, M
     int sp = pos4_species(ws.pos4[row0]);
     if (!NNP_IN(sp, P.S, ws.flags)) sp = 0;
     {
+      f2 a[4][kH1 / 32], ad[4][kH1 / 32];
+      net_zero<kH1>(a);
+      net_zero<kH1>(ad);
+      fm_gemm2<kH1, true>(a, ad, nullptr, nullptr, ws.G + (size_t)row0 * D, dG + (size_t)row0 * D, D, D,
+                          Wt.W[sp][0], Bs, As, As2);
       float acc[8][kH1 / 32], accd[8][kH1 / 32];
-      zero_acc<kH1>(acc);
-      zero_acc<kH1>(accd);
-      gemm_tile<kH1>(acc, nullptr, ws.G + (size_t)row0 * D, D, D, Wt.W[sp][0], Bs, As);
-      gemm_tile<kH1>(accd, nullptr, dG + (size_t)row0 * D, D, D, Wt.W[sp][0], Bs, As);
+      fm_rows<kH1 / 32>(a, acc);
+      fm_rows<kH1 / 32>(ad, accd);
       fm_store_fwd<kH1>(acc, accd, Wt.b[sp][0], H1T, DH1T, z, dz, row0, fm_off(0), al, inv_al);
     }
     {
+      f2 a[4][kH2 / 32], ad[4][kH2 / 32];
+      net_zero<kH2>(a);
+      net_zero<kH2>(ad);
+      fm_gemm2<kH2, false>(a, ad, H1T, DH1T, nullptr, nullptr, 0, kH1, Wt.W[sp][1], Bs, As, As2);
       float acc[8][kH2 / 32], accd[8][kH2 / 32];
-      zero_acc<kH2>(acc);
-      zero_acc<kH2>(accd);
-      gemm_tile<kH2>(acc, H1T, nullptr, 0, kH1, Wt.W[sp][1], Bs, As);
-      gemm_tile<kH2>(accd, DH1T, nullptr, 0, kH1, Wt.W[sp][1], Bs, As);
+      fm_rows<kH2 / 32>(a, acc);
+      fm_rows<kH2 / 32>(ad, accd);
       fm_store_fwd<kH2>(acc, accd, Wt.b[sp][1], H2T, DH2T, z, dz, row0, fm_off(1), al, inv_al);
     }
     {
+      f2 a[4][kH3 / 32], ad[4][kH3 / 32];
+      net_zero<kH3>(a);
+      net_zero<kH3>(ad);
+      fm_gemm2<kH3, false>(a, ad, H2T, DH2T, nullptr, nullptr, 0, kH2, Wt.W[sp][2], Bs, As, As2);
       float acc[8][kH3 / 32], accd[8][kH3 / 32];
-      zero_acc<kH3>(acc);
-      zero_acc<kH3>(accd);
-      gemm_tile<kH3>(acc, H2T, nullptr, 0, kH2, Wt.W[sp][2], Bs, As);
-      gemm_tile<kH3>(accd, DH2T, nullptr, 0, kH2, Wt.W[sp][2], Bs, As);
+      fm_rows<kH3 / 32>(a, acc);
+      fm_rows<kH3 / 32>(ad, accd);
       fm_store_fwd<kH3>(acc, accd, Wt.b[sp][2], nullptr, nullptr, z, dz, row0, fm_off(2), al, inv_al);
     }
     __syncthreads();
@@ -591,8 +571,7 @@ __global__ void __launch_bounds__(256, 1) k_fm_rev(DescParams P, Workspace ws, M
   float* P3 = T3 + kH3 * kLDX;
   float* T2 = P3 + kH3 * kLDX;
   float* P2 = T2 + kH2 * kLDX;
-  float* Bs = P2 + kH2 * kLDX;
-  float* As = Bs + kKC * kH1;
+  float* Bs = P2 + kH2 * kLDX;  // [kNKC][160]
   const float inv_al = 1.f / P.celu_alpha;
   const int ty = threadIdx.x >> 5;
   const int ntiles = ws.seg[S] / kTM;
@@ -616,19 +595,23 @@ __global__ void __launch_bounds__(256, 1) k_fm_rev(DescParams P, Workspace ws, M
       fm_store_rev<kH3>(th, ph, z, dz, t, p, T3, P3, row0, fm_off(2), valid, inv_al);
     }
     {  // layer 2: th2 = t3 W3^T, ph2 = p3 W3^T
+      f2 a[4][kH2 / 32], ad[4][kH2 / 32];
+      net_zero<kH2>(a);
+      net_zero<kH2>(ad);
+      fm_gemm2<kH2, false>(a, ad, T3, P3, nullptr, nullptr, 0, kH3, Wt.WT[sp][2], Bs, nullptr, nullptr);
       float th[8][kH2 / 32], ph[8][kH2 / 32];
-      zero_acc<kH2>(th);
-      zero_acc<kH2>(ph);
-      gemm_tile<kH2>(th, T3, nullptr, 0, kH3, Wt.WT[sp][2], Bs, As);
-      gemm_tile<kH2>(ph, P3, nullptr, 0, kH3, Wt.WT[sp][2], Bs, As);
+      fm_rows<kH2 / 32>(a, th);
+      fm_rows<kH2 / 32>(ad, ph);
       fm_store_rev<kH2>(th, ph, z, dz, t, p, T2, P2, row0, fm_off(1), valid, inv_al);
     }
     {  // layer 1: th1 = t2 W2^T, ph1 = p2 W2^T
+      f2 a[4][kH1 / 32], ad[4][kH1 / 32];
+      net_zero<kH1>(a);
+      net_zero<kH1>(ad);
+      fm_gemm2<kH1, false>(a, ad, T2, P2, nullptr, nullptr, 0, kH2, Wt.WT[sp][1], Bs, nullptr, nullptr);
       float th[8][kH1 / 32], ph[8][kH1 / 32];
-      zero_acc<kH1>(th);
-      zero_acc<kH1>(ph);
-      gemm_tile<kH1>(th, T2, nullptr, 0, kH2, Wt.WT[sp][1], Bs, As);
-      gemm_tile<kH1>(ph, P2, nullptr, 0, kH2, Wt.WT[sp][1], Bs, As);
+      fm_rows<kH1 / 32>(a, th);
+      fm_rows<kH1 / 32>(ad, ph);
       fm_store_rev<kH1>(th, ph, z, dz, t, p, nullptr, nullptr, row0, fm_off(0), valid, inv_al);
     }
     __syncthreads();
@@ -746,10 +729,10 @@ __global__ void __launch_bounds__(256) k_fm_wgrad(DescParams P, const FmJob* __r
 }
 
 size_t fm_fwd_smem(int /*D*/) {
-  return sizeof(float) * ((size_t)(2 * kH1 + 2 * kH2) * kLDX + (size_t)kKC * kH1 + (size_t)kKC * kLDX);
+  return sizeof(float) * ((size_t)(2 * kH1 + 2 * kH2) * kLDX + (size_t)kNKC * kH1 + (size_t)2 * kNKC * kLDX);
 }
 size_t fm_rev_smem() {
-  return sizeof(float) * ((size_t)(2 * kH3 + 2 * kH2) * kLDX + (size_t)kKC * kH1 + (size_t)kKC * kLDX);
+  return sizeof(float) * ((size_t)(2 * kH3 + 2 * kH2) * kLDX + (size_t)kNKC * kH1);
 }
 
 void launch_fm(int grid, cudaStream_t st, const DescParams& P, const Workspace& ws, const MlpF32Weights& W,
