@@ -623,12 +623,13 @@ __global__ void __launch_bounds__(256, 1) k_fm_rev(DescParams P, Workspace ws, M
 // l = 4 means w4 (tile of 64 x 1).  The job's rows go through shared memory
 // 32 at a time (the inputs h, dh and the adjoints t, p of the tile); thread
 // (ti, to) keeps a 4 x 4 block of the tile (inputs 4 ti.., outputs 4 to..),
-// so each row costs it four 16-byte shared loads for 32 FMAs, and each staged
-// value serves 64 products.  FP32 partials over 64 rows, FP64 sums, one FP64
-// atomic add per entry into the packed gradient (zeroed before).
+// so each row costs it four 16-byte shared loads for 32 FMAs (16 f32x2), and
+// each staged value serves 64 products.  FP32 partials over 256 rows, FP64
+// sums, one FP64 atomic add per entry into the packed gradient (zeroed before).
 constexpr int kWgT = 64;       // tile edge (inputs and outputs)
 constexpr int kWgRows = 32;    // rows staged at a time
 constexpr int kWgLd = kWgT + 4;  // floats per staged row (16-byte aligned 4-column reads)
+constexpr int kWgFlush = 8;      // chunks summed in FP32 before each FP64 flush
 __global__ void __launch_bounds__(256) k_fm_wgrad(DescParams P, const FmJob* __restrict__ jobs, int njobs,
                                                   const float* __restrict__ G, const float* __restrict__ dG,
                                                   const float* __restrict__ z, const float* __restrict__ dz,
@@ -645,7 +646,10 @@ __global__ void __launch_bounds__(256) k_fm_wgrad(DescParams P, const FmJob* __r
     const int fin = l == 1 ? D : (l == 2 ? kH1 : (l == 3 ? kH2 : kH3));
     const int fout = l == 1 ? kH1 : (l == 2 ? kH2 : (l == 3 ? kH3 : 1));
     double accd[4][4] = {}, bacc[4] = {};
-    float a[4][4] = {}, b[4] = {};
+    f2 a[4][2], b[2];  // a[x][y/2]: outputs (4ti + x, 4to + y), y pairs; b: bias sums
+#pragma unroll
+    for (int x = 0; x < 4; ++x) a[x][0] = a[x][1] = f2_make(0.f, 0.f);
+    b[0] = b[1] = f2_make(0.f, 0.f);
     int chunks = 0;
     for (int c0 = jbv.r0; c0 < jbv.r1; c0 += kWgRows) {
       const int nr = min(kWgRows, jbv.r1 - c0);
@@ -685,27 +689,35 @@ __global__ void __launch_bounds__(256) k_fm_wgrad(DescParams P, const FmJob* __r
         const float4 t4 = *reinterpret_cast<const float4*>(&Tc[rr][4 * to]);
         const float4 p4 = *reinterpret_cast<const float4*>(&Pc[rr][4 * to]);
         const float hv[4] = {h4.x, h4.y, h4.z, h4.w}, dv[4] = {d4.x, d4.y, d4.z, d4.w};
-        const float tv[4] = {t4.x, t4.y, t4.z, t4.w}, pv[4] = {p4.x, p4.y, p4.z, p4.w};
+        const f2 tp[2] = {f2_make(t4.x, t4.y), f2_make(t4.z, t4.w)};
+        const f2 pp[2] = {f2_make(p4.x, p4.y), f2_make(p4.z, p4.w)};
 #pragma unroll
-        for (int x = 0; x < 4; ++x)
+        for (int x = 0; x < 4; ++x) {
+          const f2 hh = f2_make(hv[x], hv[x]), dd = f2_make(dv[x], dv[x]);
 #pragma unroll
-          for (int y = 0; y < 4; ++y) a[x][y] = fmaf(dv[x], tv[y], fmaf(hv[x], pv[y], a[x][y]));
-#pragma unroll
-        for (int y = 0; y < 4; ++y) b[y] += pv[y];
+          for (int y = 0; y < 2; ++y) a[x][y] = f2_fma(dd, tp[y], f2_fma(hh, pp[y], a[x][y]));
+        }
+        b[0] = f2_add(b[0], pp[0]);
+        b[1] = f2_add(b[1], pp[1]);
       }
-      if (++chunks == 2 || c0 + kWgRows >= jbv.r1) {  // 64 rows in FP32, then FP64
+      // 256 rows in FP32, then FP64 (FP64 arithmetic is scarce on this part)
+      if (++chunks == kWgFlush || c0 + kWgRows >= jbv.r1) {
         chunks = 0;
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
-          for (int y = 0; y < 4; ++y) {
-            accd[x][y] += (double)a[x][y];
-            a[x][y] = 0.f;
+          for (int y = 0; y < 2; ++y) {
+            const float2 v = f2_split(a[x][y]);
+            accd[x][2 * y] += (double)v.x;
+            accd[x][2 * y + 1] += (double)v.y;
+            a[x][y] = f2_make(0.f, 0.f);
           }
 #pragma unroll
-        for (int y = 0; y < 4; ++y) {
-          bacc[y] += (double)b[y];
-          b[y] = 0.f;
+        for (int y = 0; y < 2; ++y) {
+          const float2 v = f2_split(b[y]);
+          bacc[2 * y] += (double)v.x;
+          bacc[2 * y + 1] += (double)v.y;
+          b[y] = f2_make(0.f, 0.f);
         }
       }
     }
