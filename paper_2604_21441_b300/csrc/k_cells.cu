@@ -355,16 +355,17 @@ __global__ void __launch_bounds__(1024) k_cells_small(const EvalIO* __restrict__
 // Both keep the hit masks of a lane in shared-memory slots and write the hits
 // with one loop whose step count is the same for the whole warp.  SB >= S
 // bounds the per-species register arrays and scans (2, 4 or 8).  WIN is the
-// window (512; 1024 for small systems, with row groups of at most 8 so that a
-// lane still tests at most 8 chunks).  split > 1 spreads a cell's row groups
-// over that many warps, for systems with fewer cells than the GPU has warps.
+// window (512; 1024 for small systems, with row groups of at most 8, and 2048
+// for a system of one cell, with groups of at most 4, so that a lane still
+// tests at most 8 chunks).  split > 1 spreads a cell's row groups over that
+// many warps, for systems with fewer cells than the GPU has warps.
 template <int SB, int WIN>
 __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __restrict__ io,
                                                           const SysDesc* __restrict__ sys,
                                                           DescParams P, Workspace ws, int split, int dyn) {
   constexpr int NCH = WIN / 32;                                       // window chunks
   constexpr int WF = 3 * NCH * kNbrChunkStride + WIN + 16 * 32;       // shared floats per warp
-  constexpr int GR = WIN > 512 ? 8 : 16;                              // rows per group
+  constexpr int GR = WIN > 1024 ? 4 : (WIN > 512 ? 8 : 16);           // rows per group
   constexpr unsigned F = 0xffffffffu;
   __shared__ int s_mx[3];  // maxima of the CTA's row counts; warps done
   extern __shared__ float4 s_dyn[];
@@ -767,11 +768,14 @@ cudaError_t neighbors_set_smem_limits() {
     e = cudaFuncSetAttribute(k_cells_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(int) * kScanSmemBinsSmall));
   const int s1 = (int)neighbors_smem(kNbrWin), s2 = (int)neighbors_smem(kNbrWinSmall);
+  const int s3 = (int)neighbors_smem(kNbrWinTiny);
 #define NSM(sb)                                                                                                   \
   if (e == cudaSuccess)                                                                                           \
     e = cudaFuncSetAttribute(k_neighbors<sb, kNbrWin>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1);          \
   if (e == cudaSuccess)                                                                                           \
-    e = cudaFuncSetAttribute(k_neighbors<sb, kNbrWinSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2);
+    e = cudaFuncSetAttribute(k_neighbors<sb, kNbrWinSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2);     \
+  if (e == cudaSuccess)                                                                                           \
+    e = cudaFuncSetAttribute(k_neighbors<sb, kNbrWinTiny>, cudaFuncAttributeMaxDynamicSharedMemorySize, s3);
   NSM(2) NSM(4) NSM(8)
 #undef NSM
   return e;
@@ -786,6 +790,14 @@ void launch_neighbors(int grid, cudaStream_t st, const EvalIO* io, const SysDesc
     if (P.S <= 2) k_neighbors<2, kNbrWin><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws, sp, dyn);
     else if (P.S <= 4) k_neighbors<4, kNbrWin><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws, sp, dyn);
     else k_neighbors<8, kNbrWin><<<grid, kNbrThreads, sm, st>>>(io, sys, P, ws, sp, dyn);
+    return;
+  }
+  if (cells == 1) {  // one cell: its 27 images in 2048-candidate windows, row groups of 4 over up to 32 warps
+    const int split = (int)std::max(1LL, std::min(32LL, (rows + 3) / 4));
+    const size_t sm = neighbors_smem(kNbrWinTiny);
+    if (P.S <= 2) k_neighbors<2, kNbrWinTiny><<<(split + 3) / 4, kNbrThreads, sm, st>>>(io, sys, P, ws, split, dyn);
+    else if (P.S <= 4) k_neighbors<4, kNbrWinTiny><<<(split + 3) / 4, kNbrThreads, sm, st>>>(io, sys, P, ws, split, dyn);
+    else k_neighbors<8, kNbrWinTiny><<<(split + 3) / 4, kNbrThreads, sm, st>>>(io, sys, P, ws, split, dyn);
     return;
   }
   // small systems: 1024-candidate windows, each cell's row groups over up to 8 warps

@@ -38,6 +38,7 @@ constexpr int kScanSmemBinsSmall = 16384;  // the same for k_cells_small (64 KB,
 constexpr int kNbrThreads = 128;  // k_neighbors: warp per cell, lane per row
 constexpr int kNbrWin = 512;      // neighbourhood atoms one warp stages per window
 constexpr int kNbrWinSmall = 1024;          // the same for small systems (at most kNbrRowsSmall rows)
+constexpr int kNbrWinTiny = 2048;           // one-cell systems (27 images of the cell)
 constexpr long long kNbrRowsSmall = 8192;
 constexpr long long kCellsRowsSmall = 1536;  // up to this many rows the binning runs in one block
 constexpr int kNbrChunkStride = 36;       // floats per chunk in shared memory (bank spread)
