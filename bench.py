@@ -245,6 +245,11 @@ def run_ours(args, rank, world, local_rank):
         results[prec] = (E.cpu().numpy().copy(), F.cpu().numpy().copy())
         if prec == "fp32":
             ei_abs = float(np.abs(pot.atom_energies(n)).sum())
+            if prec != args.precision:  # the FP32 network's stage time (its roofline, in the line)
+                spot32 = make(prec, flags=P.FLAG_STAGE_EVENTS)
+                _, st32 = timed(spot32, 5, 2, stage=True)
+                forms[prec]["network_ms"] = float(np.mean(np.array(st32), axis=0)[3])
+                spot32.close()
         if prec == args.precision:
             main = (pot, ms)
         else:
@@ -870,6 +875,10 @@ def main():
             "network": (fl_mlp, "tensor" if args.precision != "fp32" else "alu")}
     dom = max(work, key=lambda k: st[k])
     fl_instr, bound = work[dom]
+    f32 = r["forms"].get("fp32", {})
+    if "network_ms" in f32:  # the FP32 form's SIMT network against the FP32 ALU peak
+        f32["network_tflops"] = fl_mlp / (f32["network_ms"] * 1e-3) / 1e12
+        f32["network_frac"] = f32["network_tflops"] / alu_peak
     water = r["S"] == 2 and r["wl"]["name"].startswith("water")
     fl_scope = SCOPE_FLOP_PER_ATOM[dom] * r["n"] * (args.members if dom == "network" else 1) if water else None
     if bound == "tensor":
