@@ -235,3 +235,32 @@ def test_dense_water_rows_beyond_the_pair_matrix(P, oracle_mod):
           f"max|dF| {np.abs(F - Fr).max():.2e}")
     assert energy_error(E, Er, Eir) <= E_REL_TOL
     assert np.abs(F - Fr).max() <= F_ABS_TOL
+
+
+def test_page_locked_host_buffers(P, oracle_mod):
+    """Page-locked host inputs are read in place by the binning kernel (no
+    staging copy); pageable host and device inputs go through their own
+    paths.  All three against the oracle, and against each other to the FP64
+    reduction order, on a box with unwrapped coordinates."""
+    import torch
+    s = synth.water_box(125, 35)
+    pos = s.pos + np.array([1.5, -2.0, 0.5]) * s.box  # outside the primary cell
+    w = weights32(2, 128, 36, 37)
+    pot = _pot(P, w, max_atoms=s.n)
+    p, m = _oracle(oracle_mod, w)
+    Er, Eir, Fr, _ = oracle_mod.energy_forces(m, pos, p.species_of(s.Z), s.box)
+    pos_p = torch.from_numpy(np.ascontiguousarray(pos)).pin_memory()
+    Z_p = torch.from_numpy(s.Z.astype(np.int32)).pin_memory()
+    E_p = torch.zeros(1, dtype=torch.float64).pin_memory()
+    F_p = torch.zeros((s.n, 3), dtype=torch.float64).pin_memory()
+    pot.eval_into(pos_p, Z_p, box9(s.box), E_p, F_p)
+    Ep, Fp = float(E_p[0]), F_p.numpy().copy()
+    Eh, Fh = pot.eval(pos, s.Z, box9(s.box))  # pageable host buffers
+    Ed, Fd = pot.eval(torch.tensor(pos, device="cuda"), torch.tensor(s.Z.astype(np.int32), device="cuda"),
+                      box9(s.box))
+    Ed, Fd = float(Ed), Fd.cpu().numpy()
+    for E, F in ((Ep, Fp), (Eh, Fh), (Ed, Fd)):
+        assert energy_error(E, Er, Eir) <= E_REL_TOL
+        assert np.abs(F - Fr).max() <= F_ABS_TOL
+    assert abs(Ep - Eh) <= 1e-9 * np.abs(Eir).sum() and np.abs(Fp - Fh).max() <= 1e-9
+    assert abs(Ep - Ed) <= 1e-9 * np.abs(Eir).sum() and np.abs(Fp - Fd).max() <= 1e-9
