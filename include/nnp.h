@@ -20,8 +20,11 @@
  * Pointers.  Arrays of positions, atomic numbers, energies and forces may be
  * host or device pointers (detected with cudaPointerGetAttributes).  Host
  * pointers are staged through pinned buffers; device pointers are read and
- * written in place.  Boxes are always host pointers.  The caller owns every
- * pointer it passes; the library never keeps one after a call returns.
+ * written in place.  Page-locked host positions and atomic numbers
+ * (cudaHostAlloc'd or registered) given to nnp_eval or nnp_eval_batch are
+ * read in place by the device during the call, outside the pair-list and
+ * embedding entry points.  Boxes are always host pointers.  The caller owns
+ * every pointer it passes; the library never keeps one after a call returns.
  *
  * Errors.  Every call returns an nnp_status; no exception crosses the ABI and
  * no GPU trap is used.  nnp_last_error() gives a one-line message.  Device
