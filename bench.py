@@ -139,9 +139,17 @@ def algorithmic_flops(n_pairs_r, n_triplets, n_rows, D, S):
 
 # ---------------------------------------------------------------------------
 
-def build_workload(k):
+def build_workload(k, waters=0):
+    """Workload k of synth.workload, or (waters > 0) one seeded water box of
+    that many molecules with the water workloads' weights (other sizes, e.g.
+    for a profiler capture of a box between the named ones)."""
     import synth
-    wl = synth.workload(k)
+    if waters > 0:
+        s = synth.water_box(waters, 1000 + waters)
+        wl = dict(name=f"water-{waters} ({3 * waters:,} atoms, {s.box[0]:.1f} A)", systems=[s],
+                  atomic_numbers=(1, 8), weight_seed=synth.WEIGHT_SEED[3])
+    else:
+        wl = synth.workload(k)
     S = len(wl["atomic_numbers"])
     D = synth.aev_length(S)
     w = synth.xavier_weights(S, D, wl["weight_seed"])
@@ -162,7 +170,7 @@ def run_ours(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    wl, w, S, D = build_workload(args.workload)
+    wl, w, S, D = build_workload(args.workload, args.waters)
     off, pos_h, Z_h, boxes = concat(wl["systems"])
     B = len(wl["systems"])
     n = int(off[-1])
@@ -677,7 +685,7 @@ def run_reference(args):
     full evaluations would take more than --ref-budget seconds, each step is
     instead a bounded sample (--ref-seconds of sampled atoms, single-threaded).
     --serial-full 1 also times one full single-threaded evaluation."""
-    wl, w, S, D = build_workload(args.workload)
+    wl, w, S, D = build_workload(args.workload, args.waters)
     n = sum(s.n for s in wl["systems"])
     t_probe, threads = oracle_full_omp(wl, w)
     full = t_probe * args.steps <= args.ref_budget
@@ -824,6 +832,8 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
     ap.add_argument("--compare", default="fp32,bf16,fp8")
     ap.add_argument("--workload", type=int, default=3)
+    ap.add_argument("--waters", type=int, default=0,
+                    help="instead of --workload: one water box of this many molecules")
     ap.add_argument("--members", type=int, default=1,
                     help="networks in the ensemble (member m > 0 takes the weight seed + m); "
                          "8 with --workload 6 is the ANI-2x architecture on the seven-element box")
