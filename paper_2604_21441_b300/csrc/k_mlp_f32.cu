@@ -17,9 +17,20 @@ namespace nnp {
 
 constexpr int kTM = 64;          // rows per tile
 constexpr int kLDX = kTM + 4;    // padded leading dim of transposed activations
+constexpr float kLog2eF = 1.4426950408889634f;  // log2(e)
 
 __device__ __forceinline__ float celu_f(float z, float al, float inv_al) {
   return z > 0.f ? z : al * (expf(z * inv_al) - 1.f);
+}
+// The evaluation kernel's CELU: exp(z / alpha) as 2^(z kexp), kexp = log2(e) /
+// alpha, on the MUFU unit (ex2.approx, about 2 ulp; results below the normal
+// range flush to zero, which moves CELU by less than alpha 2^-126).  e gets
+// exp(z / alpha), which is CELU'(z) for z <= 0.
+__device__ __forceinline__ float celu_ex2(float z, float al, float kexp, float& e) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(z * kexp));
+  e = y;
+  return z > 0.f ? z : al * (y - 1.f);
 }
 // CELU'(z) from h = CELU(z): 1 for h > 0, h/alpha + 1 otherwise
 __device__ __forceinline__ float dcelu_from_h(float h, float inv_al) {
@@ -153,7 +164,7 @@ __device__ __forceinline__ void net_col(const f2 (&acc)[4][NJ], int j, float (&v
 // forward epilogue: HT(col, rows) = CELU(acc + b)
 template <int N>
 __device__ __forceinline__ void net_store_celu(const f2 (&acc)[4][N / 32], const float* bias, float* HT,
-                                               float al, float inv_al) {
+                                               float al, float kexp) {
   const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
 #pragma unroll
   for (int j = 0; j < N / 32; ++j) {
@@ -162,7 +173,10 @@ __device__ __forceinline__ void net_store_celu(const f2 (&acc)[4][N / 32], const
     float h[8];
     net_col<N / 32>(acc, j, h);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) h[i] = celu_f(h[i] + bb, al, inv_al);
+    for (int i = 0; i < 8; ++i) {
+      float e;
+      h[i] = celu_ex2(h[i] + bb, al, kexp, e);
+    }
     *reinterpret_cast<float4*>(HT + col * kLDX + ty * 8) = make_float4(h[0], h[1], h[2], h[3]);
     *reinterpret_cast<float4*>(HT + col * kLDX + ty * 8 + 4) = make_float4(h[4], h[5], h[6], h[7]);
   }
@@ -220,7 +234,7 @@ __global__ void __launch_bounds__(256, 2) k_mlp_f32(const EvalIO* __restrict__ i
   float* Bs = H3T + kH3 * kLDX;                 // [kNKC][<= 160]
   float* As = H2T;                              // [kNKC][kLDX], first layer only
   const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
-  const float al = P.celu_alpha, inv_al = 1.f / P.celu_alpha;
+  const float al = P.celu_alpha, inv_al = 1.f / P.celu_alpha, kexp = kLog2eF * inv_al;
   const int rows = ws.seg[S];
   const int ntiles = rows / kTM;
   auto tile_species = [&](int t) {
@@ -249,14 +263,14 @@ __global__ void __launch_bounds__(256, 2) k_mlp_f32(const EvalIO* __restrict__ i
       net_zero<kH1>(a1);
       net_gemm<kH1, false, true>(a1, nullptr, ws.G + (size_t)row0 * D, D, D, Wt.W[sp][0], kH1, kH1, Bs, As, pf,
                                  [&](NetPf& q) { net_fetch<kH2, false, false>(q, Wt.W[sp][1], kH2, kH2, nullptr, 0, 0); });
-      net_store_celu<kH1>(a1, Wt.b[sp][0], H1T, al, inv_al);
+      net_store_celu<kH1>(a1, Wt.b[sp][0], H1T, al, kexp);
     }
     {
       f2 a2[4][kH2 / 32];
       net_zero<kH2>(a2);
       net_gemm<kH2, false, false>(a2, H1T, nullptr, 0, kH1, Wt.W[sp][1], kH2, kH2, Bs, As, pf,
                                   [&](NetPf& q) { net_fetch<kH3, false, false>(q, Wt.W[sp][2], kH3, kH3, nullptr, 0, 0); });
-      net_store_celu<kH2>(a2, Wt.b[sp][1], H2T, al, inv_al);
+      net_store_celu<kH2>(a2, Wt.b[sp][1], H2T, al, kexp);
     }
     {
       f2 a3[4][kH3 / 32];
@@ -278,9 +292,10 @@ __global__ void __launch_bounds__(256, 2) k_mlp_f32(const EvalIO* __restrict__ i
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const float zz = z[i] + bb;
-          const float h = celu_f(zz, al, inv_al);
+          float ez;
+          const float h = celu_ex2(zz, al, kexp, ez);
           e[i] = fmaf(h, ww, e[i]);
-          g[i] = ww * (zz > 0.f ? 1.f : expf(zz * inv_al));
+          g[i] = ww * (zz > 0.f ? 1.f : ez);
         }
         *reinterpret_cast<float4*>(H3T + col * kLDX + ty * 8) = make_float4(g[0], g[1], g[2], g[3]);
         *reinterpret_cast<float4*>(H3T + col * kLDX + ty * 8 + 4) = make_float4(g[4], g[5], g[6], g[7]);
