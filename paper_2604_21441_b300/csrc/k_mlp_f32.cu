@@ -639,13 +639,14 @@ __global__ void __launch_bounds__(256, 1) k_fm_rev(DescParams P, Workspace ws, M
 // 32 at a time (the inputs h, dh and the adjoints t, p of the tile); thread
 // (ti, to) keeps a 4 x 4 block of the tile (inputs 4 ti.., outputs 4 to..),
 // so each row costs it four 16-byte shared loads for 32 FMAs (16 f32x2), and
-// each staged value serves 64 products.  FP32 partials over 256 rows, FP64
-// sums, one FP64 atomic add per entry into the packed gradient (zeroed before).
+// each staged value serves 64 products.  FP32 partials over at most 256 rows
+// (a job's rows), then one FP64 atomic add per entry into the packed gradient
+// (zeroed before).
 constexpr int kWgT = 64;       // tile edge (inputs and outputs)
 constexpr int kWgRows = 32;    // rows staged at a time
 constexpr int kWgLd = kWgT + 4;  // floats per staged row (16-byte aligned 4-column reads)
 constexpr int kWgFlush = 8;      // chunks summed in FP32 before each FP64 flush
-__global__ void __launch_bounds__(256) k_fm_wgrad(DescParams P, const FmJob* __restrict__ jobs, int njobs,
+__global__ void __launch_bounds__(256, 3) k_fm_wgrad(DescParams P, const FmJob* __restrict__ jobs, int njobs,
                                                   const float* __restrict__ G, const float* __restrict__ dG,
                                                   const float* __restrict__ z, const float* __restrict__ dz,
                                                   const float* __restrict__ t, const float* __restrict__ p,
@@ -660,12 +661,12 @@ __global__ void __launch_bounds__(256) k_fm_wgrad(DescParams P, const FmJob* __r
     const int l = jbv.l;
     const int fin = l == 1 ? D : (l == 2 ? kH1 : (l == 3 ? kH2 : kH3));
     const int fout = l == 1 ? kH1 : (l == 2 ? kH2 : (l == 3 ? kH3 : 1));
-    double accd[4][4] = {}, bacc[4] = {};
     f2 a[4][2], b[2];  // a[x][y/2]: outputs (4ti + x, 4to + y), y pairs; b: bias sums
 #pragma unroll
     for (int x = 0; x < 4; ++x) a[x][0] = a[x][1] = f2_make(0.f, 0.f);
     b[0] = b[1] = f2_make(0.f, 0.f);
     int chunks = 0;
+    const double sc = (double)jbv.scale;
     for (int c0 = jbv.r0; c0 < jbv.r1; c0 += kWgRows) {
       const int nr = min(kWgRows, jbv.r1 - c0);
       __syncthreads();
@@ -715,43 +716,32 @@ __global__ void __launch_bounds__(256) k_fm_wgrad(DescParams P, const FmJob* __r
         b[0] = f2_add(b[0], pp[0]);
         b[1] = f2_add(b[1], pp[1]);
       }
-      // 256 rows in FP32, then FP64 (FP64 arithmetic is scarce on this part)
+      // at most 256 rows in FP32, then one FP64 add per entry into the gradient
       if (++chunks == kWgFlush || c0 + kWgRows >= jbv.r1) {
         chunks = 0;
 #pragma unroll
-        for (int x = 0; x < 4; ++x)
+        for (int x = 0; x < 4; ++x) {
+          const int i = jbv.i0 + 4 * ti + x;
 #pragma unroll
           for (int y = 0; y < 2; ++y) {
             const float2 v = f2_split(a[x][y]);
-            accd[x][2 * y] += (double)v.x;
-            accd[x][2 * y + 1] += (double)v.y;
+            const int o = jbv.o0 + 4 * to + 2 * y;
+            if (i < fin && o < fout) atomicAdd(&grad[jbv.w_off + (size_t)i * fout + o], -sc * (double)v.x);
+            if (i < fin && o + 1 < fout) atomicAdd(&grad[jbv.w_off + (size_t)i * fout + o + 1], -sc * (double)v.y);
             a[x][y] = f2_make(0.f, 0.f);
           }
-#pragma unroll
-        for (int y = 0; y < 2; ++y) {
-          const float2 v = f2_split(b[y]);
-          bacc[2 * y] += (double)v.x;
-          bacc[2 * y + 1] += (double)v.y;
-          b[y] = f2_make(0.f, 0.f);
         }
+        if (ti == 0 && jbv.i0 == 0 && l < 4)
+#pragma unroll
+          for (int y = 0; y < 2; ++y) {
+            const float2 v = f2_split(b[y]);
+            const int o = jbv.o0 + 4 * to + 2 * y;
+            if (o < fout) atomicAdd(&grad[jbv.b_off + o], -sc * (double)v.x);
+            if (o + 1 < fout) atomicAdd(&grad[jbv.b_off + o + 1], -sc * (double)v.y);
+          }
+        b[0] = b[1] = f2_make(0.f, 0.f);
       }
     }
-    const double sc = (double)jbv.scale;
-#pragma unroll
-    for (int x = 0; x < 4; ++x) {
-      const int i = jbv.i0 + 4 * ti + x;
-#pragma unroll
-      for (int y = 0; y < 4; ++y) {
-        const int o = jbv.o0 + 4 * to + y;
-        if (i < fin && o < fout) atomicAdd(&grad[jbv.w_off + (size_t)i * fout + o], -sc * accd[x][y]);
-      }
-    }
-    if (ti == 0 && jbv.i0 == 0 && l < 4)
-#pragma unroll
-      for (int y = 0; y < 4; ++y) {
-        const int o = jbv.o0 + 4 * to + y;
-        if (o < fout) atomicAdd(&grad[jbv.b_off + o], -sc * bacc[y]);
-      }
   }
 }
 

@@ -279,7 +279,7 @@ int nnp_ctx::force_match_grad(const double* v, const double* Fref, double* loss,
   launch_aev_jvp(rows, num_sms, stream, b_sys, P, w, fm_v, b_dEdG);
   if (prof) CK(cudaEventRecord(fm_ev[2], stream));
   // weight-gradient jobs per member, species, layer, 64 x 64 tile and
-  // 512-row segment (the segment bounds are the last evaluation's); the
+  // 256-row segment (the segment bounds are the last evaluation's); the
   // device list is kept while the segments stay the same
   std::vector<FmJob>& jobs = fm_job_list;
   const int fin[4] = {D, kH1, kH2, kH3}, fout[4] = {kH1, kH2, kH3, 1};
@@ -296,8 +296,8 @@ int nnp_ctx::force_match_grad(const double* v, const double* Fref, double* loss,
         boff[l] = off;
         off += fout[l];
       }
-      for (int r0 = seg[sp]; r0 < seg[sp + 1]; r0 += 512) {
-        const int r1 = std::min(seg[sp + 1], r0 + 512);
+      for (int r0 = seg[sp]; r0 < seg[sp + 1]; r0 += 256) {
+        const int r1 = std::min(seg[sp + 1], r0 + 256);
         for (int l = 0; l < 4; ++l)
           for (int i0 = 0; i0 < fin[l]; i0 += 64)
             for (int o0 = 0; o0 < fout[l]; o0 += 64)

@@ -2,8 +2,8 @@
 
 L = |F - Fref|^2 / (3N) with Fref from an independently seeded teacher
 network (oracle), or seeded random reference forces on the full-size box.
-The GPU computes F and dL/dtheta in FP32 (with FP64 sums over 64-row chunks
-and 512-row segments).  Bounds, about three times the measured errors:
+The GPU computes F and dL/dtheta in FP32 (FP32 sums over 256-row segments,
+added into the FP64 gradient).  Bounds, about three times the measured errors:
 relative loss error <= 2e-6; gradient max-abs error, relative to the largest
 gradient entry, <= 2e-5 on the small systems (measured <= 7e-6) and <= 2e-4
 on the 6,134-atom workload (measured 5.8e-5); relative L2 error <= 1.5e-5
@@ -78,7 +78,7 @@ def test_force_match_gradient(P, oracle_mod, kind):
 def test_force_match_workload5_full_size(P, oracle_mod):
     """The four-species workload at full size: H/C/N/O clusters of 2,000 atoms
     in water, 40 A box, 6,134 atoms, D = 384.  H has 3,651 rows, so each of
-    its weight-gradient tiles adds the FP64 sums of eight 512-row segments.
+    its weight-gradient tiles adds the sums of fifteen 256-row segments.
     Reference forces: seeded random, RMS 0.3 eV/A (the loss and its gradient
     are defined for any reference).  Energy and every force in FP32 bounds,
     then L and dL/dtheta against the oracle."""
