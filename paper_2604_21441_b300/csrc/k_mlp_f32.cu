@@ -241,17 +241,26 @@ __global__ void __launch_bounds__(256, 2) k_mlp_f32(const EvalIO* __restrict__ i
     int s = pos4_species(ws.pos4[t * kTM]);
     return NNP_IN(s, P.S, ws.flags) ? s : 0;
   };
-  // every product's first chunk is fetched during the previous product's
-  // last one (the first layer of the next tile during the last dE/dG block)
+  // Tiles: the first by block index, the later ones from a counter (the
+  // launch's last block resets it), each claimed one tile ahead so that its
+  // species is known early.  Every product's first chunk is fetched during
+  // the previous product's last one (the first layer of the next tile during
+  // the last dE/dG block).
+  __shared__ int s_claim[2];
+  int* const tq = ws.queue + kQNet;  // claim counter, blocks done
   NetPf pf;
-  int sp = 0;
-  if ((int)blockIdx.x < ntiles) {
-    sp = tile_species(blockIdx.x);
-    net_fetch<kH1, false, true>(pf, Wt.W[sp][0], kH1, kH1, ws.G + (size_t)blockIdx.x * kTM * D, D, 0);
+  int sp = 0, tile = blockIdx.x, ntile = ntiles;
+  if (tile < ntiles) {
+    if (threadIdx.x == 0) s_claim[0] = (int)gridDim.x + atomicAdd(tq, 1);
+    sp = tile_species(tile);
+    net_fetch<kH1, false, true>(pf, Wt.W[sp][0], kH1, kH1, ws.G + (size_t)tile * kTM * D, D, 0);
+    __syncthreads();
+    ntile = s_claim[0];
   }
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int it = 1; tile < ntiles; ++it) {
     const int row0 = tile * kTM;
-    const int ntile = tile + gridDim.x;
+    // the tile after the next one (read at the end of this one, past many barriers)
+    if (threadIdx.x == 0 && ntile < ntiles) s_claim[it & 1] = (int)gridDim.x + atomicAdd(tq, 1);
     const int sp_next = ntile < ntiles ? tile_species(ntile) : 0;
     auto next_tile = [&](NetPf& q) {
       if (ntile < ntiles)
@@ -370,6 +379,15 @@ __global__ void __launch_bounds__(256, 2) k_mlp_f32(const EvalIO* __restrict__ i
       }
     }
     sp = sp_next;
+    tile = ntile;
+    ntile = tile < ntiles ? s_claim[it & 1] : ntiles;
+  }
+  if (threadIdx.x == 0) {  // after this block's last claim; the last block resets the counter
+    __threadfence();
+    if (atomicAdd(tq + 1, 1) == (int)gridDim.x - 1) {
+      atomicExch(tq, 0);
+      atomicExch(tq + 1, 0);
+    }
   }
 }
 

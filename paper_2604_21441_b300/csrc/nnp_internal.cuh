@@ -206,7 +206,7 @@ struct Workspace {
 // requests do not all arrive at the start of the launch).  Each stage has a
 // pair of counters (items handed out, warps done); the last warp of a
 // dynamic launch to finish puts both back to zero for the next launch.
-enum QueueSlot { kQNbr = 0, kQFwd = 2, kQueueWords = 8 };
+enum QueueSlot { kQNbr = 0, kQFwd = 2, kQNet = 4, kQueueWords = 8 };
 
 // Bounds-checked build (compiled with -DNNP_CHECKED): an index read from
 // device data (a neighbour-list entry, a bin, a slot, a species) is checked
