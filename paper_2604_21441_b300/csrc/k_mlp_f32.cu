@@ -19,6 +19,7 @@ constexpr int kTM = 64;          // rows per tile
 constexpr int kLDX = kTM + 4;    // padded leading dim of transposed activations
 constexpr float kLog2eF = 1.4426950408889634f;  // log2(e)
 
+// CELU with expf (the force-matching passes and weight-gradient staging)
 __device__ __forceinline__ float celu_f(float z, float al, float inv_al) {
   return z > 0.f ? z : al * (expf(z * inv_al) - 1.f);
 }
