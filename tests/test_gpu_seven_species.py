@@ -2,8 +2,8 @@
 set of the ANI-2x model), and of the wide-descriptor tensor-core network.
 
 * a small seven-element box and the full 6,047-atom workload against the FP64
-  oracle within the FP32 bounds, and small boxes of one, three and five
-  elements (the FP32 network's other product shapes);
+  oracle within the FP32 bounds, small boxes of one, three and five
+  elements (the FP32 network's other product shapes), and a box of one cell;
 * water through a seven-species context equals water through a two-species
   context with the mapped first-layer rows (the absent species' blocks are
   zero);
@@ -139,6 +139,21 @@ def test_seven_species_ensemble_batch_pairs(P, oracle_mod):
     Er, Eir, Fr = oracle_mod.ensemble_energy_forces(models, s.pos, p.species_of(s.Z), s.box)
     assert energy_error(Ep, Er, Eir) <= E_REL_TOL
     assert np.abs(Fp - Fr).max() <= F_ABS_TOL
+
+
+def test_seven_species_one_cell_box(P, oracle_mod):
+    """A 9.5 A box (one cell: its 27 images make 27 x 39 = 1,053 hydrogen
+    candidates, the one-cell neighbour search with 2,048-candidate windows
+    at eight species) against the oracle within the FP32 bounds."""
+    s = synth.hcno_box(761, L=9.5, n_cluster_atoms=40, max_waters=12,
+                       elements=synth.ANI2X_Z, probs=synth.ANI2X_P)
+    w = weights32(7, 1008, 762, 763)
+    pot = _pot(P, w, max_atoms=s.n)
+    E, F = pot.eval(s.pos, s.Z, box9(s.box))
+    p = oracle_mod.Params(atomic_numbers=Z7)
+    Er, Eir, Fr, _ = oracle_mod.energy_forces(oracle_mod.Model(p, w), s.pos, p.species_of(s.Z), s.box)
+    assert energy_error(E, Er, Eir) <= E_REL_TOL
+    assert np.abs(F - Fr).max() <= F_ABS_TOL
 
 
 @pytest.mark.parametrize("Zs", [(6,), (1, 6, 8), (1, 6, 7, 8, 9)])
