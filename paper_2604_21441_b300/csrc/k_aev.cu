@@ -303,6 +303,10 @@ __global__ void __launch_bounds__(256, 3) k_aev_fwd(const SysDesc* __restrict__ 
     for (int s = 0; s < S; ++s) {
       const int n_s = rc->nr[s], o_s = rc->orr[s];
       const int nmax = max(n_s, __shfl_xor_sync(0xffffffffu, n_s, 16));
+      if (nmax == 0) {  // neither row of the warp has this species in range: no reduction
+        if (live) put1(s * kNRad + hl, 0.f);
+        continue;
+      }
       f2 acc2[kNRad / 2];
 #pragma unroll
       for (int m = 0; m < kNRad / 2; ++m) acc2[m] = f2_make(0.f, 0.f);
@@ -537,19 +541,26 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
   const float zeta = (float)(1 << P.zeta_sq);
   // sector constants in pairs (z, z+1): base = 1/2 + uc hc + sn hs,
   // d(base^zeta)/dc = 0.95 zeta base^(zeta-1) (hc - (uc/sn) hs); the factor
-  // 0.95 zeta (times the angular term's 2) is applied once per pair (dcs)
-  f2 hc2[4], hs2[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    hc2[q] = f2_make(P.hcos_z[2 * q], P.hcos_z[2 * q + 1]);
-    hs2[q] = f2_make(P.hsin_z[2 * q], P.hsin_z[2 * q + 1]);
+  // 0.95 zeta (times the angular term's 2) is applied once per pair (dcs).
+  // The pairs sit in shared memory and are read with volatile loads where
+  // they are used: held in 16 registers they cost the pair loop more.
+  __shared__ unsigned long long s_hcs[8];
+  if (threadIdx.x < 8) {
+    const int q = threadIdx.x & 3;
+    s_hcs[threadIdx.x] = threadIdx.x < 4 ? f2_make(P.hcos_z[2 * q], P.hcos_z[2 * q + 1]).v
+                                         : f2_make(P.hsin_z[2 * q], P.hsin_z[2 * q + 1]).v;
   }
+  __syncthreads();
+  const volatile unsigned long long* vhcs = s_hcs;
   const f2 half2 = f2_make(0.5f, 0.5f);
   const float dcs = 1.9f * zeta;
   const int rows = ws.seg[S];
   const int wpb = blockDim.x >> 5;
   const int rstride = gridDim.x * wpb;
   int cached_sys = -1;
+  // the pair matrix's diagonal stays zero (a pair joins two distinct
+  // neighbours), so the row sums of step (3) need no test for it
+  for (int m = lane; m < mc; m += 32) mat[m * ms + m] = make_float2(0.f, 0.f);
   // the next row's metadata, counts and first 64 list entries are loaded one
   // row ahead, so their latency hides behind the current row's arithmetic
   int p_atom = -1, p_info = 0, p_cnt = 0, p_cna = 0, p_e0 = 0, p_e1 = 0;
@@ -598,41 +609,66 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
       nang += na[q];
     }
     const bool use_mat = nang <= mc;  // warp-uniform
-    // pair blocks (every lane computes the same table; lanes < NB store it)
+    // pair blocks: lane b builds block b (32 blocks per round), the blocks'
+    // first flat indices by a scan of their pair counts over the lanes
     int Ttot = 0;
-    {
-      int b = 0;
 #pragma unroll
-      for (int s1 = 0; s1 < S; ++s1)
+    for (int r0 = 0; r0 < NB; r0 += 32) {
+      const int b = r0 + lane;
+      const int nl = NB - r0 < 32 ? NB - r0 : 32;  // lanes holding a block this round
+      // block b -> species pair (s1, s2), s1 <= s2, s1-major
+      int s1 = 0, s2 = 0;
 #pragma unroll
-        for (int s2 = s1; s2 < S; ++s2, ++b) {
-          PairBlock pb;
-          pb.base = Ttot;
-          pb.wo = kNRad * S + b * kNAng;
-          if (s1 == s2) {
-            const int n = na[s1];
-            const int K = (n & 1) ? (n - 1) / 2 : max(0, n / 2 - 1);
-            pb.K = pb.W = n;
-            pb.vq = 1;
-            pb.oa = pb.ob = oa[s1];
-            pb.nK = n * K;
-            pb.half = (n & 1) ? 0 : n / 2;
-            pb.T = pb.nK + pb.half;
-          } else {
-            const bool sw = na[s1] > na[s2];  // list a is the shorter one
-            pb.K = sw ? na[s2] : na[s1];
-            pb.W = sw ? na[s1] : na[s2];
-            pb.vq = 0;
-            pb.oa = sw ? oa[s2] : oa[s1];
-            pb.ob = sw ? oa[s1] : oa[s2];
-            pb.nK = 0x7fffffff;
-            pb.half = 0;
-            pb.T = pb.K * pb.W;
-          }
-          pb.mg = div_magic(pb.K);
-          if (lane == b) blk[b] = pb;
-          Ttot += pb.T;
+      for (int q = 0, st = 0; q < S; st += S - q, ++q)
+        if (b >= st) {
+          s1 = q;
+          s2 = q + (b - st);
         }
+      int n1 = 0, o1 = 0, n2 = 0, o2 = 0;
+#pragma unroll
+      for (int q = 0; q < S; ++q) {
+        if (q == s1) {
+          n1 = na[q];
+          o1 = oa[q];
+        }
+        if (q == s2) {
+          n2 = na[q];
+          o2 = oa[q];
+        }
+      }
+      PairBlock pb;
+      pb.wo = kNRad * S + b * kNAng;
+      if (s1 == s2) {
+        const int K = (n1 & 1) ? (n1 - 1) / 2 : max(0, n1 / 2 - 1);
+        pb.K = pb.W = n1;
+        pb.vq = 1;
+        pb.oa = pb.ob = o1;
+        pb.nK = n1 * K;
+        pb.half = (n1 & 1) ? 0 : n1 / 2;
+        pb.T = pb.nK + pb.half;
+      } else {
+        const bool sw = n1 > n2;  // list a is the shorter one
+        pb.K = sw ? n2 : n1;
+        pb.W = sw ? n1 : n2;
+        pb.vq = 0;
+        pb.oa = sw ? o2 : o1;
+        pb.ob = sw ? o1 : o2;
+        pb.nK = 0x7fffffff;
+        pb.half = 0;
+        pb.T = pb.K * pb.W;
+      }
+      const bool mine = lane < nl;
+      pb.mg = div_magic(mine ? pb.K : 0);
+      const int T = mine ? pb.T : 0;
+      int incl = T;
+#pragma unroll
+      for (int o = 1; o < nl; o <<= 1) {
+        const int y = __shfl_up_sync(FM, incl, o);
+        if (lane >= o) incl += y;
+      }
+      pb.base = Ttot + incl - T;
+      if (mine) blk[b] = pb;
+      Ttot += __shfl_sync(FM, incl, nl - 1);
     }
     const int* lr = ws.nbr_r + (size_t)row * cr;
     float fix = 0.f, fiy = 0.f, fiz = 0.f;  // force on the centre atom
@@ -733,7 +769,10 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
         f2 X2[kNAngR], Y2[kNAngR];
 #pragma unroll
         for (int zp = 0; zp < kNAngZ / 2; ++zp) {
-          const f2 base = f2_fma(sn2, hs2[zp], f2_fma(uc2, hc2[zp], half2));
+          f2 hcz, hsz;
+          hcz.v = vhcs[zp];
+          hsz.v = vhcs[4 + zp];
+          const f2 base = f2_fma(sn2, hsz, f2_fma(uc2, hcz, half2));
           // base^(zeta-1) and base^zeta
           f2 pw = base, pm1;
           if (ZSQ >= 1) {
@@ -753,7 +792,7 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
             pw = f2_make(b0z, b1z);
             pm1 = f2_make(b0m, b1m);
           }
-          const f2 dA = f2_mul(pm1, f2_fma(nucisn2, hs2[zp], hc2[zp]));  // d(base^zeta)/dc / (0.95 zeta)
+          const f2 dA = f2_mul(pm1, f2_fma(nucisn2, hsz, hcz));  // d(base^zeta)/dc / (0.95 zeta)
 #pragma unroll
           for (int a = 0; a < kNAngR; ++a) {
             const float4 w4 = reinterpret_cast<const float4*>(wb + a * kNAngZ)[zp >> 1];
@@ -806,12 +845,13 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
     __syncwarp();
 
     // ---------------- (3) each angular neighbour sums its row of the pair matrix
+    // (the diagonal entries are zero: no pair writes them)
     for (int m = lane; m < (use_mat ? nang : 0); m += 32) {
       const float4 gm = geo[m];
       float sa = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
       const float2* row_m = mat + m * ms;
+#pragma unroll 4
       for (int p = 0; p < nang; ++p) {
-        if (p == m) continue;
         const float2 c = row_m[p];
         const float4 gp = geo[p];
         sa += c.x;

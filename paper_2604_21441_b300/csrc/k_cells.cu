@@ -116,10 +116,18 @@ __device__ __forceinline__ void scan_bins(const EvalIO* __restrict__ io, int S, 
   // coalesced loads into shared memory (and bin_len), then each thread scans
   // its contiguous range from there
   if (in_smem) {
-    for (int b = t; b < nb; b += 1024) {
-      const int c = ws.bin_count[b];
-      s_bins[b] = c;
-      ws.bin_len[b] = c;
+    // eight independent loads in flight per thread before their stores
+    // (a load after each store would wait a full round trip per bin)
+    for (int bb = t; bb < nb; bb += 8 * 1024) {
+      int c[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) c[i] = bb + i * 1024 < nb ? ws.bin_count[bb + i * 1024] : 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (bb + i * 1024 < nb) {
+          s_bins[bb + i * 1024] = c[i];
+          ws.bin_len[bb + i * 1024] = c[i];
+        }
     }
     __syncthreads();
   }
@@ -290,21 +298,25 @@ __device__ __forceinline__ void sort_bins(const EvalIO* __restrict__ io, int S, 
     if (do_sort) {
       for (int k = lane; k < cnt; k += 32) sw[k] = ws.row_atom[start + k];
       __syncwarp();
+      // each lane writes the rows of the atoms it ranked (no re-read of row_atom)
       for (int k = lane; k < cnt; k += 32) {
         const int a = sw[k];
         int rank = 0;
         for (int q = 0; q < cnt; ++q) rank += sw[q] < a;
         const int row = start + rank;
         ws.row_atom[row] = a;
+        ws.pos4[row] = ws.atom_off[a];
+        ws.row_info[row] = ws.atom_sys[a];
+        ws.row_cell[row] = ws.atom_cell[a];
       }
-      __syncwarp();
-    }
-    for (int k = lane; k < cnt; k += 32) {
-      const int row = start + k;
-      const int a = ws.row_atom[row];
-      ws.pos4[row] = ws.atom_off[a];
-      ws.row_info[row] = ws.atom_sys[a];
-      ws.row_cell[row] = ws.atom_cell[a];
+    } else {
+      for (int k = lane; k < cnt; k += 32) {
+        const int row = start + k;
+        const int a = ws.row_atom[row];
+        ws.pos4[row] = ws.atom_off[a];
+        ws.row_info[row] = ws.atom_sys[a];
+        ws.row_cell[row] = ws.atom_cell[a];
+      }
     }
     __syncwarp();
   }
