@@ -611,7 +611,7 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
     const bool use_mat = nang <= mc;  // warp-uniform
     // pair blocks: lane b builds block b (32 blocks per round), the blocks'
     // first flat indices by a scan of their pair counts over the lanes
-    int Ttot = 0;
+    int Ttot = 0, nbe = 0;  // pairs; blocks with pairs (only those are stored, in order)
 #pragma unroll
     for (int r0 = 0; r0 < NB; r0 += 32) {
       const int b = r0 + lane;
@@ -667,7 +667,9 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
         if (lane >= o) incl += y;
       }
       pb.base = Ttot + incl - T;
-      if (mine) blk[b] = pb;
+      const unsigned has_pairs = __ballot_sync(FM, T > 0);
+      if (T > 0) blk[nbe + __popc(has_pairs & ((1u << lane) - 1u))] = pb;
+      nbe += __popc(has_pairs);
       Ttot += __shfl_sync(FM, incl, nl - 1);
     }
     const int* lr = ws.nbr_r + (size_t)row * cr;
@@ -736,7 +738,7 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
       int b = 0;
       PairBlock pb = blk[0];
       for (int t = lane; t < Ttot; t += 32) {
-        while (b + 1 < NB && t >= pb.base + pb.T) pb = blk[++b];
+        while (b + 1 < nbe && t >= pb.base + pb.T) pb = blk[++b];
         const int tl = t - pb.base;
         const int q = div_by_magic(tl, pb.mg);
         int u = tl - q * pb.K;

@@ -567,6 +567,13 @@ __global__ void __launch_bounds__(kNbrThreads, 5) k_neighbors(const EvalIO* __re
         int nr = 0, tot_r = 0, tot_a = 0, wb = 0;
         for (int sp = 0; sp < S; ++sp) {
           const int wn = pick(tot, sp);
+          if (wn == 0) {  // no atom of this species near the cell (warp-uniform)
+            if (has && p == 0) {
+              ws.cnt_r[(size_t)row * kMaxS + sp] = 0;
+              ws.cnt_a[(size_t)row * kMaxS + sp] = 0;
+            }
+            continue;
+          }
           if (!all_fit) stage(sp, 0, wn, 0);
           const int nch = (wn + 31) >> 5;
           const int ch0 = (p * nch) >> lh, ch1 = ((p + 1) * nch) >> lh;
