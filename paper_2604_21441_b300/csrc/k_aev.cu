@@ -592,9 +592,10 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
       if (lane < 27) sh[lane] = shift_vec(lane, sd);
       cached_sys = sid;
     }
-    {
-      const float4* dg = reinterpret_cast<const float4*>(ws.dEdG + (size_t)row * D);
-      for (int f = lane; f < D / 4; f += 32) reinterpret_cast<float4*>(wsm)[f] = dg[f];
+    const float4* dg = reinterpret_cast<const float4*>(ws.dEdG + (size_t)row * D);
+    float4* const w4s = reinterpret_cast<float4*>(wsm);
+    if (S <= 2) {  // the whole dE/dG row (a row of the two-species model uses most of it)
+      for (int f = lane; f < D / 4; f += 32) w4s[f] = dg[f];
     }
     // counts per species (angular ones clamped to the staging capacity)
     int nr[S], orr[S], na[S], oa[S];
@@ -671,6 +672,18 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
       if (T > 0) blk[nbe + __popc(has_pairs & ((1u << lane) - 1u))] = pb;
       nbe += __popc(has_pairs);
       Ttot += __shfl_sync(FM, incl, nl - 1);
+    }
+    if (S > 2) {
+      // only the dE/dG blocks the row uses: the radial blocks of the species in
+      // range and the angular blocks with pairs (wide descriptors, most of
+      // whose blocks are unused by one row)
+      __syncwarp();  // the block table is in shared memory
+      const int nr_l = __shfl_sync(FM, cnt_l, (lane >> 2) & (kMaxS - 1));
+      if (lane < 4 * S && nr_l > 0) w4s[lane] = dg[lane];
+      for (int f = lane; f < 8 * nbe; f += 32) {
+        const int o = (blk[f >> 3].wo >> 2) + (f & 7);
+        w4s[o] = dg[o];
+      }
     }
     const int* lr = ws.nbr_r + (size_t)row * cr;
     float fix = 0.f, fiy = 0.f, fiz = 0.f;  // force on the centre atom
