@@ -382,73 +382,125 @@ __global__ void __launch_bounds__(256, 3) k_aev_fwd(const SysDesc* __restrict__ 
       }
     }
     __syncwarp();
-#pragma unroll 1
-    for (int s1 = 0; s1 < S; ++s1) {
-#pragma unroll 1
-      for (int s2 = s1; s2 < S; ++s2) {
-        const bool diag = s1 == s2;
-        const int n1 = rc->na[s1], n2 = rc->na[s2];
-        const int T = diag ? n1 * (n1 - 1) / 2 : n1 * n2;
-        const int Tmax = max(T, __shfl_xor_sync(0xffffffffu, T, 16));
-        const int f0 = kNRad * S + pair_block(S, s1, s2) * kNAng + 2 * hl;
-        if (Tmax == 0) {
-          if (live) put2(f0, 0.f, 0.f);
-          continue;
-        }
-        const PairMap pm = make_map(diag, n1, n2, rc->oa[s1], rc->oa[s2]);
-        f2 acc2[kNAngR][kNAngZ / 2];
+    // one species-pair block (s1, s2) of both rows of the warp
+    auto ang_block = [&](int s1, int s2) {
+      const bool diag = s1 == s2;
+      const int n1 = rc->na[s1], n2 = rc->na[s2];
+      const int T = diag ? n1 * (n1 - 1) / 2 : n1 * n2;
+      const int Tmax = max(T, __shfl_xor_sync(0xffffffffu, T, 16));
+      const int f0 = kNRad * S + pair_block(S, s1, s2) * kNAng + 2 * hl;
+      if (Tmax == 0) {
+        if (live) put2(f0, 0.f, 0.f);
+        return;
+      }
+      const PairMap pm = make_map(diag, n1, n2, rc->oa[s1], rc->oa[s2]);
+      f2 acc2[kNAngR][kNAngZ / 2];
 #pragma unroll
-        for (int a = 0; a < kNAngR; ++a)
+      for (int a = 0; a < kNAngR; ++a)
 #pragma unroll
-          for (int zp = 0; zp < kNAngZ / 2; ++zp) acc2[a][zp] = f2_make(0.f, 0.f);
-        for (int t0 = 0; t0 < Tmax; t0 += 16) {
-          const int t = t0 + hl;
-          if (t < T) {
-            int u, v;
-            map_pair(pm, t, u, v);
-            const float4 gu = geo[u], gv = geo[v];
-            const float c = gu.x * gv.x + gu.y * gv.y + gu.z * gv.z;
-            const float uc = 0.95f * c;
-            const float s2 = fmaxf(1.f - uc * uc, 1e-12f);  // >= 0.0975: |uc| <= 0.95
-            const float sn = s2 * rsqrtf(s2);
-            const float fp = fcs[u] * fcs[v];
-            const float rbar = 0.5f * (gu.w + gv.w);
-            f2 B2[kNAngR];
+        for (int zp = 0; zp < kNAngZ / 2; ++zp) acc2[a][zp] = f2_make(0.f, 0.f);
+      for (int t0 = 0; t0 < Tmax; t0 += 16) {
+        const int t = t0 + hl;
+        if (t < T) {
+          int u, v;
+          map_pair(pm, t, u, v);
+          const float4 gu = geo[u], gv = geo[v];
+          const float c = gu.x * gv.x + gu.y * gv.y + gu.z * gv.z;
+          const float uc = 0.95f * c;
+          const float s2 = fmaxf(1.f - uc * uc, 1e-12f);  // >= 0.0975: |uc| <= 0.95
+          const float sn = s2 * rsqrtf(s2);
+          const float fp = fcs[u] * fcs[v];
+          const float rbar = 0.5f * (gu.w + gv.w);
+          f2 B2[kNAngR];
 #pragma unroll
-            for (int a = 0; a < kNAngR; ++a) {
-              const float x = rbar - P.shf_a[a];
-              const float Bv = fp * ex2(ka * x * x);
-              B2[a] = f2_make(Bv, Bv);
-            }
-            const f2 uc2 = f2_make(uc, uc), sn2 = f2_make(sn, sn);
-#pragma unroll
-            for (int zp = 0; zp < kNAngZ / 2; ++zp) {
-              f2 hcz, hsz;
-              hcz.v = vhcs[zp];
-              hsz.v = vhcs[4 + zp];
-              f2 bz = f2_fma(sn2, hsz, f2_fma(uc2, hcz, half2));
-              if (ZSQ >= 0) {
-#pragma unroll
-                for (int i = 0; i < (ZSQ >= 0 ? ZSQ : 0); ++i) bz = f2_mul(bz, bz);
-              } else {
-                for (int i = 0; i < P.zeta_sq; ++i) bz = f2_mul(bz, bz);
-              }
-#pragma unroll
-              for (int a = 0; a < kNAngR; ++a) acc2[a][zp] = f2_fma(B2[a], bz, acc2[a][zp]);
-            }
+          for (int a = 0; a < kNAngR; ++a) {
+            const float x = rbar - P.shf_a[a];
+            const float Bv = fp * ex2(ka * x * x);
+            B2[a] = f2_make(Bv, Bv);
           }
-        }
-        float acc[kNAng];
-#pragma unroll
-        for (int a = 0; a < kNAngR; ++a)
+          const f2 uc2 = f2_make(uc, uc), sn2 = f2_make(sn, sn);
 #pragma unroll
           for (int zp = 0; zp < kNAngZ / 2; ++zp) {
-            const float2 h = f2_split(acc2[a][zp]);
-            acc[a * kNAngZ + 2 * zp] = h.x;
-            acc[a * kNAngZ + 2 * zp + 1] = h.y;
+            f2 hcz, hsz;
+            hcz.v = vhcs[zp];
+            hsz.v = vhcs[4 + zp];
+            f2 bz = f2_fma(sn2, hsz, f2_fma(uc2, hcz, half2));
+            if (ZSQ >= 0) {
+#pragma unroll
+              for (int i = 0; i < (ZSQ >= 0 ? ZSQ : 0); ++i) bz = f2_mul(bz, bz);
+            } else {
+              for (int i = 0; i < P.zeta_sq; ++i) bz = f2_mul(bz, bz);
+            }
+#pragma unroll
+            for (int a = 0; a < kNAngR; ++a) acc2[a][zp] = f2_fma(B2[a], bz, acc2[a][zp]);
           }
-        hw_reduce_scatter<kNAng>(acc, hl);
-        if (live) put2(f0, 2.f * acc[0], 2.f * acc[1]);
+        }
+      }
+      float acc[kNAng];
+#pragma unroll
+      for (int a = 0; a < kNAngR; ++a)
+#pragma unroll
+        for (int zp = 0; zp < kNAngZ / 2; ++zp) {
+          const float2 h = f2_split(acc2[a][zp]);
+          acc[a * kNAngZ + 2 * zp] = h.x;
+          acc[a * kNAngZ + 2 * zp + 1] = h.y;
+        }
+      hw_reduce_scatter<kNAng>(acc, hl);
+      if (live) put2(f0, 2.f * acc[0], 2.f * acc[1]);
+    };
+    if (S <= 2) {
+#pragma unroll 1
+      for (int s1 = 0; s1 < S; ++s1)
+#pragma unroll 1
+        for (int s2 = s1; s2 < S; ++s2) ang_block(s1, s2);
+    } else {
+      // wide descriptors: most blocks of a row are empty.  The row's angular
+      // features are zeroed in 16-byte pieces, then only the blocks with pairs
+      // in either row of the warp are evaluated (lane b tests block b).
+      if (live) {
+        const int fa = kNRad * S;
+        if (mode == kGFp32) {
+          for (int f = fa + 4 * hl; f < D; f += 64) *reinterpret_cast<float4*>(Grow + f) = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else if (mode == kGBf16) {
+          for (int f = fa + 8 * hl; f < D; f += 128) *reinterpret_cast<uint4*>(Gh + gh_offset(row, f, D)) = make_uint4(0u, 0u, 0u, 0u);
+        } else {
+          for (int f = fa + 16 * hl; f < D; f += 256) *reinterpret_cast<uint4*>(Gh + gh8_offset(row, f, D)) = make_uint4(0u, 0u, 0u, 0u);
+        }
+      }
+      __syncwarp();  // the zeros land before the blocks' values
+      constexpr int NB = S * (S + 1) / 2;
+      const RowCounts* rc0 = rc - half;  // the counts of the warp's two rows
+#pragma unroll
+      for (int b0 = 0; b0 < NB; b0 += 32) {
+        const int b = b0 + lane;
+        int s1 = 0, s2 = 0;
+#pragma unroll
+        for (int q = 0, st = 0; q < S; st += S - q, ++q)
+          if (b >= st) {
+            s1 = q;
+            s2 = q + (b - st);
+          }
+        bool any = false;
+        if (b < NB) {
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            const int n1 = rc0[hh].na[s1], n2 = rc0[hh].na[s2];
+            any |= (s1 == s2 ? n1 * (n1 - 1) / 2 : n1 * n2) > 0;
+          }
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, any);
+        while (todo) {  // warp-uniform
+          const int bb = b0 + __ffs(todo) - 1;
+          todo &= todo - 1u;
+          int t1 = 0, t2 = 0;
+#pragma unroll
+          for (int q = 0, st = 0; q < S; st += S - q, ++q)
+            if (bb >= st) {
+              t1 = q;
+              t2 = q + (bb - st);
+            }
+          ang_block(t1, t2);
+        }
       }
     }
     __syncwarp();
