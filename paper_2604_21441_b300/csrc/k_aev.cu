@@ -562,8 +562,13 @@ struct PairBlock {
 constexpr int kBwdMatCap = 32;
 __host__ __device__ inline int bwd_mat_cap(int cap_a) { return cap_a < kBwdMatCap ? cap_a : kBwdMatCap; }
 __host__ __device__ inline size_t bwd_mat_f4(int mc) { return ((size_t)mc * (mc + 1) * 2 + 3) / 4; }
+// dE/dG entries a warp keeps in shared memory: the whole row, or from five
+// species on (D >= 560) only the radial blocks, the angular weights being read
+// through the L1 cache (the smaller footprint keeps four blocks per SM)
+__host__ __device__ constexpr bool bwd_ang_global(int S) { return S >= 5; }
+__host__ __device__ constexpr int bwd_wsm_floats(int S) { return bwd_ang_global(S) ? kNRad * S : desc_len(S); }
 __host__ __device__ inline size_t bwd_warp_f4(int cap_a, int cap_r, int S) {
-  return 27 + 2 * (size_t)cap_a + bwd_mat_f4(bwd_mat_cap(cap_a)) + (size_t)desc_len(S) / 4 +
+  return 27 + 2 * (size_t)cap_a + bwd_mat_f4(bwd_mat_cap(cap_a)) + (size_t)bwd_wsm_floats(S) / 4 +
          ((size_t)3 * cap_r + 3) / 4 + ((size_t)cap_r + 3) / 4 + (sizeof(PairBlock) * (S * (S + 1) / 2) + 15) / 16;
 }
 
@@ -584,7 +589,7 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
   float2* mat = reinterpret_cast<float2*>(aux + ca);  // [ca][ca + 1]
   const int mc = bwd_mat_cap(ca), ms = mc + 1;
   float* wsm = reinterpret_cast<float*>(aux + ca + bwd_mat_f4(mc));
-  float* fsl = wsm + D;
+  float* fsl = wsm + bwd_wsm_floats(S);
   int* origs = reinterpret_cast<int*>(reinterpret_cast<float4*>(fsl) + (3 * cr + 3) / 4);
   PairBlock* blk = reinterpret_cast<PairBlock*>(reinterpret_cast<float4*>(origs) + (cr + 3) / 4);
 
@@ -732,9 +737,11 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
       __syncwarp();  // the block table is in shared memory
       const int nr_l = __shfl_sync(FM, cnt_l, (lane >> 2) & (kMaxS - 1));
       if (lane < 4 * S && nr_l > 0) w4s[lane] = dg[lane];
-      for (int f = lane; f < 8 * nbe; f += 32) {
-        const int o = (blk[f >> 3].wo >> 2) + (f & 7);
-        w4s[o] = dg[o];
+      if (!bwd_ang_global(S)) {
+        for (int f = lane; f < 8 * nbe; f += 32) {
+          const int o = (blk[f >> 3].wo >> 2) + (f & 7);
+          w4s[o] = dg[o];
+        }
       }
     }
     const int* lr = ws.nbr_r + (size_t)row * cr;
@@ -832,7 +839,7 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
           Bq[a] = -2.f * P.eta_a * x * Be[a];
         }
         const f2 uc2 = f2_make(uc, uc), sn2 = f2_make(sn, sn), nucisn2 = f2_make(-ucisn, -ucisn);
-        const float* wb = wsm + pb.wo;
+        const float* wb = (bwd_ang_global(S) ? ws.dEdG + (size_t)row * D : wsm) + pb.wo;
         f2 X2[kNAngR], Y2[kNAngR];
 #pragma unroll
         for (int zp = 0; zp < kNAngZ / 2; ++zp) {
@@ -862,7 +869,8 @@ __global__ void __launch_bounds__(128, 4) k_aev_bwd(const EvalIO* __restrict__ i
           const f2 dA = f2_mul(pm1, f2_fma(nucisn2, hsz, hcz));  // d(base^zeta)/dc / (0.95 zeta)
 #pragma unroll
           for (int a = 0; a < kNAngR; ++a) {
-            const float4 w4 = reinterpret_cast<const float4*>(wb + a * kNAngZ)[zp >> 1];
+            const float4* wp = reinterpret_cast<const float4*>(wb + a * kNAngZ) + (zp >> 1);
+            const float4 w4 = bwd_ang_global(S) ? __ldg(wp) : *wp;
             const f2 w2 = (zp & 1) ? f2_make(w4.z, w4.w) : f2_make(w4.x, w4.y);
             if (zp == 0) {
               X2[a] = f2_mul(w2, pw);
