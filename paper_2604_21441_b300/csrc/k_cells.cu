@@ -18,21 +18,48 @@ namespace nnp {
 // The four binning steps are device functions over (first thread, thread
 // stride), so that small systems run them in one block (k_cells_small) and
 // large ones as four grid-wide kernels.
+//
+// stage (k_bin; nullptr in k_cells_small): 48 double2 of shared memory per
+// warp.  With it, a warp whose 32 atoms are all present reads their 768 bytes
+// of positions as 48 aligned 16-byte pieces and redistributes them through
+// shared memory: whole 128-byte requests, which matters most when the
+// positions are page-locked host memory read over PCIe.
 __device__ __forceinline__ void bin_atoms(const EvalIO* __restrict__ io, const SysDesc* __restrict__ sys,
                                           const signed char* __restrict__ zlut, const Workspace& ws,
-                                          long long tid0, long long stride) {
+                                          long long tid0, long long stride, double2* stage) {
   const long long n = io->n_atoms;
   const int TC = io->total_cells;
   const int nsys = io->n_sys;
+  const int lane = threadIdx.x & 31;
+  const bool vec = stage != nullptr && (reinterpret_cast<uintptr_t>(io->pos) & 15) == 0;
   for (long long q = tid0; q < nsys; q += stride) io->energies[q] = 0.0;
-  for (long long a = tid0; a < n; a += stride) {
+  // the lanes of a warp go through the loop together (stride is a multiple of 32)
+  for (long long a = tid0; a - lane < n; a += stride) {
+    double p[3];
+    if (vec && a - lane + 32 <= n) {
+      const double2* src = reinterpret_cast<const double2*>(io->pos + 3 * (a - lane));
+      const double2 c0 = src[lane];
+      const double2 c1 = lane < 16 ? src[32 + lane] : make_double2(0.0, 0.0);
+      stage[lane] = c0;
+      if (lane < 16) stage[32 + lane] = c1;
+      __syncwarp();
+      const double* sp3 = reinterpret_cast<const double*>(stage) + 3 * lane;
+      p[0] = sp3[0];
+      p[1] = sp3[1];
+      p[2] = sp3[2];
+      __syncwarp();  // the stage is rewritten in the next iteration
+    } else if (a < n) {
+      p[0] = io->pos[3 * a];
+      p[1] = io->pos[3 * a + 1];
+      p[2] = io->pos[3 * a + 2];
+    }
+    if (a >= n) continue;
     int lo = 0, hi = nsys - 1;
     while (lo < hi) {
       int mid = (lo + hi + 1) >> 1;
       if (sys[mid].atom_begin <= a) lo = mid; else hi = mid - 1;
     }
     const SysDesc& sd = sys[lo];
-    double p[3] = {io->pos[3 * a], io->pos[3 * a + 1], io->pos[3 * a + 2]};
     const bool finite = isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]);
     if (!finite) {
       atomicOr(&ws.flags[kFlagNonFinite], 1);
@@ -95,7 +122,9 @@ __device__ __forceinline__ void bin_atoms(const EvalIO* __restrict__ io, const S
 
 __global__ void k_bin(const EvalIO* __restrict__ io, const SysDesc* __restrict__ sys,
                       const signed char* __restrict__ zlut, Workspace ws) {
-  bin_atoms(io, sys, zlut, ws, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+  __shared__ double2 s_pos[8][48];  // blocks of 256 threads
+  bin_atoms(io, sys, zlut, ws, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x,
+            s_pos[(threadIdx.x >> 5) & 7]);
 }
 
 // One block of 1024 threads.  bin_start[b] = first row of bin b, with each
@@ -337,7 +366,7 @@ __global__ void __launch_bounds__(1024) k_cells_small(const EvalIO* __restrict__
                                                       const signed char* __restrict__ zlut, int S, int sort,
                                                       Workspace ws) {
   extern __shared__ int s_dyn_cells[];  // [kScanSmemBinsSmall] scan, then [32][kSortCap] sort
-  bin_atoms(io, sys, zlut, ws, threadIdx.x, 1024);
+  bin_atoms(io, sys, zlut, ws, threadIdx.x, 1024, nullptr);
   __syncthreads();
   scan_bins(io, S, ws, s_dyn_cells, kScanSmemBinsSmall);
   __syncthreads();
