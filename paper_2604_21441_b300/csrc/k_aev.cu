@@ -454,9 +454,10 @@ __global__ void __launch_bounds__(256, 3) k_aev_fwd(const SysDesc* __restrict__ 
 #pragma unroll 1
         for (int s2 = s1; s2 < S; ++s2) ang_block(s1, s2);
     } else {
-      // wide descriptors: most blocks of a row are empty.  The row's angular
-      // features are zeroed in 16-byte pieces, then only the blocks with pairs
-      // in either row of the warp are evaluated (lane b tests block b).
+      // wide descriptors: when only some of the elements are present, most
+      // blocks of a row are empty.  The row's angular features are zeroed in
+      // 16-byte pieces, then only the blocks with pairs in either row of the
+      // warp are evaluated (lane b tests block b).
       if (live) {
         const int fa = kNRad * S;
         if (mode == kGFp32) {
