@@ -15,6 +15,8 @@ set of the ANI-2x model), and of the wide-descriptor tensor-core network.
 * FP8 (E4M3 forward GEMMs) of the wide-descriptor network at three, four and
   seven species, one network and a two-member ensemble, against the oracle
   within the FP8 bounds below;
+* eight species (D = 1,280, 36 species-pair blocks: the kernels' block tables
+  in two rounds of 32 lanes) in FP32 and BF16 against the oracle;
 * the FP8 form refuses one species (D = 48) and the no-allocation entry point
   more species than it takes (force matching takes all eight:
   tests/test_gpu_force_match.py).
@@ -197,6 +199,38 @@ def test_bf16_wide_descriptor(P, oracle_mod, Zs):
     assert np.sqrt((dF ** 2).mean()) <= F_RMS_BF16
     Ei = pot.atom_energies(s.n)
     assert abs(Ei.sum() - E) <= 1e-6 * np.abs(Ei).sum()
+
+
+Z8 = (1, 6, 7, 8, 9, 15, 16, 17)  # eight species, the kernels' maximum: 36 species-pair blocks
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_eight_species(P, oracle_mod, precision):
+    """Eight elements (D = 1,280): more species-pair blocks (36) than a warp
+    has lanes, so the descriptor kernels build and scan their block tables in
+    two rounds of 32; the backward reads the angular weights through L1.
+    Against the oracle within the FP32 or the BF16 bounds."""
+    S = len(Z8)
+    D = 16 * S + 32 * S * (S + 1) // 2
+    s = synth.hcno_box(781, L=16.0, n_cluster_atoms=200, max_waters=40,
+                       elements=np.array(Z8, dtype=np.int32), probs=np.full(S, 1.0 / S))
+    assert set(np.unique(s.Z).tolist()) == set(Z8)
+    w = weights32(S, D, 782, 783)
+    pot = _pot(P, w, Zs=Z8, precision=precision)
+    E, F = pot.eval(s.pos, s.Z, box9(s.box))
+    p = oracle_mod.Params(atomic_numbers=Z8)
+    Er, Eir, Fr, _ = oracle_mod.energy_forces(oracle_mod.Model(p, w), s.pos, p.species_of(s.Z), s.box)
+    dF = F - Fr
+    print(f"{precision} 8 species (D = {D}), {s.n} atoms: rel E err {energy_error(E, Er, Eir):.2e},"
+          f" max|dF| {np.abs(dF).max():.3e}, rms dF {np.sqrt((dF ** 2).mean()):.3e}")
+    if precision == "fp32":
+        assert energy_error(E, Er, Eir) <= E_REL_TOL
+        assert np.abs(dF).max() <= F_ABS_TOL
+    else:
+        assert energy_error(E, Er, Eir) <= E_BF16
+        assert np.abs(dF).max() <= F_MAX_BF16
+        assert np.sqrt((dF ** 2).mean()) <= F_RMS_BF16
+    pot.close()
 
 
 def test_bf16_seven_species_workload_and_ensemble(P):
