@@ -257,13 +257,14 @@ def test_bf16_seven_species_workload_and_ensemble(P):
         assert np.sqrt((dF ** 2).mean()) <= F_RMS_BF16
 
 
-@pytest.mark.parametrize("Zs,M", [((1, 6, 8), 1), ((1, 6, 7, 8), 1), (Z7, 1), (Z7, 2)])
+@pytest.mark.parametrize("Zs,M", [((1, 6, 8), 1), ((1, 6, 7, 8), 1), (Z7, 1), (Z7, 2), (Z8, 1), (Z8, 2)])
 def test_fp8_wide_descriptor(P, oracle_mod, Zs, M):
     """FP8 form of the wide-descriptor network (E4M3 forward GEMMs, BF16
     backward; per-member calibrated activation scales and per-column weight
     scales) against the oracle, one network and a two-member ensemble (whose
-    dE/dG is the one product over the members).  D = 240 and 1,008 are not
-    multiples of 32: the last layer-1 MMA reads zeros past D."""
+    dE/dG is the one product over the members), up to eight species
+    (D = 1,280).  D = 240 and 1,008 are not multiples of 32: the last
+    layer-1 MMA reads zeros past D."""
     S = len(Zs)
     D = 16 * S + 32 * S * (S + 1) // 2
     s = synth.hcno_box(761 + S, L=16.0, n_cluster_atoms=160, max_waters=60,
